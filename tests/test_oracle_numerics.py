@@ -1,0 +1,175 @@
+"""Pins of the oracle's FP64 arithmetic against facts other than itself.
+
+* diagonal matrices with power-of-4 entries and the identity: IEEE sqrt is
+  exact, so L = diag(2^e) bit-exactly;
+* A = L0 L0^T with L0 unit lower and entries in {-1, 0, 1}: every
+  intermediate is an integer below 2^53, so any summation order returns L0
+  bit-exactly, and the solve of A x = A x0 returns x0 bit-exactly;
+* LAPACK (numpy.linalg.cholesky) and numpy's solve within FP64 bounds;
+* tiled vs untiled oracle (different summation order) within 1e-13;
+* backward errors <= 1e-14 on the small synthetic workload;
+* non-SPD inputs report the LAPACK info column;
+* the metrics are zero on exact factors and grow with planted errors;
+* the tiled GEMM DAG equals the untiled triple loop bit for bit (same order of
+  the k sum) and numpy's matmul within FP64 bounds.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2308_15964_b300 import inputs
+
+
+def unit_lower(n, seed):
+    rng = np.random.default_rng(seed)
+    L = np.tril(rng.integers(-1, 2, size=(n, n)).astype(np.float64), -1)
+    np.fill_diagonal(L, 1.0)
+    return L
+
+
+def lower(a):
+    return np.tril(a)
+
+
+@pytest.mark.parametrize("n,b", [(1, 1), (7, 7), (64, 16), (100, 32), (130, 64)])
+def test_diagonal_power_of_four(n, b):
+    e = (np.arange(n) % 9) - 4
+    A = np.diag(4.0 ** e)
+    L = A.copy()
+    assert O.tiled_cholesky(L, b) == 0
+    assert np.array_equal(lower(L), np.diag(2.0 ** e))
+    L2 = A.copy()
+    assert O.potrf(L2) == 0
+    assert np.array_equal(lower(L2), np.diag(2.0 ** e))
+
+
+@pytest.mark.parametrize("n,b,nrhs", [(48, 16, 1), (96, 32, 3), (100, 24, 2), (64, 64, 1)])
+def test_integer_factor_exact(n, b, nrhs):
+    L0 = unit_lower(n, n)
+    A = L0 @ L0.T                        # exact: integer entries |a| <= n
+    x0 = np.random.default_rng(1).integers(-3, 4, size=(n, nrhs)).astype(np.float64)
+    B = A @ x0
+    L = A.copy()
+    X = B.copy()
+    assert O.tiled_cholesky(L, b, X) == 0
+    assert np.array_equal(lower(L), L0)
+    assert np.array_equal(X, x0)
+    # the strict upper triangle of the diagonal tiles is untouched
+    T = -(-n // b)
+    for k in range(T):
+        r = slice(k * b, min(n, k * b + b))
+        assert np.array_equal(np.triu(L[r, r], 1), np.triu(A[r, r], 1))
+    L2 = A.copy()
+    X2 = B.copy()
+    assert O.potrf(L2) == 0
+    O.solve_untiled(L2, X2)
+    assert np.array_equal(lower(L2), L0) and np.array_equal(X2, x0)
+
+
+def test_against_lapack_and_tiled_vs_untiled():
+    n, b = 512, 64
+    A = inputs.spd_matrix(n, 1.0, seed=1).numpy()
+    Bv = inputs.rhs(n, 1, seed=1).numpy()
+    Lt, X = A.copy(), Bv.copy()
+    assert O.tiled_cholesky(Lt, b, X) == 0
+    Lu = A.copy()
+    assert O.potrf(Lu) == 0
+    Llapack = np.linalg.cholesky(A)
+    eps = np.abs(lower(Lt) - Llapack).max() / np.abs(Llapack).max()
+    assert eps <= 1e-13
+    eps_tu = np.abs(lower(Lt) - lower(Lu)).max() / np.abs(lower(Lu)).max()
+    assert eps_tu <= 1e-13
+    assert O.factor_backward_error(A, Lt) <= 1e-14
+    eta = O.solve_backward_error(A, X, Bv)
+    assert eta.max() <= 1e-14
+    xs = np.linalg.solve(A, Bv)
+    assert np.abs(X - xs).max() / np.abs(xs).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n,b", [(96, 32), (100, 32), (33, 8)])
+def test_ragged_tiles(n, b):
+    A = inputs.spd_matrix(n, 1.0, seed=11).numpy()
+    Bv = inputs.rhs(n, 2, seed=11).numpy()
+    L, X = A.copy(), Bv.copy()
+    assert O.tiled_cholesky(L, b, X) == 0
+    assert np.abs(lower(L) - np.linalg.cholesky(A)).max() <= 1e-13
+    assert O.solve_backward_error(A, X, Bv).max() <= 1e-14
+
+
+def test_not_spd_info():
+    n, b = 96, 32
+    A = np.eye(n)
+    A[70, 70] = -1.0                    # pivot of global column 71 fails
+    L = A.copy()
+    assert O.tiled_cholesky(L, b) == 71
+    L2 = A.copy()
+    assert O.potrf(L2) == 71
+    A = np.eye(n)
+    A[5, 5] = np.nan
+    assert O.tiled_cholesky(A.copy(), b) == 6
+    A = inputs.spd_matrix(64, 1.0, seed=3).numpy()
+    A[40, 40] = -5.0
+    assert O.tiled_cholesky(A.copy(), 16) == O.potrf(A.copy()) == 41
+
+
+def test_metrics_zero_and_planted():
+    n = 64
+    L0 = unit_lower(n, 5)
+    A = L0 @ L0.T
+    assert O.factor_backward_error(A, L0) == 0.0
+    v = inputs.gaussian(n, 9)
+    assert O.freivalds(A, L0, v) <= 1e-16     # only the rounding of L^T v
+    x0 = np.ones((n, 1))
+    assert O.solve_backward_error(A, x0, A @ x0).max() == 0.0
+    Lbad = L0.copy()
+    Lbad[40, 3] += 1e-6
+    assert O.factor_backward_error(A, Lbad) > 1e-9
+    assert O.freivalds(A, Lbad, v) > 1e-10
+    xbad = x0.copy()
+    xbad[7, 0] += 1e-6
+    assert O.solve_backward_error(A, xbad, A @ x0).max() > 1e-9
+    # closed form: a single perturbed entry d of L gives ||A - LL^T||_F of
+    # roughly sqrt(2) * d * ||row|| -- check the order of magnitude only
+    d = 1e-6
+    beta = O.factor_backward_error(A, Lbad)
+    assert 0.1 * d / np.linalg.norm(A) < beta < 100 * d * n / np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("n,b", [(64, 16), (96, 32), (70, 32)])
+def test_gemm_dag_exact_order(n, b):
+    A = inputs.uniform((n, n), 3).numpy()
+    B = inputs.uniform((n, n), 4).numpy()
+    C = inputs.uniform((n, n), 5).numpy()
+    Ct, Cu = C.copy(), C.copy()
+    assert O.tiled_gemm(A, B, Ct, b) == 0
+    O.gemm_untiled(A, B, Cu)
+    assert np.array_equal(Ct, Cu)
+    ref = C + A @ B
+    assert np.abs(Ct - ref).max() <= 4 * n * 2.2e-16 * (np.abs(A) @ np.abs(B)).max()
+    Cc = C.copy()
+    assert O.tiled_gemm(A, B, Cc, b, commutative=True) == 0
+    assert np.array_equal(Cc, Cu)
+
+
+def test_generator_bits():
+    # splitmix64 against its scalar definition; exactness of the SPD recipe
+    import torch
+    c = torch.arange(0, 50, dtype=torch.int64)
+    got = inputs.splitmix64(c, 12345).numpy().view(np.uint64)
+    ref = np.array([inputs.splitmix64_ref(12345, i) for i in range(50)], dtype=np.uint64)
+    assert np.array_equal(got, ref)
+    # first outputs of splitmix64 seeded with 0 (published test vector of the
+    # reference implementation, Vigna's splitmix64.c with x = 0)
+    assert inputs.splitmix64_ref(0, 0) == 0xE220A8397B1DCDAF
+    assert inputs.splitmix64_ref(0, 1) == 0x6E789E6AA1B965F4
+    u = inputs.uniform((10000,), 7).numpy()
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.05
+    n = 96
+    A = inputs.spd_matrix(n, 0.5, 2).numpy()
+    assert np.array_equal(A, A.T)
+    K = inputs.int_lattice(n, n, 2).numpy()
+    assert K.min() >= -127 and K.max() <= 127
+    G = K @ K.T
+    ref = G / float(127 * 127 * n)
+    ref[np.diag_indices(n)] += 0.5
+    assert np.array_equal(A, ref)
