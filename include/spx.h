@@ -1,0 +1,238 @@
+/*
+ * spx.h - C ABI of the B300 device-scheduled STF tile-task library.
+ *
+ * The library runs a sequential-task-flow (STF) graph of tile tasks on one
+ * GPU.  A single host thread inserts tasks with their data accesses; the
+ * library derives the dependencies on the device (successor CSR + in-degree
+ * counters in HBM) and executes the graph in one persistent kernel whose CTAs
+ * pop ready tasks from a device work queue, run the tile operation and
+ * release the successors.  Model: Specx, arXiv 2308.15964, section "Task graph
+ * description" (task graph object, task insertion with SpRead / SpWrite /
+ * SpCommutativeWrite, priorities) and section "Internal implementation"
+ * (address-keyed data handles with ordered dependency lists).  The tile
+ * operations are the four task types of the paper's tiled Cholesky (section
+ * "Numerical applications": POTRF, TRSM, SYRK, GEMM), the tiled GEMM whose
+ * tasks depend on the blocks of C, and the block triangular solves.
+ *
+ * Conventions for every call:
+ *   - Return value: SPX_OK (0) on success, SPX_NOT_SPD (1) when a POTRF met a
+ *     non-positive pivot, a negative SPX_ERR_* code otherwise.  A failing call
+ *     leaves the graph unchanged unless stated.
+ *   - Pointers named dev_* are CUDA device pointers; every other pointer is a
+ *     host pointer.  Streams are cudaStream_t passed as void*.
+ *   - Matrices are row-major FP64 unless a dtype says otherwise: element
+ *     (r, c) of a tile with leading dimension ld is at ptr[r*ld + c].
+ *   - Ownership: the caller owns all tile memory and must keep it alive and
+ *     untouched by other work until spx_graph_wait returns (paper, section
+ *     "Task insertion": objects must outlive the tasks that use them).  The
+ *     graph owns its own metadata (host and device arrays).
+ *   - Not thread-safe per graph: one host thread drives a graph.
+ */
+#ifndef SPX_H_
+#define SPX_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spx_graph* spx_graph_t;
+
+/* Access modes (paper, section "Task insertion").
+ *   SPX_READ               the task only reads the data.
+ *   SPX_WRITE              the task reads and/or writes; ordered and exclusive.
+ *   SPX_COMMUTATIVE_WRITE  reads and writes, but the tasks of one run of
+ *                          commutative writes inserted one after another may
+ *                          execute in any order, one at a time.
+ * A task that names the same tile twice gets the merged mode: READ+READ =
+ * READ, COMM+COMM = COMM, anything else = WRITE. */
+enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
+
+/* Tile operations.  Operand order (the handles[] of spx_task_insert) and the
+ * required access mode of each operand are fixed per op:
+ *   SPX_OP_POTRF        (A_kk:W)                A_kk = L L^T, lower L written
+ *                                               over the lower triangle; the
+ *                                               strict upper triangle is kept.
+ *   SPX_OP_TRSM         (L_kk:R, A_ik:W)        A_ik <- A_ik L_kk^{-T}
+ *   SPX_OP_SYRK         (L_ik:R, A_ii:W)        A_ii <- A_ii - L_ik L_ik^T
+ *                                               (lower triangle only)
+ *   SPX_OP_GEMM_NT_SUB  (L_ik:R, L_jk:R, A_ij:W) A_ij <- A_ij - L_ik L_jk^T
+ *   SPX_OP_GEMM_NN_ADD  (A_ik:R, B_kj:R, C_ij:W|C) C_ij <- C_ij + A_ik B_kj
+ *   SPX_OP_TRSM_L_FWD   (L_kk:R, X_k:W)         X_k <- L_kk^{-1} X_k
+ *   SPX_OP_GEMM_FWD     (L_ik:R, X_k:R, X_i:W)  X_i <- X_i - L_ik X_k
+ *   SPX_OP_TRSM_LT_BWD  (L_kk:R, X_k:W)         X_k <- L_kk^{-T} X_k
+ *   SPX_OP_GEMM_BWD     (L_ki:R, X_k:R, X_i:W)  X_i <- X_i - L_ki^T X_k
+ *   SPX_OP_NOP          any handles, any modes  does nothing (graph tests)
+ *   SPX_OP_SPIN         any handles, any modes  busy-waits arg nanoseconds
+ * A write operand may also be given as SPX_COMMUTATIVE_WRITE; such tasks
+ * run as one part and take per-tile locks in ascending handle order (the
+ * paper locks data handles sorted by address, section "Internal
+ * implementation"). */
+enum {
+  SPX_OP_POTRF = 0,
+  SPX_OP_TRSM = 1,
+  SPX_OP_SYRK = 2,
+  SPX_OP_GEMM_NT_SUB = 3,
+  SPX_OP_GEMM_NN_ADD = 4,
+  SPX_OP_TRSM_L_FWD = 5,
+  SPX_OP_GEMM_FWD = 6,
+  SPX_OP_TRSM_LT_BWD = 7,
+  SPX_OP_GEMM_BWD = 8,
+  SPX_OP_NOP = 9,
+  SPX_OP_SPIN = 10,
+  SPX_NUM_OPS = 11
+};
+
+/* Arithmetic of a task.  SPX_F64: FP64 throughout. */
+enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2 };
+
+/* Element type of a registered tile. */
+enum { SPX_DT_F64 = 0, SPX_DT_F32 = 1, SPX_DT_BF16 = 2 };
+
+/* Executors.  SPX_EXEC_PERSISTENT is the product: one persistent kernel with a
+ * device work queue.  SPX_EXEC_PER_TASK is the comparison baseline: one kernel
+ * launch per task, on the given stream, in insertion order (a valid
+ * topological order of any STF graph), running the same tile code. */
+enum { SPX_EXEC_PERSISTENT = 0, SPX_EXEC_PER_TASK = 1 };
+
+/* Status codes. */
+enum {
+  SPX_OK = 0,
+  SPX_NOT_SPD = 1,            /* a POTRF pivot was <= 0 or NaN; info = column */
+  SPX_ERR_INVALID_ARG = -1,   /* bad pointer, size, op, mode or operand shape */
+  SPX_ERR_BAD_HANDLE = -2,    /* unknown tile handle or task id */
+  SPX_ERR_STATE = -3,         /* call not allowed in the graph's state */
+  SPX_ERR_OOM = -4,           /* host or device allocation failed */
+  SPX_ERR_QUEUE_FULL = -5,    /* device work queue capacity exceeded */
+  SPX_ERR_TIMEOUT = -6,       /* device watchdog or host wait timeout */
+  SPX_ERR_CUDA = -7,          /* a CUDA runtime call failed */
+  SPX_ERR_BAD_OP = -8,        /* device met an unknown op (corrupt graph) */
+  SPX_ERR_NO_DEVICE = -9      /* no usable CUDA device */
+};
+
+/* Graph configuration.  Zero fields take defaults. */
+typedef struct {
+  int num_ctas;               /* persistent CTAs; 0 = resident maximum        */
+  int executor;               /* SPX_EXEC_*                                   */
+  int trace;                  /* 1 = record per-task timestamps and SM ids    */
+  int no_split;               /* 1 = run every task as a single part          */
+  unsigned long long watchdog_ns; /* device gives up after this long without
+                                 finishing a task part; 0 = 10 s              */
+  long long queue_capacity;   /* entries per priority queue; 0 = exact size   */
+} spx_graph_config_t;
+
+/* Fill *cfg with the defaults. */
+void spx_config_default(spx_graph_config_t* cfg);
+
+/* Create an empty graph (paper, section "Task graph description": the task
+ * graph object is separate from the engine that runs it).  cfg may be NULL.
+ * No device memory is touched until the first execute/derive.
+ * Errors: SPX_ERR_INVALID_ARG (out NULL or bad cfg), SPX_ERR_OOM. */
+int spx_graph_create(spx_graph_t* out, const spx_graph_config_t* cfg);
+
+/* Register a tile (a data object of the STF model) and get its handle.
+ *   dev_ptr  device address of element (0,0); it is also the dependency key
+ *            (paper, section "Internal implementation": the address of the
+ *            object is the key of its data handle).  Registering the same
+ *            address again returns the same handle when rows/cols/ld/dtype
+ *            agree, SPX_ERR_INVALID_ARG otherwise.  Overlapping tiles with
+ *            different addresses are distinct handles (not detected).
+ *   rows, cols >= 1; ld >= cols; dtype SPX_DT_*; FP64 ops need SPX_DT_F64.
+ *   lowp_ptr / lowp_ld: optional low-precision copy of the tile (NULL, 0).
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE (graph already executed). */
+int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
+                      void* lowp_ptr, int lowp_ld, unsigned* out_handle);
+
+/* Insert one task (paper, section "Task insertion": one thread inserts tasks
+ * with their accesses; the result equals running them in insertion order).
+ *   op        SPX_OP_*; handles[nh] in the op's operand order; modes[nh] the
+ *             access mode of each operand; 1 <= nh <= 16 (NOP/SPIN), fixed
+ *             for the other ops; operand shapes must agree.
+ *   priority  0 = normal, >0 = high (popped first; a hint, paper section
+ *             "Task insertion" / "Scheduling").
+ *   prec      SPX_F64 (other values are accepted only where the op has a
+ *             low-precision form).
+ *   out_task  receives the task id (0, 1, 2, ... in insertion order); may be
+ *             NULL.
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_BAD_HANDLE, SPX_ERR_STATE. */
+int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* modes, int nh,
+                    int priority, int prec, unsigned* out_task);
+
+/* Set a task's integer argument: for POTRF the global column offset of the
+ * tile (info reports offset + local column, 1-based); for SPIN the spin time
+ * in nanoseconds.  Errors: SPX_ERR_BAD_HANDLE, SPX_ERR_STATE. */
+int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg);
+
+/* Derive the dependency DAG on the device (successor CSR sorted ascending,
+ * de-duplicated, and in-degrees) without executing it.  Asynchronous on
+ * stream.  Errors: SPX_ERR_STATE (no tasks), SPX_ERR_OOM, SPX_ERR_CUDA. */
+int spx_graph_derive(spx_graph_t g, void* stream);
+
+/* Derive (if not done) and launch the graph, asynchronously on stream.  The
+ * graph is then running until spx_graph_wait returns.
+ * Errors: SPX_ERR_STATE (running, or empty), SPX_ERR_OOM, SPX_ERR_CUDA. */
+int spx_graph_execute(spx_graph_t g, void* stream);
+
+/* Wait for a running graph.  timeout_ns = 0 waits without a host limit (the
+ * device watchdog still bounds the run).  info (may be NULL) receives the
+ * LAPACK-style column of a failed POTRF, else 0.
+ * Returns SPX_OK, SPX_NOT_SPD, SPX_ERR_TIMEOUT (device watchdog fired, or
+ * host timeout: then the graph stays running and wait may be called again),
+ * SPX_ERR_QUEUE_FULL, SPX_ERR_BAD_OP, SPX_ERR_CUDA, SPX_ERR_STATE. */
+int spx_graph_wait(spx_graph_t g, unsigned long long timeout_ns, int* info);
+
+/* Sizes: tasks, unique edges (valid after derive), accesses, tiles.  Any
+ * output pointer may be NULL. */
+int spx_graph_sizes(spx_graph_t g, long long* ntasks, long long* nedges, long long* naccesses,
+                    long long* ntiles);
+
+/* Copy the derived DAG to host arrays: row_ptr[ntasks+1], col[nedges],
+ * indeg[ntasks] (any may be NULL).  Successors of task u are
+ * col[row_ptr[u] .. row_ptr[u+1]) in ascending order.  Synchronises with the
+ * graph's last stream.  Errors: SPX_ERR_STATE (not derived), SPX_ERR_CUDA. */
+int spx_graph_edges(spx_graph_t g, unsigned* row_ptr, unsigned* col, unsigned* indeg);
+
+/* Execution tickets of the last run: a global counter taken when a task's
+ * first part starts (start[t]) and when its last part ends (end[t]).  For
+ * every edge u->v, end[u] < start[v].  Errors: SPX_ERR_STATE. */
+int spx_graph_tickets(spx_graph_t g, unsigned* start, unsigned* end);
+
+/* Trace of the last run with cfg.trace = 1 (paper, section "Visualization"):
+ * 4 values per task: start ns, end ns (device %globaltimer), SM id of the
+ * first part, number of parts.  Errors: SPX_ERR_STATE (tracing off). */
+int spx_graph_trace(spx_graph_t g, unsigned long long* rec);
+
+/* Counters of the last run: out[0] task parts executed, out[1] queue
+ * high-water mark (entries), out[2] pops that found the queue empty,
+ * out[3] CTAs used, out[4] busy cycles summed over CTAs, out[5] total
+ * cycles summed over CTAs.  n = number of values wanted (<= 6). */
+int spx_graph_stats(spx_graph_t g, long long* out, int n);
+
+/* Write the derived task graph in Graphviz dot format (paper, section
+ * "Visualization", generateDot).  Errors: SPX_ERR_STATE, SPX_ERR_INVALID_ARG
+ * (cannot open path). */
+int spx_graph_write_dot(spx_graph_t g, const char* path);
+
+/* Make an executed graph runnable again with the same DAG (no new
+ * derivation).  The caller restores the tile contents.  Errors: SPX_ERR_STATE. */
+int spx_graph_reset(spx_graph_t g);
+
+/* Drop all tiles and tasks but keep the allocations, so a new graph of a
+ * similar size can be built without new device allocations. */
+int spx_graph_clear(spx_graph_t g);
+
+/* Free the graph.  Waits for a running graph first.  NULL is ignored. */
+void spx_graph_destroy(spx_graph_t g);
+
+/* Static description of a status code. */
+const char* spx_strerror(int code);
+
+/* Library ABI version (incremented on incompatible changes). */
+int spx_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H_ */

@@ -1,0 +1,663 @@
+// Host side of the C ABI: the graph builder (task insertion), device memory
+// management, and the execute / wait / inspect calls.
+//
+// Insertion follows the paper's model (section "Task insertion"; section
+// "Internal implementation"): a task names tiles by address with an access
+// mode; each tile (data handle) keeps the ordered list of the tasks that use
+// it.  Here insertion is O(1) per access: it appends an access record
+// (task, handle, mode, position on the handle's list) and updates three
+// counters per handle that size the device edge buffer exactly.  Dependency
+// derivation itself (groups, edges, de-duplication, CSR, in-degrees) runs on
+// the device (derive.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "spx.h"
+#include "spx_internal.h"
+
+using namespace spx;
+
+namespace {
+
+enum State { kBuilding = 0, kFrozen = 1, kRunning = 2, kDone = 3 };
+
+struct HandleState {
+  uint32_t count = 0;      // accesses so far (next position on the list)
+  int last_mode = -1;      // mode of the last group
+  uint32_t last_size = 0;  // members of the last group
+  uint32_t prev_size = 0;  // members of the group before it
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of the single device allocation (and of the pinned upload mirror
+// for its first region).  Offsets in bytes, 256-aligned.
+struct Layout {
+  size_t tasks, tiles, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
+  size_t queue0, queue1, t_start, ff_end;
+  size_t rs, locks, t_end, trace, zero_end;
+  size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
+      indeg_w, remaining, total;
+};
+
+Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, bool trace) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1), 256);
+    return at;
+  };
+  L.tasks = take(N * sizeof(TaskDesc));
+  L.tiles = take(H * sizeof(TileDesc));
+  L.rec_handle = take(M * 4);
+  L.rec_seq = take(M * 4);
+  L.rec_mode = take(M);
+  L.task_rec = take((N + 1) * 4);
+  L.upload_end = o;
+  L.queue0 = take(Q * 4);
+  L.queue1 = take(Q * 4);
+  L.t_start = take(N * 4);
+  L.ff_end = o;
+  L.rs = take(sizeof(RunState));
+  L.locks = take(H * 4);
+  L.t_end = take(N * 4);
+  L.trace = take(trace ? N * 32 : 0);
+  L.zero_end = o;
+  L.hptr = take((H + 1) * 4);
+  L.s_task = take(M * 4);
+  L.s_mode = take(M);
+  L.s_first = take(M);
+  L.rec_pos = take(M * 4);
+  L.gid = take(M * 4);
+  L.gpos = take((M + 1) * 4);
+  L.ucount = take(N * 4);
+  L.row_ptr = take((N + 1) * 4);
+  L.col = take(E * 4);
+  L.indeg = take(N * 4);
+  L.indeg_w = take(N * 4);
+  L.remaining = take(N * 4);
+  L.total = o;
+  return L;
+}
+
+
+}  // namespace
+
+struct spx_graph {
+  spx_graph_config_t cfg{};
+  int state = kBuilding;
+  bool derived = false;     // device DAG valid
+  bool uploaded = false;    // device copy of the inserted graph valid
+  int last_status = 0;
+  int last_info = 0;
+
+  // inserted graph (host)
+  std::vector<TileDesc> tiles;
+  std::vector<int> tile_dtype;
+  std::unordered_map<uintptr_t, uint32_t> key_to_handle;
+  std::vector<HandleState> hstate;
+  std::vector<TaskDesc> tasks;
+  std::vector<uint32_t> rec_handle, rec_seq, task_rec{0};
+  std::vector<uint8_t> rec_mode;
+  unsigned long long cand_edges = 0;
+  unsigned long long items[2] = {0, 0};  // queue entries per priority
+
+  // device
+  int device = -1;
+  void* dmem = nullptr;
+  size_t dcap = 0;
+  void* pinned = nullptr;   // upload mirror
+  size_t pcap = 0;
+  RunState* host_rs = nullptr;  // pinned copy of the run state
+  cudaEvent_t done_ev = nullptr;
+  cudaStream_t last_stream = nullptr;
+  Layout lay{};
+  DevGraph dg{};
+  long long nedges = -1;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  (void)cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return SPX_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SPX_ERR_NO_DEVICE;
+  return SPX_ERR_CUDA;
+}
+
+// Operand count, shape and mode checks of the built-in ops.
+int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
+                   const unsigned* h, const int* m, int nh) {
+  static const int want_nh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1};
+  if (op == SPX_OP_NOP || op == SPX_OP_SPIN) return SPX_OK;
+  if (nh != want_nh[op]) return SPX_ERR_INVALID_ARG;
+  for (int i = 0; i < nh; ++i) {
+    if (dt[h[i]] != SPX_DT_F64) return SPX_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (h[i] == h[j]) return SPX_ERR_INVALID_ARG;
+  }
+  const int w = nh - 1;  // written operand is the last one
+  if (m[w] != SPX_WRITE && m[w] != SPX_COMMUTATIVE_WRITE) return SPX_ERR_INVALID_ARG;
+  auto R = [&](int i) { return t[h[i]].rows; };
+  auto C = [&](int i) { return t[h[i]].cols; };
+  bool ok = true;
+  switch (op) {
+    case SPX_OP_POTRF: ok = R(0) == C(0); break;
+    case SPX_OP_TRSM: ok = R(0) == C(0) && C(1) == R(0); break;
+    case SPX_OP_SYRK: ok = R(1) == C(1) && R(0) == R(1); break;
+    case SPX_OP_GEMM_NT_SUB: ok = R(0) == R(2) && R(1) == C(2) && C(0) == C(1); break;
+    case SPX_OP_GEMM_NN_ADD: ok = R(0) == R(2) && C(1) == C(2) && C(0) == R(1); break;
+    case SPX_OP_TRSM_L_FWD:
+    case SPX_OP_TRSM_LT_BWD: ok = R(0) == C(0) && R(1) == R(0); break;
+    case SPX_OP_GEMM_FWD: ok = R(0) == R(2) && C(0) == R(1) && C(1) == C(2); break;
+    case SPX_OP_GEMM_BWD: ok = R(0) == R(1) && C(0) == R(2) && C(1) == C(2); break;
+    default: ok = false;
+  }
+  return ok ? SPX_OK : SPX_ERR_INVALID_ARG;
+}
+
+int ensure_device(spx_graph* g) {
+  if (g->device >= 0) return SPX_OK;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int n = 0;
+  e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return SPX_ERR_NO_DEVICE;
+  e = cudaEventCreateWithFlags(&g->done_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaHostAlloc((void**)&g->host_rs, sizeof(RunState), cudaHostAllocDefault);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::memset(g->host_rs, 0, sizeof(RunState));
+  g->device = dev;
+  return SPX_OK;
+}
+
+// Size the device allocation for the inserted graph and upload it.
+int prepare_device(spx_graph* g, cudaStream_t st) {
+  int rc = ensure_device(g);
+  if (rc != SPX_OK) return rc;
+  const size_t N = g->tasks.size(), H = g->tiles.size(), M = g->rec_handle.size();
+  const size_t E = std::max<unsigned long long>(g->cand_edges, 1);
+  size_t Q = std::max<unsigned long long>(std::max(g->items[0], g->items[1]), 1);
+  if (g->cfg.queue_capacity > 0) Q = (size_t)g->cfg.queue_capacity;
+  if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
+  const Layout L = make_layout(N, H, M, E, Q, g->cfg.trace != 0);
+  if (L.total > g->dcap) {
+    if (g->dmem) {
+      cudaError_t e = cudaStreamSynchronize(g->last_stream ? g->last_stream : st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      cudaFree(g->dmem);
+      g->dmem = nullptr;
+      g->dcap = 0;
+    }
+    const size_t want = L.total + L.total / 4;
+    cudaError_t e = cudaMalloc(&g->dmem, want);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g->dcap = want;
+  }
+  if (L.upload_end > g->pcap) {
+    if (g->pinned) {
+      cudaStreamSynchronize(g->last_stream ? g->last_stream : st);
+      cudaFreeHost(g->pinned);
+      g->pinned = nullptr;
+      g->pcap = 0;
+    }
+    const size_t want = L.upload_end + L.upload_end / 4;
+    cudaError_t e = cudaHostAlloc(&g->pinned, want, cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g->pcap = want;
+  } else if (g->last_stream) {
+    // the previous upload may still be reading the mirror
+    cudaError_t e = cudaStreamSynchronize(g->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  char* P = (char*)g->pinned;
+  std::memcpy(P + L.tasks, g->tasks.data(), N * sizeof(TaskDesc));
+  std::memcpy(P + L.tiles, g->tiles.data(), H * sizeof(TileDesc));
+  std::memcpy(P + L.rec_handle, g->rec_handle.data(), M * 4);
+  std::memcpy(P + L.rec_seq, g->rec_seq.data(), M * 4);
+  std::memcpy(P + L.rec_mode, g->rec_mode.data(), M);
+  std::memcpy(P + L.task_rec, g->task_rec.data(), (N + 1) * 4);
+  cudaError_t e = cudaMemcpyAsync(g->dmem, g->pinned, L.upload_end, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+
+  char* D = (char*)g->dmem;
+  DevGraph& d = g->dg;
+  d = DevGraph{};
+  d.ntasks = (uint32_t)N;
+  d.ntiles = (uint32_t)H;
+  d.nrec = (uint32_t)M;
+  d.ecap = (uint32_t)E;
+  d.qcap = (uint32_t)Q;
+  d.trace = g->cfg.trace ? 1u : 0u;
+  d.watchdog_ns = g->cfg.watchdog_ns ? g->cfg.watchdog_ns : 10000000000ull;
+  d.tasks = (const TaskDesc*)(D + L.tasks);
+  d.tiles = (const TileDesc*)(D + L.tiles);
+  d.rec_handle = (const uint32_t*)(D + L.rec_handle);
+  d.rec_seq = (const uint32_t*)(D + L.rec_seq);
+  d.rec_mode = (const uint8_t*)(D + L.rec_mode);
+  d.task_rec = (const uint32_t*)(D + L.task_rec);
+  d.queue[0] = (uint32_t*)(D + L.queue0);
+  d.queue[1] = (uint32_t*)(D + L.queue1);
+  d.t_start = (uint32_t*)(D + L.t_start);
+  d.rs = (RunState*)(D + L.rs);
+  d.locks = (uint32_t*)(D + L.locks);
+  d.t_end = (uint32_t*)(D + L.t_end);
+  d.trace_rec = g->cfg.trace ? (unsigned long long*)(D + L.trace) : nullptr;
+  d.hptr = (uint32_t*)(D + L.hptr);
+  d.s_task = (uint32_t*)(D + L.s_task);
+  d.s_mode = (uint8_t*)(D + L.s_mode);
+  d.s_first = (uint8_t*)(D + L.s_first);
+  d.rec_pos = (uint32_t*)(D + L.rec_pos);
+  d.gid = (uint32_t*)(D + L.gid);
+  d.gpos = (uint32_t*)(D + L.gpos);
+  d.ucount = (uint32_t*)(D + L.ucount);
+  d.row_ptr = (uint32_t*)(D + L.row_ptr);
+  d.col = (uint32_t*)(D + L.col);
+  d.indeg = (uint32_t*)(D + L.indeg);
+  d.indeg_w = (uint32_t*)(D + L.indeg_w);
+  d.remaining = (uint32_t*)(D + L.remaining);
+  g->lay = L;
+  g->uploaded = true;
+  g->derived = false;
+  g->nedges = -1;
+  return SPX_OK;
+}
+
+// Queues to "empty", tickets, locks and run state to zero.
+int reset_run_state(spx_graph* g, cudaStream_t st) {
+  const Layout& L = g->lay;
+  char* D = (char*)g->dmem;
+  cudaError_t e = cudaMemsetAsync(D + L.queue0, 0xFF, L.ff_end - L.queue0, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D + L.rs, 0, L.zero_end - L.rs, st);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void spx_config_default(spx_graph_config_t* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->executor = SPX_EXEC_PERSISTENT;
+  cfg->watchdog_ns = 10000000000ull;
+}
+
+int spx_abi_version(void) { return 1; }
+
+const char* spx_strerror(int code) {
+  switch (code) {
+    case SPX_OK: return "ok";
+    case SPX_NOT_SPD: return "matrix is not positive definite (info = failing column)";
+    case SPX_ERR_INVALID_ARG: return "invalid argument";
+    case SPX_ERR_BAD_HANDLE: return "unknown tile handle or task id";
+    case SPX_ERR_STATE: return "call not allowed in the graph's current state";
+    case SPX_ERR_OOM: return "out of memory";
+    case SPX_ERR_QUEUE_FULL: return "device work queue capacity exceeded";
+    case SPX_ERR_TIMEOUT: return "timeout (device watchdog or host wait)";
+    case SPX_ERR_CUDA: return "CUDA runtime error";
+    case SPX_ERR_BAD_OP: return "device met an unknown task op";
+    case SPX_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status code";
+  }
+}
+
+int spx_graph_create(spx_graph_t* out, const spx_graph_config_t* cfg) {
+  if (!out) return SPX_ERR_INVALID_ARG;
+  *out = nullptr;
+  spx_graph* g = new (std::nothrow) spx_graph();
+  if (!g) return SPX_ERR_OOM;
+  spx_config_default(&g->cfg);
+  if (cfg) {
+    if (cfg->num_ctas < 0 || cfg->queue_capacity < 0 ||
+        (cfg->executor != SPX_EXEC_PERSISTENT && cfg->executor != SPX_EXEC_PER_TASK)) {
+      delete g;
+      return SPX_ERR_INVALID_ARG;
+    }
+    g->cfg = *cfg;
+    if (!g->cfg.watchdog_ns) g->cfg.watchdog_ns = 10000000000ull;
+  }
+  *out = g;
+  return SPX_OK;
+}
+
+int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
+                      void* lowp_ptr, int lowp_ld, unsigned* out_handle) {
+  if (!g || !dev_ptr || !out_handle || rows < 1 || cols < 1 || ld < cols ||
+      dtype < SPX_DT_F64 || dtype > SPX_DT_BF16 || (lowp_ptr && lowp_ld < cols))
+    return SPX_ERR_INVALID_ARG;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  const uintptr_t key = (uintptr_t)dev_ptr;
+  auto it = g->key_to_handle.find(key);
+  if (it != g->key_to_handle.end()) {
+    const TileDesc& t = g->tiles[it->second];
+    if (t.rows != rows || t.cols != cols || t.ld != ld || g->tile_dtype[it->second] != dtype)
+      return SPX_ERR_INVALID_ARG;
+    *out_handle = it->second;
+    return SPX_OK;
+  }
+  const uint32_t h = (uint32_t)g->tiles.size();
+  g->tiles.push_back(TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0});
+  g->tile_dtype.push_back(dtype);
+  g->hstate.emplace_back();
+  g->key_to_handle.emplace(key, h);
+  g->uploaded = false;
+  *out_handle = h;
+  return SPX_OK;
+}
+
+int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* modes, int nh,
+                    int priority, int prec, unsigned* out_task) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (op < 0 || op >= SPX_NUM_OPS || nh < 1 || nh > kMaxHandles || !handles || !modes ||
+      priority < 0 || prec != SPX_F64)
+    return SPX_ERR_INVALID_ARG;
+  if (g->tasks.size() >= kMaxTasks) return SPX_ERR_INVALID_ARG;
+  for (int i = 0; i < nh; ++i) {
+    if (handles[i] >= g->tiles.size()) return SPX_ERR_BAD_HANDLE;
+    if (modes[i] < SPX_READ || modes[i] > SPX_COMMUTATIVE_WRITE) return SPX_ERR_INVALID_ARG;
+  }
+  int rc = check_operands(op, g->tiles, g->tile_dtype, handles, modes, nh);
+  if (rc != SPX_OK) return rc;
+
+  // Merge repeated handles (READ+READ = READ, COMM+COMM = COMM, else WRITE)
+  // and order this task's accesses by handle (the lock order on the device).
+  uint32_t hh[kMaxHandles];
+  int mm[kMaxHandles];
+  int k = 0;
+  for (int i = 0; i < nh; ++i) {
+    int j = 0;
+    while (j < k && hh[j] != handles[i]) ++j;
+    if (j < k) {
+      if (mm[j] != modes[i]) mm[j] = SPX_WRITE;
+    } else {
+      hh[k] = handles[i];
+      mm[k] = modes[i];
+      ++k;
+    }
+  }
+  for (int i = 1; i < k; ++i)
+    for (int j = i; j > 0 && hh[j - 1] > hh[j]; --j) {
+      std::swap(hh[j - 1], hh[j]);
+      std::swap(mm[j - 1], mm[j]);
+    }
+
+  TaskDesc t{};
+  t.op = (uint8_t)op;
+  t.prec = (uint8_t)prec;
+  t.prio = priority > 0 ? 1 : 0;
+  t.flags = 0;
+  for (int i = 0; i < k; ++i)
+    if (mm[i] == SPX_COMMUTATIVE_WRITE) t.flags |= kFlagComm;
+  for (int i = 0; i < 3; ++i) t.h[i] = i < nh ? handles[i] : 0;
+  uint32_t parts = 1;
+  if (!g->cfg.no_split && !(t.flags & kFlagComm)) parts = std::min(op_units(op, g->tiles.data(), t.h), kMaxParts);
+  t.nparts = parts;
+  t.arg = 0;
+
+  const uint32_t tid = (uint32_t)g->tasks.size();
+  for (int i = 0; i < k; ++i) {
+    HandleState& s = g->hstate[hh[i]];
+    const int m = mm[i];
+    if (s.last_mode == m && m != SPX_WRITE) {
+      g->cand_edges += s.prev_size;
+      s.last_size += 1;
+    } else {
+      g->cand_edges += s.last_size;
+      s.prev_size = s.last_size;
+      s.last_size = 1;
+      s.last_mode = m;
+    }
+    g->rec_handle.push_back(hh[i]);
+    g->rec_seq.push_back(s.count++);
+    g->rec_mode.push_back((uint8_t)m);
+  }
+  g->task_rec.push_back((uint32_t)g->rec_handle.size());
+  g->tasks.push_back(t);
+  g->items[t.prio ? 0 : 1] += parts;
+  g->uploaded = false;
+  if (out_task) *out_task = tid;
+  return SPX_OK;
+}
+
+int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (task >= g->tasks.size()) return SPX_ERR_BAD_HANDLE;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  g->tasks[task].arg = arg;
+  g->uploaded = false;
+  return SPX_OK;
+}
+
+int spx_graph_derive(spx_graph_t g, void* stream) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state == kRunning) return SPX_ERR_STATE;
+  if (g->tasks.empty()) return SPX_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = SPX_OK;
+  if (!g->uploaded) rc = prepare_device(g, st);
+  if (rc != SPX_OK) return rc;
+  rc = reset_run_state(g, st);
+  if (rc != SPX_OK) return rc;
+  cudaError_t e = launch_derive(g->dg, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g->derived = true;
+  g->nedges = -1;
+  g->last_stream = st;
+  if (g->state == kBuilding) g->state = kFrozen;
+  return SPX_OK;
+}
+
+int spx_graph_execute(spx_graph_t g, void* stream) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
+  if (g->tasks.empty()) return SPX_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = SPX_OK;
+  cudaError_t e = cudaSuccess;
+  if (!g->uploaded) {
+    rc = prepare_device(g, st);
+    if (rc != SPX_OK) return rc;
+  }
+  if (g->cfg.executor == SPX_EXEC_PER_TASK) {
+    rc = reset_run_state(g, st);
+    if (rc != SPX_OK) return rc;
+    e = launch_per_task(g->dg, g->tasks.data(), st);
+  } else {
+    if (!g->derived) {
+      rc = spx_graph_derive(g, stream);  // also resets the run state
+      if (rc != SPX_OK) return rc;
+    } else {
+      rc = reset_run_state(g, st);
+      if (rc == SPX_OK) {
+        e = launch_init(g->dg, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+      if (rc != SPX_OK) return rc;
+    }
+    e = launch_persistent(g->dg, g->cfg.num_ctas, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->done_ev, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g->last_stream = st;
+  g->state = kRunning;
+  return SPX_OK;
+}
+
+int spx_graph_wait(spx_graph_t g, unsigned long long timeout_ns, int* info) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (info) *info = 0;
+  if (g->state == kDone) {
+    if (info) *info = g->last_info;
+    return g->last_status;
+  }
+  if (g->state != kRunning) return SPX_ERR_STATE;
+  const auto t0 = std::chrono::steady_clock::now();
+  long spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(g->done_ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      g->state = kDone;
+      g->last_status = cuda_fail(e);
+      return g->last_status;
+    }
+    if (timeout_ns) {
+      const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if ((unsigned long long)dt > timeout_ns) return SPX_ERR_TIMEOUT;
+    }
+    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  g->state = kDone;
+  const RunState& r = *g->host_rs;
+  g->last_status = (int)(int32_t)r.status;  // SPX_OK, SPX_NOT_SPD or a negative code
+  g->last_info = r.info;
+  if (info) *info = g->last_info;
+  return g->last_status;
+}
+
+int spx_graph_sizes(spx_graph_t g, long long* ntasks, long long* nedges, long long* naccesses,
+                    long long* ntiles) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (ntasks) *ntasks = (long long)g->tasks.size();
+  if (naccesses) *naccesses = (long long)g->rec_handle.size();
+  if (ntiles) *ntiles = (long long)g->tiles.size();
+  if (nedges) {
+    *nedges = -1;
+    if (g->derived && g->state != kRunning) {
+      if (g->nedges < 0) {
+        uint32_t e = 0;
+        cudaError_t err = cudaStreamSynchronize(g->last_stream);
+        if (err == cudaSuccess)
+          err = cudaMemcpy(&e, g->dg.row_ptr + g->tasks.size(), 4, cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) return cuda_fail(err);
+        g->nedges = e;
+      }
+      *nedges = g->nedges;
+    }
+  }
+  return SPX_OK;
+}
+
+int spx_graph_edges(spx_graph_t g, unsigned* row_ptr, unsigned* col, unsigned* indeg) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (!g->derived || g->state == kRunning) return SPX_ERR_STATE;
+  long long ne = 0;
+  int rc = spx_graph_sizes(g, nullptr, &ne, nullptr, nullptr);
+  if (rc != SPX_OK) return rc;
+  const size_t N = g->tasks.size();
+  cudaError_t e = cudaSuccess;
+  if (row_ptr) e = cudaMemcpy(row_ptr, g->dg.row_ptr, (N + 1) * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && col && ne > 0)
+    e = cudaMemcpy(col, g->dg.col, (size_t)ne * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && indeg) e = cudaMemcpy(indeg, g->dg.indeg, N * 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+int spx_graph_tickets(spx_graph_t g, unsigned* start, unsigned* end) {
+  if (!g || (!start && !end)) return SPX_ERR_INVALID_ARG;
+  if (g->state != kDone) return SPX_ERR_STATE;
+  const size_t N = g->tasks.size();
+  cudaError_t e = cudaSuccess;
+  if (start) e = cudaMemcpy(start, g->dg.t_start, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && end) e = cudaMemcpy(end, g->dg.t_end, N * 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+int spx_graph_trace(spx_graph_t g, unsigned long long* rec) {
+  if (!g || !rec) return SPX_ERR_INVALID_ARG;
+  if (g->state != kDone || !g->cfg.trace) return SPX_ERR_STATE;
+  cudaError_t e = cudaMemcpy(rec, g->dg.trace_rec, g->tasks.size() * 32, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+int spx_graph_stats(spx_graph_t g, long long* out, int n) {
+  if (!g || !out || n < 0) return SPX_ERR_INVALID_ARG;
+  if (g->state != kDone) return SPX_ERR_STATE;
+  const RunState& r = *g->host_rs;
+  const long long v[6] = {(long long)r.parts_done, (long long)r.hiwater, (long long)r.empty_pops,
+                          (long long)r.ctas, (long long)r.busy_cycles, (long long)r.total_cycles};
+  for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
+  return SPX_OK;
+}
+
+int spx_graph_write_dot(spx_graph_t g, const char* path) {
+  if (!g || !path) return SPX_ERR_INVALID_ARG;
+  if (!g->derived || g->state == kRunning) return SPX_ERR_STATE;
+  const size_t N = g->tasks.size();
+  long long ne = 0;
+  int rc = spx_graph_sizes(g, nullptr, &ne, nullptr, nullptr);
+  if (rc != SPX_OK) return rc;
+  std::vector<unsigned> rp(N + 1), col((size_t)std::max<long long>(ne, 1));
+  rc = spx_graph_edges(g, rp.data(), col.data(), nullptr);
+  if (rc != SPX_OK) return rc;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return SPX_ERR_INVALID_ARG;
+  static const char* names[SPX_NUM_OPS] = {"POTRF", "TRSM", "SYRK", "GEMM", "GEMM_NN",
+                                           "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
+                                           "NOP", "SPIN"};
+  std::fprintf(f, "digraph spx {\n");
+  for (size_t u = 0; u < N; ++u)
+    std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);
+  for (size_t u = 0; u < N; ++u)
+    for (unsigned p = rp[u]; p < rp[u + 1]; ++p) std::fprintf(f, "  t%zu -> t%u;\n", u, col[p]);
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+  return SPX_OK;
+}
+
+int spx_graph_reset(spx_graph_t g) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state != kDone) return SPX_ERR_STATE;
+  g->state = kFrozen;
+  return SPX_OK;
+}
+
+int spx_graph_clear(spx_graph_t g) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state == kRunning) return SPX_ERR_STATE;
+  g->tiles.clear();
+  g->tile_dtype.clear();
+  g->key_to_handle.clear();
+  g->hstate.clear();
+  g->tasks.clear();
+  g->rec_handle.clear();
+  g->rec_seq.clear();
+  g->rec_mode.clear();
+  g->task_rec.assign(1, 0);
+  g->cand_edges = 0;
+  g->items[0] = g->items[1] = 0;
+  g->uploaded = false;
+  g->derived = false;
+  g->nedges = -1;
+  g->state = kBuilding;
+  return SPX_OK;
+}
+
+void spx_graph_destroy(spx_graph_t g) {
+  if (!g) return;
+  if (g->state == kRunning) spx_graph_wait(g, 0, nullptr);
+  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  if (g->dmem) cudaFree(g->dmem);
+  if (g->pinned) cudaFreeHost(g->pinned);
+  if (g->host_rs) cudaFreeHost(g->host_rs);
+  if (g->done_ev) cudaEventDestroy(g->done_ev);
+  delete g;
+}
+
+}  // extern "C"

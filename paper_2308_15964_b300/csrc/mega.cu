@@ -1,0 +1,383 @@
+// Persistent device-scheduled executor and the one-launch-per-task baseline.
+//
+// Scheduling model (Specx paper, section "Scheduling"): ready tasks are pushed
+// into a scheduler and idle workers pop them.  Here the workers are
+// persistent CTAs (one or two per SM) and the scheduler is a pair of FIFO
+// queues in HBM (high and normal priority, section "Task insertion":
+// priorities are a hint the scheduler may use).  A task is split into parts
+// (independent sub-tile pieces); each queue entry is one part.
+//
+//   pop    warp 0 lane 0: claim a slot with compare-and-swap only when the
+//          queue is non-empty, then wait (bounded) for the entry to be written;
+//          high priority first.
+//   run    all 256 threads execute the part's tile op.
+//   finish a part decrements the task's remaining-part counter; the CTA that
+//          finishes the last part releases the task: warp 0 decrements the
+//          successors' in-degree counters (one lane per successor), ballots
+//          the ones that reached zero and reserves their queue entries with
+//          one atomicAdd per priority for the whole warp.
+//
+// Memory order: the writes of a part are published by __syncthreads +
+// __threadfence before the counter decrement; the releasing CTA fences again
+// before writing queue entries; a popping CTA fences after reading an entry.
+// Tile data are read with ld.global.cg.
+//
+// Every wait is bounded: a watchdog on the time since the last finished part
+// sets SPX_ERR_TIMEOUT and the abort flag, and every CTA drains and exits.
+// COMMUTATIVE_WRITE tasks run as one part and take per-tile locks in
+// ascending handle order before running (the paper locks data handles sorted
+// by address, section "Internal implementation"); a lock is held only by a
+// running task, so the ordered wait cannot deadlock.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx_internal.h"
+#include "tile_f64.cuh"
+
+namespace spx {
+namespace {
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smid() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %smid;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  return *(const volatile uint32_t*)p;
+}
+
+__device__ __forceinline__ void set_error(RunState* rs, uint32_t code, int info) {
+  if (atomicCAS(&rs->status, 0u, code) == 0u) rs->info = info;
+  atomicExch(&rs->abort, 1u);
+}
+
+__device__ __forceinline__ bool watchdog_expired(const DevGraph& g) {
+  const uint32_t last = ld_volatile(&g.rs->progress.v);
+  const uint32_t now = (uint32_t)(globaltimer() >> 10);  // ~1 us units
+  return (uint32_t)(now - last) > (uint32_t)(g.watchdog_ns >> 10);
+}
+
+__device__ __forceinline__ void touch_progress(const DevGraph& g) {
+  *(volatile uint32_t*)&g.rs->progress.v = (uint32_t)(globaltimer() >> 10);
+}
+
+// Pop one queue entry (task << 8 | part), or kExit.  Called by one thread.
+__device__ uint32_t pop(const DevGraph& g, uint32_t& empties) {
+  RunState* rs = g.rs;
+  uint32_t backoff = 32;
+  uint32_t iter = 0;
+  for (;;) {
+    if (ld_volatile(&rs->abort)) return kExit;
+    for (int q = 0; q < 2; ++q) {
+      uint32_t h = ld_volatile(&rs->head[q].v);
+      uint32_t t = min(ld_volatile(&rs->tail[q].v), g.qcap);
+      while (h < t) {
+        const uint32_t prev = atomicCAS(&rs->head[q].v, h, h + 1);
+        if (prev == h) {
+          // The slot was reserved by a pusher that is writing it now.
+          uint32_t v, spins = 0;
+          while ((v = ld_volatile(&g.queue[q][h])) == kEmpty) {
+            if ((++spins & 1023u) == 0) {
+              if (ld_volatile(&rs->abort)) return kExit;
+              if (watchdog_expired(g)) {
+                set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+                return kExit;
+              }
+            }
+          }
+          __threadfence();
+          return v;
+        }
+        h = prev;
+        t = min(ld_volatile(&rs->tail[q].v), g.qcap);
+      }
+    }
+    if (ld_volatile(&rs->done.v) >= g.ntasks) return kExit;
+    ++empties;
+    __nanosleep(backoff);
+    if (backoff < 1024) backoff <<= 1;
+    if ((++iter & 63u) == 0 && watchdog_expired(g)) {
+      set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+      return kExit;
+    }
+  }
+}
+
+// Release the successors of a finished task (warp 0, all 32 lanes).
+__device__ void release(const DevGraph& g, uint32_t task) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t r0 = g.row_ptr[task], r1 = g.row_ptr[task + 1];
+  for (uint32_t base = r0; base < r1; base += 32) {
+    const uint32_t idx = base + lane;
+    bool ready = false;
+    uint32_t s = 0, np = 0, pq = 0;
+    if (idx < r1) {
+      s = g.col[idx];
+      ready = atomicSub(&g.indeg_w[s], 1u) == 1u;
+      if (ready) {
+        np = g.tasks[s].nparts;
+        pq = g.tasks[s].prio ? 0u : 1u;
+      }
+    }
+    __threadfence();  // order the predecessors' data before the queue entries
+    for (uint32_t q = 0; q < 2; ++q) {
+      const bool mine = ready && pq == q;
+      const uint32_t cnt = mine ? np : 0u;
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total == 0) continue;
+      uint32_t slot = 0;
+      if (lane == 0) {
+        slot = atomicAdd(&g.rs->tail[q].v, total);
+        atomicMax(&g.rs->hiwater, slot + total);
+      }
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot + total > g.qcap) {
+        if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+        continue;
+      }
+      if (mine) {
+        const uint32_t at = slot + incl - cnt;
+        for (uint32_t p = 0; p < np; ++p)
+          *(volatile uint32_t*)&g.queue[q][at + p] = (s << kPartBits) | p;
+      }
+    }
+  }
+}
+
+// Bounded spin until t ns have passed (SPX_OP_SPIN); false on abort/timeout.
+__device__ bool spin_for(const DevGraph& g, long long ns) {
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    const unsigned long long dt = globaltimer() - t0;
+    if ((long long)dt >= ns) return true;
+    if (ld_volatile(&g.rs->abort)) return false;
+    if (dt > g.watchdog_ns) {
+      set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+      return false;
+    }
+    __nanosleep(1000);
+  }
+}
+
+// Run one part of a task with the whole CTA.  Returns 0, or a POTRF info.
+__device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t part, F64Smem& s) {
+  const TileDesc* T = g.tiles;
+  const uint32_t units = op_units(t.op, T, t.h);
+  const uint32_t u0 = (uint32_t)((unsigned long long)part * units / t.nparts);
+  const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / t.nparts);
+  switch (t.op) {
+    case SPX_OP_POTRF:
+      return op_potrf(T[t.h[0]], s);
+    case SPX_OP_TRSM:
+      op_trsm(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      return 0;
+    case SPX_OP_SYRK:
+      op_syrk(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      return 0;
+    case SPX_OP_GEMM_NT_SUB:
+      op_gemm<false, false>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s);
+      return 0;
+    case SPX_OP_GEMM_NN_ADD:
+      op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s);
+      return 0;
+    case SPX_OP_TRSM_L_FWD:
+      op_trsm_fwd(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      return 0;
+    case SPX_OP_GEMM_FWD:
+      op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s);
+      return 0;
+    case SPX_OP_TRSM_LT_BWD:
+      op_trsm_bwd(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      return 0;
+    case SPX_OP_GEMM_BWD:
+      op_gemm<true, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].rows, -1.0, u0, u1, s);
+      return 0;
+    case SPX_OP_NOP:
+      return 0;
+    case SPX_OP_SPIN:
+      if (threadIdx.x == 0) spin_for(g, t.arg);
+      __syncthreads();
+      return 0;
+    default:
+      return -1;
+  }
+}
+
+// Take the COMMUTATIVE_WRITE locks of task u in ascending handle order
+// (records of a task are sorted by handle).  One thread.  False on abort.
+__device__ bool lock_comm(const DevGraph& g, uint32_t u) {
+  for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r) {
+    if (g.rec_mode[r] != SPX_COMMUTATIVE_WRITE) continue;
+    uint32_t* lk = &g.locks[g.rec_handle[r]];
+    uint32_t spins = 0;
+    while (atomicCAS(lk, 0u, u + 1) != 0u) {
+      __nanosleep(64);
+      if ((++spins & 255u) == 0) {
+        if (ld_volatile(&g.rs->abort)) return false;
+        if (watchdog_expired(g)) {
+          set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+          return false;
+        }
+      }
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+__device__ void unlock_comm(const DevGraph& g, uint32_t u) {
+  __threadfence();
+  for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r)
+    if (g.rec_mode[r] == SPX_COMMUTATIVE_WRITE) atomicExch(&g.locks[g.rec_handle[r]], 0u);
+}
+
+__global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
+  __shared__ uint32_t s_item;
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  RunState* rs = g.rs;
+  const long long c_begin = clock64();
+  long long busy = 0;
+  uint32_t empties = 0;
+  if (tid == 0) touch_progress(g);
+
+  for (;;) {
+    if (tid == 0) s_item = pop(g, empties);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item == kExit) break;
+    const uint32_t u = item >> kPartBits, part = item & (kMaxParts - 1);
+    const TaskDesc t = g.tasks[u];
+    const long long c0 = clock64();
+    if (tid == 0) {
+      s_flag = 1;
+      if (t.flags & kFlagComm) s_flag = lock_comm(g, u) ? 1 : 0;
+      const uint32_t tk = atomicAdd(&rs->ticket.v, 1u);
+      atomicMin(&g.t_start[u], tk);
+      if (g.trace && part == 0) {
+        g.trace_rec[4 * u + 0] = globaltimer();
+        g.trace_rec[4 * u + 2] = smid();
+        g.trace_rec[4 * u + 3] = t.nparts;
+      }
+    }
+    __syncthreads();
+    if (!s_flag) break;
+    const int info = run_part(g, t, part, s);
+    __syncthreads();
+    busy += clock64() - c0;
+    if (tid == 0) {
+      if (info > 0) {
+        set_error(rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
+        s_flag = 0;
+      } else if (info < 0) {
+        set_error(rs, (uint32_t)SPX_ERR_BAD_OP, 0);
+        s_flag = 0;
+      } else {
+        __threadfence();
+        const uint32_t tk = atomicAdd(&rs->ticket.v, 1u);
+        atomicMax(&g.t_end[u], tk);
+        if (g.trace) atomicMax(&g.trace_rec[4 * u + 1], globaltimer());
+        atomicAdd(&rs->parts_done, 1u);
+        s_flag = atomicSub(&g.remaining[u], 1u) == 1u ? 2 : 1;
+        __threadfence();
+        touch_progress(g);
+      }
+    }
+    __syncthreads();
+    if (s_flag == 0) break;
+    if (s_flag == 2) {
+      if (tid < 32) {
+        if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
+        __syncwarp();
+        release(g, u);
+        __syncwarp();
+        if (tid == 0) {
+          __threadfence();
+          atomicAdd(&rs->done.v, 1u);
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    atomicAdd(&rs->busy_cycles, (unsigned long long)busy);
+    atomicAdd(&rs->total_cycles, (unsigned long long)(clock64() - c_begin));
+    atomicAdd(&rs->ctas, 1u);
+    atomicAdd(&rs->empty_pops, empties);
+  }
+}
+
+// Baseline: one launch per task, one CTA per part, insertion order.
+__global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = (int)ld_volatile(&g.rs->abort);
+  __syncthreads();
+  if (s_abort) return;
+  const TaskDesc t = g.tasks[u];
+  if (threadIdx.x == 0 && blockIdx.x == 0) touch_progress(g);
+  const int info = run_part(g, t, blockIdx.x, s);
+  if (threadIdx.x == 0) {
+    if (info > 0) set_error(g.rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
+    else if (info < 0) set_error(g.rs, (uint32_t)SPX_ERR_BAD_OP, 0);
+    else atomicAdd(&g.rs->parts_done, 1u);
+  }
+}
+
+int g_max_ctas_per_sm = -1;
+int g_sms = -1;
+
+}  // namespace
+
+size_t persistent_smem_bytes() { return sizeof(F64Smem); }
+
+int persistent_max_ctas(int* per_sm) {
+  if (g_max_ctas_per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(F64Smem));
+    cudaFuncSetAttribute(task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(F64Smem));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel, kThreads,
+                                                  sizeof(F64Smem));
+    g_max_ctas_per_sm = occ > 0 ? occ : 1;
+  }
+  if (per_sm) *per_sm = g_max_ctas_per_sm;
+  return g_sms * g_max_ctas_per_sm;
+}
+
+cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st) {
+  const int maxc = persistent_max_ctas(nullptr);
+  int n = num_ctas > 0 ? num_ctas : maxc;
+  if (n > maxc) n = maxc;  // every CTA resident: no CTA waits behind a spinning one
+  persistent_kernel<<<n, kThreads, sizeof(F64Smem), st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks, cudaStream_t st) {
+  persistent_max_ctas(nullptr);
+  for (uint32_t u = 0; u < g.ntasks; ++u) {
+    task_kernel<<<host_tasks[u].nparts, kThreads, sizeof(F64Smem), st>>>(g, u);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace spx

@@ -1,0 +1,144 @@
+// Throughput probes for the roofline denominators that the driver does not
+// measure: FP64 FMA on the SIMT pipe (DFMA), FP64 mma.sync (DMMA), FP32 FMA,
+// global atomics on one address and on distinct addresses, and the launch
+// rate of an empty kernel.  Each probe times itself with CUDA events on its
+// own stream and returns a rate.  Declared in include/spx_probe.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx_probe.h"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void dfma_kernel(double* out, int iters, double a, double b) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (double)(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == 12345.678) out[threadIdx.x] = s;  // keeps the loop alive
+}
+
+__global__ void ffma_kernel(float* out, int iters, float a, float b) {
+  float x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (float)(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = fmaf(x[c], a, b);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == 12345.678f) out[threadIdx.x] = s;
+}
+
+// FP64 tensor MMA m8n8k4: D(8x8) = A(8x4) B(4x8) + C, per warp.
+__global__ void dmma_kernel(double* out, int iters) {
+  double a = 1.0 + threadIdx.x * 1e-3, b = 1.0 - threadIdx.x * 1e-3;
+  double d[4][2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { d[c][0] = 0.0; d[c][1] = 0.0; }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      asm volatile(
+          "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+          : "+d"(d[c][0]), "+d"(d[c][1])
+          : "d"(a), "d"(b));
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s += d[c][0] + d[c][1];
+  if (s == 12345.678) out[threadIdx.x] = s;
+}
+
+__global__ void atomic_same_kernel(unsigned* ctr, int iters) {
+  for (int i = 0; i < iters; ++i) atomicAdd(ctr, 1u);
+}
+
+__global__ void atomic_distinct_kernel(unsigned* ctr, int iters, int n) {
+  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) % n;
+  for (int i = 0; i < iters; ++i) atomicAdd(ctr + idx, 1u);
+}
+
+__global__ void empty_kernel() {}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  return sms;
+}
+
+}  // namespace
+
+extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
+  if (!rate || !ms || iters <= 0) return -1;
+  const int sms = sm_count();
+  if (sms <= 0) return -9;
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -7;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void* buf = nullptr;
+  cudaMalloc(&buf, 1 << 20);
+  cudaMemsetAsync(buf, 0, 1 << 20, st);
+  const int blocks = sms * 8, threads = 256;
+  double work = 0.0;
+  for (int rep = 0; rep < 2; ++rep) {  // first pass warms up
+    cudaEventRecord(e0, st);
+    switch (which) {
+      case SPX_PROBE_DFMA:
+        dfma_kernel<<<blocks, threads, 0, st>>>((double*)buf, iters, 0.999999, 1e-7);
+        work = 2.0 * kChains * (double)iters * blocks * threads;
+        break;
+      case SPX_PROBE_DMMA:
+        dmma_kernel<<<blocks, threads, 0, st>>>((double*)buf, iters);
+        work = 2.0 * 8 * 8 * 4 * 4.0 * (double)iters * blocks * (threads / 32);
+        break;
+      case SPX_PROBE_FFMA:
+        ffma_kernel<<<blocks, threads, 0, st>>>((float*)buf, iters, 0.999999f, 1e-7f);
+        work = 2.0 * kChains * (double)iters * blocks * threads;
+        break;
+      case SPX_PROBE_ATOMIC_SAME:
+        atomic_same_kernel<<<sms * 2, 256, 0, st>>>((unsigned*)buf, iters);
+        work = (double)iters * sms * 2 * 256;
+        break;
+      case SPX_PROBE_ATOMIC_DISTINCT:
+        atomic_distinct_kernel<<<sms * 2, 256, 0, st>>>((unsigned*)buf, iters, 65536);
+        work = (double)iters * sms * 2 * 256;
+        break;
+      case SPX_PROBE_LAUNCH:
+        for (int i = 0; i < iters; ++i) empty_kernel<<<1, 32, 0, st>>>();
+        work = iters;
+        break;
+      default:
+        work = -1.0;
+    }
+    cudaEventRecord(e1, st);
+  }
+  cudaError_t err = cudaStreamSynchronize(st);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaFree(buf);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (work < 0) return -1;
+  if (err != cudaSuccess) return -7;
+  *ms = t;
+  *rate = work / (t * 1e-3);
+  return 0;
+}
+
+extern "C" int spx_device_sm_count(void) { return sm_count(); }

@@ -1,0 +1,134 @@
+// Internal data layout shared by the host builder (graph.cpp) and the device
+// code (derive.cu, mega.cu).  Everything the device reads lives in HBM in the
+// structures below; they are plain arrays of fixed-size records so that one
+// cudaMemcpyAsync uploads each of them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx.h"
+
+namespace spx {
+
+constexpr int kMaxHandles = 16;           // operands of one task
+constexpr int kPartBits = 8;              // queue entry = task << 8 | part
+constexpr uint32_t kMaxParts = 1u << kPartBits;
+constexpr uint32_t kMaxTasks = (1u << (32 - kPartBits)) - 2;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // free queue slot
+constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
+constexpr int kThreads = 256;             // threads per persistent CTA
+constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
+
+enum TaskFlags : uint8_t { kFlagComm = 1 };
+
+// One registered tile (a data handle of the STF model).
+struct TileDesc {
+  void* ptr;      // element (0,0), row-major
+  void* lowp;     // optional low-precision copy (nullptr if none)
+  int32_t rows, cols, ld, lowp_ld;
+};
+static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
+
+// One task: op, operands (handles in op order), parts, argument.
+struct TaskDesc {
+  uint8_t op, prec, flags, prio;  // prio: 0 = normal, 1 = high
+  uint32_t nparts;
+  uint32_t h[3];
+  uint32_t pad;
+  int64_t arg;
+};
+static_assert(sizeof(TaskDesc) == 32, "TaskDesc layout");
+
+// Run state of one execution; hot counters on separate 128-byte lines.
+struct alignas(128) Line {
+  uint32_t v;
+  uint32_t pad[31];
+};
+
+struct RunState {
+  Line head[2];          // next queue slot to pop (0 = high priority)
+  Line tail[2];          // next queue slot to fill
+  Line done;             // finished tasks
+  Line ticket;           // global ticket counter
+  Line progress;         // %globaltimer >> 10 at the last finished part
+  // control words, read by every popping CTA
+  alignas(128) uint32_t status;  // SPX_OK or an error / SPX_NOT_SPD
+  int32_t info;          // failed POTRF column (1-based)
+  uint32_t abort;        // set on any error: every CTA drains
+  // statistics
+  alignas(128) uint32_t empty_pops;  // pops that found both queues empty
+  uint32_t parts_done;
+  uint32_t hiwater;
+  uint32_t ctas;
+  unsigned long long busy_cycles;
+  unsigned long long total_cycles;
+};
+
+// Pointers and sizes handed to the device kernels by value.
+struct DevGraph {
+  uint32_t ntasks, ntiles, nrec, ecap;
+  uint32_t qcap;               // entries per priority queue
+  uint32_t trace;
+  unsigned long long watchdog_ns;
+  const TaskDesc* tasks;       // [ntasks]
+  const TileDesc* tiles;       // [ntiles]
+  // access records in insertion order (records of one task are contiguous
+  // and sorted by handle)
+  const uint32_t* rec_handle;  // [nrec]
+  const uint32_t* rec_seq;     // [nrec] position on the handle's list
+  const uint8_t* rec_mode;     // [nrec]
+  const uint32_t* task_rec;    // [ntasks+1] first record of each task
+  // derivation scratch
+  uint32_t* hptr;              // [ntiles+1] start of each handle's list
+  uint32_t* s_task;            // [nrec] per-handle lists, concatenated
+  uint8_t* s_mode;             // [nrec]
+  uint8_t* s_first;            // [nrec] 1 at the first entry of a list
+  uint32_t* rec_pos;           // [nrec] record -> position in the lists
+  uint32_t* gid;               // [nrec] group index of each list entry
+  uint32_t* gpos;              // [nrec+1] first entry of each group
+  uint32_t* ucount;            // [ntasks] unique successors per task
+  // derived DAG
+  uint32_t* row_ptr;           // [ntasks+1]
+  uint32_t* col;               // [ecap]
+  uint32_t* indeg;             // [ntasks]
+  // execution state
+  uint32_t* indeg_w;           // [ntasks] remaining predecessors
+  uint32_t* remaining;         // [ntasks] parts not finished
+  uint32_t* queue[2];          // [qcap] each
+  uint32_t* locks;             // [ntiles] owner task + 1, 0 = free
+  uint32_t* t_start;           // [ntasks] tickets
+  uint32_t* t_end;             // [ntasks]
+  unsigned long long* trace_rec;  // [4*ntasks] when trace
+  RunState* rs;
+};
+
+
+// Work units of a task: the 64-granular pieces an op splits into (row blocks
+// of a TRSM, lower block pairs of a SYRK, output blocks of a GEMM, column
+// blocks of a solve).  A task runs as min(units, kMaxParts) parts; part p
+// covers units [p*U/P, (p+1)*U/P).  Shared by host (part counts) and device.
+__host__ __device__ inline uint32_t op_units(int op, const TileDesc* t, const uint32_t* h) {
+  auto cd = [](int a) { return (uint32_t)((a + kBlk - 1) / kBlk); };
+  switch (op) {
+    case SPX_OP_TRSM: return cd(t[h[1]].rows);
+    case SPX_OP_SYRK: { const uint32_t nb = cd(t[h[1]].rows); return nb * (nb + 1) / 2; }
+    case SPX_OP_GEMM_NT_SUB:
+    case SPX_OP_GEMM_NN_ADD:
+    case SPX_OP_GEMM_FWD:
+    case SPX_OP_GEMM_BWD: return cd(t[h[2]].rows) * cd(t[h[2]].cols);
+    case SPX_OP_TRSM_L_FWD:
+    case SPX_OP_TRSM_LT_BWD: return cd(t[h[1]].cols);
+    default: return 1;
+  }
+}
+
+// Launchers implemented in the .cu files (all asynchronous on stream).
+cudaError_t launch_derive(const DevGraph& g, cudaStream_t st);
+cudaError_t launch_init(const DevGraph& g, cudaStream_t st);  // reset run state only
+cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st);
+cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks, cudaStream_t st);
+int persistent_max_ctas(int* per_sm);
+size_t persistent_smem_bytes();
+
+}  // namespace spx

@@ -1,0 +1,346 @@
+// FP64 tile operations, run by all 256 threads of one CTA.
+//
+// These are the task kernels of the paper's tiled Cholesky (section
+// "Numerical applications": POTRF, TRSM, SYRK, GEMM), of its tiled GEMM with
+// dependencies on the blocks of C, and of the block triangular solves.  On
+// the B300 the FP64 SIMT pipe (DFMA) is faster than FP64 mma.sync, and there is
+// no FP64 kind of tcgen05.mma, so every FP64 op is a DFMA loop nest: 64x64
+// output blocks, k staged through shared memory in chunks of 16, a 4x4
+// register block per thread.  Data written by other tasks is read with
+// ld.global.cg (L2), so a CTA never sees stale L1 lines of a tile that another
+// SM updated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx_internal.h"
+
+namespace spx {
+
+constexpr int kKC = 16;        // k chunk staged in shared memory
+constexpr int kLds = kBlk + 1; // padded row of a shared 64-wide array (doubles)
+
+struct GemmSmem {
+  double a[kKC][kLds];
+  double b[kKC][kLds];
+};
+
+// Shared memory of the FP64 ops: GEMM staging plus two 64x64 blocks.
+struct F64Smem {
+  GemmSmem gs;
+  double l[kBlk][kLds];   // diagonal block of L
+  double x[kBlk][kLds];   // block being solved
+  int info;
+};
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// C[0:m, 0:n] += alpha * op(A) op(B), m, n <= 64, any K.
+//   op(A)(i,k) = A_T ? A[k*lda + i] : A[i*lda + k]
+//   op(B)(k,j) = B_KN ? B[k*ldb + j] : B[j*ldb + k]
+// lower: only entries with column <= row are written (diagonal SYRK blocks).
+template <bool A_T, bool B_KN>
+__device__ void gemm_block(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                           int m, int n, int K, double alpha, bool lower, GemmSmem& s) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += kKC) {
+#pragma unroll
+    for (int e = tid; e < kBlk * kKC; e += kThreads) {
+      int i, kk;
+      if (A_T) { kk = e / kBlk; i = e % kBlk; } else { i = e / kKC; kk = e % kKC; }
+      double v = 0.0;
+      if (i < m && k0 + kk < K)
+        v = ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk);
+      s.a[kk][i] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < kBlk * kKC; e += kThreads) {
+      int j, kk;
+      if (B_KN) { kk = e / kBlk; j = e % kBlk; } else { j = e / kKC; kk = e % kKC; }
+      double v = 0.0;
+      if (j < n && k0 + kk < K)
+        v = ldcg(B_KN ? B + (size_t)(k0 + kk) * ldb + j : B + (size_t)j * ldb + k0 + kk);
+      s.b[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKC; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = s.a[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = s.b[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tx + 16 * j;
+      if (r < m && c < n && (!lower || c <= r)) {
+        double* p = C + (size_t)r * ldc + c;
+        *p = __ldcg(p) + alpha * acc[i][j];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Copy an m x n block (row-major, ld) into a shared 64-wide array and back.
+__device__ __forceinline__ void load_block(double (*dst)[kLds], const double* src, int ld, int m,
+                                           int n) {
+  for (int e = threadIdx.x; e < kBlk * kBlk; e += kThreads) {
+    const int r = e / kBlk, c = e % kBlk;
+    dst[r][c] = (r < m && c < n) ? __ldcg(src + (size_t)r * ld + c) : 0.0;
+  }
+}
+
+__device__ __forceinline__ void store_block(double* dst, int ld, const double (*src)[kLds], int m,
+                                            int n, bool lower) {
+  for (int e = threadIdx.x; e < kBlk * kBlk; e += kThreads) {
+    const int r = e / kBlk, c = e % kBlk;
+    if (r < m && c < n && (!lower || c <= r)) dst[(size_t)r * ld + c] = src[r][c];
+  }
+}
+
+// Unblocked right-looking Cholesky of the w x w block in shared memory
+// (lower).  Returns 0 or the 1-based local column of a pivot that is not > 0
+// (NaN included).  Every thread returns the same value.
+__device__ int potrf_smem(double (*a)[kLds], int w, int* s_info) {
+  const int tid = threadIdx.x;
+  if (tid == 0) *s_info = 0;
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      const double d = a[j][j];
+      if (!(d > 0.0)) *s_info = j + 1;
+      else a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (*s_info) return *s_info;
+    const double ljj = a[j][j];
+    for (int i = j + 1 + tid; i < w; i += kThreads) a[i][j] = a[i][j] / ljj;
+    __syncthreads();
+    const int t = w - j - 1;  // trailing lower triangle, rows/cols j+1..w-1
+    for (int e = tid; e < t * t; e += kThreads) {
+      const int i = j + 1 + e / t, c = j + 1 + e % t;
+      if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// X <- X L^{-T} for X (m x w) and L (w x w lower) in shared memory:
+// x_rc = (x_rc - sum_{k<c} x_rk l_ck) / l_cc, right-looking over c.
+__device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+  const int tid = threadIdx.x;
+  for (int c = 0; c < w; ++c) {
+    const double lcc = l[c][c];
+    for (int r = tid; r < m; r += kThreads) x[r][c] = x[r][c] / lcc;
+    __syncthreads();
+    const int t = w - c - 1;
+    for (int e = tid; e < m * t; e += kThreads) {
+      const int r = e / t, cc = c + 1 + e % t;
+      x[r][cc] = fma(-x[r][c], l[cc][c], x[r][cc]);
+    }
+    __syncthreads();
+  }
+}
+
+// X <- L^{-1} X for L (m x m lower) and X (m x w) in shared memory (forward
+// substitution on every column).
+__device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+  const int tid = threadIdx.x;
+  for (int i = 0; i < m; ++i) {
+    const double lii = l[i][i];
+    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
+    __syncthreads();
+    const int t = m - i - 1;
+    for (int e = tid; e < t * w; e += kThreads) {
+      const int r = i + 1 + e / w, c = e % w;
+      x[r][c] = fma(-l[r][i], x[i][c], x[r][c]);
+    }
+    __syncthreads();
+  }
+}
+
+// X <- L^{-T} X for L (m x m lower) and X (m x w) in shared memory (back
+// substitution: x_i = (x_i - sum_{k>i} l_ki x_k) / l_ii).
+__device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+  const int tid = threadIdx.x;
+  for (int i = m - 1; i >= 0; --i) {
+    const double lii = l[i][i];
+    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
+    __syncthreads();
+    for (int e = tid; e < i * w; e += kThreads) {
+      const int r = e / w, c = e % w;
+      x[r][c] = fma(-l[i][r], x[i][c], x[r][c]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Task ops.  u0..u1 is the range of work units of this part (see op_units).
+// ---------------------------------------------------------------------------
+
+// POTRF on an n x n tile (one part): left-looking by 64-column panels.
+// Returns 0 or the 1-based local column of the failed pivot.
+__device__ int op_potrf(const TileDesc& A, F64Smem& s) {
+  double* a = (double*)A.ptr;
+  const int n = A.rows, lda = A.ld;
+  for (int jb = 0; jb < n; jb += kBlk) {
+    const int w = min(kBlk, n - jb);
+    if (jb > 0) {
+      for (int ib = jb; ib < n; ib += kBlk) {
+        const int mb = min(kBlk, n - ib);
+        gemm_block<false, false>(a + (size_t)ib * lda + jb, lda, a + (size_t)ib * lda, lda,
+                                 a + (size_t)jb * lda, lda, mb, w, jb, -1.0, ib == jb, s.gs);
+      }
+    }
+    load_block(s.l, a + (size_t)jb * lda + jb, lda, w, w);
+    __syncthreads();
+    const int info = potrf_smem(s.l, w, &s.info);
+    if (info) return jb + info;
+    store_block(a + (size_t)jb * lda + jb, lda, s.l, w, w, true);
+    for (int ib = jb + w; ib < n; ib += kBlk) {
+      const int mb = min(kBlk, n - ib);
+      load_block(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
+      __syncthreads();
+      trsm_rt_smem(s.x, s.l, mb, w);
+      store_block(a + (size_t)ib * lda + jb, lda, s.x, mb, w, false);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
+// TRSM: A (m x n) <- A L^{-T}, L (n x n); units = 64-row blocks of A.
+__device__ void op_trsm(const TileDesc& Lt, const TileDesc& At, uint32_t u0, uint32_t u1,
+                        F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* a = (double*)At.ptr;
+  const int n = At.cols, lda = At.ld, ldl = Lt.ld;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int ib = u * kBlk, mb = min(kBlk, At.rows - ib);
+    double* x = a + (size_t)ib * lda;
+    for (int jb = 0; jb < n; jb += kBlk) {
+      const int w = min(kBlk, n - jb);
+      if (jb > 0)
+        gemm_block<false, false>(x + jb, lda, x, lda, l + (size_t)jb * ldl, ldl, mb, w, jb, -1.0,
+                                 false, s.gs);
+      load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+      load_block(s.x, x + jb, lda, mb, w);
+      __syncthreads();
+      trsm_rt_smem(s.x, s.l, mb, w);
+      store_block(x + jb, lda, s.x, mb, w, false);
+      __syncthreads();
+    }
+  }
+}
+
+// Lower block pair (bi >= bj) of unit u in a triangle of blocks.
+__device__ __forceinline__ void lower_pair(uint32_t u, int& bi, int& bj) {
+  int i = 0;
+  while ((uint32_t)((i + 1) * (i + 2) / 2) <= u) ++i;
+  bi = i;
+  bj = (int)(u - (uint32_t)(i * (i + 1) / 2));
+}
+
+// SYRK: C (n x n, lower) -= L L^T, L (n x k); units = lower 64-block pairs.
+__device__ void op_syrk(const TileDesc& Lt, const TileDesc& Ct, uint32_t u0, uint32_t u1,
+                        F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* c = (double*)Ct.ptr;
+  const int n = Ct.rows, k = Lt.cols;
+  for (uint32_t u = u0; u < u1; ++u) {
+    int bi, bj;
+    lower_pair(u, bi, bj);
+    const int r0 = bi * kBlk, c0 = bj * kBlk;
+    gemm_block<false, false>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, l + (size_t)r0 * Lt.ld, Lt.ld,
+                             l + (size_t)c0 * Lt.ld, Lt.ld, min(kBlk, n - r0), min(kBlk, n - c0), k,
+                             -1.0, bi == bj, s.gs);
+  }
+}
+
+// Output-block GEMMs; units = 64x64 blocks of C, row-major.
+template <bool A_T, bool B_KN>
+__device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& Ct, int K,
+                        double alpha, uint32_t u0, uint32_t u1, F64Smem& s) {
+  const double* a = (const double*)At.ptr;
+  const double* b = (const double*)Bt.ptr;
+  double* c = (double*)Ct.ptr;
+  const uint32_t nbc = (Ct.cols + kBlk - 1) / kBlk;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (u / nbc) * kBlk, c0 = (u % nbc) * kBlk;
+    const double* ap = A_T ? a + r0 : a + (size_t)r0 * At.ld;
+    const double* bp = B_KN ? b + c0 : b + (size_t)c0 * Bt.ld;
+    gemm_block<A_T, B_KN>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
+                          min(kBlk, Ct.rows - r0), min(kBlk, Ct.cols - c0), K, alpha, false, s.gs);
+  }
+}
+
+// X <- L^{-1} X (forward, L n x n, X n x r); units = 64-column blocks of X.
+__device__ void op_trsm_fwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0, uint32_t u1,
+                            F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* x = (double*)Xt.ptr;
+  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
+    for (int ib = 0; ib < n; ib += kBlk) {
+      const int mb = min(kBlk, n - ib);
+      if (ib > 0)
+        gemm_block<false, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)ib * ldl, ldl, x + c0,
+                                ldx, mb, w, ib, -1.0, false, s.gs);
+      load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
+      load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
+      __syncthreads();
+      trsm_ln_smem(s.x, s.l, mb, w);
+      store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
+      __syncthreads();
+    }
+  }
+}
+
+// X <- L^{-T} X (backward); units = 64-column blocks of X.
+__device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0, uint32_t u1,
+                            F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* x = (double*)Xt.ptr;
+  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld;
+  const int nb = (n + kBlk - 1) / kBlk;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
+    for (int bi = nb - 1; bi >= 0; --bi) {
+      const int ib = bi * kBlk, mb = min(kBlk, n - ib), below = n - ib - mb;
+      if (below > 0)
+        gemm_block<true, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)(ib + mb) * ldl + ib,
+                               ldl, x + (size_t)(ib + mb) * ldx + c0, ldx, mb, w, below, -1.0,
+                               false, s.gs);
+      load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
+      load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
+      __syncthreads();
+      trsm_lt_smem(s.x, s.l, mb, w);
+      store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace spx

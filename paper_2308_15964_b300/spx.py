@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libspx.so (include/spx.h): argument marshalling only.
+
+Every step of the hot path (DAG derivation, scheduling, tile ops) runs in the
+library's CUDA kernels.  If the library is missing this module raises at
+import time: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libspx.so")
+
+READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
+(OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
+ OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN) = range(11)
+F64, TF32, BF16 = 0, 1, 2
+DT_F64, DT_F32, DT_BF16 = 0, 1, 2
+EXEC_PERSISTENT, EXEC_PER_TASK = 0, 1
+
+OK, NOT_SPD = 0, 1
+ERR_INVALID_ARG, ERR_BAD_HANDLE, ERR_STATE, ERR_OOM, ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_CUDA, \
+    ERR_BAD_OP, ERR_NO_DEVICE = -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+
+class SpxError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("num_ctas", ctypes.c_int), ("executor", ctypes.c_int), ("trace", ctypes.c_int),
+                ("no_split", ctypes.c_int), ("watchdog_ns", ctypes.c_ulonglong),
+                ("queue_capacity", ctypes.c_longlong)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2308_15964_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    LL, ULL = ctypes.c_longlong, ctypes.c_ulonglong
+    sig = {
+        "spx_config_default": (None, [P]),
+        "spx_graph_create": (I, [P, P]),
+        "spx_tile_register": (I, [P, P, I, I, I, I, P, I, P]),
+        "spx_task_insert": (I, [P, I, P, P, I, I, I, P]),
+        "spx_task_set_arg": (I, [P, U, LL]),
+        "spx_graph_derive": (I, [P, P]),
+        "spx_graph_execute": (I, [P, P]),
+        "spx_graph_wait": (I, [P, ULL, P]),
+        "spx_graph_sizes": (I, [P, P, P, P, P]),
+        "spx_graph_edges": (I, [P, P, P, P]),
+        "spx_graph_tickets": (I, [P, P, P]),
+        "spx_graph_trace": (I, [P, P]),
+        "spx_graph_stats": (I, [P, P, I]),
+        "spx_graph_write_dot": (I, [P, ctypes.c_char_p]),
+        "spx_graph_reset": (I, [P]),
+        "spx_graph_clear": (I, [P]),
+        "spx_graph_destroy": (None, [P]),
+        "spx_strerror": (ctypes.c_char_p, [I]),
+        "spx_abi_version": (I, []),
+        "spx_probe": (I, [I, I, P, P]),
+        "spx_device_sm_count": (I, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.spx_strerror(code).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise SpxError(rc, what)
+    return rc
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return ctypes.c_void_p(int(stream))
+
+
+class Graph:
+    """An STF task graph (spx_graph_t)."""
+
+    def __init__(self, num_ctas=0, executor=EXEC_PERSISTENT, trace=False, no_split=False,
+                 watchdog_ns=0, queue_capacity=0):
+        cfg = Config()
+        lib.spx_config_default(ctypes.byref(cfg))
+        cfg.num_ctas = num_ctas
+        cfg.executor = executor
+        cfg.trace = 1 if trace else 0
+        cfg.no_split = 1 if no_split else 0
+        if watchdog_ns:
+            cfg.watchdog_ns = watchdog_ns
+        cfg.queue_capacity = queue_capacity
+        h = ctypes.c_void_p()
+        _check(lib.spx_graph_create(ctypes.byref(h), ctypes.byref(cfg)), "spx_graph_create")
+        self._h = h
+        self._keep = []          # tensors whose memory the graph refers to
+
+    # -- building ---------------------------------------------------------
+    def register(self, ptr: int, rows: int, cols: int, ld: int, dtype=DT_F64, lowp_ptr=0,
+                 lowp_ld=0) -> int:
+        out = ctypes.c_uint()
+        _check(lib.spx_tile_register(self._h, ctypes.c_void_p(ptr), rows, cols, ld, dtype,
+                                     ctypes.c_void_p(lowp_ptr or None), lowp_ld, ctypes.byref(out)),
+               "spx_tile_register")
+        return out.value
+
+    def register_tensor(self, t, dtype=DT_F64) -> int:
+        """Register a 2-D row-major view (stride(1) == 1) of a CUDA tensor."""
+        assert t.dim() == 2 and t.stride(1) == 1
+        return self.register(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), dtype)
+
+    def insert(self, op: int, handles, modes, priority=0, prec=F64) -> int:
+        h = np.ascontiguousarray(handles, dtype=np.uint32)
+        m = np.ascontiguousarray(modes, dtype=np.int32)
+        out = ctypes.c_uint()
+        _check(lib.spx_task_insert(self._h, op, _ptr(h), _ptr(m), len(h), priority, prec,
+                                   ctypes.byref(out)), "spx_task_insert")
+        return out.value
+
+    def set_arg(self, task: int, arg: int):
+        _check(lib.spx_task_set_arg(self._h, task, arg), "spx_task_set_arg")
+
+    # -- running ----------------------------------------------------------
+    def derive(self, stream=None):
+        _check(lib.spx_graph_derive(self._h, _stream_ptr(stream)), "spx_graph_derive")
+
+    def execute(self, stream=None):
+        _check(lib.spx_graph_execute(self._h, _stream_ptr(stream)), "spx_graph_execute")
+
+    def wait(self, timeout_ns: int = 0):
+        """Returns (status, info); status is OK, NOT_SPD or a negative error code."""
+        info = ctypes.c_int()
+        rc = lib.spx_graph_wait(self._h, timeout_ns, ctypes.byref(info))
+        return rc, info.value
+
+    def run(self, stream=None, timeout_ns: int = 0):
+        self.execute(stream)
+        return self.wait(timeout_ns)
+
+    def reset(self):
+        _check(lib.spx_graph_reset(self._h), "spx_graph_reset")
+
+    def clear(self):
+        _check(lib.spx_graph_clear(self._h), "spx_graph_clear")
+        self._keep.clear()
+
+    # -- inspection -------------------------------------------------------
+    def sizes(self):
+        v = [ctypes.c_longlong() for _ in range(4)]
+        _check(lib.spx_graph_sizes(self._h, *[ctypes.byref(x) for x in v]), "spx_graph_sizes")
+        return tuple(x.value for x in v)  # ntasks, nedges, naccesses, ntiles
+
+    def edges(self):
+        n, e, _, _ = self.sizes()
+        row_ptr = np.zeros(n + 1, np.uint32)
+        col = np.zeros(max(e, 1), np.uint32)
+        indeg = np.zeros(max(n, 1), np.uint32)
+        _check(lib.spx_graph_edges(self._h, _ptr(row_ptr), _ptr(col), _ptr(indeg)), "spx_graph_edges")
+        return row_ptr, col[:e].copy(), indeg[:n].copy()
+
+    def tickets(self):
+        n = self.sizes()[0]
+        s = np.zeros(n, np.uint32)
+        e = np.zeros(n, np.uint32)
+        _check(lib.spx_graph_tickets(self._h, _ptr(s), _ptr(e)), "spx_graph_tickets")
+        return s, e
+
+    def trace(self):
+        n = self.sizes()[0]
+        r = np.zeros((n, 4), np.uint64)
+        _check(lib.spx_graph_trace(self._h, _ptr(r)), "spx_graph_trace")
+        return r
+
+    def stats(self):
+        v = np.zeros(6, np.int64)
+        _check(lib.spx_graph_stats(self._h, _ptr(v), 6), "spx_graph_stats")
+        keys = ["parts", "queue_hiwater", "empty_pops", "ctas", "busy_cycles", "total_cycles"]
+        return dict(zip(keys, (int(x) for x in v)))
+
+    def write_dot(self, path: str):
+        _check(lib.spx_graph_write_dot(self._h, path.encode()), "spx_graph_write_dot")
+
+    def close(self):
+        if self._h:
+            lib.spx_graph_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def probe(which: int, iters: int):
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.spx_probe(which, iters, ctypes.byref(rate), ctypes.byref(ms)), "spx_probe")
+    return rate.value, ms.value

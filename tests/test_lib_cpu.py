@@ -1,0 +1,138 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
+every symbol the headers declare, and validates arguments on the host
+(no device call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2308_15964_b300 import build
+    build.build()
+    from paper_2308_15964_b300 import spx
+    return spx
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(spx_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(S):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(S.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert S.lib.spx_abi_version() == 1
+
+
+def test_strerror(S):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8, -9):
+        assert S.strerror(code) and S.strerror(code) != "unknown status code"
+    assert S.strerror(-99) == "unknown status code"
+
+
+FAKE = 0x7f0000000000   # host-side validation never dereferences tile pointers
+
+
+def fake_tiles(g, n, b):
+    T = n // b
+    h = {}
+    for i in range(T):
+        for j in range(T):
+            h[i, j] = g.register(FAKE + 8 * (i * b * n + j * b), b, b, n)
+    return h
+
+
+def test_register_validation(S):
+    g = S.Graph()
+    with pytest.raises(S.SpxError) as e:
+        g.register(0, 4, 4, 4)
+    assert e.value.code == S.ERR_INVALID_ARG
+    for bad in [(FAKE, 0, 4, 4), (FAKE, 4, 0, 4), (FAKE, 4, 8, 4)]:
+        with pytest.raises(S.SpxError):
+            g.register(*bad)
+    h1 = g.register(FAKE, 4, 4, 8)
+    assert g.register(FAKE, 4, 4, 8) == h1          # same address, same handle
+    with pytest.raises(S.SpxError):
+        g.register(FAKE, 4, 5, 8)                    # same address, other shape
+    h2 = g.register(FAKE + 32, 4, 4, 8)
+    assert h2 == h1 + 1
+    g.close()
+
+
+def test_insert_validation(S):
+    g = S.Graph()
+    h = fake_tiles(g, 256, 64)
+    R, W, C = S.READ, S.WRITE, S.COMMUTATIVE_WRITE
+    assert g.insert(S.OP_POTRF, [h[0, 0]], [W]) == 0
+    assert g.insert(S.OP_TRSM, [h[0, 0], h[1, 0]], [R, W]) == 1
+    assert g.insert(S.OP_GEMM_NT_SUB, [h[1, 0], h[2, 0], h[2, 1]], [R, R, C]) == 2
+    bad = [
+        (S.OP_POTRF, [h[0, 0]], [R]),                       # written operand read-only
+        (S.OP_TRSM, [h[0, 0]], [R]),                        # operand count
+        (S.OP_GEMM_NT_SUB, [h[1, 0], h[1, 0], h[1, 1]], [R, R, W]),  # repeated operand
+        (99, [h[0, 0]], [W]),                               # unknown op
+        (S.OP_NOP, [h[0, 0]], [7]),                         # unknown mode
+    ]
+    for op, hh, mm in bad:
+        with pytest.raises(S.SpxError) as e:
+            g.insert(op, hh, mm)
+        assert e.value.code == S.ERR_INVALID_ARG
+    with pytest.raises(S.SpxError) as e:
+        g.insert(S.OP_NOP, [12345], [R])
+    assert e.value.code == S.ERR_BAD_HANDLE
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_NOP, [h[0, 0]], [R], prec=9)
+    # shape mismatch: TRSM needs A_ik.cols == L_kk.rows
+    odd = g.register(FAKE + (1 << 30), 64, 32, 64)
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_TRSM, [h[0, 0], odd], [R, W])
+    # NOP / SPIN accept any handles and modes, repeated handles merge
+    assert g.insert(S.OP_NOP, [h[0, 0], h[0, 0], h[1, 1]], [R, C, W]) == 3
+    with pytest.raises(S.SpxError) as e:
+        g.set_arg(100, 5)
+    assert e.value.code == S.ERR_BAD_HANDLE
+    g.set_arg(0, 64)
+    n, ne, nacc, nt = g.sizes()
+    assert (n, nacc, nt) == (4, 1 + 2 + 3 + 2, 17) and ne == -1
+    g.close()
+
+
+def test_state_errors(S):
+    g = S.Graph()
+    rc, info = g.wait()
+    assert rc == S.ERR_STATE
+    with pytest.raises(S.SpxError) as e:
+        g.edges()
+    assert e.value.code == S.ERR_STATE
+    with pytest.raises(S.SpxError):
+        g.reset()
+    with pytest.raises(S.SpxError) as e:
+        g.execute(0)                                    # empty graph
+    assert e.value.code == S.ERR_STATE
+    h = g.register(FAKE, 8, 8, 8)
+    g.insert(S.OP_NOP, [h], [S.WRITE])
+    g.clear()
+    assert g.sizes()[0] == 0 and g.sizes()[3] == 0
+    g.close()
+    g.close()
+
+
+def test_config_validation(S):
+    with pytest.raises(S.SpxError):
+        S.Graph(executor=7)
+    with pytest.raises(S.SpxError):
+        S.Graph(num_ctas=-1)
