@@ -1,0 +1,342 @@
+"""Benchmark: FP64 tiled Cholesky as a device-scheduled STF task graph on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl spx|reference]
+                    [--n 16384] [--tile 512]
+
+One step = the whole hot path on one synthetic SPD matrix resident in HBM:
+insert the task graph (spx_cholesky_insert: POTRF/TRSM/SYRK/GEMM tasks),
+derive the DAG on the device, run it in the persistent kernel, wait.  The
+matrix is restored from a pristine copy before each step (outside the timed
+events).  Inputs (2.1 GB) are larger than L2, so no flush is needed.
+
+Printed: one JSON line (rank 0) with GFLOP/s (n^3/3 per step), tasks/s,
+p50/p99 step latency, the one-launch-per-task baseline on the same GPU,
+the small-matrix latency case (n=512, tile 64), the roofline of the
+persistent kernel against the FP64 SIMT peak, the end-to-end number through
+host buffers, the CPU oracle on a bounded sample, and the SM clocks seen.
+
+--impl reference times the CPU oracle (plain single-threaded FP64 loops,
+insertion order) on a bounded sample of the same workload.
+
+Under torchrun (N > 1) every rank factors its own matrix (replicas: the
+workload has no exchange step); value = all ranks' flops / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+METRIC = "Cholesky GFLOP/s & tasks/s (device DAG vs per-task launch); p50/p99 latency"
+PEAKS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+# FP64 SIMT peak: 2 DFMA per clock per SM (measured by spx_probe: 1.127 TFLOP/s
+# at 1942 MHz on 148 SMs) x 2 flop x 148 SMs x 2032 MHz maximum SM clock.
+FP64_DFMA_PER_CLK_SM = 2
+ORACLE_SAMPLE_N = 4096      # CPU baseline sample (about 10 s on one core)
+REFERENCE_STEP_N = 2048     # --impl reference: one step of the oracle
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="spx", choices=["spx", "reference"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--tile", type=int, default=512)
+    p.add_argument("--sigma", type=float, default=0.1)
+    p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_gflops(n: int, b: int, sigma: float, seed: int):
+    from oracle import oracle as O
+    from paper_2308_15964_b300 import inputs
+    A = inputs.spd_matrix(n, sigma, seed).numpy()
+    dt, info = O.timed_tiled_cholesky(A, b)
+    assert info == 0
+    return n ** 3 / 3.0 / dt / 1e9, dt
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n, b = REFERENCE_STEP_N, args.tile
+    times = []
+    for i in range(args.warmup + args.steps):
+        gf, dt = cpu_oracle_gflops(n, b, args.sigma, seed=2)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps * (n ** 3 / 3.0) / total / 1e9
+    sample = (f"tiled Cholesky oracle (single-threaded FP64 loops, insertion order) on n={n}, "
+              f"tile {b}, sigma {args.sigma}: one factorization per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"tiled Cholesky FP64, sample n={n} tile={b} of the n={args.n} workload",
+                   "n": n, "tile": b},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_setup()
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2308_15964_b300 import cholesky, inputs, spx
+
+    n, b = args.n, args.tile
+    flops = cholesky.cholesky_flops(n)
+    A0 = inputs.spd_matrix(n, args.sigma, seed=2, device="cuda")
+    A = torch.empty_like(A0)
+    stream = torch.cuda.current_stream()
+    g = spx.Graph()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step(graph, record=None):
+        A.copy_(A0)
+        ev[0].record()
+        graph.clear()
+        cholesky.cholesky_graph(graph, A, b)
+        graph.execute(stream)
+        rc, info = graph.wait()
+        ev[1].record()
+        ev[1].synchronize()
+        assert rc == spx.OK, (rc, info)
+        if record is not None:
+            record.append((ev[0].elapsed_time(ev[1]), graph.timing()[1]))
+
+    for _ in range(args.warmup):
+        step(g)
+    ntasks, nedges, _, _ = g.sizes()
+    recs = []
+    torch.cuda.synchronize()
+    barrier(world)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(g, recs)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    step_ms = [r[0] for r in recs]
+    run_ms = [r[1] for r in recs]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = world * args.steps * flops / (total_ms * 1e-3) / 1e9
+    stats = g.stats()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"tiled Cholesky FP64 n={n} tile={b} ({ntasks} tasks, {nedges} edges); "
+                               "step = insert + device DAG derivation + persistent execution",
+                   "n": n, "tile": b, "tasks": ntasks, "edges": nedges, "sigma": args.sigma,
+                   "l2": "inputs larger than L2 (matrix 8n^2 bytes)",
+                   "parallelism": f"replicas x{world}"},
+        "tasks_per_s": ntasks / (statistics.mean(step_ms) * 1e-3),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "wall_s": wall,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "sched": {"parts": stats["parts"], "ctas": stats["ctas"],
+                  "busy_frac": stats["busy_cycles"] / max(1, stats["total_cycles"]),
+                  "queue_hiwater": stats["queue_hiwater"]},
+    }
+
+    # Roofline of the dominant kernel (the persistent executor): algorithmic
+    # flops n^3/3 per launch / its CUDA-event duration, against the FP64 SIMT
+    # peak derived from the measured DFMA rate per SM and the max SM clock.
+    sms = spx.lib.spx_device_sm_count()
+    max_mhz = clocks.get("sm_max_mhz") or 2032.0
+    peak = FP64_DFMA_PER_CLK_SM * 2 * sms * max_mhz * 1e6 / 1e12
+    run_mean = statistics.mean(run_ms)
+    achieved = flops / (run_mean * 1e-3) / 1e12
+    probe_rate, _ = spx.probe(0, 4000)
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "persistent_kernel (FP64 DFMA tile ops)",
+                       "kernel_ms": run_mean,
+                       "peak_note": "2 DFMA/clk/SM x 148 SMs x max SM clock (derived); "
+                                    f"live DFMA probe {probe_rate / 1e12:.3f} TFLOP/s"}
+
+    if rank == 0 and not args.no_extras:
+        # one-launch-per-task baseline, same tile code, same stream
+        gb = spx.Graph(executor=spx.EXEC_PER_TASK)
+        step(gb)
+        brec = []
+        for _ in range(2):
+            step(gb, brec)
+        bms = [r[0] for r in brec]
+        out["baseline_per_task"] = {"value": flops / (statistics.mean(bms) * 1e-3) / 1e9,
+                                    "unit": "GFLOP/s", "ms_per_step": statistics.mean(bms),
+                                    "tasks_per_s": ntasks / (statistics.mean(bms) * 1e-3),
+                                    "p99_ms": float(np.percentile(bms, 99)), "steps": len(bms)}
+        gb.close()
+        out["latency_small"] = small_latency(spx, cholesky, inputs, torch)
+
+        # end to end through host buffers: H2D of A, the step, D2H of L
+        Ah = A0.cpu().pin_memory()
+        Lh = torch.empty_like(Ah).pin_memory()
+        e2e = []
+        for i in range(3):
+            ev[0].record()
+            A.copy_(Ah, non_blocking=True)
+            g.clear()
+            cholesky.cholesky_graph(g, A, b)
+            g.execute(stream)
+            rc, _ = g.wait()
+            assert rc == spx.OK
+            Lh.copy_(A, non_blocking=True)
+            ev[1].record()
+            ev[1].synchronize()
+            if i > 0:
+                e2e.append(ev[0].elapsed_time(ev[1]))
+        out["e2e"] = {"value": flops / (statistics.mean(e2e) * 1e-3) / 1e9, "unit": "GFLOP/s",
+                      "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
+                      "ms_per_step": statistics.mean(e2e)}
+        del Ah, Lh
+        gf, dt = cpu_oracle_gflops(ORACLE_SAMPLE_N, b, args.sigma, seed=2)
+        out["cpu_baseline"] = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"tiled Cholesky oracle, n={ORACLE_SAMPLE_N} tile {b} "
+                                         f"(same tile and recipe, {dt:.1f} s on one host core; "
+                                         f"host has {os.cpu_count()} cores)"}
+    g.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def small_latency(spx, cholesky, inputs, torch, reps=200):
+    """Latency of the small case (n=512, tile 64, 120 factorization tasks):
+    execute -> wait on a reset graph, persistent vs per-task executor."""
+    n, b = 512, 64
+    A0 = inputs.spd_matrix(n, 1.0, seed=1, device="cuda")
+    A = torch.empty_like(A0)
+    res = {}
+    for name, ex, rederive in (("persistent", spx.EXEC_PERSISTENT, False),
+                               ("persistent_insert_derive", spx.EXEC_PERSISTENT, True),
+                               ("per_task", spx.EXEC_PER_TASK, False)):
+        g = spx.Graph(executor=ex)
+        cholesky.cholesky_graph(g, A, b)
+        lat = []
+        for i in range(reps + 5):
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if rederive and i > 0:
+                g.clear()
+                cholesky.cholesky_graph(g, A, b)
+            g.execute()
+            rc, _ = g.wait()
+            t1 = time.perf_counter()
+            assert rc == spx.OK
+            if not rederive:
+                g.reset()
+            if i >= 5:
+                lat.append((t1 - t0) * 1e3)
+        res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "gflops": cholesky.cholesky_flops(n) / (np.median(lat) * 1e-3) / 1e9}
+        g.close()
+    res["workload"] = ("n=512 tile=64, 120 tasks, host wall time of execute->wait; persistent and "
+                       "per_task reuse the inserted graph (reset), persistent_insert_derive inserts "
+                       "and derives every time")
+    return res
+
+
+if __name__ == "__main__":
+    main()

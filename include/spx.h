@@ -209,6 +209,13 @@ int spx_graph_trace(spx_graph_t g, unsigned long long* rec);
  * cycles summed over CTAs.  n = number of values wanted (<= 6). */
 int spx_graph_stats(spx_graph_t g, long long* out, int n);
 
+/* Device time of the last execution, from CUDA events recorded on the
+ * execute stream: prep_ms = queue/state reset plus DAG derivation (or the
+ * re-initialisation of a reset graph), run_ms = the executor (the persistent
+ * kernel, or all per-task launches).  Either pointer may be NULL.
+ * Errors: SPX_ERR_STATE (no finished execution). */
+int spx_graph_timing(spx_graph_t g, float* prep_ms, float* run_ms);
+
 /* Write the derived task graph in Graphviz dot format (paper, section
  * "Visualization", generateDot).  Errors: SPX_ERR_STATE, SPX_ERR_INVALID_ARG
  * (cannot open path). */
@@ -224,6 +231,34 @@ int spx_graph_clear(spx_graph_t g);
 
 /* Free the graph.  Waits for a running graph first.  NULL is ignored. */
 void spx_graph_destroy(spx_graph_t g);
+
+/* Insert the whole tiled Cholesky of the paper's numerical applications
+ * (section "Numerical applications": POTRF on diagonal tiles, TRSM, SYRK and
+ * GEMM on the others), right-looking with k outer:
+ *   for k: POTRF(k); TRSM(i,k) for i>k; SYRK(i,k) for i>k;
+ *          GEMM(i,j,k) for j>k, i>j (j outer)
+ * and, when dev_X != NULL, the block solve A Y = X (Y over X): forward
+ * TRSM_L_FWD(k), GEMM_FWD(i,k) for k ascending, then backward
+ * TRSM_LT_BWD(k), GEMM_BWD(i,k) for k descending.
+ *   dev_A   n x n FP64 row-major (lda >= n); the lower triangle is replaced by
+ *           L, the strict upper triangle is not touched.  Tiles are b x b
+ *           (the last tile row/column is ragged when b does not divide n).
+ *   dev_X   n x nrhs FP64 row-major (ldx >= nrhs) or NULL.
+ *   lookahead  1: POTRF, TRSM, SYRK, the GEMMs of the next panel column and
+ *           the diagonal solves get the high priority.
+ *   prec    SPX_F64.
+ *   out_ntasks  number of tasks inserted (may be NULL).
+ * Errors: as spx_tile_register / spx_task_insert; tasks inserted before an
+ * error stay in the graph. */
+int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b, double* dev_X,
+                        int nrhs, int ldx, int lookahead, int prec, long long* out_ntasks);
+
+/* Insert the tiled GEMM C += A B of the paper's numerical applications: one
+ * GEMM_NN_ADD task per (i, j, k), i and j outer, k inner, each with a WRITE
+ * (or, with commutative = 1, a COMMUTATIVE_WRITE) on the block C_ij.  A, B, C
+ * are n x n FP64 row-major with leading dimension ld; tiles b x b. */
+int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n, int ld,
+                    int b, int commutative, long long* out_ntasks);
 
 /* Static description of a status code. */
 const char* spx_strerror(int code);

@@ -119,6 +119,7 @@ struct spx_graph {
   size_t pcap = 0;
   RunState* host_rs = nullptr;  // pinned copy of the run state
   cudaEvent_t done_ev = nullptr;
+  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};  // derive start, run start, run end
   cudaStream_t last_stream = nullptr;
   Layout lay{};
   DevGraph dg{};
@@ -174,6 +175,8 @@ int ensure_device(spx_graph* g) {
   e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess || n == 0) return SPX_ERR_NO_DEVICE;
   e = cudaEventCreateWithFlags(&g->done_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->tev[i]);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaHostAlloc((void**)&g->host_rs, sizeof(RunState), cudaHostAllocDefault);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -471,10 +474,13 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     rc = prepare_device(g, st);
     if (rc != SPX_OK) return rc;
   }
+  e = cudaEventRecord(g->tev[0], st);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (g->cfg.executor == SPX_EXEC_PER_TASK) {
     rc = reset_run_state(g, st);
     if (rc != SPX_OK) return rc;
-    e = launch_per_task(g->dg, g->tasks.data(), st);
+    e = cudaEventRecord(g->tev[1], st);
+    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), st);
   } else {
     if (!g->derived) {
       rc = spx_graph_derive(g, stream);  // also resets the run state
@@ -487,8 +493,10 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
       }
       if (rc != SPX_OK) return rc;
     }
-    e = launch_persistent(g->dg, g->cfg.num_ctas, st);
+    e = cudaEventRecord(g->tev[1], st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, st);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(g->done_ev, st);
@@ -621,6 +629,18 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
   return SPX_OK;
 }
 
+int spx_graph_timing(spx_graph_t g, float* prep_ms, float* run_ms) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state != kDone || !g->tev[0]) return SPX_ERR_STATE;
+  float a = 0.f, b = 0.f;
+  cudaError_t e = cudaEventElapsedTime(&a, g->tev[0], g->tev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&b, g->tev[1], g->tev[2]);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (prep_ms) *prep_ms = a;
+  if (run_ms) *run_ms = b;
+  return SPX_OK;
+}
+
 int spx_graph_reset(spx_graph_t g) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state != kDone) return SPX_ERR_STATE;
@@ -657,6 +677,8 @@ void spx_graph_destroy(spx_graph_t g) {
   if (g->pinned) cudaFreeHost(g->pinned);
   if (g->host_rs) cudaFreeHost(g->host_rs);
   if (g->done_ev) cudaEventDestroy(g->done_ev);
+  for (int i = 0; i < 3; ++i)
+    if (g->tev[i]) cudaEventDestroy(g->tev[i]);
   delete g;
 }
 

@@ -1,0 +1,117 @@
+// Task-graph builders for the paper's workloads (section "Numerical
+// applications"), written on top of the public insertion calls so that a
+// whole graph is inserted in one C call:
+//   * tiled Cholesky A = L L^T with POTRF, TRSM, SYRK and GEMM tasks,
+//     right-looking, k outer, optionally followed by the block forward and
+//     back solves of A Y = X;
+//   * tiled GEMM C += A B with one task per (i, j, k) that depends on the
+//     block C_ij it updates.
+#include <vector>
+
+#include "spx.h"
+
+namespace {
+
+struct Tiles {
+  int T = 0, b = 0;
+  std::vector<unsigned> h;
+  unsigned& at(int i, int j) { return h[(size_t)i * T + j]; }
+};
+
+int register_tiles(spx_graph_t g, double* base, int n_rows, int n_cols, int ld, int b,
+                   bool lower_only, Tiles& out) {
+  const int Tr = (n_rows + b - 1) / b, Tc = (n_cols + b - 1) / b;
+  out.T = Tr > Tc ? Tr : Tc;
+  out.b = b;
+  out.h.assign((size_t)out.T * out.T, 0xFFFFFFFFu);
+  for (int i = 0; i < Tr; ++i)
+    for (int j = 0; j < Tc; ++j) {
+      if (lower_only && j > i) continue;
+      const int r = n_rows - i * b < b ? n_rows - i * b : b;
+      const int c = n_cols - j * b < b ? n_cols - j * b : b;
+      int rc = spx_tile_register(g, base + (size_t)i * b * ld + (size_t)j * b, r, c, ld, SPX_DT_F64,
+                                 nullptr, 0, &out.at(i, j));
+      if (rc != SPX_OK) return rc;
+    }
+  return SPX_OK;
+}
+
+}  // namespace
+
+extern "C" int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                   double* dev_X, int nrhs, int ldx, int lookahead, int prec,
+                                   long long* out_ntasks) {
+  if (!g || !dev_A || n < 1 || b < 1 || lda < n || prec != SPX_F64 ||
+      (dev_X && (nrhs < 1 || ldx < nrhs)))
+    return SPX_ERR_INVALID_ARG;
+  Tiles A;
+  int rc = register_tiles(g, dev_A, n, n, lda, b, true, A);
+  if (rc != SPX_OK) return rc;
+  const int T = A.T;
+  const int R = SPX_READ, W = SPX_WRITE;
+  const int hi = lookahead ? 1 : 0;
+  long long count = 0;
+  auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
+                 int prio, unsigned* id) {
+    const unsigned* hp = hs.begin();
+    const int* mp = ms.begin();
+    int r = spx_task_insert(g, op, hp, mp, (int)hs.size(), prio, prec, id);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+    unsigned t = 0;
+    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, hi, &t);
+    if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
+    for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+      rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, hi, nullptr);
+    for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+      rc = ins(SPX_OP_SYRK, {A.at(i, k), A.at(i, i)}, {R, W}, hi, nullptr);
+    for (int j = k + 1; j < T && rc == SPX_OK; ++j)
+      for (int i = j + 1; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_GEMM_NT_SUB, {A.at(i, k), A.at(j, k), A.at(i, j)}, {R, R, W},
+                 j == k + 1 ? hi : 0, nullptr);
+  }
+  if (rc == SPX_OK && dev_X) {
+    std::vector<unsigned> x(T);
+    for (int i = 0; i < T && rc == SPX_OK; ++i) {
+      const int r = n - i * b < b ? n - i * b : b;
+      rc = spx_tile_register(g, dev_X + (size_t)i * b * ldx, r, nrhs, ldx, SPX_DT_F64, nullptr, 0,
+                             &x[i]);
+    }
+    for (int k = 0; k < T && rc == SPX_OK; ++k) {
+      rc = ins(SPX_OP_TRSM_L_FWD, {A.at(k, k), x[k]}, {R, W}, hi, nullptr);
+      for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_GEMM_FWD, {A.at(i, k), x[k], x[i]}, {R, R, W}, 0, nullptr);
+    }
+    for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
+      rc = ins(SPX_OP_TRSM_LT_BWD, {A.at(k, k), x[k]}, {R, W}, hi, nullptr);
+      for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
+        rc = ins(SPX_OP_GEMM_BWD, {A.at(k, i), x[k], x[i]}, {R, R, W}, 0, nullptr);
+    }
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,
+                               int ld, int b, int commutative, long long* out_ntasks) {
+  if (!g || !dev_A || !dev_B || !dev_C || n < 1 || b < 1 || ld < n) return SPX_ERR_INVALID_ARG;
+  Tiles A, B, C;
+  int rc = register_tiles(g, dev_A, n, n, ld, b, false, A);
+  if (rc == SPX_OK) rc = register_tiles(g, dev_B, n, n, ld, b, false, B);
+  if (rc == SPX_OK) rc = register_tiles(g, dev_C, n, n, ld, b, false, C);
+  const int T = A.T;
+  const int mode = commutative ? SPX_COMMUTATIVE_WRITE : SPX_WRITE;
+  long long count = 0;
+  for (int i = 0; i < T && rc == SPX_OK; ++i)
+    for (int j = 0; j < T && rc == SPX_OK; ++j)
+      for (int k = 0; k < T && rc == SPX_OK; ++k) {
+        const unsigned hs[3] = {A.at(i, k), B.at(k, j), C.at(i, j)};
+        const int ms[3] = {SPX_READ, SPX_READ, mode};
+        rc = spx_task_insert(g, SPX_OP_GEMM_NN_ADD, hs, ms, 3, 0, SPX_F64, nullptr);
+        if (rc == SPX_OK) ++count;
+      }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}

@@ -63,6 +63,9 @@ def _load():
         "spx_graph_clear": (I, [P]),
         "spx_graph_destroy": (None, [P]),
         "spx_strerror": (ctypes.c_char_p, [I]),
+        "spx_graph_timing": (I, [P, P, P]),
+        "spx_cholesky_insert": (I, [P, P, I, I, I, P, I, I, I, I, P]),
+        "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),
         "spx_device_sm_count": (I, []),
@@ -200,6 +203,12 @@ class Graph:
         _check(lib.spx_graph_stats(self._h, _ptr(v), 6), "spx_graph_stats")
         keys = ["parts", "queue_hiwater", "empty_pops", "ctas", "busy_cycles", "total_cycles"]
         return dict(zip(keys, (int(x) for x in v)))
+
+    def timing(self):
+        """(prep_ms, run_ms) of the last execution (device events)."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(lib.spx_graph_timing(self._h, ctypes.byref(a), ctypes.byref(b)), "spx_graph_timing")
+        return a.value, b.value
 
     def write_dot(self, path: str):
         _check(lib.spx_graph_write_dot(self._h, path.encode()), "spx_graph_write_dot")
