@@ -260,6 +260,46 @@ int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b, dou
 int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n, int ld,
                     int b, int commutative, long long* out_ntasks);
 
+/* Largest inputs of spx_graph_derive_noalloc (its fixed scratch is sized
+ * for these: about 5.3 MB of device memory per GPU). */
+#define SPX_NOALLOC_MAX_RECORDS 262144
+#define SPX_NOALLOC_MAX_HANDLES 65536
+
+/* Dependency derivation that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a host callback, a runtime that owns every device byte through
+ * its own pool, a server that must not touch the allocator while it serves)
+ * and therefore cannot use a graph object, whose execute call allocates.
+ * It computes the same successor CSR and in-degrees as spx_graph_derive, from
+ * access records the caller already holds in device memory, using a fixed
+ * scratch array inside the library instead of allocated scratch.
+ *   dev_task_rec   [ntasks+1] first record of each task; task_rec[0] = 0,
+ *                  task_rec[ntasks] = nrec, 1..16 records per task.
+ *   dev_rec_handle [nrec] handle of each record (< nhandles); a task names a
+ *                  handle at most once (merge repeated accesses first).
+ *   dev_rec_seq    [nrec] position of the record on its handle's list: the
+ *                  records of handle h, in task order, have 0, 1, 2, ...
+ *   dev_rec_mode   [nrec] SPX_READ / SPX_WRITE / SPX_COMMUTATIVE_WRITE.
+ *   dev_row_ptr    [ntasks+1] out; dev_col [col_cap] out; dev_indeg [ntasks]
+ *                  out; dev_status [1] out (device int).
+ * Asynchronous on stream.  Host-side errors (returned): SPX_ERR_INVALID_ARG
+ * for NULL pointers, bad counts, or nrec > SPX_NOALLOC_MAX_RECORDS or
+ * nhandles > SPX_NOALLOC_MAX_HANDLES; SPX_ERR_CUDA if the set-up or the launch
+ * fails.  Device-side (in *dev_status once the stream reaches it): 0, or
+ * SPX_ERR_INVALID_ARG for malformed records, or for col_cap smaller than the
+ * number of edges, which is then in dev_row_ptr[ntasks] (col and indeg not
+ * written).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the scratch array: calls that
+ * overlap on the GPU (other streams, other threads) race and give wrong
+ * results; calls in sequence on one stream are independent. */
+int spx_graph_derive_noalloc(const unsigned* dev_task_rec, const unsigned* dev_rec_handle,
+                             const unsigned* dev_rec_seq, const unsigned char* dev_rec_mode,
+                             int ntasks, int nhandles, long long nrec, unsigned* dev_row_ptr,
+                             unsigned* dev_col, long long col_cap, unsigned* dev_indeg,
+                             int* dev_status, void* stream);
+
 /* Static description of a status code. */
 const char* spx_strerror(int code);
 

@@ -1,0 +1,164 @@
+// Device steps of the dependency derivation, shared by the derivation
+// kernels.  One CTA of kDeriveThreads threads runs every step; block
+// barriers separate the steps.  See derive.cu for the model and the steps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx_internal.h"
+
+namespace spx {
+namespace {
+
+constexpr int kDeriveThreads = 1024;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// In-place exclusive scan of a[0..n) by the whole CTA; returns the total.
+// Every thread must call it.
+__device__ uint32_t block_excl_scan(uint32_t* a, uint32_t n, uint32_t* sh) {
+  constexpr int kItems = 4;
+  constexpr int kWarps = kDeriveThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < n; base += kDeriveThreads * kItems) {
+    uint32_t v[kItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t idx = base + tid * kItems + i;
+      v[i] = idx < n ? a[idx] : 0u;
+      sum += v[i];
+    }
+    const uint32_t incl = warp_incl_scan(sum);
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = lane < kWarps ? sh[lane] : 0u;
+      const uint32_t wi = warp_incl_scan(w);
+      if (lane < kWarps) sh[lane] = wi - w;
+      if (lane == kWarps - 1) sh[kWarps] = wi;
+    }
+    __syncthreads();
+    uint32_t run = carry + sh[warp] + incl - sum;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t idx = base + tid * kItems + i;
+      if (idx < n) a[idx] = run;
+      run += v[i];
+    }
+    carry += sh[kWarps];
+    __syncthreads();
+  }
+  return carry;
+}
+
+__device__ __forceinline__ bool group_start(const DevGraph& g, uint32_t p) {
+  const uint8_t m = g.s_mode[p];
+  return g.s_first[p] || m == SPX_WRITE || m != g.s_mode[p - 1];
+}
+
+// Unique successors of task u: merge of the next-group ranges of its
+// accesses.  With col == nullptr only counts; else writes col[0..] and bumps
+// the successors' in-degrees.
+__device__ uint32_t merge_successors(const DevGraph& g, uint32_t u, uint32_t ngroups,
+                                     uint32_t* col) {
+  uint32_t a[kMaxHandles], b[kMaxHandles];
+  const uint32_t r0 = g.task_rec[u], r1 = g.task_rec[u + 1];
+  const int k = (int)(r1 - r0);
+  for (int i = 0; i < k; ++i) {
+    const uint32_t p = g.rec_pos[r0 + i];
+    const uint32_t gi = g.gid[p];
+    a[i] = b[i] = 0;
+    if (gi + 1 < ngroups) {
+      const uint32_t q = g.gpos[gi + 1];
+      if (!g.s_first[q]) {  // next group on the same handle
+        a[i] = q;
+        b[i] = g.gpos[gi + 2];
+      }
+    }
+  }
+  uint32_t count = 0;
+  for (;;) {
+    uint32_t mn = 0xFFFFFFFFu;
+    for (int i = 0; i < k; ++i)
+      if (a[i] < b[i]) mn = min(mn, g.s_task[a[i]]);
+    if (mn == 0xFFFFFFFFu) break;
+    if (col) {
+      col[count] = mn;
+      atomicAdd(&g.indeg[mn], 1u);
+    }
+    ++count;
+    for (int i = 0; i < k; ++i)
+      if (a[i] < b[i] && g.s_task[a[i]] == mn) ++a[i];
+  }
+  return count;
+}
+
+// Steps 1-4: per-handle lists, groups, unique successors (row_ptr, col,
+// indeg).  Reads rec_*, task_rec; uses hptr, s_task, s_mode, s_first,
+// rec_pos, gid, gpos as scratch.  Returns false, with row_ptr[ntasks] = E
+// and col / indeg not written, when E > ecap.  Every thread must call it.
+__device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
+  const uint32_t N = g.ntasks, H = g.ntiles, M = g.nrec;
+  const int tid = threadIdx.x;
+
+  // 1. accesses per handle -> list offsets
+  for (uint32_t i = tid; i <= H; i += kDeriveThreads) g.hptr[i] = 0;
+  for (uint32_t i = tid; i < N; i += kDeriveThreads) g.indeg[i] = 0;
+  __syncthreads();
+  for (uint32_t r = tid; r < M; r += kDeriveThreads) atomicAdd(&g.hptr[g.rec_handle[r]], 1u);
+  __syncthreads();
+  block_excl_scan(g.hptr, H + 1, sh);
+  __syncthreads();
+
+  // 2. per-handle lists in insertion order
+  for (uint32_t u = tid; u < N; u += kDeriveThreads) {
+    for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r) {
+      const uint32_t seq = g.rec_seq[r];
+      const uint32_t p = g.hptr[g.rec_handle[r]] + seq;
+      g.s_task[p] = u;
+      g.s_mode[p] = g.rec_mode[r];
+      g.s_first[p] = seq == 0 ? 1 : 0;
+      g.rec_pos[r] = p;
+    }
+  }
+  __syncthreads();
+
+  // 3. groups
+  for (uint32_t p = tid; p < M; p += kDeriveThreads) g.gid[p] = group_start(g, p) ? 1u : 0u;
+  __syncthreads();
+  const uint32_t G = block_excl_scan(g.gid, M, sh);
+  __syncthreads();
+  for (uint32_t p = tid; p < M; p += kDeriveThreads) {
+    const bool f = group_start(g, p);
+    const uint32_t gi = g.gid[p] + (f ? 1u : 0u) - 1u;
+    g.gid[p] = gi;
+    if (f) g.gpos[gi] = p;
+  }
+  if (tid == 0) g.gpos[G] = M;
+  __syncthreads();
+
+  // 4. unique successors: count, scan, write
+  for (uint32_t u = tid; u < N; u += kDeriveThreads) g.row_ptr[u] = merge_successors(g, u, G, nullptr);
+  if (tid == 0) g.row_ptr[N] = 0;
+  __syncthreads();
+  const uint32_t E = block_excl_scan(g.row_ptr, N + 1, sh);
+  __syncthreads();
+  if (E > g.ecap) return false;
+  for (uint32_t u = tid; u < N; u += kDeriveThreads) merge_successors(g, u, G, g.col + g.row_ptr[u]);
+  __syncthreads();
+  return true;
+}
+
+}  // namespace
+}  // namespace spx

@@ -66,6 +66,7 @@ def _load():
         "spx_graph_timing": (I, [P, P, P]),
         "spx_cholesky_insert": (I, [P, P, I, I, I, P, I, I, I, I, P]),
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
+        "spx_graph_derive_noalloc": (I, [P, P, P, P, I, I, LL, P, P, LL, P, P, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),
         "spx_device_sm_count": (I, []),
