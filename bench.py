@@ -205,9 +205,11 @@ def main():
     barrier(world)
     with Clocks(local) as clk:
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("spx_timed")
         for _ in range(args.steps):
             step(g, recs)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier(world)
         wall = time.perf_counter() - t0
     clocks = clk.summary()

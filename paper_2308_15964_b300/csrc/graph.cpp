@@ -43,7 +43,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t tasks, tiles, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
   size_t queue0, queue1, t_start, ff_end;
-  size_t rs, locks, t_end, trace, zero_end;
+  size_t rs, locks, t_end, trace, phase, zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
@@ -71,6 +71,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, bool trace)
   L.locks = take(H * 4);
   L.t_end = take(N * 4);
   L.trace = take(trace ? N * 32 : 0);
+  L.phase = take(N * 4);
   L.zero_end = o;
   L.hptr = take((H + 1) * 4);
   L.s_task = take(M * 4);
@@ -270,6 +271,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.indeg = (uint32_t*)(D + L.indeg);
   d.indeg_w = (uint32_t*)(D + L.indeg_w);
   d.remaining = (uint32_t*)(D + L.remaining);
+  d.phase = (uint32_t*)(D + L.phase);
   g->lay = L;
   g->uploaded = true;
   g->derived = false;
@@ -405,9 +407,18 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   for (int i = 0; i < k; ++i)
     if (mm[i] == SPX_COMMUTATIVE_WRITE) t.flags |= kFlagComm;
   for (int i = 0; i < 3; ++i) t.h[i] = i < nh ? handles[i] : 0;
-  uint32_t parts = 1;
-  if (!g->cfg.no_split && !(t.flags & kFlagComm)) parts = std::min(op_units(op, g->tiles.data(), t.h), kMaxParts);
-  t.nparts = parts;
+  uint32_t items = 1;  // queue entries over all phases
+  if (g->cfg.no_split || (t.flags & kFlagComm)) {
+    t.flags |= kFlagSerial;
+    t.nphases = 1;
+    t.nparts = 1;
+  } else {
+    t.nphases = op_phases(op, g->tiles.data(), t.h);
+    t.nparts = phase_parts(op_phase_units(op, g->tiles.data(), t.h, 0));
+    items = 0;
+    for (uint32_t ph = 0; ph < t.nphases; ++ph)
+      items += phase_parts(op_phase_units(op, g->tiles.data(), t.h, ph));
+  }
   t.arg = 0;
 
   const uint32_t tid = (uint32_t)g->tasks.size();
@@ -429,7 +440,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   g->task_rec.push_back((uint32_t)g->rec_handle.size());
   g->tasks.push_back(t);
-  g->items[t.prio ? 0 : 1] += parts;
+  g->items[t.prio ? 0 : 1] += items;
   g->uploaded = false;
   if (out_task) *out_task = tid;
   return SPX_OK;
@@ -480,7 +491,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     rc = reset_run_state(g, st);
     if (rc != SPX_OK) return rc;
     e = cudaEventRecord(g->tev[1], st);
-    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), st);
+    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), st);
   } else {
     if (!g->derived) {
       rc = spx_graph_derive(g, stream);  // also resets the run state

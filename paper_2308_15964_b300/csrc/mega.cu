@@ -172,17 +172,16 @@ __device__ bool spin_for(const DevGraph& g, long long ns) {
   }
 }
 
-// Run one part of a task with the whole CTA.  Returns 0, or a POTRF info.
-__device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t part, F64Smem& s) {
+// Run units u0..u1 of one phase of a task with the whole CTA.  Returns 0,
+// a POTRF info (1-based column in the tile), or -1 for an unknown op.
+__device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t u0,
+                         uint32_t u1, F64Smem& s) {
   const TileDesc* T = g.tiles;
-  const uint32_t units = op_units(t.op, T, t.h);
-  const uint32_t u0 = (uint32_t)((unsigned long long)part * units / t.nparts);
-  const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / t.nparts);
   switch (t.op) {
     case SPX_OP_POTRF:
-      return op_potrf(T[t.h[0]], s);
+      return op_potrf_units(T[t.h[0]], phase, u0, u1, s);
     case SPX_OP_TRSM:
-      op_trsm(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_SYRK:
       op_syrk(T[t.h[0]], T[t.h[1]], u0, u1, s);
@@ -216,6 +215,45 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t part, F64
   }
 }
 
+// Run part `part` of phase `phase`; a serial task runs all of its phases
+// and units here, in order.
+__device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t part,
+                        F64Smem& s) {
+  const TileDesc* T = g.tiles;
+  if (t.flags & kFlagSerial) {
+    const uint32_t nph = op_phases(t.op, T, t.h);
+    for (uint32_t ph = 0; ph < nph; ++ph) {
+      const int r = run_units(g, t, ph, 0, op_phase_units(t.op, T, t.h, ph), s);
+      if (r) return r;
+      __syncthreads();
+    }
+    return 0;
+  }
+  const uint32_t units = op_phase_units(t.op, T, t.h, phase);
+  const uint32_t parts = phase_parts(units);
+  const uint32_t u0 = (uint32_t)((unsigned long long)part * units / parts);
+  const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / parts);
+  return run_units(g, t, phase, u0, u1, s);
+}
+
+// Push the np parts of the next phase of task u (warp 0, all lanes).
+__device__ void push_phase(const DevGraph& g, uint32_t u, uint32_t np, uint32_t prio) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t q = prio ? 0u : 1u;
+  uint32_t slot = 0;
+  if (lane == 0) {
+    slot = atomicAdd(&g.rs->tail[q].v, np);
+    atomicMax(&g.rs->hiwater, slot + np);
+  }
+  slot = __shfl_sync(0xffffffffu, slot, 0);
+  if (slot + np > g.qcap) {
+    if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+    return;
+  }
+  for (uint32_t p = lane; p < np; p += 32)
+    *(volatile uint32_t*)&g.queue[q][slot + p] = (u << kPartBits) | p;
+}
+
 // Take the COMMUTATIVE_WRITE locks of task u in ascending handle order
 // (records of a task are sorted by handle).  One thread.  False on abort.
 __device__ bool lock_comm(const DevGraph& g, uint32_t u) {
@@ -247,7 +285,7 @@ __device__ void unlock_comm(const DevGraph& g, uint32_t u) {
 __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_np;
   __shared__ int s_flag;
   const int tid = threadIdx.x;
   RunState* rs = g.rs;
@@ -263,13 +301,15 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     if (item == kExit) break;
     const uint32_t u = item >> kPartBits, part = item & (kMaxParts - 1);
     const TaskDesc t = g.tasks[u];
+    // the phase was written before its parts were pushed (and fenced)
+    const uint32_t phase = t.nphases > 1 ? ld_volatile(&g.phase[u]) : 0u;
     const long long c0 = clock64();
     if (tid == 0) {
       s_flag = 1;
       if (t.flags & kFlagComm) s_flag = lock_comm(g, u) ? 1 : 0;
       const uint32_t tk = atomicAdd(&rs->ticket.v, 1u);
       atomicMin(&g.t_start[u], tk);
-      if (g.trace && part == 0) {
+      if (g.trace && part == 0 && phase == 0) {
         g.trace_rec[4 * u + 0] = globaltimer();
         g.trace_rec[4 * u + 2] = smid();
         g.trace_rec[4 * u + 3] = t.nparts;
@@ -277,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (!s_flag) break;
-    const int info = run_part(g, t, part, s);
+    const int info = run_part(g, t, phase, part, s);
     __syncthreads();
     busy += clock64() - c0;
     if (tid == 0) {
@@ -294,12 +334,21 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         if (g.trace) atomicMax(&g.trace_rec[4 * u + 1], globaltimer());
         atomicAdd(&rs->parts_done, 1u);
         s_flag = atomicSub(&g.remaining[u], 1u) == 1u ? 2 : 1;
+        if (s_flag == 2 && phase + 1 < t.nphases) {
+          // last part of a phase: set up the next phase before pushing it
+          const uint32_t np = phase_parts(op_phase_units(t.op, g.tiles, t.h, phase + 1));
+          *(volatile uint32_t*)&g.phase[u] = phase + 1;
+          atomicExch(&g.remaining[u], np);
+          s_np = np;
+          s_flag = 3;
+        }
         __threadfence();
         touch_progress(g);
       }
     }
     __syncthreads();
     if (s_flag == 0) break;
+    if (s_flag == 3 && tid < 32) push_phase(g, u, s_np, t.prio);
     if (s_flag == 2) {
       if (tid < 32) {
         if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
@@ -322,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
 }
 
 // Baseline: one launch per task, one CTA per part, insertion order.
-__global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u) {
+__global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u, uint32_t phase) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
   __shared__ int s_abort;
@@ -331,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t 
   if (s_abort) return;
   const TaskDesc t = g.tasks[u];
   if (threadIdx.x == 0 && blockIdx.x == 0) touch_progress(g);
-  const int info = run_part(g, t, blockIdx.x, s);
+  const int info = run_part(g, t, phase, blockIdx.x, s);
   if (threadIdx.x == 0) {
     if (info > 0) set_error(g.rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
     else if (info < 0) set_error(g.rs, (uint32_t)SPX_ERR_BAD_OP, 0);
@@ -372,10 +421,16 @@ cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks, cudaStream_t st) {
+cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
+                            const TileDesc* host_tiles, cudaStream_t st) {
   persistent_max_ctas(nullptr);
   for (uint32_t u = 0; u < g.ntasks; ++u) {
-    task_kernel<<<host_tasks[u].nparts, kThreads, sizeof(F64Smem), st>>>(g, u);
+    const TaskDesc& t = host_tasks[u];
+    for (uint32_t ph = 0; ph < t.nphases; ++ph) {
+      const uint32_t np = (t.flags & kFlagSerial)
+                              ? 1u : phase_parts(op_phase_units(t.op, host_tiles, t.h, ph));
+      task_kernel<<<np, kThreads, sizeof(F64Smem), st>>>(g, u, ph);
+    }
   }
   return cudaGetLastError();
 }

@@ -20,7 +20,11 @@ constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
 constexpr int kThreads = 256;             // threads per persistent CTA
 constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 
-enum TaskFlags : uint8_t { kFlagComm = 1 };
+// kFlagComm: the task has a COMMUTATIVE_WRITE access (runs as one part and
+// takes tile locks).  kFlagSerial: one CTA runs every phase and every unit of
+// the task in order (no-split graphs and commutative tasks); the arithmetic
+// per unit is the same as when the units are spread over CTAs.
+enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2 };
 
 // One registered tile (a data handle of the STF model).
 struct TileDesc {
@@ -33,9 +37,9 @@ static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
 // One task: op, operands (handles in op order), parts, argument.
 struct TaskDesc {
   uint8_t op, prec, flags, prio;  // prio: 0 = normal, 1 = high
-  uint32_t nparts;
+  uint32_t nparts;   // parts of phase 0
   uint32_t h[3];
-  uint32_t pad;
+  uint32_t nphases;  // phases run one after another (1 for serial tasks)
   int64_t arg;
 };
 static_assert(sizeof(TaskDesc) == 32, "TaskDesc layout");
@@ -94,7 +98,8 @@ struct DevGraph {
   uint32_t* indeg;             // [ntasks]
   // execution state
   uint32_t* indeg_w;           // [ntasks] remaining predecessors
-  uint32_t* remaining;         // [ntasks] parts not finished
+  uint32_t* remaining;         // [ntasks] parts of the current phase not finished
+  uint32_t* phase;             // [ntasks] current phase of a multi-phase task
   uint32_t* queue[2];          // [qcap] each
   uint32_t* locks;             // [ntiles] owner task + 1, 0 = free
   uint32_t* t_start;           // [ntasks] tickets
@@ -104,30 +109,64 @@ struct DevGraph {
 };
 
 
-// Work units of a task: the 64-granular pieces an op splits into (row blocks
-// of a TRSM, lower block pairs of a SYRK, output blocks of a GEMM, column
-// blocks of a solve).  A task runs as min(units, kMaxParts) parts; part p
-// covers units [p*U/P, (p+1)*U/P).  Shared by host (part counts) and device.
-__host__ __device__ inline uint32_t op_units(int op, const TileDesc* t, const uint32_t* h) {
-  auto cd = [](int a) { return (uint32_t)((a + kBlk - 1) / kBlk); };
+// Phases and work units of a task.  A task runs its phases one after
+// another; the units of a phase are independent 64-granular pieces that any
+// CTAs may run in parallel (parts = min(units, kMaxParts); part p covers
+// units [p*U/P, (p+1)*U/P)).  When the last part of a phase finishes, the
+// parts of the next phase are pushed; after the last phase the task releases
+// its successors.  Shared by the host (part and queue-entry counts) and the
+// device.
+//   POTRF (nb = diagonal 64-blocks): for j = 0..nb-1, phase 3j factors block
+//     (j,j) (1 unit), phase 3j+1 solves blocks (i,j), i > j (nb-1-j units),
+//     phase 3j+2 updates the lower blocks (i,l), j < l <= i
+//     ((nb-1-j)(nb-j)/2 units); 3nb-2 phases.
+//   TRSM (A m x n, nbr row blocks, nbc column blocks): for j = 0..nbc-1,
+//     phase 2j solves column block j of every row block (nbr units), phase
+//     2j+1 updates the column blocks l > j (nbr*(nbc-1-j) units).
+//   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
+//     blocks.  Solves: one phase, 64-column blocks of the right-hand sides.
+__host__ __device__ inline uint32_t cdiv64(int a) { return (uint32_t)((a + kBlk - 1) / kBlk); }
+
+__host__ __device__ inline uint32_t op_phases(int op, const TileDesc* t, const uint32_t* h) {
   switch (op) {
-    case SPX_OP_TRSM: return cd(t[h[1]].rows);
-    case SPX_OP_SYRK: { const uint32_t nb = cd(t[h[1]].rows); return nb * (nb + 1) / 2; }
+    case SPX_OP_POTRF: return 3 * cdiv64(t[h[0]].rows) - 2;
+    case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1;
+    default: return 1;
+  }
+}
+
+__host__ __device__ inline uint32_t op_phase_units(int op, const TileDesc* t, const uint32_t* h,
+                                                   uint32_t phase) {
+  switch (op) {
+    case SPX_OP_POTRF: {
+      const uint32_t nb = cdiv64(t[h[0]].rows), j = phase / 3, r = nb - 1 - j;
+      return phase % 3 == 0 ? 1u : (phase % 3 == 1 ? r : r * (r + 1) / 2);
+    }
+    case SPX_OP_TRSM: {
+      const uint32_t nbr = cdiv64(t[h[1]].rows), nbc = cdiv64(t[h[1]].cols), j = phase / 2;
+      return phase % 2 == 0 ? nbr : nbr * (nbc - 1 - j);
+    }
+    case SPX_OP_SYRK: { const uint32_t nb = cdiv64(t[h[1]].rows); return nb * (nb + 1) / 2; }
     case SPX_OP_GEMM_NT_SUB:
     case SPX_OP_GEMM_NN_ADD:
     case SPX_OP_GEMM_FWD:
-    case SPX_OP_GEMM_BWD: return cd(t[h[2]].rows) * cd(t[h[2]].cols);
+    case SPX_OP_GEMM_BWD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
     case SPX_OP_TRSM_L_FWD:
-    case SPX_OP_TRSM_LT_BWD: return cd(t[h[1]].cols);
+    case SPX_OP_TRSM_LT_BWD: return cdiv64(t[h[1]].cols);
     default: return 1;
   }
+}
+
+__host__ __device__ inline uint32_t phase_parts(uint32_t units) {
+  return units < kMaxParts ? units : kMaxParts;
 }
 
 // Launchers implemented in the .cu files (all asynchronous on stream).
 cudaError_t launch_derive(const DevGraph& g, cudaStream_t st);
 cudaError_t launch_init(const DevGraph& g, cudaStream_t st);  // reset run state only
 cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st);
-cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks, cudaStream_t st);
+cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
+                            const TileDesc* host_tiles, cudaStream_t st);
 int persistent_max_ctas(int* per_sm);
 size_t persistent_smem_bytes();
 

@@ -195,64 +195,9 @@ __device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, 
 }
 
 // ---------------------------------------------------------------------------
-// Task ops.  u0..u1 is the range of work units of this part (see op_units).
+// Task ops.  u0..u1 is the range of work units of this part (see
+// op_phase_units).
 // ---------------------------------------------------------------------------
-
-// POTRF on an n x n tile (one part): left-looking by 64-column panels.
-// Returns 0 or the 1-based local column of the failed pivot.
-__device__ int op_potrf(const TileDesc& A, F64Smem& s) {
-  double* a = (double*)A.ptr;
-  const int n = A.rows, lda = A.ld;
-  for (int jb = 0; jb < n; jb += kBlk) {
-    const int w = min(kBlk, n - jb);
-    if (jb > 0) {
-      for (int ib = jb; ib < n; ib += kBlk) {
-        const int mb = min(kBlk, n - ib);
-        gemm_block<false, false>(a + (size_t)ib * lda + jb, lda, a + (size_t)ib * lda, lda,
-                                 a + (size_t)jb * lda, lda, mb, w, jb, -1.0, ib == jb, s.gs);
-      }
-    }
-    load_block(s.l, a + (size_t)jb * lda + jb, lda, w, w);
-    __syncthreads();
-    const int info = potrf_smem(s.l, w, &s.info);
-    if (info) return jb + info;
-    store_block(a + (size_t)jb * lda + jb, lda, s.l, w, w, true);
-    for (int ib = jb + w; ib < n; ib += kBlk) {
-      const int mb = min(kBlk, n - ib);
-      load_block(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
-      __syncthreads();
-      trsm_rt_smem(s.x, s.l, mb, w);
-      store_block(a + (size_t)ib * lda + jb, lda, s.x, mb, w, false);
-      __syncthreads();
-    }
-    __syncthreads();
-  }
-  return 0;
-}
-
-// TRSM: A (m x n) <- A L^{-T}, L (n x n); units = 64-row blocks of A.
-__device__ void op_trsm(const TileDesc& Lt, const TileDesc& At, uint32_t u0, uint32_t u1,
-                        F64Smem& s) {
-  const double* l = (const double*)Lt.ptr;
-  double* a = (double*)At.ptr;
-  const int n = At.cols, lda = At.ld, ldl = Lt.ld;
-  for (uint32_t u = u0; u < u1; ++u) {
-    const int ib = u * kBlk, mb = min(kBlk, At.rows - ib);
-    double* x = a + (size_t)ib * lda;
-    for (int jb = 0; jb < n; jb += kBlk) {
-      const int w = min(kBlk, n - jb);
-      if (jb > 0)
-        gemm_block<false, false>(x + jb, lda, x, lda, l + (size_t)jb * ldl, ldl, mb, w, jb, -1.0,
-                                 false, s.gs);
-      load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
-      load_block(s.x, x + jb, lda, mb, w);
-      __syncthreads();
-      trsm_rt_smem(s.x, s.l, mb, w);
-      store_block(x + jb, lda, s.x, mb, w, false);
-      __syncthreads();
-    }
-  }
-}
 
 // Lower block pair (bi >= bj) of unit u in a triangle of blocks.
 __device__ __forceinline__ void lower_pair(uint32_t u, int& bi, int& bj) {
@@ -260,6 +205,82 @@ __device__ __forceinline__ void lower_pair(uint32_t u, int& bi, int& bj) {
   while ((uint32_t)((i + 1) * (i + 2) / 2) <= u) ++i;
   bi = i;
   bj = (int)(u - (uint32_t)(i * (i + 1) / 2));
+}
+
+// POTRF phase `phase`, units u0..u1 (see op_phase_units): right-looking
+// over 64-column block steps j.  Returns 0 or the 1-based column (within the
+// tile) of a pivot that is not > 0.
+__device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, uint32_t u1,
+                              F64Smem& s) {
+  double* a = (double*)A.ptr;
+  const int n = A.rows, lda = A.ld;
+  const int j = (int)(phase / 3), jb = j * kBlk, w = min(kBlk, n - jb);
+  double* ajj = a + (size_t)jb * lda + jb;
+  switch (phase % 3) {
+    case 0: {  // factor the diagonal block
+      load_block(s.l, ajj, lda, w, w);
+      __syncthreads();
+      const int info = potrf_smem(s.l, w, &s.info);
+      if (info) return jb + info;
+      store_block(ajj, lda, s.l, w, w, true);
+      __syncthreads();
+      return 0;
+    }
+    case 1: {  // blocks (i, j) below the diagonal block: X <- X L_jj^{-T}
+      load_block(s.l, ajj, lda, w, w);
+      for (uint32_t u = u0; u < u1; ++u) {
+        const int ib = (j + 1 + (int)u) * kBlk, mb = min(kBlk, n - ib);
+        load_block(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
+        __syncthreads();
+        trsm_rt_smem(s.x, s.l, mb, w);
+        store_block(a + (size_t)ib * lda + jb, lda, s.x, mb, w, false);
+        __syncthreads();
+      }
+      return 0;
+    }
+    default: {  // trailing lower blocks (i, l), j < l <= i: A_il -= L_ij L_lj^T
+      for (uint32_t u = u0; u < u1; ++u) {
+        int bi, bl;
+        lower_pair(u, bi, bl);
+        const int ib = (j + 1 + bi) * kBlk, lb = (j + 1 + bl) * kBlk;
+        gemm_block<false, false>(a + (size_t)ib * lda + lb, lda, a + (size_t)ib * lda + jb, lda,
+                                 a + (size_t)lb * lda + jb, lda, min(kBlk, n - ib),
+                                 min(kBlk, n - lb), w, -1.0, bi == bl, s.gs);
+      }
+      return 0;
+    }
+  }
+}
+
+// TRSM phase `phase`, units u0..u1: A (m x n) <- A L^{-T}, right-looking over
+// 64-column blocks j of A: solve block column j, then update the columns to
+// its right.
+__device__ void op_trsm_units(const TileDesc& Lt, const TileDesc& At, uint32_t phase, uint32_t u0,
+                              uint32_t u1, F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* a = (double*)At.ptr;
+  const int m = At.rows, n = At.cols, lda = At.ld, ldl = Lt.ld;
+  const int j = (int)(phase / 2), jb = j * kBlk, w = min(kBlk, n - jb);
+  if (phase % 2 == 0) {
+    load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+    for (uint32_t u = u0; u < u1; ++u) {
+      const int ib = (int)u * kBlk, mb = min(kBlk, m - ib);
+      double* x = a + (size_t)ib * lda + jb;
+      load_block(s.x, x, lda, mb, w);
+      __syncthreads();
+      trsm_rt_smem(s.x, s.l, mb, w);
+      store_block(x, lda, s.x, mb, w, false);
+      __syncthreads();
+    }
+  } else {
+    const uint32_t right = cdiv64(n) - 1 - (uint32_t)j;
+    for (uint32_t u = u0; u < u1; ++u) {
+      const int ib = (int)(u / right) * kBlk, lb = (j + 1 + (int)(u % right)) * kBlk;
+      gemm_block<false, false>(a + (size_t)ib * lda + lb, lda, a + (size_t)ib * lda + jb, lda,
+                               l + (size_t)lb * ldl + jb, ldl, min(kBlk, m - ib), min(kBlk, n - lb),
+                               w, -1.0, false, s.gs);
+    }
+  }
 }
 
 // SYRK: C (n x n, lower) -= L L^T, L (n x k); units = lower 64-block pairs.
