@@ -120,6 +120,11 @@ typedef struct {
   unsigned long long watchdog_ns; /* device gives up after this long without
                                  finishing a task part; 0 = 10 s              */
   long long queue_capacity;   /* entries per priority queue; 0 = exact size   */
+  int cuda_graph;             /* 1 = capture the re-execution sequence of a
+                                 reset graph (state reset, queue set-up,
+                                 executor, status copy) into a CUDA graph on
+                                 its second execute and replay it after     */
+  int pad_;
 } spx_graph_config_t;
 
 /* Fill *cfg with the defaults. */
@@ -222,7 +227,9 @@ int spx_graph_timing(spx_graph_t g, float* prep_ms, float* run_ms);
 int spx_graph_write_dot(spx_graph_t g, const char* path);
 
 /* Make an executed graph runnable again with the same DAG (no new
- * derivation).  The caller restores the tile contents.  Errors: SPX_ERR_STATE. */
+ * derivation).  The caller restores the tile contents.  With
+ * cfg.cuda_graph = 1 the next execute replays one CUDA graph.
+ * Errors: SPX_ERR_STATE. */
 int spx_graph_reset(spx_graph_t g);
 
 /* Drop all tiles and tasks but keep the allocations, so a new graph of a
@@ -299,6 +306,15 @@ int spx_graph_derive_noalloc(const unsigned* dev_task_rec, const unsigned* dev_r
                              int ntasks, int nhandles, long long nrec, unsigned* dev_row_ptr,
                              unsigned* dev_col, long long col_cap, unsigned* dev_indeg,
                              int* dev_status, void* stream);
+
+/* Insert `count` independent Cholesky solves into one graph (the batched
+ * form of spx_cholesky_insert: problem i uses dev_A[i], n[i], lda[i], b[i],
+ * dev_X[i] (may be NULL), nrhs[i], ldx[i]).  The problems share no tile, so
+ * their DAGs are disjoint and one persistent launch runs all of them.
+ * Host arrays of length count.  Errors as spx_cholesky_insert. */
+int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const* dev_A, const int* n,
+                              const int* lda, const int* b, double* const* dev_X, const int* nrhs,
+                              const int* ldx, int lookahead, int prec, long long* out_ntasks);
 
 /* Static description of a status code. */
 const char* spx_strerror(int code);

@@ -125,6 +125,9 @@ struct spx_graph {
   Layout lay{};
   DevGraph dg{};
   long long nedges = -1;
+  // CUDA-graph replay of the re-execution sequence (cfg.cuda_graph)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
@@ -196,6 +199,10 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   if (g->cfg.queue_capacity > 0) Q = (size_t)g->cfg.queue_capacity;
   if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
   const Layout L = make_layout(N, H, M, E, Q, g->cfg.trace != 0);
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
   if (L.total > g->dcap) {
     if (g->dmem) {
       cudaError_t e = cudaStreamSynchronize(g->last_stream ? g->last_stream : st);
@@ -474,6 +481,47 @@ int spx_graph_derive(spx_graph_t g, void* stream) {
   return SPX_OK;
 }
 
+// The sequence that re-runs an uploaded (and, for the persistent executor,
+// derived) graph: run-state reset, queue initialisation, executor, status
+// copy.  Enqueued on st, or captured into a CUDA graph.
+int enqueue_rerun(spx_graph* g, cudaStream_t st) {
+  int rc = reset_run_state(g, st);
+  if (rc != SPX_OK) return rc;
+  cudaError_t e;
+  if (g->cfg.executor == SPX_EXEC_PER_TASK) {
+    e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), st);
+  } else {
+    e = launch_init(g->dg, st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+int build_replay(spx_graph* g) {
+  cudaError_t e = cudaSuccess;
+  if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int rc = enqueue_rerun(g, g->cap_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(g->cap_stream, &graph);
+  if (rc != SPX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(&g->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->gexec = nullptr;
+    return cuda_fail(e);
+  }
+  return SPX_OK;
+}
+
 int spx_graph_execute(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
@@ -484,6 +532,23 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
   if (!g->uploaded) {
     rc = prepare_device(g, st);
     if (rc != SPX_OK) return rc;
+  }
+  const bool replay = g->cfg.cuda_graph && g->state == kFrozen &&
+                      (g->cfg.executor == SPX_EXEC_PER_TASK || g->derived);
+  if (replay) {
+    if (!g->gexec) {
+      rc = build_replay(g);
+      if (rc != SPX_OK) return rc;
+    }
+    e = cudaEventRecord(g->tev[0], st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->tev[1], st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->gexec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->done_ev, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g->last_stream = st;
+    g->state = kRunning;
+    return SPX_OK;
   }
   e = cudaEventRecord(g->tev[0], st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -677,6 +742,10 @@ int spx_graph_clear(spx_graph_t g) {
   g->derived = false;
   g->nedges = -1;
   g->state = kBuilding;
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
   return SPX_OK;
 }
 
@@ -687,6 +756,8 @@ void spx_graph_destroy(spx_graph_t g) {
   if (g->dmem) cudaFree(g->dmem);
   if (g->pinned) cudaFreeHost(g->pinned);
   if (g->host_rs) cudaFreeHost(g->host_rs);
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   if (g->done_ev) cudaEventDestroy(g->done_ev);
   for (int i = 0; i < 3; ++i)
     if (g->tev[i]) cudaEventDestroy(g->tev[i]);

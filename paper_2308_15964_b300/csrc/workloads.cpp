@@ -115,3 +115,21 @@ extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, doub
   if (out_ntasks) *out_ntasks = count;
   return rc;
 }
+
+extern "C" int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const* dev_A,
+                                         const int* n, const int* lda, const int* b,
+                                         double* const* dev_X, const int* nrhs, const int* ldx,
+                                         int lookahead, int prec, long long* out_ntasks) {
+  if (!g || count < 0 || (count > 0 && (!dev_A || !n || !lda || !b))) return SPX_ERR_INVALID_ARG;
+  long long total = 0;
+  int rc = SPX_OK;
+  for (int i = 0; i < count && rc == SPX_OK; ++i) {
+    long long nt = 0;
+    double* x = dev_X ? dev_X[i] : nullptr;
+    rc = spx_cholesky_insert(g, dev_A[i], n[i], lda[i], b[i], x, x ? nrhs[i] : 0, x ? ldx[i] : 0,
+                             lookahead, prec, &nt);
+    total += nt;
+  }
+  if (out_ntasks) *out_ntasks = total;
+  return rc;
+}

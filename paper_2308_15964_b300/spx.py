@@ -35,7 +35,8 @@ class SpxError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("num_ctas", ctypes.c_int), ("executor", ctypes.c_int), ("trace", ctypes.c_int),
                 ("no_split", ctypes.c_int), ("watchdog_ns", ctypes.c_ulonglong),
-                ("queue_capacity", ctypes.c_longlong)]
+                ("queue_capacity", ctypes.c_longlong), ("cuda_graph", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
 
 
 def _load():
@@ -66,6 +67,7 @@ def _load():
         "spx_graph_timing": (I, [P, P, P]),
         "spx_cholesky_insert": (I, [P, P, I, I, I, P, I, I, I, I, P]),
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
+        "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
         "spx_graph_derive_noalloc": (I, [P, P, P, P, I, I, LL, P, P, LL, P, P, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),
@@ -108,7 +110,7 @@ class Graph:
     """An STF task graph (spx_graph_t)."""
 
     def __init__(self, num_ctas=0, executor=EXEC_PERSISTENT, trace=False, no_split=False,
-                 watchdog_ns=0, queue_capacity=0):
+                 watchdog_ns=0, queue_capacity=0, cuda_graph=False):
         cfg = Config()
         lib.spx_config_default(ctypes.byref(cfg))
         cfg.num_ctas = num_ctas
@@ -118,6 +120,7 @@ class Graph:
         if watchdog_ns:
             cfg.watchdog_ns = watchdog_ns
         cfg.queue_capacity = queue_capacity
+        cfg.cuda_graph = 1 if cuda_graph else 0
         h = ctypes.c_void_p()
         _check(lib.spx_graph_create(ctypes.byref(h), ctypes.byref(cfg)), "spx_graph_create")
         self._h = h
