@@ -307,6 +307,20 @@ int spx_graph_derive_noalloc(const unsigned* dev_task_rec, const unsigned* dev_r
                              unsigned* dev_col, long long col_cap, unsigned* dev_indeg,
                              int* dev_status, void* stream);
 
+/* Low-precision tile update on the tensor cores, stand-alone: the building
+ * block of the mixed-precision SYRK / GEMM tasks (the trailing updates of the
+ * paper's tiled Cholesky run in BF16 or TF32 with FP32 accumulation while the
+ * trailing matrix stays FP64):
+ *     C (m x n, FP64, ldc) -= A (m x K) * B (n x K)^T
+ * A and B row-major low precision (prec SPX_BF16: bfloat16; SPX_TF32: FP32
+ * storage whose low 13 mantissa bits the tensor core ignores), leading
+ * dimensions lda, ldb in elements (rows 16-byte aligned).  tcgen05.mma with
+ * TMEM accumulators, operands by TMA.  Asynchronous on stream; *dev_err (a
+ * device int the caller zeroes) becomes 1 if a device wait timed out.
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_CUDA. */
+int spx_tc_gemm_nt(double* dev_C, int ldc, int m, int n, const void* dev_A, int lda,
+                   const void* dev_B, int ldb, int K, int prec, int* dev_err, void* stream);
+
 /* Insert `count` independent Cholesky solves into one graph (the batched
  * form of spx_cholesky_insert: problem i uses dev_A[i], n[i], lda[i], b[i],
  * dev_X[i] (may be NULL), nrhs[i], ldx[i]).  The problems share no tile, so

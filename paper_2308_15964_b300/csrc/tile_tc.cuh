@@ -1,0 +1,269 @@
+// Low-precision trailing updates on the 5th-generation tensor cores.
+//
+// One work unit = one 128 x 128 block of an FP64 tile C:
+//     C[r0:r0+128, c0:c0+128] -= A_lo[ar0:ar0+128, 0:K] * B_lo[br0:br0+128, 0:K]^T
+// where A_lo and B_lo are BF16 or TF32 copies of factor tiles (both K-major,
+// i.e. row-major with K contiguous).  The operands arrive in shared memory by
+// TMA (cp.async.bulk.tensor, 128-byte swizzle, one 128-row x 128-byte box per
+// operand and K chunk, three stages), one thread issues tcgen05.mma
+// (M = 128, N = 128, FP32 accumulation in TMEM, K = 16 for BF16 / 8 for
+// TF32 per instruction), tcgen05.commit signals completion on mbarriers, and
+// all eight warps read the accumulator back with tcgen05.ld and subtract it
+// from the FP64 block (the paper's mixed-precision workload keeps the
+// trailing matrix in FP64 and runs only the update products in low precision).
+//
+// Every wait on an mbarrier is bounded; on expiry the unit returns false and
+// the caller reports an error (the TMEM allocation is released by the caller
+// at kernel exit).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx_internal.h"
+
+namespace spx {
+
+constexpr int kTcM = 128, kTcN = 128;
+constexpr int kTcStages = 3;
+constexpr int kTcChunkBytes = 128;                 // K bytes per stage (one swizzle row)
+constexpr int kTcStageBytes = kTcM * kTcChunkBytes; // 16 KB per operand per stage
+constexpr uint32_t kTcTmemCols = 128;              // FP32 accumulator columns
+constexpr uint32_t kTcSpinLimit = 1u << 26;
+
+// Operand stages (1024-byte aligned for the 128-byte swizzle atoms).  In the
+// persistent kernel they share shared memory with the FP64 ops.
+struct __align__(1024) TcBuf {
+  uint8_t a[kTcStages][kTcStageBytes];
+  uint8_t b[kTcStages][kTcStageBytes];
+};
+
+// Barriers and accumulator address; live for the whole kernel.
+struct TcState {
+  uint64_t full[kTcStages];   // TMA landed
+  uint64_t empty[kTcStages];  // MMAs that read the stage finished
+  uint64_t done;              // all MMAs of the unit finished
+  uint32_t tmem_base;
+  uint32_t full_phase, empty_phase, done_phase;  // parity bit s = stage s
+  int error;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, A and B of type `fmt` (1 = BF16
+// for kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+         ((uint32_t)(kTcM >> 4) << 24);
+}
+
+template <bool kBf16>
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  if (kBf16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(tc_idesc(1)), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(tc_idesc(2)), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Allocate the CTA's accumulator columns (warp 0, all lanes) and initialise
+// the barriers (thread 0).  Call once per kernel, before __syncthreads.
+__device__ __forceinline__ void tc_setup(TcState& s) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s.tmem_base)),
+                 "r"(kTcTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTcStages; ++i) {
+      mbar_init(&s.full[i], 1);
+      mbar_init(&s.empty[i], 1);
+    }
+    mbar_init(&s.done, 1);
+    s.full_phase = s.empty_phase = s.done_phase = 0;
+    s.error = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+}
+
+// Release the accumulator columns (warp 0).  Call once at kernel exit, after
+// a __syncthreads that follows the last tcgen05 use.
+__device__ __forceinline__ void tc_teardown(TcState& s) {
+  tc_fence_after();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem_base),
+                 "r"(kTcTmemCols));
+  }
+}
+
+// One 128 x 128 unit (see the file comment).  m, n: valid rows / columns of
+// the output block (<= 128); K: reduction length (elements); the A rows
+// start at (ay, ax0) and the B rows at (by, bx0) in their tensor maps (x is
+// the K coordinate).  lower: write only entries with column <= row.  All
+// threads call it; returns false on a barrier timeout.
+template <bool kBf16>
+__device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int ax0, int ay,
+                             const CUtensorMap* bmap, int bx0, int by, int K, double* C, int ldc,
+                             int m, int n, bool lower) {
+  constexpr int kElem = kBf16 ? 2 : 4;
+  constexpr int kChunk = kTcChunkBytes / kElem;   // K elements per stage
+  constexpr int kMmaK = kBf16 ? 16 : 8;           // K per instruction
+  const int nchunks = (K + kChunk - 1) / kChunk;
+  const int tid = threadIdx.x;
+  const uint32_t tmem = s.tmem_base;
+  if (tid == 0) {
+    tc_fence_after();
+    bool ok = true;
+    uint32_t fph = s.full_phase, eph = s.empty_phase;
+    const int pre = nchunks < kTcStages ? nchunks : kTcStages;
+    for (int c = 0; c < pre; ++c) {
+      mbar_arrive_expect_tx(&s.full[c], 2 * kTcStageBytes);
+      tma_load_2d(buf.a[c], amap, &s.full[c], ax0 + c * kChunk, ay);
+      tma_load_2d(buf.b[c], bmap, &s.full[c], bx0 + c * kChunk, by);
+    }
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int st = c % kTcStages;
+      ok = mbar_wait(&s.full[st], (fph >> st) & 1u);
+      fph ^= 1u << st;
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(buf.a[st]), b0 = smem_u32(buf.b[st]);
+#pragma unroll
+      for (int k = 0; k < kChunk / kMmaK; ++k) {
+        tc_mma<kBf16>(tmem, smem_desc(a0 + k * kMmaK * kElem), smem_desc(b0 + k * kMmaK * kElem),
+                      (c > 0 || k > 0) ? 1u : 0u);
+      }
+      tc_commit(&s.empty[st]);
+      if (c + kTcStages < nchunks) {
+        ok = mbar_wait(&s.empty[st], (eph >> st) & 1u);
+        eph ^= 1u << st;
+        if (!ok) break;
+        mbar_arrive_expect_tx(&s.full[st], 2 * kTcStageBytes);
+        tma_load_2d(buf.a[st], amap, &s.full[st], ax0 + (c + kTcStages) * kChunk, ay);
+        tma_load_2d(buf.b[st], bmap, &s.full[st], bx0 + (c + kTcStages) * kChunk, by);
+      }
+    }
+    tc_commit(&s.done);
+    if (ok) ok = mbar_wait(&s.done, s.done_phase & 1u);
+    s.done_phase ^= 1u;
+    // consume the empty phases of the last chunks (no reload waited on them)
+    for (int c = nchunks > kTcStages ? nchunks - kTcStages : 0; c < nchunks && ok; ++c) {
+      const int st = c % kTcStages;
+      ok = mbar_wait(&s.empty[st], (eph >> st) & 1u);
+      eph ^= 1u << st;
+    }
+    s.full_phase = fph;
+    s.empty_phase = eph;
+    if (!ok) s.error = 1;
+  }
+  __syncthreads();
+  if (s.error) return false;
+  tc_fence_after();
+  // epilogue: warp w reads TMEM lanes 32*(w%4).., columns 64*(w/4)..+64
+  const int warp = tid >> 5, lane = tid & 31;
+  const int row = 32 * (warp & 3) + lane;
+  const int col0 = 64 * (warp >> 2);
+  float v[32];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cb = col0 + 32 * h;
+    tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
+    if (row < m) {
+      double* cr = C + (size_t)row * ldc;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = cb + j;
+        if (c < n && (!lower || c <= row)) cr[c] = __ldcg(cr + c) - (double)v[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  return true;
+}
+
+}  // namespace spx
