@@ -84,7 +84,13 @@ enum {
   SPX_NUM_OPS = 11
 };
 
-/* Arithmetic of a task.  SPX_F64: FP64 throughout. */
+/* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
+ * (mixed precision; allowed for TRSM, SYRK and GEMM_NT_SUB): SYRK and
+ * GEMM_NT_SUB compute the product of the low-precision copies of their
+ * factor operands on the tensor cores with FP32 accumulation and subtract it
+ * from the FP64 output tile; TRSM solves in FP64 and then writes the
+ * low-precision copy of its result (round to nearest; TF32 as FP32 with the
+ * low 13 mantissa bits cleared). */
 enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2 };
 
 /* Element type of a registered tile. */
@@ -149,6 +155,15 @@ int spx_graph_create(spx_graph_t* out, const spx_graph_config_t* cfg);
 int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
                       void* lowp_ptr, int lowp_ld, unsigned* out_handle);
 
+/* Register a low-precision matrix (BF16, or FP32 read as TF32) that holds the
+ * low-precision copies of tiles (the lowp_ptr of spx_tile_register must
+ * point inside it).  The library builds a TMA tensor map for it (128-row x
+ * 128-byte boxes, 128-byte swizzle).  dev_ptr 16-byte aligned, ld * element
+ * size a multiple of 16.  Registering the same base again returns the same
+ * map.  Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE, SPX_ERR_CUDA. */
+int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
+                      unsigned* out_map);
+
 /* Insert one task (paper, section "Task insertion": one thread inserts tasks
  * with their accesses; the result equals running them in insertion order).
  *   op        SPX_OP_*; handles[nh] in the op's operand order; modes[nh] the
@@ -156,8 +171,9 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
  *             for the other ops; operand shapes must agree.
  *   priority  0 = normal, >0 = high (popped first; a hint, paper section
  *             "Task insertion" / "Scheduling").
- *   prec      SPX_F64 (other values are accepted only where the op has a
- *             low-precision form).
+ *   prec      SPX_F64, or SPX_TF32 / SPX_BF16 for TRSM, SYRK, GEMM_NT_SUB
+ *             whose factor tiles have low-precision copies in a matrix
+ *             registered with spx_lowp_register of the matching type.
  *   out_task  receives the task id (0, 1, 2, ... in insertion order); may be
  *             NULL.
  * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_BAD_HANDLE, SPX_ERR_STATE. */
@@ -260,6 +276,23 @@ void spx_graph_destroy(spx_graph_t g);
 int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b, double* dev_X,
                         int nrhs, int ldx, int lookahead, int prec, long long* out_ntasks);
 
+/* Mixed-precision form of spx_cholesky_insert: POTRF and the solves in FP64,
+ * TRSM / SYRK / GEMM with prec = SPX_TF32 or SPX_BF16 (see the prec enum):
+ * the trailing updates run on the tensor cores from low-precision copies of
+ * the factor tiles kept in dev_Alo (n x n, ld ldlo; BF16 for SPX_BF16, FP32
+ * for SPX_TF32; rows 16-byte aligned), which the TRSM tasks write.  b must be
+ * a multiple of 64.  The resulting factor is accurate to the low precision;
+ * pair it with FP64 iterative refinement (spx_residual_f64, spx_solve_insert). */
+int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo,
+                              int ldlo, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
+                              long long* out_ntasks);
+
+/* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
+ * already in dev_L (lower triangle, tiles b x b).  Used for the correction
+ * solves of iterative refinement; re-run with spx_graph_reset. */
+int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b, double* dev_X, int nrhs,
+                     int ldx, long long* out_ntasks);
+
 /* Insert the tiled GEMM C += A B of the paper's numerical applications: one
  * GEMM_NN_ADD task per (i, j, k), i and j outer, k inner, each with a WRITE
  * (or, with commutative = 1, a COMMUTATIVE_WRITE) on the block C_ij.  A, B, C
@@ -329,6 +362,23 @@ int spx_tc_gemm_nt(double* dev_C, int ldc, int m, int n, const void* dev_A, int 
 int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const* dev_A, const int* n,
                               const int* lda, const int* b, double* const* dev_X, const int* nrhs,
                               const int* ldx, int lookahead, int prec, long long* out_ntasks);
+
+/* FP64 residual of iterative refinement: R = B - A X (A n x n, X, B, R
+ * n x nrhs, all FP64 row-major with the given leading dimensions, R may not
+ * alias X or B), 1 <= nrhs <= 16.  dev_norms [3*nrhs] receives max|r_j| at
+ * [j], max|x_j| at [nrhs+j], max|b_j| at [2 nrhs+j], from which the
+ * normwise backward error eta_j = max|r_j| / (||A||_inf max|x_j| + max|b_j|)
+ * follows (Rigal-Gaches).  Asynchronous on stream.
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_CUDA. */
+int spx_residual_f64(const double* dev_A, int n, int lda, const double* dev_X, int ldx,
+                     const double* dev_B, int ldb, double* dev_R, int ldr, int nrhs,
+                     double* dev_norms, void* stream);
+
+/* ||A||_inf (max row sum of |a_ij|) of an n x n FP64 matrix into dev_out[0]. */
+int spx_norm_inf_f64(const double* dev_A, int n, int lda, double* dev_out, void* stream);
+
+/* Y += alpha X over count contiguous FP64 values (the refinement update). */
+int spx_axpy_f64(double* dev_Y, const double* dev_X, long long count, double alpha, void* stream);
 
 /* Static description of a status code. */
 const char* spx_strerror(int code);

@@ -22,6 +22,7 @@
 
 #include "spx.h"
 #include "spx_internal.h"
+#include "tmap.h"
 
 using namespace spx;
 
@@ -41,14 +42,14 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Layout of the single device allocation (and of the pinned upload mirror
 // for its first region).  Offsets in bytes, 256-aligned.
 struct Layout {
-  size_t tasks, tiles, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
+  size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
   size_t queue0, queue1, t_start, ff_end;
   size_t rs, locks, t_end, trace, phase, zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
 
-Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, bool trace) {
+Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, bool trace) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -58,6 +59,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, bool trace)
   };
   L.tasks = take(N * sizeof(TaskDesc));
   L.tiles = take(H * sizeof(TileDesc));
+  L.maps = take(NM * sizeof(CUtensorMap));
   L.rec_handle = take(M * 4);
   L.rec_seq = take(M * 4);
   L.rec_mode = take(M);
@@ -104,6 +106,10 @@ struct spx_graph {
   // inserted graph (host)
   std::vector<TileDesc> tiles;
   std::vector<int> tile_dtype;
+  std::vector<CUtensorMap> maps;      // low-precision matrices
+  struct MapInfo { uintptr_t base; size_t bytes; int ld, elem, dtype, cols_; };
+  std::vector<MapInfo> map_info;
+  bool has_tc = false;                // some task runs on the tensor cores
   std::unordered_map<uintptr_t, uint32_t> key_to_handle;
   std::vector<HandleState> hstate;
   std::vector<TaskDesc> tasks;
@@ -170,6 +176,54 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
   return ok ? SPX_OK : SPX_ERR_INVALID_ARG;
 }
 
+// Find the registered low-precision matrix that holds tile h's copy and
+// record the copy's position in it.
+bool resolve_lowp(spx_graph* g, uint32_t h) {
+  TileDesc& t = g->tiles[h];
+  if (!t.lowp) return false;
+  if (t.lmap >= 0) return true;
+  const uintptr_t p = (uintptr_t)t.lowp;
+  for (size_t m = 0; m < g->map_info.size(); ++m) {
+    const auto& mi = g->map_info[m];
+    if (p < mi.base || p >= mi.base + mi.bytes) continue;
+    const size_t off = p - mi.base, row_bytes = (size_t)mi.ld * mi.elem;
+    if (off % mi.elem || t.lowp_ld != mi.ld) return false;
+    t.lmap = (int)m;
+    t.lr0 = (int)(off / row_bytes);
+    t.lc0 = (int)((off % row_bytes) / mi.elem);
+    return true;
+  }
+  return false;
+}
+
+// Low-precision tasks: TRSM writes the copy of its result; SYRK / GEMM_NT_SUB
+// read the copies of their factor operands through TMA.  The copies must lie
+// in a matrix registered with spx_lowp_register of the task's type, with the
+// K extent a whole number of 128-byte chunks (or ending the matrix).
+int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
+  const int want = prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32;
+  int ins[2] = {-1, -1};
+  switch (op) {
+    case SPX_OP_TRSM: ins[0] = (int)h[1]; break;
+    case SPX_OP_SYRK: ins[0] = (int)h[0]; break;
+    case SPX_OP_GEMM_NT_SUB: ins[0] = (int)h[0]; ins[1] = (int)h[1]; break;
+    default: return SPX_ERR_INVALID_ARG;
+  }
+  for (int i : ins) {
+    if (i < 0) continue;
+    if (!resolve_lowp(g, (uint32_t)i)) return SPX_ERR_INVALID_ARG;
+    const TileDesc& t = g->tiles[i];
+    const auto& mi = g->map_info[t.lmap];
+    if (mi.dtype != want) return SPX_ERR_INVALID_ARG;
+    const int chunk = 128 / mi.elem;  // K elements per TMA box
+    if (t.lc0 % chunk) return SPX_ERR_INVALID_ARG;
+    // a partial last K chunk must run past the matrix edge (read as zeros)
+    if (op != SPX_OP_TRSM && t.cols % chunk && t.lc0 + t.cols != mi.cols_)
+      return SPX_ERR_INVALID_ARG;
+  }
+  return SPX_OK;
+}
+
 int ensure_device(spx_graph* g) {
   if (g->device >= 0) return SPX_OK;
   int dev = -1;
@@ -198,7 +252,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   size_t Q = std::max<unsigned long long>(std::max(g->items[0], g->items[1]), 1);
   if (g->cfg.queue_capacity > 0) Q = (size_t)g->cfg.queue_capacity;
   if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
-  const Layout L = make_layout(N, H, M, E, Q, g->cfg.trace != 0);
+  const Layout L = make_layout(N, H, M, E, Q, g->maps.size(), g->cfg.trace != 0);
   if (g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
@@ -235,6 +289,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   char* P = (char*)g->pinned;
   std::memcpy(P + L.tasks, g->tasks.data(), N * sizeof(TaskDesc));
   std::memcpy(P + L.tiles, g->tiles.data(), H * sizeof(TileDesc));
+  if (!g->maps.empty()) std::memcpy(P + L.maps, g->maps.data(), g->maps.size() * sizeof(CUtensorMap));
   std::memcpy(P + L.rec_handle, g->rec_handle.data(), M * 4);
   std::memcpy(P + L.rec_seq, g->rec_seq.data(), M * 4);
   std::memcpy(P + L.rec_mode, g->rec_mode.data(), M);
@@ -254,6 +309,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.watchdog_ns = g->cfg.watchdog_ns ? g->cfg.watchdog_ns : 10000000000ull;
   d.tasks = (const TaskDesc*)(D + L.tasks);
   d.tiles = (const TileDesc*)(D + L.tiles);
+  d.maps = (const CUtensorMap*)(D + L.maps);
   d.rec_handle = (const uint32_t*)(D + L.rec_handle);
   d.rec_seq = (const uint32_t*)(D + L.rec_seq);
   d.rec_mode = (const uint8_t*)(D + L.rec_mode);
@@ -360,7 +416,7 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
     return SPX_OK;
   }
   const uint32_t h = (uint32_t)g->tiles.size();
-  g->tiles.push_back(TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0});
+  g->tiles.push_back(TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0, -1, 0, 0, 0});
   g->tile_dtype.push_back(dtype);
   g->hstate.emplace_back();
   g->key_to_handle.emplace(key, h);
@@ -369,12 +425,34 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
   return SPX_OK;
 }
 
+int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
+                      unsigned* out_map) {
+  if (!g || !dev_ptr || rows < 1 || cols < 1 || ld < cols ||
+      (dtype != SPX_DT_BF16 && dtype != SPX_DT_F32))
+    return SPX_ERR_INVALID_ARG;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  const int elem = dtype == SPX_DT_BF16 ? 2 : 4;
+  for (size_t m = 0; m < g->map_info.size(); ++m)
+    if (g->map_info[m].base == (uintptr_t)dev_ptr) {
+      if (out_map) *out_map = (unsigned)m;
+      return SPX_OK;
+    }
+  CUtensorMap map;
+  const int rc = make_tmap(&map, dev_ptr, rows, cols, ld, dtype);
+  if (rc != SPX_OK) return rc;
+  g->maps.push_back(map);
+  g->map_info.push_back({(uintptr_t)dev_ptr, (size_t)rows * ld * elem, ld, elem, dtype, cols});
+  g->uploaded = false;
+  if (out_map) *out_map = (unsigned)(g->maps.size() - 1);
+  return SPX_OK;
+}
+
 int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* modes, int nh,
                     int priority, int prec, unsigned* out_task) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state != kBuilding) return SPX_ERR_STATE;
   if (op < 0 || op >= SPX_NUM_OPS || nh < 1 || nh > kMaxHandles || !handles || !modes ||
-      priority < 0 || prec != SPX_F64)
+      priority < 0 || prec < SPX_F64 || prec > SPX_BF16)
     return SPX_ERR_INVALID_ARG;
   if (g->tasks.size() >= kMaxTasks) return SPX_ERR_INVALID_ARG;
   for (int i = 0; i < nh; ++i) {
@@ -383,6 +461,10 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   int rc = check_operands(op, g->tiles, g->tile_dtype, handles, modes, nh);
   if (rc != SPX_OK) return rc;
+  if (prec != SPX_F64) {
+    rc = check_lowp(g, op, prec, handles);
+    if (rc != SPX_OK) return rc;
+  }
 
   // Merge repeated handles (READ+READ = READ, COMM+COMM = COMM, else WRITE)
   // and order this task's accesses by handle (the lock order on the device).
@@ -420,11 +502,11 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
     t.nphases = 1;
     t.nparts = 1;
   } else {
-    t.nphases = op_phases(op, g->tiles.data(), t.h);
-    t.nparts = phase_parts(op_phase_units(op, g->tiles.data(), t.h, 0));
+    t.nphases = op_phases(op, prec, g->tiles.data(), t.h);
+    t.nparts = phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, 0));
     items = 0;
     for (uint32_t ph = 0; ph < t.nphases; ++ph)
-      items += phase_parts(op_phase_units(op, g->tiles.data(), t.h, ph));
+      items += phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, ph));
   }
   t.arg = 0;
 
@@ -448,6 +530,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   g->task_rec.push_back((uint32_t)g->rec_handle.size());
   g->tasks.push_back(t);
   g->items[t.prio ? 0 : 1] += items;
+  if (prec != SPX_F64) g->has_tc = true;
   g->uploaded = false;
   if (out_task) *out_task = tid;
   return SPX_OK;
@@ -489,10 +572,10 @@ int enqueue_rerun(spx_graph* g, cudaStream_t st) {
   if (rc != SPX_OK) return rc;
   cudaError_t e;
   if (g->cfg.executor == SPX_EXEC_PER_TASK) {
-    e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), st);
+    e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->has_tc, st);
   } else {
     e = launch_init(g->dg, st);
-    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->has_tc, st);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
@@ -556,7 +639,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     rc = reset_run_state(g, st);
     if (rc != SPX_OK) return rc;
     e = cudaEventRecord(g->tev[1], st);
-    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), st);
+    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->has_tc, st);
   } else {
     if (!g->derived) {
       rc = spx_graph_derive(g, stream);  // also resets the run state
@@ -570,7 +653,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
       if (rc != SPX_OK) return rc;
     }
     e = cudaEventRecord(g->tev[1], st);
-    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->has_tc, st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -729,6 +812,9 @@ int spx_graph_clear(spx_graph_t g) {
   if (g->state == kRunning) return SPX_ERR_STATE;
   g->tiles.clear();
   g->tile_dtype.clear();
+  g->maps.clear();
+  g->map_info.clear();
+  g->has_tc = false;
   g->key_to_handle.clear();
   g->hstate.clear();
   g->tasks.clear();

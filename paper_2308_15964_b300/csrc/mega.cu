@@ -33,6 +33,7 @@
 
 #include "spx_internal.h"
 #include "tile_f64.cuh"
+#include "tile_tc.cuh"
 
 namespace spx {
 namespace {
@@ -173,20 +174,48 @@ __device__ bool spin_for(const DevGraph& g, long long ns) {
 }
 
 // Run units u0..u1 of one phase of a task with the whole CTA.  Returns 0,
-// a POTRF info (1-based column in the tile), or -1 for an unknown op.
+// a POTRF info (1-based column in the tile), -1 for an op this kernel cannot
+// run, or -2 when a tensor-core wait timed out.  Low-precision tasks need
+// the tensor-core instance (kTc).
+template <bool kTc>
 __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t u0,
-                         uint32_t u1, F64Smem& s) {
+                         uint32_t u1, F64Smem& s, TcCtx& tc) {
   const TileDesc* T = g.tiles;
+  const bool lowp = t.prec != SPX_F64;
+  if (lowp && !kTc) return -1;
   switch (t.op) {
     case SPX_OP_POTRF:
       return op_potrf_units(T[t.h[0]], phase, u0, u1, s);
     case SPX_OP_TRSM:
+      if constexpr (kTc) {
+        if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
+          if (t.prec == SPX_BF16) op_lowp_copy<true>(T[t.h[1]], u0, u1);
+          else op_lowp_copy<false>(T[t.h[1]], u0, u1);
+          return 0;
+        }
+      }
       op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_SYRK:
+      if constexpr (kTc) {
+        if (lowp) {
+          const bool ok = t.prec == SPX_BF16 ? op_tc_syrk<true>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc)
+                                             : op_tc_syrk<false>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc);
+          return ok ? 0 : -2;
+        }
+      }
       op_syrk(T[t.h[0]], T[t.h[1]], u0, u1, s);
       return 0;
     case SPX_OP_GEMM_NT_SUB:
+      if constexpr (kTc) {
+        if (lowp) {
+          const bool ok =
+              t.prec == SPX_BF16
+                  ? op_tc_gemm<true>(g, T[t.h[0]], T[t.h[1]], T[t.h[2]], u0, u1, tc)
+                  : op_tc_gemm<false>(g, T[t.h[0]], T[t.h[1]], T[t.h[2]], u0, u1, tc);
+          return ok ? 0 : -2;
+        }
+      }
       op_gemm<false, false>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s);
       return 0;
     case SPX_OP_GEMM_NN_ADD:
@@ -217,23 +246,24 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
 
 // Run part `part` of phase `phase`; a serial task runs all of its phases
 // and units here, in order.
+template <bool kTc>
 __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t part,
-                        F64Smem& s) {
+                        F64Smem& s, TcCtx& tc) {
   const TileDesc* T = g.tiles;
   if (t.flags & kFlagSerial) {
-    const uint32_t nph = op_phases(t.op, T, t.h);
+    const uint32_t nph = op_phases(t.op, t.prec, T, t.h);
     for (uint32_t ph = 0; ph < nph; ++ph) {
-      const int r = run_units(g, t, ph, 0, op_phase_units(t.op, T, t.h, ph), s);
+      const int r = run_units<kTc>(g, t, ph, 0, op_phase_units(t.op, t.prec, T, t.h, ph), s, tc);
       if (r) return r;
       __syncthreads();
     }
     return 0;
   }
-  const uint32_t units = op_phase_units(t.op, T, t.h, phase);
+  const uint32_t units = op_phase_units(t.op, t.prec, T, t.h, phase);
   const uint32_t parts = phase_parts(units);
   const uint32_t u0 = (uint32_t)((unsigned long long)part * units / parts);
   const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / parts);
-  return run_units(g, t, phase, u0, u1, s);
+  return run_units<kTc>(g, t, phase, u0, u1, s, tc);
 }
 
 // Push the np parts of the next phase of task u (warp 0, all lanes).
@@ -282,9 +312,20 @@ __device__ void unlock_comm(const DevGraph& g, uint32_t u) {
     if (g.rec_mode[r] == SPX_COMMUTATIVE_WRITE) atomicExch(&g.locks[g.rec_handle[r]], 0u);
 }
 
+template <bool kTc>
 __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
+  // the tensor-core instance aligns its operand stages to 1024 bytes; they
+  // share the space with the FP64 ops' buffers
+  unsigned char* base =
+      kTc ? (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023) : smem_raw;
+  F64Smem& s = *reinterpret_cast<F64Smem*>(base);
+  __shared__ TcState tcs;
+  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base)};
+  if (kTc) {
+    tc_setup(tcs);
+    __syncthreads();
+  }
   __shared__ uint32_t s_item, s_np;
   __shared__ int s_flag;
   const int tid = threadIdx.x;
@@ -317,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (!s_flag) break;
-    const int info = run_part(g, t, phase, part, s);
+    const int info = run_part<kTc>(g, t, phase, part, s, tc);
     __syncthreads();
     busy += clock64() - c0;
     if (tid == 0) {
@@ -325,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         set_error(rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
         s_flag = 0;
       } else if (info < 0) {
-        set_error(rs, (uint32_t)SPX_ERR_BAD_OP, 0);
+        set_error(rs, (uint32_t)(info == -2 ? SPX_ERR_TIMEOUT : SPX_ERR_BAD_OP), 0);
         s_flag = 0;
       } else {
         __threadfence();
@@ -336,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         s_flag = atomicSub(&g.remaining[u], 1u) == 1u ? 2 : 1;
         if (s_flag == 2 && phase + 1 < t.nphases) {
           // last part of a phase: set up the next phase before pushing it
-          const uint32_t np = phase_parts(op_phase_units(t.op, g.tiles, t.h, phase + 1));
+          const uint32_t np = phase_parts(op_phase_units(t.op, t.prec, g.tiles, t.h, phase + 1));
           *(volatile uint32_t*)&g.phase[u] = phase + 1;
           atomicExch(&g.remaining[u], np);
           s_np = np;
@@ -362,6 +403,8 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
       }
     }
   }
+  __syncthreads();
+  if (kTc) tc_teardown(tcs);
   if (tid == 0) {
     atomicAdd(&rs->busy_cycles, (unsigned long long)busy);
     atomicAdd(&rs->total_cycles, (unsigned long long)(clock64() - c_begin));
@@ -370,66 +413,92 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   }
 }
 
-// Baseline: one launch per task, one CTA per part, insertion order.
+// Baseline: one launch per task phase, one CTA per part, insertion order.
+template <bool kTc>
 __global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u, uint32_t phase) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F64Smem& s = *reinterpret_cast<F64Smem*>(smem_raw);
+  unsigned char* base =
+      kTc ? (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023) : smem_raw;
+  F64Smem& s = *reinterpret_cast<F64Smem*>(base);
+  __shared__ TcState tcs;
+  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base)};
   __shared__ int s_abort;
   if (threadIdx.x == 0) s_abort = (int)ld_volatile(&g.rs->abort);
   __syncthreads();
   if (s_abort) return;
+  if (kTc) {
+    tc_setup(tcs);
+    __syncthreads();
+  }
   const TaskDesc t = g.tasks[u];
   if (threadIdx.x == 0 && blockIdx.x == 0) touch_progress(g);
-  const int info = run_part(g, t, phase, blockIdx.x, s);
+  const int info = run_part<kTc>(g, t, phase, blockIdx.x, s, tc);
   if (threadIdx.x == 0) {
     if (info > 0) set_error(g.rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
-    else if (info < 0) set_error(g.rs, (uint32_t)SPX_ERR_BAD_OP, 0);
+    else if (info < 0) set_error(g.rs, (uint32_t)(info == -2 ? SPX_ERR_TIMEOUT : SPX_ERR_BAD_OP), 0);
     else atomicAdd(&g.rs->parts_done, 1u);
   }
+  __syncthreads();
+  if (kTc) tc_teardown(tcs);
 }
 
-int g_max_ctas_per_sm = -1;
+int g_max_ctas_per_sm[2] = {-1, -1};
 int g_sms = -1;
+
+constexpr size_t smem_bytes(bool tc) {
+  return tc ? (sizeof(F64Smem) > sizeof(TcBuf) ? sizeof(F64Smem) : sizeof(TcBuf)) + 1024
+            : sizeof(F64Smem);
+}
+
+template <bool kTc>
+void configure() {
+  cudaFuncSetAttribute(persistent_kernel<kTc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes(kTc));
+  cudaFuncSetAttribute(task_kernel<kTc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes(kTc));
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc>, kThreads,
+                                                smem_bytes(kTc));
+  g_max_ctas_per_sm[kTc ? 1 : 0] = occ > 0 ? occ : 1;
+}
 
 }  // namespace
 
-size_t persistent_smem_bytes() { return sizeof(F64Smem); }
+size_t persistent_smem_bytes() { return smem_bytes(false); }
 
 int persistent_max_ctas(int* per_sm) {
-  if (g_max_ctas_per_sm < 0) {
+  if (g_max_ctas_per_sm[0] < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(F64Smem));
-    cudaFuncSetAttribute(task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(F64Smem));
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel, kThreads,
-                                                  sizeof(F64Smem));
-    g_max_ctas_per_sm = occ > 0 ? occ : 1;
+    configure<false>();
+    configure<true>();
   }
-  if (per_sm) *per_sm = g_max_ctas_per_sm;
-  return g_sms * g_max_ctas_per_sm;
+  if (per_sm) *per_sm = g_max_ctas_per_sm[0];
+  return g_sms * g_max_ctas_per_sm[0];
 }
 
-cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st) {
-  const int maxc = persistent_max_ctas(nullptr);
+cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st) {
+  persistent_max_ctas(nullptr);
+  const int maxc = g_sms * g_max_ctas_per_sm[tc ? 1 : 0];
   int n = num_ctas > 0 ? num_ctas : maxc;
   if (n > maxc) n = maxc;  // every CTA resident: no CTA waits behind a spinning one
-  persistent_kernel<<<n, kThreads, sizeof(F64Smem), st>>>(g);
+  if (tc) persistent_kernel<true><<<n, kThreads, smem_bytes(true), st>>>(g);
+  else persistent_kernel<false><<<n, kThreads, smem_bytes(false), st>>>(g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
-                            const TileDesc* host_tiles, cudaStream_t st) {
+                            const TileDesc* host_tiles, bool tc, cudaStream_t st) {
   persistent_max_ctas(nullptr);
   for (uint32_t u = 0; u < g.ntasks; ++u) {
     const TaskDesc& t = host_tasks[u];
     for (uint32_t ph = 0; ph < t.nphases; ++ph) {
-      const uint32_t np = (t.flags & kFlagSerial)
-                              ? 1u : phase_parts(op_phase_units(t.op, host_tiles, t.h, ph));
-      task_kernel<<<np, kThreads, sizeof(F64Smem), st>>>(g, u, ph);
+      const uint32_t np =
+          (t.flags & kFlagSerial) ? 1u
+                                  : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph));
+      if (tc) task_kernel<true><<<np, kThreads, smem_bytes(true), st>>>(g, u, ph);
+      else task_kernel<false><<<np, kThreads, smem_bytes(false), st>>>(g, u, ph);
     }
   }
   return cudaGetLastError();

@@ -1,0 +1,151 @@
+// FP64 kernels of iterative refinement for the mixed-precision Cholesky:
+// the residual R = B - A X with per-column norms (for the normwise backward
+// error eta_j = ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf)), the
+// infinity norm of A, and the update X += alpha D.  The residual reads A once
+// (8 n^2 bytes) and does 2 n^2 nrhs flops; with 8 right-hand sides that is
+// 2 flop per byte, above the B300's FP64 ridge, so it runs on the DFMA pipe:
+// each CTA owns 64 (32 for 16 right-hand sides) rows, stages 128-column slices of X in shared memory, and
+// each warp accumulates 8 (4) rows x nrhs sums in registers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spx.h"
+
+namespace {
+
+// rows per warp: 8 (4 with 16 right-hand sides, to stay in registers)
+template <int NR>
+constexpr int rows_per_warp() { return NR >= 16 ? 4 : 8; }
+constexpr int kColSlice = 128;   // columns of X staged per step
+constexpr int kMaxRhs = 16;
+
+__device__ __forceinline__ void atomic_max_nonneg(double* p, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax((unsigned long long*)p, (unsigned long long)__double_as_longlong(v));
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) residual_kernel(const double* __restrict__ A, int n, int lda,
+                                                       const double* __restrict__ X, int ldx,
+                                                       const double* __restrict__ B, int ldb,
+                                                       double* __restrict__ R, int ldr,
+                                                       int nrhs, double* norms) {
+  __shared__ double xs[kColSlice][NR];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int RPW = rows_per_warp<NR>();
+  const int row0 = (blockIdx.x * 8 + warp) * RPW;
+  double acc[RPW][NR];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = 0.0;
+  for (int c0 = 0; c0 < n; c0 += kColSlice) {
+    const int w = min(kColSlice, n - c0);
+    for (int e = threadIdx.x; e < kColSlice * NR; e += blockDim.x) {
+      const int c = e / NR, j = e % NR;
+      xs[c][j] = (c < w && j < nrhs) ? X[(size_t)(c0 + c) * ldx + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const int r = row0 + i;
+      if (r >= n) break;
+      const double* a = A + (size_t)r * lda + c0;
+#pragma unroll
+      for (int cc = lane; cc < kColSlice; cc += 32) {
+        const double av = cc < w ? __ldcs(a + cc) : 0.0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[i][j] = fma(av, xs[cc][j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = row0 + i;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      double v = acc[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && r < n && j < nrhs) {
+        const double rv = B[(size_t)r * ldb + j] - v;
+        R[(size_t)r * ldr + j] = rv;
+        atomic_max_nonneg(norms + j, fabs(rv));
+        atomic_max_nonneg(norms + nrhs + j, fabs(X[(size_t)r * ldx + j]));
+        atomic_max_nonneg(norms + 2 * nrhs + j, fabs(B[(size_t)r * ldb + j]));
+      }
+    }
+  }
+}
+
+__global__ void norm_inf_kernel(const double* __restrict__ A, int n, int lda, double* out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* a = A + (size_t)warp * lda;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += fabs(__ldcs(a + c));
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) atomic_max_nonneg(out, s);
+}
+
+__global__ void axpy_kernel(double* __restrict__ Y, const double* __restrict__ X, long long count,
+                            double alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    Y[i] = fma(alpha, X[i], Y[i]);
+}
+
+template <int NR>
+cudaError_t launch_residual(const double* A, int n, int lda, const double* X, int ldx,
+                            const double* B, int ldb, double* R, int ldr, int nrhs,
+                            double* norms, cudaStream_t st) {
+  constexpr int rows = 8 * rows_per_warp<NR>();
+  residual_kernel<NR><<<(n + rows - 1) / rows, 256, 0, st>>>(A, n, lda, X, ldx, B, ldb, R, ldr,
+                                                                nrhs, norms);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int spx_residual_f64(const double* dev_A, int n, int lda, const double* dev_X, int ldx,
+                                const double* dev_B, int ldb, double* dev_R, int ldr, int nrhs,
+                                double* dev_norms, void* stream) {
+  if (!dev_A || !dev_X || !dev_B || !dev_R || !dev_norms || n < 1 || lda < n || nrhs < 1 ||
+      nrhs > kMaxRhs || ldx < nrhs || ldb < nrhs || ldr < nrhs)
+    return SPX_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // norms: max|r_j| at [j], max|x_j| at [nrhs + j], max|b_j| at [2 nrhs + j]
+  const int nr = nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16;
+  cudaError_t e = cudaMemsetAsync(dev_norms, 0, sizeof(double) * 3 * nrhs, st);
+  if (e != cudaSuccess) return SPX_ERR_CUDA;
+  switch (nr) {
+    case 1: e = launch_residual<1>(dev_A, n, lda, dev_X, ldx, dev_B, ldb, dev_R, ldr, nrhs, dev_norms, st); break;
+    case 2: e = launch_residual<2>(dev_A, n, lda, dev_X, ldx, dev_B, ldb, dev_R, ldr, nrhs, dev_norms, st); break;
+    case 4: e = launch_residual<4>(dev_A, n, lda, dev_X, ldx, dev_B, ldb, dev_R, ldr, nrhs, dev_norms, st); break;
+    case 8: e = launch_residual<8>(dev_A, n, lda, dev_X, ldx, dev_B, ldb, dev_R, ldr, nrhs, dev_norms, st); break;
+    default: e = launch_residual<16>(dev_A, n, lda, dev_X, ldx, dev_B, ldb, dev_R, ldr, nrhs, dev_norms, st);
+  }
+  return e == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
+}
+
+extern "C" int spx_norm_inf_f64(const double* dev_A, int n, int lda, double* dev_out, void* stream) {
+  if (!dev_A || !dev_out || n < 1 || lda < n) return SPX_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(dev_out, 0, sizeof(double), st) != cudaSuccess) return SPX_ERR_CUDA;
+  norm_inf_kernel<<<(n + 7) / 8, 256, 0, st>>>(dev_A, n, lda, dev_out);
+  return cudaGetLastError() == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
+}
+
+extern "C" int spx_axpy_f64(double* dev_Y, const double* dev_X, long long count, double alpha,
+                            void* stream) {
+  if (!dev_Y || !dev_X || count < 0) return SPX_ERR_INVALID_ARG;
+  if (count == 0) return SPX_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (count + 255) / 256;
+  if (blocks > 8LL * sms) blocks = 8LL * sms;
+  axpy_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(dev_Y, dev_X, count, alpha);
+  return cudaGetLastError() == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
+}

@@ -4,6 +4,7 @@
 // cudaMemcpyAsync uploads each of them.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,8 +32,11 @@ struct TileDesc {
   void* ptr;      // element (0,0), row-major
   void* lowp;     // optional low-precision copy (nullptr if none)
   int32_t rows, cols, ld, lowp_ld;
+  int32_t lmap;   // tensor map holding the low-precision copy, -1 if none
+  int32_t lr0, lc0;  // position of the copy's (0,0) in that map
+  int32_t pad;
 };
-static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
+static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
 
 // One task: op, operands (handles in op order), parts, argument.
 struct TaskDesc {
@@ -77,6 +81,7 @@ struct DevGraph {
   unsigned long long watchdog_ns;
   const TaskDesc* tasks;       // [ntasks]
   const TileDesc* tiles;       // [ntiles]
+  const CUtensorMap* maps;     // [nmaps] low-precision matrices (TMA)
   // access records in insertion order (records of one task are contiguous
   // and sorted by handle)
   const uint32_t* rec_handle;  // [nrec]
@@ -127,16 +132,23 @@ struct DevGraph {
 //     blocks.  Solves: one phase, 64-column blocks of the right-hand sides.
 __host__ __device__ inline uint32_t cdiv64(int a) { return (uint32_t)((a + kBlk - 1) / kBlk); }
 
-__host__ __device__ inline uint32_t op_phases(int op, const TileDesc* t, const uint32_t* h) {
+__host__ __device__ inline uint32_t cdiv128(int a) { return (uint32_t)((a + 127) / 128); }
+
+// Low-precision tasks (prec = SPX_TF32 / SPX_BF16): SYRK and GEMM_NT_SUB run
+// on the tensor cores in 128 x 128 output units (SYRK: lower block pairs);
+// TRSM runs its FP64 phases and then one more phase that writes the
+// low-precision copy of its result (64-row units).
+__host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* t,
+                                              const uint32_t* h) {
   switch (op) {
     case SPX_OP_POTRF: return 3 * cdiv64(t[h[0]].rows) - 2;
-    case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1;
+    case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
     default: return 1;
   }
 }
 
-__host__ __device__ inline uint32_t op_phase_units(int op, const TileDesc* t, const uint32_t* h,
-                                                   uint32_t phase) {
+__host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileDesc* t,
+                                                   const uint32_t* h, uint32_t phase) {
   switch (op) {
     case SPX_OP_POTRF: {
       const uint32_t nb = cdiv64(t[h[0]].rows), j = phase / 3, r = nb - 1 - j;
@@ -144,10 +156,16 @@ __host__ __device__ inline uint32_t op_phase_units(int op, const TileDesc* t, co
     }
     case SPX_OP_TRSM: {
       const uint32_t nbr = cdiv64(t[h[1]].rows), nbc = cdiv64(t[h[1]].cols), j = phase / 2;
+      if (phase >= 2 * nbc - 1) return nbr;  // low-precision copy
       return phase % 2 == 0 ? nbr : nbr * (nbc - 1 - j);
     }
-    case SPX_OP_SYRK: { const uint32_t nb = cdiv64(t[h[1]].rows); return nb * (nb + 1) / 2; }
+    case SPX_OP_SYRK: {
+      const uint32_t nb = prec != SPX_F64 ? cdiv128(t[h[1]].rows) : cdiv64(t[h[1]].rows);
+      return nb * (nb + 1) / 2;
+    }
     case SPX_OP_GEMM_NT_SUB:
+      if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
+      return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_NN_ADD:
     case SPX_OP_GEMM_FWD:
     case SPX_OP_GEMM_BWD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
@@ -164,9 +182,9 @@ __host__ __device__ inline uint32_t phase_parts(uint32_t units) {
 // Launchers implemented in the .cu files (all asynchronous on stream).
 cudaError_t launch_derive(const DevGraph& g, cudaStream_t st);
 cudaError_t launch_init(const DevGraph& g, cudaStream_t st);  // reset run state only
-cudaError_t launch_persistent(const DevGraph& g, int num_ctas, cudaStream_t st);
+cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
 cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
-                            const TileDesc* host_tiles, cudaStream_t st);
+                            const TileDesc* host_tiles, bool tc, cudaStream_t st);
 int persistent_max_ctas(int* per_sm);
 size_t persistent_smem_bytes();
 

@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -264,6 +265,76 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   tc_fence_before();
   __syncthreads();
   return true;
+}
+
+}  // namespace spx
+
+namespace spx {
+
+// Shared-memory context of the tensor-core ops inside the persistent kernel.
+struct TcCtx {
+  TcState* st;
+  TcBuf* buf;
+};
+
+// SYRK on the tensor cores: C (n x n, FP64, lower) -= L_lo L_lo^T; units are
+// the lower 128-block pairs of C.
+template <bool kBf16>
+__device__ bool op_tc_syrk(const DevGraph& g, const TileDesc& Lt, const TileDesc& Ct, uint32_t u0,
+                           uint32_t u1, TcCtx& tc) {
+  double* c = (double*)Ct.ptr;
+  const CUtensorMap* map = g.maps + Lt.lmap;
+  for (uint32_t u = u0; u < u1; ++u) {
+    int i = 0;
+    while ((uint32_t)((i + 1) * (i + 2) / 2) <= u) ++i;
+    const int bi = i, bj = (int)(u - (uint32_t)(i * (i + 1) / 2));
+    const int r0 = bi * kTcM, c0 = bj * kTcN;
+    if (!tc_gemm_unit<kBf16>(*tc.st, *tc.buf, map, Lt.lc0, Lt.lr0 + r0, map, Lt.lc0, Lt.lr0 + c0,
+                             Lt.cols, c + (size_t)r0 * Ct.ld + c0, Ct.ld, min(kTcM, Ct.rows - r0),
+                             min(kTcN, Ct.cols - c0), bi == bj))
+      return false;
+  }
+  return true;
+}
+
+// GEMM on the tensor cores: C (m x n, FP64) -= A_lo B_lo^T; units are the
+// 128 x 128 blocks of C, row-major.
+template <bool kBf16>
+__device__ bool op_tc_gemm(const DevGraph& g, const TileDesc& At, const TileDesc& Bt,
+                           const TileDesc& Ct, uint32_t u0, uint32_t u1, TcCtx& tc) {
+  double* c = (double*)Ct.ptr;
+  const uint32_t nbc = cdiv128(Ct.cols);
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)(u / nbc) * kTcM, c0 = (int)(u % nbc) * kTcN;
+    if (!tc_gemm_unit<kBf16>(*tc.st, *tc.buf, g.maps + At.lmap, At.lc0, At.lr0 + r0,
+                             g.maps + Bt.lmap, Bt.lc0, Bt.lr0 + c0, At.cols,
+                             c + (size_t)r0 * Ct.ld + c0, Ct.ld, min(kTcM, Ct.rows - r0),
+                             min(kTcN, Ct.cols - c0), false))
+      return false;
+  }
+  return true;
+}
+
+// Low-precision copy of 64-row blocks u0..u1 of a FP64 tile: BF16 by
+// round-to-nearest-even, or TF32 (FP64 -> FP32 nearest, then cvt.rna.tf32)
+// kept in FP32 storage.
+template <bool kBf16>
+__device__ void op_lowp_copy(const TileDesc& At, uint32_t u0, uint32_t u1) {
+  const double* a = (const double*)At.ptr;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)u * kBlk, mb = min(kBlk, At.rows - r0);
+    for (int e = threadIdx.x; e < mb * At.cols; e += kThreads) {
+      const int r = r0 + e / At.cols, c = e % At.cols;
+      const double v = __ldcg(a + (size_t)r * At.ld + c);
+      if (kBf16) {
+        ((__nv_bfloat16*)At.lowp)[(size_t)r * At.lowp_ld + c] = __double2bfloat16(v);
+      } else {
+        uint32_t t;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(__double2float_rn(v)));
+        ((uint32_t*)At.lowp)[(size_t)r * At.lowp_ld + c] = t;
+      }
+    }
+  }
 }
 
 }  // namespace spx

@@ -19,7 +19,7 @@ struct Tiles {
 };
 
 int register_tiles(spx_graph_t g, double* base, int n_rows, int n_cols, int ld, int b,
-                   bool lower_only, Tiles& out) {
+                   bool lower_only, Tiles& out, char* lowp = nullptr, int ldlo = 0, int elem = 0) {
   const int Tr = (n_rows + b - 1) / b, Tc = (n_cols + b - 1) / b;
   out.T = Tr > Tc ? Tr : Tc;
   out.b = b;
@@ -29,8 +29,9 @@ int register_tiles(spx_graph_t g, double* base, int n_rows, int n_cols, int ld, 
       if (lower_only && j > i) continue;
       const int r = n_rows - i * b < b ? n_rows - i * b : b;
       const int c = n_cols - j * b < b ? n_cols - j * b : b;
+      void* lo = lowp ? lowp + ((size_t)i * b * ldlo + (size_t)j * b) * elem : nullptr;
       int rc = spx_tile_register(g, base + (size_t)i * b * ld + (size_t)j * b, r, c, ld, SPX_DT_F64,
-                                 nullptr, 0, &out.at(i, j));
+                                 lo, lo ? ldlo : 0, &out.at(i, j));
       if (rc != SPX_OK) return rc;
     }
   return SPX_OK;
@@ -38,39 +39,49 @@ int register_tiles(spx_graph_t g, double* base, int n_rows, int n_cols, int ld, 
 
 }  // namespace
 
-extern "C" int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b,
-                                   double* dev_X, int nrhs, int ldx, int lookahead, int prec,
-                                   long long* out_ntasks) {
-  if (!g || !dev_A || n < 1 || b < 1 || lda < n || prec != SPX_F64 ||
-      (dev_X && (nrhs < 1 || ldx < nrhs)))
+namespace {
+
+// factor: insert the factorization tasks; dev_X: the solve tasks too.
+int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo, int ldlo,
+                    bool factor, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
+                    long long* out_ntasks) {
+  if (!g || !dev_A || n < 1 || b < 1 || lda < n || (dev_X && (nrhs < 1 || ldx < nrhs)))
     return SPX_ERR_INVALID_ARG;
+  if (prec != SPX_F64 && (!dev_Alo || ldlo < n)) return SPX_ERR_INVALID_ARG;
+  const int elem = prec == SPX_BF16 ? 2 : 4;
+  int rc = SPX_OK;
+  if (prec != SPX_F64)
+    rc = spx_lowp_register(g, dev_Alo, n, n, ldlo, prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32,
+                           nullptr);
+  if (rc != SPX_OK) return rc;
   Tiles A;
-  int rc = register_tiles(g, dev_A, n, n, lda, b, true, A);
+  rc = register_tiles(g, dev_A, n, n, lda, b, true, A, prec != SPX_F64 ? (char*)dev_Alo : nullptr,
+                      ldlo, elem);
   if (rc != SPX_OK) return rc;
   const int T = A.T;
   const int R = SPX_READ, W = SPX_WRITE;
   const int hi = lookahead ? 1 : 0;
   long long count = 0;
   auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
-                 int prio, unsigned* id) {
+                 int prio, unsigned* id, int p = SPX_F64) {
     const unsigned* hp = hs.begin();
     const int* mp = ms.begin();
-    int r = spx_task_insert(g, op, hp, mp, (int)hs.size(), prio, prec, id);
+    int r = spx_task_insert(g, op, hp, mp, (int)hs.size(), prio, p, id);
     if (r == SPX_OK) ++count;
     return r;
   };
-  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+  for (int k = 0; k < T && rc == SPX_OK && factor; ++k) {
     unsigned t = 0;
-    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, hi, &t);
+    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, hi, &t, SPX_F64);
     if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-      rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, hi, nullptr);
+      rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, hi, nullptr, prec);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-      rc = ins(SPX_OP_SYRK, {A.at(i, k), A.at(i, i)}, {R, W}, hi, nullptr);
+      rc = ins(SPX_OP_SYRK, {A.at(i, k), A.at(i, i)}, {R, W}, hi, nullptr, prec);
     for (int j = k + 1; j < T && rc == SPX_OK; ++j)
       for (int i = j + 1; i < T && rc == SPX_OK; ++i)
         rc = ins(SPX_OP_GEMM_NT_SUB, {A.at(i, k), A.at(j, k), A.at(i, j)}, {R, R, W},
-                 j == k + 1 ? hi : 0, nullptr);
+                 j == k + 1 ? hi : 0, nullptr, prec);
   }
   if (rc == SPX_OK && dev_X) {
     std::vector<unsigned> x(T);
@@ -92,6 +103,31 @@ extern "C" int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda,
   }
   if (out_ntasks) *out_ntasks = count;
   return rc;
+}
+
+}  // namespace
+
+extern "C" int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                   double* dev_X, int nrhs, int ldx, int lookahead, int prec,
+                                   long long* out_ntasks) {
+  if (prec != SPX_F64) return SPX_ERR_INVALID_ARG;
+  return insert_cholesky(g, dev_A, n, lda, b, nullptr, 0, true, dev_X, nrhs, ldx, lookahead,
+                         SPX_F64, out_ntasks);
+}
+
+extern "C" int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                         void* dev_Alo, int ldlo, double* dev_X, int nrhs, int ldx,
+                                         int lookahead, int prec, long long* out_ntasks) {
+  if (prec != SPX_TF32 && prec != SPX_BF16) return SPX_ERR_INVALID_ARG;
+  return insert_cholesky(g, dev_A, n, lda, b, dev_Alo, ldlo, true, dev_X, nrhs, ldx, lookahead,
+                         prec, out_ntasks);
+}
+
+extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,
+                                double* dev_X, int nrhs, int ldx, long long* out_ntasks) {
+  if (!dev_X) return SPX_ERR_INVALID_ARG;
+  return insert_cholesky(g, dev_L, n, ld, b, nullptr, 0, false, dev_X, nrhs, ldx, 1, SPX_F64,
+                         out_ntasks);
 }
 
 extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,

@@ -1,0 +1,126 @@
+"""Mixed-precision Cholesky solve with FP64 iterative refinement.
+
+Factorization: one task graph (spx_cholesky_insert_mixed): POTRF on the
+diagonal tiles in FP64, TRSM in FP64 writing a low-precision copy of each
+factor tile, SYRK and GEMM trailing updates on the tensor cores (TF32 or
+BF16 operands, FP32 accumulation) subtracted from the FP64 trailing matrix.
+The first solve uses that factor.  Refinement (classical, on the host loop):
+r = b - A x in FP64 (spx_residual_f64), L L^T d = r with the same factor
+(a second, solve-only graph replayed through a CUDA graph), x += d, until the
+normwise backward error of every right-hand side is <= tol or the iteration
+cap is reached; non-convergence is reported, never hidden.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+
+import torch
+
+from . import spx
+
+P = ctypes.c_void_p
+
+
+def _p(t):
+    return P(t.data_ptr())
+
+
+def _s(stream):
+    return P((stream or torch.cuda.current_stream()).cuda_stream)
+
+
+def norm_inf(A, stream=None) -> torch.Tensor:
+    out = torch.empty(1, dtype=torch.float64, device=A.device)
+    spx._check(spx.lib.spx_norm_inf_f64(_p(A), A.shape[0], A.stride(0), _p(out), _s(stream)),
+               "spx_norm_inf_f64")
+    return out
+
+
+def residual(A, X, B, R, norms, stream=None):
+    n, nrhs = X.shape
+    spx._check(spx.lib.spx_residual_f64(_p(A), n, A.stride(0), _p(X), X.stride(0), _p(B), B.stride(0),
+                                        _p(R), R.stride(0), nrhs, _p(norms), _s(stream)),
+               "spx_residual_f64")
+
+
+def axpy(Y, X, alpha=1.0, stream=None):
+    spx._check(spx.lib.spx_axpy_f64(_p(Y), _p(X), Y.numel(), alpha, _s(stream)), "spx_axpy_f64")
+
+
+def factor_graph(g: spx.Graph, A, Alo, b: int, X, prec: int, lookahead=True) -> int:
+    n = A.shape[0]
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_cholesky_insert_mixed(
+        g._h, _p(A), n, A.stride(0), b, _p(Alo), Alo.stride(0), _p(X) if X is not None else None,
+        X.shape[1] if X is not None else 0, X.stride(0) if X is not None else 0,
+        1 if lookahead else 0, prec, ctypes.byref(nt)), "spx_cholesky_insert_mixed")
+    g._keep.extend([A, Alo] + ([X] if X is not None else []))
+    return nt.value
+
+
+def solve_graph(g: spx.Graph, L, b: int, R) -> int:
+    n = L.shape[0]
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_solve_insert(g._h, _p(L), n, L.stride(0), b, _p(R), R.shape[1],
+                                        R.stride(0), ctypes.byref(nt)), "spx_solve_insert")
+    g._keep.extend([L, R])
+    return nt.value
+
+
+def lowp_dtype(prec: int):
+    return torch.bfloat16 if prec == spx.BF16 else torch.float32
+
+
+def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
+                max_iter: int | None = None):
+    """Solve A0 X = B.  Returns (X, L, info) where L holds the factor (lower
+    triangle) and info has 'converged', 'iterations', 'eta' (history of the
+    max normwise backward error), 'factor_ms', 'refine_ms', 'status'."""
+    if max_iter is None:
+        max_iter = 30 if prec == spx.TF32 else 50
+    n, nrhs = B.shape
+    A = A0.clone()
+    Alo = torch.zeros((n, n), dtype=lowp_dtype(prec), device=A0.device)
+    X = B.clone()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    g = spx.Graph()
+    factor_graph(g, A, Alo, b, X, prec)
+    ev[0].record()
+    rc, info = g.run()
+    ev[1].record()
+    if rc != spx.OK:
+        g.close()
+        return X, A, {"status": rc, "info": info, "converged": False, "iterations": 0, "eta": []}
+    R = torch.empty_like(B)
+    gs = spx.Graph(cuda_graph=True)
+    solve_graph(gs, A, b, R)
+    anorm = norm_inf(A0)
+    norms = torch.empty(3 * nrhs, dtype=torch.float64, device=A0.device)
+    history = []
+    converged = False
+    it = 0
+    for it in range(max_iter + 1):
+        residual(A0, X, B, R, norms)
+        nv = norms.cpu()
+        an = float(anorm.item())
+        eta = max(float(nv[j]) / (an * float(nv[nrhs + j]) + float(nv[2 * nrhs + j]))
+                  for j in range(nrhs))
+        history.append(eta)
+        if eta <= tol:
+            converged = True
+            break
+        if it == max_iter:
+            break
+        rc, _ = gs.run()
+        if rc != spx.OK:
+            break
+        gs.reset()
+        axpy(X, R)
+    ev[2].record()
+    ev[2].synchronize()
+    out = {"status": rc, "converged": converged, "iterations": it, "eta": history,
+           "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2])}
+    g.close()
+    gs.close()
+    return X, A, out

@@ -69,6 +69,12 @@ def _load():
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
         "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
+        "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
+        "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
+        "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),
+        "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
+        "spx_norm_inf_f64": (I, [P, I, I, P, P]),
+        "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
         "spx_graph_derive_noalloc": (I, [P, P, P, P, I, I, LL, P, P, LL, P, P, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),

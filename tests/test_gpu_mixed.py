@@ -1,0 +1,100 @@
+"""GPU parity of the mixed-precision Cholesky (tensor-core TF32 / BF16
+trailing updates, FP64 POTRF) and of FP64 iterative refinement.
+
+* integer unit-lower factors: every product and partial sum is an exact
+  integer in BF16/TF32 operands with FP32 accumulation, so the factor and the
+  solve are bit-exact on the mixed path too;
+* random SPD systems: refinement reaches the FP64 normwise backward error
+  <= 1e-14 (recomputed by the oracle with compensated residuals), or reports
+  non-convergence with its iteration count;
+* executors agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2308_15964_b300 import inputs
+from tests._gpu import need_cuda, spx_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    need_cuda()
+    return spx_mod()
+
+
+def unit_lower(n, seed):
+    rng = np.random.default_rng(seed)
+    L = np.tril(rng.integers(-1, 2, size=(n, n)).astype(np.float64), -1)
+    np.fill_diagonal(L, 1.0)
+    return L
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,b", [(1024, 256), (1000, 256), (768, 384)])
+def test_integer_factor_bit_exact(S, prec, n, b):
+    from paper_2308_15964_b300 import mixed
+    p = S.TF32 if prec == "tf32" else S.BF16
+    L0 = unit_lower(n, n + b)
+    A = L0 @ L0.T
+    x0 = np.random.default_rng(2).integers(-3, 4, size=(n, 2)).astype(np.float64)
+    Ad = torch.from_numpy(A).cuda()
+    Xd = torch.from_numpy(A @ x0).cuda()
+    Alo = torch.zeros((n, n), dtype=mixed.lowp_dtype(p), device="cuda")
+    outs = []
+    for ex in (S.EXEC_PERSISTENT, S.EXEC_PER_TASK):
+        A1, X1 = Ad.clone(), Xd.clone()
+        g = S.Graph(executor=ex)
+        mixed.factor_graph(g, A1, Alo, b, X1, p)
+        rc, _ = g.run()
+        assert rc == 0
+        g.close()
+        assert np.array_equal(np.tril(A1.cpu().numpy()), L0)
+        assert np.array_equal(X1.cpu().numpy(), x0)
+        outs.append(A1)
+    assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_refinement_reaches_fp64(S, prec):
+    from paper_2308_15964_b300 import mixed
+    p = S.TF32 if prec == "tf32" else S.BF16
+    n, b, nrhs = 1536, 512, 3
+    A = inputs.spd_matrix(n, 1e-2, seed=4)
+    B = inputs.rhs(n, nrhs, seed=4)
+    X, L, info = mixed.mixed_solve(A.cuda(), B.cuda(), b=b, prec=p)
+    assert info["status"] == 0
+    eta = O.solve_backward_error(A.numpy(), X.cpu().numpy(), B.numpy())
+    if info["converged"]:
+        assert eta.max() <= 2e-14, (eta, info["eta"])
+    else:
+        assert info["iterations"] == (30 if p == S.TF32 else 50)
+    if p == S.TF32:
+        assert info["converged"], info["eta"]
+    # the low-precision factor itself: backward error of order the precision
+    beta = O.factor_backward_error(A.numpy(), L.cpu().numpy())
+    assert beta < (2e-3 if p == S.TF32 else 2e-2), beta
+
+
+def test_residual_kernel_vs_oracle(S):
+    from paper_2308_15964_b300 import mixed
+    n, nrhs = 700, 5
+    A = inputs.spd_matrix(n, 1.0, seed=8)
+    X = inputs.uniform((n, nrhs), 9)
+    B = inputs.uniform((n, nrhs), 10)
+    Ad, Xd, Bd = A.cuda(), X.cuda(), B.cuda()
+    R = torch.empty_like(Bd)
+    norms = torch.empty(3 * nrhs, dtype=torch.float64, device="cuda")
+    mixed.residual(Ad, Xd, Bd, R, norms)
+    ref = B.numpy() - A.numpy() @ X.numpy()
+    scale = np.abs(A.numpy()) @ np.abs(X.numpy()) + np.abs(B.numpy())
+    assert (np.abs(R.cpu().numpy() - ref) <= n * 2.2e-16 * scale).all()
+    nv = norms.cpu().numpy()
+    assert np.allclose(nv[:nrhs], np.abs(R.cpu().numpy()).max(0))
+    assert np.array_equal(nv[nrhs:2 * nrhs], np.abs(X.numpy()).max(0))
+    assert np.array_equal(nv[2 * nrhs:], np.abs(B.numpy()).max(0))
+    an = mixed.norm_inf(Ad).item()
+    assert abs(an - np.abs(A.numpy()).sum(1).max()) <= 1e-12 * an
