@@ -42,7 +42,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     objdir = os.path.join(PKG, "_build")
     os.makedirs(objdir, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+    # -fno-unswitch-loops: GCC 13 at -O3 unswitches the loop that sums a task's
+    # queue entries over its phases (a switch inside an inlined function) into
+    # wrong code; the host side is not hot, so that transform is turned off.
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-fno-unswitch-loops", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr", "-prec-div=true", "-prec-sqrt=true", "-fmad=true"]
     objs = []
     for src in sources():

@@ -757,9 +757,10 @@ int spx_graph_stats(spx_graph_t g, long long* out, int n) {
   if (!g || !out || n < 0) return SPX_ERR_INVALID_ARG;
   if (g->state != kDone) return SPX_ERR_STATE;
   const RunState& r = *g->host_rs;
-  const long long v[6] = {(long long)r.parts_done, (long long)r.hiwater, (long long)r.empty_pops,
-                          (long long)r.ctas, (long long)r.busy_cycles, (long long)r.total_cycles};
-  for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
+  const long long v[9] = {(long long)r.parts_done, (long long)r.hiwater, (long long)r.empty_pops,
+                          (long long)r.ctas, (long long)r.busy_cycles, (long long)r.total_cycles,
+                          (long long)g->dg.qcap, (long long)r.tail[0].v, (long long)r.tail[1].v};
+  for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
   return SPX_OK;
 }
 

@@ -210,9 +210,10 @@ class Graph:
         return r
 
     def stats(self):
-        v = np.zeros(6, np.int64)
-        _check(lib.spx_graph_stats(self._h, _ptr(v), 6), "spx_graph_stats")
-        keys = ["parts", "queue_hiwater", "empty_pops", "ctas", "busy_cycles", "total_cycles"]
+        v = np.zeros(9, np.int64)
+        _check(lib.spx_graph_stats(self._h, _ptr(v), 9), "spx_graph_stats")
+        keys = ["parts", "queue_hiwater", "empty_pops", "ctas", "busy_cycles", "total_cycles",
+                "queue_capacity", "pushed_high", "pushed_normal"]
         return dict(zip(keys, (int(x) for x in v)))
 
     def timing(self):

@@ -27,7 +27,7 @@ def rel_entry_err(L, Lref):
     return np.abs(L - Lref).max() / np.abs(Lref).max()
 
 
-@pytest.mark.parametrize("n,b,nrhs", [(512, 64, 1), (100, 32, 3), (1000, 128, 2), (64, 64, 1),
+@pytest.mark.parametrize("n,b,nrhs", [(512, 64, 1), (100, 32, 3), (1000, 128, 2), (64, 64, 1), (1024, 256, 2),
                                       (33, 8, 1), (700, 256, 5), (2048, 512, 1)])
 def test_factor_solve_vs_oracle(S, n, b, nrhs):
     A = inputs.spd_matrix(n, 1.0, seed=1).numpy()
