@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
-    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch"],
+    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     return p.parse_args()
@@ -181,6 +181,9 @@ def main():
     if args.workload == "batch":
         run_batch(args, world, rank, local)
         return
+    if args.workload == "mixed":
+        run_mixed(args, world, rank, local)
+        return
 
     n, b = args.n, args.tile
     flops = cholesky.cholesky_flops(n)
@@ -307,6 +310,61 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_mixed(args, world, rank, local):
+    """Mixed precision: TF32 and BF16 tensor-core trailing updates, FP64 POTRF,
+    FP64 refinement of 8 right-hand sides to eta <= 1e-14 (n = 32768, tile 512,
+    sigma = 1e-3 unless given)."""
+    import torch
+    from paper_2308_15964_b300 import cholesky, inputs, mixed, spx
+    n = args.n if args.n != 16384 else 32768
+    b, nrhs = args.tile, 8
+    sigma = args.sigma if args.sigma != 0.1 else 1e-3
+    A0 = inputs.spd_matrix(n, sigma, seed=4 + rank, device="cuda")
+    B = inputs.rhs(n, nrhs, seed=4 + rank, device="cuda")
+    out = {"metric": METRIC, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "tf32/bf16 updates, f64 potrf+refinement", "data": "synthetic",
+           "config": {"workload": f"mixed-precision Cholesky n={n} tile={b}, {nrhs} RHS, "
+                                  f"A = B B^T/n + {sigma} I, FP64 refinement to eta <= 1e-14",
+                      "n": n, "tile": b, "nrhs": nrhs, "sigma": sigma}}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with Clocks(local) as clk:
+        for name, prec in (("tf32", spx.TF32), ("bf16", spx.BF16)):
+            runs = []
+            for i in range(args.warmup + args.steps):
+                ev[0].record()
+                X, L, info = mixed.mixed_solve(A0, B, b=b, prec=prec)
+                ev[1].record()
+                ev[1].synchronize()
+                if i >= args.warmup:
+                    runs.append((ev[0].elapsed_time(ev[1]), info))
+                del X, L
+            ms = statistics.mean(r[0] for r in runs)
+            inf = runs[-1][1]
+            fac = statistics.mean(r[1]["factor_ms"] for r in runs)
+            flops = cholesky.cholesky_flops(n, nrhs)
+            out[name] = {"ms_per_solve": ms, "factor_ms": fac,
+                         "refine_ms": statistics.mean(r[1]["refine_ms"] for r in runs),
+                         "gflops_total": flops / (ms * 1e-3) / 1e9,
+                         "factor_gflops": n ** 3 / 3 / (fac * 1e-3) / 1e9,
+                         "converged": inf["converged"], "iterations": inf["iterations"],
+                         "eta_final": inf["eta"][-1] if inf["eta"] else None,
+                         "eta_history": inf["eta"]}
+    out["value"] = out["tf32"]["gflops_total"]
+    out["ms_per_step"] = out["tf32"]["ms_per_solve"]
+    out["clocks"] = clk.summary()
+    trailing_bytes = 16.0 * n ** 3 / (6 * b)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6451.5)
+    out["roofline"] = {"bound": "hbm", "achieved": trailing_bytes / (out["tf32"]["factor_ms"] * 1e-3) / 1e9,
+                       "peak": hbm, "unit": "GB/s",
+                       "frac": trailing_bytes / (out["tf32"]["factor_ms"] * 1e-3) / 1e9 / hbm,
+                       "traffic": None, "kernel": "persistent_kernel<tensor cores> (factorization)",
+                       "note": "algorithmic trailing traffic 16 n^3/(6 b) bytes over the factor time"}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_batch(args, world, rank, local):
