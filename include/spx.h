@@ -382,6 +382,62 @@ int spx_norm_inf_f64(const double* dev_A, int n, int lda, double* dev_out, void*
 /* Y += alpha X over count contiguous FP64 values (the refinement update). */
 int spx_axpy_f64(double* dev_Y, const double* dev_X, long long count, double alpha, void* stream);
 
+/* ---- Continuous-batching server ------------------------------------------
+ * One resident persistent kernel runs the tasks of every live request; new
+ * requests are admitted while it runs (the serving form of the executor: the
+ * paper's runtime keeps accepting tasks while workers compute, section
+ * "Background" / "Task insertion").  A request is a graph built with the
+ * calls above and not executed; the server copies it (the graph may be
+ * cleared or destroyed after submit returns, the tile memory must live until
+ * the request is done).  Requests may not use COMMUTATIVE_WRITE; low-precision
+ * tasks need tensor_cores = 1. */
+typedef struct spx_server* spx_server_t;
+
+typedef struct {
+  long long max_tasks;       /* pool sizes shared by all live requests       */
+  long long max_tiles;
+  long long max_records;
+  long long max_edges;
+  long long max_maps;
+  long long queue_capacity;  /* ring entries per priority                    */
+  int num_ctas;              /* resident CTAs; 0 = resident maximum          */
+  int tensor_cores;          /* 1 = resident kernel with TMEM (TF32/BF16)    */
+  unsigned long long watchdog_ns; /* live work without progress -> error     */
+  unsigned long long idle_ns;     /* resident kernel exits when idle this long
+                                     (relaunched by the next submit/poll)   */
+} spx_server_config_t;
+
+void spx_server_config_default(spx_server_config_t* cfg);
+
+/* Allocate the pools (one device arena) and the host-mapped control block.
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_OOM, SPX_ERR_CUDA. */
+int spx_server_create(spx_server_t* out, const spx_server_config_t* cfg);
+
+/* Copy graph g into the pools and publish it; the resident kernel derives
+ * its DAG on the device and interleaves its tasks with the other requests'.
+ * Launches the resident kernel if it is not running.  *out_request receives
+ * the request id.  SPX_ERR_OOM: no room now (pools, request slots or queue
+ * entries) - poll finished requests and retry (admission).  Errors also:
+ * SPX_ERR_INVALID_ARG, SPX_ERR_STATE, SPX_ERR_CUDA, or the server's failure
+ * status (SPX_ERR_TIMEOUT, SPX_ERR_QUEUE_FULL) if its kernel died. */
+int spx_server_submit(spx_server_t s, spx_graph_t g, unsigned long long* out_request);
+
+/* 1 when the request finished (status: SPX_OK or SPX_NOT_SPD with info, its
+ * pool ranges are freed and the id becomes invalid), 0 while it runs,
+ * negative on error (SPX_ERR_BAD_HANDLE for an unknown id). */
+int spx_server_poll(spx_server_t s, unsigned long long request, int* status, int* info);
+
+/* Let the resident kernel finish the live requests and exit; returns its
+ * status.  The server can be used again afterwards. */
+int spx_server_stop(spx_server_t s);
+
+/* Counters (after stop): out[0] parts run, out[1] tasks finished, out[2]
+ * requests claimed, out[3] requests live, out[4] busy cycles, out[5] total
+ * cycles.  n <= 6.  SPX_ERR_STATE while the kernel runs. */
+int spx_server_stats(spx_server_t s, long long* out, int n);
+
+void spx_server_destroy(spx_server_t s);
+
 /* Static description of a status code. */
 const char* spx_strerror(int code);
 

@@ -1,5 +1,5 @@
 // Device steps of the dependency derivation, shared by the derivation
-// kernels.  One CTA of kDeriveThreads threads runs every step; block
+// kernels.  One CTA (kDeriveThreads threads unless given) runs every step; block
 // barriers separate the steps.  See derive.cu for the model and the steps.
 #pragma once
 
@@ -23,14 +23,15 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   return v;
 }
 
-// In-place exclusive scan of a[0..n) by the whole CTA; returns the total.
-// Every thread must call it.
+// In-place exclusive scan of a[0..n) by the whole CTA of NT threads
+// (sh: NT/32 + 1 words); returns the total.  Every thread must call it.
+template <int NT = kDeriveThreads>
 __device__ uint32_t block_excl_scan(uint32_t* a, uint32_t n, uint32_t* sh) {
   constexpr int kItems = 4;
-  constexpr int kWarps = kDeriveThreads / 32;
+  constexpr int kWarps = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t carry = 0;
-  for (uint32_t base = 0; base < n; base += kDeriveThreads * kItems) {
+  for (uint32_t base = 0; base < n; base += NT * kItems) {
     uint32_t v[kItems];
     uint32_t sum = 0;
 #pragma unroll
@@ -108,21 +109,23 @@ __device__ uint32_t merge_successors(const DevGraph& g, uint32_t u, uint32_t ngr
 // indeg).  Reads rec_*, task_rec; uses hptr, s_task, s_mode, s_first,
 // rec_pos, gid, gpos as scratch.  Returns false, with row_ptr[ntasks] = E
 // and col / indeg not written, when E > ecap.  Every thread must call it.
+// Steps 1-4 run by a CTA of NT threads (sh: NT/32 + 1 words).
+template <int NT = kDeriveThreads>
 __device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
   const uint32_t N = g.ntasks, H = g.ntiles, M = g.nrec;
   const int tid = threadIdx.x;
 
   // 1. accesses per handle -> list offsets
-  for (uint32_t i = tid; i <= H; i += kDeriveThreads) g.hptr[i] = 0;
-  for (uint32_t i = tid; i < N; i += kDeriveThreads) g.indeg[i] = 0;
+  for (uint32_t i = tid; i <= H; i += NT) g.hptr[i] = 0;
+  for (uint32_t i = tid; i < N; i += NT) g.indeg[i] = 0;
   __syncthreads();
-  for (uint32_t r = tid; r < M; r += kDeriveThreads) atomicAdd(&g.hptr[g.rec_handle[r]], 1u);
+  for (uint32_t r = tid; r < M; r += NT) atomicAdd(&g.hptr[g.rec_handle[r]], 1u);
   __syncthreads();
-  block_excl_scan(g.hptr, H + 1, sh);
+  block_excl_scan<NT>(g.hptr, H + 1, sh);
   __syncthreads();
 
   // 2. per-handle lists in insertion order
-  for (uint32_t u = tid; u < N; u += kDeriveThreads) {
+  for (uint32_t u = tid; u < N; u += NT) {
     for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r) {
       const uint32_t seq = g.rec_seq[r];
       const uint32_t p = g.hptr[g.rec_handle[r]] + seq;
@@ -135,11 +138,11 @@ __device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
   __syncthreads();
 
   // 3. groups
-  for (uint32_t p = tid; p < M; p += kDeriveThreads) g.gid[p] = group_start(g, p) ? 1u : 0u;
+  for (uint32_t p = tid; p < M; p += NT) g.gid[p] = group_start(g, p) ? 1u : 0u;
   __syncthreads();
-  const uint32_t G = block_excl_scan(g.gid, M, sh);
+  const uint32_t G = block_excl_scan<NT>(g.gid, M, sh);
   __syncthreads();
-  for (uint32_t p = tid; p < M; p += kDeriveThreads) {
+  for (uint32_t p = tid; p < M; p += NT) {
     const bool f = group_start(g, p);
     const uint32_t gi = g.gid[p] + (f ? 1u : 0u) - 1u;
     g.gid[p] = gi;
@@ -149,13 +152,13 @@ __device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
   __syncthreads();
 
   // 4. unique successors: count, scan, write
-  for (uint32_t u = tid; u < N; u += kDeriveThreads) g.row_ptr[u] = merge_successors(g, u, G, nullptr);
+  for (uint32_t u = tid; u < N; u += NT) g.row_ptr[u] = merge_successors(g, u, G, nullptr);
   if (tid == 0) g.row_ptr[N] = 0;
   __syncthreads();
-  const uint32_t E = block_excl_scan(g.row_ptr, N + 1, sh);
+  const uint32_t E = block_excl_scan<NT>(g.row_ptr, N + 1, sh);
   __syncthreads();
   if (E > g.ecap) return false;
-  for (uint32_t u = tid; u < N; u += kDeriveThreads) merge_successors(g, u, G, g.col + g.row_ptr[u]);
+  for (uint32_t u = tid; u < N; u += NT) merge_successors(g, u, G, g.col + g.row_ptr[u]);
   __syncthreads();
   return true;
 }

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "spx.h"
+#include "graph_access.h"
 #include "spx_internal.h"
 #include "tmap.h"
 
@@ -852,3 +853,22 @@ void spx_graph_destroy(spx_graph_t g) {
 }
 
 }  // extern "C"
+
+int spx_graph_view(spx_graph_t g, spx::GraphView* v) {
+  if (!g || !v) return SPX_ERR_INVALID_ARG;
+  if (g->state == kRunning) return SPX_ERR_STATE;
+  v->tasks = g->tasks.data();
+  v->ntasks = g->tasks.size();
+  v->tiles = g->tiles.data();
+  v->ntiles = g->tiles.size();
+  v->maps = g->maps.data();
+  v->nmaps = g->maps.size();
+  v->rec_handle = g->rec_handle.data();
+  v->rec_seq = g->rec_seq.data();
+  v->rec_mode = g->rec_mode.data();
+  v->nrec = g->rec_handle.size();
+  v->task_rec = g->task_rec.data();
+  v->cand_edges = g->cand_edges;
+  v->items = g->items[0] + g->items[1];
+  return SPX_OK;
+}

@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "derive_steps.cuh"
 #include "spx_internal.h"
 #include "tile_f64.cuh"
 #include "tile_tc.cuh"
@@ -312,7 +313,194 @@ __device__ void unlock_comm(const DevGraph& g, uint32_t u) {
     if (g.rec_mode[r] == SPX_COMMUTATIVE_WRITE) atomicExch(&g.locks[g.rec_handle[r]], 0u);
 }
 
-template <bool kTc>
+
+// ---------------------------------------------------------------------------
+// Server mode.  Queues are bounded MPMC rings with one sequence word per cell
+// (the cell of ticket t can be written when seq == t and read when
+// seq == t + 1; the reader hands it to ticket t + qcap).  Pushers wait
+// (bounded) for a slow reader of the previous round, so no entry is lost
+// when the ring wraps.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSubmit = 0xFFFFFFFDu;  // pop result: a submission was claimed
+
+__device__ bool ring_put(const DevGraph& g, uint32_t q, uint32_t ticket, uint32_t v) {
+  const uint32_t cell = ticket % g.qcap;
+  uint32_t spins = 0;
+  while (ld_volatile(&g.qseq[q][cell]) != ticket) {
+    if ((++spins & 1023u) == 0) {
+      if (ld_volatile(&g.rs->abort)) return false;
+      if (watchdog_expired(g)) {
+        set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+        return false;
+      }
+    }
+  }
+  *(volatile uint32_t*)&g.queue[q][cell] = v;
+  __threadfence();
+  *(volatile uint32_t*)&g.qseq[q][cell] = ticket + 1;
+  return true;
+}
+
+// Push np consecutive parts of pool task u (one thread).
+__device__ void ring_push_task(const DevGraph& g, uint32_t u, uint32_t np, uint32_t prio) {
+  const uint32_t q = prio ? 0u : 1u;
+  const uint32_t t0 = atomicAdd(&g.rs->tail[q].v, np);
+  atomicMax(&g.rs->hiwater, t0 + np - ld_volatile(&g.rs->head[q].v));
+  for (uint32_t p = 0; p < np; ++p)
+    if (!ring_put(g, q, t0 + p, (u << kPartBits) | p)) return;
+}
+
+// Pop a queue entry, claim a submission (kSubmit, entry copied to *sub), or
+// leave (kExit): after shutdown with no live request, after idle_ns with
+// nothing live, on abort, or when live work makes no progress (watchdog).
+__device__ uint32_t pop_server(const DevGraph& g, uint32_t& empties, SubEntry* sub) {
+  RunState* rs = g.rs;
+  uint32_t backoff = 64, iter = 0;
+  unsigned long long idle_start = 0;
+  for (;;) {
+    if (ld_volatile(&rs->abort)) return kExit;
+    for (int q = 0; q < 2; ++q) {
+      uint32_t h = ld_volatile(&rs->head[q].v);
+      uint32_t t = ld_volatile(&rs->tail[q].v);
+      while ((int32_t)(t - h) > 0) {
+        const uint32_t prev = atomicCAS(&rs->head[q].v, h, h + 1);
+        if (prev == h) {
+          const uint32_t cell = h % g.qcap;
+          uint32_t spins = 0;
+          while (ld_volatile(&g.qseq[q][cell]) != h + 1) {
+            if ((++spins & 1023u) == 0) {
+              if (ld_volatile(&rs->abort)) return kExit;
+              if (watchdog_expired(g)) {
+                set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+                return kExit;
+              }
+            }
+          }
+          __threadfence();
+          const uint32_t v = ld_volatile(&g.queue[q][cell]);
+          __threadfence();
+          *(volatile uint32_t*)&g.qseq[q][cell] = h + g.qcap;
+          return v;
+        }
+        h = prev;
+        t = ld_volatile(&rs->tail[q].v);
+      }
+    }
+    const uint32_t stail = g.ctl->sub_tail;
+    const uint32_t shead = ld_volatile(&rs->sub_head.v);
+    if ((int32_t)(stail - shead) > 0) {
+      if (atomicCAS(&rs->sub_head.v, shead, shead + 1) == shead) {
+        const volatile uint32_t* src = (const volatile uint32_t*)&g.ctl->ring[shead % kSubRing];
+        uint32_t* dst = (uint32_t*)sub;
+        for (int i = 0; i < (int)(sizeof(SubEntry) / 4); ++i) dst[i] = src[i];
+        atomicAdd(&rs->live.v, 1u);
+        touch_progress(g);
+        return kSubmit;
+      }
+      continue;
+    }
+    ++empties;
+    const uint32_t live = ld_volatile(&rs->live.v);
+    if (live == 0) {
+      if (g.ctl->shutdown) return kExit;
+      const unsigned long long now = globaltimer();
+      if (!idle_start) idle_start = now;
+      else if (now - idle_start > g.idle_ns) return kExit;
+    } else {
+      idle_start = 0;
+      if ((++iter & 63u) == 0 && watchdog_expired(g)) {
+        set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+        return kExit;
+      }
+    }
+    __nanosleep(backoff);
+    if (backoff < 2048) backoff <<= 1;
+  }
+}
+
+// Derive the DAG of a claimed request with this CTA, set up its tasks and
+// push its ready ones.  All threads.
+__device__ void server_admit(const DevGraph& g, const SubEntry& e, uint32_t* sh) {
+  DevGraph v = g;
+  v.ntasks = e.ntasks;
+  v.ntiles = e.ntiles;
+  v.nrec = e.nrec;
+  v.ecap = e.ecap;
+  v.tasks = g.tasks + e.tb;
+  v.tiles = g.tiles + e.hb;
+  v.rec_handle = g.rec_handle + e.rb;
+  v.rec_seq = g.rec_seq + e.rb;
+  v.rec_mode = g.rec_mode + e.rb;
+  v.task_rec = g.task_rec + e.tb;
+  v.hptr = g.hptr + e.hb;
+  v.s_task = g.s_task + e.rb;
+  v.s_mode = g.s_mode + e.rb;
+  v.s_first = g.s_first + e.rb;
+  v.rec_pos = g.rec_pos + e.rb;
+  v.gid = g.gid + e.rb;
+  v.gpos = g.gpos + e.rb;
+  v.row_ptr = g.row_ptr + e.tb;
+  v.col = g.col + e.eb;
+  v.indeg = g.indeg + e.tb;
+  const bool ok = derive_dag<kThreads>(v, sh);
+  const int tid = threadIdx.x;
+  for (uint32_t u = tid; u < e.ntasks; u += kThreads) {
+    const uint32_t gu = e.tb + u;
+    g.indeg_w[gu] = g.indeg[gu];
+    g.remaining[gu] = g.tasks[gu].nparts;
+    g.phase[gu] = 0;
+    g.task_req[gu] = e.slot;
+    g.t_start[gu] = 0xFFFFFFFFu;
+    g.t_end[gu] = 0;
+  }
+  if (tid == 0) {
+    ReqDev& r = g.reqs[e.slot];
+    r.tb = e.tb; r.ntasks = e.ntasks; r.hb = e.hb; r.ntiles = e.ntiles;
+    r.rb = e.rb; r.nrec = e.nrec; r.eb = e.eb; r.ecap = e.ecap;
+    r.remaining = e.ntasks;
+    r.status = ok ? 0u : (uint32_t)SPX_ERR_QUEUE_FULL;
+    r.info = 0;
+    r.seq = e.seq;
+  }
+  __threadfence();
+  __syncthreads();
+  for (uint32_t u = tid; u < e.ntasks; u += kThreads) {
+    const uint32_t gu = e.tb + u;
+    if (g.indeg[gu] == 0) ring_push_task(g, gu, g.tasks[gu].nparts, g.tasks[gu].prio);
+  }
+  __syncthreads();
+}
+
+// Release the successors of a finished pool task u of request slot r
+// (warp 0): request-local successor ids are offset by the request's task base.
+__device__ void release_server(const DevGraph& g, uint32_t u, uint32_t r) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t tb = g.reqs[r].tb, eb = g.reqs[r].eb;
+  const uint32_t r0 = g.row_ptr[u], r1 = g.row_ptr[u + 1];
+  for (uint32_t base = r0; base < r1; base += 32) {
+    const uint32_t idx = base + lane;
+    if (idx < r1) {
+      const uint32_t s = tb + g.col[eb + idx];
+      if (atomicSub(&g.indeg_w[s], 1u) == 1u) {
+        __threadfence();
+        ring_push_task(g, s, g.tasks[s].nparts, g.tasks[s].prio);
+      }
+    }
+  }
+}
+
+// Last task of request r finished: publish its status to the host.
+__device__ void finish_request(const DevGraph& g, uint32_t r) {
+  const ReqDev& q = g.reqs[r];
+  g.ctl->done_status[r] = (int32_t)ld_volatile(&q.status);
+  g.ctl->done_info[r] = q.info;
+  __threadfence_system();
+  g.ctl->done_seq[r] = q.seq;
+  __threadfence_system();
+  atomicSub(&g.rs->live.v, 1u);
+}
+
+template <bool kTc, bool kServer>
 __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the tensor-core instance aligns its operand stages to 1024 bytes; they
@@ -328,6 +516,8 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   }
   __shared__ uint32_t s_item, s_np;
   __shared__ int s_flag;
+  __shared__ SubEntry s_sub;
+  __shared__ uint32_t s_scan[kThreads / 32 + 1];
   const int tid = threadIdx.x;
   RunState* rs = g.rs;
   const long long c_begin = clock64();
@@ -336,14 +526,23 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   if (tid == 0) touch_progress(g);
 
   for (;;) {
-    if (tid == 0) s_item = pop(g, empties);
+    if (tid == 0) s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties);
     __syncthreads();
     const uint32_t item = s_item;
     if (item == kExit) break;
+    if constexpr (kServer) {
+      if (item == kSubmit) {
+        server_admit(g, s_sub, s_scan);
+        continue;
+      }
+    }
     const uint32_t u = item >> kPartBits, part = item & (kMaxParts - 1);
     const TaskDesc t = g.tasks[u];
     // the phase was written before its parts were pushed (and fenced)
     const uint32_t phase = t.nphases > 1 ? ld_volatile(&g.phase[u]) : 0u;
+    const uint32_t req = kServer ? g.task_req[u] : 0u;
+    // a request whose task failed drains without running its other tasks
+    const bool skip = kServer && ld_volatile(&g.reqs[req].status) != 0u;
     const long long c0 = clock64();
     if (tid == 0) {
       s_flag = 1;
@@ -358,11 +557,16 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (!s_flag) break;
-    const int info = run_part<kTc>(g, t, phase, part, s, tc);
+    const int info = skip ? 0 : run_part<kTc>(g, t, phase, part, s, tc);
     __syncthreads();
     busy += clock64() - c0;
     if (tid == 0) {
-      if (info > 0) {
+      if (info > 0 && kServer) {
+        // the request fails; the server and the other requests go on
+        if (atomicCAS(&g.reqs[req].status, 0u, (uint32_t)SPX_NOT_SPD) == 0u)
+          g.reqs[req].info = (int)t.arg + info;
+      }
+      if (info > 0 && !kServer) {
         set_error(rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
         s_flag = 0;
       } else if (info < 0) {
@@ -389,16 +593,29 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (s_flag == 0) break;
-    if (s_flag == 3 && tid < 32) push_phase(g, u, s_np, t.prio);
-    if (s_flag == 2) {
-      if (tid < 32) {
-        if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
-        __syncwarp();
-        release(g, u);
+    if constexpr (kServer) {
+      if (s_flag == 3 && tid == 0) ring_push_task(g, u, s_np, t.prio);
+      if (s_flag == 2 && tid < 32) {
+        release_server(g, u, req);
         __syncwarp();
         if (tid == 0) {
           __threadfence();
           atomicAdd(&rs->done.v, 1u);
+          if (atomicSub(&g.reqs[req].remaining, 1u) == 1u) finish_request(g, req);
+        }
+      }
+    } else {
+      if (s_flag == 3 && tid < 32) push_phase(g, u, s_np, t.prio);
+      if (s_flag == 2) {
+        if (tid < 32) {
+          if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
+          __syncwarp();
+          release(g, u);
+          __syncwarp();
+          if (tid == 0) {
+            __threadfence();
+            atomicAdd(&rs->done.v, 1u);
+          }
         }
       }
     }
@@ -452,12 +669,14 @@ constexpr size_t smem_bytes(bool tc) {
 
 template <bool kTc>
 void configure() {
-  cudaFuncSetAttribute(persistent_kernel<kTc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(persistent_kernel<kTc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes(kTc));
+  cudaFuncSetAttribute(persistent_kernel<kTc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem_bytes(kTc));
   cudaFuncSetAttribute(task_kernel<kTc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem_bytes(kTc));
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc>, kThreads,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc, false>, kThreads,
                                                 smem_bytes(kTc));
   g_max_ctas_per_sm[kTc ? 1 : 0] = occ > 0 ? occ : 1;
 }
@@ -483,8 +702,30 @@ cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStre
   const int maxc = g_sms * g_max_ctas_per_sm[tc ? 1 : 0];
   int n = num_ctas > 0 ? num_ctas : maxc;
   if (n > maxc) n = maxc;  // every CTA resident: no CTA waits behind a spinning one
-  if (tc) persistent_kernel<true><<<n, kThreads, smem_bytes(true), st>>>(g);
-  else persistent_kernel<false><<<n, kThreads, smem_bytes(false), st>>>(g);
+  if (tc) persistent_kernel<true, false><<<n, kThreads, smem_bytes(true), st>>>(g);
+  else persistent_kernel<false, false><<<n, kThreads, smem_bytes(false), st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st) {
+  persistent_max_ctas(nullptr);
+  const int maxc = g_sms * g_max_ctas_per_sm[tc ? 1 : 0];
+  int n = num_ctas > 0 ? num_ctas : maxc;
+  if (n > maxc) n = maxc;
+  if (tc) persistent_kernel<true, true><<<n, kThreads, smem_bytes(true), st>>>(g);
+  else persistent_kernel<false, true><<<n, kThreads, smem_bytes(false), st>>>(g);
+  return cudaGetLastError();
+}
+
+__global__ void ring_init_kernel(uint32_t* s0, uint32_t* s1, uint32_t cap) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+    s0[i] = i;
+    s1[i] = i;
+  }
+}
+
+cudaError_t launch_ring_init(const DevGraph& g, cudaStream_t st) {
+  ring_init_kernel<<<256, 256, 0, st>>>(g.qseq[0], g.qseq[1], g.qcap);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,48 @@ struct TaskDesc {
 };
 static_assert(sizeof(TaskDesc) == 32, "TaskDesc layout");
 
+// ---------------------------------------------------------------------------
+// Server mode (continuous batching): one resident persistent kernel, task
+// graphs submitted while it runs.  Each submitted graph (a request) gets
+// ranges of pool arrays; its CSR keeps request-local task ids and edge
+// offsets, mapped to pool ids at release.
+// ---------------------------------------------------------------------------
+constexpr int kSubRing = 1024;      // submission ring entries (host-mapped)
+constexpr int kMaxRequests = 1024;  // request slots
+
+// One submission (host -> device), written to host-mapped memory.
+struct SubEntry {
+  uint32_t seq, slot;
+  uint32_t tb, ntasks;  // task range [tb, tb + ntasks] (ntasks + 1 entries)
+  uint32_t hb, ntiles;  // tile range (ntiles + 1 entries)
+  uint32_t rb, nrec;    // access-record range (nrec + 1 entries)
+  uint32_t eb, ecap;    // edge range
+  uint32_t pad[6];
+};
+static_assert(sizeof(SubEntry) == 64, "SubEntry layout");
+
+// Host-mapped control block of a server.
+struct HostCtl {
+  volatile uint32_t sub_tail;   // submissions published by the host
+  volatile uint32_t shutdown;   // 1: exit once no request is live
+  uint32_t pad0[30];
+  SubEntry ring[kSubRing];
+  volatile uint32_t done_seq[kMaxRequests];   // seq of the finished request in a slot
+  volatile int32_t done_status[kMaxRequests];
+  volatile int32_t done_info[kMaxRequests];
+};
+
+// Device record of a live request.
+struct ReqDev {
+  uint32_t tb, ntasks, hb, ntiles, rb, nrec, eb, ecap;
+  uint32_t remaining;  // tasks not finished
+  uint32_t status;     // 0, or the first failure of one of its tasks
+  uint32_t seq;
+  int32_t info;
+  uint32_t pad[4];
+};
+static_assert(sizeof(ReqDev) == 64, "ReqDev layout");
+
 // Run state of one execution; hot counters on separate 128-byte lines.
 struct alignas(128) Line {
   uint32_t v;
@@ -60,6 +102,8 @@ struct RunState {
   Line done;             // finished tasks
   Line ticket;           // global ticket counter
   Line progress;         // %globaltimer >> 10 at the last finished part
+  Line sub_head;         // server: submissions claimed by the device
+  Line live;             // server: requests claimed and not finished
   // control words, read by every popping CTA
   alignas(128) uint32_t status;  // SPX_OK or an error / SPX_NOT_SPD
   int32_t info;          // failed POTRF column (1-based)
@@ -111,6 +155,14 @@ struct DevGraph {
   uint32_t* t_end;             // [ntasks]
   unsigned long long* trace_rec;  // [4*ntasks] when trace
   RunState* rs;
+  // server mode only (server = 1): ring queues, requests, host control
+  uint32_t server;
+  uint32_t pad_;
+  unsigned long long idle_ns;  // exit after this long with nothing live
+  uint32_t* qseq[2];           // [qcap] ring cell sequence numbers
+  uint32_t* task_req;          // [pool tasks] request slot of a task
+  ReqDev* reqs;                // [kMaxRequests]
+  HostCtl* ctl;                // device address of the host-mapped block
 };
 
 
@@ -185,6 +237,8 @@ cudaError_t launch_init(const DevGraph& g, cudaStream_t st);  // reset run state
 cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
 cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
                             const TileDesc* host_tiles, bool tc, cudaStream_t st);
+cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
+cudaError_t launch_ring_init(const DevGraph& g, cudaStream_t st);
 int persistent_max_ctas(int* per_sm);
 size_t persistent_smem_bytes();
 

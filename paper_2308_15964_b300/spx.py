@@ -75,6 +75,13 @@ def _load():
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),
         "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
+        "spx_server_config_default": (None, [P]),
+        "spx_server_create": (I, [P, P]),
+        "spx_server_submit": (I, [P, P, P]),
+        "spx_server_poll": (I, [P, ULL, P, P]),
+        "spx_server_stop": (I, [P]),
+        "spx_server_stats": (I, [P, P, I]),
+        "spx_server_destroy": (None, [P]),
         "spx_graph_derive_noalloc": (I, [P, P, P, P, I, I, LL, P, P, LL, P, P, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),
@@ -242,6 +249,69 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_tasks", ctypes.c_longlong), ("max_tiles", ctypes.c_longlong),
+                ("max_records", ctypes.c_longlong), ("max_edges", ctypes.c_longlong),
+                ("max_maps", ctypes.c_longlong), ("queue_capacity", ctypes.c_longlong),
+                ("num_ctas", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("watchdog_ns", ctypes.c_ulonglong), ("idle_ns", ctypes.c_ulonglong)]
+
+
+class Server:
+    """Continuous-batching server (spx_server_t): one resident persistent
+    kernel; graphs submitted while it runs are admitted and interleaved."""
+
+    def __init__(self, **kw):
+        cfg = ServerConfig()
+        lib.spx_server_config_default(ctypes.byref(cfg))
+        for k, v in kw.items():
+            setattr(cfg, k, int(v))
+        h = ctypes.c_void_p()
+        _check(lib.spx_server_create(ctypes.byref(h), ctypes.byref(cfg)), "spx_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, g: "Graph"):
+        """Request id, or None when the server has no room now (retry later)."""
+        rid = ctypes.c_ulonglong()
+        rc = lib.spx_server_submit(self._h, g._h, ctypes.byref(rid))
+        if rc == ERR_OOM:
+            return None
+        _check(rc, "spx_server_submit")
+        self._keep[rid.value] = list(g._keep)
+        return rid.value
+
+    def poll(self, rid: int):
+        """None while running, else (status, info)."""
+        st, info = ctypes.c_int(), ctypes.c_int()
+        rc = _check(lib.spx_server_poll(self._h, rid, ctypes.byref(st), ctypes.byref(info)),
+                    "spx_server_poll")
+        if rc == 0:
+            return None
+        self._keep.pop(rid, None)
+        return st.value, info.value
+
+    def stop(self) -> int:
+        return lib.spx_server_stop(self._h)
+
+    def stats(self):
+        v = np.zeros(6, np.int64)
+        _check(lib.spx_server_stats(self._h, _ptr(v), 6), "spx_server_stats")
+        return dict(zip(["parts", "tasks", "requests", "live", "busy_cycles", "total_cycles"],
+                        (int(x) for x in v)))
+
+    def close(self):
+        if self._h:
+            lib.spx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def probe(which: int, iters: int):
