@@ -60,10 +60,13 @@ __device__ __forceinline__ void set_error(RunState* rs, uint32_t code, int info)
   atomicExch(&rs->abort, 1u);
 }
 
+// Expired when the last finished part is older than the watchdog.  The stamp
+// may come from another SM whose %globaltimer reading is slightly ahead of
+// ours, so the difference is signed (a negative age is not a stall).
 __device__ __forceinline__ bool watchdog_expired(const DevGraph& g) {
   const uint32_t last = ld_volatile(&g.rs->progress.v);
   const uint32_t now = (uint32_t)(globaltimer() >> 10);  // ~1 us units
-  return (uint32_t)(now - last) > (uint32_t)(g.watchdog_ns >> 10);
+  return (int32_t)(now - last) > (int32_t)(g.watchdog_ns >> 10);
 }
 
 __device__ __forceinline__ void touch_progress(const DevGraph& g) {
