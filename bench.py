@@ -53,9 +53,11 @@ def parse():
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
-    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed"],
+    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
+    p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
+    p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     return p.parse_args()
 
 
@@ -184,6 +186,9 @@ def main():
     if args.workload == "mixed":
         run_mixed(args, world, rank, local)
         return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local)
+        return
 
     n, b = args.n, args.tile
     flops = cholesky.cholesky_flops(n)
@@ -310,6 +315,26 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_serve(args, world, rank, local):
+    """Serving: Poisson stream (seeded) of Cholesky-solve requests, n log-uniform
+    in [64, 16384], 1..64 RHS, FP64 or TF32 + 4 FP64 refinement sweeps,
+    admitted under a 120 GB HBM budget into one resident server kernel."""
+    from paper_2308_15964_b300 import serve
+    with Clocks(local) as clk:
+        out = serve.serve(rate=args.rate, duration=args.duration, budget=120e9, seed=6 + rank,
+                          drain=False, max_wall=args.duration + 120)
+    res = {"metric": METRIC, "value": out["gflops"], "unit": "GFLOP/s", "n_gpus": world,
+           "steps": 1, "warmup": 0, "ms_per_step": out["wall_s"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 / tf32+f64 refinement",
+           "data": "synthetic",
+           "config": {"workload": f"serving: Poisson {args.rate}/s for {args.duration} s, n log-uniform "
+                                  "64..16384, 1..64 RHS, 50% TF32+refinement, 120 GB budget",
+                      "rate": args.rate, "duration_s": args.duration},
+           "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "serve": out, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(res))
 
 
 def run_mixed(args, world, rank, local):

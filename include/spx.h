@@ -65,6 +65,8 @@ enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
  *   SPX_OP_GEMM_BWD     (L_ki:R, X_k:R, X_i:W)  X_i <- X_i - L_ki^T X_k
  *   SPX_OP_NOP          any handles, any modes  does nothing (graph tests)
  *   SPX_OP_SPIN         any handles, any modes  busy-waits arg nanoseconds
+ *   SPX_OP_COPY         (X:R, Y:W)              Y <- X (same shape)
+ *   SPX_OP_AXPY         (X:R, Y:W)              Y <- Y + X (same shape)
  * A write operand may also be given as SPX_COMMUTATIVE_WRITE; such tasks
  * run as one part and take per-tile locks in ascending handle order (the
  * paper locks data handles sorted by address, section "Internal
@@ -81,7 +83,9 @@ enum {
   SPX_OP_GEMM_BWD = 8,
   SPX_OP_NOP = 9,
   SPX_OP_SPIN = 10,
-  SPX_NUM_OPS = 11
+  SPX_OP_COPY = 11,
+  SPX_OP_AXPY = 12,
+  SPX_NUM_OPS = 13
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
@@ -295,6 +299,16 @@ int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int 
 int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b, double* dev_X, int nrhs,
                      int ldx, long long* out_ntasks);
 
+/* Insert `sweeps` FP64 iterative-refinement sweeps as tasks (so that they run
+ * inside the same graph, e.g. in the server): each sweep is
+ *   R_i <- B_i (COPY);  R_i <- R_i - A0_ij X_j for all i, j (GEMM_FWD);
+ *   L L^T D = R by the block solves (D over R);  X_i <- X_i + R_i (AXPY).
+ * A0: n x n original matrix in full (lda); L: the factor (lower triangle of
+ * dev_L, ldl); B, X, R: n x nrhs (ldx).  X holds the current solution. */
+int spx_refine_insert(spx_graph_t g, double* dev_A0, int n, int lda, double* dev_L, int ldl, int b,
+                      double* dev_B, double* dev_X, double* dev_R, int nrhs, int ldx, int sweeps,
+                      long long* out_ntasks);
+
 /* Insert the tiled GEMM C += A B of the paper's numerical applications: one
  * GEMM_NN_ADD task per (i, j, k), i and j outer, k inner, each with a WRITE
  * (or, with commutative = 1, a COMMUTATIVE_WRITE) on the block C_ij.  A, B, C
@@ -437,6 +451,12 @@ int spx_server_stop(spx_server_t s);
 int spx_server_stats(spx_server_t s, long long* out, int n);
 
 void spx_server_destroy(spx_server_t s);
+
+/* Strided 2-D copy by the copy engines (cudaMemcpy2DAsync, any direction):
+ * rows x width_bytes from src (row pitch spitch) to dst (dpitch).  Used to
+ * stage request inputs while a resident server kernel holds every SM. */
+int spx_copy2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width_bytes,
+               size_t rows, void* stream);
 
 /* Static description of a status code. */
 const char* spx_strerror(int code);

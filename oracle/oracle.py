@@ -27,7 +27,7 @@ SRC = os.path.join(HERE, "spx_oracle.cpp")
 
 READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
 (POTRF, TRSM, SYRK, GEMM_NT_SUB, GEMM_NN_ADD, TRSM_L_FWD, GEMM_FWD,
- TRSM_LT_BWD, GEMM_BWD, NOP, SPIN) = range(11)
+ TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY) = range(13)
 
 
 def build(force: bool = False) -> str:

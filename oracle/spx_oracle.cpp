@@ -62,7 +62,9 @@ enum {
   O_TRSM_LT_BWD = 7,  // X_k <- L_kk^{-T} X_k
   O_GEMM_BWD = 8,     // X_i <- X_i - L_ki^T X_k
   O_NOP = 9,
-  O_SPIN = 10
+  O_SPIN = 10,
+  O_COPY = 11,        // Y <- X
+  O_AXPY = 12         // Y <- Y + X
 };
 
 // ---------------------------------------------------------------------------
@@ -352,6 +354,18 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
         const spxo_tile& Xk = tile(1);
         const spxo_tile& Xi = tile(2);
         gemm_bwd(L.ptr, L.ld, Xk.ptr, Xk.ld, Xi.ptr, Xi.ld, Xi.rows, L.rows, Xi.cols);
+        break;
+      }
+      case O_COPY:
+      case O_AXPY: {
+        const spxo_tile& X = tile(0);
+        const spxo_tile& Y = tile(1);
+        for (int r = 0; r < Y.rows; ++r)
+          for (int c = 0; c < Y.cols; ++c) {
+            const double v = X.ptr[(size_t)r * X.ld + c];
+            double& y = Y.ptr[(size_t)r * Y.ld + c];
+            y = task_op[t] == O_AXPY ? y + v : v;
+          }
         break;
       }
       case O_NOP:

@@ -237,6 +237,10 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_GEMM_BWD:
       op_gemm<true, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].rows, -1.0, u0, u1, s);
       return 0;
+    case SPX_OP_COPY:
+    case SPX_OP_AXPY:
+      op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY);
+      return 0;
     case SPX_OP_NOP:
       return 0;
     case SPX_OP_SPIN:

@@ -149,3 +149,12 @@ extern "C" int spx_axpy_f64(double* dev_Y, const double* dev_X, long long count,
   axpy_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(dev_Y, dev_X, count, alpha);
   return cudaGetLastError() == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
 }
+
+extern "C" int spx_copy2d(void* dst, size_t dpitch, const void* src, size_t spitch,
+                          size_t width_bytes, size_t rows, void* stream) {
+  if (!dst || !src || dpitch < width_bytes || spitch < width_bytes) return SPX_ERR_INVALID_ARG;
+  if (!rows || !width_bytes) return SPX_OK;
+  const cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, width_bytes, rows,
+                                          cudaMemcpyDefault, (cudaStream_t)stream);
+  return e == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
+}

@@ -223,6 +223,8 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     case SPX_OP_GEMM_BWD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return cdiv64(t[h[1]].cols);
+    case SPX_OP_COPY:
+    case SPX_OP_AXPY: return cdiv64(t[h[1]].rows);
     default: return 1;
   }
 }

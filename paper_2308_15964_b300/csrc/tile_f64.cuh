@@ -364,4 +364,20 @@ __device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0,
   }
 }
 
+// Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1.
+__device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
+                             bool axpy) {
+  const double* x = (const double*)Xt.ptr;
+  double* y = (double*)Yt.ptr;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)u * kBlk, mb = min(kBlk, Yt.rows - r0);
+    for (int e = threadIdx.x; e < mb * Yt.cols; e += kThreads) {
+      const int r = r0 + e / Yt.cols, c = e % Yt.cols;
+      const double v = __ldcg(x + (size_t)r * Xt.ld + c);
+      double* py = y + (size_t)r * Yt.ld + c;
+      *py = axpy ? __ldcg(py) + v : v;
+    }
+  }
+}
+
 }  // namespace spx

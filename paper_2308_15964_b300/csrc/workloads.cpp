@@ -169,3 +169,53 @@ extern "C" int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const
   if (out_ntasks) *out_ntasks = total;
   return rc;
 }
+
+extern "C" int spx_refine_insert(spx_graph_t g, double* dev_A0, int n, int lda, double* dev_L,
+                                 int ldl, int b, double* dev_B, double* dev_X, double* dev_R,
+                                 int nrhs, int ldx, int sweeps, long long* out_ntasks) {
+  if (!g || !dev_A0 || !dev_L || !dev_B || !dev_X || !dev_R || n < 1 || b < 1 || lda < n ||
+      ldl < n || nrhs < 1 || ldx < nrhs || sweeps < 0)
+    return SPX_ERR_INVALID_ARG;
+  Tiles A0, L;
+  int rc = register_tiles(g, dev_A0, n, n, lda, b, false, A0);
+  if (rc == SPX_OK) rc = register_tiles(g, dev_L, n, n, ldl, b, true, L);
+  if (rc != SPX_OK) return rc;
+  const int T = A0.T;
+  std::vector<unsigned> xb(T), xx(T), xr(T);
+  for (int i = 0; i < T && rc == SPX_OK; ++i) {
+    const int r = n - i * b < b ? n - i * b : b;
+    const size_t off = (size_t)i * b * ldx;
+    rc = spx_tile_register(g, dev_B + off, r, nrhs, ldx, SPX_DT_F64, nullptr, 0, &xb[i]);
+    if (rc == SPX_OK) rc = spx_tile_register(g, dev_X + off, r, nrhs, ldx, SPX_DT_F64, nullptr, 0, &xx[i]);
+    if (rc == SPX_OK) rc = spx_tile_register(g, dev_R + off, r, nrhs, ldx, SPX_DT_F64, nullptr, 0, &xr[i]);
+  }
+  const int R = SPX_READ, W = SPX_WRITE;
+  long long count = 0;
+  auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms, int prio) {
+    int r = spx_task_insert(g, op, hs.begin(), ms.begin(), (int)hs.size(), prio, SPX_F64, nullptr);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  for (int sw = 0; sw < sweeps && rc == SPX_OK; ++sw) {
+    // r = b - A0 x
+    for (int i = 0; i < T && rc == SPX_OK; ++i) rc = ins(SPX_OP_COPY, {xb[i], xr[i]}, {R, W}, 0);
+    for (int i = 0; i < T && rc == SPX_OK; ++i)
+      for (int j = 0; j < T && rc == SPX_OK; ++j)
+        rc = ins(SPX_OP_GEMM_FWD, {A0.at(i, j), xx[j], xr[i]}, {R, R, W}, 0);
+    // L L^T d = r, d over r
+    for (int k = 0; k < T && rc == SPX_OK; ++k) {
+      rc = ins(SPX_OP_TRSM_L_FWD, {L.at(k, k), xr[k]}, {R, W}, 1);
+      for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_GEMM_FWD, {L.at(i, k), xr[k], xr[i]}, {R, R, W}, 0);
+    }
+    for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
+      rc = ins(SPX_OP_TRSM_LT_BWD, {L.at(k, k), xr[k]}, {R, W}, 1);
+      for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
+        rc = ins(SPX_OP_GEMM_BWD, {L.at(k, i), xr[k], xr[i]}, {R, R, W}, 0);
+    }
+    // x += d
+    for (int i = 0; i < T && rc == SPX_OK; ++i) rc = ins(SPX_OP_AXPY, {xr[i], xx[i]}, {R, W}, 0);
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 
 READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
- OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN) = range(11)
+ OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY) = range(13)
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK = 0, 1
@@ -82,6 +82,8 @@ def _load():
         "spx_server_stop": (I, [P]),
         "spx_server_stats": (I, [P, P, I]),
         "spx_server_destroy": (None, [P]),
+        "spx_refine_insert": (I, [P, P, I, I, P, I, I, P, P, P, I, I, I, P]),
+        "spx_copy2d": (I, [P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_size_t, P]),
         "spx_graph_derive_noalloc": (I, [P, P, P, P, I, I, LL, P, P, LL, P, P, P]),
         "spx_abi_version": (I, []),
         "spx_probe": (I, [I, I, P, P]),

@@ -98,3 +98,28 @@ def test_residual_kernel_vs_oracle(S):
     assert np.array_equal(nv[2 * nrhs:], np.abs(B.numpy()).max(0))
     an = mixed.norm_inf(Ad).item()
     assert abs(an - np.abs(A.numpy()).sum(1).max()) <= 1e-12 * an
+
+
+def test_refinement_sweeps_as_tasks(S):
+    """Refinement sweeps inserted as graph tasks (COPY, GEMM_FWD with the
+    original matrix, block solves, AXPY) after the mixed factorization."""
+    import ctypes
+    from paper_2308_15964_b300 import mixed
+    n, b, nrhs = 1024, 256, 3
+    A = inputs.spd_matrix(n, 1.0, seed=12)
+    B = inputs.rhs(n, nrhs, seed=12)
+    Ad, A0, Bd = A.cuda(), A.cuda(), B.cuda()
+    X, R = Bd.clone(), torch.empty_like(Bd)
+    Alo = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    g = S.Graph()
+    mixed.factor_graph(g, Ad, Alo, b, X, S.TF32)
+    P = ctypes.c_void_p
+    nt = ctypes.c_longlong()
+    assert S.lib.spx_refine_insert(g._h, P(A0.data_ptr()), n, n, P(Ad.data_ptr()), n, b,
+                                   P(Bd.data_ptr()), P(X.data_ptr()), P(R.data_ptr()), nrhs, nrhs, 4,
+                                   ctypes.byref(nt)) == 0
+    rc, _ = g.run()
+    assert rc == 0
+    eta = O.solve_backward_error(A.numpy(), X.cpu().numpy(), B.numpy())
+    assert eta.max() <= 1e-14, eta
+    g.close()
