@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
-    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve"],
+    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve", "tc"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -189,6 +189,9 @@ def main():
     if args.workload == "serve":
         run_serve(args, world, rank, local)
         return
+    if args.workload == "tc":
+        run_tc(args, world, rank, local)
+        return
 
     n, b = args.n, args.tile
     flops = cholesky.cholesky_flops(n)
@@ -315,6 +318,53 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_tc(args, world, rank, local):
+    """Stand-alone tensor-core tile update C (FP64, m x m) -= A B^T with BF16 and
+    TF32 operands (m x K): the trailing-update kernel of the mixed path."""
+    import ctypes
+    import torch
+    from paper_2308_15964_b300 import spx
+    m, K = args.n if args.n != 16384 else 8192, args.tile if args.tile != 512 else 1024
+    C = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = {"metric": METRIC, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic", "config": {"workload": f"tensor-core tile update C(fp64 {m}x{m}) -= "
+                                                       f"A({m}x{K}) B({m}x{K})^T", "m": m, "K": K}}
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    P = ctypes.c_void_p
+    st = torch.cuda.current_stream()
+    for name, prec, dt in (("bf16", spx.BF16, torch.bfloat16), ("tf32", spx.TF32, torch.float32)):
+        A = (torch.rand((m, K), device="cuda") * 2 - 1).to(dt)
+        B = (torch.rand((m, K), device="cuda") * 2 - 1).to(dt)
+        call = lambda: spx.lib.spx_tc_gemm_nt(P(C.data_ptr()), m, m, m, P(A.data_ptr()), K,
+                                              P(B.data_ptr()), K, K, prec, P(err.data_ptr()),
+                                              P(st.cuda_stream))
+        for _ in range(args.warmup):
+            call()
+        ev[0].record()
+        for _ in range(args.steps):
+            call()
+        ev[1].record()
+        ev[1].synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        flops = 2.0 * m * m * K
+        bytes_ = 16.0 * m * m + 2 * m * K * A.element_size()
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "gbs": bytes_ / ms / 1e6,
+                     "frac_hbm": bytes_ / ms / 1e6 / peaks.get("hbm_gbs", 6451.5),
+                     "frac_bf16_peak": flops / ms / 1e9 / peaks.get("bf16_tflops", 1736.0)}
+    assert int(err.item()) == 0
+    out["value"] = out["bf16"]["tflops"]
+    out["ms_per_step"] = out["bf16"]["ms"]
+    out["roofline"] = {"bound": "hbm", "achieved": out["bf16"]["gbs"], "peak": peaks.get("hbm_gbs", 6451.5),
+                       "unit": "GB/s", "frac": out["bf16"]["frac_hbm"], "traffic": None,
+                       "kernel": "tc_gemm_kernel<bf16>",
+                       "note": "algorithmic bytes: FP64 C read+write 16 m^2 + operands"}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_serve(args, world, rank, local):

@@ -40,15 +40,18 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 //   op(A)(i,k) = A_T ? A[k*lda + i] : A[i*lda + k]
 //   op(B)(k,j) = B_KN ? B[k*ldb + j] : B[j*ldb + k]
 // lower: only entries with column <= row are written (diagonal SYRK blocks).
-template <bool A_T, bool B_KN>
+// CJ: output columns per thread (4: a 64-column block; 1: at most 16 columns,
+// for the narrow right-hand-side blocks of the solves).
+template <bool A_T, bool B_KN, int CJ = 4>
 __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
                            int m, int n, int K, double alpha, bool lower, GemmSmem& s) {
+  constexpr int BN = 16 * CJ;  // columns of the block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[4][CJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < CJ; ++j) acc[i][j] = 0.0;
 
   for (int k0 = 0; k0 < K; k0 += kKC) {
 #pragma unroll
@@ -61,9 +64,9 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
       s.a[kk][i] = v;
     }
 #pragma unroll
-    for (int e = tid; e < kBlk * kKC; e += kThreads) {
+    for (int e = tid; e < BN * kKC; e += kThreads) {
       int j, kk;
-      if (B_KN) { kk = e / kBlk; j = e % kBlk; } else { j = e / kKC; kk = e % kKC; }
+      if (B_KN) { kk = e / BN; j = e % BN; } else { j = e / kKC; kk = e % kKC; }
       double v = 0.0;
       if (j < n && k0 + kk < K)
         v = ldcg(B_KN ? B + (size_t)(k0 + kk) * ldb + j : B + (size_t)j * ldb + k0 + kk);
@@ -72,15 +75,15 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kKC; ++kk) {
-      double av[4], bv[4];
+      double av[4], bv[CJ];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = s.a[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = s.b[kk][tx + 16 * j];
+      for (int j = 0; j < CJ; ++j) bv[j] = s.b[kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < CJ; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -88,7 +91,7 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
   for (int i = 0; i < 4; ++i) {
     const int r = ty + 16 * i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < CJ; ++j) {
       const int c = tx + 16 * j;
       if (r < m && c < n && (!lower || c <= r)) {
         double* p = C + (size_t)r * ldc + c;
@@ -311,8 +314,13 @@ __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& 
     const int r0 = (u / nbc) * kBlk, c0 = (u % nbc) * kBlk;
     const double* ap = A_T ? a + r0 : a + (size_t)r0 * At.ld;
     const double* bp = B_KN ? b + c0 : b + (size_t)c0 * Bt.ld;
-    gemm_block<A_T, B_KN>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
-                          min(kBlk, Ct.rows - r0), min(kBlk, Ct.cols - c0), K, alpha, false, s.gs);
+    const int nb = min(kBlk, Ct.cols - c0);
+    if (nb <= 16)
+      gemm_block<A_T, B_KN, 1>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
+                               min(kBlk, Ct.rows - r0), nb, K, alpha, false, s.gs);
+    else
+      gemm_block<A_T, B_KN>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
+                            min(kBlk, Ct.rows - r0), nb, K, alpha, false, s.gs);
   }
 }
 
@@ -326,7 +334,10 @@ __device__ void op_trsm_fwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0,
     const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
     for (int ib = 0; ib < n; ib += kBlk) {
       const int mb = min(kBlk, n - ib);
-      if (ib > 0)
+      if (ib > 0 && w <= 16)
+        gemm_block<false, true, 1>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)ib * ldl, ldl,
+                                   x + c0, ldx, mb, w, ib, -1.0, false, s.gs);
+      else if (ib > 0)
         gemm_block<false, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)ib * ldl, ldl, x + c0,
                                 ldx, mb, w, ib, -1.0, false, s.gs);
       load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
@@ -350,7 +361,12 @@ __device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0,
     const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
     for (int bi = nb - 1; bi >= 0; --bi) {
       const int ib = bi * kBlk, mb = min(kBlk, n - ib), below = n - ib - mb;
-      if (below > 0)
+      if (below > 0 && w <= 16)
+        gemm_block<true, true, 1>(x + (size_t)ib * ldx + c0, ldx,
+                                  l + (size_t)(ib + mb) * ldl + ib, ldl,
+                                  x + (size_t)(ib + mb) * ldx + c0, ldx, mb, w, below, -1.0,
+                                  false, s.gs);
+      else if (below > 0)
         gemm_block<true, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)(ib + mb) * ldl + ib,
                                ldl, x + (size_t)(ib + mb) * ldx + c0, ldx, mb, w, below, -1.0,
                                false, s.gs);
