@@ -14,7 +14,7 @@ namespace spx {
 namespace {
 
 template <bool kBf16>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                    double* C, int ldc, int m, int n, int K, int* err) {
   extern __shared__ __align__(16) uint8_t raw[];
@@ -57,7 +57,7 @@ extern "C" int spx_tc_gemm_nt(double* dev_C, int ldc, int m, int n, const void* 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int units = ((m + kTcM - 1) / kTcM) * ((n + kTcN - 1) / kTcN);
-  const int grid = units < sms ? units : sms;
+  const int grid = units < 2 * sms ? units : 2 * sms;  // two CTAs per SM
   const size_t smem = sizeof(TcBuf) + 1024;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == SPX_BF16) {

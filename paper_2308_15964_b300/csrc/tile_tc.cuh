@@ -196,6 +196,10 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   const int nchunks = (K + kChunk - 1) / kChunk;
   const int tid = threadIdx.x;
   const uint32_t tmem = s.tmem_base;
+  // the stages may hold generic-proxy writes (the previous epilogue, or an
+  // FP64 op's buffers that share this memory): order them before TMA writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
   if (tid == 0) {
     tc_fence_after();
     bool ok = true;
@@ -206,6 +210,7 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
       tma_load_2d(buf.a[c], amap, &s.full[c], ax0 + c * kChunk, ay);
       tma_load_2d(buf.b[c], bmap, &s.full[c], bx0 + c * kChunk, by);
     }
+    int waited = 0;  // chunks whose stage-free (empty) phase has been consumed
     for (int c = 0; c < nchunks && ok; ++c) {
       const int st = c % kTcStages;
       ok = mbar_wait(&s.full[st], (fph >> st) & 1u);
@@ -219,20 +224,25 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
                       (c > 0 || k > 0) ? 1u : 0u);
       }
       tc_commit(&s.empty[st]);
-      if (c + kTcStages < nchunks) {
-        ok = mbar_wait(&s.empty[st], (eph >> st) & 1u);
-        eph ^= 1u << st;
+      // refill the stage of the previous chunk (its MMAs were issued one
+      // step earlier) while this chunk's MMAs run
+      const int pc = c - 1;
+      if (pc >= 0 && pc + kTcStages < nchunks) {
+        const int ps = pc % kTcStages;
+        ok = mbar_wait(&s.empty[ps], (eph >> ps) & 1u);
+        eph ^= 1u << ps;
+        waited = pc + 1;
         if (!ok) break;
-        mbar_arrive_expect_tx(&s.full[st], 2 * kTcStageBytes);
-        tma_load_2d(buf.a[st], amap, &s.full[st], ax0 + (c + kTcStages) * kChunk, ay);
-        tma_load_2d(buf.b[st], bmap, &s.full[st], bx0 + (c + kTcStages) * kChunk, by);
+        mbar_arrive_expect_tx(&s.full[ps], 2 * kTcStageBytes);
+        tma_load_2d(buf.a[ps], amap, &s.full[ps], ax0 + (pc + kTcStages) * kChunk, ay);
+        tma_load_2d(buf.b[ps], bmap, &s.full[ps], bx0 + (pc + kTcStages) * kChunk, by);
       }
     }
     tc_commit(&s.done);
     if (ok) ok = mbar_wait(&s.done, s.done_phase & 1u);
     s.done_phase ^= 1u;
-    // consume the empty phases of the last chunks (no reload waited on them)
-    for (int c = nchunks > kTcStages ? nchunks - kTcStages : 0; c < nchunks && ok; ++c) {
+    // consume the stage-free phases not waited on above, in chunk order
+    for (int c = waited; c < nchunks && ok; ++c) {
       const int st = c % kTcStages;
       ok = mbar_wait(&s.empty[st], (eph >> st) & 1u);
       eph ^= 1u << st;
@@ -244,25 +254,37 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   __syncthreads();
   if (s.error) return false;
   tc_fence_after();
-  // epilogue: warp w reads TMEM lanes 32*(w%4).., columns 64*(w/4)..+64
+  // epilogue, 1: accumulator -> shared memory (the operand stages are free
+  // now).  Warp w reads TMEM lanes 32*(w%4).. (rows), columns 64*(w/4)..+64.
+  constexpr int kLde = kTcN + 1;
+  static_assert(sizeof(float) * kTcM * kLde <= sizeof(TcBuf), "epilogue staging fits the stages");
+  float* E = reinterpret_cast<float*>(&buf);
   const int warp = tid >> 5, lane = tid & 31;
-  const int row = 32 * (warp & 3) + lane;
-  const int col0 = 64 * (warp >> 2);
-  float v[32];
+  {
+    const int row = 32 * (warp & 3) + lane;
+    const int col0 = 64 * (warp >> 2);
+    float v[32];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int cb = col0 + 32 * h;
-    tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
-    if (row < m) {
-      double* cr = C + (size_t)row * ldc;
+    for (int h = 0; h < 2; ++h) {
+      const int cb = col0 + 32 * h;
+      tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = cb + j;
-        if (c < n && (!lower || c <= row)) cr[c] = __ldcg(cr + c) - (double)v[j];
-      }
+      for (int j = 0; j < 32; ++j) E[row * kLde + cb + j] = v[j];
     }
   }
   tc_fence_before();
+  __syncthreads();
+  // epilogue, 2: coalesced FP64 read-modify-write of the output block, one
+  // row per warp step, 4 consecutive columns per lane
+  for (int r = warp; r < m; r += kThreads / 32) {
+    double* cr = C + (size_t)r * ldc;
+    const float* er = E + r * kLde;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      if (c < n && (!lower || c <= r)) cr[c] = __ldcg(cr + c) - (double)er[c];
+    }
+  }
   __syncthreads();
   return true;
 }
