@@ -200,6 +200,15 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   // FP64 op's buffers that share this memory): order them before TMA writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
+  if (tid >= 32) {
+    // while thread 0 drives TMA and the MMAs, pull the FP64 output block
+    // into L2 for the epilogue (one prefetch per 128-byte line)
+    const int lines_per_row = (n * 8 + 127) / 128;
+    for (int e = tid - 32; e < m * lines_per_row; e += kThreads - 32) {
+      const int r = e / lines_per_row, l = e % lines_per_row;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)r * ldc + l * 16));
+    }
+  }
   if (tid == 0) {
     tc_fence_after();
     bool ok = true;
@@ -274,15 +283,28 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   }
   tc_fence_before();
   __syncthreads();
-  // epilogue, 2: coalesced FP64 read-modify-write of the output block, one
-  // row per warp step, 4 consecutive columns per lane
-  for (int r = warp; r < m; r += kThreads / 32) {
-    double* cr = C + (size_t)r * ldc;
-    const float* er = E + r * kLde;
+  // epilogue, 2: coalesced FP64 read-modify-write of the output block; each
+  // warp loads 8 rows (4 columns per lane each) before writing any of them
+  constexpr int kWarps = kThreads / 32;
+  for (int r0 = warp; r0 < m; r0 += 8 * kWarps) {
+    double cv[8][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = lane + 32 * q;
-      if (c < n && (!lower || c <= r)) cr[c] = __ldcg(cr + c) - (double)er[c];
+    for (int k = 0; k < 8; ++k) {
+      const int r = r0 + kWarps * k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = lane + 32 * q;
+        cv[k][q] = (r < m && c < n && (!lower || c <= r)) ? __ldcg(C + (size_t)r * ldc + c) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int r = r0 + kWarps * k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = lane + 32 * q;
+        if (r < m && c < n && (!lower || c <= r)) C[(size_t)r * ldc + c] = cv[k][q] - (double)E[r * kLde + c];
+      }
     }
   }
   __syncthreads();
