@@ -123,163 +123,78 @@ __device__ __forceinline__ void store_block(double* dst, int ld, const double (*
 // (lower).  Returns 0 or the 1-based local column of a pivot that is not > 0
 // (NaN included).  Every thread returns the same value.
 __device__ int potrf_smem(double (*a)[kLds], int w, int* s_info) {
-  // One warp factors the block (lane j owns rows j and j + 32); the other
-  // warps wait at the final barrier.  Same operations per element as a
-  // column-by-column right-looking Cholesky.
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int info = 0;
-    for (int j = 0; j < w; ++j) {
-      const double d = a[j][j];
-      if (!(d > 0.0)) {
-        info = j + 1;
-        break;
-      }
-      const double ljj = sqrt(d);
-      __syncwarp();
-      if (lane == 0) a[j][j] = ljj;
-      for (int r = lane; r < w; r += 32)
-        if (r > j) a[r][j] = a[r][j] / ljj;
-      __syncwarp();
-      for (int r = lane; r < w; r += 32) {
-        if (r <= j) continue;
-        const double arj = a[r][j];
-        for (int c = j + 1; c <= r; ++c) a[r][c] = fma(-arj, a[c][j], a[r][c]);
-      }
-      __syncwarp();
-    }
-    if (lane == 0) *s_info = info;
-  }
+  const int tid = threadIdx.x;
+  if (tid == 0) *s_info = 0;
   __syncthreads();
-  return *s_info;
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      const double d = a[j][j];
+      if (!(d > 0.0)) *s_info = j + 1;
+      else a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (*s_info) return *s_info;
+    const double ljj = a[j][j];
+    for (int i = j + 1 + tid; i < w; i += kThreads) a[i][j] = a[i][j] / ljj;
+    __syncthreads();
+    const int t = w - j - 1;  // trailing lower triangle, rows/cols j+1..w-1
+    for (int e = tid; e < t * t; e += kThreads) {
+      const int i = j + 1 + e / t, c = j + 1 + e % t;
+      if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+    }
+    __syncthreads();
+  }
+  return 0;
 }
 
-// The triangular solves below are warp-synchronous: each warp owns whole rows
-// (or right-hand-side columns), keeps them in registers (lane j holds
-// entries j and j + 32), and broadcasts each solved entry with a shuffle, so
-// a 64-step substitution costs no block barrier.  Every element sees the same
-// division and the same FMA sequence as a plain right-looking substitution.
-
-// X <- X L^{-T} for X (m x w) and L (w x w lower) in shared memory, m, w <= 64:
+// X <- X L^{-T} for X (m x w) and L (w x w lower) in shared memory:
 // x_rc = (x_rc - sum_{k<c} x_rk l_ck) / l_cc, right-looking over c.
 __device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
-  constexpr int kWarps = kThreads / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double v0[8], v1[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int r = warp + kWarps * k;
-    v0[k] = (r < m && lane < w) ? x[r][lane] : 0.0;
-    v1[k] = (r < m && lane + 32 < w) ? x[r][lane + 32] : 0.0;
-  }
+  const int tid = threadIdx.x;
   for (int c = 0; c < w; ++c) {
     const double lcc = l[c][c];
-    const int owner = c & 31;
-    const double l0 = lane > c ? l[lane][c] : 0.0;
-    const double l1 = lane + 32 > c && lane + 32 < w ? l[lane + 32][c] : 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      double xc;
-      if (c < 32) {
-        if (lane == owner) v0[k] = v0[k] / lcc;
-        xc = __shfl_sync(0xffffffffu, v0[k], owner);
-      } else {
-        if (lane == owner) v1[k] = v1[k] / lcc;
-        xc = __shfl_sync(0xffffffffu, v1[k], owner);
-      }
-      if (lane > c) v0[k] = fma(-xc, l0, v0[k]);
-      if (lane + 32 > c && lane + 32 < w) v1[k] = fma(-xc, l1, v1[k]);
+    for (int r = tid; r < m; r += kThreads) x[r][c] = x[r][c] / lcc;
+    __syncthreads();
+    const int t = w - c - 1;
+    for (int e = tid; e < m * t; e += kThreads) {
+      const int r = e / t, cc = c + 1 + e % t;
+      x[r][cc] = fma(-x[r][c], l[cc][c], x[r][cc]);
     }
+    __syncthreads();
   }
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int r = warp + kWarps * k;
-    if (r < m && lane < w) x[r][lane] = v0[k];
-    if (r < m && lane + 32 < w) x[r][lane + 32] = v1[k];
-  }
-  __syncthreads();
 }
 
 // X <- L^{-1} X for L (m x m lower) and X (m x w) in shared memory (forward
-// substitution on every column; warps own columns).
+// substitution on every column).
 __device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
-  constexpr int kWarps = kThreads / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c0 = warp; c0 < w; c0 += 2 * kWarps) {
-    const int cs[2] = {c0, c0 + kWarps};
-    double v0[2], v1[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      v0[k] = (cs[k] < w && lane < m) ? x[lane][cs[k]] : 0.0;
-      v1[k] = (cs[k] < w && lane + 32 < m) ? x[lane + 32][cs[k]] : 0.0;
+  const int tid = threadIdx.x;
+  for (int i = 0; i < m; ++i) {
+    const double lii = l[i][i];
+    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
+    __syncthreads();
+    const int t = m - i - 1;
+    for (int e = tid; e < t * w; e += kThreads) {
+      const int r = i + 1 + e / w, c = e % w;
+      x[r][c] = fma(-l[r][i], x[i][c], x[r][c]);
     }
-    for (int i = 0; i < m; ++i) {
-      const double lii = l[i][i];
-      const int owner = i & 31;
-      const double l0 = lane > i && lane < m ? l[lane][i] : 0.0;
-      const double l1 = lane + 32 > i && lane + 32 < m ? l[lane + 32][i] : 0.0;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        double xi;
-        if (i < 32) {
-          if (lane == owner) v0[k] = v0[k] / lii;
-          xi = __shfl_sync(0xffffffffu, v0[k], owner);
-        } else {
-          if (lane == owner) v1[k] = v1[k] / lii;
-          xi = __shfl_sync(0xffffffffu, v1[k], owner);
-        }
-        if (lane > i && lane < m) v0[k] = fma(-l0, xi, v0[k]);
-        if (lane + 32 > i && lane + 32 < m) v1[k] = fma(-l1, xi, v1[k]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (cs[k] < w && lane < m) x[lane][cs[k]] = v0[k];
-      if (cs[k] < w && lane + 32 < m) x[lane + 32][cs[k]] = v1[k];
-    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // X <- L^{-T} X for L (m x m lower) and X (m x w) in shared memory (back
-// substitution x_i = (x_i - sum_{k>i} l_ki x_k) / l_ii; warps own columns).
+// substitution: x_i = (x_i - sum_{k>i} l_ki x_k) / l_ii).
 __device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
-  constexpr int kWarps = kThreads / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c0 = warp; c0 < w; c0 += 2 * kWarps) {
-    const int cs[2] = {c0, c0 + kWarps};
-    double v0[2], v1[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      v0[k] = (cs[k] < w && lane < m) ? x[lane][cs[k]] : 0.0;
-      v1[k] = (cs[k] < w && lane + 32 < m) ? x[lane + 32][cs[k]] : 0.0;
+  const int tid = threadIdx.x;
+  for (int i = m - 1; i >= 0; --i) {
+    const double lii = l[i][i];
+    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
+    __syncthreads();
+    for (int e = tid; e < i * w; e += kThreads) {
+      const int r = e / w, c = e % w;
+      x[r][c] = fma(-l[i][r], x[i][c], x[r][c]);
     }
-    for (int i = m - 1; i >= 0; --i) {
-      const double lii = l[i][i];
-      const int owner = i & 31;
-      const double l0 = lane < i ? l[i][lane] : 0.0;
-      const double l1 = lane + 32 < i ? l[i][lane + 32] : 0.0;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        double xi;
-        if (i < 32) {
-          if (lane == owner) v0[k] = v0[k] / lii;
-          xi = __shfl_sync(0xffffffffu, v0[k], owner);
-        } else {
-          if (lane == owner) v1[k] = v1[k] / lii;
-          xi = __shfl_sync(0xffffffffu, v1[k], owner);
-        }
-        if (lane < i) v0[k] = fma(-l0, xi, v0[k]);
-        if (lane + 32 < i) v1[k] = fma(-l1, xi, v1[k]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (cs[k] < w && lane < m) x[lane][cs[k]] = v0[k];
-      if (cs[k] < w && lane + 32 < m) x[lane + 32][cs[k]] = v1[k];
-    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------

@@ -284,12 +284,12 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   tc_fence_before();
   __syncthreads();
   // epilogue, 2: coalesced FP64 read-modify-write of the output block; each
-  // warp loads 8 rows (4 columns per lane each) before writing any of them
+  // warp loads 4 rows (4 columns per lane each) before writing any of them
   constexpr int kWarps = kThreads / 32;
-  for (int r0 = warp; r0 < m; r0 += 8 * kWarps) {
-    double cv[8][4];
+  for (int r0 = warp; r0 < m; r0 += 4 * kWarps) {
+    double cv[4][4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 4; ++k) {
       const int r = r0 + kWarps * k;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -298,7 +298,7 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
       }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 4; ++k) {
       const int r = r0 + kWarps * k;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
