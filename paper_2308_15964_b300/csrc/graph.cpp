@@ -495,7 +495,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   t.op = (uint8_t)op;
   t.prec = (uint8_t)prec;
   t.prio = priority > 0 ? 1 : 0;
-  t.flags = 0;
+  t.flags = priority >= 2 ? kFlagFine : 0;
   for (int i = 0; i < k; ++i)
     if (mm[i] == SPX_COMMUTATIVE_WRITE) t.flags |= kFlagComm;
   for (int i = 0; i < 3; ++i) t.h[i] = i < nh ? handles[i] : 0;
@@ -506,10 +506,11 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
     t.nparts = 1;
   } else {
     t.nphases = op_phases(op, prec, g->tiles.data(), t.h);
-    t.nparts = phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, 0));
+    const bool fine = t.flags & kFlagFine;
+    t.nparts = phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, 0, fine));
     items = 0;
     for (uint32_t ph = 0; ph < t.nphases; ++ph)
-      items += phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, ph));
+      items += phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, ph, fine));
   }
   t.arg = 0;
 

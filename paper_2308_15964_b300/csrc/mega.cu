@@ -189,7 +189,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
   if (lowp && !kTc) return -1;
   switch (t.op) {
     case SPX_OP_POTRF:
-      return op_potrf_units(T[t.h[0]], phase, u0, u1, s);
+      return op_potrf_units(T[t.h[0]], phase, u0, u1, s, t.flags & kFlagFine);
     case SPX_OP_TRSM:
       if constexpr (kTc) {
         if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
@@ -198,7 +198,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
           return 0;
         }
       }
-      op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
+      op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s, t.flags & kFlagFine);
       return 0;
     case SPX_OP_SYRK:
       if constexpr (kTc) {
@@ -208,7 +208,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
           return ok ? 0 : -2;
         }
       }
-      op_syrk(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      op_syrk(T[t.h[0]], T[t.h[1]], u0, u1, s, t.flags & kFlagFine);
       return 0;
     case SPX_OP_GEMM_NT_SUB:
       if constexpr (kTc) {
@@ -226,16 +226,21 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s);
       return 0;
     case SPX_OP_TRSM_L_FWD:
-      op_trsm_fwd(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_GEMM_FWD:
-      op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s);
+    case SPX_OP_GEMM_BWD: {
+      const TileDesc &L = T[t.h[0]], &Xk = T[t.h[1]], &Xi = T[t.h[2]];
+      if (t.op == SPX_OP_GEMM_FWD)
+        rhs_update<false>((const double*)L.ptr, L.ld, (const double*)Xk.ptr, Xk.ld,
+                          (double*)Xi.ptr, Xi.ld, Xi.rows, Xi.cols, L.cols, u0, u1, s);
+      else
+        rhs_update<true>((const double*)L.ptr, L.ld, (const double*)Xk.ptr, Xk.ld,
+                         (double*)Xi.ptr, Xi.ld, Xi.rows, Xi.cols, L.rows, u0, u1, s);
       return 0;
+    }
     case SPX_OP_TRSM_LT_BWD:
-      op_trsm_bwd(T[t.h[0]], T[t.h[1]], u0, u1, s);
-      return 0;
-    case SPX_OP_GEMM_BWD:
-      op_gemm<true, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].rows, -1.0, u0, u1, s);
+      op_trsm_bwd(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_COPY:
     case SPX_OP_AXPY:
@@ -261,13 +266,14 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
   if (t.flags & kFlagSerial) {
     const uint32_t nph = op_phases(t.op, t.prec, T, t.h);
     for (uint32_t ph = 0; ph < nph; ++ph) {
-      const int r = run_units<kTc>(g, t, ph, 0, op_phase_units(t.op, t.prec, T, t.h, ph), s, tc);
+      const uint32_t nu = op_phase_units(t.op, t.prec, T, t.h, ph, t.flags & kFlagFine);
+      const int r = run_units<kTc>(g, t, ph, 0, nu, s, tc);
       if (r) return r;
       __syncthreads();
     }
     return 0;
   }
-  const uint32_t units = op_phase_units(t.op, t.prec, T, t.h, phase);
+  const uint32_t units = op_phase_units(t.op, t.prec, T, t.h, phase, t.flags & kFlagFine);
   const uint32_t parts = phase_parts(units);
   const uint32_t u0 = (uint32_t)((unsigned long long)part * units / parts);
   const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / parts);
@@ -588,7 +594,8 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         s_flag = atomicSub(&g.remaining[u], 1u) == 1u ? 2 : 1;
         if (s_flag == 2 && phase + 1 < t.nphases) {
           // last part of a phase: set up the next phase before pushing it
-          const uint32_t np = phase_parts(op_phase_units(t.op, t.prec, g.tiles, t.h, phase + 1));
+          const uint32_t np = phase_parts(
+              op_phase_units(t.op, t.prec, g.tiles, t.h, phase + 1, t.flags & kFlagFine));
           *(volatile uint32_t*)&g.phase[u] = phase + 1;
           atomicExch(&g.remaining[u], np);
           s_np = np;
@@ -743,8 +750,9 @@ cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
     const TaskDesc& t = host_tasks[u];
     for (uint32_t ph = 0; ph < t.nphases; ++ph) {
       const uint32_t np =
-          (t.flags & kFlagSerial) ? 1u
-                                  : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph));
+          (t.flags & kFlagSerial)
+              ? 1u
+              : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph, t.flags & kFlagFine));
       if (tc) task_kernel<true><<<np, kThreads, smem_bytes(true), st>>>(g, u, ph);
       else task_kernel<false><<<np, kThreads, smem_bytes(false), st>>>(g, u, ph);
     }

@@ -24,8 +24,10 @@ constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 // kFlagComm: the task has a COMMUTATIVE_WRITE access (runs as one part and
 // takes tile locks).  kFlagSerial: one CTA runs every phase and every unit of
 // the task in order (no-split graphs and commutative tasks); the arithmetic
-// per unit is the same as when the units are spread over CTAs.
-enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2 };
+// per unit is the same as when the units are spread over CTAs.  kFlagFine:
+// the task is on the critical path (inserted with priority >= 2): its POTRF,
+// TRSM and FP64 SYRK phases use smaller units so that more SMs share it.
+enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2, kFlagFine = 4 };
 
 // One registered tile (a data handle of the STF model).
 struct TileDesc {
@@ -174,17 +176,44 @@ struct DevGraph {
 // its successors.  Shared by the host (part and queue-entry counts) and the
 // device.
 //   POTRF (nb = diagonal 64-blocks): for j = 0..nb-1, phase 3j factors block
-//     (j,j) (1 unit), phase 3j+1 solves blocks (i,j), i > j (nb-1-j units),
-//     phase 3j+2 updates the lower blocks (i,l), j < l <= i
-//     ((nb-1-j)(nb-j)/2 units); 3nb-2 phases.
-//   TRSM (A m x n, nbr row blocks, nbc column blocks): for j = 0..nbc-1,
-//     phase 2j solves column block j of every row block (nbr units), phase
-//     2j+1 updates the column blocks l > j (nbr*(nbc-1-j) units).
+//     (j,j) (1 unit), phase 3j+1 solves the rows below it (64-row units),
+//     phase 3j+2 updates the lower triangle below it (64 x 64 block pairs);
+//     3nb-2 phases.
+//   TRSM (A m x n, nbc column blocks): for j = 0..nbc-1, phase 2j solves
+//     column block j (64-row units), phase 2j+1 updates the column blocks
+//     l > j (64 x 64 units).
+//   Fine tasks (kFlagFine) use 16-row units for the row solves and the TRSM
+//     updates and 32 x 32 block pairs for the POTRF and SYRK updates: one SM
+//     does about 2 FP64 FMA per clock, so a 64 x 64 x 64 unit alone takes
+//     tens of microseconds, and the critical path is a chain of such units.
 //   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
-//     blocks.  Solves: one phase, 64-column blocks of the right-hand sides.
+//     blocks.
+//   Block solves (L n x n, X n x r): TRSM_L_FWD, for j = 0..nb-1, phase 2j
+//     solves row block j of X with L_jj (one unit per column block of X),
+//     phase 2j+1 subtracts L_ij X_j from the rows below it; TRSM_LT_BWD does
+//     the same from the last row block up, with L_jj^T and the rows above.
+//     The update units, and those of GEMM_FWD / GEMM_BWD, are row blocks x
+//     column blocks of X: 16-row blocks of all r columns when X is narrow
+//     (r <= 16: a 64-row block would leave most SMs idle on the solve's
+//     critical path and waste lanes), 64 x 64 blocks otherwise.
 __host__ __device__ inline uint32_t cdiv64(int a) { return (uint32_t)((a + kBlk - 1) / kBlk); }
 
 __host__ __device__ inline uint32_t cdiv128(int a) { return (uint32_t)((a + 127) / 128); }
+__host__ __device__ inline uint32_t cdiv16(int a) { return (uint32_t)((a + 15) / 16); }
+__host__ __device__ inline uint32_t cdiv32(int a) { return (uint32_t)((a + 31) / 32); }
+
+constexpr int kNarrowRows = 16;  // rows of a narrow right-hand-side unit
+__host__ __device__ inline bool rhs_narrow(int cols) { return cols <= 16; }
+__host__ __device__ inline uint32_t rhs_unit_rows(int cols) {
+  return rhs_narrow(cols) ? (uint32_t)kNarrowRows : (uint32_t)kBlk;
+}
+__host__ __device__ inline uint32_t rhs_col_blocks(int cols) {
+  return rhs_narrow(cols) ? 1u : cdiv64(cols);
+}
+__host__ __device__ inline uint32_t rhs_row_units(int rows, int cols) {
+  const uint32_t rb = rhs_unit_rows(cols);
+  return ((uint32_t)rows + rb - 1) / rb;
+}
 
 // Low-precision tasks (prec = SPX_TF32 / SPX_BF16): SYRK and GEMM_NT_SUB run
 // on the tensor cores in 128 x 128 output units (SYRK: lower block pairs);
@@ -195,34 +224,49 @@ __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* 
   switch (op) {
     case SPX_OP_POTRF: return 3 * cdiv64(t[h[0]].rows) - 2;
     case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
+    case SPX_OP_TRSM_L_FWD:
+    case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
     default: return 1;
   }
 }
 
 __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileDesc* t,
-                                                   const uint32_t* h, uint32_t phase) {
+                                                   const uint32_t* h, uint32_t phase,
+                                                   bool fine) {
   switch (op) {
     case SPX_OP_POTRF: {
-      const uint32_t nb = cdiv64(t[h[0]].rows), j = phase / 3, r = nb - 1 - j;
-      return phase % 3 == 0 ? 1u : (phase % 3 == 1 ? r : r * (r + 1) / 2);
+      const int n = t[h[0]].rows, below = n - kBlk * (int)(phase / 3 + 1);
+      if (phase % 3 == 0) return 1u;
+      if (phase % 3 == 1) return fine ? cdiv16(below) : cdiv64(below);
+      const uint32_t q = fine ? cdiv32(below) : cdiv64(below);
+      return q * (q + 1) / 2;
     }
     case SPX_OP_TRSM: {
       const uint32_t nbr = cdiv64(t[h[1]].rows), nbc = cdiv64(t[h[1]].cols), j = phase / 2;
       if (phase >= 2 * nbc - 1) return nbr;  // low-precision copy
-      return phase % 2 == 0 ? nbr : nbr * (nbc - 1 - j);
+      const uint32_t rb = fine ? cdiv16(t[h[1]].rows) : nbr;
+      return phase % 2 == 0 ? rb : rb * (nbc - 1 - j);
     }
     case SPX_OP_SYRK: {
-      const uint32_t nb = prec != SPX_F64 ? cdiv128(t[h[1]].rows) : cdiv64(t[h[1]].rows);
+      const uint32_t nb = prec != SPX_F64 ? cdiv128(t[h[1]].rows)
+                                          : (fine ? cdiv32(t[h[1]].rows) : cdiv64(t[h[1]].rows));
       return nb * (nb + 1) / 2;
     }
     case SPX_OP_GEMM_NT_SUB:
       if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
       return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
-    case SPX_OP_GEMM_NN_ADD:
+    case SPX_OP_GEMM_NN_ADD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_FWD:
-    case SPX_OP_GEMM_BWD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
+    case SPX_OP_GEMM_BWD:
+      return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_L_FWD:
-    case SPX_OP_TRSM_LT_BWD: return cdiv64(t[h[1]].cols);
+    case SPX_OP_TRSM_LT_BWD: {
+      const int n = t[h[0]].rows, cols = t[h[1]].cols;
+      const uint32_t nb = cdiv64(n), j = phase / 2;
+      if (phase % 2 == 0) return rhs_col_blocks(cols);
+      const int rest = op == SPX_OP_TRSM_L_FWD ? n - kBlk * (int)(j + 1) : kBlk * (int)(nb - 1 - j);
+      return rhs_row_units(rest, cols) * rhs_col_blocks(cols);
+    }
     case SPX_OP_COPY:
     case SPX_OP_AXPY: return cdiv64(t[h[1]].rows);
     default: return 1;

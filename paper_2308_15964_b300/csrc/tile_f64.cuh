@@ -31,33 +31,36 @@ struct F64Smem {
   GemmSmem gs;
   double l[kBlk][kLds];   // diagonal block of L
   double x[kBlk][kLds];   // block being solved
+  double rinv[kBlk];      // reciprocals of the diagonal of l
   int info;
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// C[0:m, 0:n] += alpha * op(A) op(B), m, n <= 64, any K.
+// C[0:m, 0:n] += alpha * op(A) op(B), m <= 16 RI, n <= 16 CJ, any K.
 //   op(A)(i,k) = A_T ? A[k*lda + i] : A[i*lda + k]
 //   op(B)(k,j) = B_KN ? B[k*ldb + j] : B[j*ldb + k]
 // lower: only entries with column <= row are written (diagonal SYRK blocks).
-// CJ: output columns per thread (4: a 64-column block; 1: at most 16 columns,
-// for the narrow right-hand-side blocks of the solves).
-template <bool A_T, bool B_KN, int CJ = 4>
+// CJ / RI: output columns / rows per thread (4 / 4: a 64 x 64 block; CJ = 1:
+// at most 16 columns, for right-hand-side blocks; RI = 1 or 2: 16- or
+// 32-row blocks, for the finer parts of the POTRF and TRSM phases).
+template <bool A_T, bool B_KN, int CJ = 4, int RI = 4>
 __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
                            int m, int n, int K, double alpha, bool lower, GemmSmem& s) {
   constexpr int BN = 16 * CJ;  // columns of the block
+  constexpr int BM = 16 * RI;  // rows of the block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][CJ];
+  double acc[RI][CJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < CJ; ++j) acc[i][j] = 0.0;
 
   for (int k0 = 0; k0 < K; k0 += kKC) {
 #pragma unroll
-    for (int e = tid; e < kBlk * kKC; e += kThreads) {
+    for (int e = tid; e < BM * kKC; e += kThreads) {
       int i, kk;
-      if (A_T) { kk = e / kBlk; i = e % kBlk; } else { i = e / kKC; kk = e % kKC; }
+      if (A_T) { kk = e / BM; i = e % BM; } else { i = e / kKC; kk = e % kKC; }
       double v = 0.0;
       if (i < m && k0 + kk < K)
         v = ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk);
@@ -75,20 +78,20 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kKC; ++kk) {
-      double av[4], bv[CJ];
+      double av[RI], bv[CJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = s.a[kk][ty + 16 * i];
+      for (int i = 0; i < RI; ++i) av[i] = s.a[kk][ty + 16 * i];
 #pragma unroll
       for (int j = 0; j < CJ; ++j) bv[j] = s.b[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int j = 0; j < CJ; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RI; ++i) {
     const int r = ty + 16 * i;
 #pragma unroll
     for (int j = 0; j < CJ; ++j) {
@@ -102,12 +105,92 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
   __syncthreads();
 }
 
+// Narrow right-hand-side blocks: C[0:m, 0:n] += alpha * op(A) B for m <= 16
+// rows and n <= 16 columns, any K (B is K x n, row-major).  The 256 threads
+// are 16 rows x BN columns x KS = 256 / (16 BN) slices of each 64-deep k
+// chunk, so every lane of every FP64 instruction does useful work for
+// BN = 2, 4, 8, 16; the slices are summed in a fixed order (deterministic).
+constexpr int kNKC = 64;  // k chunk of a narrow block
+struct NarrowSmem {
+  double a[kNKC][kNarrowRows + 1];
+  double b[kNKC][17];
+  double red[kThreads];
+};
+
+template <bool A_T, int BN>
+__device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, const double* B,
+                               int ldb, int m, int n, int K, double alpha, NarrowSmem& s) {
+  constexpr int KS = kThreads / (kNarrowRows * BN);
+  const int tid = threadIdx.x, c = tid % BN, r = (tid / BN) % kNarrowRows,
+            ks = tid / (kNarrowRows * BN);
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int k0 = 0; k0 < K; k0 += kNKC) {
+    for (int e = tid; e < kNarrowRows * kNKC; e += kThreads) {
+      int i, kk;
+      if (A_T) { kk = e / kNarrowRows; i = e % kNarrowRows; } else { i = e / kNKC; kk = e % kNKC; }
+      double v = 0.0;
+      if (i < m && k0 + kk < K)
+        v = ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk);
+      s.a[kk][i] = v;
+    }
+    for (int e = tid; e < BN * kNKC; e += kThreads) {
+      const int kk = e / BN, j = e % BN;
+      s.b[kk][j] = (j < n && k0 + kk < K) ? ldcg(B + (size_t)(k0 + kk) * ldb + j) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = ks; kk < kNKC; kk += 2 * KS) {
+      acc0 = fma(s.a[kk][r], s.b[kk][c], acc0);
+      acc1 = fma(s.a[kk + KS][r], s.b[kk + KS][c], acc1);
+    }
+    __syncthreads();
+  }
+  s.red[tid] = acc0 + acc1;
+  __syncthreads();
+  if (ks == 0) {
+    double v = s.red[tid];
+#pragma unroll
+    for (int q = 1; q < KS; ++q) v += s.red[tid + q * kNarrowRows * BN];
+    if (r < m && c < n) {
+      double* p = C + (size_t)r * ldc + c;
+      *p = __ldcg(p) + alpha * v;
+    }
+  }
+  __syncthreads();
+}
+
+template <bool A_T>
+__device__ void gemm_narrow(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                            int m, int n, int K, double alpha, NarrowSmem& s) {
+  if (n <= 2) gemm_narrow_bn<A_T, 2>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
+  else if (n <= 4) gemm_narrow_bn<A_T, 4>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
+  else if (n <= 8) gemm_narrow_bn<A_T, 8>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
+  else gemm_narrow_bn<A_T, 16>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
+}
+
 // Copy an m x n block (row-major, ld) into a shared 64-wide array and back.
 __device__ __forceinline__ void load_block(double (*dst)[kLds], const double* src, int ld, int m,
                                            int n) {
   for (int e = threadIdx.x; e < kBlk * kBlk; e += kThreads) {
     const int r = e / kBlk, c = e % kBlk;
     dst[r][c] = (r < m && c < n) ? __ldcg(src + (size_t)r * ld + c) : 0.0;
+  }
+}
+
+// The first m rows only (m <= 64), for the 16-row units.
+__device__ __forceinline__ void load_rows(double (*dst)[kLds], const double* src, int ld, int m,
+                                          int n) {
+  for (int e = threadIdx.x; e < m * kBlk; e += kThreads) {
+    const int r = e / kBlk, c = e % kBlk;
+    dst[r][c] = c < n ? __ldcg(src + (size_t)r * ld + c) : 0.0;
+  }
+}
+
+__device__ __forceinline__ void store_rows(double* dst, int ld, const double (*src)[kLds], int m,
+                                           int n) {
+  for (int e = threadIdx.x; e < m * kBlk; e += kThreads) {
+    const int r = e / kBlk, c = e % kBlk;
+    if (c < n) dst[(size_t)r * ld + c] = src[r][c];
   }
 }
 
@@ -147,18 +230,27 @@ __device__ int potrf_smem(double (*a)[kLds], int w, int* s_info) {
   return 0;
 }
 
+// In-tile triangular solves.  Each computes the reciprocals of the diagonal
+// once (IEEE division) and scales by them, and scales the next row (column)
+// in the same pass that completes it, so one step costs one barrier and no
+// division on the dependency chain (a FP64 division is a long dependent
+// sequence on this GPU's FP64 pipe).
+
 // X <- X L^{-T} for X (m x w) and L (w x w lower) in shared memory:
 // x_rc = (x_rc - sum_{k<c} x_rk l_ck) / l_cc, right-looking over c.
-__device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+__device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
+                             double* rinv) {
   const int tid = threadIdx.x;
-  for (int c = 0; c < w; ++c) {
-    const double lcc = l[c][c];
-    for (int r = tid; r < m; r += kThreads) x[r][c] = x[r][c] / lcc;
-    __syncthreads();
+  for (int i = tid; i < w; i += kThreads) rinv[i] = 1.0 / l[i][i];
+  __syncthreads();
+  for (int r = tid; r < m; r += kThreads) x[r][0] *= rinv[0];
+  __syncthreads();
+  for (int c = 0; c + 1 < w; ++c) {
     const int t = w - c - 1;
     for (int e = tid; e < m * t; e += kThreads) {
       const int r = e / t, cc = c + 1 + e % t;
-      x[r][cc] = fma(-x[r][c], l[cc][c], x[r][cc]);
+      const double v = fma(-x[r][c], l[cc][c], x[r][cc]);
+      x[r][cc] = cc == c + 1 ? v * rinv[cc] : v;
     }
     __syncthreads();
   }
@@ -166,16 +258,19 @@ __device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, 
 
 // X <- L^{-1} X for L (m x m lower) and X (m x w) in shared memory (forward
 // substitution on every column).
-__device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+__device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
+                             double* rinv) {
   const int tid = threadIdx.x;
-  for (int i = 0; i < m; ++i) {
-    const double lii = l[i][i];
-    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
-    __syncthreads();
+  for (int i = tid; i < m; i += kThreads) rinv[i] = 1.0 / l[i][i];
+  __syncthreads();
+  for (int c = tid; c < w; c += kThreads) x[0][c] *= rinv[0];
+  __syncthreads();
+  for (int i = 0; i + 1 < m; ++i) {
     const int t = m - i - 1;
     for (int e = tid; e < t * w; e += kThreads) {
       const int r = i + 1 + e / w, c = e % w;
-      x[r][c] = fma(-l[r][i], x[i][c], x[r][c]);
+      const double v = fma(-l[r][i], x[i][c], x[r][c]);
+      x[r][c] = r == i + 1 ? v * rinv[r] : v;
     }
     __syncthreads();
   }
@@ -183,15 +278,18 @@ __device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, 
 
 // X <- L^{-T} X for L (m x m lower) and X (m x w) in shared memory (back
 // substitution: x_i = (x_i - sum_{k>i} l_ki x_k) / l_ii).
-__device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w) {
+__device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
+                             double* rinv) {
   const int tid = threadIdx.x;
-  for (int i = m - 1; i >= 0; --i) {
-    const double lii = l[i][i];
-    for (int c = tid; c < w; c += kThreads) x[i][c] = x[i][c] / lii;
-    __syncthreads();
+  for (int i = tid; i < m; i += kThreads) rinv[i] = 1.0 / l[i][i];
+  __syncthreads();
+  for (int c = tid; c < w; c += kThreads) x[m - 1][c] *= rinv[m - 1];
+  __syncthreads();
+  for (int i = m - 1; i > 0; --i) {
     for (int e = tid; e < i * w; e += kThreads) {
       const int r = e / w, c = e % w;
-      x[r][c] = fma(-l[i][r], x[i][c], x[r][c]);
+      const double v = fma(-l[i][r], x[i][c], x[r][c]);
+      x[r][c] = r == i - 1 ? v * rinv[r] : v;
     }
     __syncthreads();
   }
@@ -214,7 +312,7 @@ __device__ __forceinline__ void lower_pair(uint32_t u, int& bi, int& bj) {
 // over 64-column block steps j.  Returns 0 or the 1-based column (within the
 // tile) of a pivot that is not > 0.
 __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, uint32_t u1,
-                              F64Smem& s) {
+                              F64Smem& s, bool fine) {
   double* a = (double*)A.ptr;
   const int n = A.rows, lda = A.ld;
   const int j = (int)(phase / 3), jb = j * kBlk, w = min(kBlk, n - jb);
@@ -229,26 +327,35 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
       __syncthreads();
       return 0;
     }
-    case 1: {  // blocks (i, j) below the diagonal block: X <- X L_jj^{-T}
+    case 1: {  // row blocks below the diagonal block: X <- X L_jj^{-T}
+      const int rb = fine ? 16 : kBlk;
       load_block(s.l, ajj, lda, w, w);
       for (uint32_t u = u0; u < u1; ++u) {
-        const int ib = (j + 1 + (int)u) * kBlk, mb = min(kBlk, n - ib);
-        load_block(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
+        const int ib = jb + w + rb * (int)u, mb = min(rb, n - ib);
+        load_rows(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
         __syncthreads();
-        trsm_rt_smem(s.x, s.l, mb, w);
-        store_block(a + (size_t)ib * lda + jb, lda, s.x, mb, w, false);
+        trsm_rt_smem(s.x, s.l, mb, w, s.rinv);
+        store_rows(a + (size_t)ib * lda + jb, lda, s.x, mb, w);
         __syncthreads();
       }
       return 0;
     }
-    default: {  // trailing lower blocks (i, l), j < l <= i: A_il -= L_ij L_lj^T
+    default: {  // trailing lower blocks (i, l), l <= i: A_il -= L_ij L_lj^T
       for (uint32_t u = u0; u < u1; ++u) {
         int bi, bl;
         lower_pair(u, bi, bl);
-        const int ib = (j + 1 + bi) * kBlk, lb = (j + 1 + bl) * kBlk;
-        gemm_block<false, false>(a + (size_t)ib * lda + lb, lda, a + (size_t)ib * lda + jb, lda,
-                                 a + (size_t)lb * lda + jb, lda, min(kBlk, n - ib),
-                                 min(kBlk, n - lb), w, -1.0, bi == bl, s.gs);
+        if (fine) {
+          const int ib = jb + w + 32 * bi, lb = jb + w + 32 * bl;
+          gemm_block<false, false, 2, 2>(a + (size_t)ib * lda + lb, lda,
+                                         a + (size_t)ib * lda + jb, lda,
+                                         a + (size_t)lb * lda + jb, lda, min(32, n - ib),
+                                         min(32, n - lb), w, -1.0, bi == bl, s.gs);
+        } else {
+          const int ib = jb + w + kBlk * bi, lb = jb + w + kBlk * bl;
+          gemm_block<false, false>(a + (size_t)ib * lda + lb, lda, a + (size_t)ib * lda + jb,
+                                   lda, a + (size_t)lb * lda + jb, lda, min(kBlk, n - ib),
+                                   min(kBlk, n - lb), w, -1.0, bi == bl, s.gs);
+        }
       }
       return 0;
     }
@@ -259,46 +366,60 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
 // 64-column blocks j of A: solve block column j, then update the columns to
 // its right.
 __device__ void op_trsm_units(const TileDesc& Lt, const TileDesc& At, uint32_t phase, uint32_t u0,
-                              uint32_t u1, F64Smem& s) {
+                              uint32_t u1, F64Smem& s, bool fine) {
   const double* l = (const double*)Lt.ptr;
   double* a = (double*)At.ptr;
   const int m = At.rows, n = At.cols, lda = At.ld, ldl = Lt.ld;
   const int j = (int)(phase / 2), jb = j * kBlk, w = min(kBlk, n - jb);
-  if (phase % 2 == 0) {
+  const int rb = fine ? 16 : kBlk;
+  if (phase % 2 == 0) {  // row-block units
     load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
     for (uint32_t u = u0; u < u1; ++u) {
-      const int ib = (int)u * kBlk, mb = min(kBlk, m - ib);
+      const int ib = rb * (int)u, mb = min(rb, m - ib);
       double* x = a + (size_t)ib * lda + jb;
-      load_block(s.x, x, lda, mb, w);
+      load_rows(s.x, x, lda, mb, w);
       __syncthreads();
-      trsm_rt_smem(s.x, s.l, mb, w);
-      store_block(x, lda, s.x, mb, w, false);
+      trsm_rt_smem(s.x, s.l, mb, w, s.rinv);
+      store_rows(x, lda, s.x, mb, w);
       __syncthreads();
     }
-  } else {
+  } else {  // row-block x 64-column units
     const uint32_t right = cdiv64(n) - 1 - (uint32_t)j;
     for (uint32_t u = u0; u < u1; ++u) {
-      const int ib = (int)(u / right) * kBlk, lb = (j + 1 + (int)(u % right)) * kBlk;
-      gemm_block<false, false>(a + (size_t)ib * lda + lb, lda, a + (size_t)ib * lda + jb, lda,
-                               l + (size_t)lb * ldl + jb, ldl, min(kBlk, m - ib), min(kBlk, n - lb),
-                               w, -1.0, false, s.gs);
+      const int ib = rb * (int)(u / right), lb = (j + 1 + (int)(u % right)) * kBlk;
+      double* c = a + (size_t)ib * lda + lb;
+      const double* ap = a + (size_t)ib * lda + jb;
+      const double* bp = l + (size_t)lb * ldl + jb;
+      if (fine)
+        gemm_block<false, false, 4, 1>(c, lda, ap, lda, bp, ldl, min(16, m - ib),
+                                       min(kBlk, n - lb), w, -1.0, false, s.gs);
+      else
+        gemm_block<false, false>(c, lda, ap, lda, bp, ldl, min(kBlk, m - ib), min(kBlk, n - lb),
+                                 w, -1.0, false, s.gs);
     }
   }
 }
 
 // SYRK: C (n x n, lower) -= L L^T, L (n x k); units = lower 64-block pairs.
 __device__ void op_syrk(const TileDesc& Lt, const TileDesc& Ct, uint32_t u0, uint32_t u1,
-                        F64Smem& s) {
+                        F64Smem& s, bool fine) {
   const double* l = (const double*)Lt.ptr;
   double* c = (double*)Ct.ptr;
   const int n = Ct.rows, k = Lt.cols;
   for (uint32_t u = u0; u < u1; ++u) {
     int bi, bj;
     lower_pair(u, bi, bj);
-    const int r0 = bi * kBlk, c0 = bj * kBlk;
-    gemm_block<false, false>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, l + (size_t)r0 * Lt.ld, Lt.ld,
-                             l + (size_t)c0 * Lt.ld, Lt.ld, min(kBlk, n - r0), min(kBlk, n - c0), k,
-                             -1.0, bi == bj, s.gs);
+    if (fine) {  // 32 x 32 block pairs
+      const int r0 = bi * 32, c0 = bj * 32;
+      gemm_block<false, false, 2, 2>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, l + (size_t)r0 * Lt.ld,
+                                     Lt.ld, l + (size_t)c0 * Lt.ld, Lt.ld, min(32, n - r0),
+                                     min(32, n - c0), k, -1.0, bi == bj, s.gs);
+    } else {
+      const int r0 = bi * kBlk, c0 = bj * kBlk;
+      gemm_block<false, false>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, l + (size_t)r0 * Lt.ld, Lt.ld,
+                               l + (size_t)c0 * Lt.ld, Lt.ld, min(kBlk, n - r0),
+                               min(kBlk, n - c0), k, -1.0, bi == bj, s.gs);
+    }
   }
 }
 
@@ -324,60 +445,88 @@ __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& 
   }
 }
 
-// X <- L^{-1} X (forward, L n x n, X n x r); units = 64-column blocks of X.
-__device__ void op_trsm_fwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0, uint32_t u1,
-                            F64Smem& s) {
-  const double* l = (const double*)Lt.ptr;
-  double* x = (double*)Xt.ptr;
-  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld;
+// The narrow-block staging overlays the two 64x64 blocks (unused by GEMM
+// parts).
+static_assert(sizeof(NarrowSmem) <= 2 * sizeof(double) * kBlk * kLds, "narrow staging");
+__device__ __forceinline__ NarrowSmem& narrow_smem(F64Smem& s) {
+  return *reinterpret_cast<NarrowSmem*>(&s.l[0][0]);
+}
+
+// C (rows x r) -= op(A) B for the block solves (units: see op_phase_units):
+// 16-row units of all columns when r <= 16, else 64 x 64 output blocks.
+// op(A) = A (A_T false) or A^T (A_T true); r0_c / r0_a: first row of C and
+// of op(A) covered by unit 0.
+template <bool A_T>
+__device__ void rhs_update(const double* a, int lda, const double* b, int ldb, double* c, int ldc,
+                           int rows, int cols, int K, uint32_t u0, uint32_t u1, F64Smem& s) {
+  const int rb = (int)rhs_unit_rows(cols);
+  const uint32_t ncb = rhs_col_blocks(cols);
   for (uint32_t u = u0; u < u1; ++u) {
-    const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
-    for (int ib = 0; ib < n; ib += kBlk) {
-      const int mb = min(kBlk, n - ib);
-      if (ib > 0 && w <= 16)
-        gemm_block<false, true, 1>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)ib * ldl, ldl,
-                                   x + c0, ldx, mb, w, ib, -1.0, false, s.gs);
-      else if (ib > 0)
-        gemm_block<false, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)ib * ldl, ldl, x + c0,
-                                ldx, mb, w, ib, -1.0, false, s.gs);
-      load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
-      load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
-      __syncthreads();
-      trsm_ln_smem(s.x, s.l, mb, w);
-      store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
-      __syncthreads();
-    }
+    const int r0 = (int)(u / ncb) * rb, c0 = (int)(u % ncb) * kBlk;
+    const int m = min(rb, rows - r0), w = rhs_narrow(cols) ? cols : min(kBlk, cols - c0);
+    const double* ap = A_T ? a + r0 : a + (size_t)r0 * lda;
+    double* cp = c + (size_t)r0 * ldc + c0;
+    if (rhs_narrow(cols))
+      gemm_narrow<A_T>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, narrow_smem(s));
+    else if (w <= 16)
+      gemm_block<A_T, true, 1>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
+    else
+      gemm_block<A_T, true>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
   }
 }
 
-// X <- L^{-T} X (backward); units = 64-column blocks of X.
-__device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t u0, uint32_t u1,
-                            F64Smem& s) {
+// Diagonal step of a block solve: X[ib:ib+mb, column block u] <- L_jj^{-1}
+// (or L_jj^{-T}) times itself, L_jj = L[ib:ib+mb, ib:ib+mb].
+template <bool kTrans>
+__device__ void rhs_diag(const double* l, int ldl, double* x, int ldx, int ib, int mb, int cols,
+                         uint32_t u0, uint32_t u1, F64Smem& s) {
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int c0 = rhs_narrow(cols) ? 0 : (int)u * kBlk;
+    const int w = rhs_narrow(cols) ? cols : min(kBlk, cols - c0);
+    load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
+    load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
+    __syncthreads();
+    if (kTrans) trsm_lt_smem(s.x, s.l, mb, w, s.rinv);
+    else trsm_ln_smem(s.x, s.l, mb, w, s.rinv);
+    store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
+    __syncthreads();
+  }
+}
+
+// X <- L^{-1} X (forward substitution, L n x n lower, X n x r), right-looking
+// over 64-row blocks j: phase 2j solves block j, phase 2j+1 updates the rows
+// below it (X_below -= L[below, j] X_j).
+__device__ void op_trsm_fwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t phase, uint32_t u0,
+                            uint32_t u1, F64Smem& s) {
   const double* l = (const double*)Lt.ptr;
   double* x = (double*)Xt.ptr;
-  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld;
-  const int nb = (n + kBlk - 1) / kBlk;
-  for (uint32_t u = u0; u < u1; ++u) {
-    const int c0 = u * kBlk, w = min(kBlk, Xt.cols - c0);
-    for (int bi = nb - 1; bi >= 0; --bi) {
-      const int ib = bi * kBlk, mb = min(kBlk, n - ib), below = n - ib - mb;
-      if (below > 0 && w <= 16)
-        gemm_block<true, true, 1>(x + (size_t)ib * ldx + c0, ldx,
-                                  l + (size_t)(ib + mb) * ldl + ib, ldl,
-                                  x + (size_t)(ib + mb) * ldx + c0, ldx, mb, w, below, -1.0,
-                                  false, s.gs);
-      else if (below > 0)
-        gemm_block<true, true>(x + (size_t)ib * ldx + c0, ldx, l + (size_t)(ib + mb) * ldl + ib,
-                               ldl, x + (size_t)(ib + mb) * ldx + c0, ldx, mb, w, below, -1.0,
-                               false, s.gs);
-      load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
-      load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
-      __syncthreads();
-      trsm_lt_smem(s.x, s.l, mb, w);
-      store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
-      __syncthreads();
-    }
+  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld, cols = Xt.cols;
+  const int ib = (int)(phase / 2) * kBlk, mb = min(kBlk, n - ib);
+  if (phase % 2 == 0) {
+    rhs_diag<false>(l, ldl, x, ldx, ib, mb, cols, u0, u1, s);
+    return;
   }
+  const int r0 = ib + mb;
+  rhs_update<false>(l + (size_t)r0 * ldl + ib, ldl, x + (size_t)ib * ldx, ldx,
+                    x + (size_t)r0 * ldx, ldx, n - r0, cols, mb, u0, u1, s);
+}
+
+// X <- L^{-T} X (back substitution), over 64-row blocks from the last:
+// phase 2q solves block j = nb-1-q with L_jj^T, phase 2q+1 updates the rows
+// above it (X_above -= L[j, above]^T X_j).
+__device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t phase, uint32_t u0,
+                            uint32_t u1, F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* x = (double*)Xt.ptr;
+  const int n = Lt.rows, ldl = Lt.ld, ldx = Xt.ld, cols = Xt.cols;
+  const int nb = (n + kBlk - 1) / kBlk;
+  const int ib = (nb - 1 - (int)(phase / 2)) * kBlk, mb = min(kBlk, n - ib);
+  if (phase % 2 == 0) {
+    rhs_diag<true>(l, ldl, x, ldx, ib, mb, cols, u0, u1, s);
+    return;
+  }
+  rhs_update<true>(l + (size_t)ib * ldl, ldl, x + (size_t)ib * ldx, ldx, x, ldx, ib, cols, mb, u0,
+                   u1, s);
 }
 
 // Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1.

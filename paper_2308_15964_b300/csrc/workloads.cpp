@@ -61,6 +61,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
   const int T = A.T;
   const int R = SPX_READ, W = SPX_WRITE;
   const int hi = lookahead ? 1 : 0;
+  const int crit = lookahead ? 2 : 0;  // critical path: high priority, finer parts
   long long count = 0;
   auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
                  int prio, unsigned* id, int p = SPX_F64) {
@@ -72,12 +73,14 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
   };
   for (int k = 0; k < T && rc == SPX_OK && factor; ++k) {
     unsigned t = 0;
-    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, hi, &t, SPX_F64);
+    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, crit, &t, SPX_F64);
     if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-      rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, hi, nullptr, prec);
+      rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr,
+               prec);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-      rc = ins(SPX_OP_SYRK, {A.at(i, k), A.at(i, i)}, {R, W}, hi, nullptr, prec);
+      rc = ins(SPX_OP_SYRK, {A.at(i, k), A.at(i, i)}, {R, W}, i == k + 1 ? crit : hi, nullptr,
+               prec);
     for (int j = k + 1; j < T && rc == SPX_OK; ++j)
       for (int i = j + 1; i < T && rc == SPX_OK; ++i)
         rc = ins(SPX_OP_GEMM_NT_SUB, {A.at(i, k), A.at(j, k), A.at(i, j)}, {R, R, W},
@@ -93,12 +96,14 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
     for (int k = 0; k < T && rc == SPX_OK; ++k) {
       rc = ins(SPX_OP_TRSM_L_FWD, {A.at(k, k), x[k]}, {R, W}, hi, nullptr);
       for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-        rc = ins(SPX_OP_GEMM_FWD, {A.at(i, k), x[k], x[i]}, {R, R, W}, 0, nullptr);
+        rc = ins(SPX_OP_GEMM_FWD, {A.at(i, k), x[k], x[i]}, {R, R, W}, i == k + 1 ? hi : 0,
+                 nullptr);
     }
     for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
       rc = ins(SPX_OP_TRSM_LT_BWD, {A.at(k, k), x[k]}, {R, W}, hi, nullptr);
       for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
-        rc = ins(SPX_OP_GEMM_BWD, {A.at(k, i), x[k], x[i]}, {R, R, W}, 0, nullptr);
+        rc = ins(SPX_OP_GEMM_BWD, {A.at(k, i), x[k], x[i]}, {R, R, W}, i == k - 1 ? hi : 0,
+                 nullptr);
     }
   }
   if (out_ntasks) *out_ntasks = count;
@@ -206,12 +211,12 @@ extern "C" int spx_refine_insert(spx_graph_t g, double* dev_A0, int n, int lda, 
     for (int k = 0; k < T && rc == SPX_OK; ++k) {
       rc = ins(SPX_OP_TRSM_L_FWD, {L.at(k, k), xr[k]}, {R, W}, 1);
       for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-        rc = ins(SPX_OP_GEMM_FWD, {L.at(i, k), xr[k], xr[i]}, {R, R, W}, 0);
+        rc = ins(SPX_OP_GEMM_FWD, {L.at(i, k), xr[k], xr[i]}, {R, R, W}, i == k + 1 ? 1 : 0);
     }
     for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
       rc = ins(SPX_OP_TRSM_LT_BWD, {L.at(k, k), xr[k]}, {R, W}, 1);
       for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
-        rc = ins(SPX_OP_GEMM_BWD, {L.at(k, i), xr[k], xr[i]}, {R, R, W}, 0);
+        rc = ins(SPX_OP_GEMM_BWD, {L.at(k, i), xr[k], xr[i]}, {R, R, W}, i == k - 1 ? 1 : 0);
     }
     // x += d
     for (int i = 0; i < T && rc == SPX_OK; ++i) rc = ins(SPX_OP_AXPY, {xr[i], xx[i]}, {R, W}, 0);
