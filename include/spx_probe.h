@@ -1,11 +1,13 @@
 /*
- * spx_probe.h - throughput probes behind the roofline denominators.
+ * spx_probe.h - throughput and latency probes behind the roofline
+ * denominators and the tile-kernel design.
  *
  * The paper has no counterpart: these calls measure the B300's FP64 and
  * FP32 pipes, global atomics and the kernel launch rate, which the roofline
- * fractions reported by the benchmark are divided by.  Each call runs on its
- * own stream of the current device, allocates 1 MiB of device scratch, and
- * synchronises before returning.
+ * fractions reported by the benchmark are divided by, and the FP64 and
+ * barrier latencies that bound the in-tile triangular solves.  Each call
+ * runs on its own stream of the current device, allocates 1 MiB of device
+ * scratch, and synchronises before returning.
  */
 #ifndef SPX_PROBE_H_
 #define SPX_PROBE_H_
@@ -20,7 +22,18 @@ enum {
   SPX_PROBE_FFMA = 2,            /* FP32 FMA: rate in FLOP/s                */
   SPX_PROBE_ATOMIC_SAME = 3,     /* atomicAdd on one address: ops/s         */
   SPX_PROBE_ATOMIC_DISTINCT = 4, /* atomicAdd on 64 Ki addresses: ops/s     */
-  SPX_PROBE_LAUNCH = 5           /* empty <<<1,32>>> launches: launches/s   */
+  SPX_PROBE_LAUNCH = 5,          /* empty <<<1,32>>> launches: launches/s   */
+  /* Latency probes (one block of 256 threads on one SM): *rate receives SM
+   * clock cycles per step instead of a rate. */
+  SPX_PROBE_LAT_DFMA = 6,        /* dependent FP64 FMA chain, one thread    */
+  SPX_PROBE_LAT_DDIV = 7,        /* dependent FP64 division chain           */
+  SPX_PROBE_LAT_DSQRT = 8,       /* dependent FP64 square-root chain        */
+  SPX_PROBE_LAT_SYNC = 9,        /* __syncthreads() of 256 threads          */
+  SPX_PROBE_WARP_DFMA = 10,      /* cycles per warp FP64 FMA instruction,   */
+                                 /* 8 warps x 8 independent chains          */
+  SPX_PROBE_WARP_DDIV = 11,      /* cycles per warp FP64 division, same     */
+  SPX_PROBE_LAT_DRCP = 12,       /* dependent __drcp_rn + multiply chain    */
+  SPX_PROBE_LAT_DRSQRT = 13      /* dependent rsqrt chain                   */
 };
 
 /* Run probe `which` with `iters` inner iterations (or launches).  Writes the

@@ -32,7 +32,8 @@
 namespace spx {
 namespace {
 
-// Execution state and initial ready queues (step 5).  Uses ucount as
+// Execution state and initial ready queues (step 5): one entry per ready
+// task, (task << kPartBits) | (parts - 1).  Uses ucount as
 // scratch.  Every thread of the CTA must call it.
 __device__ void init_run(const DevGraph& g, uint32_t* sh) {
   const uint32_t N = g.ntasks;
@@ -46,7 +47,7 @@ __device__ void init_run(const DevGraph& g, uint32_t* sh) {
     for (uint32_t u = tid; u < N; u += kDeriveThreads) {
       const TaskDesc& t = g.tasks[u];
       const bool in_q = g.indeg[u] == 0 && (q == 0 ? t.prio != 0 : t.prio == 0);
-      g.ucount[u] = in_q ? t.nparts : 0u;
+      g.ucount[u] = in_q ? 1u : 0u;
     }
     __syncthreads();
     const uint32_t total = block_excl_scan(g.ucount, N, sh);
@@ -60,10 +61,7 @@ __device__ void init_run(const DevGraph& g, uint32_t* sh) {
     for (uint32_t u = tid; u < N; u += kDeriveThreads) {
       const TaskDesc& t = g.tasks[u];
       const bool in_q = g.indeg[u] == 0 && (q == 0 ? t.prio != 0 : t.prio == 0);
-      if (in_q) {
-        const uint32_t base = g.ucount[u];
-        for (uint32_t p = 0; p < t.nparts; ++p) g.queue[q][base + p] = (u << kPartBits) | p;
-      }
+      if (in_q) g.queue[q][g.ucount[u]] = (u << kPartBits) | (t.nparts - 1);
     }
     if (tid == 0) {
       g.rs->tail[q].v = total;

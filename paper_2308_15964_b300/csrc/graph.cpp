@@ -45,7 +45,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
   size_t queue0, queue1, t_start, ff_end;
-  size_t rs, locks, t_end, trace, phase, zero_end;
+  size_t rs, locks, t_end, trace, phase, qclaim0, qclaim1, zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
@@ -75,6 +75,8 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.t_end = take(N * 4);
   L.trace = take(trace ? N * 32 : 0);
   L.phase = take(N * 4);
+  L.qclaim0 = take(Q * 4);
+  L.qclaim1 = take(Q * 4);
   L.zero_end = o;
   L.hptr = take((H + 1) * 4);
   L.s_task = take(M * 4);
@@ -319,6 +321,8 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.task_rec = (const uint32_t*)(D + L.task_rec);
   d.queue[0] = (uint32_t*)(D + L.queue0);
   d.queue[1] = (uint32_t*)(D + L.queue1);
+  d.qclaim[0] = (uint32_t*)(D + L.qclaim0);
+  d.qclaim[1] = (uint32_t*)(D + L.qclaim1);
   d.t_start = (uint32_t*)(D + L.t_start);
   d.rs = (RunState*)(D + L.rs);
   d.locks = (uint32_t*)(D + L.locks);

@@ -82,26 +82,28 @@ __device__ uint32_t pop(const DevGraph& g, uint32_t& empties) {
     if (ld_volatile(&rs->abort)) return kExit;
     for (int q = 0; q < 2; ++q) {
       uint32_t h = ld_volatile(&rs->head[q].v);
-      uint32_t t = min(ld_volatile(&rs->tail[q].v), g.qcap);
-      while (h < t) {
-        const uint32_t prev = atomicCAS(&rs->head[q].v, h, h + 1);
-        if (prev == h) {
-          // The slot was reserved by a pusher that is writing it now.
-          uint32_t v, spins = 0;
-          while ((v = ld_volatile(&g.queue[q][h])) == kEmpty) {
-            if ((++spins & 1023u) == 0) {
-              if (ld_volatile(&rs->abort)) return kExit;
-              if (watchdog_expired(g)) {
-                set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
-                return kExit;
-              }
+      while (h < min(ld_volatile(&rs->tail[q].v), g.qcap)) {
+        // Slot h holds one phase of a task; its parts are claimed with
+        // atomicAdd on the slot's counter.  The claimer of the last part
+        // (or anyone who finds the slot exhausted) moves the head past it.
+        uint32_t v, spins = 0;
+        while ((v = ld_volatile(&g.queue[q][h])) == kEmpty) {  // reserved, being written
+          if ((++spins & 1023u) == 0) {
+            if (ld_volatile(&rs->abort)) return kExit;
+            if (watchdog_expired(g)) {
+              set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+              return kExit;
             }
           }
-          __threadfence();
-          return v;
         }
-        h = prev;
-        t = min(ld_volatile(&rs->tail[q].v), g.qcap);
+        const uint32_t np = (v & (kMaxParts - 1u)) + 1u;
+        const uint32_t p = atomicAdd(&g.qclaim[q][h], 1u);
+        if (p + 1u >= np) atomicMax(&rs->head[q].v, h + 1u);
+        if (p < np) {
+          __threadfence();
+          return (v & ~(kMaxParts - 1u)) | p;
+        }
+        h = max(h + 1u, ld_volatile(&rs->head[q].v));
       }
     }
     if (ld_volatile(&rs->done.v) >= g.ntasks) return kExit;
@@ -134,7 +136,7 @@ __device__ void release(const DevGraph& g, uint32_t task) {
     __threadfence();  // order the predecessors' data before the queue entries
     for (uint32_t q = 0; q < 2; ++q) {
       const bool mine = ready && pq == q;
-      const uint32_t cnt = mine ? np : 0u;
+      const uint32_t cnt = mine ? 1u : 0u;  // one entry: phase 0 of task s
       uint32_t incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -153,11 +155,7 @@ __device__ void release(const DevGraph& g, uint32_t task) {
         if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
         continue;
       }
-      if (mine) {
-        const uint32_t at = slot + incl - cnt;
-        for (uint32_t p = 0; p < np; ++p)
-          *(volatile uint32_t*)&g.queue[q][at + p] = (s << kPartBits) | p;
-      }
+      if (mine) *(volatile uint32_t*)&g.queue[q][slot + incl - 1] = (s << kPartBits) | (np - 1);
     }
   }
 }
@@ -280,22 +278,22 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
   return run_units<kTc>(g, t, phase, u0, u1, s, tc);
 }
 
-// Push the np parts of the next phase of task u (warp 0, all lanes).
+// Push the next phase (np parts) of task u (thread 0).  The CTA that
+// finished the phase runs part 0 itself, without a queue round trip, so the
+// slot's claim counter starts at 1; a single-part phase (the diagonal steps
+// on the critical path) never touches the queue.
 __device__ void push_phase(const DevGraph& g, uint32_t u, uint32_t np, uint32_t prio) {
-  const int lane = threadIdx.x & 31;
+  if (np <= 1) return;
   const uint32_t q = prio ? 0u : 1u;
-  uint32_t slot = 0;
-  if (lane == 0) {
-    slot = atomicAdd(&g.rs->tail[q].v, np);
-    atomicMax(&g.rs->hiwater, slot + np);
-  }
-  slot = __shfl_sync(0xffffffffu, slot, 0);
-  if (slot + np > g.qcap) {
-    if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+  const uint32_t slot = atomicAdd(&g.rs->tail[q].v, 1u);
+  atomicMax(&g.rs->hiwater, slot + 1u);
+  if (slot >= g.qcap) {
+    set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
     return;
   }
-  for (uint32_t p = lane; p < np; p += 32)
-    *(volatile uint32_t*)&g.queue[q][slot + p] = (u << kPartBits) | p;
+  atomicExch(&g.qclaim[q][slot], 1u);
+  __threadfence();
+  *(volatile uint32_t*)&g.queue[q][slot] = (u << kPartBits) | (np - 1);
 }
 
 // Take the COMMUTATIVE_WRITE locks of task u in ascending handle order
@@ -355,12 +353,14 @@ __device__ bool ring_put(const DevGraph& g, uint32_t q, uint32_t ticket, uint32_
 }
 
 // Push np consecutive parts of pool task u (one thread).
-__device__ void ring_push_task(const DevGraph& g, uint32_t u, uint32_t np, uint32_t prio) {
-  const uint32_t q = prio ? 0u : 1u;
-  const uint32_t t0 = atomicAdd(&g.rs->tail[q].v, np);
-  atomicMax(&g.rs->hiwater, t0 + np - ld_volatile(&g.rs->head[q].v));
-  for (uint32_t p = 0; p < np; ++p)
-    if (!ring_put(g, q, t0 + p, (u << kPartBits) | p)) return;
+__device__ void ring_push_task(const DevGraph& g, uint32_t u, uint32_t p0, uint32_t np,
+                               uint32_t prio) {
+  if (p0 >= np) return;
+  const uint32_t q = prio ? 0u : 1u, cnt = np - p0;
+  const uint32_t t0 = atomicAdd(&g.rs->tail[q].v, cnt);
+  atomicMax(&g.rs->hiwater, t0 + cnt - ld_volatile(&g.rs->head[q].v));
+  for (uint32_t p = 0; p < cnt; ++p)
+    if (!ring_put(g, q, t0 + p, (u << kPartBits) | (p0 + p))) return;
 }
 
 // Pop a queue entry, claim a submission (kSubmit, entry copied to *sub), or
@@ -479,7 +479,7 @@ __device__ void server_admit(const DevGraph& g, const SubEntry& e, uint32_t* sh)
   __syncthreads();
   for (uint32_t u = tid; u < e.ntasks; u += kThreads) {
     const uint32_t gu = e.tb + u;
-    if (g.indeg[gu] == 0) ring_push_task(g, gu, g.tasks[gu].nparts, g.tasks[gu].prio);
+    if (g.indeg[gu] == 0) ring_push_task(g, gu, 0, g.tasks[gu].nparts, g.tasks[gu].prio);
   }
   __syncthreads();
 }
@@ -496,7 +496,7 @@ __device__ void release_server(const DevGraph& g, uint32_t u, uint32_t r) {
       const uint32_t s = tb + g.col[eb + idx];
       if (atomicSub(&g.indeg_w[s], 1u) == 1u) {
         __threadfence();
-        ring_push_task(g, s, g.tasks[s].nparts, g.tasks[s].prio);
+        ring_push_task(g, s, 0, g.tasks[s].nparts, g.tasks[s].prio);
       }
     }
   }
@@ -536,10 +536,15 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   const long long c_begin = clock64();
   long long busy = 0;
   uint32_t empties = 0;
+  uint32_t next = kEmpty;  // thread 0: part 0 of a phase this CTA just opened
   if (tid == 0) touch_progress(g);
 
   for (;;) {
-    if (tid == 0) s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties);
+    if (tid == 0) {
+      if (next != kEmpty) s_item = next;
+      else s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties);
+      next = kEmpty;
+    }
     __syncthreads();
     const uint32_t item = s_item;
     if (item == kExit) break;
@@ -608,7 +613,10 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     __syncthreads();
     if (s_flag == 0) break;
     if constexpr (kServer) {
-      if (s_flag == 3 && tid == 0) ring_push_task(g, u, s_np, t.prio);
+      if (s_flag == 3 && tid == 0) {
+        ring_push_task(g, u, 1, s_np, t.prio);
+        next = u << kPartBits;
+      }
       if (s_flag == 2 && tid < 32) {
         release_server(g, u, req);
         __syncwarp();
@@ -619,7 +627,10 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         }
       }
     } else {
-      if (s_flag == 3 && tid < 32) push_phase(g, u, s_np, t.prio);
+      if (s_flag == 3 && tid == 0) {
+        push_phase(g, u, s_np, t.prio);
+        next = u << kPartBits;
+      }
       if (s_flag == 2) {
         if (tid < 32) {
           if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);

@@ -72,6 +72,60 @@ __global__ void atomic_distinct_kernel(unsigned* ctr, int iters, int n) {
 
 __global__ void empty_kernel() {}
 
+// Latency probes: one block, thread 0 times a dependent chain with clock64()
+// and writes the SM cycles per step to out[0].
+enum LatOp { kLatDfma, kLatDdiv, kLatDsqrt, kLatSync, kLatWarpDfma, kLatWarpDdiv, kLatDrcp,
+             kLatDrsqrt };
+
+__global__ void latency_kernel(double* out, int iters, int op, double a, double b) {
+  double x = 1.0 + threadIdx.x * 1e-9, y[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) y[c] = x + c;
+  __syncthreads();
+  const long long t0 = clock64();
+  switch (op) {
+    case kLatDfma:
+      for (int i = 0; i < iters; ++i) x = fma(x, a, b);
+      break;
+    case kLatDdiv:
+      for (int i = 0; i < iters; ++i) x = a / x;
+      break;
+    case kLatDsqrt:
+      for (int i = 0; i < iters; ++i) x = sqrt(x) + b;
+      break;
+    case kLatSync:
+      for (int i = 0; i < iters; ++i) __syncthreads();
+      break;
+    case kLatWarpDfma:  // all threads, kChains independent chains each
+      for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) y[c] = fma(y[c], a, b);
+      break;
+    case kLatWarpDdiv:  // all threads, kChains independent divisions each
+      for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) y[c] = a / y[c];
+      break;
+    case kLatDrcp:  // correctly rounded reciprocal
+      for (int i = 0; i < iters; ++i) x = __drcp_rn(x) * a;
+      break;
+    default:  // kLatDrsqrt
+      for (int i = 0; i < iters; ++i) x = rsqrt(x) + b;
+      break;
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  double s = x;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += y[c];
+  if (s == 12345.678) out[1] = s;
+  if (threadIdx.x == 0) {
+    const bool warps = op == kLatWarpDfma || op == kLatWarpDdiv;
+    const double steps = warps ? (double)iters * kChains * (blockDim.x / 32) : iters;
+    out[0] = (double)(t1 - t0) / steps;
+  }
+}
+
 int sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -122,6 +176,18 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
         for (int i = 0; i < iters; ++i) empty_kernel<<<1, 32, 0, st>>>();
         work = iters;
         break;
+      case SPX_PROBE_LAT_DFMA:
+      case SPX_PROBE_LAT_DDIV:
+      case SPX_PROBE_LAT_DSQRT:
+      case SPX_PROBE_LAT_SYNC:
+      case SPX_PROBE_WARP_DFMA:
+      case SPX_PROBE_WARP_DDIV:
+      case SPX_PROBE_LAT_DRCP:
+      case SPX_PROBE_LAT_DRSQRT:
+        latency_kernel<<<1, 256, 0, st>>>((double*)buf, iters, which - SPX_PROBE_LAT_DFMA,
+                                          1.0000001, 1e-9);
+        work = 0.0;
+        break;
       default:
         work = -1.0;
     }
@@ -130,6 +196,9 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   cudaError_t err = cudaStreamSynchronize(st);
   float t = 0.f;
   cudaEventElapsedTime(&t, e0, e1);
+  double cyc = 0.0;  // latency probes: cycles per step, written by the kernel
+  if (err == cudaSuccess && which >= SPX_PROBE_LAT_DFMA)
+    err = cudaMemcpy(&cyc, buf, sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(buf);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -137,7 +206,7 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   if (work < 0) return -1;
   if (err != cudaSuccess) return -7;
   *ms = t;
-  *rate = work / (t * 1e-3);
+  *rate = which >= SPX_PROBE_LAT_DFMA ? cyc : work / (t * 1e-3);
   return 0;
 }
 

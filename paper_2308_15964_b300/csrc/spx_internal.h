@@ -152,6 +152,10 @@ struct DevGraph {
   uint32_t* remaining;         // [ntasks] parts of the current phase not finished
   uint32_t* phase;             // [ntasks] current phase of a multi-phase task
   uint32_t* queue[2];          // [qcap] each
+  // graph runs: an entry is one phase of a task, (task << kPartBits) |
+  // (parts - 1); qclaim counts the parts claimed from each slot (atomicAdd,
+  // so a wide phase is handed out without a compare-and-swap loop)
+  uint32_t* qclaim[2];         // [qcap] each, zero at the start of a run
   uint32_t* locks;             // [ntiles] owner task + 1, 0 = free
   uint32_t* t_start;           // [ntasks] tickets
   uint32_t* t_end;             // [ntasks]

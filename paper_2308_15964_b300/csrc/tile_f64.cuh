@@ -204,95 +204,171 @@ __device__ __forceinline__ void store_block(double* dst, int ld, const double (*
 
 // Unblocked right-looking Cholesky of the w x w block in shared memory
 // (lower).  Returns 0 or the 1-based local column of a pivot that is not > 0
-// (NaN included).  Every thread returns the same value.
-__device__ int potrf_smem(double (*a)[kLds], int w, int* s_info) {
-  const int tid = threadIdx.x;
-  if (tid == 0) *s_info = 0;
+// (NaN included).  Every thread returns the same value.  The columns stay
+// unscaled while the trailing matrix is updated (S_ic -= S_ij S_cj / S_jj,
+// with the correctly rounded reciprocal of each pivot taken once), so the
+// chain per column is one reciprocal (about 730 clocks) and two dependent
+// FP64 operations instead of a square root and a division (about 2400); at
+// the end l_jj = sqrt(S_jj) and l_ij = S_ij (1 / l_jj).
+// `rc` is w doubles of scratch.
+__device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    const double d = a[0][0];
+    *s_info = d > 0.0 ? 0 : 1;
+    rc[0] = __drcp_rn(d);
+  }
   __syncthreads();
   for (int j = 0; j < w; ++j) {
-    if (tid == 0) {
-      const double d = a[j][j];
-      if (!(d > 0.0)) *s_info = j + 1;
-      else a[j][j] = sqrt(d);
-    }
-    __syncthreads();
     if (*s_info) return *s_info;
-    const double ljj = a[j][j];
-    for (int i = j + 1 + tid; i < w; i += kThreads) a[i][j] = a[i][j] / ljj;
-    __syncthreads();
-    const int t = w - j - 1;  // trailing lower triangle, rows/cols j+1..w-1
-    for (int e = tid; e < t * t; e += kThreads) {
-      const int i = j + 1 + e / t, c = j + 1 + e % t;
-      if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+    const double r = rc[j];
+    // Trailing lower triangle (rows and columns j+1..w-1, column <= row).
+    // Local row p is paired with row t-1-p, so every pair holds t+1 entries
+    // and no lane idles on the upper half.  Entry (j+1, j+1) is the first of
+    // thread 0, which takes the next pivot's reciprocal right after it.
+    const int t = w - j - 1;
+    for (int p = warp; p < (t + 1) / 2; p += kThreads / 32) {
+      const int ra = p, rb = t - 1 - p;
+      const int na = ra + 1, nb = rb != ra ? rb + 1 : 0;
+      for (int q = lane; q < na + nb; q += 32) {
+        const int rr = q < na ? ra : rb, cc = q < na ? q : q - na;
+        const int i = j + 1 + rr, c = j + 1 + cc;
+        a[i][c] = fma(-a[i][j] * r, a[c][j], a[i][c]);
+        if (i == j + 1 && c == j + 1) {
+          const double d = a[i][c];
+          if (d > 0.0) rc[j + 1] = __drcp_rn(d);
+          else *s_info = j + 2;
+        }
+      }
     }
     __syncthreads();
   }
+  for (int j = tid; j < w; j += kThreads) {
+    const double sd = sqrt(a[j][j]);
+    a[j][j] = sd;
+    rc[j] = 1.0 / sd;
+  }
+  __syncthreads();
+  for (int e = tid; e < w * w; e += kThreads) {
+    const int i = e / w, c = e % w;
+    if (i > c) a[i][c] *= rc[c];
+  }
+  __syncthreads();
   return 0;
 }
 
-// In-tile triangular solves.  Each computes the reciprocals of the diagonal
-// once (IEEE division) and scales by them, and scales the next row (column)
-// in the same pass that completes it, so one step costs one barrier and no
-// division on the dependency chain (a FP64 division is a long dependent
-// sequence on this GPU's FP64 pipe).
+// In-tile triangular solves.  On this GPU a dependent FP64 FMA takes about
+// 128 clocks and a FP64 division about 1100, so the substitutions keep
+// divisions and scalings off their dependency chains: prep_lower takes the
+// reciprocals of the diagonal once and scales the strict lower part of L by
+// them (by column for X L^-T and L^-1 X, by row for L^-T X); the solves then
+// carry y_k = x_k l_kk (one FMA per step on the chain) and scale at the end.
+// Narrow shapes run warp-synchronously (shuffles, no block barrier per
+// step): 16-row blocks of X L^-T (rows are independent) and up to 16 columns
+// of L^-1 X and L^-T X (columns are independent).
 
-// X <- X L^{-T} for X (m x w) and L (w x w lower) in shared memory:
-// x_rc = (x_rc - sum_{k<c} x_rk l_ck) / l_cc, right-looking over c.
-__device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
-                             double* rinv) {
+// l (w x w lower, shared memory): rinv[i] = 1 / l_ii; l_rc *= rinv[c] (by
+// column) or rinv[r] (by row) for r > c.  Ends with a barrier.
+__device__ void prep_lower(double (*l)[kLds], int w, double* rinv, bool by_row) {
   const int tid = threadIdx.x;
   for (int i = tid; i < w; i += kThreads) rinv[i] = 1.0 / l[i][i];
   __syncthreads();
-  for (int r = tid; r < m; r += kThreads) x[r][0] *= rinv[0];
+  for (int e = tid; e < w * w; e += kThreads) {
+    const int r = e / w, c = e % w;
+    if (c < r) l[r][c] *= rinv[by_row ? r : c];
+  }
   __syncthreads();
+}
+
+// X <- X L^{-T} for X (m x w) and L (w x w lower, scaled by column) in
+// shared memory: y_c = x_c - sum_{k<c} y_k l~_ck, x_c = y_c / l_cc.
+__device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], const double* rinv,
+                             int m, int w) {
+  const int tid = threadIdx.x;
+  if (m <= 16) {  // half-warp per row; lane q holds columns q, q+16, q+32, q+48
+    const int r = tid >> 4, q = tid & 15;
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = q + 16 * j < w ? x[r][q + 16 * j] : 0.0;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      for (int cl = 0; cl < 16; ++cl) {
+        const int c = 16 * jj + cl;
+        if (c >= w) break;
+        const double yc = __shfl_sync(0xffffffffu, v[jj], cl, 16);
+#pragma unroll
+        for (int j = jj; j < 4; ++j) {
+          const int cc = q + 16 * j;
+          if (cc > c && cc < w) v[j] = fma(-yc, l[cc][c], v[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (q + 16 * j < w) x[r][q + 16 * j] = v[j] * rinv[q + 16 * j];
+    __syncthreads();
+    return;
+  }
   for (int c = 0; c + 1 < w; ++c) {
     const int t = w - c - 1;
+#pragma unroll 4
     for (int e = tid; e < m * t; e += kThreads) {
       const int r = e / t, cc = c + 1 + e % t;
-      const double v = fma(-x[r][c], l[cc][c], x[r][cc]);
-      x[r][cc] = cc == c + 1 ? v * rinv[cc] : v;
+      x[r][cc] = fma(-x[r][c], l[cc][c], x[r][cc]);
     }
     __syncthreads();
   }
+  for (int e = tid; e < m * w; e += kThreads) x[e / w][e % w] *= rinv[e % w];
+  __syncthreads();
 }
 
-// X <- L^{-1} X for L (m x m lower) and X (m x w) in shared memory (forward
-// substitution on every column).
-__device__ void trsm_ln_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
-                             double* rinv) {
+// X <- L^{-1} X (forward, L scaled by column) or X <- L^{-T} X (backward, L
+// scaled by row) for L (m x m lower) and X (m x w) in shared memory.
+template <bool kTrans>
+__device__ void trsm_left_smem(double (*x)[kLds], const double (*l)[kLds], const double* rinv,
+                               int m, int w) {
   const int tid = threadIdx.x;
-  for (int i = tid; i < m; i += kThreads) rinv[i] = 1.0 / l[i][i];
-  __syncthreads();
-  for (int c = tid; c < w; c += kThreads) x[0][c] *= rinv[0];
-  __syncthreads();
-  for (int i = 0; i + 1 < m; ++i) {
-    const int t = m - i - 1;
+  if (w <= 16) {  // warp per column (and the column 8 to its right); 2 rows per lane
+    const int warp = tid >> 5, lane = tid & 31, c0 = warp, c1 = warp + 8;
+    const bool two = c1 < w;
+    if (c0 < w) {
+      double a0 = x[lane][c0], a1 = x[lane + 32][c0];
+      double b0 = two ? x[lane][c1] : 0.0, b1 = two ? x[lane + 32][c1] : 0.0;
+      for (int s = 0; s < m; ++s) {
+        const int i = kTrans ? m - 1 - s : s;
+        const double ya = __shfl_sync(0xffffffffu, i < 32 ? a0 : a1, i & 31);
+        const double l0 = kTrans ? l[i][lane] : l[lane][i];
+        const double l1 = kTrans ? l[i][lane + 32] : l[lane + 32][i];
+        const bool u0 = kTrans ? lane < i : lane > i, u1 = kTrans ? lane + 32 < i : lane + 32 > i;
+        if (u0) a0 = fma(-l0, ya, a0);
+        if (u1) a1 = fma(-l1, ya, a1);
+        if (two) {
+          const double yb = __shfl_sync(0xffffffffu, i < 32 ? b0 : b1, i & 31);
+          if (u0) b0 = fma(-l0, yb, b0);
+          if (u1) b1 = fma(-l1, yb, b1);
+        }
+      }
+      x[lane][c0] = a0 * rinv[lane];
+      x[lane + 32][c0] = a1 * rinv[lane + 32];
+      if (two) {
+        x[lane][c1] = b0 * rinv[lane];
+        x[lane + 32][c1] = b1 * rinv[lane + 32];
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  for (int s = 0; s + 1 < m; ++s) {
+    const int i = kTrans ? m - 1 - s : s, t = m - 1 - s;  // rows still to update
+#pragma unroll 4
     for (int e = tid; e < t * w; e += kThreads) {
-      const int r = i + 1 + e / w, c = e % w;
-      const double v = fma(-l[r][i], x[i][c], x[r][c]);
-      x[r][c] = r == i + 1 ? v * rinv[r] : v;
+      const int r = kTrans ? e / w : i + 1 + e / w, c = e % w;
+      x[r][c] = fma(-(kTrans ? l[i][r] : l[r][i]), x[i][c], x[r][c]);
     }
     __syncthreads();
   }
-}
-
-// X <- L^{-T} X for L (m x m lower) and X (m x w) in shared memory (back
-// substitution: x_i = (x_i - sum_{k>i} l_ki x_k) / l_ii).
-__device__ void trsm_lt_smem(double (*x)[kLds], const double (*l)[kLds], int m, int w,
-                             double* rinv) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < m; i += kThreads) rinv[i] = 1.0 / l[i][i];
+  for (int e = tid; e < m * w; e += kThreads) x[e / w][e % w] *= rinv[e / w];
   __syncthreads();
-  for (int c = tid; c < w; c += kThreads) x[m - 1][c] *= rinv[m - 1];
-  __syncthreads();
-  for (int i = m - 1; i > 0; --i) {
-    for (int e = tid; e < i * w; e += kThreads) {
-      const int r = e / w, c = e % w;
-      const double v = fma(-l[i][r], x[i][c], x[r][c]);
-      x[r][c] = r == i - 1 ? v * rinv[r] : v;
-    }
-    __syncthreads();
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -321,7 +397,7 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
     case 0: {  // factor the diagonal block
       load_block(s.l, ajj, lda, w, w);
       __syncthreads();
-      const int info = potrf_smem(s.l, w, &s.info);
+      const int info = potrf_smem(s.l, w, &s.info, s.rinv);
       if (info) return jb + info;
       store_block(ajj, lda, s.l, w, w, true);
       __syncthreads();
@@ -330,11 +406,13 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
     case 1: {  // row blocks below the diagonal block: X <- X L_jj^{-T}
       const int rb = fine ? 16 : kBlk;
       load_block(s.l, ajj, lda, w, w);
+      __syncthreads();
+      prep_lower(s.l, w, s.rinv, false);
       for (uint32_t u = u0; u < u1; ++u) {
         const int ib = jb + w + rb * (int)u, mb = min(rb, n - ib);
         load_rows(s.x, a + (size_t)ib * lda + jb, lda, mb, w);
         __syncthreads();
-        trsm_rt_smem(s.x, s.l, mb, w, s.rinv);
+        trsm_rt_smem(s.x, s.l, s.rinv, mb, w);
         store_rows(a + (size_t)ib * lda + jb, lda, s.x, mb, w);
         __syncthreads();
       }
@@ -374,12 +452,14 @@ __device__ void op_trsm_units(const TileDesc& Lt, const TileDesc& At, uint32_t p
   const int rb = fine ? 16 : kBlk;
   if (phase % 2 == 0) {  // row-block units
     load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+    __syncthreads();
+    prep_lower(s.l, w, s.rinv, false);
     for (uint32_t u = u0; u < u1; ++u) {
       const int ib = rb * (int)u, mb = min(rb, m - ib);
       double* x = a + (size_t)ib * lda + jb;
       load_rows(s.x, x, lda, mb, w);
       __syncthreads();
-      trsm_rt_smem(s.x, s.l, mb, w, s.rinv);
+      trsm_rt_smem(s.x, s.l, s.rinv, mb, w);
       store_rows(x, lda, s.x, mb, w);
       __syncthreads();
     }
@@ -486,8 +566,8 @@ __device__ void rhs_diag(const double* l, int ldl, double* x, int ldx, int ib, i
     load_block(s.l, l + (size_t)ib * ldl + ib, ldl, mb, mb);
     load_block(s.x, x + (size_t)ib * ldx + c0, ldx, mb, w);
     __syncthreads();
-    if (kTrans) trsm_lt_smem(s.x, s.l, mb, w, s.rinv);
-    else trsm_ln_smem(s.x, s.l, mb, w, s.rinv);
+    prep_lower(s.l, mb, s.rinv, kTrans);
+    trsm_left_smem<kTrans>(s.x, s.l, s.rinv, mb, w);
     store_block(x + (size_t)ib * ldx + c0, ldx, s.x, mb, w, false);
     __syncthreads();
   }
