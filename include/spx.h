@@ -175,8 +175,8 @@ int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
  *             for the other ops; operand shapes must agree.
  *   priority  0 = normal, >0 = high (popped first; a hint, paper section
  *             "Task insertion" / "Scheduling"); >= 2 also marks the task as
- *             on the critical path: its POTRF, TRSM and FP64 SYRK phases are
- *             cut into smaller parts (16-row / 32 x 32 units instead of 64),
+ *             on the critical path: its POTRF, TRSM and FP64 SYRK / GEMM phases
+ *             are cut into smaller parts (16-row / 32 x 32 units instead of 64),
  *             trading some per-part overhead for more SMs on the task.
  *   prec      SPX_F64, or SPX_TF32 / SPX_BF16 for TRSM, SYRK, GEMM_NT_SUB
  *             whose factor tiles have low-precision copies in a matrix

@@ -42,11 +42,11 @@ __device__ void init_run(const DevGraph& g, uint32_t* sh) {
     g.indeg_w[u] = g.indeg[u];
     g.remaining[u] = g.tasks[u].nparts;
   }
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < kQueues; ++q) {
     __syncthreads();
     for (uint32_t u = tid; u < N; u += kDeriveThreads) {
       const TaskDesc& t = g.tasks[u];
-      const bool in_q = g.indeg[u] == 0 && (q == 0 ? t.prio != 0 : t.prio == 0);
+      const bool in_q = g.indeg[u] == 0 && graph_queue(t.prio) == (uint32_t)q;
       g.ucount[u] = in_q ? 1u : 0u;
     }
     __syncthreads();
@@ -60,7 +60,7 @@ __device__ void init_run(const DevGraph& g, uint32_t* sh) {
     }
     for (uint32_t u = tid; u < N; u += kDeriveThreads) {
       const TaskDesc& t = g.tasks[u];
-      const bool in_q = g.indeg[u] == 0 && (q == 0 ? t.prio != 0 : t.prio == 0);
+      const bool in_q = g.indeg[u] == 0 && graph_queue(t.prio) == (uint32_t)q;
       if (in_q) g.queue[q][g.ucount[u]] = (u << kPartBits) | (t.nparts - 1);
     }
     if (tid == 0) {

@@ -44,8 +44,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // for its first region).  Offsets in bytes, 256-aligned.
 struct Layout {
   size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
-  size_t queue0, queue1, t_start, ff_end;
-  size_t rs, locks, t_end, trace, phase, qclaim0, qclaim1, zero_end;
+  size_t queue[kQueues], t_start, ff_end;
+  size_t rs, locks, t_end, trace, phase, qclaim[kQueues], zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
@@ -66,8 +66,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.rec_mode = take(M);
   L.task_rec = take((N + 1) * 4);
   L.upload_end = o;
-  L.queue0 = take(Q * 4);
-  L.queue1 = take(Q * 4);
+  for (int q = 0; q < kQueues; ++q) L.queue[q] = take(Q * 4);
   L.t_start = take(N * 4);
   L.ff_end = o;
   L.rs = take(sizeof(RunState));
@@ -75,8 +74,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.t_end = take(N * 4);
   L.trace = take(trace ? N * 32 : 0);
   L.phase = take(N * 4);
-  L.qclaim0 = take(Q * 4);
-  L.qclaim1 = take(Q * 4);
+  for (int q = 0; q < kQueues; ++q) L.qclaim[q] = take(Q * 4);
   L.zero_end = o;
   L.hptr = take((H + 1) * 4);
   L.s_task = take(M * 4);
@@ -119,7 +117,7 @@ struct spx_graph {
   std::vector<uint32_t> rec_handle, rec_seq, task_rec{0};
   std::vector<uint8_t> rec_mode;
   unsigned long long cand_edges = 0;
-  unsigned long long items[2] = {0, 0};  // queue entries per priority
+  unsigned long long items[kQueues] = {0, 0, 0};  // queue parts per graph queue
 
   // device
   int device = -1;
@@ -254,7 +252,8 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   if (rc != SPX_OK) return rc;
   const size_t N = g->tasks.size(), H = g->tiles.size(), M = g->rec_handle.size();
   const size_t E = std::max<unsigned long long>(g->cand_edges, 1);
-  size_t Q = std::max<unsigned long long>(std::max(g->items[0], g->items[1]), 1);
+  size_t Q = std::max<unsigned long long>(
+      std::max(std::max(g->items[0], g->items[1]), g->items[2]), 1);
   if (g->cfg.queue_capacity > 0) Q = (size_t)g->cfg.queue_capacity;
   if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
   const Layout L = make_layout(N, H, M, E, Q, g->maps.size(), g->cfg.trace != 0);
@@ -319,10 +318,10 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.rec_seq = (const uint32_t*)(D + L.rec_seq);
   d.rec_mode = (const uint8_t*)(D + L.rec_mode);
   d.task_rec = (const uint32_t*)(D + L.task_rec);
-  d.queue[0] = (uint32_t*)(D + L.queue0);
-  d.queue[1] = (uint32_t*)(D + L.queue1);
-  d.qclaim[0] = (uint32_t*)(D + L.qclaim0);
-  d.qclaim[1] = (uint32_t*)(D + L.qclaim1);
+  for (int q = 0; q < kQueues; ++q) {
+    d.queue[q] = (uint32_t*)(D + L.queue[q]);
+    d.qclaim[q] = (uint32_t*)(D + L.qclaim[q]);
+  }
   d.t_start = (uint32_t*)(D + L.t_start);
   d.rs = (RunState*)(D + L.rs);
   d.locks = (uint32_t*)(D + L.locks);
@@ -353,7 +352,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
 int reset_run_state(spx_graph* g, cudaStream_t st) {
   const Layout& L = g->lay;
   char* D = (char*)g->dmem;
-  cudaError_t e = cudaMemsetAsync(D + L.queue0, 0xFF, L.ff_end - L.queue0, st);
+  cudaError_t e = cudaMemsetAsync(D + L.queue[0], 0xFF, L.ff_end - L.queue[0], st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D + L.rs, 0, L.zero_end - L.rs, st);
   return e == cudaSuccess ? SPX_OK : cuda_fail(e);
 }
@@ -498,7 +497,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   TaskDesc t{};
   t.op = (uint8_t)op;
   t.prec = (uint8_t)prec;
-  t.prio = priority > 0 ? 1 : 0;
+  t.prio = (uint8_t)(priority > 2 ? 2 : priority);
   t.flags = priority >= 2 ? kFlagFine : 0;
   for (int i = 0; i < k; ++i)
     if (mm[i] == SPX_COMMUTATIVE_WRITE) t.flags |= kFlagComm;
@@ -537,7 +536,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   g->task_rec.push_back((uint32_t)g->rec_handle.size());
   g->tasks.push_back(t);
-  g->items[t.prio ? 0 : 1] += items;
+  g->items[graph_queue(t.prio)] += items;
   if (prec != SPX_F64) g->has_tc = true;
   g->uploaded = false;
   if (out_task) *out_task = tid;
@@ -767,7 +766,8 @@ int spx_graph_stats(spx_graph_t g, long long* out, int n) {
   const RunState& r = *g->host_rs;
   const long long v[9] = {(long long)r.parts_done, (long long)r.hiwater, (long long)r.empty_pops,
                           (long long)r.ctas, (long long)r.busy_cycles, (long long)r.total_cycles,
-                          (long long)g->dg.qcap, (long long)r.tail[0].v, (long long)r.tail[1].v};
+                          (long long)g->dg.qcap, (long long)(r.tail[0].v + r.tail[1].v),
+                          (long long)r.tail[2].v};
   for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
   return SPX_OK;
 }
@@ -832,7 +832,7 @@ int spx_graph_clear(spx_graph_t g) {
   g->rec_mode.clear();
   g->task_rec.assign(1, 0);
   g->cand_edges = 0;
-  g->items[0] = g->items[1] = 0;
+  g->items[0] = g->items[1] = g->items[2] = 0;
   g->uploaded = false;
   g->derived = false;
   g->nedges = -1;
@@ -876,6 +876,6 @@ int spx_graph_view(spx_graph_t g, spx::GraphView* v) {
   v->nrec = g->rec_handle.size();
   v->task_rec = g->task_rec.data();
   v->cand_edges = g->cand_edges;
-  v->items = g->items[0] + g->items[1];
+  v->items = g->items[0] + g->items[1] + g->items[2];
   return SPX_OK;
 }

@@ -80,7 +80,7 @@ __device__ uint32_t pop(const DevGraph& g, uint32_t& empties) {
   uint32_t iter = 0;
   for (;;) {
     if (ld_volatile(&rs->abort)) return kExit;
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kQueues; ++q) {
       uint32_t h = ld_volatile(&rs->head[q].v);
       while (h < min(ld_volatile(&rs->tail[q].v), g.qcap)) {
         // Slot h holds one phase of a task; its parts are claimed with
@@ -130,11 +130,11 @@ __device__ void release(const DevGraph& g, uint32_t task) {
       ready = atomicSub(&g.indeg_w[s], 1u) == 1u;
       if (ready) {
         np = g.tasks[s].nparts;
-        pq = g.tasks[s].prio ? 0u : 1u;
+        pq = graph_queue(g.tasks[s].prio);
       }
     }
     __threadfence();  // order the predecessors' data before the queue entries
-    for (uint32_t q = 0; q < 2; ++q) {
+    for (uint32_t q = 0; q < (uint32_t)kQueues; ++q) {
       const bool mine = ready && pq == q;
       const uint32_t cnt = mine ? 1u : 0u;  // one entry: phase 0 of task s
       uint32_t incl = cnt;
@@ -218,10 +218,12 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
           return ok ? 0 : -2;
         }
       }
-      op_gemm<false, false>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s);
+      op_gemm<false, false>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, -1.0, u0, u1, s,
+                            t.flags & kFlagFine);
       return 0;
     case SPX_OP_GEMM_NN_ADD:
-      op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s);
+      op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s,
+                           t.flags & kFlagFine);
       return 0;
     case SPX_OP_TRSM_L_FWD:
       op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
@@ -284,7 +286,7 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
 // on the critical path) never touches the queue.
 __device__ void push_phase(const DevGraph& g, uint32_t u, uint32_t np, uint32_t prio) {
   if (np <= 1) return;
-  const uint32_t q = prio ? 0u : 1u;
+  const uint32_t q = graph_queue(prio);
   const uint32_t slot = atomicAdd(&g.rs->tail[q].v, 1u);
   atomicMax(&g.rs->hiwater, slot + 1u);
   if (slot >= g.qcap) {

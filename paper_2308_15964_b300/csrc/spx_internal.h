@@ -18,6 +18,13 @@ constexpr uint32_t kMaxParts = 1u << kPartBits;
 constexpr uint32_t kMaxTasks = (1u << (32 - kPartBits)) - 2;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // free queue slot
 constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
+// Work queues of a graph run, popped in this order: critical-path tasks
+// (priority >= 2), high priority, normal.  The server keeps two ring queues
+// (critical and high share the first).
+constexpr int kQueues = 3;
+__host__ __device__ inline uint32_t graph_queue(uint32_t prio) {
+  return prio >= 2 ? 0u : (prio == 1 ? 1u : 2u);
+}
 constexpr int kThreads = 256;             // threads per persistent CTA
 constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 
@@ -26,7 +33,8 @@ constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 // the task in order (no-split graphs and commutative tasks); the arithmetic
 // per unit is the same as when the units are spread over CTAs.  kFlagFine:
 // the task is on the critical path (inserted with priority >= 2): its POTRF,
-// TRSM and FP64 SYRK phases use smaller units so that more SMs share it.
+// TRSM and FP64 SYRK / GEMM phases use smaller units so that more SMs share
+// it.
 enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2, kFlagFine = 4 };
 
 // One registered tile (a data handle of the STF model).
@@ -42,7 +50,7 @@ static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
 
 // One task: op, operands (handles in op order), parts, argument.
 struct TaskDesc {
-  uint8_t op, prec, flags, prio;  // prio: 0 = normal, 1 = high
+  uint8_t op, prec, flags, prio;  // prio: 0 = normal, 1 = high, 2 = critical path
   uint32_t nparts;   // parts of phase 0
   uint32_t h[3];
   uint32_t nphases;  // phases run one after another (1 for serial tasks)
@@ -99,8 +107,8 @@ struct alignas(128) Line {
 };
 
 struct RunState {
-  Line head[2];          // next queue slot to pop (0 = high priority)
-  Line tail[2];          // next queue slot to fill
+  Line head[kQueues];    // next queue slot to pop (0 = most urgent)
+  Line tail[kQueues];    // next queue slot to fill
   Line done;             // finished tasks
   Line ticket;           // global ticket counter
   Line progress;         // %globaltimer >> 10 at the last finished part
@@ -151,11 +159,11 @@ struct DevGraph {
   uint32_t* indeg_w;           // [ntasks] remaining predecessors
   uint32_t* remaining;         // [ntasks] parts of the current phase not finished
   uint32_t* phase;             // [ntasks] current phase of a multi-phase task
-  uint32_t* queue[2];          // [qcap] each
+  uint32_t* queue[kQueues];    // [qcap] each (the server uses the first two)
   // graph runs: an entry is one phase of a task, (task << kPartBits) |
   // (parts - 1); qclaim counts the parts claimed from each slot (atomicAdd,
   // so a wide phase is handed out without a compare-and-swap loop)
-  uint32_t* qclaim[2];         // [qcap] each, zero at the start of a run
+  uint32_t* qclaim[kQueues];   // [qcap] each, zero at the start of a run
   uint32_t* locks;             // [ntiles] owner task + 1, 0 = free
   uint32_t* t_start;           // [ntasks] tickets
   uint32_t* t_end;             // [ntasks]
@@ -186,8 +194,9 @@ struct DevGraph {
 //   TRSM (A m x n, nbc column blocks): for j = 0..nbc-1, phase 2j solves
 //     column block j (64-row units), phase 2j+1 updates the column blocks
 //     l > j (64 x 64 units).
-//   Fine tasks (kFlagFine) use 16-row units for the row solves and the TRSM
-//     updates and 32 x 32 block pairs for the POTRF and SYRK updates: one SM
+//   Fine tasks (kFlagFine) use 16-row units for the row solves, the TRSM
+//     updates and the FP64 GEMMs (16 x 64 blocks), and 32 x 32 block pairs
+//     for the POTRF and SYRK updates: one SM
 //     does about 2 FP64 FMA per clock, so a 64 x 64 x 64 unit alone takes
 //     tens of microseconds, and the critical path is a chain of such units.
 //   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
@@ -258,8 +267,9 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     }
     case SPX_OP_GEMM_NT_SUB:
       if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
-      return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
-    case SPX_OP_GEMM_NN_ADD: return cdiv64(t[h[2]].rows) * cdiv64(t[h[2]].cols);
+      return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
+    case SPX_OP_GEMM_NN_ADD:
+      return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_FWD:
     case SPX_OP_GEMM_BWD:
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);

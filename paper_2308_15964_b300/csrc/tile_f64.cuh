@@ -223,21 +223,26 @@ __device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc) {
     if (*s_info) return *s_info;
     const double r = rc[j];
     // Trailing lower triangle (rows and columns j+1..w-1, column <= row).
-    // Local row p is paired with row t-1-p, so every pair holds t+1 entries
-    // and no lane idles on the upper half.  Entry (j+1, j+1) is the first of
-    // thread 0, which takes the next pivot's reciprocal right after it.
+    // Thread 0 alone updates the next pivot (j+1, j+1) and takes its
+    // reciprocal, the chain of the factorization; warps 1..7 update the
+    // rest, local row p paired with row t-1-p so that every pair holds t+1
+    // entries and no lane idles on the upper half.
     const int t = w - j - 1;
-    for (int p = warp; p < (t + 1) / 2; p += kThreads / 32) {
-      const int ra = p, rb = t - 1 - p;
-      const int na = ra + 1, nb = rb != ra ? rb + 1 : 0;
-      for (int q = lane; q < na + nb; q += 32) {
-        const int rr = q < na ? ra : rb, cc = q < na ? q : q - na;
-        const int i = j + 1 + rr, c = j + 1 + cc;
-        a[i][c] = fma(-a[i][j] * r, a[c][j], a[i][c]);
-        if (i == j + 1 && c == j + 1) {
-          const double d = a[i][c];
-          if (d > 0.0) rc[j + 1] = __drcp_rn(d);
-          else *s_info = j + 2;
+    if (warp == 0) {
+      if (lane == 0 && t > 0) {
+        const double d = fma(-a[j + 1][j] * r, a[j + 1][j], a[j + 1][j + 1]);
+        a[j + 1][j + 1] = d;
+        if (d > 0.0) rc[j + 1] = __drcp_rn(d);
+        else *s_info = j + 2;
+      }
+    } else {
+      for (int p = warp - 1; p < (t + 1) / 2; p += kThreads / 32 - 1) {
+        const int ra = p, rb = t - 1 - p;
+        const int na = ra + 1, nb = rb != ra ? rb + 1 : 0;
+        for (int q = lane + (p == 0 ? 1 : 0); q < na + nb; q += 32) {
+          const int rr = q < na ? ra : rb, cc = q < na ? q : q - na;
+          const int i = j + 1 + rr, c = j + 1 + cc;
+          a[i][c] = fma(-a[i][j] * r, a[c][j], a[i][c]);
         }
       }
     }
@@ -263,9 +268,9 @@ __device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc) {
 // reciprocals of the diagonal once and scales the strict lower part of L by
 // them (by column for X L^-T and L^-1 X, by row for L^-T X); the solves then
 // carry y_k = x_k l_kk (one FMA per step on the chain) and scale at the end.
-// Narrow shapes run warp-synchronously (shuffles, no block barrier per
-// step): 16-row blocks of X L^-T (rows are independent) and up to 16 columns
-// of L^-1 X and L^-T X (columns are independent).
+// They run warp-synchronously (shuffles, no block barrier per step): X L^-T
+// 16 rows at a time (rows are independent), L^-1 X and L^-T X of up to 32
+// columns 16 columns at a time (columns are independent).
 
 // l (w x w lower, shared memory): rinv[i] = 1 / l_ii; l_rc *= rinv[c] (by
 // column) or rinv[r] (by row) for r > c.  Ends with a barrier.
@@ -281,12 +286,15 @@ __device__ void prep_lower(double (*l)[kLds], int w, double* rinv, bool by_row) 
 }
 
 // X <- X L^{-T} for X (m x w) and L (w x w lower, scaled by column) in
-// shared memory: y_c = x_c - sum_{k<c} y_k l~_ck, x_c = y_c / l_cc.
+// shared memory: y_c = x_c - sum_{k<c} y_k l~_ck, x_c = y_c / l_cc.  Rows
+// are independent: 16 at a time, a half-warp per row, lane q holding
+// columns q, q+16, q+32, q+48 (about 2x the FMA rate of a barrier per
+// step over all rows).
 __device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], const double* rinv,
                              int m, int w) {
-  const int tid = threadIdx.x;
-  if (m <= 16) {  // half-warp per row; lane q holds columns q, q+16, q+32, q+48
-    const int r = tid >> 4, q = tid & 15;
+  const int tid = threadIdx.x, q = tid & 15;
+  for (int r0 = 0; r0 < m; r0 += 16) {
+    const int r = r0 + (tid >> 4);
     double v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = q + 16 * j < w ? x[r][q + 16 * j] : 0.0;
@@ -306,30 +314,36 @@ __device__ void trsm_rt_smem(double (*x)[kLds], const double (*l)[kLds], const d
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (q + 16 * j < w) x[r][q + 16 * j] = v[j] * rinv[q + 16 * j];
-    __syncthreads();
-    return;
   }
-  for (int c = 0; c + 1 < w; ++c) {
-    const int t = w - c - 1;
-#pragma unroll 4
-    for (int e = tid; e < m * t; e += kThreads) {
-      const int r = e / t, cc = c + 1 + e % t;
-      x[r][cc] = fma(-x[r][c], l[cc][c], x[r][cc]);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < m * w; e += kThreads) x[e / w][e % w] *= rinv[e % w];
   __syncthreads();
 }
 
 // X <- L^{-1} X (forward, L scaled by column) or X <- L^{-T} X (backward, L
-// scaled by row) for L (m x m lower) and X (m x w) in shared memory.
+// scaled by row) for L (m x m lower, m <= 64) and X (m x w) in shared
+// memory.  Up to 32 columns: 16 at a time, a warp per column and the column
+// 8 to its right, 2 rows per lane, shuffles instead of barriers (columns are
+// independent).  Wider X: one barrier per step over all rows and columns,
+// where the warp form would leave most lanes of the late steps idle.
 template <bool kTrans>
 __device__ void trsm_left_smem(double (*x)[kLds], const double (*l)[kLds], const double* rinv,
                                int m, int w) {
-  const int tid = threadIdx.x;
-  if (w <= 16) {  // warp per column (and the column 8 to its right); 2 rows per lane
-    const int warp = tid >> 5, lane = tid & 31, c0 = warp, c1 = warp + 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (w > 32) {
+    for (int s = 0; s + 1 < m; ++s) {
+      const int i = kTrans ? m - 1 - s : s, t = m - 1 - s;  // rows still to update
+#pragma unroll 4
+      for (int e = tid; e < t * w; e += kThreads) {
+        const int r = kTrans ? e / w : i + 1 + e / w, c = e % w;
+        x[r][c] = fma(-(kTrans ? l[i][r] : l[r][i]), x[i][c], x[r][c]);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < m * w; e += kThreads) x[e / w][e % w] *= rinv[e / w];
+    __syncthreads();
+    return;
+  }
+  for (int cb = 0; cb < w; cb += 16) {
+    const int c0 = cb + warp, c1 = cb + warp + 8;
     const bool two = c1 < w;
     if (c0 < w) {
       double a0 = x[lane][c0], a1 = x[lane + 32][c0];
@@ -355,19 +369,7 @@ __device__ void trsm_left_smem(double (*x)[kLds], const double (*l)[kLds], const
         x[lane + 32][c1] = b1 * rinv[lane + 32];
       }
     }
-    __syncthreads();
-    return;
   }
-  for (int s = 0; s + 1 < m; ++s) {
-    const int i = kTrans ? m - 1 - s : s, t = m - 1 - s;  // rows still to update
-#pragma unroll 4
-    for (int e = tid; e < t * w; e += kThreads) {
-      const int r = kTrans ? e / w : i + 1 + e / w, c = e % w;
-      x[r][c] = fma(-(kTrans ? l[i][r] : l[r][i]), x[i][c], x[r][c]);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < m * w; e += kThreads) x[e / w][e % w] *= rinv[e / w];
   __syncthreads();
 }
 
@@ -503,25 +505,28 @@ __device__ void op_syrk(const TileDesc& Lt, const TileDesc& Ct, uint32_t u0, uin
   }
 }
 
-// Output-block GEMMs; units = 64x64 blocks of C, row-major.
+// Output-block GEMMs; units = 64x64 blocks of C, row-major (16 x 64 blocks
+// for fine tasks).
 template <bool A_T, bool B_KN>
 __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& Ct, int K,
-                        double alpha, uint32_t u0, uint32_t u1, F64Smem& s) {
+                        double alpha, uint32_t u0, uint32_t u1, F64Smem& s, bool fine) {
   const double* a = (const double*)At.ptr;
   const double* b = (const double*)Bt.ptr;
   double* c = (double*)Ct.ptr;
   const uint32_t nbc = (Ct.cols + kBlk - 1) / kBlk;
+  const int rb = fine ? 16 : kBlk;
   for (uint32_t u = u0; u < u1; ++u) {
-    const int r0 = (u / nbc) * kBlk, c0 = (u % nbc) * kBlk;
+    const int r0 = (int)(u / nbc) * rb, c0 = (int)(u % nbc) * kBlk;
     const double* ap = A_T ? a + r0 : a + (size_t)r0 * At.ld;
     const double* bp = B_KN ? b + c0 : b + (size_t)c0 * Bt.ld;
-    const int nb = min(kBlk, Ct.cols - c0);
-    if (nb <= 16)
-      gemm_block<A_T, B_KN, 1>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
-                               min(kBlk, Ct.rows - r0), nb, K, alpha, false, s.gs);
+    double* cp = c + (size_t)r0 * Ct.ld + c0;
+    const int mb = min(rb, Ct.rows - r0), nb = min(kBlk, Ct.cols - c0);
+    if (fine)
+      gemm_block<A_T, B_KN, 4, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
+    else if (nb <= 16)
+      gemm_block<A_T, B_KN, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
     else
-      gemm_block<A_T, B_KN>(c + (size_t)r0 * Ct.ld + c0, Ct.ld, ap, At.ld, bp, Bt.ld,
-                            min(kBlk, Ct.rows - r0), nb, K, alpha, false, s.gs);
+      gemm_block<A_T, B_KN>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
   }
 }
 

@@ -84,7 +84,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
     for (int j = k + 1; j < T && rc == SPX_OK; ++j)
       for (int i = j + 1; i < T && rc == SPX_OK; ++i)
         rc = ins(SPX_OP_GEMM_NT_SUB, {A.at(i, k), A.at(j, k), A.at(i, j)}, {R, R, W},
-                 j == k + 1 ? hi : 0, nullptr, prec);
+                 j == k + 1 ? (i == k + 2 ? crit : hi) : 0, nullptr, prec);
   }
   if (rc == SPX_OK && dev_X) {
     std::vector<unsigned> x(T);
