@@ -235,8 +235,10 @@ int spx_graph_trace(spx_graph_t g, unsigned long long* rec);
  * high-water mark (entries), out[2] pops that found the queue empty,
  * out[3] CTAs used, out[4] busy cycles summed over CTAs, out[5] total
  * cycles summed over CTAs, out[6] queue capacity (entries per priority),
- * out[7] / out[8] entries pushed to the high / normal priority queue.
- * n = number of values wanted (<= 9). */
+ * out[7] / out[8] entries pushed to the high (critical path and high) /
+ * normal priority queues, out[9 + op] busy cycles of the parts of each op
+ * (SPX_OP_*), summed over CTAs.  n = number of values wanted
+ * (<= 9 + SPX_NUM_OPS). */
 int spx_graph_stats(spx_graph_t g, long long* out, int n);
 
 /* Device time of the last execution, from CUDA events recorded on the

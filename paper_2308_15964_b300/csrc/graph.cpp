@@ -764,11 +764,12 @@ int spx_graph_stats(spx_graph_t g, long long* out, int n) {
   if (!g || !out || n < 0) return SPX_ERR_INVALID_ARG;
   if (g->state != kDone) return SPX_ERR_STATE;
   const RunState& r = *g->host_rs;
-  const long long v[9] = {(long long)r.parts_done, (long long)r.hiwater, (long long)r.empty_pops,
-                          (long long)r.ctas, (long long)r.busy_cycles, (long long)r.total_cycles,
-                          (long long)g->dg.qcap, (long long)(r.tail[0].v + r.tail[1].v),
-                          (long long)r.tail[2].v};
-  for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+  long long v[9 + SPX_NUM_OPS] = {
+      (long long)r.parts_done,  (long long)r.hiwater,      (long long)r.empty_pops,
+      (long long)r.ctas,        (long long)r.busy_cycles,  (long long)r.total_cycles,
+      (long long)g->dg.qcap,    (long long)(r.tail[0].v + r.tail[1].v), (long long)r.tail[2].v};
+  for (int op = 0; op < SPX_NUM_OPS; ++op) v[9 + op] = (long long)r.op_cycles[op];
+  for (int i = 0; i < n && i < 9 + SPX_NUM_OPS; ++i) out[i] = v[i];
   return SPX_OK;
 }
 

@@ -579,7 +579,9 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     if (!s_flag) break;
     const int info = skip ? 0 : run_part<kTc>(g, t, phase, part, s, tc);
     __syncthreads();
-    busy += clock64() - c0;
+    const long long dt = clock64() - c0;
+    busy += dt;
+    if (tid == 0) atomicAdd(&rs->op_cycles[t.op & 15], (unsigned long long)dt);
     if (tid == 0) {
       if (info > 0 && kServer) {
         // the request fails; the server and the other requests go on
@@ -694,14 +696,18 @@ constexpr size_t smem_bytes(bool tc) {
             : sizeof(F64Smem);
 }
 
+// Every kernel prefers the largest shared-memory carveout.  (A kernel that
+// allocates tensor memory is held to one CTA per SM by the occupancy rules
+// of this GPU, whatever its shared memory; the FP64 kernel runs two.)
 template <bool kTc>
 void configure() {
-  cudaFuncSetAttribute(persistent_kernel<kTc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem_bytes(kTc));
-  cudaFuncSetAttribute(persistent_kernel<kTc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem_bytes(kTc));
-  cudaFuncSetAttribute(task_kernel<kTc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem_bytes(kTc));
+  const void* fns[3] = {(const void*)persistent_kernel<kTc, false>,
+                        (const void*)persistent_kernel<kTc, true>, (const void*)task_kernel<kTc>};
+  for (const void* f : fns) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(kTc));
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  }
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc, false>, kThreads,
                                                 smem_bytes(kTc));

@@ -125,6 +125,7 @@ struct RunState {
   uint32_t ctas;
   unsigned long long busy_cycles;
   unsigned long long total_cycles;
+  unsigned long long op_cycles[16];  // busy cycles by op (SPX_NUM_OPS <= 16)
 };
 
 // Pointers and sizes handed to the device kernels by value.

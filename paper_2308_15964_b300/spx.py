@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
  OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY) = range(13)
+OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
+            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY")
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK = 0, 1
@@ -219,11 +221,13 @@ class Graph:
         return r
 
     def stats(self):
-        v = np.zeros(9, np.int64)
-        _check(lib.spx_graph_stats(self._h, _ptr(v), 9), "spx_graph_stats")
+        v = np.zeros(9 + len(OP_NAMES), np.int64)
+        _check(lib.spx_graph_stats(self._h, _ptr(v), len(v)), "spx_graph_stats")
         keys = ["parts", "queue_hiwater", "empty_pops", "ctas", "busy_cycles", "total_cycles",
                 "queue_capacity", "pushed_high", "pushed_normal"]
-        return dict(zip(keys, (int(x) for x in v)))
+        out = dict(zip(keys, (int(x) for x in v[:9])))
+        out["op_cycles"] = {nm: int(c) for nm, c in zip(OP_NAMES, v[9:]) if c}
+        return out
 
     def timing(self):
         """(prep_ms, run_ms) of the last execution (device events)."""
