@@ -27,7 +27,7 @@ SRC = os.path.join(HERE, "spx_oracle.cpp")
 
 READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
 (POTRF, TRSM, SYRK, GEMM_NT_SUB, GEMM_NN_ADD, TRSM_L_FWD, GEMM_FWD,
- TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY) = range(13)
+ TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI) = range(15)
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +57,7 @@ def lib():
         L.spxo_potrf.argtypes = [P, ctypes.c_int, ctypes.c_int]
         L.spxo_trsv_lower.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.spxo_trsv_lower_t.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.spxo_trtri.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
         L.spxo_execute.restype = ctypes.c_int
         L.spxo_execute.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P]
         L.spxo_gemm_untiled.argtypes = [P, P, P, ctypes.c_int]
@@ -132,6 +133,38 @@ def cholesky_tasks(T: int, b: int, with_solve: bool = False):
     return tasks
 
 
+def trtri_tasks(T: int):
+    """Inverse of every diagonal factor tile: V_k <- L_kk^{-1}."""
+    return [(TRTRI, [(("A", k, k), READ), (("V", k), WRITE)], 0) for k in range(T)]
+
+
+def solve_inv_tasks(T: int):
+    """Block solve L L^T x = r with the inverses of the diagonal tiles applied
+    as products (y_k = L_kk^{-1} (r_k - sum_j L_kj y_j), then x_k = L_kk^{-T}
+    (y_k - sum_i L_ik^T x_i)).  The right-hand side starts in R; the forward
+    sweep writes y into D, the backward sweep writes x back into R."""
+    tasks = []
+    for k in range(T):
+        tasks.append((TRMM, [(("V", k), READ), (("R", k), READ), (("D", k), WRITE)], 0))
+        for i in range(k + 1, T):
+            tasks.append((GEMM_FWD, [(("A", i, k), READ), (("D", k), READ), (("R", i), WRITE)], 0))
+    for k in range(T - 1, -1, -1):
+        tasks.append((TRMM, [(("V", k), READ), (("D", k), READ), (("R", k), WRITE)], 1))
+        for i in range(k - 1, -1, -1):
+            tasks.append((GEMM_BWD, [(("A", k, i), READ), (("R", k), READ), (("D", i), WRITE)], 0))
+    return tasks
+
+
+def trtri(L: np.ndarray) -> np.ndarray:
+    """Inverse of the lower triangle of L (untiled, forward substitution on
+    the identity)."""
+    n = L.shape[0]
+    L = np.ascontiguousarray(L, np.float64)
+    V = np.zeros((n, n), np.float64)
+    lib().spxo_trtri(_p(L), L.shape[1], _p(V), n, n)
+    return V
+
+
 def gemm_tasks(T: int, commutative: bool = False):
     """Tiled C += A B with one task per (i, j, k), i and j outer, k inner; each
     task depends on the block C_ij it updates (section "Numerical applications")."""
@@ -172,14 +205,19 @@ class _Tile(ctypes.Structure):
 
 def _tile_views(names, mats, b):
     """Tile table for named tiles ("A", i, j) / ("B", ...) / ("C", ...) of square
-    row-major matrices and ("X", i) row blocks of an n x nrhs matrix."""
+    row-major matrices, ("X", i) / ("R", i) / ("D", i) row blocks of n x nrhs
+    matrices and ("V", i) square diagonal-block tiles stacked in an n x b
+    matrix (the inverses of the diagonal factor tiles)."""
     tiles = (_Tile * max(1, len(names)))()
     for name, idx in names.items():
         m = mats[name[0]]
         n_rows, n_cols = m.shape
-        if name[0] == "X":
+        if name[0] in ("X", "R", "D"):
             r0, c0 = name[1] * b, 0
             rows, cols = min(b, n_rows - r0), n_cols
+        elif name[0] == "V":
+            r0, c0 = name[1] * b, 0
+            rows = cols = min(b, n_rows - r0)
         else:
             r0, c0 = name[1] * b, name[2] * b
             rows, cols = min(b, n_rows - r0), min(b, n_cols - c0)

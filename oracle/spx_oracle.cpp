@@ -22,6 +22,9 @@
 //   * spxo_potrf / spxo_trsv_* - unblocked Cholesky (Cholesky-Crout, column
 //                        by column) and forward/back substitution; used both
 //                        as the POTRF tile op and as the untiled reference.
+//   * spxo_trtri       - inverse of a lower-triangular tile by forward
+//                        substitution on the identity (the block solve can
+//                        apply L_kk^{-1} as a product: y_k = L_kk^{-1} b_k).
 //   * metrics          - factor backward error ||A-LL^T||_F/||A||_F,
 //                        normwise backward error of a solve (Rigal-Gaches),
 //                        a Freivalds-style probe; residual sums use the
@@ -64,7 +67,9 @@ enum {
   O_NOP = 9,
   O_SPIN = 10,
   O_COPY = 11,        // Y <- X
-  O_AXPY = 12         // Y <- Y + X
+  O_AXPY = 12,        // Y <- Y + X
+  O_TRMM = 13,        // Y <- T X (arg 0) or T^T X (arg 1), T lower triangular
+  O_TRTRI = 14        // V <- L^{-1}, L lower triangular
 };
 
 // ---------------------------------------------------------------------------
@@ -273,6 +278,31 @@ static void gemm_bwd(const double* l, int ldl, const double* xk, int ldk, double
     }
 }
 
+// Inverse of a lower-triangular L (n x n): column c of V solves L v = e_c by
+// forward substitution (the definition of the inverse, one column at a
+// time).  Entries above the diagonal come out zero.
+void spxo_trtri(const double* l, int ldl, double* v, int n, int ldv) {
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < n; ++i) {
+      double s = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s = s - l[(size_t)i * ldl + k] * v[(size_t)k * ldv + c];
+      v[(size_t)i * ldv + c] = s / l[(size_t)i * ldl + i];
+    }
+}
+
+// Y <- T X or Y <- T^T X (T n x n, X and Y n x nrhs): plain matrix product
+// over the whole of T.
+static void trmm(const double* t, int ldt, bool trans, const double* x, int ldx, double* y,
+                 int ldy, int n, int nrhs) {
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k)
+        s = s + (trans ? t[(size_t)k * ldt + i] : t[(size_t)i * ldt + k]) * x[(size_t)k * ldx + c];
+      y[(size_t)i * ldy + c] = s;
+    }
+}
+
 // A tile: base pointer, shape and leading dimension (row-major).
 typedef struct {
   double* ptr;
@@ -366,6 +396,19 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
             double& y = Y.ptr[(size_t)r * Y.ld + c];
             y = task_op[t] == O_AXPY ? y + v : v;
           }
+        break;
+      }
+      case O_TRMM: {
+        const spxo_tile& Tt = tile(0);
+        const spxo_tile& X = tile(1);
+        const spxo_tile& Y = tile(2);
+        trmm(Tt.ptr, Tt.ld, task_arg[t] != 0, X.ptr, X.ld, Y.ptr, Y.ld, Y.rows, Y.cols);
+        break;
+      }
+      case O_TRTRI: {
+        const spxo_tile& L = tile(0);
+        const spxo_tile& V = tile(1);
+        spxo_trtri(L.ptr, L.ld, V.ptr, L.rows, V.ld);
         break;
       }
       case O_NOP:

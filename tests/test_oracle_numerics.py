@@ -173,3 +173,91 @@ def test_generator_bits():
     ref = G / float(127 * 127 * n)
     ref[np.diag_indices(n)] += 0.5
     assert np.array_equal(A, ref)
+
+
+# ---------------------------------------------------------------------------
+# Inverses of the diagonal tiles and the block solve that applies them.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 5, 40])
+def test_trtri_integer_unit_lower_exact(n):
+    # the inverse of an integer unit-lower matrix is an integer unit-lower
+    # matrix; every intermediate is an exact integer
+    L = unit_lower(n, 3 * n)
+    V = O.trtri(L)
+    assert np.array_equal(L @ V, np.eye(n))
+    assert np.array_equal(V, np.round(V))
+    assert np.array_equal(np.triu(V, 1), np.zeros((n, n)))
+
+
+def test_trtri_power_of_two_diagonal():
+    e = (np.arange(30) % 11) - 5
+    V = O.trtri(np.diag(2.0 ** e))
+    assert np.array_equal(V, np.diag(2.0 ** -e))
+
+
+def test_trtri_against_numpy():
+    A = inputs.spd_matrix(96, 1.0, seed=11).numpy()
+    L = np.linalg.cholesky(A)
+    V = O.trtri(L)
+    Vn = np.linalg.inv(L)
+    assert np.abs(V - Vn).max() <= 1e-13 * np.abs(Vn).max()
+    assert np.abs(L @ V - np.eye(96)).max() <= 1e-14
+
+
+def _solve_inv(L, R, b):
+    """Oracle block solve with the diagonal inverses: R in, R out."""
+    n, nrhs = R.shape
+    T = -(-n // b)
+    V = np.zeros((n, b))
+    D = np.zeros_like(R)
+    Lc = np.ascontiguousarray(L)
+    assert O.execute(O.trtri_tasks(T), {"A": Lc, "V": V}, b) == 0
+    assert O.execute(O.solve_inv_tasks(T), {"A": Lc, "V": V, "R": R, "D": D}, b) == 0
+    return V
+
+
+@pytest.mark.parametrize("n,b,nrhs", [(48, 16, 1), (100, 32, 3), (64, 64, 2)])
+def test_solve_inv_integer_exact(n, b, nrhs):
+    L0 = unit_lower(n, n + 7)
+    A = L0 @ L0.T
+    x0 = np.random.default_rng(2).integers(-3, 4, size=(n, nrhs)).astype(np.float64)
+    L = A.copy()
+    assert O.tiled_cholesky(L, b) == 0
+    R = A @ x0
+    V = _solve_inv(lower(L), R, b)
+    assert np.array_equal(R, x0)
+    # V holds the inverse of each diagonal tile (ragged last tile included)
+    for k in range(-(-n // b)):
+        r = slice(k * b, min(n, k * b + b))
+        m = r.stop - r.start
+        assert np.array_equal(V[r, :m] @ L0[r, r], np.eye(m))
+
+
+@pytest.mark.parametrize("n,b", [(200, 64), (130, 32)])
+def test_solve_inv_matches_substitution(n, b):
+    A = inputs.spd_matrix(n, 1.0, seed=n).numpy()
+    B = inputs.rhs(n, 3, seed=n).numpy()
+    L = A.copy()
+    assert O.tiled_cholesky(L, b) == 0
+    L = lower(L)
+    X1 = B.copy()
+    O.solve_untiled(np.ascontiguousarray(L), X1)
+    X2 = B.copy()
+    _solve_inv(L, X2, b)
+    assert np.abs(X1 - X2).max() <= 1e-12 * np.abs(X1).max()
+    assert O.solve_backward_error(A, X2, B).max() <= 1e-14
+
+
+def test_trmm_plain_product():
+    rng = np.random.default_rng(5)
+    n, r = 24, 4
+    T = np.tril(rng.uniform(-1, 1, (n, n)))
+    X = rng.uniform(-1, 1, (n, r))
+    for arg, ref in ((0, T @ X), (1, T.T @ X)):
+        V = np.ascontiguousarray(T)
+        R = X.copy()
+        D = np.zeros_like(X)
+        tasks = [(O.TRMM, [(("V", 0), O.READ), (("R", 0), O.READ), (("D", 0), O.WRITE)], arg)]
+        assert O.execute(tasks, {"V": V, "R": R, "D": D}, n) == 0
+        assert np.abs(D - ref).max() <= 1e-14 * n
