@@ -36,6 +36,38 @@ import numpy as np
 
 METRIC = "Cholesky GFLOP/s & tasks/s (device DAG vs per-task launch); p50/p99 latency"
 PEAKS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+ROOT = os.path.dirname(os.path.abspath(__file__))
+DRAM_PROFILE = os.path.join(ROOT, "profiles", "persistent_kernel_dram_cholesky_n16384_t512.md")
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the CUDA/C++ sources and public
+    headers the kernels are built from."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2308_15964_b300", "csrc", "*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(path: str = DRAM_PROFILE):
+    """DRAM bytes (read + write) of one launch from a committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0].strip() in ("source-hash", "traffic-bytes-per-launch"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("source-hash") != kernel_source_hash() or "traffic-bytes-per-launch" not in fields:
+        return None
+    return int(fields["traffic-bytes-per-launch"])
 # FP64 SIMT peak: 2 DFMA per clock per SM (measured by spx_probe: 1.127 TFLOP/s
 # at 1942 MHz on 148 SMs) x 2 flop x 148 SMs x 2032 MHz maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2
@@ -264,8 +296,12 @@ def main():
     run_mean = statistics.mean(run_ms)
     achieved = flops / (run_mean * 1e-3) / 1e12
     probe_rate, _ = spx.probe(0, 4000)
+    traffic = measured_traffic() if (n, b) == (16384, 512) else None
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak, "traffic": traffic,
+                       "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                       "from the committed ncu summary of this workload; null when "
+                                       "the kernel sources differ from the captured ones",
                        "kernel": "persistent_kernel (FP64 DFMA tile ops)",
                        "kernel_ms": run_mean,
                        "peak_note": "2 DFMA/clk/SM x 148 SMs x max SM clock (derived); "

@@ -67,6 +67,16 @@ enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
  *   SPX_OP_SPIN         any handles, any modes  busy-waits arg nanoseconds
  *   SPX_OP_COPY         (X:R, Y:W)              Y <- X (same shape)
  *   SPX_OP_AXPY         (X:R, Y:W)              Y <- Y + X (same shape)
+ *   SPX_OP_TRMM         (T:R, X:R, Y:W)         Y <- T X (arg 0) or T^T X
+ *                                               (arg 1); T square, lower
+ *                                               triangular: its entries above
+ *                                               the diagonal must be zero (as
+ *                                               TRTRI leaves them); X and Y
+ *                                               distinct tiles
+ *   SPX_OP_TRTRI        (L_kk:R, V_k:W)         V_k <- L_kk^{-1} (lower
+ *                                               triangle of L_kk; V_k square,
+ *                                               written whole, zero above its
+ *                                               diagonal)
  * A write operand may also be given as SPX_COMMUTATIVE_WRITE; such tasks
  * run as one part and take per-tile locks in ascending handle order (the
  * paper locks data handles sorted by address, section "Internal
@@ -85,7 +95,9 @@ enum {
   SPX_OP_SPIN = 10,
   SPX_OP_COPY = 11,
   SPX_OP_AXPY = 12,
-  SPX_NUM_OPS = 13
+  SPX_OP_TRMM = 13,
+  SPX_OP_TRTRI = 14,
+  SPX_NUM_OPS = 15
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
@@ -303,6 +315,29 @@ int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int 
  * solves of iterative refinement; re-run with spx_graph_reset. */
 int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b, double* dev_X, int nrhs,
                      int ldx, long long* out_ntasks);
+
+/* Insert one TRTRI task per diagonal tile of the factor in dev_L (n x n,
+ * lower, tiles b x b): V_k <- L_kk^{-1} into the square b_k x b_k block at
+ * row k*b of dev_V (n x b FP64 row-major, ld ldv >= b; b_k = b, or the
+ * ragged remainder for the last tile).  The block solve y_k = L_kk^{-1} b_k
+ * can then apply each inverse as a product (spx_solve_inv_insert).
+ * Errors: as spx_tile_register / spx_task_insert. */
+int spx_trtri_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b, double* dev_V, int ldv,
+                     long long* out_ntasks);
+
+/* Insert the block solve L L^T x = r with the diagonal inverses of
+ * spx_trtri_insert applied as products: forward, for k ascending, y_k =
+ * V_k (r_k - sum_{j<k} L_kj y_j); backward, for k descending, x_k = V_k^T
+ * (y_k - sum_{i>k} L_ik^T x_i).  dev_R (n x nrhs, ldx) holds r on entry and
+ * x on exit; dev_D (same shape) receives y.  One TRMM per block step
+ * replaces the 2 nb - 1 dependent phases of a substitution, so the chain of
+ * the solve is shorter; the result equals the substitution's up to rounding
+ * (the products reassociate it).  Used for the correction solves of
+ * iterative refinement; re-run with spx_graph_reset.
+ * Errors: as spx_tile_register / spx_task_insert. */
+int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b, double* dev_V,
+                         int ldv, double* dev_R, double* dev_D, int nrhs, int ldx,
+                         long long* out_ntasks);
 
 /* Insert `sweeps` FP64 iterative-refinement sweeps as tasks (so that they run
  * inside the same graph, e.g. in the server): each sweep is

@@ -149,7 +149,7 @@ int cuda_fail(cudaError_t e) {
 // Operand count, shape and mode checks of the built-in ops.
 int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
                    const unsigned* h, const int* m, int nh) {
-  static const int want_nh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2};
+  static const int want_nh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2};
   if (op == SPX_OP_NOP || op == SPX_OP_SPIN) return SPX_OK;
   if (nh != want_nh[op]) return SPX_ERR_INVALID_ARG;
   for (int i = 0; i < nh; ++i) {
@@ -174,6 +174,8 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     case SPX_OP_GEMM_BWD: ok = R(0) == R(1) && C(0) == R(2) && C(1) == C(2); break;
     case SPX_OP_COPY:
     case SPX_OP_AXPY: ok = R(0) == R(1) && C(0) == C(1); break;
+    case SPX_OP_TRMM: ok = R(0) == C(0) && C(0) == R(1) && R(2) == R(0) && C(2) == C(1); break;
+    case SPX_OP_TRTRI: ok = R(0) == C(0) && R(1) == R(0) && C(1) == C(0); break;
     default: ok = false;
   }
   return ok ? SPX_OK : SPX_ERR_INVALID_ARG;
@@ -787,7 +789,7 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
   if (!f) return SPX_ERR_INVALID_ARG;
   static const char* names[SPX_NUM_OPS] = {"POTRF", "TRSM", "SYRK", "GEMM", "GEMM_NN",
                                            "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
-                                           "NOP", "SPIN", "COPY", "AXPY"};
+                                           "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI"};
   std::fprintf(f, "digraph spx {\n");
   for (size_t u = 0; u < N; ++u)
     std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);

@@ -246,6 +246,13 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_AXPY:
       op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY);
       return 0;
+    case SPX_OP_TRMM:
+      op_trmm(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
+      return 0;
+    case SPX_OP_TRTRI:
+      if (phase == 0) op_identity(T[t.h[1]], u0, u1);
+      else op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase - 1, u0, u1, s);
+      return 0;
     case SPX_OP_NOP:
       return 0;
     case SPX_OP_SPIN:

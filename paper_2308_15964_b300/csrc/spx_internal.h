@@ -201,7 +201,9 @@ struct DevGraph {
 //     does about 2 FP64 FMA per clock, so a 64 x 64 x 64 unit alone takes
 //     tens of microseconds, and the critical path is a chain of such units.
 //   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
-//     blocks.
+//     blocks.  TRMM: one phase, the units of GEMM_FWD.  TRTRI (V <- L^{-1}):
+//     phase 0 writes the identity into V (64-row units), phases 1.. are the
+//     TRSM_L_FWD phases of L V = I.
 //   Block solves (L n x n, X n x r): TRSM_L_FWD, for j = 0..nb-1, phase 2j
 //     solves row block j of X with L_jj (one unit per column block of X),
 //     phase 2j+1 subtracts L_ij X_j from the rows below it; TRSM_LT_BWD does
@@ -240,8 +242,18 @@ __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* 
     case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
+    case SPX_OP_TRTRI: return 2 * cdiv64(t[h[0]].rows);  // identity, then L^{-1} I
     default: return 1;
   }
+}
+
+// Units of phase `phase` of a block solve with an n x n factor and an
+// n x cols right-hand side (forward or backward).
+__host__ __device__ inline uint32_t solve_phase_units(bool fwd, int n, int cols, uint32_t phase) {
+  const uint32_t nb = cdiv64(n), j = phase / 2;
+  if (phase % 2 == 0) return rhs_col_blocks(cols);
+  const int rest = fwd ? n - kBlk * (int)(j + 1) : kBlk * (int)(nb - 1 - j);
+  return rhs_row_units(rest, cols) * rhs_col_blocks(cols);
 }
 
 __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileDesc* t,
@@ -275,15 +287,15 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     case SPX_OP_GEMM_BWD:
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_L_FWD:
-    case SPX_OP_TRSM_LT_BWD: {
-      const int n = t[h[0]].rows, cols = t[h[1]].cols;
-      const uint32_t nb = cdiv64(n), j = phase / 2;
-      if (phase % 2 == 0) return rhs_col_blocks(cols);
-      const int rest = op == SPX_OP_TRSM_L_FWD ? n - kBlk * (int)(j + 1) : kBlk * (int)(nb - 1 - j);
-      return rhs_row_units(rest, cols) * rhs_col_blocks(cols);
-    }
+    case SPX_OP_TRSM_LT_BWD:
+      return solve_phase_units(op == SPX_OP_TRSM_L_FWD, t[h[0]].rows, t[h[1]].cols, phase);
     case SPX_OP_COPY:
     case SPX_OP_AXPY: return cdiv64(t[h[1]].rows);
+    case SPX_OP_TRMM:
+      return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
+    case SPX_OP_TRTRI:  // phase 0 writes the identity (64-row units), then the forward solve
+      return phase == 0 ? cdiv64(t[h[1]].rows)
+                        : solve_phase_units(true, t[h[0]].rows, t[h[1]].cols, phase - 1);
     default: return 1;
   }
 }

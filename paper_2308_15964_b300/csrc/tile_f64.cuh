@@ -41,12 +41,14 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 //   op(A)(i,k) = A_T ? A[k*lda + i] : A[i*lda + k]
 //   op(B)(k,j) = B_KN ? B[k*ldb + j] : B[j*ldb + k]
 // lower: only entries with column <= row are written (diagonal SYRK blocks).
+// set: C = alpha op(A) op(B) instead of C += ... (products into a fresh tile).
 // CJ / RI: output columns / rows per thread (4 / 4: a 64 x 64 block; CJ = 1:
 // at most 16 columns, for right-hand-side blocks; RI = 1 or 2: 16- or
 // 32-row blocks, for the finer parts of the POTRF and TRSM phases).
 template <bool A_T, bool B_KN, int CJ = 4, int RI = 4>
 __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                           int m, int n, int K, double alpha, bool lower, GemmSmem& s) {
+                           int m, int n, int K, double alpha, bool lower, GemmSmem& s,
+                           bool set = false) {
   constexpr int BN = 16 * CJ;  // columns of the block
   constexpr int BM = 16 * RI;  // rows of the block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -98,7 +100,7 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
       const int c = tx + 16 * j;
       if (r < m && c < n && (!lower || c <= r)) {
         double* p = C + (size_t)r * ldc + c;
-        *p = __ldcg(p) + alpha * acc[i][j];
+        *p = set ? alpha * acc[i][j] : __ldcg(p) + alpha * acc[i][j];
       }
     }
   }
@@ -119,7 +121,8 @@ struct NarrowSmem {
 
 template <bool A_T, int BN>
 __device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, const double* B,
-                               int ldb, int m, int n, int K, double alpha, NarrowSmem& s) {
+                               int ldb, int m, int n, int K, double alpha, NarrowSmem& s,
+                               bool set) {
   constexpr int KS = kThreads / (kNarrowRows * BN);
   const int tid = threadIdx.x, c = tid % BN, r = (tid / BN) % kNarrowRows,
             ks = tid / (kNarrowRows * BN);
@@ -153,7 +156,7 @@ __device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, con
     for (int q = 1; q < KS; ++q) v += s.red[tid + q * kNarrowRows * BN];
     if (r < m && c < n) {
       double* p = C + (size_t)r * ldc + c;
-      *p = __ldcg(p) + alpha * v;
+      *p = set ? alpha * v : __ldcg(p) + alpha * v;
     }
   }
   __syncthreads();
@@ -161,11 +164,11 @@ __device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, con
 
 template <bool A_T>
 __device__ void gemm_narrow(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                            int m, int n, int K, double alpha, NarrowSmem& s) {
-  if (n <= 2) gemm_narrow_bn<A_T, 2>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
-  else if (n <= 4) gemm_narrow_bn<A_T, 4>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
-  else if (n <= 8) gemm_narrow_bn<A_T, 8>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
-  else gemm_narrow_bn<A_T, 16>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s);
+                            int m, int n, int K, double alpha, NarrowSmem& s, bool set = false) {
+  if (n <= 2) gemm_narrow_bn<A_T, 2>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
+  else if (n <= 4) gemm_narrow_bn<A_T, 4>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
+  else if (n <= 8) gemm_narrow_bn<A_T, 8>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
+  else gemm_narrow_bn<A_T, 16>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
 }
 
 // Copy an m x n block (row-major, ld) into a shared 64-wide array and back.
@@ -612,6 +615,58 @@ __device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t pha
   }
   rhs_update<true>(l + (size_t)ib * ldl, ldl, x + (size_t)ib * ldx, ldx, x, ldx, ib, cols, mb, u0,
                    u1, s);
+}
+
+// Y <- T X (trans false) or T^T X (trans true) for T (n x n, zero above its
+// diagonal) and X, Y (n x r, distinct tiles); the units of GEMM_FWD.  Each
+// unit covers rows r0..r0+m-1 of Y and multiplies over the part of T that
+// can be nonzero for them: columns [0, r0 + m) of T, or rows [r0, n) of T
+// for the transpose.
+__device__ void op_trmm(const TileDesc& Tt, const TileDesc& Xt, const TileDesc& Yt, bool trans,
+                        uint32_t u0, uint32_t u1, F64Smem& s) {
+  const double* tp = (const double*)Tt.ptr;
+  const double* x = (const double*)Xt.ptr;
+  double* y = (double*)Yt.ptr;
+  const int n = Tt.rows, cols = Yt.cols, ldt = Tt.ld, ldx = Xt.ld, ldy = Yt.ld;
+  const int rb = (int)rhs_unit_rows(cols);
+  const uint32_t ncb = rhs_col_blocks(cols);
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)(u / ncb) * rb, c0 = (int)(u % ncb) * kBlk;
+    const int m = min(rb, n - r0), w = rhs_narrow(cols) ? cols : min(kBlk, cols - c0);
+    double* yp = y + (size_t)r0 * ldy + c0;
+    if (!trans) {  // rows r0.. of T, columns [0, r0 + m)
+      const double* ap = tp + (size_t)r0 * ldt;
+      const int K = r0 + m;
+      if (rhs_narrow(cols))
+        gemm_narrow<false>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, narrow_smem(s), true);
+      else if (w <= 16)
+        gemm_block<false, true, 1>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs, true);
+      else
+        gemm_block<false, true>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs, true);
+    } else {  // columns r0.. of T, rows [r0, n)
+      const double* ap = tp + (size_t)r0 * ldt + r0;
+      const double* bp = x + (size_t)r0 * ldx + c0;
+      const int K = n - r0;
+      if (rhs_narrow(cols))
+        gemm_narrow<true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, narrow_smem(s), true);
+      else if (w <= 16)
+        gemm_block<true, true, 1>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
+      else
+        gemm_block<true, true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
+    }
+  }
+}
+
+// V <- I on 64-row units (phase 0 of TRTRI).
+__device__ void op_identity(const TileDesc& Vt, uint32_t u0, uint32_t u1) {
+  double* v = (double*)Vt.ptr;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)u * kBlk, mb = min(kBlk, Vt.rows - r0);
+    for (int e = threadIdx.x; e < mb * Vt.cols; e += kThreads) {
+      const int r = r0 + e / Vt.cols, c = e % Vt.cols;
+      v[(size_t)r * Vt.ld + c] = r == c ? 1.0 : 0.0;
+    }
+  }
 }
 
 // Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1.

@@ -5,7 +5,9 @@
 //     right-looking, k outer, optionally followed by the block forward and
 //     back solves of A Y = X;
 //   * tiled GEMM C += A B with one task per (i, j, k) that depends on the
-//     block C_ij it updates.
+//     block C_ij it updates;
+//   * the inverses of the diagonal factor tiles (TRTRI) and the block solve
+//     that applies them as products (TRMM), for refinement.
 #include <vector>
 
 #include "spx.h"
@@ -133,6 +135,98 @@ extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int
   if (!dev_X) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_L, n, ld, b, nullptr, 0, false, dev_X, nrhs, ldx, 1, SPX_F64,
                          out_ntasks);
+}
+
+namespace {
+
+// Square b_k x b_k blocks stacked in an n x b matrix (row block k at row
+// k*b): the inverses of the diagonal factor tiles.
+int register_diag_blocks(spx_graph_t g, double* base, int n, int ld, int b,
+                         std::vector<unsigned>& out) {
+  const int T = (n + b - 1) / b;
+  out.assign(T, 0);
+  for (int k = 0; k < T; ++k) {
+    const int r = n - k * b < b ? n - k * b : b;
+    const int rc = spx_tile_register(g, base + (size_t)k * b * ld, r, r, ld, SPX_DT_F64, nullptr, 0,
+                                     &out[k]);
+    if (rc != SPX_OK) return rc;
+  }
+  return SPX_OK;
+}
+
+// Row blocks (b_k x nrhs) of an n x nrhs right-hand side.
+int register_row_blocks(spx_graph_t g, double* base, int n, int nrhs, int ld, int b,
+                        std::vector<unsigned>& out) {
+  const int T = (n + b - 1) / b;
+  out.assign(T, 0);
+  for (int k = 0; k < T; ++k) {
+    const int r = n - k * b < b ? n - k * b : b;
+    const int rc = spx_tile_register(g, base + (size_t)k * b * ld, r, nrhs, ld, SPX_DT_F64, nullptr,
+                                     0, &out[k]);
+    if (rc != SPX_OK) return rc;
+  }
+  return SPX_OK;
+}
+
+}  // namespace
+
+extern "C" int spx_trtri_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b,
+                                double* dev_V, int ldv, long long* out_ntasks) {
+  if (!g || !dev_L || !dev_V || n < 1 || b < 1 || ldl < n || ldv < (b < n ? b : n))
+    return SPX_ERR_INVALID_ARG;
+  Tiles L;
+  std::vector<unsigned> V;
+  int rc = register_tiles(g, dev_L, n, n, ldl, b, true, L);
+  if (rc == SPX_OK) rc = register_diag_blocks(g, dev_V, n, ldv, b, V);
+  long long count = 0;
+  const int R = SPX_READ, W = SPX_WRITE;
+  for (int k = 0; k < L.T && rc == SPX_OK; ++k) {
+    const unsigned hs[2] = {L.at(k, k), V[k]};
+    const int ms[2] = {R, W};
+    rc = spx_task_insert(g, SPX_OP_TRTRI, hs, ms, 2, 0, SPX_F64, nullptr);
+    if (rc == SPX_OK) ++count;
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b,
+                                    double* dev_V, int ldv, double* dev_R, double* dev_D,
+                                    int nrhs, int ldx, long long* out_ntasks) {
+  if (!g || !dev_L || !dev_V || !dev_R || !dev_D || dev_R == dev_D || n < 1 || b < 1 ||
+      ldl < n || ldv < (b < n ? b : n) || nrhs < 1 || ldx < nrhs)
+    return SPX_ERR_INVALID_ARG;
+  Tiles L;
+  std::vector<unsigned> V, Rb, Db;
+  int rc = register_tiles(g, dev_L, n, n, ldl, b, true, L);
+  if (rc == SPX_OK) rc = register_diag_blocks(g, dev_V, n, ldv, b, V);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_R, n, nrhs, ldx, b, Rb);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_D, n, nrhs, ldx, b, Db);
+  const int R = SPX_READ, W = SPX_WRITE, T = L.T;
+  long long count = 0;
+  auto ins = [&](int op, unsigned h0, unsigned h1, unsigned h2, int prio, long long arg) {
+    const unsigned hs[3] = {h0, h1, h2};
+    const int ms[3] = {R, R, W};
+    unsigned id = 0;
+    int r = spx_task_insert(g, op, hs, ms, 3, prio, SPX_F64, &id);
+    if (r == SPX_OK && arg) r = spx_task_set_arg(g, id, arg);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  // forward: D_k = V_k (R_k - sum_{j<k} L_kj D_j)
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+    rc = ins(SPX_OP_TRMM, V[k], Rb[k], Db[k], 1, 0);
+    for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+      rc = ins(SPX_OP_GEMM_FWD, L.at(i, k), Db[k], Rb[i], i == k + 1 ? 1 : 0, 0);
+  }
+  // backward: R_k = V_k^T (D_k - sum_{i>k} L_ik^T R_i)
+  for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
+    rc = ins(SPX_OP_TRMM, V[k], Db[k], Rb[k], 1, 1);
+    for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
+      rc = ins(SPX_OP_GEMM_BWD, L.at(k, i), Rb[k], Db[i], i == k - 1 ? 1 : 0, 0);
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
 }
 
 extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,

@@ -6,7 +6,9 @@ factor tile, SYRK and GEMM trailing updates on the tensor cores (TF32 or
 BF16 operands, FP32 accumulation) subtracted from the FP64 trailing matrix.
 The first solve uses that factor.  Refinement (classical, on the host loop):
 r = b - A x in FP64 (spx_residual_f64), L L^T d = r with the same factor
-(a second, solve-only graph replayed through a CUDA graph), x += d, until the
+(a second, solve-only graph replayed through a CUDA graph; by default it
+applies the FP64 inverses of the diagonal factor tiles, computed once by a
+TRTRI graph, as products), x += d, until the
 normwise backward error of every right-hand side is <= tol or the iteration
 cap is reached; non-convergence is reported, never hidden.
 """
@@ -68,15 +70,40 @@ def solve_graph(g: spx.Graph, L, b: int, R) -> int:
     return nt.value
 
 
+def trtri_graph(g: spx.Graph, L, b: int, V) -> int:
+    """V (n x b) <- the inverses of the diagonal b x b tiles of L."""
+    n = L.shape[0]
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_trtri_insert(g._h, _p(L), n, L.stride(0), b, _p(V), V.stride(0),
+                                        ctypes.byref(nt)), "spx_trtri_insert")
+    g._keep.extend([L, V])
+    return nt.value
+
+
+def solve_inv_graph(g: spx.Graph, L, b: int, V, R, D) -> int:
+    """Block solve L L^T x = r applying the diagonal inverses V: R in, R out,
+    D scratch (same shape as R)."""
+    n = L.shape[0]
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_solve_inv_insert(g._h, _p(L), n, L.stride(0), b, _p(V), V.stride(0),
+                                            _p(R), _p(D), R.shape[1], R.stride(0),
+                                            ctypes.byref(nt)), "spx_solve_inv_insert")
+    g._keep.extend([L, V, R, D])
+    return nt.value
+
+
 def lowp_dtype(prec: int):
     return torch.bfloat16 if prec == spx.BF16 else torch.float32
 
 
 def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
-                max_iter: int | None = None):
+                max_iter: int | None = None, inverse: bool = True):
     """Solve A0 X = B.  Returns (X, L, info) where L holds the factor (lower
     triangle) and info has 'converged', 'iterations', 'eta' (history of the
-    max normwise backward error), 'factor_ms', 'refine_ms', 'status'."""
+    max normwise backward error), 'factor_ms', 'refine_ms', 'status'.  With
+    `inverse`, the correction solves apply the inverses of the diagonal factor
+    tiles (computed once, FP64, timed in refine_ms) as products; otherwise
+    they substitute."""
     if max_iter is None:
         max_iter = 30 if prec == spx.TF32 else 50
     n, nrhs = B.shape
@@ -94,7 +121,19 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
         return X, A, {"status": rc, "info": info, "converged": False, "iterations": 0, "eta": []}
     R = torch.empty_like(B)
     gs = spx.Graph(cuda_graph=True)
-    solve_graph(gs, A, b, R)
+    if inverse:
+        V = torch.empty((n, min(b, n)), dtype=torch.float64, device=A0.device)
+        D = torch.empty_like(B)
+        gt = spx.Graph()
+        trtri_graph(gt, A, b, V)
+        rc, _ = gt.run()
+        gt.close()
+        if rc != spx.OK:
+            g.close()
+            return X, A, {"status": rc, "converged": False, "iterations": 0, "eta": []}
+        solve_inv_graph(gs, A, b, V, R, D)
+    else:
+        solve_graph(gs, A, b, R)
     anorm = norm_inf(A0)
     norms = torch.empty(3 * nrhs, dtype=torch.float64, device=A0.device)
     history = []

@@ -16,9 +16,9 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 
 READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
- OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY) = range(13)
+ OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI) = range(15)
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
-            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY")
+            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI")
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK = 0, 1
@@ -74,6 +74,8 @@ def _load():
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),
+        "spx_trtri_insert": (I, [P, P, I, I, I, P, I, P]),
+        "spx_solve_inv_insert": (I, [P, P, I, I, I, P, I, P, P, I, I, P]),
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),
         "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
