@@ -462,18 +462,28 @@ def run_mixed(args, world, rank, local):
                          "factor_gflops": n ** 3 / 3 / (fac * 1e-3) / 1e9,
                          "converged": inf["converged"], "iterations": inf["iterations"],
                          "eta_final": inf["eta"][-1] if inf["eta"] else None,
-                         "eta_history": inf["eta"]}
+                         "eta_history": inf["eta"],
+                         "factor_cta_time_share": {k: round(v, 4) for k, v in
+                                                   inf.get("factor_op_share", {}).items()}}
     out["value"] = out["tf32"]["gflops_total"]
     out["ms_per_step"] = out["tf32"]["ms_per_solve"]
     out["clocks"] = clk.summary()
-    trailing_bytes = 16.0 * n ** 3 / (6 * b)
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    hbm = peaks.get("hbm_gbs", 6451.5)
-    out["roofline"] = {"bound": "hbm", "achieved": trailing_bytes / (out["tf32"]["factor_ms"] * 1e-3) / 1e9,
-                       "peak": hbm, "unit": "GB/s",
-                       "frac": trailing_bytes / (out["tf32"]["factor_ms"] * 1e-3) / 1e9 / hbm,
-                       "traffic": None, "kernel": "persistent_kernel<tensor cores> (factorization)",
-                       "note": "algorithmic trailing traffic 16 n^3/(6 b) bytes over the factor time"}
+    # The factor's FP64 work (TRSM b^3 and POTRF b^3/3 per tile, full tiles)
+    # dominates its CTA time (factor_cta_time_share); the trailing updates run
+    # on the tensor cores.  Roofline: that FP64 work over the factor time
+    # against the FP64 DFMA peak.
+    T = n // b
+    fp64_flops = T * (T - 1) / 2 * b ** 3 + T * b ** 3 / 3
+    sms = spx.lib.spx_device_sm_count()
+    peak = FP64_DFMA_PER_CLK_SM * 2 * sms * (out["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e12
+    ach = fp64_flops / (out["tf32"]["factor_ms"] * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                       "frac": ach / peak, "traffic": None,
+                       "kernel": "persistent_kernel<tensor cores> (TF32 factorization)",
+                       "note": "FP64 flops of the factor (TRSM + POTRF tiles, "
+                               f"{fp64_flops / 1e9:.0f} GFLOP) over the TF32 factor time; the "
+                               f"{(n ** 3 / 3 - fp64_flops) / 1e12:.1f} TFLOP of trailing updates run "
+                               "on the tensor cores"}
     if rank == 0:
         print(json.dumps(out))
 

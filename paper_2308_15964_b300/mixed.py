@@ -116,6 +116,8 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
     ev[0].record()
     rc, info = g.run()
     ev[1].record()
+    st = g.stats()
+    share = {k: v / max(1, st["total_cycles"]) for k, v in st["op_cycles"].items()}
     if rc != spx.OK:
         g.close()
         return X, A, {"status": rc, "info": info, "converged": False, "iterations": 0, "eta": []}
@@ -159,7 +161,8 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
     ev[2].record()
     ev[2].synchronize()
     out = {"status": rc, "converged": converged, "iterations": it, "eta": history,
-           "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2])}
+           "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2]),
+           "factor_op_share": share}
     g.close()
     gs.close()
     return X, A, out
