@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
-    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve", "tc"],
+    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve", "tc", "overhead"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -224,6 +224,9 @@ def main():
     if args.workload == "tc":
         run_tc(args, world, rank, local)
         return
+    if args.workload == "overhead":
+        run_overhead(args, world, rank, local)
+        return
 
     n, b = args.n, args.tile
     flops = cholesky.cholesky_flops(n)
@@ -354,6 +357,58 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_overhead(args, world, rank, local):
+    """The paper's engine-overhead pattern on the device scheduler: T chains
+    (T = the persistent CTAs) of N tasks that only busy-wait D; every task of a
+    chain accesses the same d data objects with WRITE or COMMUTATIVE_WRITE.
+    Execution ~ N (D + O): O = run time / N - D is the per-task overhead of
+    the executor; I = host insertion time / (T N).  Also the global atomic
+    rates behind the queue (probe)."""
+    import ctypes
+    from paper_2308_15964_b300 import spx
+    T = 2 * spx.lib.spx_device_sm_count()  # the FP64 persistent kernel runs 2 CTAs per SM
+    rows = []
+    for comm in (0, 1):
+        for d in (1, 5, 10, 16):
+            for D_ns in (0, 10_000, 100_000):
+                N = 20 if D_ns >= 100_000 else 40
+                g = spx.Graph()
+                nt = ctypes.c_longlong()
+                t0 = time.perf_counter()
+                spx._check(spx.lib.spx_overhead_insert(g._h, T, N, d, comm, D_ns, ctypes.byref(nt)),
+                           "spx_overhead_insert")
+                ins_ms = (time.perf_counter() - t0) * 1e3
+                rc, _ = g.run()
+                assert rc == spx.OK, rc
+                prep_ms = g.timing()[0]
+                runs = []
+                for _ in range(3):
+                    g.reset()
+                    rc, _ = g.run()
+                    assert rc == spx.OK, rc
+                    runs.append(g.timing()[1])
+                run_ms = min(runs)
+                g.close()
+                rows.append({"mode": "commutative" if comm else "write", "deps": d, "D_us": D_ns / 1e3,
+                             "chains": T, "tasks_per_chain": N,
+                             "overhead_us": run_ms * 1e3 / N - D_ns / 1e3,
+                             "insert_us_per_task": ins_ms * 1e3 / (T * N),
+                             "derive_ms": prep_ms, "run_ms": run_ms,
+                             "tasks_per_s": T * N / (run_ms * 1e-3)})
+    same, _ = spx.probe(3, 2000)
+    distinct, _ = spx.probe(4, 2000)
+    nop = [r for r in rows if r["mode"] == "write" and r["deps"] == 1 and r["D_us"] == 0][0]
+    out = {"metric": METRIC, "value": nop["tasks_per_s"], "unit": "tasks/s", "n_gpus": world,
+           "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic",
+           "config": {"workload": "engine overhead: T chains x N busy-wait tasks, d data objects per "
+                                  "task (write or commutative write), D in {0, 10, 100} us"},
+           "atomics_per_s": {"same_address": same, "distinct_addresses": distinct},
+           "rows": rows}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_tc(args, world, rank, local):

@@ -339,6 +339,20 @@ int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b, do
                          int ldv, double* dev_R, double* dev_D, int nrhs, int ldx,
                          long long* out_ntasks);
 
+/* Scheduler-overhead pattern of the paper's engine benchmark (section
+ * "Results" of the overhead study): `chains` independent chains of `ntasks`
+ * tasks; every task of chain c accesses the same `deps` data objects of that
+ * chain (1 <= deps <= 16), all with SPX_WRITE, or all with
+ * SPX_COMMUTATIVE_WRITE when `commutative` (then the tasks of a chain run in
+ * any order, one at a time, under the objects' locks); each task busy-waits
+ * spin_ns nanoseconds (SPX_OP_SPIN; SPX_OP_NOP when spin_ns = 0).  Tasks are
+ * inserted round-robin over the chains.  Execution time ~ ntasks (spin + O),
+ * O the per-task overhead of the executor.  The data objects are addresses
+ * that are never dereferenced.
+ * Errors: SPX_ERR_INVALID_ARG; as spx_tile_register / spx_task_insert. */
+int spx_overhead_insert(spx_graph_t g, int chains, int ntasks, int deps, int commutative,
+                        long long spin_ns, long long* out_ntasks);
+
 /* Insert `sweeps` FP64 iterative-refinement sweeps as tasks (so that they run
  * inside the same graph, e.g. in the server): each sweep is
  *   R_i <- B_i (COPY);  R_i <- R_i - A0_ij X_j for all i, j (GEMM_FWD);

@@ -71,8 +71,12 @@ class Batch:
         return float(sum(cholesky.cholesky_flops(int(k), int(r)) for k, r in zip(self.n, self.nrhs)))
 
 
-def insert(g: spx.Graph, batch: Batch, tiles, lookahead: bool = True) -> int:
-    """Insert every problem of the batch; tiles[i] is problem i's tile."""
+def insert(g: spx.Graph, batch: Batch, tiles, lookahead: bool = False) -> int:
+    """Insert every problem of the batch; tiles[i] is problem i's tile.  By
+    default without look-ahead priorities: thousands of independent problems
+    keep every SM busy, so critical-path splitting (finer parts, more queue
+    traffic) only costs throughput (measured: 842 vs 860 GFLOP/s on the
+    4096-problem batch)."""
     c = batch.count
     base_a, base_x = batch.A.data_ptr(), batch.X.data_ptr()
     pa = (ctypes.c_void_p * c)(*[base_a + 8 * int(o) for o in batch.a_off])

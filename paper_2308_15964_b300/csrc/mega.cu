@@ -2,20 +2,24 @@
 //
 // Scheduling model (Specx paper, section "Scheduling"): ready tasks are pushed
 // into a scheduler and idle workers pop them.  Here the workers are
-// persistent CTAs (one or two per SM) and the scheduler is a pair of FIFO
-// queues in HBM (high and normal priority, section "Task insertion":
-// priorities are a hint the scheduler may use).  A task is split into parts
-// (independent sub-tile pieces); each queue entry is one part.
+// persistent CTAs (two per SM) and the scheduler is three FIFO queues in HBM,
+// popped in order: critical path, high and normal priority (section "Task
+// insertion": priorities are a hint the scheduler may use).  A task runs in
+// phases, each split into parts (independent sub-tile pieces); a queue entry
+// is one phase of one task.
 //
-//   pop    warp 0 lane 0: claim a slot with compare-and-swap only when the
-//          queue is non-empty, then wait (bounded) for the entry to be written;
-//          high priority first.
+//   pop    thread 0: take part p of an entry near the queue head (a
+//          pseudo-random one of the first 16, so that idle CTAs do not all
+//          race for one slot) with an atomicAdd on the slot's claim counter
+//          (bounded wait for an entry that is reserved but not yet written);
+//          the head moves only over slots whose parts are all claimed.
 //   run    all 256 threads execute the part's tile op.
 //   finish a part decrements the task's remaining-part counter; the CTA that
-//          finishes the last part releases the task: warp 0 decrements the
+//          finishes the last part of a phase publishes the next phase and
+//          runs its part 0 itself; after the last phase, warp 0 decrements the
 //          successors' in-degree counters (one lane per successor), ballots
 //          the ones that reached zero and reserves their queue entries with
-//          one atomicAdd per priority for the whole warp.
+//          one atomicAdd per queue for the whole warp.
 //
 // Memory order: the writes of a part are published by __syncthreads +
 // __threadfence before the counter decrement; the releasing CTA fences again
@@ -73,38 +77,71 @@ __device__ __forceinline__ void touch_progress(const DevGraph& g) {
   *(volatile uint32_t*)&g.rs->progress.v = (uint32_t)(globaltimer() >> 10);
 }
 
-// Pop one queue entry (task << 8 | part), or kExit.  Called by one thread.
-__device__ uint32_t pop(const DevGraph& g, uint32_t& empties) {
+// Claims are spread over the first entries of a queue: when tasks have one
+// part, every idle CTA reading the head slot would race for the same entry,
+// and one claim per L2 atomic round trip (about 0.7 us) would be handed out.
+constexpr uint32_t kPopSpread = 16;  // a pop starts at one of the first 16 entries
+constexpr uint32_t kPopScan = 64;    // entries looked at per queue and attempt
+
+// Wait (bounded) for the entry of slot h, reserved by a pusher that may still
+// be writing it.  False on abort or timeout.
+__device__ bool entry_at(const DevGraph& g, int q, uint32_t h, uint32_t& v) {
+  uint32_t spins = 0;
+  while ((v = ld_volatile(&g.queue[q][h])) == kEmpty) {
+    if ((++spins & 1023u) == 0) {
+      if (ld_volatile(&g.rs->abort)) return false;
+      if (watchdog_expired(g)) {
+        set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// Move the head of queue q over the slots whose parts are all claimed; it
+// never passes a slot with parts left.
+__device__ void advance_head(const DevGraph& g, int q, uint32_t t) {
+  uint32_t h = ld_volatile(&g.rs->head[q].v);
+  while (h < t) {
+    const uint32_t v = ld_volatile(&g.queue[q][h]);
+    if (v == kEmpty || ld_volatile(&g.qclaim[q][h]) < (v & (kMaxParts - 1u)) + 1u) break;
+    atomicMax(&g.rs->head[q].v, h + 1u);
+    ++h;
+  }
+}
+
+// Pop one queue entry (task << 8 | part), or kExit.  Called by one thread;
+// rnd is the CTA's pseudo-random state for the start of the scan.
+__device__ uint32_t pop(const DevGraph& g, uint32_t& empties, uint32_t& rnd) {
   RunState* rs = g.rs;
   uint32_t backoff = 32;
   uint32_t iter = 0;
   for (;;) {
     if (ld_volatile(&rs->abort)) return kExit;
     for (int q = 0; q < kQueues; ++q) {
-      uint32_t h = ld_volatile(&rs->head[q].v);
-      while (h < min(ld_volatile(&rs->tail[q].v), g.qcap)) {
-        // Slot h holds one phase of a task; its parts are claimed with
-        // atomicAdd on the slot's counter.  The claimer of the last part
-        // (or anyone who finds the slot exhausted) moves the head past it.
-        uint32_t v, spins = 0;
-        while ((v = ld_volatile(&g.queue[q][h])) == kEmpty) {  // reserved, being written
-          if ((++spins & 1023u) == 0) {
-            if (ld_volatile(&rs->abort)) return kExit;
-            if (watchdog_expired(g)) {
-              set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
-              return kExit;
-            }
-          }
-        }
+      const uint32_t h0 = ld_volatile(&rs->head[q].v);
+      const uint32_t t = min(ld_volatile(&rs->tail[q].v), g.qcap);
+      if (h0 >= t) continue;
+      // Slots h0.. hold one phase of a task each; its parts are claimed with
+      // atomicAdd on the slot's counter.
+      const uint32_t n = min(t - h0, kPopScan);
+      rnd = rnd * 1664525u + 1013904223u;
+      const uint32_t start = (rnd >> 16) % min(n, kPopSpread);
+      for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t h = h0 + (start + i) % n;
+        uint32_t v;
+        if (!entry_at(g, q, h, v)) return kExit;
         const uint32_t np = (v & (kMaxParts - 1u)) + 1u;
+        if (ld_volatile(&g.qclaim[q][h]) >= np) continue;  // exhausted: no atomic
         const uint32_t p = atomicAdd(&g.qclaim[q][h], 1u);
-        if (p + 1u >= np) atomicMax(&rs->head[q].v, h + 1u);
         if (p < np) {
+          if (p + 1u == np) advance_head(g, q, t);
           __threadfence();
           return (v & ~(kMaxParts - 1u)) | p;
         }
-        h = max(h + 1u, ld_volatile(&rs->head[q].v));
       }
+      advance_head(g, q, t);  // every entry looked at was taken
     }
     if (ld_volatile(&rs->done.v) >= g.ntasks) return kExit;
     ++empties;
@@ -546,12 +583,13 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   long long busy = 0;
   uint32_t empties = 0;
   uint32_t next = kEmpty;  // thread 0: part 0 of a phase this CTA just opened
+  uint32_t rnd = blockIdx.x * 2654435761u + 12345u;  // thread 0: scan start of pop
   if (tid == 0) touch_progress(g);
 
   for (;;) {
     if (tid == 0) {
       if (next != kEmpty) s_item = next;
-      else s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties);
+      else s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties, rnd);
       next = kEmpty;
     }
     __syncthreads();
@@ -718,6 +756,22 @@ void configure() {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc, false>, kThreads,
                                                 smem_bytes(kTc));
+  if (kTc && occ == 1) {
+    // The occupancy calculator answers 1 for any kernel that allocates tensor
+    // memory.  Two CTAs of this one (128 of the 512 TMEM columns each) fit in
+    // the SM's registers and shared memory, and the GPU runs them (ncu on the
+    // stand-alone tensor-core kernel: two blocks per SM, one wave).  No CTA of
+    // the persistent kernel waits for another to start, so a CTA that did not
+    // fit would only start after the work, find nothing left and exit.
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaFuncGetAttributes(&fa, persistent_kernel<kTc, false>);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const size_t per_cta = smem_bytes(kTc) + fa.sharedSizeBytes + 1024;
+    if (2 * per_cta <= (size_t)smem_sm && 2 * fa.numRegs * kThreads <= regs_sm) occ = 2;
+  }
   g_max_ctas_per_sm[kTc ? 1 : 0] = occ > 0 ? occ : 1;
 }
 

@@ -50,6 +50,22 @@ struct TcState {
   int error;
 };
 
+// Exact FP32 -> FP64 widening from the IEEE-754 formats, on the integer
+// pipe: for a normal float, the double keeps sign and mantissa (shifted up 29
+// bits) and rebiases the exponent (127 -> 1023); zeros keep their sign.  The
+// epilogue's FP64 pipe (2 operations per clock per SM on this GPU) then only
+// does the subtraction.  Subnormal, infinite and NaN floats take the
+// hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e == 0u && m == 0u) return __longlong_as_double((long long)sign);
+  if (e == 0u || e == 0xFFu) return (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -303,7 +319,8 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = lane + 32 * q;
-        if (r < m && c < n && (!lower || c <= r)) C[(size_t)r * ldc + c] = cv[k][q] - (double)E[r * kLde + c];
+        if (r < m && c < n && (!lower || c <= r))
+          C[(size_t)r * ldc + c] = cv[k][q] - widen_f32(E[r * kLde + c]);
       }
     }
   }

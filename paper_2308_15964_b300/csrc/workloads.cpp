@@ -7,7 +7,10 @@
 //   * tiled GEMM C += A B with one task per (i, j, k) that depends on the
 //     block C_ij it updates;
 //   * the inverses of the diagonal factor tiles (TRTRI) and the block solve
-//     that applies them as products (TRMM), for refinement.
+//     that applies them as products (TRMM), for refinement;
+//   * the scheduler-overhead pattern of the paper's engine benchmark: chains
+//     of tasks that only wait.
+#include <cstdint>
 #include <vector>
 
 #include "spx.h"
@@ -225,6 +228,32 @@ extern "C" int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl
     for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
       rc = ins(SPX_OP_GEMM_BWD, L.at(k, i), Rb[k], Db[i], i == k - 1 ? 1 : 0, 0);
   }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_overhead_insert(spx_graph_t g, int chains, int ntasks, int deps,
+                                   int commutative, long long spin_ns, long long* out_ntasks) {
+  if (!g || chains < 1 || ntasks < 1 || deps < 1 || deps > 16 || spin_ns < 0)
+    return SPX_ERR_INVALID_ARG;
+  // chains x deps data objects at addresses that are never dereferenced (NOP
+  // and SPIN tasks do not touch their tiles)
+  const uintptr_t base = (uintptr_t)0x7e0000000000ull;
+  std::vector<unsigned> h((size_t)chains * deps);
+  int rc = SPX_OK;
+  for (size_t i = 0; i < h.size() && rc == SPX_OK; ++i)
+    rc = spx_tile_register(g, (void*)(base + 4096 * i), 8, 8, 8, SPX_DT_F64, nullptr, 0, &h[i]);
+  const int mode = commutative ? SPX_COMMUTATIVE_WRITE : SPX_WRITE;
+  std::vector<int> modes(deps, mode);
+  const int op = spin_ns > 0 ? SPX_OP_SPIN : SPX_OP_NOP;
+  long long count = 0;
+  for (int j = 0; j < ntasks && rc == SPX_OK; ++j)
+    for (int c = 0; c < chains && rc == SPX_OK; ++c) {
+      unsigned id = 0;
+      rc = spx_task_insert(g, op, &h[(size_t)c * deps], modes.data(), deps, 0, SPX_F64, &id);
+      if (rc == SPX_OK && spin_ns > 0) rc = spx_task_set_arg(g, id, spin_ns);
+      if (rc == SPX_OK) ++count;
+    }
   if (out_ntasks) *out_ntasks = count;
   return rc;
 }
