@@ -41,13 +41,15 @@ DRAM_PROFILE = os.path.join(ROOT, "profiles", "persistent_kernel_dram_cholesky_n
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 (first 16 hex digits) of the CUDA/C++ sources and public
-    headers the kernels are built from."""
+    """SHA-256 (first 16 hex digits) of the device sources the kernels are
+    built from: the .cu files and the headers they include (host-only graph
+    builders and bindings do not change a kernel)."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2308_15964_b300", "csrc", "*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    csrc = os.path.join(ROOT, "paper_2308_15964_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   glob.glob(os.path.join(csrc, "*.h")))
     for f in files:
         if os.path.isfile(f):
             h.update(os.path.basename(f).encode())

@@ -363,6 +363,16 @@ int spx_refine_insert(spx_graph_t g, double* dev_A0, int n, int lda, double* dev
                       double* dev_B, double* dev_X, double* dev_R, int nrhs, int ldx, int sweeps,
                       long long* out_ntasks);
 
+/* spx_refine_insert with the correction solves of spx_solve_inv_insert: one
+ * TRTRI task per diagonal factor tile first (V_k <- L_kk^{-1} into dev_V,
+ * n x b, ldv >= b), then each sweep applies the inverses as products, with
+ * dev_D (n x nrhs, ldx) as the forward sweep's output.  Shorter chains per
+ * sweep than the substitution form; same result up to rounding. */
+int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int lda, double* dev_L, int ldl,
+                          int b, double* dev_V, int ldv, double* dev_B, double* dev_X,
+                          double* dev_R, double* dev_D, int nrhs, int ldx, int sweeps,
+                          long long* out_ntasks);
+
 /* Insert the tiled GEMM C += A B of the paper's numerical applications: one
  * GEMM_NN_ADD task per (i, j, k), i and j outer, k inner, each with a WRITE
  * (or, with commutative = 1, a COMMUTATIVE_WRITE) on the block C_ij.  A, B, C

@@ -734,6 +734,7 @@ __global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t 
 }
 
 int g_max_ctas_per_sm[2] = {-1, -1};
+int g_api_ctas_per_sm[2] = {-1, -1};  // what the occupancy calculator guarantees
 int g_sms = -1;
 
 constexpr size_t smem_bytes(bool tc) {
@@ -756,6 +757,7 @@ void configure() {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel<kTc, false>, kThreads,
                                                 smem_bytes(kTc));
+  g_api_ctas_per_sm[kTc ? 1 : 0] = occ > 0 ? occ : 1;
   if (kTc && occ == 1) {
     // The occupancy calculator answers 1 for any kernel that allocates tensor
     // memory.  Two CTAs of this one (128 of the 512 TMEM columns each) fit in
@@ -803,7 +805,10 @@ cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStre
 
 cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st) {
   persistent_max_ctas(nullptr);
-  const int maxc = g_sms * g_max_ctas_per_sm[tc ? 1 : 0];
+  // The server kernel exits when idle and is launched again by the next
+  // submission: it keeps to the occupancy the calculator guarantees, so that
+  // no CTA of an exited launch can start late beside the next one.
+  const int maxc = g_sms * g_api_ctas_per_sm[tc ? 1 : 0];
   int n = num_ctas > 0 ? num_ctas : maxc;
   if (n > maxc) n = maxc;
   if (tc) persistent_kernel<true, true><<<n, kThreads, smem_bytes(true), st>>>(g);

@@ -258,6 +258,60 @@ extern "C" int spx_overhead_insert(spx_graph_t g, int chains, int ntasks, int de
   return rc;
 }
 
+extern "C" int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int lda, double* dev_L,
+                                     int ldl, int b, double* dev_V, int ldv, double* dev_B,
+                                     double* dev_X, double* dev_R, double* dev_D, int nrhs, int ldx,
+                                     int sweeps, long long* out_ntasks) {
+  if (!g || !dev_A0 || !dev_L || !dev_V || !dev_B || !dev_X || !dev_R || !dev_D || n < 1 ||
+      b < 1 || lda < n || ldl < n || ldv < (b < n ? b : n) || nrhs < 1 || ldx < nrhs ||
+      sweeps < 0 || dev_R == dev_D)
+    return SPX_ERR_INVALID_ARG;
+  Tiles A0, L;
+  std::vector<unsigned> V, xb, xx, xr, xd;
+  int rc = register_tiles(g, dev_A0, n, n, lda, b, false, A0);
+  if (rc == SPX_OK) rc = register_tiles(g, dev_L, n, n, ldl, b, true, L);
+  if (rc == SPX_OK) rc = register_diag_blocks(g, dev_V, n, ldv, b, V);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_B, n, nrhs, ldx, b, xb);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_X, n, nrhs, ldx, b, xx);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_R, n, nrhs, ldx, b, xr);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_D, n, nrhs, ldx, b, xd);
+  if (rc != SPX_OK) return rc;
+  const int T = A0.T, R = SPX_READ, W = SPX_WRITE;
+  long long count = 0;
+  auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
+                 int prio, long long arg) {
+    unsigned id = 0;
+    int r = spx_task_insert(g, op, hs.begin(), ms.begin(), (int)hs.size(), prio, SPX_F64, &id);
+    if (r == SPX_OK && arg) r = spx_task_set_arg(g, id, arg);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  for (int k = 0; k < T && rc == SPX_OK; ++k)
+    rc = ins(SPX_OP_TRTRI, {L.at(k, k), V[k]}, {R, W}, 1, 0);
+  for (int sw = 0; sw < sweeps && rc == SPX_OK; ++sw) {
+    // r = b - A0 x
+    for (int i = 0; i < T && rc == SPX_OK; ++i) rc = ins(SPX_OP_COPY, {xb[i], xr[i]}, {R, W}, 0, 0);
+    for (int i = 0; i < T && rc == SPX_OK; ++i)
+      for (int j = 0; j < T && rc == SPX_OK; ++j)
+        rc = ins(SPX_OP_GEMM_FWD, {A0.at(i, j), xx[j], xr[i]}, {R, R, W}, 0, 0);
+    // L L^T d = r with the diagonal inverses: forward into D, backward into R
+    for (int k = 0; k < T && rc == SPX_OK; ++k) {
+      rc = ins(SPX_OP_TRMM, {V[k], xr[k], xd[k]}, {R, R, W}, 1, 0);
+      for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_GEMM_FWD, {L.at(i, k), xd[k], xr[i]}, {R, R, W}, i == k + 1 ? 1 : 0, 0);
+    }
+    for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
+      rc = ins(SPX_OP_TRMM, {V[k], xd[k], xr[k]}, {R, R, W}, 1, 1);
+      for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
+        rc = ins(SPX_OP_GEMM_BWD, {L.at(k, i), xr[k], xd[i]}, {R, R, W}, i == k - 1 ? 1 : 0, 0);
+    }
+    // x += d
+    for (int i = 0; i < T && rc == SPX_OK; ++i) rc = ins(SPX_OP_AXPY, {xr[i], xx[i]}, {R, W}, 0, 0);
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
 extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,
                                int ld, int b, int commutative, long long* out_ntasks) {
   if (!g || !dev_A || !dev_B || !dev_C || n < 1 || b < 1 || ld < n) return SPX_ERR_INVALID_ARG;

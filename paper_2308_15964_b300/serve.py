@@ -4,7 +4,8 @@ continuous-batching server (spx_server_*).
 Each request is one task graph: the tiled Cholesky of its matrix plus the
 block solve of its right-hand sides, in FP64, or in mixed precision (TF32
 tensor-core trailing updates) followed by FP64 refinement sweeps expressed as
-tasks of the same graph.  Requests are admitted in arrival order (no
+tasks of the same graph (their correction solves apply the FP64 inverses of
+the diagonal factor tiles, computed by TRTRI tasks of the graph).  Requests are admitted in arrival order (no
 skipping) when their buffers fit in the HBM budget, an arena allocated once;
 their inputs are staged into the arena by the copy engines (the resident
 kernel holds the SMs).  Latency = completion time - arrival time (host wall
@@ -73,8 +74,10 @@ def request_bytes(n: int, nrhs: int, prec: int) -> int:
     pad = lambda b: (b + 255) // 256 * 256
     if prec == spx.F64:
         return pad(8 * n * n) + pad(8 * n * nrhs)
-    # A (factored), A0 (original), A_lo (FP32 for TF32), B, X, R
-    return 2 * pad(8 * n * n) + pad(4 * n * n) + 3 * pad(8 * n * nrhs)
+    # A (factored), A0 (original), A_lo (FP32 for TF32), V (diagonal-tile
+    # inverses, n x tile), B, X, R, D
+    return (2 * pad(8 * n * n) + pad(4 * n * n) + pad(8 * n * min(tile_for(n, prec), n)) +
+            4 * pad(8 * n * nrhs))
 
 
 class Arena:
@@ -152,16 +155,20 @@ def build_graph(req: Request, arena: Arena, src: Sources, stream, sweeps: int = 
     X = arena.view(o, (n, r))
     o += pad(8 * n * r)
     R = arena.view(o, (n, r))
+    o += pad(8 * n * r)
+    D = arena.view(o, (n, r))
+    o += pad(8 * n * r)
+    vb = min(req.tile, n)
+    V = arena.view(o, (n, vb))
     for dst, s_, rows, cols in ((A, src.A, n, n), (A0, src.A, n, n), (B, src.B, n, r), (X, src.B, n, r)):
         src.stage(dst, s_, rows, cols, stream)
     stream.synchronize()
     mixed.factor_graph(g, A, Alo, req.tile, X, req.prec)
     nt = ctypes.c_longlong()
-    spx._check(spx.lib.spx_refine_insert(g._h, ctypes.c_void_p(A0.data_ptr()), n, n,
-                                         ctypes.c_void_p(A.data_ptr()), n, req.tile,
-                                         ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
-                                         ctypes.c_void_p(R.data_ptr()), r, r, sweeps,
-                                         ctypes.byref(nt)), "spx_refine_insert")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    spx._check(spx.lib.spx_refine_inv_insert(g._h, P(A0), n, n, P(A), n, req.tile, P(V), vb, P(B),
+                                             P(X), P(R), P(D), r, r, sweeps, ctypes.byref(nt)),
+               "spx_refine_inv_insert")
     req.views = {"A": A, "A0": A0, "B": B, "X": X}
     return g
 

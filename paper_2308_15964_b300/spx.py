@@ -76,6 +76,7 @@ def _load():
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),
         "spx_trtri_insert": (I, [P, P, I, I, I, P, I, P]),
         "spx_overhead_insert": (I, [P, I, I, I, I, LL, P]),
+        "spx_refine_inv_insert": (I, [P, P, I, I, P, I, I, P, I, P, P, P, P, I, I, I, P]),
         "spx_solve_inv_insert": (I, [P, P, I, I, I, P, I, P, P, I, I, P]),
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),

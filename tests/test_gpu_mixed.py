@@ -123,3 +123,42 @@ def test_refinement_sweeps_as_tasks(S):
     eta = O.solve_backward_error(A.numpy(), X.cpu().numpy(), B.numpy())
     assert eta.max() <= 1e-14, eta
     g.close()
+
+
+@pytest.mark.parametrize("n,b,nrhs", [(1024, 256, 3), (1000, 256, 8)])
+def test_refinement_sweeps_with_inverses(S, n, b, nrhs):
+    """The same in-graph sweeps with the correction solves applying the FP64
+    inverses of the diagonal tiles (TRTRI tasks, then TRMM products): the
+    backward error reaches the FP64 bound, and the result agrees with the
+    substitution form to rounding."""
+    import ctypes
+    from paper_2308_15964_b300 import mixed
+    A = inputs.spd_matrix(n, 1.0, seed=13)
+    B = inputs.rhs(n, nrhs, seed=13)
+    P = ctypes.c_void_p
+    out = []
+    for inverse in (True, False):
+        Ad, A0, Bd = A.cuda(), A.cuda(), B.cuda()
+        X, R, D = Bd.clone(), torch.empty_like(Bd), torch.empty_like(Bd)
+        V = torch.empty((n, b), dtype=torch.float64, device="cuda")
+        Alo = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+        g = S.Graph()
+        mixed.factor_graph(g, Ad, Alo, b, X, S.TF32)
+        nt = ctypes.c_longlong()
+        if inverse:
+            rc = S.lib.spx_refine_inv_insert(g._h, P(A0.data_ptr()), n, n, P(Ad.data_ptr()), n, b,
+                                             P(V.data_ptr()), b, P(Bd.data_ptr()), P(X.data_ptr()),
+                                             P(R.data_ptr()), P(D.data_ptr()), nrhs, nrhs, 4,
+                                             ctypes.byref(nt))
+        else:
+            rc = S.lib.spx_refine_insert(g._h, P(A0.data_ptr()), n, n, P(Ad.data_ptr()), n, b,
+                                         P(Bd.data_ptr()), P(X.data_ptr()), P(R.data_ptr()), nrhs,
+                                         nrhs, 4, ctypes.byref(nt))
+        assert rc == 0
+        rc, _ = g.run()
+        assert rc == 0
+        g.close()
+        x = X.cpu().numpy()
+        assert O.solve_backward_error(A.numpy(), x, B.numpy()).max() <= 1e-14
+        out.append(x)
+    assert np.abs(out[0] - out[1]).max() <= 1e-11 * np.abs(out[1]).max()
