@@ -325,6 +325,19 @@ def main():
                                     "tasks_per_s": ntasks / (statistics.mean(bms) * 1e-3),
                                     "p99_ms": float(np.percentile(bms, 99)), "steps": len(bms)}
         gb.close()
+        # the paper's GPU set-up: per-task launches over four streams, an event
+        # wait per cross-stream predecessor
+        gs = spx.Graph(executor=spx.EXEC_STREAMS)
+        step(gs)
+        srec = []
+        for _ in range(2):
+            step(gs, srec)
+        sms_ = [r[0] for r in srec]
+        out["baseline_streams"] = {"value": flops / (statistics.mean(sms_) * 1e-3) / 1e9,
+                                   "unit": "GFLOP/s", "ms_per_step": statistics.mean(sms_),
+                                   "tasks_per_s": ntasks / (statistics.mean(sms_) * 1e-3),
+                                   "p99_ms": float(np.percentile(sms_, 99)), "steps": len(sms_)}
+        gs.close()
         out["latency_small"] = small_latency(spx, cholesky, inputs, torch)
 
         # end to end through host buffers: H2D of A, the step, D2H of L
@@ -634,14 +647,16 @@ def run_batch(args, world, rank, local):
 
 def small_latency(spx, cholesky, inputs, torch, reps=200):
     """Latency of the small case (n=512, tile 64, 120 factorization tasks):
-    execute -> wait on a reset graph, persistent vs per-task executor."""
+    execute -> wait on a reset graph, persistent vs the per-task executors
+    (one stream; four streams with event waits)."""
     n, b = 512, 64
     A0 = inputs.spd_matrix(n, 1.0, seed=1, device="cuda")
     A = torch.empty_like(A0)
     res = {}
     for name, ex, rederive in (("persistent", spx.EXEC_PERSISTENT, False),
                                ("persistent_insert_derive", spx.EXEC_PERSISTENT, True),
-                               ("per_task", spx.EXEC_PER_TASK, False)):
+                               ("per_task", spx.EXEC_PER_TASK, False),
+                               ("streams", spx.EXEC_STREAMS, False)):
         g = spx.Graph(executor=ex)
         cholesky.cholesky_graph(g, A, b)
         lat = []

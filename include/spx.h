@@ -115,8 +115,15 @@ enum { SPX_DT_F64 = 0, SPX_DT_F32 = 1, SPX_DT_BF16 = 2 };
 /* Executors.  SPX_EXEC_PERSISTENT is the product: one persistent kernel with a
  * device work queue.  SPX_EXEC_PER_TASK is the comparison baseline: one kernel
  * launch per task, on the given stream, in insertion order (a valid
- * topological order of any STF graph), running the same tile code. */
-enum { SPX_EXEC_PERSISTENT = 0, SPX_EXEC_PER_TASK = 1 };
+ * topological order of any STF graph), running the same tile code.
+ * SPX_EXEC_STREAMS is a second baseline after the paper's GPU set-up (four
+ * streams per GPU, section "Numerical Applications"): the same per-task
+ * launches in insertion order, round-robin over four streams, with one event
+ * wait per predecessor that ran on another stream (the DAG is derived on the
+ * device and read back once); tasks with a commutative write all go to the
+ * first stream, so the members of a commutative run never overlap.
+ * cfg.cuda_graph is ignored for it. */
+enum { SPX_EXEC_PERSISTENT = 0, SPX_EXEC_PER_TASK = 1, SPX_EXEC_STREAMS = 2 };
 
 /* Status codes. */
 enum {

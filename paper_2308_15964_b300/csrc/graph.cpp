@@ -135,6 +135,11 @@ struct spx_graph {
   // CUDA-graph replay of the re-execution sequence (cfg.cuda_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // SPX_EXEC_STREAMS: predecessor lists (host), four streams, events
+  std::vector<uint32_t> pred_ptr, pred;
+  cudaStream_t xs[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> task_ev;
 };
 
 namespace {
@@ -346,6 +351,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   g->lay = L;
   g->uploaded = true;
   g->derived = false;
+  g->pred_ptr.clear();  // the four-stream executor reads the new DAG back
   g->nedges = -1;
   return SPX_OK;
 }
@@ -397,7 +403,8 @@ int spx_graph_create(spx_graph_t* out, const spx_graph_config_t* cfg) {
   spx_config_default(&g->cfg);
   if (cfg) {
     if (cfg->num_ctas < 0 || cfg->queue_capacity < 0 ||
-        (cfg->executor != SPX_EXEC_PERSISTENT && cfg->executor != SPX_EXEC_PER_TASK)) {
+        (cfg->executor != SPX_EXEC_PERSISTENT && cfg->executor != SPX_EXEC_PER_TASK &&
+         cfg->executor != SPX_EXEC_STREAMS)) {
       delete g;
       return SPX_ERR_INVALID_ARG;
     }
@@ -614,6 +621,69 @@ int build_replay(spx_graph* g) {
   return SPX_OK;
 }
 
+// SPX_EXEC_STREAMS set-up: the derived DAG read back once as predecessor
+// lists, the four streams, and the events (created once, reused).
+int prepare_streams(spx_graph* g, cudaStream_t st) {
+  const size_t N = g->tasks.size();
+  cudaError_t e = cudaSuccess;
+  if (g->pred_ptr.size() != N + 1) {
+    e = cudaStreamSynchronize(st);  // the derivation has to finish first
+    if (e != cudaSuccess) return cuda_fail(e);
+    long long ne = 0;
+    int rc = spx_graph_sizes(g, nullptr, &ne, nullptr, nullptr);
+    if (rc != SPX_OK) return rc;
+    std::vector<uint32_t> rp(N + 1), col((size_t)std::max<long long>(ne, 1));
+    e = cudaMemcpy(rp.data(), g->dg.row_ptr, (N + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ne > 0)
+      e = cudaMemcpy(col.data(), g->dg.col, (size_t)ne * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g->pred_ptr.assign(N + 1, 0);
+    for (size_t u = 0; u < N; ++u)
+      for (uint32_t k = rp[u]; k < rp[u + 1]; ++k) ++g->pred_ptr[col[k] + 1];
+    for (size_t v = 0; v < N; ++v) g->pred_ptr[v + 1] += g->pred_ptr[v];
+    g->pred.assign((size_t)std::max<long long>(ne, 1), 0);
+    std::vector<uint32_t> fill(g->pred_ptr.begin(), g->pred_ptr.end() - 1);
+    for (size_t u = 0; u < N; ++u)
+      for (uint32_t k = rp[u]; k < rp[u + 1]; ++k) g->pred[fill[col[k]]++] = (uint32_t)u;
+  }
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    if (!g->xs[i]) e = cudaStreamCreateWithFlags(&g->xs[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    if (!g->join_ev[i]) e = cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess && !g->fork_ev) e = cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming);
+  while (e == cudaSuccess && g->task_ev.size() < N) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) g->task_ev.push_back(ev);
+  }
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+// Per-task launches over four streams (see SPX_EXEC_STREAMS), joined on st.
+cudaError_t launch_streams(spx_graph* g, cudaStream_t st) {
+  persistent_max_ctas(nullptr);
+  const size_t N = g->tasks.size();
+  auto stream_of = [&](size_t u) {
+    return (g->tasks[u].flags & kFlagComm) ? 0 : (int)(u % 4);
+  };
+  cudaError_t e = cudaEventRecord(g->fork_ev, st);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(g->xs[i], g->fork_ev, 0);
+  for (size_t u = 0; u < N && e == cudaSuccess; ++u) {
+    const int si = stream_of(u);
+    for (uint32_t k = g->pred_ptr[u]; k < g->pred_ptr[u + 1] && e == cudaSuccess; ++k)
+      if (stream_of(g->pred[k]) != si) e = cudaStreamWaitEvent(g->xs[si], g->task_ev[g->pred[k]], 0);
+    if (e == cudaSuccess)
+      e = launch_task(g->dg, (uint32_t)u, g->tasks[u], g->tiles.data(), g->has_tc, g->xs[si]);
+    if (e == cudaSuccess) e = cudaEventRecord(g->task_ev[u], g->xs[si]);
+  }
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(g->join_ev[i], g->xs[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->join_ev[i], 0);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
 int spx_graph_execute(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
@@ -626,6 +696,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     if (rc != SPX_OK) return rc;
   }
   const bool replay = g->cfg.cuda_graph && g->state == kFrozen &&
+                      g->cfg.executor != SPX_EXEC_STREAMS &&
                       (g->cfg.executor == SPX_EXEC_PER_TASK || g->derived);
   if (replay) {
     if (!g->gexec) {
@@ -649,6 +720,12 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     if (rc != SPX_OK) return rc;
     e = cudaEventRecord(g->tev[1], st);
     if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->has_tc, st);
+  } else if (g->cfg.executor == SPX_EXEC_STREAMS) {
+    rc = g->derived ? reset_run_state(g, st) : spx_graph_derive(g, stream);
+    if (rc == SPX_OK) rc = prepare_streams(g, st);
+    if (rc != SPX_OK) return rc;
+    e = cudaEventRecord(g->tev[1], st);
+    if (e == cudaSuccess) e = launch_streams(g, st);
   } else {
     if (!g->derived) {
       rc = spx_graph_derive(g, stream);  // also resets the run state
@@ -856,6 +933,12 @@ void spx_graph_destroy(spx_graph_t g) {
   if (g->host_rs) cudaFreeHost(g->host_rs);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  for (int i = 0; i < 4; ++i) {
+    if (g->xs[i]) cudaStreamDestroy(g->xs[i]);
+    if (g->join_ev[i]) cudaEventDestroy(g->join_ev[i]);
+  }
+  if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+  for (cudaEvent_t ev : g->task_ev) cudaEventDestroy(ev);
   if (g->done_ev) cudaEventDestroy(g->done_ev);
   for (int i = 0; i < 3; ++i)
     if (g->tev[i]) cudaEventDestroy(g->tev[i]);

@@ -828,20 +828,23 @@ cudaError_t launch_ring_init(const DevGraph& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_task(const DevGraph& g, uint32_t u, const TaskDesc& t,
+                        const TileDesc* host_tiles, bool tc, cudaStream_t st) {
+  for (uint32_t ph = 0; ph < t.nphases; ++ph) {
+    const uint32_t np =
+        (t.flags & kFlagSerial)
+            ? 1u
+            : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph, t.flags & kFlagFine));
+    if (tc) task_kernel<true><<<np, kThreads, smem_bytes(true), st>>>(g, u, ph);
+    else task_kernel<false><<<np, kThreads, smem_bytes(false), st>>>(g, u, ph);
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
                             const TileDesc* host_tiles, bool tc, cudaStream_t st) {
   persistent_max_ctas(nullptr);
-  for (uint32_t u = 0; u < g.ntasks; ++u) {
-    const TaskDesc& t = host_tasks[u];
-    for (uint32_t ph = 0; ph < t.nphases; ++ph) {
-      const uint32_t np =
-          (t.flags & kFlagSerial)
-              ? 1u
-              : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph, t.flags & kFlagFine));
-      if (tc) task_kernel<true><<<np, kThreads, smem_bytes(true), st>>>(g, u, ph);
-      else task_kernel<false><<<np, kThreads, smem_bytes(false), st>>>(g, u, ph);
-    }
-  }
+  for (uint32_t u = 0; u < g.ntasks; ++u) launch_task(g, u, host_tasks[u], host_tiles, tc, st);
   return cudaGetLastError();
 }
 

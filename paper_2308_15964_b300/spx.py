@@ -21,7 +21,7 @@ OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD",
             "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI")
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
-EXEC_PERSISTENT, EXEC_PER_TASK = 0, 1
+EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
 
 OK, NOT_SPD = 0, 1
 ERR_INVALID_ARG, ERR_BAD_HANDLE, ERR_STATE, ERR_OOM, ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_CUDA, \

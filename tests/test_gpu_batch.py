@@ -70,7 +70,7 @@ def test_per_task_cuda_graph_replay(S):
     bt = Bt.Batch(n, r, seed=6)
     tiles = [64] * len(n)
     outs = []
-    for ex in (S.EXEC_PERSISTENT, S.EXEC_PER_TASK):
+    for ex in (S.EXEC_PERSISTENT, S.EXEC_PER_TASK, S.EXEC_STREAMS):
         g = S.Graph(executor=ex, cuda_graph=True)
         Bt.insert(g, bt, tiles)
         for rep in range(3):
@@ -80,7 +80,8 @@ def test_per_task_cuda_graph_replay(S):
             g.reset()
         outs.append((bt.A.clone(), bt.X.clone()))
         g.close()
-    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    for o in outs[1:]:
+        assert torch.equal(outs[0][0], o[0]) and torch.equal(outs[0][1], o[1])
 
 
 def test_autotune_small(S):

@@ -77,9 +77,10 @@ def test_not_spd_info(S, col):
     rc, info, _, _, g = run_cholesky(A, b)
     assert rc == S.NOT_SPD and info == expect
     g.close()
-    rc, info, _, _, g = run_cholesky(A, b, executor=S.EXEC_PER_TASK)
-    assert rc == S.NOT_SPD and info == expect
-    g.close()
+    for ex in (S.EXEC_PER_TASK, S.EXEC_STREAMS):
+        rc, info, _, _, g = run_cholesky(A, b, executor=ex)
+        assert rc == S.NOT_SPD and info == expect
+        g.close()
 
 
 def test_determinism_and_executors(S):
@@ -88,6 +89,7 @@ def test_determinism_and_executors(S):
     B = inputs.rhs(n, 3, seed=4).numpy()
     ref = run_cholesky(A, b, B)
     outs = [run_cholesky(A, b, B), run_cholesky(A, b, B, executor=S.EXEC_PER_TASK),
+            run_cholesky(A, b, B, executor=S.EXEC_STREAMS),
             run_cholesky(A, b, B, no_split=True), run_cholesky(A, b, B, num_ctas=3),
             run_cholesky(A, b, B, lookahead=False)]
     for o in outs:
