@@ -148,3 +148,44 @@ def test_priority_and_ctas(S):
     check_tickets(g, rp, col)
     assert g.stats()["ctas"] == 1
     g.close()
+
+
+@pytest.mark.parametrize("commutative", [False, True])
+@pytest.mark.parametrize("deps,spin_ns", [(1, 0), (3, 2000), (16, 0)])
+def test_overhead_pattern(S, commutative, deps, spin_ns):
+    """The engine-overhead graph (T chains of N tasks on d objects each): its
+    DAG equals the oracle's for the same access lists, every edge is kept at
+    run time, and the commutative tasks of a chain never overlap."""
+    import ctypes
+    T, N = 7, 5
+    g = S.Graph()
+    nt = ctypes.c_longlong()
+    assert S.lib.spx_overhead_insert(g._h, T, N, deps, int(commutative), spin_ns,
+                                     ctypes.byref(nt)) == 0
+    assert nt.value == T * N
+    mode = O.COMMUTATIVE_WRITE if commutative else O.WRITE
+    # oracle view: task j*T + c accesses objects c*deps .. c*deps + deps - 1
+    t = np.repeat(np.arange(T * N, dtype=np.uint32), deps)
+    k = np.array([(u % T) * deps + d for u in range(T * N) for d in range(deps)], np.uint64)
+    m = np.full(T * N * deps, mode, np.int32)
+    rp, col, _ = check_same(g, T * N, t, k, m)
+    if not commutative:
+        assert [(u, int(col[p])) for u in range(T * N) for p in range(rp[u], rp[u + 1])] == \
+            [(u, u + T) for u in range(T * (N - 1))]
+    else:
+        assert len(col) == 0
+    s, e = check_tickets(g, rp, col)
+    if commutative:
+        for c in range(T):
+            iv = sorted((s[j * T + c], e[j * T + c]) for j in range(N))
+            assert all(iv[i][1] < iv[i + 1][0] for i in range(N - 1))
+    g.close()
+
+
+def test_overhead_pattern_rejects_bad_sizes(S):
+    import ctypes
+    g = S.Graph()
+    nt = ctypes.c_longlong()
+    for args in ((0, 4, 1), (4, 0, 1), (4, 4, 0), (4, 4, 17)):
+        assert S.lib.spx_overhead_insert(g._h, *args, 0, 0, ctypes.byref(nt)) == S.ERR_INVALID_ARG
+    g.close()
