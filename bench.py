@@ -338,6 +338,27 @@ def main():
                                    "tasks_per_s": ntasks / (statistics.mean(sms_) * 1e-3),
                                    "p99_ms": float(np.percentile(sms_, 99)), "steps": len(sms_)}
         gs.close()
+        # one launch per task, the launch sequence replayed through a CUDA graph
+        # (inserted once; re-runs reset and replay)
+        gg = spx.Graph(executor=spx.EXEC_PER_TASK, cuda_graph=True)
+        A.copy_(A0)
+        cholesky.cholesky_graph(gg, A, b)
+        assert gg.run()[0] == spx.OK
+        grec = []
+        for i in range(3):
+            A.copy_(A0)
+            gg.reset()
+            ev[0].record()
+            rc_, _ = gg.run()
+            ev[1].record()
+            ev[1].synchronize()
+            assert rc_ == spx.OK
+            if i > 0:                     # the first reset run captures the graph
+                grec.append(ev[0].elapsed_time(ev[1]))
+        out["baseline_per_task_cudagraph"] = {"value": flops / (statistics.mean(grec) * 1e-3) / 1e9,
+                                              "unit": "GFLOP/s", "ms_per_step": statistics.mean(grec),
+                                              "note": "execution only (the graph is inserted once)"}
+        gg.close()
         out["latency_small"] = small_latency(spx, cholesky, inputs, torch)
 
         # end to end through host buffers: H2D of A, the step, D2H of L
@@ -653,11 +674,12 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
     A0 = inputs.spd_matrix(n, 1.0, seed=1, device="cuda")
     A = torch.empty_like(A0)
     res = {}
-    for name, ex, rederive in (("persistent", spx.EXEC_PERSISTENT, False),
-                               ("persistent_insert_derive", spx.EXEC_PERSISTENT, True),
-                               ("per_task", spx.EXEC_PER_TASK, False),
-                               ("streams", spx.EXEC_STREAMS, False)):
-        g = spx.Graph(executor=ex)
+    for name, ex, rederive, cg in (("persistent", spx.EXEC_PERSISTENT, False, False),
+                                   ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False),
+                                   ("per_task", spx.EXEC_PER_TASK, False, False),
+                                   ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True),
+                                   ("streams", spx.EXEC_STREAMS, False, False)):
+        g = spx.Graph(executor=ex, cuda_graph=cg)
         cholesky.cholesky_graph(g, A, b)
         lat = []
         for i in range(reps + 5):
