@@ -382,11 +382,21 @@ def main():
                       "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
                       "ms_per_step": statistics.mean(e2e)}
         del Ah, Lh
+        sizes = {}
+        for ns in (1024, 2048):
+            if ns < ORACLE_SAMPLE_N:
+                sizes[ns] = cpu_oracle_gflops(ns, b, args.sigma, seed=2)[1]
         gf, dt = cpu_oracle_gflops(ORACLE_SAMPLE_N, b, args.sigma, seed=2)
+        sizes[ORACLE_SAMPLE_N] = dt
         out["cpu_baseline"] = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                                "sample": f"tiled Cholesky oracle, n={ORACLE_SAMPLE_N} tile {b} "
                                          f"(same tile and recipe, {dt:.1f} s on one host core; "
-                                         f"host has {os.cpu_count()} cores)"}
+                                         f"host has {os.cpu_count()} cores)",
+                               "seconds_by_n": {str(k): v for k, v in sizes.items()},
+                               "extrapolated_s_at_n": {
+                                   "n": n, "seconds": dt * (n / ORACLE_SAMPLE_N) ** 3,
+                                   "note": "n^3 extrapolation of the n=%d time, not measured"
+                                           % ORACLE_SAMPLE_N}}
     g.close()
     if rank == 0:
         print(json.dumps(out))
