@@ -4,8 +4,9 @@
 // infinity norm of A, and the update X += alpha D.  The residual reads A once
 // (8 n^2 bytes) and does 2 n^2 nrhs flops; with 8 right-hand sides that is
 // 2 flop per byte, above the B300's FP64 ridge, so it runs on the DFMA pipe:
-// each CTA owns 64 (32 for 16 right-hand sides) rows, stages 128-column slices of X in shared memory, and
-// each warp accumulates 8 (4) rows x nrhs sums in registers.
+// each CTA owns 8 x rows-per-warp rows, stages 128-column slices of X in
+// shared memory, and each warp accumulates rows-per-warp x nrhs sums in
+// registers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,9 +14,12 @@
 
 namespace {
 
-// rows per warp: 8 (4 with 16 right-hand sides, to stay in registers)
+// rows per warp: 8 x NR accumulators at most, and small CTAs for wide
+// right-hand sides, so that the grid has many more CTAs than the GPU holds at
+// once (with 64-row CTAs, n = 32768 gave 512 CTAs of about one per SM: the
+// last of ~3.5 waves ran half empty)
 template <int NR>
-constexpr int rows_per_warp() { return NR >= 16 ? 4 : 8; }
+constexpr int rows_per_warp() { return NR >= 16 ? 1 : (NR >= 8 ? 2 : (NR >= 4 ? 4 : 8)); }
 constexpr int kColSlice = 128;   // columns of X staged per step
 constexpr int kMaxRhs = 16;
 
