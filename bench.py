@@ -563,7 +563,7 @@ def run_mixed(args, world, rank, local):
                          "factor_gflops": n ** 3 / 3 / (fac * 1e-3) / 1e9,
                          "converged": inf["converged"], "iterations": inf["iterations"],
                          "eta_final": inf["eta"][-1] if inf["eta"] else None,
-                         "eta_history": inf["eta"],
+                         "eta_history": inf["eta"], "correction_solve": inf.get("correction"),
                          "factor_cta_time_share": {k: round(v, 4) for k, v in
                                                    inf.get("factor_op_share", {}).items()}}
     out["value"] = out["tf32"]["gflops_total"]

@@ -77,6 +77,11 @@ enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
  *                                               triangle of L_kk; V_k square,
  *                                               written whole, zero above its
  *                                               diagonal)
+ * Operand element types: SPX_DT_F64 throughout, except that GEMM_FWD,
+ * GEMM_BWD and TRMM also take all three operands SPX_DT_F32 (FP32
+ * arithmetic) when the written tile has at most 16 columns, and COPY / AXPY
+ * take X and Y each SPX_DT_F64 or SPX_DT_F32 (FP64 -> FP32 rounds to
+ * nearest, FP32 -> FP64 is exact); anything else is SPX_ERR_INVALID_ARG.
  * A write operand may also be given as SPX_COMMUTATIVE_WRITE; such tasks
  * run as one part and take per-tile locks in ascending handle order (the
  * paper locks data handles sorted by address, section "Internal
@@ -345,6 +350,26 @@ int spx_trtri_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b, double
 int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl, int b, double* dev_V,
                          int ldv, double* dev_R, double* dev_D, int nrhs, int ldx,
                          long long* out_ntasks);
+
+/* The correction step of mixed-precision refinement with the solve in FP32:
+ * COPY tasks round the FP64 residual dev_R (n x nrhs, ldx) into dev_R32, the
+ * block solve of spx_solve_inv_insert runs on FP32 copies of the factor
+ * (dev_L32: n x n row-major FP32, ld ldl, strictly lower tiles read) and of
+ * the diagonal inverses (dev_V32: n x b FP32, ld ldv), with dev_D32 as its
+ * forward result, and AXPY tasks add the correction to dev_X (FP64, ldx):
+ * x <- x + (L L^T)^{-1} r.  The factor of a TF32 / BF16 Cholesky is only
+ * accurate to that precision, so solving for the correction in FP32 does
+ * not slow the refinement, and it runs on the FP32 pipe instead of FP64.
+ * dev_R32 and dev_D32 are n x nrhs FP32 with ld ldx, distinct buffers;
+ * 1 <= nrhs <= 16.  The copies are the caller's (FP64 -> FP32 of L and V,
+ * e.g. with one COPY task each).  No counterpart in the paper (the workload
+ * definition's refinement).
+ * Errors: SPX_ERR_INVALID_ARG for null or aliased pointers, bad sizes or
+ * nrhs > 16; otherwise as spx_tile_register / spx_task_insert. */
+int spx_solve_inv_f32_insert(spx_graph_t g, const float* dev_L32, int n, int ldl, int b,
+                             const float* dev_V32, int ldv, const double* dev_R, float* dev_R32,
+                             float* dev_D32, double* dev_X, int nrhs, int ldx,
+                             long long* out_ntasks);
 
 /* Scheduler-overhead pattern of the paper's engine benchmark (section
  * "Results" of the overhead study): `chains` independent chains of `ntasks`

@@ -157,8 +157,16 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
   static const int want_nh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2};
   if (op == SPX_OP_NOP || op == SPX_OP_SPIN) return SPX_OK;
   if (nh != want_nh[op]) return SPX_ERR_INVALID_ARG;
+  // FP64 throughout, except: the solve updates (GEMM_FWD, GEMM_BWD, TRMM)
+  // also run with all operands FP32 on at most 16 right-hand-side columns,
+  // and COPY / AXPY convert between FP64 and FP32 in either direction.
+  const bool f32_ok = op == SPX_OP_GEMM_FWD || op == SPX_OP_GEMM_BWD || op == SPX_OP_TRMM;
+  const bool conv_ok = op == SPX_OP_COPY || op == SPX_OP_AXPY;
+  const bool all_f32 = f32_ok && dt[h[0]] == SPX_DT_F32;
   for (int i = 0; i < nh; ++i) {
-    if (dt[h[i]] != SPX_DT_F64) return SPX_ERR_INVALID_ARG;
+    const int d = dt[h[i]];
+    if (conv_ok ? d != SPX_DT_F64 && d != SPX_DT_F32 : d != (all_f32 ? SPX_DT_F32 : SPX_DT_F64))
+      return SPX_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (h[i] == h[j]) return SPX_ERR_INVALID_ARG;
   }
@@ -183,6 +191,7 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     case SPX_OP_TRTRI: ok = R(0) == C(0) && R(1) == R(0) && C(1) == C(0); break;
     default: ok = false;
   }
+  if (all_f32 && C(nh - 1) > 16) ok = false;
   return ok ? SPX_OK : SPX_ERR_INVALID_ARG;
 }
 
@@ -431,7 +440,8 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
     return SPX_OK;
   }
   const uint32_t h = (uint32_t)g->tiles.size();
-  g->tiles.push_back(TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0, -1, 0, 0, 0});
+  g->tiles.push_back(
+      TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0, -1, 0, 0, dtype});
   g->tile_dtype.push_back(dtype);
   g->hstate.emplace_back();
   g->key_to_handle.emplace(key, h);

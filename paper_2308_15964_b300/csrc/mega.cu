@@ -268,6 +268,15 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_GEMM_FWD:
     case SPX_OP_GEMM_BWD: {
       const TileDesc &L = T[t.h[0]], &Xk = T[t.h[1]], &Xi = T[t.h[2]];
+      if (L.dtype == SPX_DT_F32) {  // FP32 correction solve (all operands FP32)
+        if (t.op == SPX_OP_GEMM_FWD)
+          rhs_update<false, float>((const float*)L.ptr, L.ld, (const float*)Xk.ptr, Xk.ld,
+                                   (float*)Xi.ptr, Xi.ld, Xi.rows, Xi.cols, L.cols, u0, u1, s);
+        else
+          rhs_update<true, float>((const float*)L.ptr, L.ld, (const float*)Xk.ptr, Xk.ld,
+                                  (float*)Xi.ptr, Xi.ld, Xi.rows, Xi.cols, L.rows, u0, u1, s);
+        return 0;
+      }
       if (t.op == SPX_OP_GEMM_FWD)
         rhs_update<false>((const double*)L.ptr, L.ld, (const double*)Xk.ptr, Xk.ld,
                           (double*)Xi.ptr, Xi.ld, Xi.rows, Xi.cols, L.cols, u0, u1, s);
@@ -284,7 +293,10 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY);
       return 0;
     case SPX_OP_TRMM:
-      op_trmm(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
+      if (T[t.h[0]].dtype == SPX_DT_F32)
+        op_trmm<float>(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
+      else
+        op_trmm<double>(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
       return 0;
     case SPX_OP_TRTRI:
       if (phase == 0) op_identity(T[t.h[1]], u0, u1);

@@ -44,7 +44,7 @@ struct TileDesc {
   int32_t rows, cols, ld, lowp_ld;
   int32_t lmap;   // tensor map holding the low-precision copy, -1 if none
   int32_t lr0, lc0;  // position of the copy's (0,0) in that map
-  int32_t pad;
+  int32_t dtype;  // SPX_DT_* of the tile's elements
 };
 static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
 

@@ -10,6 +10,7 @@
 // ld.global.cg (L2), so a CTA never sees stale L1 lines of a tile that another
 // SM updated.
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -112,33 +113,36 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
 // are 16 rows x BN columns x KS = 256 / (16 BN) slices of each 64-deep k
 // chunk, so every lane of every FP64 instruction does useful work for
 // BN = 2, 4, 8, 16; the slices are summed in a fixed order (deterministic).
+// Element type E: double, or float for the FP32 correction solves.
 constexpr int kNKC = 64;  // k chunk of a narrow block
-struct NarrowSmem {
-  double a[kNKC][kNarrowRows + 1];
-  double b[kNKC][17];
-  double red[kThreads];
+template <typename E>
+struct NarrowSmemT {
+  E a[kNKC][kNarrowRows + 1];
+  E b[kNKC][17];
+  E red[kThreads];
 };
+using NarrowSmem = NarrowSmemT<double>;
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
-template <bool A_T, int BN>
-__device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, const double* B,
-                               int ldb, int m, int n, int K, double alpha, NarrowSmem& s,
-                               bool set) {
+template <bool A_T, int BN, typename E>
+__device__ void gemm_narrow_bn(E* C, int ldc, const E* A, int lda, const E* B, int ldb, int m,
+                               int n, int K, E alpha, NarrowSmemT<E>& s, bool set) {
   constexpr int KS = kThreads / (kNarrowRows * BN);
   const int tid = threadIdx.x, c = tid % BN, r = (tid / BN) % kNarrowRows,
             ks = tid / (kNarrowRows * BN);
-  double acc0 = 0.0, acc1 = 0.0;
+  E acc0 = 0, acc1 = 0;
   for (int k0 = 0; k0 < K; k0 += kNKC) {
     for (int e = tid; e < kNarrowRows * kNKC; e += kThreads) {
       int i, kk;
       if (A_T) { kk = e / kNarrowRows; i = e % kNarrowRows; } else { i = e / kNKC; kk = e % kNKC; }
-      double v = 0.0;
+      E v = 0;
       if (i < m && k0 + kk < K)
         v = ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk);
       s.a[kk][i] = v;
     }
     for (int e = tid; e < BN * kNKC; e += kThreads) {
       const int kk = e / BN, j = e % BN;
-      s.b[kk][j] = (j < n && k0 + kk < K) ? ldcg(B + (size_t)(k0 + kk) * ldb + j) : 0.0;
+      s.b[kk][j] = (j < n && k0 + kk < K) ? ldcg(B + (size_t)(k0 + kk) * ldb + j) : E(0);
     }
     __syncthreads();
 #pragma unroll
@@ -151,20 +155,20 @@ __device__ void gemm_narrow_bn(double* C, int ldc, const double* A, int lda, con
   s.red[tid] = acc0 + acc1;
   __syncthreads();
   if (ks == 0) {
-    double v = s.red[tid];
+    E v = s.red[tid];
 #pragma unroll
     for (int q = 1; q < KS; ++q) v += s.red[tid + q * kNarrowRows * BN];
     if (r < m && c < n) {
-      double* p = C + (size_t)r * ldc + c;
+      E* p = C + (size_t)r * ldc + c;
       *p = set ? alpha * v : __ldcg(p) + alpha * v;
     }
   }
   __syncthreads();
 }
 
-template <bool A_T>
-__device__ void gemm_narrow(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                            int m, int n, int K, double alpha, NarrowSmem& s, bool set = false) {
+template <bool A_T, typename E>
+__device__ void gemm_narrow(E* C, int ldc, const E* A, int lda, const E* B, int ldb, int m, int n,
+                            int K, E alpha, NarrowSmemT<E>& s, bool set = false) {
   if (n <= 2) gemm_narrow_bn<A_T, 2>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
   else if (n <= 4) gemm_narrow_bn<A_T, 4>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
   else if (n <= 8) gemm_narrow_bn<A_T, 8>(C, ldc, A, lda, B, ldb, m, n, K, alpha, s, set);
@@ -536,30 +540,34 @@ __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& 
 // The narrow-block staging overlays the two 64x64 blocks (unused by GEMM
 // parts).
 static_assert(sizeof(NarrowSmem) <= 2 * sizeof(double) * kBlk * kLds, "narrow staging");
-__device__ __forceinline__ NarrowSmem& narrow_smem(F64Smem& s) {
-  return *reinterpret_cast<NarrowSmem*>(&s.l[0][0]);
+template <typename E = double>
+__device__ __forceinline__ NarrowSmemT<E>& narrow_smem(F64Smem& s) {
+  return *reinterpret_cast<NarrowSmemT<E>*>(&s.l[0][0]);
 }
 
 // C (rows x r) -= op(A) B for the block solves (units: see op_phase_units):
 // 16-row units of all columns when r <= 16, else 64 x 64 output blocks.
 // op(A) = A (A_T false) or A^T (A_T true); r0_c / r0_a: first row of C and
-// of op(A) covered by unit 0.
-template <bool A_T>
-__device__ void rhs_update(const double* a, int lda, const double* b, int ldb, double* c, int ldc,
-                           int rows, int cols, int K, uint32_t u0, uint32_t u1, F64Smem& s) {
+// of op(A) covered by unit 0.  E = float: FP32 operands, narrow shapes only
+// (the operand checks keep FP32 solves to at most 16 columns).
+template <bool A_T, typename E = double>
+__device__ void rhs_update(const E* a, int lda, const E* b, int ldb, E* c, int ldc, int rows,
+                           int cols, int K, uint32_t u0, uint32_t u1, F64Smem& s) {
   const int rb = (int)rhs_unit_rows(cols);
   const uint32_t ncb = rhs_col_blocks(cols);
   for (uint32_t u = u0; u < u1; ++u) {
     const int r0 = (int)(u / ncb) * rb, c0 = (int)(u % ncb) * kBlk;
     const int m = min(rb, rows - r0), w = rhs_narrow(cols) ? cols : min(kBlk, cols - c0);
-    const double* ap = A_T ? a + r0 : a + (size_t)r0 * lda;
-    double* cp = c + (size_t)r0 * ldc + c0;
+    const E* ap = A_T ? a + r0 : a + (size_t)r0 * lda;
+    E* cp = c + (size_t)r0 * ldc + c0;
     if (rhs_narrow(cols))
-      gemm_narrow<A_T>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, narrow_smem(s));
-    else if (w <= 16)
-      gemm_block<A_T, true, 1>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
-    else
-      gemm_block<A_T, true>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
+      gemm_narrow<A_T>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, E(-1), narrow_smem<E>(s));
+    else if constexpr (std::is_same<E, double>::value) {
+      if (w <= 16)
+        gemm_block<A_T, true, 1>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
+      else
+        gemm_block<A_T, true>(cp, ldc, ap, lda, b + c0, ldb, m, w, K, -1.0, false, s.gs);
+    }
   }
 }
 
@@ -621,38 +629,44 @@ __device__ void op_trsm_bwd(const TileDesc& Lt, const TileDesc& Xt, uint32_t pha
 // diagonal) and X, Y (n x r, distinct tiles); the units of GEMM_FWD.  Each
 // unit covers rows r0..r0+m-1 of Y and multiplies over the part of T that
 // can be nonzero for them: columns [0, r0 + m) of T, or rows [r0, n) of T
-// for the transpose.
+// for the transpose.  E = float: FP32 tiles, narrow shapes only.
+template <typename E = double>
 __device__ void op_trmm(const TileDesc& Tt, const TileDesc& Xt, const TileDesc& Yt, bool trans,
                         uint32_t u0, uint32_t u1, F64Smem& s) {
-  const double* tp = (const double*)Tt.ptr;
-  const double* x = (const double*)Xt.ptr;
-  double* y = (double*)Yt.ptr;
+  const E* tp = (const E*)Tt.ptr;
+  const E* x = (const E*)Xt.ptr;
+  E* y = (E*)Yt.ptr;
   const int n = Tt.rows, cols = Yt.cols, ldt = Tt.ld, ldx = Xt.ld, ldy = Yt.ld;
   const int rb = (int)rhs_unit_rows(cols);
   const uint32_t ncb = rhs_col_blocks(cols);
   for (uint32_t u = u0; u < u1; ++u) {
     const int r0 = (int)(u / ncb) * rb, c0 = (int)(u % ncb) * kBlk;
     const int m = min(rb, n - r0), w = rhs_narrow(cols) ? cols : min(kBlk, cols - c0);
-    double* yp = y + (size_t)r0 * ldy + c0;
+    E* yp = y + (size_t)r0 * ldy + c0;
     if (!trans) {  // rows r0.. of T, columns [0, r0 + m)
-      const double* ap = tp + (size_t)r0 * ldt;
+      const E* ap = tp + (size_t)r0 * ldt;
       const int K = r0 + m;
       if (rhs_narrow(cols))
-        gemm_narrow<false>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, narrow_smem(s), true);
-      else if (w <= 16)
-        gemm_block<false, true, 1>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs, true);
-      else
-        gemm_block<false, true>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs, true);
+        gemm_narrow<false>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, E(1), narrow_smem<E>(s), true);
+      else if constexpr (std::is_same<E, double>::value) {
+        if (w <= 16)
+          gemm_block<false, true, 1>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs,
+                                     true);
+        else
+          gemm_block<false, true>(yp, ldy, ap, ldt, x + c0, ldx, m, w, K, 1.0, false, s.gs, true);
+      }
     } else {  // columns r0.. of T, rows [r0, n)
-      const double* ap = tp + (size_t)r0 * ldt + r0;
-      const double* bp = x + (size_t)r0 * ldx + c0;
+      const E* ap = tp + (size_t)r0 * ldt + r0;
+      const E* bp = x + (size_t)r0 * ldx + c0;
       const int K = n - r0;
       if (rhs_narrow(cols))
-        gemm_narrow<true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, narrow_smem(s), true);
-      else if (w <= 16)
-        gemm_block<true, true, 1>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
-      else
-        gemm_block<true, true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
+        gemm_narrow<true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, E(1), narrow_smem<E>(s), true);
+      else if constexpr (std::is_same<E, double>::value) {
+        if (w <= 16)
+          gemm_block<true, true, 1>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
+        else
+          gemm_block<true, true>(yp, ldy, ap, ldt, bp, ldx, m, w, K, 1.0, false, s.gs, true);
+      }
     }
   }
 }
@@ -669,20 +683,32 @@ __device__ void op_identity(const TileDesc& Vt, uint32_t u0, uint32_t u1) {
   }
 }
 
-// Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1.
-__device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
-                             bool axpy) {
-  const double* x = (const double*)Xt.ptr;
-  double* y = (double*)Yt.ptr;
+// Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1,
+// for X and Y each FP64 or FP32 (EX, EY); FP32 -> FP64 is exact, FP64 -> FP32
+// rounds to nearest.
+template <typename EX, typename EY>
+__device__ void copy_axpy_t(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
+                            bool axpy) {
+  const EX* x = (const EX*)Xt.ptr;
+  EY* y = (EY*)Yt.ptr;
   for (uint32_t u = u0; u < u1; ++u) {
     const int r0 = (int)u * kBlk, mb = min(kBlk, Yt.rows - r0);
     for (int e = threadIdx.x; e < mb * Yt.cols; e += kThreads) {
       const int r = r0 + e / Yt.cols, c = e % Yt.cols;
-      const double v = __ldcg(x + (size_t)r * Xt.ld + c);
-      double* py = y + (size_t)r * Yt.ld + c;
-      *py = axpy ? __ldcg(py) + v : v;
+      const EX v = __ldcg(x + (size_t)r * Xt.ld + c);
+      EY* py = y + (size_t)r * Yt.ld + c;
+      *py = axpy ? (EY)(__ldcg(py) + (EY)v) : (EY)v;
     }
   }
+}
+
+__device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
+                             bool axpy) {
+  const bool xf = Xt.dtype == SPX_DT_F32, yf = Yt.dtype == SPX_DT_F32;
+  if (!xf && !yf) copy_axpy_t<double, double>(Xt, Yt, u0, u1, axpy);
+  else if (!xf) copy_axpy_t<double, float>(Xt, Yt, u0, u1, axpy);
+  else if (!yf) copy_axpy_t<float, double>(Xt, Yt, u0, u1, axpy);
+  else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy);
 }
 
 }  // namespace spx

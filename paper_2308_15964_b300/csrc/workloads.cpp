@@ -144,28 +144,30 @@ namespace {
 
 // Square b_k x b_k blocks stacked in an n x b matrix (row block k at row
 // k*b): the inverses of the diagonal factor tiles.
-int register_diag_blocks(spx_graph_t g, double* base, int n, int ld, int b,
-                         std::vector<unsigned>& out) {
+size_t dt_bytes(int dtype) { return dtype == SPX_DT_F32 ? 4 : 8; }
+
+int register_diag_blocks(spx_graph_t g, void* base, int n, int ld, int b,
+                         std::vector<unsigned>& out, int dtype = SPX_DT_F64) {
   const int T = (n + b - 1) / b;
   out.assign(T, 0);
   for (int k = 0; k < T; ++k) {
     const int r = n - k * b < b ? n - k * b : b;
-    const int rc = spx_tile_register(g, base + (size_t)k * b * ld, r, r, ld, SPX_DT_F64, nullptr, 0,
-                                     &out[k]);
+    char* p = (char*)base + (size_t)k * b * ld * dt_bytes(dtype);
+    const int rc = spx_tile_register(g, p, r, r, ld, dtype, nullptr, 0, &out[k]);
     if (rc != SPX_OK) return rc;
   }
   return SPX_OK;
 }
 
 // Row blocks (b_k x nrhs) of an n x nrhs right-hand side.
-int register_row_blocks(spx_graph_t g, double* base, int n, int nrhs, int ld, int b,
-                        std::vector<unsigned>& out) {
+int register_row_blocks(spx_graph_t g, void* base, int n, int nrhs, int ld, int b,
+                        std::vector<unsigned>& out, int dtype = SPX_DT_F64) {
   const int T = (n + b - 1) / b;
   out.assign(T, 0);
   for (int k = 0; k < T; ++k) {
     const int r = n - k * b < b ? n - k * b : b;
-    const int rc = spx_tile_register(g, base + (size_t)k * b * ld, r, nrhs, ld, SPX_DT_F64, nullptr,
-                                     0, &out[k]);
+    char* p = (char*)base + (size_t)k * b * ld * dt_bytes(dtype);
+    const int rc = spx_tile_register(g, p, r, nrhs, ld, dtype, nullptr, 0, &out[k]);
     if (rc != SPX_OK) return rc;
   }
   return SPX_OK;
@@ -227,6 +229,73 @@ extern "C" int spx_solve_inv_insert(spx_graph_t g, double* dev_L, int n, int ldl
     rc = ins(SPX_OP_TRMM, V[k], Db[k], Rb[k], 1, 1);
     for (int i = k - 1; i >= 0 && rc == SPX_OK; --i)
       rc = ins(SPX_OP_GEMM_BWD, L.at(k, i), Rb[k], Db[i], i == k - 1 ? 1 : 0, 0);
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_solve_inv_f32_insert(spx_graph_t g, const float* dev_L32, int n, int ldl,
+                                        int b, const float* dev_V32, int ldv, const double* dev_R,
+                                        float* dev_R32, float* dev_D32, double* dev_X, int nrhs,
+                                        int ldx, long long* out_ntasks) {
+  if (!g || !dev_L32 || !dev_V32 || !dev_R || !dev_R32 || !dev_D32 || !dev_X ||
+      dev_R32 == dev_D32 || (const void*)dev_R == (const void*)dev_X || n < 1 || b < 1 ||
+      ldl < n || ldv < (b < n ? b : n) || nrhs < 1 || nrhs > 16 || ldx < nrhs)
+    return SPX_ERR_INVALID_ARG;
+  const int T = (n + b - 1) / b;
+  Tiles L;
+  L.T = T;
+  L.b = b;
+  L.h.assign((size_t)T * T, 0xFFFFFFFFu);
+  int rc = SPX_OK;
+  for (int i = 0; i < T && rc == SPX_OK; ++i)
+    for (int j = 0; j < i && rc == SPX_OK; ++j) {  // strictly lower tiles (the updates' operands)
+      const int r = n - i * b < b ? n - i * b : b, c = b;
+      rc = spx_tile_register(g, (void*)(dev_L32 + (size_t)i * b * ldl + (size_t)j * b), r, c, ldl,
+                             SPX_DT_F32, nullptr, 0, &L.at(i, j));
+    }
+  std::vector<unsigned> V, R64, X64, Rb, Db;
+  if (rc == SPX_OK) rc = register_diag_blocks(g, (void*)dev_V32, n, ldv, b, V, SPX_DT_F32);
+  if (rc == SPX_OK) rc = register_row_blocks(g, (void*)dev_R, n, nrhs, ldx, b, R64);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_X, n, nrhs, ldx, b, X64);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_R32, n, nrhs, ldx, b, Rb, SPX_DT_F32);
+  if (rc == SPX_OK) rc = register_row_blocks(g, dev_D32, n, nrhs, ldx, b, Db, SPX_DT_F32);
+  long long count = 0;
+  auto ins = [&](int op, const unsigned* hs, int nh, int prio, long long arg) {
+    int ms[3] = {SPX_READ, SPX_READ, SPX_READ};
+    ms[nh - 1] = SPX_WRITE;
+    unsigned id = 0;
+    int r = spx_task_insert(g, op, hs, ms, nh, prio, SPX_F64, &id);
+    if (r == SPX_OK && arg) r = spx_task_set_arg(g, id, arg);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  // r (FP64) rounded to FP32
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+    const unsigned hs[2] = {R64[k], Rb[k]};
+    rc = ins(SPX_OP_COPY, hs, 2, k == 0 ? 1 : 0, 0);
+  }
+  // the block solve of spx_solve_inv_insert on the FP32 copies
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+    const unsigned hd[3] = {V[k], Rb[k], Db[k]};
+    rc = ins(SPX_OP_TRMM, hd, 3, 1, 0);
+    for (int i = k + 1; i < T && rc == SPX_OK; ++i) {
+      const unsigned hu[3] = {L.at(i, k), Db[k], Rb[i]};
+      rc = ins(SPX_OP_GEMM_FWD, hu, 3, i == k + 1 ? 1 : 0, 0);
+    }
+  }
+  for (int k = T - 1; k >= 0 && rc == SPX_OK; --k) {
+    const unsigned hd[3] = {V[k], Db[k], Rb[k]};
+    rc = ins(SPX_OP_TRMM, hd, 3, 1, 1);
+    for (int i = k - 1; i >= 0 && rc == SPX_OK; --i) {
+      const unsigned hu[3] = {L.at(k, i), Rb[k], Db[i]};
+      rc = ins(SPX_OP_GEMM_BWD, hu, 3, i == k - 1 ? 1 : 0, 0);
+    }
+  }
+  // x += d (FP32 correction widened exactly)
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {
+    const unsigned hs[2] = {Rb[k], X64[k]};
+    rc = ins(SPX_OP_AXPY, hs, 2, 0, 0);
   }
   if (out_ntasks) *out_ntasks = count;
   return rc;

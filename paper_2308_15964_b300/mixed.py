@@ -92,21 +92,50 @@ def solve_inv_graph(g: spx.Graph, L, b: int, V, R, D) -> int:
     return nt.value
 
 
+def convert_graph(g: spx.Graph, src, dst) -> int:
+    """dst <- src (same shape; FP64 -> FP32 rounds to nearest) as one COPY task."""
+    hs = g.register_tensor(src, _dt(src))
+    hd = g.register_tensor(dst, _dt(dst))
+    return g.insert(spx.OP_COPY, [hs, hd], [spx.READ, spx.WRITE])
+
+
+def _dt(t):
+    return spx.DT_F32 if t.dtype == torch.float32 else spx.DT_F64
+
+
+def solve_inv_f32_graph(g: spx.Graph, L32, b: int, V32, R, R32, D32, X) -> int:
+    """x <- x + (L L^T)^{-1} r with the solve in FP32 on the copies L32, V32:
+    R (FP64 residual) in, X (FP64) updated, R32 / D32 FP32 scratch."""
+    n, nrhs = R.shape
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_solve_inv_f32_insert(g._h, _p(L32), n, L32.stride(0), b, _p(V32),
+                                                V32.stride(0), _p(R), _p(R32), _p(D32), _p(X),
+                                                nrhs, R.stride(0), ctypes.byref(nt)),
+               "spx_solve_inv_f32_insert")
+    return nt.value
+
+
 def lowp_dtype(prec: int):
     return torch.bfloat16 if prec == spx.BF16 else torch.float32
 
 
 def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
-                max_iter: int | None = None, inverse: bool = True):
+                max_iter: int | None = None, inverse: bool = True, correction: str = "auto"):
     """Solve A0 X = B.  Returns (X, L, info) where L holds the factor (lower
     triangle) and info has 'converged', 'iterations', 'eta' (history of the
     max normwise backward error), 'factor_ms', 'refine_ms', 'status'.  With
     `inverse`, the correction solves apply the inverses of the diagonal factor
     tiles (computed once, FP64, timed in refine_ms) as products; otherwise
-    they substitute."""
+    they substitute.  `correction` = "f32" (with `inverse`, at most 16
+    right-hand sides) solves for each correction in FP32 on FP32 copies of the
+    factor and of the inverses: the factor is only accurate to TF32 / BF16, so
+    FP32 costs the refinement no iterations and runs on the FP32 pipe; "f64"
+    keeps the FP64 solve; "auto" (default) takes "f32" where it applies."""
     if max_iter is None:
         max_iter = 30 if prec == spx.TF32 else 50
     n, nrhs = B.shape
+    if correction == "auto":
+        correction = "f32" if inverse and nrhs <= 16 else "f64"
     A = A0.clone()
     Alo = torch.zeros((n, n), dtype=lowp_dtype(prec), device=A0.device)
     X = B.clone()
@@ -133,7 +162,24 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
         if rc != spx.OK:
             g.close()
             return X, A, {"status": rc, "converged": False, "iterations": 0, "eta": []}
-        solve_inv_graph(gs, A, b, V, R, D)
+        if correction == "f32":
+            if nrhs > 16:
+                raise ValueError("the FP32 correction solve takes at most 16 right-hand sides")
+            L32 = torch.empty((n, n), dtype=torch.float32, device=A0.device)
+            V32 = torch.empty(V.shape, dtype=torch.float32, device=A0.device)
+            R32, D32 = (torch.empty(B.shape, dtype=torch.float32, device=A0.device)
+                        for _ in range(2))
+            gc = spx.Graph()
+            convert_graph(gc, A, L32)
+            convert_graph(gc, V, V32)
+            rc, _ = gc.run()
+            gc.close()
+            if rc != spx.OK:
+                g.close()
+                return X, A, {"status": rc, "converged": False, "iterations": 0, "eta": []}
+            solve_inv_f32_graph(gs, L32, b, V32, R, R32, D32, X)
+        else:
+            solve_inv_graph(gs, A, b, V, R, D)
     else:
         solve_graph(gs, A, b, R)
     anorm = norm_inf(A0)
@@ -157,12 +203,13 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
         if rc != spx.OK:
             break
         gs.reset()
-        axpy(X, R)
+        if not (inverse and correction == "f32"):   # the FP32 graph adds it itself
+            axpy(X, R)
     ev[2].record()
     ev[2].synchronize()
     out = {"status": rc, "converged": converged, "iterations": it, "eta": history,
            "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2]),
-           "factor_op_share": share}
+           "factor_op_share": share, "correction": correction if inverse else "f64"}
     g.close()
     gs.close()
     return X, A, out

@@ -78,6 +78,7 @@ def _load():
         "spx_overhead_insert": (I, [P, I, I, I, I, LL, P]),
         "spx_refine_inv_insert": (I, [P, P, I, I, P, I, I, P, I, P, P, P, P, I, I, I, P]),
         "spx_solve_inv_insert": (I, [P, P, I, I, I, P, I, P, P, I, I, P]),
+        "spx_solve_inv_f32_insert": (I, [P, P, I, I, I, P, I, P, P, P, P, I, I, P]),
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),
         "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
