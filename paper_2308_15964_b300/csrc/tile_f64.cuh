@@ -130,21 +130,48 @@ __device__ void gemm_narrow_bn(E* C, int ldc, const E* A, int lda, const E* B, i
   constexpr int KS = kThreads / (kNarrowRows * BN);
   const int tid = threadIdx.x, c = tid % BN, r = (tid / BN) % kNarrowRows,
             ks = tid / (kNarrowRows * BN);
-  E acc0 = 0, acc1 = 0;
-  for (int k0 = 0; k0 < K; k0 += kNKC) {
-    for (int e = tid; e < kNarrowRows * kNKC; e += kThreads) {
+  // The next k chunk is loaded into registers while the current one is
+  // multiplied, so its load latency overlaps the barrier and the FMAs (the
+  // per-thread summation order is unchanged).
+  constexpr int kAE = kNarrowRows * kNKC / kThreads;          // A elements per thread
+  constexpr int kBE = (BN * kNKC + kThreads - 1) / kThreads;  // B elements per thread
+  static_assert(kAE * kThreads == kNarrowRows * kNKC, "A chunk split");
+  E ra[kAE], rb[kBE];
+  auto a_pos = [&](int e, int& i, int& kk) {
+    if (A_T) { kk = e / kNarrowRows; i = e % kNarrowRows; } else { i = e / kNKC; kk = e % kNKC; }
+  };
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < kAE; ++q) {
       int i, kk;
-      if (A_T) { kk = e / kNarrowRows; i = e % kNarrowRows; } else { i = e / kNKC; kk = e % kNKC; }
-      E v = 0;
-      if (i < m && k0 + kk < K)
-        v = ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk);
-      s.a[kk][i] = v;
+      a_pos(tid + q * kThreads, i, kk);
+      ra[q] = (i < m && k0 + kk < K)
+                  ? ldcg(A_T ? A + (size_t)(k0 + kk) * lda + i : A + (size_t)i * lda + k0 + kk)
+                  : E(0);
     }
-    for (int e = tid; e < BN * kNKC; e += kThreads) {
-      const int kk = e / BN, j = e % BN;
-      s.b[kk][j] = (j < n && k0 + kk < K) ? ldcg(B + (size_t)(k0 + kk) * ldb + j) : E(0);
+#pragma unroll
+    for (int q = 0; q < kBE; ++q) {
+      const int e = tid + q * kThreads, kk = e / BN, j = e % BN;
+      rb[q] = (e < BN * kNKC && j < n && k0 + kk < K) ? ldcg(B + (size_t)(k0 + kk) * ldb + j)
+                                                      : E(0);
+    }
+  };
+  E acc0 = 0, acc1 = 0;
+  fetch(0);
+  for (int k0 = 0; k0 < K; k0 += kNKC) {
+#pragma unroll
+    for (int q = 0; q < kAE; ++q) {
+      int i, kk;
+      a_pos(tid + q * kThreads, i, kk);
+      s.a[kk][i] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kBE; ++q) {
+      const int e = tid + q * kThreads;
+      if (e < BN * kNKC) s.b[e / BN][e % BN] = rb[q];
     }
     __syncthreads();
+    if (k0 + kNKC < K) fetch(k0 + kNKC);
 #pragma unroll
     for (int kk = ks; kk < kNKC; kk += 2 * KS) {
       acc0 = fma(s.a[kk][r], s.b[kk][c], acc0);
