@@ -439,13 +439,18 @@ int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, 
  * nhandles > SPX_NOALLOC_MAX_HANDLES; SPX_ERR_CUDA if the set-up or the launch
  * fails.  Device-side (in *dev_status once the stream reaches it): 0, or
  * SPX_ERR_INVALID_ARG for malformed records, or for col_cap smaller than the
- * number of edges, which is then in dev_row_ptr[ntasks] (col and indeg not
- * written).
+ * number of edges E.  In the last case dev_col and dev_indeg are not written
+ * and dev_row_ptr[ntasks] holds E, or 0xFFFFFFFF when E does not fit 32 bits
+ * (E is summed in 64 bits: a valid list can have more than 2^32 edges, e.g.
+ * 65536 READs followed by 65536 COMMUTATIVE_WRITEs on one handle); the other
+ * dev_row_ptr entries are then unspecified.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the scratch array: calls that
- * overlap on the GPU (other streams, other threads) race and give wrong
- * results; calls in sequence on one stream are independent. */
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call this function on a device after cudaDeviceReset (the kept address
+ * belongs to the destroyed context).  Every call shares the scratch array:
+ * calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong results; calls in sequence on one stream are independent. */
 int spx_graph_derive_noalloc(const unsigned* dev_task_rec, const unsigned* dev_rec_handle,
                              const unsigned* dev_rec_seq, const unsigned char* dev_rec_mode,
                              int ntasks, int nhandles, long long nrec, unsigned* dev_row_ptr,

@@ -48,7 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-fno-unswitch-loops", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr", "-prec-div=true", "-prec-sqrt=true", "-fmad=true"]
-    objs = []
+    objs, procs = [], []
+    # one nvcc per source, all at once (the persistent kernel's file dominates)
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [NVCC, *ARCH, *common, "-c", src, "-o", obj]
@@ -56,13 +57,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd += ["-Xptxas", "-v"] if verbose else []
         else:
             cmd += ["-x", "cu"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            sys.stderr.write(r.stdout + r.stderr)
-            raise RuntimeError(f"nvcc failed on {src}")
-        if verbose:
-            sys.stderr.write(r.stderr)
+        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                            text=True)))
         objs.append(obj)
+    failed = None
+    for src, pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            sys.stderr.write(out + err)
+            failed = failed or src
+        elif verbose:
+            sys.stderr.write(err)
+    if failed:
+        raise RuntimeError(f"nvcc failed on {failed}")
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -107,17 +107,21 @@ __device__ uint32_t merge_successors(const DevGraph& g, uint32_t u, uint32_t ngr
 
 // Steps 1-4: per-handle lists, groups, unique successors (row_ptr, col,
 // indeg).  Reads rec_*, task_rec; uses hptr, s_task, s_mode, s_first,
-// rec_pos, gid, gpos as scratch.  Returns false, with row_ptr[ntasks] = E
-// and col / indeg not written, when E > ecap.  Every thread must call it.
+// rec_pos, gid, gpos as scratch.  The edge total E is summed in 64 bits
+// before any scan: E can exceed 2^32 for valid inputs (65536 READs followed by
+// 65536 COMMUTATIVE_WRITEs on one handle give 2^32 edges).  Returns false,
+// with row_ptr[ntasks] = E (0xFFFFFFFF when E does not fit 32 bits) and col /
+// indeg not written, when E > ecap.  Every thread must call it.
 // Steps 1-4 run by a CTA of NT threads (sh: NT/32 + 1 words).
 template <int NT = kDeriveThreads>
 __device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
+  __shared__ unsigned long long e_total;
   const uint32_t N = g.ntasks, H = g.ntiles, M = g.nrec;
   const int tid = threadIdx.x;
 
   // 1. accesses per handle -> list offsets
   for (uint32_t i = tid; i <= H; i += NT) g.hptr[i] = 0;
-  for (uint32_t i = tid; i < N; i += NT) g.indeg[i] = 0;
+  if (tid == 0) e_total = 0;
   __syncthreads();
   for (uint32_t r = tid; r < M; r += NT) atomicAdd(&g.hptr[g.rec_handle[r]], 1u);
   __syncthreads();
@@ -151,13 +155,28 @@ __device__ bool derive_dag(const DevGraph& g, uint32_t* sh) {
   if (tid == 0) g.gpos[G] = M;
   __syncthreads();
 
-  // 4. unique successors: count, scan, write
-  for (uint32_t u = tid; u < N; u += NT) g.row_ptr[u] = merge_successors(g, u, G, nullptr);
+  // 4. unique successors: count (64-bit total), scan, write
+  unsigned long long mine = 0;
+  for (uint32_t u = tid; u < N; u += NT) {
+    const uint32_t c = merge_successors(g, u, G, nullptr);
+    g.row_ptr[u] = c;
+    mine += c;
+  }
   if (tid == 0) g.row_ptr[N] = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((tid & 31) == 0 && mine) atomicAdd(&e_total, mine);
   __syncthreads();
-  const uint32_t E = block_excl_scan<NT>(g.row_ptr, N + 1, sh);
+  const unsigned long long E = e_total;
+  if (E <= 0xFFFFFFFFull) {
+    block_excl_scan<NT>(g.row_ptr, N + 1, sh);
+  } else if (tid == 0) {
+    g.row_ptr[N] = 0xFFFFFFFFu;
+  }
   __syncthreads();
-  if (E > g.ecap) return false;
+  if (E > (unsigned long long)g.ecap) return false;
+  for (uint32_t i = tid; i < N; i += NT) g.indeg[i] = 0;
+  __syncthreads();
   for (uint32_t u = tid; u < N; u += NT) merge_successors(g, u, G, g.col + g.row_ptr[u]);
   __syncthreads();
   return true;

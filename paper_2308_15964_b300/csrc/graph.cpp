@@ -267,6 +267,8 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   int rc = ensure_device(g);
   if (rc != SPX_OK) return rc;
   const size_t N = g->tasks.size(), H = g->tiles.size(), M = g->rec_handle.size();
+  // edge offsets and counts are 32-bit on the device
+  if (g->cand_edges > 0xFFFFFFFFull) return SPX_ERR_INVALID_ARG;
   const size_t E = std::max<unsigned long long>(g->cand_edges, 1);
   size_t Q = std::max<unsigned long long>(
       std::max(std::max(g->items[0], g->items[1]), g->items[2]), 1);

@@ -269,6 +269,7 @@ int spx_server_submit(spx_server_t s, spx_graph_t g, unsigned long long* out_req
   const unsigned long long items = v.items;
   if (s->free_slots.empty() || s->live_items + items > (unsigned long long)s->cfg.queue_capacity)
     return SPX_ERR_OOM;
+  if (v.cand_edges > 0xFFFFFFFFull) return SPX_ERR_INVALID_ARG;  // 32-bit edge offsets
   Live L{};
   L.nt = v.ntasks + 1;
   L.nh = v.ntiles + 1;

@@ -18,6 +18,7 @@
 #include "spx_internal.h"
 
 namespace spx {
+namespace {
 
 constexpr int kKC = 16;        // k chunk staged in shared memory
 constexpr int kLds = kBlk + 1; // padded row of a shared 64-wide array (doubles)
@@ -738,4 +739,5 @@ __device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0
   else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy);
 }
 
+}  // namespace
 }  // namespace spx

@@ -25,6 +25,7 @@
 #include "spx_internal.h"
 
 namespace spx {
+namespace {
 
 constexpr int kTcM = 128, kTcN = 128;
 constexpr int kTcStages = 3;
@@ -328,9 +329,11 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   return true;
 }
 
+}  // namespace
 }  // namespace spx
 
 namespace spx {
+namespace {
 
 // Shared-memory context of the tensor-core ops inside the persistent kernel.
 struct TcCtx {
@@ -398,4 +401,5 @@ __device__ void op_lowp_copy(const TileDesc& At, uint32_t u0, uint32_t u1) {
   }
 }
 
+}  // namespace
 }  // namespace spx

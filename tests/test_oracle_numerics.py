@@ -135,6 +135,26 @@ def test_metrics_zero_and_planted():
     assert 0.1 * d / np.linalg.norm(A) < beta < 100 * d * n / np.linalg.norm(A)
 
 
+def test_solve_backward_error_closed_form():
+    """Rigal-Gaches eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+    on a hand-worked 3 x 3 case.  A is not symmetric, so its infinity norm
+    (max row sum 5) differs from its 1-norm (max column sum 6); each x has
+    ||x||_1 != ||x||_inf; b = A x + d with d exactly representable, so the
+    residual is exactly d.  By hand:
+      column 0: x = (1, -2, 3), A x = (6, -2, 7), d = (0, 1/2, 0),
+                b = (6, -3/2, 7): eta = (1/2) / (5*3 + 7) = 1/44;
+      column 1: x = (-3, 0, 1), A x = (-12, -2, 1), d = (-1/4, 0, 1/8),
+                b = (-49/4, -2, 9/8): eta = (1/4) / (5*3 + 49/4) = 1/109.
+    A 1-norm of A would give 1/50 and 1/121; ||x||_1 1/74 and 1/129; a dropped
+    ||b|| term 1/30 and 1/60; the residual of a wrong sign or a transposed A
+    changes the numerators."""
+    A = np.array([[4.0, -1.0, 0.0], [1.0, 3.0, 1.0], [0.0, -2.0, 1.0]])
+    X = np.array([[1.0, -3.0], [-2.0, 0.0], [3.0, 1.0]])
+    B = np.array([[6.0, -12.25], [-1.5, -2.0], [7.0, 1.125]])
+    eta = O.solve_backward_error(A, X, B)
+    assert eta[0] == 1.0 / 44.0 and eta[1] == 1.0 / 109.0, eta
+
+
 @pytest.mark.parametrize("n,b", [(64, 16), (96, 32), (70, 32)])
 def test_gemm_dag_exact_order(n, b):
     A = inputs.uniform((n, n), 3).numpy()
