@@ -74,6 +74,7 @@ def measured_traffic(path: str = DRAM_PROFILE):
 # at 1942 MHz on 148 SMs) x 2 flop x 148 SMs x 2032 MHz maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2
 ORACLE_SAMPLE_N = 4096      # CPU baseline sample (about 10 s on one core)
+COMPARATOR_STEPS = 5        # timed steps of each comparison executor
 REFERENCE_STEP_N = 2048     # --impl reference: one step of the oracle
 
 
@@ -87,7 +88,8 @@ def parse():
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
-    p.add_argument("--workload", default="cholesky", choices=["cholesky", "batch", "mixed", "serve", "tc", "overhead"],
+    p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
+                                                      "overhead"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -229,6 +231,9 @@ def main():
     if args.workload == "overhead":
         run_overhead(args, world, rank, local)
         return
+    if args.workload == "gemm":
+        run_gemm(args, world, rank, local)
+        return
 
     n, b = args.n, args.tile
     flops = cholesky.cholesky_flops(n)
@@ -317,7 +322,7 @@ def main():
         gb = spx.Graph(executor=spx.EXEC_PER_TASK)
         step(gb)
         brec = []
-        for _ in range(2):
+        for _ in range(COMPARATOR_STEPS):
             step(gb, brec)
         bms = [r[0] for r in brec]
         out["baseline_per_task"] = {"value": flops / (statistics.mean(bms) * 1e-3) / 1e9,
@@ -330,7 +335,7 @@ def main():
         gs = spx.Graph(executor=spx.EXEC_STREAMS)
         step(gs)
         srec = []
-        for _ in range(2):
+        for _ in range(COMPARATOR_STEPS):
             step(gs, srec)
         sms_ = [r[0] for r in srec]
         out["baseline_streams"] = {"value": flops / (statistics.mean(sms_) * 1e-3) / 1e9,
@@ -345,7 +350,7 @@ def main():
         cholesky.cholesky_graph(gg, A, b)
         assert gg.run()[0] == spx.OK
         grec = []
-        for i in range(3):
+        for i in range(COMPARATOR_STEPS + 1):
             A.copy_(A0)
             gg.reset()
             ev[0].record()
@@ -360,6 +365,8 @@ def main():
                                               "note": "execution only (the graph is inserted once)"}
         gg.close()
         out["latency_small"] = small_latency(spx, cholesky, inputs, torch)
+        out["gemm_dag"] = gemm_dag(spx, cholesky, inputs, torch, 8192, b, args.warmup, args.steps,
+                                   max_mhz, comparators=True)
 
         # end to end through host buffers: H2D of A, the step, D2H of L
         Ah = A0.cpu().pin_memory()
@@ -403,6 +410,117 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, comparators=False):
+    """The paper's tiled GEMM whose tasks depend on the blocks of C (section
+    "Numerical applications"): C += A B, one GEMM_NN_ADD task per (i, j, k),
+    each with a WRITE on C_ij (the 16 tasks of a block form a chain) or a
+    COMMUTATIVE_WRITE (any order, one at a time).  Entries uniform[-1, 1)
+    (seeds 3, 4, 5).  Step = insert + derive + execute + wait; value = 2 n^3
+    over the step's device time.  Inputs 3 x 8 n^2 bytes, larger than L2."""
+    A = inputs.uniform((n, n), 3, device="cuda")
+    B = inputs.uniform((n, n), 4, device="cuda")
+    C0 = inputs.uniform((n, n), 5, device="cuda")
+    C = torch.empty_like(C0)
+    flops = cholesky.gemm_flops(n)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    sms = spx.lib.spx_device_sm_count()
+    peak = FP64_DFMA_PER_CLK_SM * 2 * sms * max_mhz * 1e6 / 1e12
+    res = {"workload": f"tiled GEMM C += A B as a task graph, FP64, n={n} tile={b}, "
+                       "one task per (i, j, k) on C_ij (WRITE chain or COMMUTATIVE_WRITE run)",
+           "n": n, "tile": b, "flops_per_step": flops}
+
+    def timed(g, commutative, nsteps, nwarm):
+        rec = []
+        for i in range(nwarm + nsteps):
+            C.copy_(C0)
+            ev[0].record()
+            g.clear()
+            cholesky.gemm_graph(g, A, B, C, b, commutative=commutative)
+            g.execute(stream)
+            rc, _ = g.wait()
+            ev[1].record()
+            ev[1].synchronize()
+            assert rc == spx.OK, rc
+            if i >= nwarm:
+                rec.append((ev[0].elapsed_time(ev[1]), g.timing()[1]))
+        return rec
+
+    for mode, comm in (("write", False), ("commutative", True)):
+        g = spx.Graph()
+        rec = timed(g, comm, steps, warmup)
+        ntasks, nedges, _, _ = g.sizes()
+        g.close()
+        ms = [r[0] for r in rec]
+        kern = statistics.mean(r[1] for r in rec)
+        row = {"value": flops / (statistics.mean(ms) * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "ms_per_step": statistics.mean(ms), "steps": len(ms), "tasks": ntasks,
+               "edges": nedges, "tasks_per_s": ntasks / (statistics.mean(ms) * 1e-3),
+               "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+               "roofline": {"bound": "alu", "achieved": flops / (kern * 1e-3) / 1e12, "peak": peak,
+                            "unit": "TFLOP/s", "frac": flops / (kern * 1e-3) / 1e12 / peak,
+                            "kernel": "persistent_kernel (FP64 DFMA tile ops)", "kernel_ms": kern}}
+        # comparators on the WRITE DAG only: a commutative task runs as one
+        # part (one CTA), so one launch per task would serialise 4096
+        # single-CTA GEMMs (minutes per step) and measure nothing new
+        if comparators and not comm:
+            for name, ex in (("baseline_per_task", spx.EXEC_PER_TASK),
+                             ("baseline_streams", spx.EXEC_STREAMS)):
+                gb = spx.Graph(executor=ex)
+                brec = timed(gb, comm, COMPARATOR_STEPS, 1)
+                gb.close()
+                bms = [r[0] for r in brec]
+                row[name] = {"value": flops / (statistics.mean(bms) * 1e-3) / 1e9,
+                             "unit": "GFLOP/s", "ms_per_step": statistics.mean(bms),
+                             "tasks_per_s": ntasks / (statistics.mean(bms) * 1e-3),
+                             "p99_ms": float(np.percentile(bms, 99)), "steps": len(bms)}
+        res[mode] = row
+    del A, B, C, C0
+    torch.cuda.empty_cache()
+    # CPU oracle (one host core, insertion order): bounded samples (about 4 s
+    # in all; n = 2048 takes 40 s), n^3 extrapolation to the workload size
+    from oracle import oracle as O
+    secs = {}
+    for ns in (512, 1024):
+        Ah = inputs.uniform((ns, ns), 3).numpy()
+        Bh = inputs.uniform((ns, ns), 4).numpy()
+        Ch = inputs.uniform((ns, ns), 5).numpy()
+        t0 = time.perf_counter()
+        assert O.tiled_gemm(Ah, Bh, Ch, b) == 0
+        secs[ns] = time.perf_counter() - t0
+    top = max(secs)
+    res["cpu_baseline"] = {"value": cholesky.gemm_flops(top) / secs[top] / 1e9, "unit": "GFLOP/s",
+                           "cores": 1, "kind": "oracle",
+                           "sample": f"tiled GEMM oracle (WRITE order), n in {sorted(secs)}, tile {b}",
+                           "seconds_by_n": {str(k): v for k, v in secs.items()},
+                           "extrapolated_s_at_n": {"n": n, "seconds": secs[top] * (n / top) ** 3,
+                                                   "note": f"n^3 extrapolation of the n={top} time, "
+                                                           "not measured"}}
+    return res
+
+
+def run_gemm(args, world, rank, local):
+    """--workload gemm: the tiled GEMM DAG alone (n = 8192, tile 512)."""
+    import torch
+    from paper_2308_15964_b300 import cholesky, inputs, spx
+    n = args.n if args.n != 16384 else 8192
+    with Clocks(local) as clk:
+        res = gemm_dag(spx, cholesky, inputs, torch, n, args.tile, args.warmup, args.steps, 2032.0,
+                       comparators=not args.no_extras)
+    clocks = clk.summary()
+    w = res["write"]
+    out = {"metric": METRIC, "value": w["value"], "unit": "GFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": res["workload"], "n": n, "tile": args.tile,
+                      "l2": "inputs larger than L2 (3 x 8 n^2 bytes)"},
+           "roofline": w["roofline"], "cpu_baseline": res["cpu_baseline"], "gemm_dag": res,
+           "clocks": clocks, "gpu_launches": 2 * args.steps}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_overhead(args, world, rank, local):
@@ -542,16 +660,19 @@ def run_mixed(args, world, rank, local):
                                   f"A = B B^T/n + {sigma} I, FP64 refinement to eta <= 1e-14",
                       "n": n, "tile": b, "nrhs": nrhs, "sigma": sigma}}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    last = {}
     with Clocks(local) as clk:
         for name, prec in (("tf32", spx.TF32), ("bf16", spx.BF16)):
             runs = []
             for i in range(args.warmup + args.steps):
+                last.pop(name, None)
                 ev[0].record()
                 X, L, info = mixed.mixed_solve(A0, B, b=b, prec=prec)
                 ev[1].record()
                 ev[1].synchronize()
                 if i >= args.warmup:
                     runs.append((ev[0].elapsed_time(ev[1]), info))
+                last[name] = (X, L)
                 del X, L
             ms = statistics.mean(r[0] for r in runs)
             inf = runs[-1][1]
@@ -559,13 +680,42 @@ def run_mixed(args, world, rank, local):
             flops = cholesky.cholesky_flops(n, nrhs)
             out[name] = {"ms_per_solve": ms, "factor_ms": fac,
                          "refine_ms": statistics.mean(r[1]["refine_ms"] for r in runs),
+                         "ms_per_solve_runs": [round(r[0], 2) for r in runs],
                          "gflops_total": flops / (ms * 1e-3) / 1e9,
                          "factor_gflops": n ** 3 / 3 / (fac * 1e-3) / 1e9,
                          "converged": inf["converged"], "iterations": inf["iterations"],
-                         "eta_final": inf["eta"][-1] if inf["eta"] else None,
-                         "eta_history": inf["eta"], "correction_solve": inf.get("correction"),
+                         "eta_device": inf["eta_final"],
+                         "eta_history": inf["eta"],
+                         "eta_history_compensated": inf["eta_compensated"],
+                         "correction_solve": inf.get("correction"),
                          "factor_cta_time_share": {k: round(v, 4) for k, v in
                                                    inf.get("factor_op_share", {}).items()}}
+    if rank == 0:
+        # The oracle's checks of the last run of each precision (host, one
+        # core): normwise backward error of X with compensated residuals, and
+        # a Freivalds probe ||A v - L (L^T v)|| / (||A||_F ||v||) of the
+        # low-precision factor (its backward error, of order the precision).
+        from oracle import oracle as O
+        A0h, Bh = A0.cpu().numpy(), B.cpu().numpy()
+        v = inputs.gaussian(n, 9)
+        for name in ("tf32", "bf16"):
+            X, L = last[name]
+            Xh = X.cpu().numpy()
+            del X
+            t0 = time.perf_counter()
+            eta = O.solve_backward_error(A0h, Xh, Bh)
+            t1 = time.perf_counter()
+            Lh = L.cpu().numpy()
+            del L
+            fr = O.freivalds(A0h, Lh, v)
+            t2 = time.perf_counter()
+            del Lh
+            out[name]["eta_oracle"] = float(eta.max())
+            out[name]["eta_oracle_per_rhs"] = [float(x) for x in eta]
+            out[name]["factor_freivalds_oracle"] = fr
+            out[name]["oracle_check_s"] = {"eta": t1 - t0, "freivalds": t2 - t1}
+        del A0h
+    last.clear()
     out["value"] = out["tf32"]["gflops_total"]
     out["ms_per_step"] = out["tf32"]["ms_per_solve"]
     out["clocks"] = clk.summary()
@@ -677,28 +827,39 @@ def run_batch(args, world, rank, local):
 
 
 def small_latency(spx, cholesky, inputs, torch, reps=200):
-    """Latency of the small case (n=512, tile 64, 120 factorization tasks):
-    execute -> wait on a reset graph, persistent vs the per-task executors
-    (one stream; four streams with event waits)."""
+    """Latency of the small case: n=512, tile 64, A = B B^T/n + I (seed 1),
+    one right-hand side: the factorization (120 tasks) and the block solve
+    (72 tasks) in one graph of 192 tasks.  Host wall time of execute -> wait
+    on a reset graph, persistent vs the per-task executors (one stream; the
+    same through a CUDA graph; four streams with event waits); the
+    factorization alone beside it.  Then the critical path of one traced
+    persistent run, split into the time tasks run and the time between a
+    predecessor's end and the task's start (release + pop)."""
     n, b = 512, 64
     A0 = inputs.spd_matrix(n, 1.0, seed=1, device="cuda")
-    A = torch.empty_like(A0)
+    X0 = inputs.rhs(n, 1, seed=1, device="cuda")
+    A, X = torch.empty_like(A0), torch.empty_like(X0)
+    flops_fs = cholesky.cholesky_flops(n, 1)
     res = {}
-    for name, ex, rederive, cg in (("persistent", spx.EXEC_PERSISTENT, False, False),
-                                   ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False),
-                                   ("per_task", spx.EXEC_PER_TASK, False, False),
-                                   ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True),
-                                   ("streams", spx.EXEC_STREAMS, False, False)):
+    for name, ex, rederive, cg, solve in (
+            ("persistent", spx.EXEC_PERSISTENT, False, False, True),
+            ("persistent_factor_only", spx.EXEC_PERSISTENT, False, False, False),
+            ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False, True),
+            ("per_task", spx.EXEC_PER_TASK, False, False, True),
+            ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True, True),
+            ("streams", spx.EXEC_STREAMS, False, False, True)):
         g = spx.Graph(executor=ex, cuda_graph=cg)
-        cholesky.cholesky_graph(g, A, b)
+        Xs = X if solve else None
+        ntasks = cholesky.cholesky_graph(g, A, b, Xs)
         lat = []
         for i in range(reps + 5):
             A.copy_(A0)
+            X.copy_(X0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if rederive and i > 0:
                 g.clear()
-                cholesky.cholesky_graph(g, A, b)
+                cholesky.cholesky_graph(g, A, b, Xs)
             g.execute()
             rc, _ = g.wait()
             t1 = time.perf_counter()
@@ -707,13 +868,78 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
                 g.reset()
             if i >= 5:
                 lat.append((t1 - t0) * 1e3)
-        res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "gflops": cholesky.cholesky_flops(n) / (np.median(lat) * 1e-3) / 1e9}
+        fl = flops_fs if solve else cholesky.cholesky_flops(n)
+        res[name] = {"tasks": ntasks, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)),
+                     "gflops": fl / (np.median(lat) * 1e-3) / 1e9}
         g.close()
-    res["workload"] = ("n=512 tile=64, 120 tasks, host wall time of execute->wait; persistent and "
-                       "per_task reuse the inserted graph (reset), persistent_insert_derive inserts "
-                       "and derives every time")
+    res["workload"] = ("n=512 tile=64, 1 RHS: factorization + block solve, 192 tasks (the "
+                       "_factor_only row: the 120 factorization tasks); host wall time of "
+                       "execute->wait over %d runs; the graph is reset and re-run, except "
+                       "persistent_insert_derive, which inserts and derives every time" % reps)
+    res["critical_path"] = critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b)
     return res
+
+
+def critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b):
+    """Critical path of one traced persistent run of the small case: walk back
+    from the last task to finish, each time to the predecessor that finished
+    last; per task on that path, the time it ran (first part start to last
+    part end, %globaltimer) and the gap since that predecessor's end (the
+    release of its successors, the pop, and the wait for a free CTA)."""
+    g = spx.Graph(trace=True)
+    cholesky.cholesky_graph(g, A, b, X)
+    runs = []
+    for _ in range(6):
+        A.copy_(A0)
+        X.copy_(X0)
+        torch.cuda.synchronize()
+        g.execute()
+        assert g.wait()[0] == spx.OK
+        runs.append(g.trace().astype(np.int64))
+        g.reset()
+    rp, col, _ = g.edges()
+    ops, prio = g.task_ops()
+    g.close()
+    N = len(ops)
+    preds = [[] for _ in range(N)]
+    for u in range(N):
+        for v in col[rp[u]:rp[u + 1]]:
+            preds[int(v)].append(u)
+    out = []
+    for tr in runs[1:]:
+        start, end = tr[:, 0], tr[:, 1]
+        u = int(np.argmax(end))
+        chain = [u]
+        while preds[u]:
+            u = max(preds[u], key=lambda p: end[p])
+            chain.append(u)
+        chain.reverse()
+        rows = []
+        for i, t in enumerate(chain):
+            gap = 0 if i == 0 else int(start[t] - end[chain[i - 1]])
+            rows.append((spx.OP_NAMES[ops[t]], int(end[t] - start[t]), gap, int(tr[t, 3])))
+        out.append({"span_us": (end.max() - start.min()) / 1e3, "rows": rows})
+    best = min(out, key=lambda r: r["span_us"])
+    by_op = {}
+    for name, run_ns, gap_ns, parts in best["rows"]:
+        d = by_op.setdefault(name, {"tasks": 0, "run_us": 0.0, "gap_us": 0.0, "parts": 0})
+        d["tasks"] += 1
+        d["run_us"] += run_ns / 1e3
+        d["gap_us"] += gap_ns / 1e3
+        d["parts"] += parts
+    run_us = sum(r[1] for r in best["rows"]) / 1e3
+    gap_us = sum(r[2] for r in best["rows"]) / 1e3
+    return {"tasks_on_path": len(best["rows"]), "span_us": best["span_us"],
+            "run_us": run_us, "gap_us": gap_us,
+            "per_task_us": best["span_us"] / len(best["rows"]),
+            "spans_us_of_5_runs": [round(r["span_us"], 1) for r in out],
+            "by_op": {k: {kk: round(vv, 2) if isinstance(vv, float) else vv
+                          for kk, vv in v.items()} for k, v in by_op.items()},
+            "path": [{"op": r[0], "run_us": round(r[1] / 1e3, 2), "gap_us": round(r[2] / 1e3, 2),
+                      "parts": r[3]} for r in best["rows"]],
+            "note": "device %globaltimer; the fastest of 5 traced runs; gap = start of the task "
+                    "minus end of its latest-finishing predecessor"}
 
 
 if __name__ == "__main__":

@@ -45,9 +45,28 @@ typedef struct spx_graph* spx_graph_t;
  *   SPX_COMMUTATIVE_WRITE  reads and writes, but the tasks of one run of
  *                          commutative writes inserted one after another may
  *                          execute in any order, one at a time.
- * A task that names the same tile twice gets the merged mode: READ+READ =
- * READ, COMM+COMM = COMM, anything else = WRITE. */
-enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
+ *   SPX_ATOMIC_WRITE       reads and writes, the task protecting its own
+ *                          updates: ordered like a READ (a run of atomic
+ *                          writes inserted one after another forms one group
+ *                          whose members may run at the same time; accesses
+ *                          of other modes before and after the run are
+ *                          ordered with it).  The tile ops that accept it
+ *                          (GEMM_NN_ADD and AXPY on the written operand)
+ *                          then add into the tile with atomic additions, in
+ *                          an order that varies from run to run.
+ *   SPX_MAYBE_WRITE        the task may or may not write.  The paper attaches
+ *                          speculative execution to it; this library does not
+ *                          speculate, so it is ordered exactly like a WRITE.
+ * A task that names the same tile twice gets the merged mode: the mode when
+ * both agree (READ+READ = READ, COMM+COMM = COMM, ATOMIC+ATOMIC = ATOMIC,
+ * MAYBE+MAYBE = MAYBE), WRITE otherwise. */
+enum {
+  SPX_READ = 0,
+  SPX_WRITE = 1,
+  SPX_COMMUTATIVE_WRITE = 2,
+  SPX_ATOMIC_WRITE = 3,
+  SPX_MAYBE_WRITE = 4
+};
 
 /* Tile operations.  Operand order (the handles[] of spx_task_insert) and the
  * required access mode of each operand are fixed per op:
@@ -77,6 +96,15 @@ enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
  *                                               triangle of L_kk; V_k square,
  *                                               written whole, zero above its
  *                                               diagonal)
+ *   SPX_OP_TRSM_INV     (V_kk:R, A_ik:W)        A_ik <- A_ik V_kk^T with V_kk
+ *                                               = L_kk^{-1} from TRTRI (lower,
+ *                                               zero above the diagonal): the
+ *                                               TRSM of the mixed-precision
+ *                                               factorization as a product on
+ *                                               the tensor cores; prec
+ *                                               SPX_TF32 / SPX_BF16 only (see
+ *                                               the prec enum), A_ik.cols a
+ *                                               multiple of 32
  * Operand element types: SPX_DT_F64 throughout, except that GEMM_FWD,
  * GEMM_BWD and TRMM also take all three operands SPX_DT_F32 (FP32
  * arithmetic) when the written tile has at most 16 columns, and COPY / AXPY
@@ -85,7 +113,9 @@ enum { SPX_READ = 0, SPX_WRITE = 1, SPX_COMMUTATIVE_WRITE = 2 };
  * A write operand may also be given as SPX_COMMUTATIVE_WRITE; such tasks
  * run as one part and take per-tile locks in ascending handle order (the
  * paper locks data handles sorted by address, section "Internal
- * implementation"). */
+ * implementation").  SPX_MAYBE_WRITE is accepted wherever SPX_WRITE is;
+ * SPX_ATOMIC_WRITE only on the written operand of GEMM_NN_ADD and AXPY (and
+ * by NOP / SPIN). */
 enum {
   SPX_OP_POTRF = 0,
   SPX_OP_TRSM = 1,
@@ -102,16 +132,24 @@ enum {
   SPX_OP_AXPY = 12,
   SPX_OP_TRMM = 13,
   SPX_OP_TRTRI = 14,
-  SPX_NUM_OPS = 15
+  SPX_OP_TRSM_INV = 15,
+  SPX_NUM_OPS = 16
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
- * (mixed precision; allowed for TRSM, SYRK and GEMM_NT_SUB): SYRK and
- * GEMM_NT_SUB compute the product of the low-precision copies of their
+ * (mixed precision; allowed for TRSM, TRSM_INV, SYRK and GEMM_NT_SUB): SYRK
+ * and GEMM_NT_SUB compute the product of the low-precision copies of their
  * factor operands on the tensor cores with FP32 accumulation and subtract it
  * from the FP64 output tile; TRSM solves in FP64 and then writes the
  * low-precision copy of its result (round to nearest; TF32 as FP32 with the
- * low 13 mantissa bits cleared). */
+ * low 13 mantissa bits cleared).  TRSM_INV (either prec) forms A_ik V_kk^T
+ * on the tensor cores from split operands: every FP64 entry x is split into
+ * TF32 parts hi + lo (hi = x rounded to TF32, lo = the rest rounded to
+ * TF32; |x - hi - lo| <= about 2^-22 |x|) and the three products
+ * hi*hi + hi*lo + lo*hi accumulate in FP32 (the lo*lo term, about 2^-22
+ * relative, is dropped), i.e. about FP32 accuracy; the FP64 tile receives
+ * the accumulator widened exactly and the low-precision copy its rounding
+ * to the task's type. */
 enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2 };
 
 /* Element type of a registered tile. */
@@ -226,6 +264,34 @@ int spx_graph_derive(spx_graph_t g, void* stream);
  * Errors: SPX_ERR_STATE (running, or empty), SPX_ERR_OOM, SPX_ERR_CUDA. */
 int spx_graph_execute(spx_graph_t g, void* stream);
 
+/* Run several independently built graphs in one persistent launch (the
+ * batched form of spx_graph_execute; the paper's runtime runs each task-graph
+ * object on its own, section "Task graph description"; batching many small
+ * graphs into one launch is this library's).
+ *   gs[ng]   graphs that are built and not running (spx_graph_reset a
+ *            finished one first), each with at least one task, all distinct.
+ * The graphs' tiles, low-precision matrices and tasks are merged, members in
+ * the order gs[0], gs[1], ..., tasks in their insertion order, into one
+ * graph that gs[0] owns (kept for its next batch; freed with gs[0]); its DAG
+ * is derived on the device and run by one persistent kernel with gs[0]'s
+ * configuration (num_ctas, trace, no_split, watchdog; the members' own
+ * executors are not used).  Graphs that share no tile address run as if
+ * each ran alone, with bit-identical results for deterministic tile ops; a
+ * tile address registered in several members orders their accesses as if
+ * the members ran one after another.
+ * Every member is then running.  spx_graph_wait on a member waits for the
+ * launch and returns that member's own status: a POTRF that fails in one
+ * member (SPX_NOT_SPD, info = its column) skips only that member's later
+ * tasks, the other members finish normally; a run-wide error (watchdog,
+ * queue) is returned for every member.  spx_graph_timing and spx_graph_stats
+ * on a finished member report the whole launch; spx_graph_edges, tickets and
+ * trace are not available for members.  After spx_graph_reset a member can
+ * run alone or in another batch.
+ * Errors: SPX_ERR_INVALID_ARG (NULL, ng < 1, a graph given twice, or tiles
+ * of one address with different shapes), SPX_ERR_STATE (a graph running,
+ * finished and not reset, or empty), SPX_ERR_OOM, SPX_ERR_CUDA. */
+int spx_batch_execute(spx_graph_t* gs, int ng, void* stream);
+
 /* Wait for a running graph.  timeout_ns = 0 waits without a host limit (the
  * device watchdog still bounds the run).  info (may be NULL) receives the
  * LAPACK-style column of a failed POTRF, else 0.
@@ -254,6 +320,12 @@ int spx_graph_tickets(spx_graph_t g, unsigned* start, unsigned* end);
  * 4 values per task: start ns, end ns (device %globaltimer), SM id of the
  * first part, number of parts.  Errors: SPX_ERR_STATE (tracing off). */
 int spx_graph_trace(spx_graph_t g, unsigned long long* rec);
+
+/* Op (SPX_OP_*) and scheduling class (0 normal, 1 high, 2 critical path) of
+ * every task, in insertion order: ops[ntasks], priorities[ntasks] (either may
+ * be NULL).  Host data only; any state.  Labels for traces (paper, section
+ * "Visualization").  Errors: SPX_ERR_INVALID_ARG. */
+int spx_graph_task_ops(spx_graph_t g, int* ops, int* priorities);
 
 /* Counters of the last run: out[0] task parts executed, out[1] queue
  * high-water mark (entries), out[2] pops that found the queue empty,
@@ -321,6 +393,25 @@ int spx_cholesky_insert(spx_graph_t g, double* dev_A, int n, int lda, int b, dou
 int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo,
                               int ldlo, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
                               long long* out_ntasks);
+
+/* spx_cholesky_insert_mixed with the panel solves on the tensor cores: per
+ * k, POTRF(k) in FP64, TRTRI(k) writes V_k = L_kk^{-1} (FP64) into the square
+ * block at row k*b of dev_V (n x b FP64 row-major, ldv >= b), and
+ * TRSM_INV(i, k) forms A_ik V_k^T on the tensor cores from split TF32
+ * operands (about FP32 accuracy, see the prec enum) and writes the
+ * low-precision copy of the result.  The TRSM tasks' b^3 flops per tile leave
+ * the FP64 pipe, which they held for most of the mixed factorization's time
+ * (the factor is only accurate to the low precision anyway).  On return dev_V
+ * holds the inverses of all diagonal factor tiles, ready for the correction
+ * solves of refinement (spx_solve_inv_insert, spx_solve_inv_f32_insert).
+ * Solving with the diagonal inverses instead of substituting is a reading of
+ * this library, not of the paper (whose TRSM task is a library call).
+ * b a multiple of 64.  Errors: as spx_cholesky_insert_mixed, and
+ * SPX_ERR_INVALID_ARG for a NULL dev_V or ldv < b. */
+int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                  void* dev_Alo, int ldlo, double* dev_V, int ldv, double* dev_X,
+                                  int nrhs, int ldx, int lookahead, int prec,
+                                  long long* out_ntasks);
 
 /* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
  * already in dev_L (lower triangle, tiles b x b).  Used for the correction
@@ -407,8 +498,11 @@ int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int lda, double*
 
 /* Insert the tiled GEMM C += A B of the paper's numerical applications: one
  * GEMM_NN_ADD task per (i, j, k), i and j outer, k inner, each with a WRITE
- * (or, with commutative = 1, a COMMUTATIVE_WRITE) on the block C_ij.  A, B, C
- * are n x n FP64 row-major with leading dimension ld; tiles b x b. */
+ * (commutative = 0), a COMMUTATIVE_WRITE (1: the tasks of a block run one at
+ * a time in any order) or an ATOMIC_WRITE (2: the tasks of a block run at the
+ * same time and add into it atomically) on the block C_ij.  A, B, C are
+ * n x n FP64 row-major with leading dimension ld; tiles b x b.
+ * Errors: SPX_ERR_INVALID_ARG; as spx_tile_register / spx_task_insert. */
 int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n, int ld,
                     int b, int commutative, long long* out_ntasks);
 
@@ -431,7 +525,8 @@ int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, 
  *                  handle at most once (merge repeated accesses first).
  *   dev_rec_seq    [nrec] position of the record on its handle's list: the
  *                  records of handle h, in task order, have 0, 1, 2, ...
- *   dev_rec_mode   [nrec] SPX_READ / SPX_WRITE / SPX_COMMUTATIVE_WRITE.
+ *   dev_rec_mode   [nrec] SPX_READ / SPX_WRITE / SPX_COMMUTATIVE_WRITE /
+ *                  SPX_ATOMIC_WRITE / SPX_MAYBE_WRITE.
  *   dev_row_ptr    [ntasks+1] out; dev_col [col_cap] out; dev_indeg [ntasks]
  *                  out; dev_status [1] out (device int).
  * Asynchronous on stream.  Host-side errors (returned): SPX_ERR_INVALID_ARG
@@ -490,6 +585,29 @@ int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const* dev_A, co
 int spx_residual_f64(const double* dev_A, int n, int lda, const double* dev_X, int ldx,
                      const double* dev_B, int ldb, double* dev_R, int ldr, int nrhs,
                      double* dev_norms, void* stream);
+
+/* Residual and normwise backward error of iterative refinement, both on the
+ * device: R = B - A X as in spx_residual_f64 (same arguments, norms in
+ * dev_norms [3*nrhs]), then dev_eta[j] = max|r_j| / (||A||_inf max|x_j| +
+ * max|b_j|) for j < nrhs (Rigal-Gaches normwise backward error, the
+ * stopping test of the refinement) and dev_eta[nrhs] = max_j dev_eta[j].
+ * dev_anorm [1] holds ||A||_inf (spx_norm_inf_f64).
+ *   compensated = 0: plain FP64 FMA sums (the fast residual; its rounding
+ *                    error is of the order gamma_n (|A||x| + |b|), as large as
+ *                    eta itself once the refinement has converged).
+ *   compensated = 1: every row summed with Dot2 (Ogita-Rump-Oishi 2005,
+ *                    TwoProduct + TwoSum with separately summed errors):
+ *                    R is as accurate as a residual computed in twice the
+ *                    working precision and rounded, so eta bounds the
+ *                    backward error of X to a relative O(u); about ten FP64
+ *                    operations per term instead of one.
+ * No counterpart in the paper (the workload definition's refinement).
+ * Asynchronous on stream.  Errors: SPX_ERR_INVALID_ARG (as spx_residual_f64,
+ * or NULL dev_anorm / dev_eta, or compensated not 0 / 1), SPX_ERR_CUDA. */
+int spx_residual_eta_f64(const double* dev_A, int n, int lda, const double* dev_X, int ldx,
+                         const double* dev_B, int ldb, double* dev_R, int ldr, int nrhs,
+                         const double* dev_anorm, double* dev_norms, double* dev_eta,
+                         int compensated, void* stream);
 
 /* ||A||_inf (max row sum of |a_ij|) of an n x n FP64 matrix into dev_out[0]. */
 int spx_norm_inf_f64(const double* dev_A, int n, int lda, double* dev_out, void* stream);

@@ -25,9 +25,9 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 SRC = os.path.join(HERE, "spx_oracle.cpp")
 
-READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
+READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (POTRF, TRSM, SYRK, GEMM_NT_SUB, GEMM_NN_ADD, TRSM_L_FWD, GEMM_FWD,
- TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI) = range(15)
+ TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI, TRSM_INV) = range(16)
 
 
 def build(force: bool = False) -> str:
@@ -133,6 +133,34 @@ def cholesky_tasks(T: int, b: int, with_solve: bool = False):
     return tasks
 
 
+def cholesky_inv_tasks(T: int, b: int):
+    """The tiled Cholesky with the panel solves by the inverse of the diagonal
+    tile: for k, POTRF(k), TRTRI(L_kk -> V_k), TRSM_INV(V_k, A_ik) for i > k
+    (A_ik <- A_ik V_k^T, the same L_ik as TRSM up to rounding), then SYRK and
+    GEMM as in cholesky_tasks."""
+    tasks = []
+    for k in range(T):
+        tasks.append((POTRF, [(("A", k, k), WRITE)], k * b))
+        tasks.append((TRTRI, [(("A", k, k), READ), (("V", k), WRITE)], 0))
+        for i in range(k + 1, T):
+            tasks.append((TRSM_INV, [(("V", k), READ), (("A", i, k), WRITE)], 0))
+        for i in range(k + 1, T):
+            tasks.append((SYRK, [(("A", i, k), READ), (("A", i, i), WRITE)], 0))
+        for j in range(k + 1, T):
+            for i in range(j + 1, T):
+                tasks.append((GEMM_NT_SUB, [(("A", i, k), READ), (("A", j, k), READ),
+                                            (("A", i, j), WRITE)], 0))
+    return tasks
+
+
+def tiled_cholesky_inv(A: np.ndarray, b: int, V: np.ndarray) -> int:
+    """cholesky_inv_tasks on A in place; V (n x b) receives the inverses of
+    the diagonal factor tiles.  Returns info."""
+    n = A.shape[0]
+    T = -(-n // b)
+    return execute(cholesky_inv_tasks(T, b), {"A": A, "V": V}, b)
+
+
 def trtri_tasks(T: int):
     """Inverse of every diagonal factor tile: V_k <- L_kk^{-1}."""
     return [(TRTRI, [(("A", k, k), READ), (("V", k), WRITE)], 0) for k in range(T)]
@@ -165,10 +193,12 @@ def trtri(L: np.ndarray) -> np.ndarray:
     return V
 
 
-def gemm_tasks(T: int, commutative: bool = False):
+def gemm_tasks(T: int, commutative: bool = False, mode: int | None = None):
     """Tiled C += A B with one task per (i, j, k), i and j outer, k inner; each
-    task depends on the block C_ij it updates (section "Numerical applications")."""
-    mode = COMMUTATIVE_WRITE if commutative else WRITE
+    task depends on the block C_ij it updates (section "Numerical applications"),
+    with a WRITE, a COMMUTATIVE_WRITE (commutative) or any given mode."""
+    if mode is None:
+        mode = COMMUTATIVE_WRITE if commutative else WRITE
     tasks = []
     for i in range(T):
         for j in range(T):

@@ -50,7 +50,11 @@
 extern "C" {
 
 // Access modes (section "Task insertion").
-enum { O_READ = 0, O_WRITE = 1, O_COMMUTE = 2 };
+// Access modes (section "Task insertion"): SpRead, SpWrite,
+// SpCommutativeWrite, SpAtomicWrite (handled like a read by the runtime: a run
+// of them is one group; the task protects its own writes) and SpMaybeWrite
+// (a possible write; without speculation it orders exactly like a write).
+enum { O_READ = 0, O_WRITE = 1, O_COMMUTE = 2, O_ATOMIC = 3, O_MAYBE = 4 };
 
 // Tile operations of the tiled Cholesky (section "Numerical applications")
 // and of the block solve / tiled GEMM workloads.
@@ -69,7 +73,8 @@ enum {
   O_COPY = 11,        // Y <- X
   O_AXPY = 12,        // Y <- Y + X
   O_TRMM = 13,        // Y <- T X (arg 0) or T^T X (arg 1), T lower triangular
-  O_TRTRI = 14        // V <- L^{-1}, L lower triangular
+  O_TRTRI = 14,       // V <- L^{-1}, L lower triangular
+  O_TRSM_INV = 15     // A_ik <- A_ik V^T, V = L_kk^{-1} (the TRSM by the inverse)
 };
 
 // ---------------------------------------------------------------------------
@@ -77,15 +82,17 @@ enum {
 // ---------------------------------------------------------------------------
 
 // One group on a handle's dependency list: a run of READs, a run of
-// COMMUTATIVE_WRITEs inserted one after the other, or a single WRITE.
+// COMMUTATIVE_WRITEs inserted one after the other, a run of ATOMIC_WRITEs, or
+// a single WRITE or MAYBE_WRITE.
 struct Group {
   int mode;
   std::vector<uint32_t> tasks;
 };
 
 // Merge two modes of the same task on the same handle.  The paper is silent;
-// the reading used here: READ+READ = READ, COMM+COMM = COMM, anything else
-// (a WRITE involved, or READ mixed with COMM) = WRITE.
+// the reading used here: the same mode twice stays that mode (READ+READ =
+// READ, COMM+COMM = COMM, ATOMIC+ATOMIC = ATOMIC, MAYBE+MAYBE = MAYBE), any
+// two different modes give WRITE.
 static int merge_mode(int a, int b) {
   if (a == b) return a;
   return O_WRITE;
@@ -112,7 +119,7 @@ long long spxo_derive(int ntasks, long long nacc, const uint32_t* acc_task,
     std::vector<std::pair<uint64_t, int>> mine;
     while (a < nacc && acc_task[a] == t) {
       const int m = acc_mode[a];
-      if (m < O_READ || m > O_COMMUTE) return -1;
+      if (m < O_READ || m > O_MAYBE) return -1;
       bool found = false;
       for (auto& km : mine) {
         if (km.first == acc_key[a]) {
@@ -128,7 +135,7 @@ long long spxo_derive(int ntasks, long long nacc, const uint32_t* acc_task,
       std::vector<Group>& list = handles[km.first];
       const int m = km.second;
       const bool joins = !list.empty() && list.back().mode == m &&
-                         (m == O_READ || m == O_COMMUTE);
+                         (m == O_READ || m == O_COMMUTE || m == O_ATOMIC);
       if (joins) {
         // Same run as the last group: depends on the group before it.
         if (list.size() >= 2) {
@@ -303,6 +310,20 @@ static void trmm(const double* t, int ldt, bool trans, const double* x, int ldx,
     }
 }
 
+// A <- A V^T (A m x n, V n x n): plain matrix product over the whole of V,
+// one row of A at a time through a copy of the row (the update is in place).
+static void trsm_inv(const double* v, int ldv, double* a, int lda, int m, int n) {
+  std::vector<double> row(n);
+  for (int i = 0; i < m; ++i) {
+    for (int k = 0; k < n; ++k) row[k] = a[(size_t)i * lda + k];
+    for (int c = 0; c < n; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s = s + row[k] * v[(size_t)c * ldv + k];
+      a[(size_t)i * lda + c] = s;
+    }
+  }
+}
+
 // A tile: base pointer, shape and leading dimension (row-major).
 typedef struct {
   double* ptr;
@@ -409,6 +430,12 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
         const spxo_tile& L = tile(0);
         const spxo_tile& V = tile(1);
         spxo_trtri(L.ptr, L.ld, V.ptr, L.rows, V.ld);
+        break;
+      }
+      case O_TRSM_INV: {
+        const spxo_tile& V = tile(0);
+        const spxo_tile& A = tile(1);
+        trsm_inv(V.ptr, V.ld, A.ptr, A.ld, A.rows, A.cols);
         break;
       }
       case O_NOP:

@@ -37,6 +37,16 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
+def _obj_up_to_date(src: str, obj: str) -> bool:
+    dep = obj + ".d"
+    if not (os.path.exists(obj) and os.path.exists(dep)):
+        return False
+    text = open(dep).read().replace("\\\n", " ")
+    files = text.split(":", 1)[1].split() if ":" in text else []
+    t = os.path.getmtime(obj)
+    return all(os.path.exists(f) and os.path.getmtime(f) <= t for f in files + [src])
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
@@ -49,17 +59,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
               "-fno-unswitch-loops", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr", "-prec-div=true", "-prec-sqrt=true", "-fmad=true"]
     objs, procs = [], []
-    # one nvcc per source, all at once (the persistent kernel's file dominates)
+    # one nvcc per out-of-date source, all at once; each object's header
+    # dependencies come from the .d file nvcc wrote beside it
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = [NVCC, *ARCH, *common, "-c", src, "-o", obj]
+        objs.append(obj)
+        if not force and _obj_up_to_date(src, obj):
+            continue
+        cmd = [NVCC, *ARCH, *common, "-MD", "-MF", obj + ".d", "-c", src, "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         else:
             cmd += ["-x", "cu"]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
                                             text=True)))
-        objs.append(obj)
     failed = None
     for src, pr in procs:
         out, err = pr.communicate()

@@ -35,13 +35,15 @@ def cholesky_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, prec
     return nt.value
 
 
-def gemm_graph(g: spx.Graph, A, B, C, b: int, commutative: bool = False):
-    """Insert C += A B, one task per (i, j, k), i and j outer, k inner."""
+def gemm_graph(g: spx.Graph, A, B, C, b: int, commutative: bool = False, atomic: bool = False):
+    """Insert C += A B, one task per (i, j, k), i and j outer, k inner, with a
+    WRITE, COMMUTATIVE_WRITE (commutative) or ATOMIC_WRITE (atomic) on C_ij."""
     n = A.shape[0]
     assert A.stride(0) == B.stride(0) == C.stride(0)
     nt = ctypes.c_longlong()
+    sel = 2 if atomic else (1 if commutative else 0)
     spx._check(spx.lib.spx_gemm_insert(g._h, _ptr(A), _ptr(B), _ptr(C), n, A.stride(0), b,
-                                       1 if commutative else 0, ctypes.byref(nt)), "spx_gemm_insert")
+                                       sel, ctypes.byref(nt)), "spx_gemm_insert")
     g._keep.extend([A, B, C])
     return nt.value
 

@@ -64,7 +64,7 @@ __device__ bool validate(const DevGraph& g, uint32_t* sh, int* status) {
     if (r1 <= r0 || r1 - r0 > (uint32_t)kMaxHandles || r1 > M) bad = 1;
   }
   for (uint32_t r = tid; r < M; r += kDeriveThreads) {
-    if (g.rec_handle[r] >= H || g.rec_mode[r] > SPX_COMMUTATIVE_WRITE) bad = 1;
+    if (g.rec_handle[r] >= H || g.rec_mode[r] > SPX_MAYBE_WRITE) bad = 1;
     else atomicAdd(&g.hptr[g.rec_handle[r]], 1u);
   }
   __syncthreads();

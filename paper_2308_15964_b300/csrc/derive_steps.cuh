@@ -63,9 +63,12 @@ __device__ uint32_t block_excl_scan(uint32_t* a, uint32_t n, uint32_t* sh) {
   return carry;
 }
 
+// A list entry opens a new group unless it continues a run of READs, of
+// COMMUTATIVE_WRITEs or of ATOMIC_WRITEs; a WRITE or MAYBE_WRITE is a group of
+// its own.
 __device__ __forceinline__ bool group_start(const DevGraph& g, uint32_t p) {
   const uint8_t m = g.s_mode[p];
-  return g.s_first[p] || m == SPX_WRITE || m != g.s_mode[p - 1];
+  return g.s_first[p] || m == SPX_WRITE || m == SPX_MAYBE_WRITE || m != g.s_mode[p - 1];
 }
 
 // Unique successors of task u: merge of the next-group ranges of its

@@ -43,14 +43,15 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Layout of the single device allocation (and of the pinned upload mirror
 // for its first region).  Offsets in bytes, 256-aligned.
 struct Layout {
-  size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, upload_end;
+  size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, task_group, upload_end;
   size_t queue[kQueues], t_start, ff_end;
-  size_t rs, locks, t_end, trace, phase, qclaim[kQueues], zero_end;
+  size_t rs, locks, t_end, trace, phase, qclaim[kQueues], groups, zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
 
-Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, bool trace) {
+Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, bool trace,
+                   size_t NG) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -65,6 +66,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.rec_seq = take(M * 4);
   L.rec_mode = take(M);
   L.task_rec = take((N + 1) * 4);
+  L.task_group = take(NG ? N * 4 : 0);
   L.upload_end = o;
   for (int q = 0; q < kQueues; ++q) L.queue[q] = take(Q * 4);
   L.t_start = take(N * 4);
@@ -75,6 +77,7 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.trace = take(trace ? N * 32 : 0);
   L.phase = take(N * 4);
   for (int q = 0; q < kQueues; ++q) L.qclaim[q] = take(Q * 4);
+  L.groups = take(NG * sizeof(GroupState));
   L.zero_end = o;
   L.hptr = take((H + 1) * 4);
   L.s_task = take(M * 4);
@@ -140,6 +143,18 @@ struct spx_graph {
   cudaStream_t xs[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> task_ev;
+  // batched execution (spx_batch_execute).  The first graph of a batch owns
+  // the merged graph that runs it (batch); every member points to the
+  // merged graph of its last batched run (batch_of).  The merged graph keeps
+  // its members, the member of each of its tasks and a pinned copy of the
+  // members' statuses.
+  spx_graph* batch = nullptr;
+  spx_graph* batch_of = nullptr;
+  uint32_t batch_index = 0;
+  std::vector<spx_graph*> members;
+  std::vector<uint32_t> task_group;
+  GroupState* host_groups = nullptr;
+  size_t host_groups_cap = 0;
 };
 
 namespace {
@@ -152,11 +167,13 @@ int cuda_fail(cudaError_t e) {
 }
 
 // Operand count, shape and mode checks of the built-in ops.
+// Operand count of each built-in op (-1: any, 1..16).
+const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2};
+
 int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
                    const unsigned* h, const int* m, int nh) {
-  static const int want_nh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2};
   if (op == SPX_OP_NOP || op == SPX_OP_SPIN) return SPX_OK;
-  if (nh != want_nh[op]) return SPX_ERR_INVALID_ARG;
+  if (nh != kWantNh[op]) return SPX_ERR_INVALID_ARG;
   // FP64 throughout, except: the solve updates (GEMM_FWD, GEMM_BWD, TRMM)
   // also run with all operands FP32 on at most 16 right-hand-side columns,
   // and COPY / AXPY convert between FP64 and FP32 in either direction.
@@ -171,7 +188,10 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
       if (h[i] == h[j]) return SPX_ERR_INVALID_ARG;
   }
   const int w = nh - 1;  // written operand is the last one
-  if (m[w] != SPX_WRITE && m[w] != SPX_COMMUTATIVE_WRITE) return SPX_ERR_INVALID_ARG;
+  const bool atomic_ok = op == SPX_OP_GEMM_NN_ADD || op == SPX_OP_AXPY;
+  if (m[w] != SPX_WRITE && m[w] != SPX_COMMUTATIVE_WRITE && m[w] != SPX_MAYBE_WRITE &&
+      !(m[w] == SPX_ATOMIC_WRITE && atomic_ok))
+    return SPX_ERR_INVALID_ARG;
   auto R = [&](int i) { return t[h[i]].rows; };
   auto C = [&](int i) { return t[h[i]].cols; };
   bool ok = true;
@@ -189,6 +209,7 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     case SPX_OP_AXPY: ok = R(0) == R(1) && C(0) == C(1); break;
     case SPX_OP_TRMM: ok = R(0) == C(0) && C(0) == R(1) && R(2) == R(0) && C(2) == C(1); break;
     case SPX_OP_TRTRI: ok = R(0) == C(0) && R(1) == R(0) && C(1) == C(0); break;
+    case SPX_OP_TRSM_INV: ok = R(0) == C(0) && C(1) == R(0) && C(1) % 32 == 0; break;
     default: ok = false;
   }
   if (all_f32 && C(nh - 1) > 16) ok = false;
@@ -223,7 +244,8 @@ int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
   const int want = prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32;
   int ins[2] = {-1, -1};
   switch (op) {
-    case SPX_OP_TRSM: ins[0] = (int)h[1]; break;
+    case SPX_OP_TRSM:
+    case SPX_OP_TRSM_INV: ins[0] = (int)h[1]; break;
     case SPX_OP_SYRK: ins[0] = (int)h[0]; break;
     case SPX_OP_GEMM_NT_SUB: ins[0] = (int)h[0]; ins[1] = (int)h[1]; break;
     default: return SPX_ERR_INVALID_ARG;
@@ -237,7 +259,8 @@ int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
     const int chunk = 128 / mi.elem;  // K elements per TMA box
     if (t.lc0 % chunk) return SPX_ERR_INVALID_ARG;
     // a partial last K chunk must run past the matrix edge (read as zeros)
-    if (op != SPX_OP_TRSM && t.cols % chunk && t.lc0 + t.cols != mi.cols_)
+    if (op != SPX_OP_TRSM && op != SPX_OP_TRSM_INV && t.cols % chunk &&
+        t.lc0 + t.cols != mi.cols_)
       return SPX_ERR_INVALID_ARG;
   }
   return SPX_OK;
@@ -274,7 +297,8 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
       std::max(std::max(g->items[0], g->items[1]), g->items[2]), 1);
   if (g->cfg.queue_capacity > 0) Q = (size_t)g->cfg.queue_capacity;
   if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
-  const Layout L = make_layout(N, H, M, E, Q, g->maps.size(), g->cfg.trace != 0);
+  const size_t NG = g->task_group.empty() ? 0 : g->members.size();
+  const Layout L = make_layout(N, H, M, E, Q, g->maps.size(), g->cfg.trace != 0, NG);
   if (g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
@@ -316,6 +340,7 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   std::memcpy(P + L.rec_seq, g->rec_seq.data(), M * 4);
   std::memcpy(P + L.rec_mode, g->rec_mode.data(), M);
   std::memcpy(P + L.task_rec, g->task_rec.data(), (N + 1) * 4);
+  if (NG) std::memcpy(P + L.task_group, g->task_group.data(), N * 4);
   cudaError_t e = cudaMemcpyAsync(g->dmem, g->pinned, L.upload_end, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e);
 
@@ -359,6 +384,8 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.indeg_w = (uint32_t*)(D + L.indeg_w);
   d.remaining = (uint32_t*)(D + L.remaining);
   d.phase = (uint32_t*)(D + L.phase);
+  d.task_group = NG ? (const uint32_t*)(D + L.task_group) : nullptr;
+  d.groups = NG ? (GroupState*)(D + L.groups) : nullptr;
   g->lay = L;
   g->uploaded = true;
   g->derived = false;
@@ -484,17 +511,18 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   if (g->tasks.size() >= kMaxTasks) return SPX_ERR_INVALID_ARG;
   for (int i = 0; i < nh; ++i) {
     if (handles[i] >= g->tiles.size()) return SPX_ERR_BAD_HANDLE;
-    if (modes[i] < SPX_READ || modes[i] > SPX_COMMUTATIVE_WRITE) return SPX_ERR_INVALID_ARG;
+    if (modes[i] < SPX_READ || modes[i] > SPX_MAYBE_WRITE) return SPX_ERR_INVALID_ARG;
   }
   int rc = check_operands(op, g->tiles, g->tile_dtype, handles, modes, nh);
   if (rc != SPX_OK) return rc;
+  if (op == SPX_OP_TRSM_INV && prec == SPX_F64) return SPX_ERR_INVALID_ARG;  // tensor cores only
   if (prec != SPX_F64) {
     rc = check_lowp(g, op, prec, handles);
     if (rc != SPX_OK) return rc;
   }
 
-  // Merge repeated handles (READ+READ = READ, COMM+COMM = COMM, else WRITE)
-  // and order this task's accesses by handle (the lock order on the device).
+  // Merge repeated handles (the same mode twice stays, else WRITE) and order
+  // this task's accesses by handle (the lock order on the device).
   uint32_t hh[kMaxHandles];
   int mm[kMaxHandles];
   int k = 0;
@@ -520,8 +548,13 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   t.prec = (uint8_t)prec;
   t.prio = (uint8_t)(priority > 2 ? 2 : priority);
   t.flags = priority >= 2 ? kFlagFine : 0;
-  for (int i = 0; i < k; ++i)
+  for (int i = 0; i < k; ++i) {
     if (mm[i] == SPX_COMMUTATIVE_WRITE) t.flags |= kFlagComm;
+    // the written operand of GEMM_NN_ADD / AXPY accumulated atomically
+    if (mm[i] == SPX_ATOMIC_WRITE && hh[i] == handles[nh - 1] &&
+        (op == SPX_OP_GEMM_NN_ADD || op == SPX_OP_AXPY))
+      t.flags |= kFlagAtomic;
+  }
   for (int i = 0; i < 3; ++i) t.h[i] = i < nh ? handles[i] : 0;
   uint32_t items = 1;  // queue entries over all phases
   if (g->cfg.no_split || (t.flags & kFlagComm)) {
@@ -542,7 +575,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   for (int i = 0; i < k; ++i) {
     HandleState& s = g->hstate[hh[i]];
     const int m = mm[i];
-    if (s.last_mode == m && m != SPX_WRITE) {
+    if (s.last_mode == m && m != SPX_WRITE && m != SPX_MAYBE_WRITE) {
       g->cand_edges += s.prev_size;
       s.last_size += 1;
     } else {
@@ -700,6 +733,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
   if (g->tasks.empty()) return SPX_ERR_STATE;
+  g->batch_of = nullptr;  // runs alone from now on
   cudaStream_t st = (cudaStream_t)stream;
   int rc = SPX_OK;
   cudaError_t e = cudaSuccess;
@@ -756,6 +790,9 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
   if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && g->dg.groups)
+    e = cudaMemcpyAsync(g->host_groups, g->dg.groups, g->members.size() * sizeof(GroupState),
+                        cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(g->done_ev, st);
   if (e != cudaSuccess) return cuda_fail(e);
   g->last_stream = st;
@@ -771,6 +808,26 @@ int spx_graph_wait(spx_graph_t g, unsigned long long timeout_ns, int* info) {
     return g->last_status;
   }
   if (g->state != kRunning) return SPX_ERR_STATE;
+  if (g->batch_of) {
+    // a member of a batched run: wait for the merged graph, then give every
+    // member its own status (a run-wide error, else the member's)
+    spx_graph* B = g->batch_of;
+    const int rc = spx_graph_wait(B, timeout_ns, nullptr);
+    if (rc == SPX_ERR_TIMEOUT && B->state == kRunning) return rc;
+    for (spx_graph* m : B->members) {
+      if (!m || m->batch_of != B || m->state != kRunning) continue;
+      m->state = kDone;
+      if (B->last_status != SPX_OK) {
+        m->last_status = B->last_status;
+        m->last_info = B->last_info;
+      } else {
+        m->last_status = (int)(int32_t)B->host_groups[m->batch_index].status;
+        m->last_info = B->host_groups[m->batch_index].info;
+      }
+    }
+    if (info) *info = g->last_info;
+    return g->last_status;
+  }
   const auto t0 = std::chrono::steady_clock::now();
   long spins = 0;
   for (;;) {
@@ -851,8 +908,18 @@ int spx_graph_trace(spx_graph_t g, unsigned long long* rec) {
   return e == cudaSuccess ? SPX_OK : cuda_fail(e);
 }
 
+int spx_graph_task_ops(spx_graph_t g, int* ops, int* priorities) {
+  if (!g || (!ops && !priorities)) return SPX_ERR_INVALID_ARG;
+  for (size_t i = 0; i < g->tasks.size(); ++i) {
+    if (ops) ops[i] = g->tasks[i].op;
+    if (priorities) priorities[i] = g->tasks[i].prio;
+  }
+  return SPX_OK;
+}
+
 int spx_graph_stats(spx_graph_t g, long long* out, int n) {
   if (!g || !out || n < 0) return SPX_ERR_INVALID_ARG;
+  if (g->batch_of && g->state == kDone) g = g->batch_of;  // the batched run
   if (g->state != kDone) return SPX_ERR_STATE;
   const RunState& r = *g->host_rs;
   long long v[9 + SPX_NUM_OPS] = {
@@ -878,7 +945,8 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
   if (!f) return SPX_ERR_INVALID_ARG;
   static const char* names[SPX_NUM_OPS] = {"POTRF", "TRSM", "SYRK", "GEMM", "GEMM_NN",
                                            "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
-                                           "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI"};
+                                           "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI",
+                                           "TRSM_INV"};
   std::fprintf(f, "digraph spx {\n");
   for (size_t u = 0; u < N; ++u)
     std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);
@@ -890,6 +958,7 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
 }
 
 int spx_graph_timing(spx_graph_t g, float* prep_ms, float* run_ms) {
+  if (g && g->batch_of && g->state == kDone) g = g->batch_of;  // the batched run
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state != kDone || !g->tev[0]) return SPX_ERR_STATE;
   float a = 0.f, b = 0.f;
@@ -911,6 +980,7 @@ int spx_graph_reset(spx_graph_t g) {
 int spx_graph_clear(spx_graph_t g) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning) return SPX_ERR_STATE;
+  g->batch_of = nullptr;
   g->tiles.clear();
   g->tile_dtype.clear();
   g->maps.clear();
@@ -936,9 +1006,112 @@ int spx_graph_clear(spx_graph_t g) {
   return SPX_OK;
 }
 
+int spx_batch_execute(spx_graph_t* gs, int ng, void* stream) {
+  if (!gs || ng < 1) return SPX_ERR_INVALID_ARG;
+  for (int i = 0; i < ng; ++i) {
+    if (!gs[i]) return SPX_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (gs[j] == gs[i]) return SPX_ERR_INVALID_ARG;
+    if (gs[i]->state == kRunning || gs[i]->state == kDone) return SPX_ERR_STATE;
+    if (gs[i]->tasks.empty()) return SPX_ERR_STATE;
+  }
+  spx_graph* owner = gs[0];
+  if (owner->batch && owner->batch->state == kRunning) return SPX_ERR_STATE;
+  if (!owner->batch) {
+    spx_graph_config_t cfg = owner->cfg;
+    cfg.executor = SPX_EXEC_PERSISTENT;
+    cfg.cuda_graph = 0;
+    const int rc = spx_graph_create(&owner->batch, &cfg);
+    if (rc != SPX_OK) return rc;
+  }
+  spx_graph* B = owner->batch;
+  for (spx_graph* m : B->members)  // the previous batch's members run alone now
+    if (m && m->batch_of == B) m->batch_of = nullptr;
+  spx_graph_clear(B);
+  B->members.assign(gs, gs + ng);
+  B->task_group.clear();
+  // Merge: every member's tiles (one handle per address), low-precision
+  // matrices and tasks, members in order, tasks in insertion order.
+  std::vector<unsigned> hmap;
+  for (int i = 0; i < ng; ++i) {
+    const spx_graph* m = gs[i];
+    for (const auto& mi : m->map_info) {
+      const int rows = (int)(mi.bytes / ((size_t)mi.ld * mi.elem));
+      const int rc = spx_lowp_register(B, (void*)mi.base, rows, mi.cols_, mi.ld, mi.dtype, nullptr);
+      if (rc != SPX_OK) return rc;
+    }
+    hmap.assign(m->tiles.size(), 0);
+    for (size_t h = 0; h < m->tiles.size(); ++h) {
+      const TileDesc& t = m->tiles[h];
+      const int rc = spx_tile_register(B, t.ptr, t.rows, t.cols, t.ld, m->tile_dtype[h], t.lowp,
+                                       t.lowp ? t.lowp_ld : 0, &hmap[h]);
+      if (rc != SPX_OK) return rc;
+    }
+    for (size_t u = 0; u < m->tasks.size(); ++u) {
+      const TaskDesc& t = m->tasks[u];
+      const uint32_t r0 = m->task_rec[u], r1 = m->task_rec[u + 1];
+      unsigned hh[kMaxHandles];
+      int mm[kMaxHandles];
+      int nh = 0;
+      if (kWantNh[t.op] < 0) {  // NOP / SPIN: the merged accesses
+        for (uint32_t r = r0; r < r1; ++r, ++nh) {
+          hh[nh] = hmap[m->rec_handle[r]];
+          mm[nh] = m->rec_mode[r];
+        }
+      } else {                   // the op's operands in order, with their modes
+        nh = kWantNh[t.op];
+        for (int j = 0; j < nh; ++j) {
+          hh[j] = hmap[t.h[j]];
+          mm[j] = SPX_READ;
+          for (uint32_t r = r0; r < r1; ++r)
+            if (m->rec_handle[r] == t.h[j]) mm[j] = m->rec_mode[r];
+        }
+      }
+      unsigned tid = 0;
+      int rc = spx_task_insert(B, t.op, hh, mm, nh, t.prio, t.prec, &tid);
+      if (rc == SPX_OK) rc = spx_task_set_arg(B, tid, t.arg);
+      if (rc != SPX_OK) return rc;
+      B->task_group.push_back((uint32_t)i);
+    }
+  }
+  if (B->host_groups_cap < (size_t)ng) {
+    if (B->host_groups) cudaFreeHost(B->host_groups);
+    B->host_groups = nullptr;
+    B->host_groups_cap = 0;
+    const cudaError_t e =
+        cudaHostAlloc((void**)&B->host_groups, ng * sizeof(GroupState), cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(e);
+    B->host_groups_cap = (size_t)ng;
+  }
+  const int rc = spx_graph_execute(B, stream);
+  if (rc != SPX_OK) return rc;
+  for (int i = 0; i < ng; ++i) {
+    gs[i]->batch_of = B;
+    gs[i]->batch_index = (uint32_t)i;
+    gs[i]->state = kRunning;
+  }
+  return SPX_OK;
+}
+
 void spx_graph_destroy(spx_graph_t g) {
   if (!g) return;
   if (g->state == kRunning) spx_graph_wait(g, 0, nullptr);
+  if (g->batch_of) {  // leave the merged graph's member list
+    for (spx_graph*& m : g->batch_of->members)
+      if (m == g) m = nullptr;
+  }
+  if (g->batch) {     // the merged graph this graph owns: detach its members
+    if (g->batch->state == kRunning) spx_graph_wait(g->batch, 0, nullptr);
+    for (spx_graph* m : g->batch->members)
+      if (m && m != g && m->batch_of == g->batch) {
+        if (m->state == kRunning) spx_graph_wait(m, 0, nullptr);
+        m->batch_of = nullptr;
+      }
+    g->batch->members.clear();
+    spx_graph_destroy(g->batch);
+    g->batch = nullptr;
+  }
+  if (g->host_groups) cudaFreeHost(g->host_groups);
   if (g->last_stream) cudaStreamSynchronize(g->last_stream);
   if (g->dmem) cudaFree(g->dmem);
   if (g->pinned) cudaFreeHost(g->pinned);

@@ -264,7 +264,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_GEMM_NN_ADD:
       op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s,
-                           t.flags & kFlagFine);
+                           t.flags & kFlagFine, t.flags & kFlagAtomic);
       return 0;
     case SPX_OP_TRSM_L_FWD:
       op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
@@ -294,7 +294,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_COPY:
     case SPX_OP_AXPY:
-      op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY);
+      op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY, t.flags & kFlagAtomic);
       return 0;
     case SPX_OP_TRMM:
       if (T[t.h[0]].dtype == SPX_DT_F32)
@@ -302,6 +302,14 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       else
         op_trmm<double>(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
       return 0;
+    case SPX_OP_TRSM_INV:
+      if constexpr (kTc) {
+        const bool ok = t.prec == SPX_BF16
+                            ? op_tc_trsm_inv<true>(T[t.h[0]], T[t.h[1]], u0, u1, tc)
+                            : op_tc_trsm_inv<false>(T[t.h[0]], T[t.h[1]], u0, u1, tc);
+        return ok ? 0 : -2;
+      }
+      return -1;
     case SPX_OP_TRTRI:
       if (phase == 0) op_identity(T[t.h[1]], u0, u1);
       else op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase - 1, u0, u1, s);
@@ -626,9 +634,11 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     const TaskDesc t = g.tasks[u];
     // the phase was written before its parts were pushed (and fenced)
     const uint32_t phase = t.nphases > 1 ? ld_volatile(&g.phase[u]) : 0u;
-    const uint32_t req = kServer ? g.task_req[u] : 0u;
-    // a request whose task failed drains without running its other tasks
-    const bool skip = kServer && ld_volatile(&g.reqs[req].status) != 0u;
+    const uint32_t req = kServer ? g.task_req[u] : (g.task_group ? g.task_group[u] : 0u);
+    // a request (or a member of a batched run) whose task failed drains
+    // without running its other tasks
+    const bool skip = kServer ? ld_volatile(&g.reqs[req].status) != 0u
+                              : (g.task_group && ld_volatile(&g.groups[req].status) != 0u);
     const long long c0 = clock64();
     if (tid == 0) {
       s_flag = 1;
@@ -654,7 +664,12 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         if (atomicCAS(&g.reqs[req].status, 0u, (uint32_t)SPX_NOT_SPD) == 0u)
           g.reqs[req].info = (int)t.arg + info;
       }
-      if (info > 0 && !kServer) {
+      if (info > 0 && !kServer && g.task_group) {
+        // the batch member fails; the other members go on
+        if (atomicCAS(&g.groups[req].status, 0u, (uint32_t)SPX_NOT_SPD) == 0u)
+          g.groups[req].info = (int)t.arg + info;
+      }
+      if (info > 0 && !kServer && !g.task_group) {
         set_error(rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
         s_flag = 0;
       } else if (info < 0) {

@@ -35,7 +35,9 @@ constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 // the task is on the critical path (inserted with priority >= 2): its POTRF,
 // TRSM and FP64 SYRK / GEMM phases use smaller units so that more SMs share
 // it.
-enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2, kFlagFine = 4 };
+// kFlagAtomic: the written operand is an ATOMIC_WRITE (the op adds into it
+// with atomic additions).
+enum TaskFlags : uint8_t { kFlagComm = 1, kFlagSerial = 2, kFlagFine = 4, kFlagAtomic = 8 };
 
 // One registered tile (a data handle of the STF model).
 struct TileDesc {
@@ -128,6 +130,12 @@ struct RunState {
   unsigned long long op_cycles[16];  // busy cycles by op (SPX_NUM_OPS <= 16)
 };
 
+// Status of one member graph of a batched run.
+struct GroupState {
+  uint32_t status;  // SPX_OK or SPX_NOT_SPD
+  int32_t info;     // failed POTRF column (1-based)
+};
+
 // Pointers and sizes handed to the device kernels by value.
 struct DevGraph {
   uint32_t ntasks, ntiles, nrec, ecap;
@@ -170,6 +178,12 @@ struct DevGraph {
   uint32_t* t_end;             // [ntasks]
   unsigned long long* trace_rec;  // [4*ntasks] when trace
   RunState* rs;
+  // batched graph runs (spx_batch_execute): the member graph of each task and
+  // each member's status; nullptr otherwise.  A POTRF failure then fails its
+  // member only: that member's later tasks are skipped (popped and released
+  // without running), the other members go on.
+  const uint32_t* task_group;  // [ntasks]
+  GroupState* groups;          // [members], zero at the start of a run
   // server mode only (server = 1): ring queues, requests, host control
   uint32_t server;
   uint32_t pad_;
@@ -200,6 +214,10 @@ struct DevGraph {
 //     for the POTRF and SYRK updates: one SM
 //     does about 2 FP64 FMA per clock, so a 64 x 64 x 64 unit alone takes
 //     tens of microseconds, and the critical path is a chain of such units.
+//   TRSM_INV (A_ik <- A_ik V^T, tensor cores): one phase, 128-row blocks of
+//     A_ik (each block runs its 128-column output blocks right to left: output
+//     column c needs input columns <= c only, V being lower triangular, so
+//     the block is updated in place).
 //   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
 //     blocks.  TRMM: one phase, the units of GEMM_FWD.  TRTRI (V <- L^{-1}):
 //     phase 0 writes the identity into V (64-row units), phases 1.. are the
@@ -293,6 +311,8 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     case SPX_OP_AXPY: return cdiv64(t[h[1]].rows);
     case SPX_OP_TRMM:
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
+    case SPX_OP_TRSM_INV:  // 128-row blocks of A_ik (tensor cores)
+      return cdiv128(t[h[1]].rows);
     case SPX_OP_TRTRI:  // phase 0 writes the identity (64-row units), then the forward solve
       return phase == 0 ? cdiv64(t[h[1]].rows)
                         : solve_phase_units(true, t[h[0]].rows, t[h[1]].cols, phase - 1);

@@ -50,7 +50,7 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 template <bool A_T, bool B_KN, int CJ = 4, int RI = 4>
 __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
                            int m, int n, int K, double alpha, bool lower, GemmSmem& s,
-                           bool set = false) {
+                           bool set = false, bool atomic = false) {
   constexpr int BN = 16 * CJ;  // columns of the block
   constexpr int BM = 16 * RI;  // rows of the block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -102,7 +102,8 @@ __device__ void gemm_block(double* C, int ldc, const double* A, int lda, const d
       const int c = tx + 16 * j;
       if (r < m && c < n && (!lower || c <= r)) {
         double* p = C + (size_t)r * ldc + c;
-        *p = set ? alpha * acc[i][j] : __ldcg(p) + alpha * acc[i][j];
+        if (atomic) atomicAdd(p, alpha * acc[i][j]);  // ATOMIC_WRITE on C
+        else *p = set ? alpha * acc[i][j] : __ldcg(p) + alpha * acc[i][j];
       }
     }
   }
@@ -544,7 +545,8 @@ __device__ void op_syrk(const TileDesc& Lt, const TileDesc& Ct, uint32_t u0, uin
 // for fine tasks).
 template <bool A_T, bool B_KN>
 __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& Ct, int K,
-                        double alpha, uint32_t u0, uint32_t u1, F64Smem& s, bool fine) {
+                        double alpha, uint32_t u0, uint32_t u1, F64Smem& s, bool fine,
+                        bool atomic = false) {
   const double* a = (const double*)At.ptr;
   const double* b = (const double*)Bt.ptr;
   double* c = (double*)Ct.ptr;
@@ -557,11 +559,14 @@ __device__ void op_gemm(const TileDesc& At, const TileDesc& Bt, const TileDesc& 
     double* cp = c + (size_t)r0 * Ct.ld + c0;
     const int mb = min(rb, Ct.rows - r0), nb = min(kBlk, Ct.cols - c0);
     if (fine)
-      gemm_block<A_T, B_KN, 4, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
+      gemm_block<A_T, B_KN, 4, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs,
+                                  false, atomic);
     else if (nb <= 16)
-      gemm_block<A_T, B_KN, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
+      gemm_block<A_T, B_KN, 1>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs,
+                               false, atomic);
     else
-      gemm_block<A_T, B_KN>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs);
+      gemm_block<A_T, B_KN>(cp, Ct.ld, ap, At.ld, bp, Bt.ld, mb, nb, K, alpha, false, s.gs, false,
+                            atomic);
   }
 }
 
@@ -716,7 +721,7 @@ __device__ void op_identity(const TileDesc& Vt, uint32_t u0, uint32_t u1) {
 // rounds to nearest.
 template <typename EX, typename EY>
 __device__ void copy_axpy_t(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
-                            bool axpy) {
+                            bool axpy, bool atomic) {
   const EX* x = (const EX*)Xt.ptr;
   EY* y = (EY*)Yt.ptr;
   for (uint32_t u = u0; u < u1; ++u) {
@@ -725,18 +730,19 @@ __device__ void copy_axpy_t(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0,
       const int r = r0 + e / Yt.cols, c = e % Yt.cols;
       const EX v = __ldcg(x + (size_t)r * Xt.ld + c);
       EY* py = y + (size_t)r * Yt.ld + c;
-      *py = axpy ? (EY)(__ldcg(py) + (EY)v) : (EY)v;
+      if (axpy && atomic) atomicAdd(py, (EY)v);  // ATOMIC_WRITE on Y
+      else *py = axpy ? (EY)(__ldcg(py) + (EY)v) : (EY)v;
     }
   }
 }
 
 __device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
-                             bool axpy) {
+                             bool axpy, bool atomic = false) {
   const bool xf = Xt.dtype == SPX_DT_F32, yf = Yt.dtype == SPX_DT_F32;
-  if (!xf && !yf) copy_axpy_t<double, double>(Xt, Yt, u0, u1, axpy);
-  else if (!xf) copy_axpy_t<double, float>(Xt, Yt, u0, u1, axpy);
-  else if (!yf) copy_axpy_t<float, double>(Xt, Yt, u0, u1, axpy);
-  else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy);
+  if (!xf && !yf) copy_axpy_t<double, double>(Xt, Yt, u0, u1, axpy, atomic);
+  else if (!xf) copy_axpy_t<double, float>(Xt, Yt, u0, u1, axpy, atomic);
+  else if (!yf) copy_axpy_t<float, double>(Xt, Yt, u0, u1, axpy, atomic);
+  else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy, atomic);
 }
 
 }  // namespace

@@ -329,6 +329,141 @@ __device__ bool tc_gemm_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, in
   return true;
 }
 
+// FP64 -> two TF32 parts held in FP32 bit patterns: hi = x rounded to the 11
+// significant bits of TF32 (to nearest, ties away from zero, as
+// cvt.rna.tf32.f32), lo = (x rounded to FP32) - hi, rounded the same way;
+// |x - hi - lo| <= 1.25 * 2^-22 |x|.  For x in the FP32 normal range both
+// roundings are done on the integer pipe from the FP64 bit pattern (FP64
+// operations run at 2 per clock per SM on this GPU) and the FP32 difference
+// is exact (hi and x rounded to FP32 lie within a factor of two of each
+// other); zeros, subnormals and values outside that range take the hardware
+// conversions.
+__device__ __forceinline__ void split_tf32(double x, uint32_t& hi, uint32_t& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFu) - 1023 + 127;
+  float f;
+  if (e >= 2 && e <= 252) {
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const uint32_t top = ((uint32_t)(b >> 63) << 31) | ((uint32_t)e << 23);
+    hi = (top | ((uint32_t)(m >> 42) << 13)) + (((uint32_t)(m >> 41) & 1u) << 13);
+    f = __uint_as_float((top | (uint32_t)(m >> 29)) + ((uint32_t)(m >> 28) & 1u));
+  } else {
+    f = __double2float_rn(x);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(f));
+  }
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(f - __uint_as_float(hi)));
+}
+
+// TRSM by the inverse on the tensor cores, one block of m <= 128 rows of A:
+//     A[0:m, 0:n] <- A[0:m, 0:n] V^T,   V = L^{-1} (n x n FP64, lower, zero
+// above the diagonal; n a multiple of 32).  Every FP64 operand entry is split
+// into TF32 hi + lo (split_tf32) and the accumulator collects hi*hi + hi*lo +
+// lo*hi per K step (kind::tf32, M = N = 128, K = 8).  The 128-column output
+// blocks run right to left: output column c needs input columns <= c only
+// (V^T is upper triangular), so block c0 reads columns < c0 + 128, none of
+// which a later block writes, and the update is in place.  Per 32-column K
+// chunk all threads load the chunk (16 rows of A and of V per warp, one
+// element per lane, all loads in flight together) and convert it into the
+// four 128-byte-swizzled operand buffers; thread 0 issues the twelve MMAs and
+// waits for them (bounded) before the buffers are rewritten.
+// The epilogue writes the accumulator widened exactly to FP64 into A and its
+// rounding (BF16 when kBf16, else TF32 in FP32 storage) into the
+// low-precision copy (lowp, ld lowp_ld).  All threads; false on a timeout.
+template <bool kBf16>
+__device__ bool tc_trsm_inv_rows(TcState& s, TcBuf& buf, const double* V, int ldv, double* A,
+                                 int lda, int m, int n, void* lowp, int lowp_ld) {
+  constexpr int kChunk = 32;                          // K per chunk: 128 bytes of TF32
+  constexpr int kRowsPerWarp = kTcM / (kThreads / 32);
+  static_assert(kRowsPerWarp * (kThreads / 32) == kTcM, "rows per warp");
+  uint8_t* const a_hi = buf.a[0];
+  uint8_t* const a_lo = buf.a[1];
+  uint8_t* const v_hi = buf.b[0];
+  uint8_t* const v_lo = buf.b[1];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t tmem = s.tmem_base;
+  constexpr int kLde = kTcN + 1;
+  float* E = reinterpret_cast<float*>(&buf);
+  for (int c0 = (n - 1) / kTcN * kTcN; c0 >= 0; c0 -= kTcN) {
+    const int nc = min(kTcN, n - c0);
+    const int nchunks = (c0 + nc) / kChunk;
+    for (int c = 0; c < nchunks; ++c) {
+      __syncthreads();  // the previous chunk's MMAs are done (thread 0 waited)
+      if (s.error) return false;
+      // rows warp, warp + 8, ... of the A block and of the V block (V rows
+      // are the output columns c0 ..), element k0 + lane of each, stored
+      // K-major with the 128-byte swizzle: the 16-byte group j of row r sits
+      // at group j ^ (r mod 8) of the row (the layout TMA writes)
+      const int k0 = c * kChunk;
+#pragma unroll 4
+      for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int r = warp + 8 * i;
+        const double xa = r < m ? __ldcg(A + (size_t)r * lda + k0 + lane) : 0.0;
+        const double xv = r < nc ? __ldcg(V + (size_t)(c0 + r) * ldv + k0 + lane) : 0.0;
+        const uint32_t off =
+            (uint32_t)r * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)r & 7u)) << 4) +
+            (((uint32_t)lane & 3u) << 2);
+        uint32_t h, l;
+        split_tf32(xa, h, l);
+        *reinterpret_cast<uint32_t*>(a_hi + off) = h;
+        *reinterpret_cast<uint32_t*>(a_lo + off) = l;
+        split_tf32(xv, h, l);
+        *reinterpret_cast<uint32_t*>(v_hi + off) = h;
+        *reinterpret_cast<uint32_t*>(v_lo + off) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+        const uint32_t vh = smem_u32(v_hi), vl = smem_u32(v_lo);
+#pragma unroll
+        for (int k = 0; k < kChunk / 8; ++k) {
+          const uint32_t o = (uint32_t)k * 32u;  // 8 TF32 elements per K step
+          tc_mma<false>(tmem, smem_desc(ah + o), smem_desc(vh + o), (c > 0 || k > 0) ? 1u : 0u);
+          tc_mma<false>(tmem, smem_desc(ah + o), smem_desc(vl + o), 1u);
+          tc_mma<false>(tmem, smem_desc(al + o), smem_desc(vh + o), 1u);
+        }
+        tc_commit(&s.done);
+      }
+      if (tid == 0) {
+        if (!mbar_wait(&s.done, s.done_phase & 1u)) s.error = 1;
+        s.done_phase ^= 1u;
+      }
+    }
+    __syncthreads();
+    if (s.error) return false;
+    tc_fence_after();
+    {  // accumulator -> shared memory, as in tc_gemm_unit
+      const int row = 32 * (warp & 3) + lane;
+      const int col0 = 64 * (warp >> 2);
+      float v[32];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cb = col0 + 32 * h;
+        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) E[row * kLde + cb + j] = v[j];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    for (int e = tid; e < m * nc; e += kThreads) {
+      const int r = e / nc, c = e % nc;
+      const float v = E[r * kLde + c];
+      A[(size_t)r * lda + c0 + c] = widen_f32(v);
+      if (kBf16) {
+        reinterpret_cast<__nv_bfloat16*>(lowp)[(size_t)r * lowp_ld + c0 + c] = __float2bfloat16_rn(v);
+      } else {
+        uint32_t t;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+        reinterpret_cast<uint32_t*>(lowp)[(size_t)r * lowp_ld + c0 + c] = t;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 }  // namespace
 }  // namespace spx
 
@@ -374,6 +509,23 @@ __device__ bool op_tc_gemm(const DevGraph& g, const TileDesc& At, const TileDesc
                              g.maps + Bt.lmap, Bt.lc0, Bt.lr0 + c0, At.cols,
                              c + (size_t)r0 * Ct.ld + c0, Ct.ld, min(kTcM, Ct.rows - r0),
                              min(kTcN, Ct.cols - c0), false))
+      return false;
+  }
+  return true;
+}
+
+// TRSM_INV on the tensor cores: A_ik <- A_ik V^T, units are the 128-row
+// blocks of A_ik (see tc_trsm_inv_rows).  Not inlined: it keeps its
+// registers out of the persistent kernel's main loop.
+template <bool kBf16>
+__device__ __noinline__ bool op_tc_trsm_inv(const TileDesc& Vt, const TileDesc& At, uint32_t u0,
+                                            uint32_t u1, TcCtx& tc) {
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)u * kTcM;
+    char* lowp = (char*)At.lowp + (size_t)r0 * At.lowp_ld * (kBf16 ? 2 : 4);
+    if (!tc_trsm_inv_rows<kBf16>(*tc.st, *tc.buf, (const double*)Vt.ptr, Vt.ld,
+                                 (double*)At.ptr + (size_t)r0 * At.ld, At.ld,
+                                 min(kTcM, At.rows - r0), At.cols, lowp, At.lowp_ld))
       return false;
   }
   return true;

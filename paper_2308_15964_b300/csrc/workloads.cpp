@@ -46,13 +46,15 @@ int register_tiles(spx_graph_t g, double* base, int n_rows, int n_cols, int ld, 
 
 namespace {
 
-// factor: insert the factorization tasks; dev_X: the solve tasks too.
+// factor: insert the factorization tasks; dev_X: the solve tasks too;
+// dev_V (mixed precision only): the panel solves as TRTRI + TRSM_INV.
 int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo, int ldlo,
                     bool factor, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
-                    long long* out_ntasks) {
+                    long long* out_ntasks, double* dev_V = nullptr, int ldv = 0) {
   if (!g || !dev_A || n < 1 || b < 1 || lda < n || (dev_X && (nrhs < 1 || ldx < nrhs)))
     return SPX_ERR_INVALID_ARG;
   if (prec != SPX_F64 && (!dev_Alo || ldlo < n)) return SPX_ERR_INVALID_ARG;
+  if (dev_V && (prec == SPX_F64 || ldv < (b < n ? b : n))) return SPX_ERR_INVALID_ARG;
   const int elem = prec == SPX_BF16 ? 2 : 4;
   int rc = SPX_OK;
   if (prec != SPX_F64)
@@ -80,7 +82,18 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
     unsigned t = 0;
     rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, crit, &t, SPX_F64);
     if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
-    for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+    if (dev_V) {
+      // V_k <- L_kk^{-1} (FP64), then A_ik <- A_ik V_k^T on the tensor cores
+      const int bk = n - k * b < b ? n - k * b : b;
+      unsigned v = 0;
+      if (rc == SPX_OK)
+        rc = spx_tile_register(g, dev_V + (size_t)k * b * ldv, bk, bk, ldv, SPX_DT_F64, nullptr, 0,
+                               &v);
+      if (rc == SPX_OK) rc = ins(SPX_OP_TRTRI, {A.at(k, k), v}, {R, W}, crit, nullptr);
+      for (int i = k + 1; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_TRSM_INV, {v, A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr, prec);
+    }
+    for (int i = k + 1; i < T && rc == SPX_OK && !dev_V; ++i)
       rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr,
                prec);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
@@ -131,6 +144,15 @@ extern "C" int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, in
   if (prec != SPX_TF32 && prec != SPX_BF16) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_A, n, lda, b, dev_Alo, ldlo, true, dev_X, nrhs, ldx, lookahead,
                          prec, out_ntasks);
+}
+
+extern "C" int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                             void* dev_Alo, int ldlo, double* dev_V, int ldv,
+                                             double* dev_X, int nrhs, int ldx, int lookahead,
+                                             int prec, long long* out_ntasks) {
+  if ((prec != SPX_TF32 && prec != SPX_BF16) || !dev_V) return SPX_ERR_INVALID_ARG;
+  return insert_cholesky(g, dev_A, n, lda, b, dev_Alo, ldlo, true, dev_X, nrhs, ldx, lookahead,
+                         prec, out_ntasks, dev_V, ldv);
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,
@@ -383,13 +405,17 @@ extern "C" int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int l
 
 extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,
                                int ld, int b, int commutative, long long* out_ntasks) {
-  if (!g || !dev_A || !dev_B || !dev_C || n < 1 || b < 1 || ld < n) return SPX_ERR_INVALID_ARG;
+  if (!g || !dev_A || !dev_B || !dev_C || n < 1 || b < 1 || ld < n || commutative < 0 ||
+      commutative > 2)
+    return SPX_ERR_INVALID_ARG;
   Tiles A, B, C;
   int rc = register_tiles(g, dev_A, n, n, ld, b, false, A);
   if (rc == SPX_OK) rc = register_tiles(g, dev_B, n, n, ld, b, false, B);
   if (rc == SPX_OK) rc = register_tiles(g, dev_C, n, n, ld, b, false, C);
   const int T = A.T;
-  const int mode = commutative ? SPX_COMMUTATIVE_WRITE : SPX_WRITE;
+  const int mode = commutative == 2   ? SPX_ATOMIC_WRITE
+                   : commutative == 1 ? SPX_COMMUTATIVE_WRITE
+                                      : SPX_WRITE;
   long long count = 0;
   for (int i = 0; i < T && rc == SPX_OK; ++i)
     for (int j = 0; j < T && rc == SPX_OK; ++j)

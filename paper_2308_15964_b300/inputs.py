@@ -123,12 +123,13 @@ def gaussian(n: int, seed: int) -> np.ndarray:
 
 
 def random_access_lists(ntasks: int, nkeys: int, max_handles: int, seed: int,
-                        allow_repeats: bool = True):
+                        allow_repeats: bool = True, nmodes: int = 3):
     """Random STF access lists: per task 1..max_handles accesses on keys 0..nkeys-1.
 
-    Returns (task, key, mode) int arrays in insertion order.  Modes are
-    0 = READ, 1 = WRITE, 2 = COMMUTATIVE_WRITE.  Keys may repeat inside a task
-    when allow_repeats is set (the merge rule is then exercised).
+    Returns (task, key, mode) int arrays in insertion order.  Modes are drawn
+    from the first nmodes of 0 = READ, 1 = WRITE, 2 = COMMUTATIVE_WRITE,
+    3 = ATOMIC_WRITE, 4 = MAYBE_WRITE.  Keys may repeat inside a task when
+    allow_repeats is set (the merge rule is then exercised).
     """
     x = splitmix64(_counters(0, ntasks * (1 + 3 * max_handles), "cpu"), seed).numpy()
     x = x.view(np.uint64)
@@ -140,7 +141,7 @@ def random_access_lists(ntasks: int, nkeys: int, max_handles: int, seed: int,
         used = set()
         for _ in range(nh):
             k = int(x[pos] % np.uint64(nkeys))
-            m = int(x[pos + 1] % np.uint64(3))
+            m = int(x[pos + 1] % np.uint64(nmodes))
             pos += 3
             if not allow_repeats and k in used:
                 continue

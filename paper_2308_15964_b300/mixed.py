@@ -5,12 +5,20 @@ diagonal tiles in FP64, TRSM in FP64 writing a low-precision copy of each
 factor tile, SYRK and GEMM trailing updates on the tensor cores (TF32 or
 BF16 operands, FP32 accumulation) subtracted from the FP64 trailing matrix.
 The first solve uses that factor.  Refinement (classical, on the host loop):
-r = b - A x in FP64 (spx_residual_f64), L L^T d = r with the same factor
-(a second, solve-only graph replayed through a CUDA graph; by default it
-applies the FP64 inverses of the diagonal factor tiles, computed once by a
-TRTRI graph, as products), x += d, until the
-normwise backward error of every right-hand side is <= tol or the iteration
-cap is reached; non-convergence is reported, never hidden.
+r = b - A x in FP64 with the normwise backward error of every right-hand side
+computed on the device (spx_residual_eta_f64), L L^T d = r with the same
+factor (a second, solve-only graph replayed through a CUDA graph; by default
+it applies the FP64 inverses of the diagonal factor tiles, computed once by a
+TRTRI graph, as products), x += d, until the backward error is <= tol or the
+iteration cap is reached; non-convergence is reported, never hidden.
+
+Stopping test: the fast plain FP64 residual drives the iterations; once its
+eta is <= tol, a compensated residual (Dot2) recomputes eta, accurate to a
+relative O(u), and only that value decides convergence.  If it is above tol,
+or if the plain eta stops decreasing (its own rounding noise reached), every
+later iteration uses the compensated residual, whose corrections also bring
+x closer to the exact solution.  The host only compares the device's eta with
+tol.
 """
 from __future__ import annotations
 
@@ -46,17 +54,39 @@ def residual(A, X, B, R, norms, stream=None):
                "spx_residual_f64")
 
 
+def residual_eta(A, X, B, R, anorm, norms, eta, compensated=False, stream=None):
+    """R = B - A X and eta[j] (normwise backward error per right-hand side),
+    eta[nrhs] = max_j eta[j], all on the device; anorm = ||A||_inf (device)."""
+    n, nrhs = X.shape
+    spx._check(spx.lib.spx_residual_eta_f64(_p(A), n, A.stride(0), _p(X), X.stride(0), _p(B),
+                                            B.stride(0), _p(R), R.stride(0), nrhs, _p(anorm),
+                                            _p(norms), _p(eta), 1 if compensated else 0,
+                                            _s(stream)),
+               "spx_residual_eta_f64")
+
+
 def axpy(Y, X, alpha=1.0, stream=None):
     spx._check(spx.lib.spx_axpy_f64(_p(Y), _p(X), Y.numel(), alpha, _s(stream)), "spx_axpy_f64")
 
 
-def factor_graph(g: spx.Graph, A, Alo, b: int, X, prec: int, lookahead=True) -> int:
+def factor_graph(g: spx.Graph, A, Alo, b: int, X, prec: int, lookahead=True, V=None) -> int:
+    """Insert the mixed-precision factorization (and the first solve when X is
+    given).  With V (n x b FP64), the panel solves run as TRTRI into V plus
+    TRSM_INV on the tensor cores (spx_cholesky_insert_mixed_inv); else as
+    FP64 TRSM tasks."""
     n = A.shape[0]
     nt = ctypes.c_longlong()
-    spx._check(spx.lib.spx_cholesky_insert_mixed(
-        g._h, _p(A), n, A.stride(0), b, _p(Alo), Alo.stride(0), _p(X) if X is not None else None,
-        X.shape[1] if X is not None else 0, X.stride(0) if X is not None else 0,
-        1 if lookahead else 0, prec, ctypes.byref(nt)), "spx_cholesky_insert_mixed")
+    xa = (_p(X) if X is not None else None, X.shape[1] if X is not None else 0,
+          X.stride(0) if X is not None else 0)
+    if V is None:
+        spx._check(spx.lib.spx_cholesky_insert_mixed(
+            g._h, _p(A), n, A.stride(0), b, _p(Alo), Alo.stride(0), *xa,
+            1 if lookahead else 0, prec, ctypes.byref(nt)), "spx_cholesky_insert_mixed")
+    else:
+        spx._check(spx.lib.spx_cholesky_insert_mixed_inv(
+            g._h, _p(A), n, A.stride(0), b, _p(Alo), Alo.stride(0), _p(V), V.stride(0), *xa,
+            1 if lookahead else 0, prec, ctypes.byref(nt)), "spx_cholesky_insert_mixed_inv")
+        g._keep.append(V)
     g._keep.extend([A, Alo] + ([X] if X is not None else []))
     return nt.value
 
@@ -120,28 +150,40 @@ def lowp_dtype(prec: int):
 
 
 def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
-                max_iter: int | None = None, inverse: bool = True, correction: str = "auto"):
+                max_iter: int | None = None, inverse: bool = True, correction: str = "auto",
+                panel: str = "tc"):
     """Solve A0 X = B.  Returns (X, L, info) where L holds the factor (lower
     triangle) and info has 'converged', 'iterations', 'eta' (history of the
-    max normwise backward error), 'factor_ms', 'refine_ms', 'status'.  With
+    max normwise backward error, device-computed, plain or compensated
+    residual per 'eta_compensated'), 'eta_final' (the last compensated eta:
+    the certified backward error of the returned X), 'factor_ms',
+    'refine_ms', 'status'.  With
     `inverse`, the correction solves apply the inverses of the diagonal factor
     tiles (computed once, FP64, timed in refine_ms) as products; otherwise
     they substitute.  `correction` = "f32" (with `inverse`, at most 16
     right-hand sides) solves for each correction in FP32 on FP32 copies of the
     factor and of the inverses: the factor is only accurate to TF32 / BF16, so
     FP32 costs the refinement no iterations and runs on the FP32 pipe; "f64"
-    keeps the FP64 solve; "auto" (default) takes "f32" where it applies."""
+    keeps the FP64 solve; "auto" (default) takes "f32" where it applies.
+    `panel` = "tc" (default) runs the factorization's panel solves as TRTRI +
+    TRSM_INV on the tensor cores (split TF32, about FP32 accuracy; the
+    inverses then serve the correction solves too); "fp64" keeps FP64 TRSM
+    tasks."""
     if max_iter is None:
         max_iter = 30 if prec == spx.TF32 else 50
     n, nrhs = B.shape
     if correction == "auto":
         correction = "f32" if inverse and nrhs <= 16 else "f64"
+    if panel not in ("tc", "fp64"):
+        raise ValueError("panel is 'tc' or 'fp64'")
     A = A0.clone()
     Alo = torch.zeros((n, n), dtype=lowp_dtype(prec), device=A0.device)
     X = B.clone()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     g = spx.Graph()
-    factor_graph(g, A, Alo, b, X, prec)
+    V = (torch.empty((n, min(b, n)), dtype=torch.float64, device=A0.device)
+         if panel == "tc" else None)
+    factor_graph(g, A, Alo, b, X, prec, V=V)
     ev[0].record()
     rc, info = g.run()
     ev[1].record()
@@ -153,15 +195,16 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
     R = torch.empty_like(B)
     gs = spx.Graph(cuda_graph=True)
     if inverse:
-        V = torch.empty((n, min(b, n)), dtype=torch.float64, device=A0.device)
         D = torch.empty_like(B)
-        gt = spx.Graph()
-        trtri_graph(gt, A, b, V)
-        rc, _ = gt.run()
-        gt.close()
-        if rc != spx.OK:
-            g.close()
-            return X, A, {"status": rc, "converged": False, "iterations": 0, "eta": []}
+        if V is None:       # the factorization did not leave the inverses
+            V = torch.empty((n, min(b, n)), dtype=torch.float64, device=A0.device)
+            gt = spx.Graph()
+            trtri_graph(gt, A, b, V)
+            rc, _ = gt.run()
+            gt.close()
+            if rc != spx.OK:
+                g.close()
+                return X, A, {"status": rc, "converged": False, "iterations": 0, "eta": []}
         if correction == "f32":
             if nrhs > 16:
                 raise ValueError("the FP32 correction solve takes at most 16 right-hand sides")
@@ -184,19 +227,33 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
         solve_graph(gs, A, b, R)
     anorm = norm_inf(A0)
     norms = torch.empty(3 * nrhs, dtype=torch.float64, device=A0.device)
-    history = []
+    eta_d = torch.empty(nrhs + 1, dtype=torch.float64, device=A0.device)
+    history, comp_flags = [], []
     converged = False
+    compensated = False      # plain residuals until their eta reaches tol
+    eta_final = None
     it = 0
     for it in range(max_iter + 1):
-        residual(A0, X, B, R, norms)
-        nv = norms.cpu()
-        an = float(anorm.item())
-        eta = max(float(nv[j]) / (an * float(nv[nrhs + j]) + float(nv[2 * nrhs + j]))
-                  for j in range(nrhs))
+        residual_eta(A0, X, B, R, anorm, norms, eta_d, compensated)
+        eta = float(eta_d[nrhs].item())
         history.append(eta)
-        if eta <= tol:
-            converged = True
-            break
+        comp_flags.append(compensated)
+        if compensated:
+            eta_final = eta
+            if eta <= tol:
+                converged = True
+                break
+        elif eta <= tol or (len(history) > 1 and eta > 0.9 * history[-2]):
+            # reached tol, or stagnated at the plain residual's rounding
+            # noise: certify (and continue) with the compensated residual
+            compensated = True
+            residual_eta(A0, X, B, R, anorm, norms, eta_d, True)
+            eta_final = float(eta_d[nrhs].item())
+            history.append(eta_final)
+            comp_flags.append(True)
+            if eta_final <= tol:
+                converged = True
+                break
         if it == max_iter:
             break
         rc, _ = gs.run()
@@ -208,8 +265,10 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
     ev[2].record()
     ev[2].synchronize()
     out = {"status": rc, "converged": converged, "iterations": it, "eta": history,
+           "eta_compensated": comp_flags, "eta_final": eta_final,
            "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2]),
-           "factor_op_share": share, "correction": correction if inverse else "f64"}
+           "factor_op_share": share, "correction": correction if inverse else "f64",
+           "panel": panel}
     g.close()
     gs.close()
     return X, A, out

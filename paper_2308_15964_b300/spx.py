@@ -14,11 +14,12 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libspx.so")
 
-READ, WRITE, COMMUTATIVE_WRITE = 0, 1, 2
+READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
- OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI) = range(15)
+ OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI,
+ OP_TRSM_INV) = range(16)
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
-            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI")
+            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV")
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
@@ -55,12 +56,14 @@ def _load():
         "spx_task_set_arg": (I, [P, U, LL]),
         "spx_graph_derive": (I, [P, P]),
         "spx_graph_execute": (I, [P, P]),
+        "spx_batch_execute": (I, [P, I, P]),
         "spx_graph_wait": (I, [P, ULL, P]),
         "spx_graph_sizes": (I, [P, P, P, P, P]),
         "spx_graph_edges": (I, [P, P, P, P]),
         "spx_graph_tickets": (I, [P, P, P]),
         "spx_graph_trace": (I, [P, P]),
         "spx_graph_stats": (I, [P, P, I]),
+        "spx_graph_task_ops": (I, [P, P, P]),
         "spx_graph_write_dot": (I, [P, ctypes.c_char_p]),
         "spx_graph_reset": (I, [P]),
         "spx_graph_clear": (I, [P]),
@@ -73,6 +76,7 @@ def _load():
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
+        "spx_cholesky_insert_mixed_inv": (I, [P, P, I, I, I, P, I, P, I, P, I, I, I, I, P]),
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),
         "spx_trtri_insert": (I, [P, P, I, I, I, P, I, P]),
         "spx_overhead_insert": (I, [P, I, I, I, I, LL, P]),
@@ -80,6 +84,7 @@ def _load():
         "spx_solve_inv_insert": (I, [P, P, I, I, I, P, I, P, P, I, I, P]),
         "spx_solve_inv_f32_insert": (I, [P, P, I, I, I, P, I, P, P, P, P, I, I, P]),
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
+        "spx_residual_eta_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P, P, I, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),
         "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
         "spx_server_config_default": (None, [P]),
@@ -225,6 +230,14 @@ class Graph:
         _check(lib.spx_graph_trace(self._h, _ptr(r)), "spx_graph_trace")
         return r
 
+    def task_ops(self):
+        """(op, priority class) of every task, in insertion order."""
+        n = self.sizes()[0]
+        ops = np.zeros(max(n, 1), np.int32)
+        pr = np.zeros(max(n, 1), np.int32)
+        _check(lib.spx_graph_task_ops(self._h, _ptr(ops), _ptr(pr)), "spx_graph_task_ops")
+        return ops[:n], pr[:n]
+
     def stats(self):
         v = np.zeros(9 + len(OP_NAMES), np.int64)
         _check(lib.spx_graph_stats(self._h, _ptr(v), len(v)), "spx_graph_stats")
@@ -260,6 +273,13 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def batch_execute(graphs, stream=None):
+    """Run built graphs in one persistent launch (spx_batch_execute); then
+    wait on each graph for its own status."""
+    arr = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
+    _check(lib.spx_batch_execute(arr, len(graphs), _stream_ptr(stream)), "spx_batch_execute")
 
 
 class ServerConfig(ctypes.Structure):
@@ -306,6 +326,14 @@ class Server:
 
     def stop(self) -> int:
         return lib.spx_server_stop(self._h)
+
+    def task_ops(self):
+        """(op, priority class) of every task, in insertion order."""
+        n = self.sizes()[0]
+        ops = np.zeros(max(n, 1), np.int32)
+        pr = np.zeros(max(n, 1), np.int32)
+        _check(lib.spx_graph_task_ops(self._h, _ptr(ops), _ptr(pr)), "spx_graph_task_ops")
+        return ops[:n], pr[:n]
 
     def stats(self):
         v = np.zeros(6, np.int64)

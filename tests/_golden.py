@@ -4,7 +4,7 @@ import os
 import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-_MODES = {"R": 0, "W": 1, "C": 2}
+_MODES = {"R": 0, "W": 1, "C": 2, "A": 3, "M": 4}
 
 
 def load_dag_fixture(name="dag_modes_small.txt"):

@@ -99,8 +99,11 @@ def test_determinism_and_executors(S):
     ref[4].close()
 
 
-@pytest.mark.parametrize("commutative", [False, True])
-def test_gemm_dag_vs_oracle(S, commutative):
+@pytest.mark.parametrize("mode", ["write", "commutative", "atomic"])
+def test_gemm_dag_vs_oracle(S, mode):
+    """The tiled GEMM DAG with a WRITE chain, a COMMUTATIVE_WRITE run or an
+    ATOMIC_WRITE run on each C block (atomic: all tasks of a block run at
+    once and add with atomic FP64 additions) against the oracle."""
     from paper_2308_15964_b300 import cholesky
     n, b = 320, 64
     A = inputs.uniform((n, n), 3).numpy()
@@ -110,7 +113,11 @@ def test_gemm_dag_vs_oracle(S, commutative):
     O.tiled_gemm(A, B, Co, b)
     dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C))
     g = S.Graph()
-    cholesky.gemm_graph(g, dA, dB, dC, b, commutative)
+    cholesky.gemm_graph(g, dA, dB, dC, b, commutative=mode == "commutative",
+                        atomic=mode == "atomic")
+    if mode == "atomic":
+        g.derive()
+        assert g.sizes()[1] == 0        # no edges: every block is one atomic run
     rc, _ = g.run()
     assert rc == 0
     got = dC.cpu().numpy()

@@ -42,6 +42,28 @@ def check_tickets(g, rp, col, acc=None):
     return s, e
 
 
+def test_golden_fixture_atomic_maybe(S):
+    n, t, k, m, edges, indeg = load_dag_fixture("dag_modes_atomic_maybe.txt")
+    g = nop_graph(S, n, t, k, m)
+    rp, col, deg = check_same(g, n, t, k, m)
+    got = [(u, int(col[p])) for u in range(n) for p in range(rp[u], rp[u + 1])]
+    assert got == edges and list(deg) == indeg
+    check_tickets(g, rp, col)
+    g.close()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_access_lists_five_modes(S, seed):
+    ntask = [3, 40, 300, 2000][seed % 4]
+    nkeys = [1, 3, 16][seed % 3]
+    t, k, m = inputs.random_access_lists(ntask, nkeys, 5, seed=8800 + seed, nmodes=5)
+    n = int(t.max()) + 1
+    g = nop_graph(S, n, t, k, m)
+    rp, col, _ = check_same(g, n, t, k, m)
+    check_tickets(g, rp, col)
+    g.close()
+
+
 def test_golden_fixture(S):
     n, t, k, m, edges, indeg = load_dag_fixture()
     g = nop_graph(S, n, t, k, m)

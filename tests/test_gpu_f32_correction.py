@@ -109,7 +109,9 @@ def test_refinement_with_f32_correction(S, prec, n, b, nrhs):
     X, info = runs["f32"]
     assert info["converged"] == runs["f64"][1]["converged"]
     if info["converged"]:
-        assert O.solve_backward_error(A.numpy(), X, B.numpy()).max() <= 2e-14
+        eta = O.solve_backward_error(A.numpy(), X, B.numpy()).max()
+        assert eta <= 1e-14, eta
+        assert abs(info["eta_final"] - eta) <= 1e-6 * eta
         assert info["iterations"] <= runs["f64"][1]["iterations"] + 1
 
 

@@ -136,3 +136,28 @@ def test_config_validation(S):
         S.Graph(executor=7)
     with pytest.raises(S.SpxError):
         S.Graph(num_ctas=-1)
+
+
+def test_batch_validation(S):
+    """spx_batch_execute refuses bad batches on the host, before any device
+    work: no graphs, a graph given twice, an empty graph, and one tile
+    address registered with two shapes in two members."""
+    import ctypes
+    assert S.lib.spx_batch_execute(None, 1, None) == S.ERR_INVALID_ARG
+    g1, g2, g3 = S.Graph(), S.Graph(), S.Graph()
+    h1 = g1.register(FAKE, 8, 8, 8)
+    g1.insert(S.OP_NOP, [h1], [S.WRITE])
+    h2 = g2.register(FAKE, 8, 4, 8)                 # same address, other shape
+    g2.insert(S.OP_NOP, [h2], [S.WRITE])
+    arr = (ctypes.c_void_p * 2)(g1._h.value, g1._h.value)
+    assert S.lib.spx_batch_execute(arr, 0, None) == S.ERR_INVALID_ARG
+    assert S.lib.spx_batch_execute(arr, 2, None) == S.ERR_INVALID_ARG   # g1 twice
+    with pytest.raises(S.SpxError) as e:
+        S.batch_execute([g1, g3], 0)                # g3 has no task
+    assert e.value.code == S.ERR_STATE
+    with pytest.raises(S.SpxError) as e:
+        S.batch_execute([g1, g2], 0)                # tile shape conflict
+    assert e.value.code == S.ERR_INVALID_ARG
+    assert g1.wait()[0] == S.ERR_STATE              # nothing started
+    for g in (g1, g2, g3):
+        g.close()

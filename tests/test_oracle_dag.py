@@ -25,8 +25,9 @@ def csr_edges(row_ptr, col):
     return out
 
 
-def test_golden_modes_graph():
-    n, t, k, m, edges, indeg = load_dag_fixture()
+@pytest.mark.parametrize("name", ["dag_modes_small.txt", "dag_modes_atomic_maybe.txt"])
+def test_golden_modes_graph(name):
+    n, t, k, m, edges, indeg = load_dag_fixture(name)
     row_ptr, col, deg = O.derive(n, t, k, m)
     assert csr_edges(row_ptr, col) == edges
     assert list(deg) == indeg
@@ -97,8 +98,9 @@ def merged(n, t, k, m):
 
 def conflict_closure(n, acc):
     """Brute-force STF order: u < v must be ordered when they share a key,
-    unless both only read it, or both are commutative writes of the same run
-    (no other kind of access to that key between them)."""
+    unless both only read it, or both are commutative writes of the same run,
+    or both are atomic writes of the same run (no access of another mode to
+    that key between them).  A maybe-write (4) conflicts like a write."""
     need = np.zeros((n, n), bool)
     for u in range(n):
         for v in range(u + 1, n):
@@ -106,7 +108,8 @@ def conflict_closure(n, acc):
                 a, b = acc[u][key], acc[v][key]
                 if a == 0 and b == 0:
                     continue
-                if a == 2 and b == 2 and all(acc[w].get(key, 2) == 2 for w in range(u + 1, v)):
+                if a == b and a in (2, 3) and all(acc[w].get(key, a) == a
+                                                  for w in range(u + 1, v)):
                     continue
                 need[u, v] = True
     return closure(need)
@@ -133,12 +136,33 @@ def test_bruteforce_small_random(seed):
     acc = merged(ntask, t, k, m)
     assert (closure(adj) == conflict_closure(ntask, acc)).all()
     assert (adj.sum(0) == deg).all()
-    # no edge inside a READ group or a commutative run: such a pair never
-    # conflicts on any key it shares, so an edge needs another shared key.
+    # no edge inside a READ group: such a pair never conflicts on any key it
+    # shares, so an edge needs another shared key.
     for u, v in csr_edges(row_ptr, col):
         shared = set(acc[u]) & set(acc[v])
         assert shared
         assert any(not (acc[u][x] == 0 and acc[v][x] == 0) for x in shared)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_bruteforce_small_random_five_modes(seed):
+    """The same brute force with atomic and maybe writes in the lists."""
+    n = 2 + seed % 9
+    t, k, m = inputs.random_access_lists(n, 1 + seed % 4, 4, seed=3000 + seed, nmodes=5)
+    ntask = int(t.max()) + 1
+    row_ptr, col, deg = O.derive(ntask, t, k, m)
+    adj = np.zeros((ntask, ntask), bool)
+    for u, v in csr_edges(row_ptr, col):
+        assert u < v
+        adj[u, v] = True
+    acc = merged(ntask, t, k, m)
+    assert (closure(adj) == conflict_closure(ntask, acc)).all()
+    assert (adj.sum(0) == deg).all()
+    # no edge inside an atomic run: an edge needs a shared key on which the
+    # pair is not two atomic writes
+    for u, v in csr_edges(row_ptr, col):
+        shared = set(acc[u]) & set(acc[v])
+        assert any(not (acc[u][x] == 3 and acc[v][x] == 3) for x in shared)
 
 
 def linear_extensions_ok(n, acc, adj):
@@ -154,16 +178,16 @@ def linear_extensions_ok(n, acc, adj):
         for tsk in order:
             for key, md in acc[tsk].items():
                 segs = state.setdefault(key, [])
-                if md == 2:
-                    if segs and isinstance(segs[-1], frozenset):
+                if md in (2, 3):   # a commutative or atomic run: a set
+                    if segs and isinstance(segs[-1], tuple) and segs[-1][0] == md:
                         seen[(tsk, key)] = tuple(segs[:-1])
-                        segs[-1] = segs[-1] | {tsk}
+                        segs[-1] = (md, segs[-1][1] | {tsk})
                     else:
                         seen[(tsk, key)] = tuple(segs)
-                        segs.append(frozenset([tsk]))
+                        segs.append((md, frozenset([tsk])))
                 else:
                     seen[(tsk, key)] = tuple(segs)
-                    if md == 1:
+                    if md in (1, 4):   # a write, or a maybe-write
                         segs.append(("W", tsk))
         # the final state of every key must agree as well
         return seen, {k: tuple(v) for k, v in state.items()}
@@ -178,16 +202,30 @@ def linear_extensions_ok(n, acc, adj):
     return True
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(20))
 def test_exhaustive_schedules(seed):
     n = 3 + seed % 5                         # 3..7 tasks
-    t, k, m = inputs.random_access_lists(n, 2, 3, seed=7000 + seed)
+    t, k, m = inputs.random_access_lists(n, 2, 3, seed=7000 + seed,
+                                         nmodes=3 if seed < 12 else 5)
     ntask = int(t.max()) + 1
     row_ptr, col, _ = O.derive(ntask, t, k, m)
     adj = np.zeros((ntask, ntask), bool)
     for u, v in csr_edges(row_ptr, col):
         adj[u, v] = True
     assert linear_extensions_ok(ntask, merged(ntask, t, k, m), adj)
+
+
+def test_gemm_dag_atomic_counts():
+    # ATOMIC_WRITE on C_ij: each block's tasks form one group, no edges
+    tasks = O.gemm_tasks(4, mode=O.ATOMIC_WRITE)
+    t, k, m, _ = O.access_arrays(tasks)
+    _, col, _ = O.derive(len(tasks), t, k, m)
+    assert len(col) == 0
+    # MAYBE_WRITE orders like WRITE: the chains of the WRITE DAG
+    tasks = O.gemm_tasks(4, mode=O.MAYBE_WRITE)
+    t, k, m, _ = O.access_arrays(tasks)
+    _, col, _ = O.derive(len(tasks), t, k, m)
+    assert len(col) == 4 * 4 * 3
 
 
 def test_merge_rule():
@@ -206,3 +244,5 @@ def test_malformed():
         O.derive(2, np.array([1, 0], np.uint32), np.array([0, 0], np.uint64), np.array([0, 0], np.int32))
     with pytest.raises(ValueError):
         O.derive(1, np.array([0], np.uint32), np.array([0], np.uint64), np.array([5], np.int32))
+    with pytest.raises(ValueError):
+        O.derive(1, np.array([0], np.uint32), np.array([0], np.uint64), np.array([-1], np.int32))

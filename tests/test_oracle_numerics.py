@@ -281,3 +281,36 @@ def test_trmm_plain_product():
         tasks = [(O.TRMM, [(("V", 0), O.READ), (("R", 0), O.READ), (("D", 0), O.WRITE)], arg)]
         assert O.execute(tasks, {"V": V, "R": R, "D": D}, n) == 0
         assert np.abs(D - ref).max() <= 1e-14 * n
+
+
+@pytest.mark.parametrize("n,b", [(64, 16), (80, 32), (48, 48)])
+def test_cholesky_inv_integer_exact(n, b):
+    """The Cholesky whose panel solves apply the inverse of the diagonal tile
+    (TRTRI, then A_ik <- A_ik V_k^T): for A = L0 L0^T with L0 unit lower and
+    entries in {-1, 0, 1}, every intermediate (the inverses included, whose
+    entries stay far below 2^53 at these tile sizes) is an integer, so the
+    factor is L0 exactly and V holds the exact inverses of its diagonal
+    tiles.  A transposed or misplaced V fails this."""
+    L0 = unit_lower(n, n + b)
+    A = L0 @ L0.T
+    V = np.zeros((n, b), np.float64)
+    assert O.tiled_cholesky_inv(A, b, V) == 0
+    assert np.array_equal(np.tril(A), L0)
+    for k in range(0, n, b):
+        bk = min(b, n - k)
+        blk = L0[k:k + bk, k:k + bk]
+        assert np.array_equal(V[k:k + bk, :bk] @ blk, np.eye(bk))
+
+
+@pytest.mark.parametrize("n,b", [(96, 32), (100, 32), (128, 64)])
+def test_cholesky_inv_matches_substitution(n, b):
+    """On a random SPD matrix the inverse-based panel solve gives the factor
+    of the substitution form (itself pinned above) to FP64 rounding, and
+    TRSM_INV(TRTRI(L_kk), A_ik) equals TRSM(L_kk, A_ik) tile by tile."""
+    A = inputs.spd_matrix(n, 0.1, seed=n).numpy()
+    L1, L2 = A.copy(), A.copy()
+    V = np.zeros((n, b), np.float64)
+    assert O.tiled_cholesky(L1, b) == 0
+    assert O.tiled_cholesky_inv(L2, b, V) == 0
+    err = np.abs(np.tril(L1) - np.tril(L2)).max() / np.abs(np.tril(L1)).max()
+    assert err <= 1e-13, err
