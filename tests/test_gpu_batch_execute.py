@@ -84,7 +84,7 @@ def run_alone(S, members):
     return out
 
 
-def run_batch(S, members):
+def run_batch(S, members, stats=None):
     for m in members:
         restore(m)
     S.batch_execute([m["g"] for m in members])
@@ -93,6 +93,8 @@ def run_batch(S, members):
         rc, info = m["g"].wait()
         out.append((rc, info, result(m)))
     torch.cuda.synchronize()
+    if stats is not None:               # counters of the whole launch, via a member
+        stats.update(members[0]["g"].stats())
     for m in members:
         m["g"].reset()
     return out
@@ -151,11 +153,11 @@ def test_failing_member_is_isolated(S):
 def test_mixed_and_fp64_members_share_a_launch(S):
     members = [mixed_member(S, 512, 128, 51), chol_member(S, 384, 64, 2, 52)]
     alone = run_alone(S, members)
-    batched = run_batch(S, members)
+    st = {}
+    batched = run_batch(S, members, stats=st)
     for (rc_a, _, r_a), (rc_b, _, r_b) in zip(alone, batched):
         assert rc_a == rc_b == 0
         assert np.array_equal(r_a, r_b)
-    st = members[0]["g"].stats()          # the whole launch
-    assert st["parts"] > 0
+    assert st["parts"] > 0 and "SYRK" in st["op_cycles"] and "TRSM" in st["op_cycles"]
     for m in members:
         m["g"].close()
