@@ -395,11 +395,13 @@ int spx_cholesky_insert_mixed(spx_graph_t g, double* dev_A, int n, int lda, int 
                               long long* out_ntasks);
 
 /* spx_cholesky_insert_mixed with the panel solves on the tensor cores: per
- * k, POTRF(k) in FP64, TRTRI(k) writes V_k = L_kk^{-1} (FP64) into the square
- * block at row k*b of dev_V (n x b FP64 row-major, ldv >= b), and
- * TRSM_INV(i, k) forms A_ik V_k^T on the tensor cores from split TF32
- * operands (about FP32 accuracy, see the prec enum) and writes the
- * low-precision copy of the result.  The TRSM tasks' b^3 flops per tile leave
+ * k, POTRF(k) in FP64, the critical panel tile TRSM(k+1, k) by FP64
+ * substitution (it is on the critical path, and must not wait for the
+ * inversion), TRTRI(k) writes V_k = L_kk^{-1} (FP64) into the square block at
+ * row k*b of dev_V (n x b FP64 row-major, ldv >= b), and TRSM_INV(i, k) for
+ * i >= k+2 forms A_ik V_k^T on the tensor cores from split TF32 operands
+ * (about FP32 accuracy, see the prec enum) and writes the low-precision copy
+ * of the result.  The TRSM tasks' b^3 flops per tile leave
  * the FP64 pipe, which they held for most of the mixed factorization's time
  * (the factor is only accurate to the low precision anyway).  On return dev_V
  * holds the inverses of all diagonal factor tiles, ready for the correction

@@ -135,14 +135,16 @@ def cholesky_tasks(T: int, b: int, with_solve: bool = False):
 
 def cholesky_inv_tasks(T: int, b: int):
     """The tiled Cholesky with the panel solves by the inverse of the diagonal
-    tile: for k, POTRF(k), TRTRI(L_kk -> V_k), TRSM_INV(V_k, A_ik) for i > k
-    (A_ik <- A_ik V_k^T, the same L_ik as TRSM up to rounding), then SYRK and
-    GEMM as in cholesky_tasks."""
+    tile: for k, POTRF(k), TRSM(k+1, k) by substitution, TRTRI(L_kk -> V_k),
+    TRSM_INV(V_k, A_ik) for i > k + 1 (A_ik <- A_ik V_k^T, the same L_ik as
+    TRSM up to rounding), then SYRK and GEMM as in cholesky_tasks."""
     tasks = []
     for k in range(T):
         tasks.append((POTRF, [(("A", k, k), WRITE)], k * b))
+        if k + 1 < T:
+            tasks.append((TRSM, [(("A", k, k), READ), (("A", k + 1, k), WRITE)], 0))
         tasks.append((TRTRI, [(("A", k, k), READ), (("V", k), WRITE)], 0))
-        for i in range(k + 1, T):
+        for i in range(k + 2, T):
             tasks.append((TRSM_INV, [(("V", k), READ), (("A", i, k), WRITE)], 0))
         for i in range(k + 1, T):
             tasks.append((SYRK, [(("A", i, k), READ), (("A", i, i), WRITE)], 0))

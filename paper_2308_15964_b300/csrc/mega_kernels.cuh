@@ -311,8 +311,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       }
       return -1;
     case SPX_OP_TRTRI:
-      if (phase == 0) op_identity(T[t.h[1]], u0, u1);
-      else op_trsm_fwd(T[t.h[0]], T[t.h[1]], phase - 1, u0, u1, s);
+      op_trtri_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_NOP:
       return 0;

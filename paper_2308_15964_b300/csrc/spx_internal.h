@@ -219,9 +219,15 @@ struct DevGraph {
 //     column c needs input columns <= c only, V being lower triangular, so
 //     the block is updated in place).
 //   SYRK: one phase, lower 64-block pairs.  GEMMs: one phase, 64x64 output
-//     blocks.  TRMM: one phase, the units of GEMM_FWD.  TRTRI (V <- L^{-1}):
-//     phase 0 writes the identity into V (64-row units), phases 1.. are the
-//     TRSM_L_FWD phases of L V = I.
+//     blocks.  TRMM: one phase, the units of GEMM_FWD.  TRTRI (V <- L^{-1},
+//     by blocks): phase 0 inverts the 64 x 64 diagonal blocks of L, one unit
+//     each, and zeroes V to their right; then, for block sizes s = 64, 128,
+//     ... (level l, s = 64 * 2^(l-1)), the diagonal s-blocks pair up (top T,
+//     bottom B) into the inverse of their 2s-block: phase 2l - 1 forms
+//     W^T = (L_BT V_TT)^T into the zero upper block V_TB (16 x 64 units),
+//     phase 2l forms V_BT = -V_BB W (16 x 64 units); the last phase zeroes the
+//     upper part again (64-row units).  1 + 2 levels (+ 1) phases, all of
+//     them parallel, instead of the 2 nb of a substitution.
 //   Block solves (L n x n, X n x r): TRSM_L_FWD, for j = 0..nb-1, phase 2j
 //     solves row block j of X with L_jj (one unit per column block of X),
 //     phase 2j+1 subtracts L_ij X_j from the rows below it; TRSM_LT_BWD does
@@ -249,6 +255,39 @@ __host__ __device__ inline uint32_t rhs_row_units(int rows, int cols) {
   return ((uint32_t)rows + rb - 1) / rb;
 }
 
+// TRTRI by blocks (see above): levels = ceil(log2(64-blocks)).
+__host__ __device__ inline uint32_t trtri_levels(int n) {
+  uint32_t lv = 0;
+  while ((uint32_t)kBlk << lv < (uint32_t)n) ++lv;
+  return lv;
+}
+__host__ __device__ inline uint32_t trtri_phases(int n) {
+  const uint32_t lv = trtri_levels(n);
+  return 1u + 2u * lv + (lv ? 1u : 0u);
+}
+// Units of TRTRI level phase (1 .. 2 levels) for an n x n L, and the pair
+// (p, s, sB: top block [p, p+s), bottom block [p+s, p+s+sB)) and local unit of
+// unit u when pair_of != nullptr.
+__host__ __device__ inline uint32_t trtri_level_units(int n, uint32_t phase, uint32_t u = 0,
+                                                      int* pair_of = nullptr) {
+  const uint32_t lvl = (phase + 1) / 2;  // 1-based
+  const bool pa = phase % 2 == 1;        // W^T = (L_BT V_TT)^T, else V_BT = -V_BB W
+  const int s = kBlk << (lvl - 1);
+  uint32_t total = 0;
+  for (int p = 0; p + s < n; p += 2 * s) {
+    const int sb = n - p - s < s ? n - p - s : s;
+    const uint32_t cnt = pa ? (uint32_t)(s / 16) * cdiv64(sb) : cdiv16(sb) * (uint32_t)(s / kBlk);
+    if (pair_of && u >= total && u < total + cnt) {
+      pair_of[0] = p;
+      pair_of[1] = s;
+      pair_of[2] = sb;
+      pair_of[3] = (int)(u - total);
+    }
+    total += cnt;
+  }
+  return total;
+}
+
 // Low-precision tasks (prec = SPX_TF32 / SPX_BF16): SYRK and GEMM_NT_SUB run
 // on the tensor cores in 128 x 128 output units (SYRK: lower block pairs);
 // TRSM runs its FP64 phases and then one more phase that writes the
@@ -260,7 +299,7 @@ __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* 
     case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
-    case SPX_OP_TRTRI: return 2 * cdiv64(t[h[0]].rows);  // identity, then L^{-1} I
+    case SPX_OP_TRTRI: return trtri_phases(t[h[0]].rows);
     default: return 1;
   }
 }
@@ -313,9 +352,11 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_INV:  // 128-row blocks of A_ik (tensor cores)
       return cdiv128(t[h[1]].rows);
-    case SPX_OP_TRTRI:  // phase 0 writes the identity (64-row units), then the forward solve
-      return phase == 0 ? cdiv64(t[h[1]].rows)
-                        : solve_phase_units(true, t[h[0]].rows, t[h[1]].cols, phase - 1);
+    case SPX_OP_TRTRI: {  // diagonal inverses, level products, zeroing (64-block units)
+      const int n = t[h[0]].rows;
+      if (phase == 0 || phase + 1 == trtri_phases(n)) return cdiv64(n);
+      return trtri_level_units(n, phase);
+    }
     default: return 1;
   }
 }

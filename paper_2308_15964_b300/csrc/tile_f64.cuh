@@ -704,6 +704,76 @@ __device__ void op_trmm(const TileDesc& Tt, const TileDesc& Xt, const TileDesc& 
   }
 }
 
+// TRTRI by blocks, phase `phase`, units u0..u1: V (n x n) <- L^{-1} for the
+// lower triangle of L (see trtri_phases).  Phase 0, unit j: the inverse of
+// the diagonal block L_jj, as the transpose of X = I L_jj^{-T} (the in-tile
+// row solve), and zeros to its right.  Level phases: for each pair of
+// diagonal s-blocks T = [p, p+s), B = [p+s, p+s+sB):
+//   a) W^T = V_TT^T L_BT^T (s x sB) into V[p:p+s, p+s:p+s+sB], which is above
+//      the diagonal (zero in the result, so free scratch); V_TT lower, so
+//      output row j of W^T sums over k >= j only;
+//   b) V_BT = -V_BB W, V_BB lower, so output row i sums over k <= i only.
+// The k ranges start and end on 16-row bands inside the diagonal 64-blocks,
+// so no product reads the scratch of an earlier level.  Last phase: the part
+// of V above the diagonal 64-blocks back to zero.
+__device__ void op_trtri_units(const TileDesc& Lt, const TileDesc& Vt, uint32_t phase, uint32_t u0,
+                               uint32_t u1, F64Smem& s) {
+  const double* l = (const double*)Lt.ptr;
+  double* v = (double*)Vt.ptr;
+  const int n = Lt.rows, ldl = Lt.ld, ldv = Vt.ld;
+  if (phase == 0) {
+    for (uint32_t u = u0; u < u1; ++u) {
+      const int jb = (int)u * kBlk, w = min(kBlk, n - jb);
+      load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+      for (int e = threadIdx.x; e < kBlk * kBlk; e += kThreads)
+        s.x[e / kBlk][e % kBlk] = (e / kBlk == e % kBlk) ? 1.0 : 0.0;
+      __syncthreads();
+      prep_lower(s.l, w, s.rinv, false);
+      trsm_rt_smem(s.x, s.l, s.rinv, w, w);  // X = L_jj^{-T}
+      for (int e = threadIdx.x; e < w * (n - jb); e += kThreads) {
+        const int r = e / (n - jb), c = e % (n - jb);
+        v[(size_t)(jb + r) * ldv + jb + c] = c < w ? s.x[c][r] : 0.0;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  if (phase + 1 == trtri_phases(n)) {  // zero above the diagonal 64-blocks
+    for (uint32_t u = u0; u < u1; ++u) {
+      const int jb = (int)u * kBlk, w = min(kBlk, n - jb), c0 = jb + w;
+      for (int e = threadIdx.x; e < w * (n - c0); e += kThreads)
+        v[(size_t)(jb + e / (n - c0)) * ldv + c0 + e % (n - c0)] = 0.0;
+    }
+    return;
+  }
+  for (uint32_t u = u0; u < u1; ++u) {
+    int pr[4];
+    trtri_level_units(n, phase, u, pr);
+    const int p = pr[0], sz = pr[1], sb = pr[2], lu = pr[3];
+    double* wt = v + (size_t)p * ldv + p + sz;  // W^T scratch, s x sB
+    if (phase % 2 == 1) {
+      // unit: 16 rows [j0, j0+16) of W^T x 64 columns [c0, c0+64)
+      const uint32_t ncb = cdiv64(sb);
+      const int j0 = 16 * (int)(lu / ncb), c0 = kBlk * (int)(lu % ncb);
+      const double* vtt = v + (size_t)p * ldv + p;              // V_TT, A^T operand
+      const double* lbt = l + (size_t)(p + sz) * ldl + p;       // L_BT, B stored n x k
+      gemm_block<true, false, 4, 1>(wt + (size_t)j0 * ldv + c0, ldv, vtt + (size_t)j0 * ldv + j0,
+                                    ldv, lbt + (size_t)c0 * ldl + j0, ldl, min(16, sz - j0),
+                                    min(kBlk, sb - c0), sz - j0, 1.0, false, s.gs, true);
+    } else {
+      // unit: 16 rows [i0, i0+16) of V_BT x 64 columns [c0, c0+64)
+      const uint32_t ncb = (uint32_t)(sz / kBlk);
+      const int i0 = 16 * (int)(lu / ncb), c0 = kBlk * (int)(lu % ncb);
+      const double* vbb = v + (size_t)(p + sz) * ldv + p + sz;  // V_BB
+      double* vbt = v + (size_t)(p + sz) * ldv + p;
+      // W[k][c] = W^T[c][k]: B stored n x k
+      gemm_block<false, false, 4, 1>(vbt + (size_t)i0 * ldv + c0, ldv, vbb + (size_t)i0 * ldv, ldv,
+                                     wt + (size_t)c0 * ldv, ldv, min(16, sb - i0), kBlk,
+                                     min(i0 + 16, sb), -1.0, false, s.gs, true);
+    }
+  }
+}
+
 // V <- I on 64-row units (phase 0 of TRTRI).
 __device__ void op_identity(const TileDesc& Vt, uint32_t u0, uint32_t u1) {
   double* v = (double*)Vt.ptr;

@@ -83,15 +83,20 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
     rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, crit, &t, SPX_F64);
     if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
     if (dev_V) {
-      // V_k <- L_kk^{-1} (FP64), then A_ik <- A_ik V_k^T on the tensor cores
+      // The panel below the critical one: V_k <- L_kk^{-1} (FP64), then
+      // A_ik <- A_ik V_k^T on the tensor cores.  The critical panel tile
+      // (k+1, k) is solved by FP64 substitution straight after POTRF, so the
+      // inversion stays off the critical path.
       const int bk = n - k * b < b ? n - k * b : b;
       unsigned v = 0;
+      if (rc == SPX_OK && k + 1 < T)
+        rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, crit, nullptr, prec);
       if (rc == SPX_OK)
         rc = spx_tile_register(g, dev_V + (size_t)k * b * ldv, bk, bk, ldv, SPX_DT_F64, nullptr, 0,
                                &v);
-      if (rc == SPX_OK) rc = ins(SPX_OP_TRTRI, {A.at(k, k), v}, {R, W}, crit, nullptr);
-      for (int i = k + 1; i < T && rc == SPX_OK; ++i)
-        rc = ins(SPX_OP_TRSM_INV, {v, A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr, prec);
+      if (rc == SPX_OK) rc = ins(SPX_OP_TRTRI, {A.at(k, k), v}, {R, W}, hi, nullptr);
+      for (int i = k + 2; i < T && rc == SPX_OK; ++i)
+        rc = ins(SPX_OP_TRSM_INV, {v, A.at(i, k)}, {R, W}, hi, nullptr, prec);
     }
     for (int i = k + 1; i < T && rc == SPX_OK && !dev_V; ++i)
       rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr,
