@@ -89,7 +89,7 @@ def parse():
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
     p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
-                                                      "overhead"],
+                                                      "overhead", "axpy", "nbody"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -233,6 +233,12 @@ def main():
         return
     if args.workload == "gemm":
         run_gemm(args, world, rank, local)
+        return
+    if args.workload == "axpy":
+        run_axpy(args, world, rank, local)
+        return
+    if args.workload == "nbody":
+        run_nbody(args, world, rank, local)
         return
 
     n, b = args.n, args.tile
@@ -518,6 +524,186 @@ def run_gemm(args, world, rank, local):
            "config": {"workload": res["workload"], "n": n, "tile": args.tile,
                       "l2": "inputs larger than L2 (3 x 8 n^2 bytes)"},
            "roofline": w["roofline"], "cpu_baseline": res["cpu_baseline"], "gemm_dag": res,
+           "clocks": clocks, "gpu_launches": 2 * args.steps}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def timed_graph_runs(spx, torch, build, restore, nsteps, nwarm, executor=0):
+    """Run `build(g)` (insert) + execute + wait nwarm + nsteps times on a
+    fresh graph each step (the full hot path); returns [(step_ms, kernel_ms)]."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    g = spx.Graph(executor=executor)
+    rec = []
+    for i in range(nwarm + nsteps):
+        restore()
+        ev[0].record()
+        g.clear()
+        build(g)
+        g.execute()
+        rc, _ = g.wait()
+        ev[1].record()
+        ev[1].synchronize()
+        assert rc == spx.OK, rc
+        if i >= nwarm:
+            rec.append((ev[0].elapsed_time(ev[1]), g.timing()[1]))
+    ntasks = g.sizes()[0]
+    g.close()
+    return rec, ntasks
+
+
+def run_axpy(args, world, rank, local):
+    """The paper's AXPY test case (FP32, a vector split into independent
+    pieces): n = 2^28 values (x, y 1 GiB each), pieces of 2^14 .. 2^22 values;
+    step = insert + derive + execute + wait.  HBM-bound: 12 bytes per value
+    (read x, read and write y)."""
+    import ctypes
+    import torch
+    from paper_2308_15964_b300 import inputs, spx
+    n = args.n if args.n != 16384 else 1 << 28
+    x = inputs.uniform((n,), 21, device="cuda").to(torch.float32)
+    y0 = inputs.uniform((n,), 22, device="cuda").to(torch.float32)
+    y = y0.clone()
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    nbytes = 12.0 * n
+    alpha = 1.5
+
+    def build_for(piece):
+        def build(g):
+            spx._check(spx.lib.spx_axpy_insert(g._h, ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), n, piece, alpha,
+                                               None), "spx_axpy_insert")
+        return build
+
+    rows = []
+    with Clocks(local) as clk:
+        for lg in (14, 16, 18, 20, 22):
+            piece = 1 << lg
+            row = {"piece": piece, "tasks": -(-n // piece)}
+            for name, ex in (("persistent", spx.EXEC_PERSISTENT), ("per_task", spx.EXEC_PER_TASK),
+                             ("streams", spx.EXEC_STREAMS)):
+                steps = args.steps if name == "persistent" else COMPARATOR_STEPS
+                rec, nt = timed_graph_runs(spx, torch, build_for(piece), lambda: None, steps,
+                                           args.warmup if name == "persistent" else 1, ex)
+                ms = statistics.mean(r[0] for r in rec)
+                kern = statistics.mean(r[1] for r in rec)
+                row[name] = {"ms_per_step": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
+                             "tasks_per_s": nt / (ms * 1e-3), "kernel_ms": kern,
+                             "kernel_GBps": nbytes / (kern * 1e-3) / 1e9,
+                             "p99_ms": float(np.percentile([r[0] for r in rec], 99))}
+            rows.append(row)
+    clocks = clk.summary()
+    head = [r for r in rows if r["piece"] == 1 << 20][0]
+    # CPU oracle: the same loop on one host core over a bounded sample
+    from oracle import oracle as O
+    m = 1 << 24
+    xs, ys = x[:m].cpu().numpy(), y0[:m].cpu().numpy().copy()
+    t0 = time.perf_counter()
+    O.axpy_f32(xs, ys, alpha)
+    dt = time.perf_counter() - t0
+    out = {"metric": METRIC, "value": head["persistent"]["GBps"], "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": head["persistent"]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"AXPY FP32 y += {alpha} x, n = {n}, pieces of 2^20 "
+                                  "(other piece sizes in rows); step = insert + derive + "
+                                  "execute + wait", "n": n,
+                      "l2": "inputs larger than L2 (8 n bytes)"},
+           "tasks_per_s": head["persistent"]["tasks_per_s"], "rows": rows,
+           "roofline": {"bound": "hbm", "achieved": head["persistent"]["kernel_GBps"],
+                        "peak": hbm, "unit": "GB/s",
+                        "frac": head["persistent"]["kernel_GBps"] / hbm, "traffic": None,
+                        "kernel": "persistent_kernel (AXPY tile op)",
+                        "note": "12 bytes per value: x read, y read and written; peak = the "
+                                "measured copy bandwidth"},
+           "cpu_baseline": {"value": 12.0 * m / dt / 1e9, "unit": "GB/s", "cores": 1,
+                            "kind": "oracle", "sample": f"the oracle's FP32 loop on {m} values"},
+           "clocks": clocks, "gpu_launches": 2 * args.steps}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+NBODY_FLOPS = 20   # per interaction: 3 sub, r^2 (5), sqrt, division, 3 mul, add, 3 FMA (6)
+
+
+def run_nbody(args, world, rank, local):
+    """The paper's particle test case (FP64 direct Coulomb sum, dependencies on
+    whole groups): G = 64 groups of 128 .. 2048 particles (seeded), positions
+    and charges uniform in [-1, 1]; tasks SELF(i) and PAIR(i, j) with WRITE on
+    the groups (and a COMMUTATIVE_WRITE row).  Interactions = N (N - 1) per
+    step; ALU-bound, against the measured rate of the same arithmetic."""
+    import ctypes
+    import torch
+    from paper_2308_15964_b300 import inputs, spx
+    G = 64
+    u = inputs.uniform((G,), 61).numpy()
+    sizes = (128 + np.floor((u + 1) / 2 * (2048 - 128 + 1))).astype(np.int64)
+    sizes = np.minimum(sizes, 2048)
+    N = int(sizes.sum())
+    P0 = torch.zeros((N, 8), dtype=torch.float64, device="cuda")
+    P0[:, 0:3] = inputs.uniform((N, 3), 62, device="cuda")
+    P0[:, 3] = inputs.uniform((N,), 63, device="cuda")
+    P = P0.clone()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    ptrs = (ctypes.c_void_p * G)(*[P.data_ptr() + 64 * int(o) for o in offs[:-1]])
+    sz = (ctypes.c_int * G)(*[int(v) for v in sizes])
+    inter = float(N) * (N - 1)
+
+    def build_for(comm):
+        def build(g):
+            spx._check(spx.lib.spx_nbody_insert(g._h, G, ptrs, sz, comm, None), "spx_nbody_insert")
+        return build
+
+    def restore():
+        P.copy_(P0)
+
+    probe_rate, _ = spx.probe(14, 2000)
+    res = {}
+    with Clocks(local) as clk:
+        for name, ex, comm in (("write", spx.EXEC_PERSISTENT, 0),
+                               ("commutative", spx.EXEC_PERSISTENT, 1),
+                               ("per_task", spx.EXEC_PER_TASK, 0),
+                               ("streams", spx.EXEC_STREAMS, 0)):
+            steps = args.steps if name == "write" else COMPARATOR_STEPS
+            rec, nt = timed_graph_runs(spx, torch, build_for(comm), restore, steps,
+                                       args.warmup if name == "write" else 1, ex)
+            ms = statistics.mean(r[0] for r in rec)
+            kern = statistics.mean(r[1] for r in rec)
+            res[name] = {"ms_per_step": ms, "interactions_per_s": inter / (ms * 1e-3),
+                         "gflops": NBODY_FLOPS * inter / (ms * 1e-3) / 1e9, "tasks": nt,
+                         "tasks_per_s": nt / (ms * 1e-3), "kernel_ms": kern,
+                         "p99_ms": float(np.percentile([r[0] for r in rec], 99))}
+    clocks = clk.summary()
+    w = res["write"]
+    # CPU oracle on a bounded sample: the first 4 groups
+    from oracle import oracle as O
+    k = 4
+    Ph = P0[:int(offs[k])].cpu().numpy().copy()
+    t0 = time.perf_counter()
+    assert O.nbody(Ph, [int(v) for v in sizes[:k]]) == 0
+    dt = time.perf_counter() - t0
+    ns = int(offs[k])
+    out = {"metric": METRIC, "value": w["gflops"], "unit": "GFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"particle interactions FP64: {G} groups, N = {N} particles "
+                                  f"(sizes 128..2048), {len(sizes) * (len(sizes) + 1) // 2} tasks, "
+                                  f"{NBODY_FLOPS} flops per interaction; step = insert + derive "
+                                  "+ execute + wait", "groups": G, "N": N},
+           "interactions_per_s": w["interactions_per_s"], "tasks_per_s": w["tasks_per_s"],
+           "p50_ms": w["ms_per_step"], "p99_ms": w["p99_ms"], "executors": res,
+           "roofline": {"bound": "alu", "achieved": inter / (w["kernel_ms"] * 1e-3),
+                        "peak": probe_rate, "unit": "interactions/s",
+                        "frac": inter / (w["kernel_ms"] * 1e-3) / probe_rate, "traffic": None,
+                        "kernel": "persistent_kernel (NBODY tile ops)",
+                        "note": "peak = spx_probe(SPX_PROBE_NBODY): the same FP64 interaction "
+                                "arithmetic on register data over all SMs"},
+           "cpu_baseline": {"value": NBODY_FLOPS * ns * (ns - 1) / dt / 1e9, "unit": "GFLOP/s",
+                            "cores": 1, "kind": "oracle",
+                            "sample": f"the oracle's task list on the first {k} groups "
+                                      f"({ns} particles)"},
            "clocks": clocks, "gpu_launches": 2 * args.steps}
     if rank == 0:
         print(json.dumps(out))

@@ -85,7 +85,12 @@ enum {
  *   SPX_OP_NOP          any handles, any modes  does nothing (graph tests)
  *   SPX_OP_SPIN         any handles, any modes  busy-waits arg nanoseconds
  *   SPX_OP_COPY         (X:R, Y:W)              Y <- X (same shape)
- *   SPX_OP_AXPY         (X:R, Y:W)              Y <- Y + X (same shape)
+ *   SPX_OP_AXPY         (X:R, Y:W)              Y <- Y + alpha X (same shape;
+ *                                               alpha from spx_task_set_scalar,
+ *                                               default 1; computed as
+ *                                               fl(fl(alpha x) + y) in Y's
+ *                                               type, one rounding when
+ *                                               alpha = 1)
  *   SPX_OP_TRMM         (T:R, X:R, Y:W)         Y <- T X (arg 0) or T^T X
  *                                               (arg 1); T square, lower
  *                                               triangular: its entries above
@@ -96,6 +101,20 @@ enum {
  *                                               triangle of L_kk; V_k square,
  *                                               written whole, zero above its
  *                                               diagonal)
+ *   SPX_OP_NBODY_SELF   (P:W)                   interactions of the particles
+ *                                               of group P with each other
+ *   SPX_OP_NBODY_PAIR   (P:W, Q:W)              interactions between groups P
+ *                                               and Q (both updated)
+ *                       A particle group is an n x 8 FP64 tile, one particle
+ *                       per row: x, y, z, charge q, then the accumulated
+ *                       potential phi and field E (3 components).  Each
+ *                       interaction of target i with source j (j != i) adds
+ *                       q_j / r to phi_i and q_j (x_i - x_j) / r^3 to E_i,
+ *                       r = |x_i - x_j| (the paper's particle test case: a
+ *                       direct Coulomb summation, about 17 flops and one
+ *                       square root per interaction, section "Numerical
+ *                       applications"); coincident particles (r = 0) do not
+ *                       interact.
  *   SPX_OP_TRSM_INV     (V_kk:R, A_ik:W)        A_ik <- A_ik V_kk^T with V_kk
  *                                               = L_kk^{-1} from TRTRI (lower,
  *                                               zero above the diagonal): the
@@ -133,7 +152,9 @@ enum {
   SPX_OP_TRMM = 13,
   SPX_OP_TRTRI = 14,
   SPX_OP_TRSM_INV = 15,
-  SPX_NUM_OPS = 16
+  SPX_OP_NBODY_SELF = 16,
+  SPX_OP_NBODY_PAIR = 17,
+  SPX_NUM_OPS = 18
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
@@ -253,6 +274,11 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
  * tile (info reports offset + local column, 1-based); for SPIN the spin time
  * in nanoseconds.  Errors: SPX_ERR_BAD_HANDLE, SPX_ERR_STATE. */
 int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg);
+
+/* Set the scalar of an AXPY task (Y <- Y + alpha X; alpha 1 by default).
+ * Errors: SPX_ERR_BAD_HANDLE, SPX_ERR_STATE, SPX_ERR_INVALID_ARG (not an
+ * AXPY task, or alpha not finite or zero). */
+int spx_task_set_scalar(spx_graph_t g, unsigned task, double alpha);
 
 /* Derive the dependency DAG on the device (successor CSR sorted ascending,
  * de-duplicated, and in-degrees) without executing it.  Asynchronous on
@@ -508,6 +534,30 @@ int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int lda, double*
 int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n, int ld,
                     int b, int commutative, long long* out_ntasks);
 
+/* Insert the AXPY of the paper's numerical applications (section "Numerical
+ * applications": a vector split into pieces, one independent task per piece,
+ * single precision): y <- y + alpha x over n FP32 values (dev_x, dev_y
+ * distinct device arrays), in pieces of `piece` values (the last one
+ * ragged), one AXPY task per piece with x_p READ and y_p WRITE.  A piece is
+ * registered as a (len / 1024) x 1024 tile when 1024 divides its length,
+ * else as one row.  Each value is computed as fl(fl(alpha x) + y) (one
+ * rounding when alpha = 1).
+ * Errors: SPX_ERR_INVALID_ARG; as spx_tile_register / spx_task_insert. */
+int spx_axpy_insert(spx_graph_t g, float* dev_x, float* dev_y, long long n, long long piece,
+                    double alpha, long long* out_ntasks);
+
+/* Insert the particle-interaction test case of the paper's numerical
+ * applications (direct Coulomb summation in FP64; dependencies on whole
+ * groups): ngroups groups, group i an sizes[i] x 8 FP64 tile at
+ * dev_groups[i] (ld 8; x, y, z, q, phi, E, see SPX_OP_NBODY_SELF), tasks in
+ * the order NBODY_SELF(i), then NBODY_PAIR(i, j) for j > i, for i = 0, 1,
+ * ...; each task writes its groups (SPX_WRITE, or SPX_COMMUTATIVE_WRITE when
+ * commutative: a group's accumulations may then run in any order).  phi and
+ * E accumulate into the tiles (zero them first for the plain sums).
+ * Errors: SPX_ERR_INVALID_ARG; as spx_tile_register / spx_task_insert. */
+int spx_nbody_insert(spx_graph_t g, int ngroups, double* const* dev_groups, const int* sizes,
+                     int commutative, long long* out_ntasks);
+
 /* Largest inputs of spx_graph_derive_noalloc (its fixed scratch is sized
  * for these: about 5.3 MB of device memory per GPU). */
 #define SPX_NOALLOC_MAX_RECORDS 262144
@@ -610,6 +660,47 @@ int spx_residual_eta_f64(const double* dev_A, int n, int lda, const double* dev_
                          const double* dev_B, int ldb, double* dev_R, int ldr, int nrhs,
                          const double* dev_anorm, double* dev_norms, double* dev_eta,
                          int compensated, void* stream);
+
+/* GMRES-based iterative refinement (Carson and Higham 2017, 2018; the
+ * paper's refinement is the workload definition's, its GMRES form this
+ * library's): solve A X = B (A n x n FP64, lda; B, X n x nrhs FP64 row-major,
+ * ld = nrhs, 1 <= nrhs <= 16; X holds the first solution on entry) by
+ * refinement steps whose correction equation A d = r is solved by GMRES on
+ * M^{-1} A d = M^{-1} r, M = L L^T the low-precision factor.  precond is a
+ * solve graph the caller built over dev_R (n x nrhs FP64, ld = nrhs): one
+ * execution must leave M^{-1} R in dev_R (e.g. spx_solve_inv_insert or
+ * spx_solve_insert on the factor); the driver resets and runs it as needed.
+ * Each step: the residual and its normwise backward error on the device
+ * (spx_residual_eta_f64 logic: plain residuals until eta <= tol or eta stops
+ * falling, then compensated ones, so the final eta is certified), then up to
+ * max_inner GMRES iterations (FP64; CGS2 orthogonalisation; Givens
+ * rotations; all right-hand sides in lockstep) until the largest relative
+ * GMRES residual is <= inner_tol, then x += d.  dev_work: device workspace of
+ * spx_gmres_ir_workspace(n, nrhs, max_inner) bytes (the call allocates
+ * nothing).  Synchronous on stream (it reads device scalars to decide).
+ * Returns SPX_OK with out filled (converged or not: non-convergence is
+ * reported, never hidden), or an error of the precond graph, or
+ * SPX_ERR_INVALID_ARG / SPX_ERR_CUDA. */
+typedef struct {
+  int max_outer;     /* refinement steps (0 = 20)                         */
+  int max_inner;     /* GMRES iterations per step, <= 64 (0 = 30)         */
+  double inner_tol;  /* relative GMRES residual (0 = 1e-10)               */
+  double tol;        /* target normwise backward error (0 = 1e-14)        */
+} spx_gmres_config_t;
+
+typedef struct {
+  int converged;     /* 1 when the certified eta <= tol                   */
+  int outer;         /* refinement steps taken                            */
+  int inner;         /* GMRES iterations over all steps                   */
+  int pad_;
+  double eta;        /* last (compensated when converged) max eta         */
+} spx_gmres_result_t;
+
+long long spx_gmres_ir_workspace(int n, int nrhs, int max_inner);
+
+int spx_gmres_ir(const double* dev_A, int n, int lda, const double* dev_B, double* dev_X, int nrhs,
+                 spx_graph_t precond, double* dev_R, void* dev_work, long long work_bytes,
+                 const spx_gmres_config_t* cfg, spx_gmres_result_t* out, void* stream);
 
 /* ||A||_inf (max row sum of |a_ij|) of an n x n FP64 matrix into dev_out[0]. */
 int spx_norm_inf_f64(const double* dev_A, int n, int lda, double* dev_out, void* stream);

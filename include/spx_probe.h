@@ -33,7 +33,11 @@ enum {
                                  /* 8 warps x 8 independent chains          */
   SPX_PROBE_WARP_DDIV = 11,      /* cycles per warp FP64 division, same     */
   SPX_PROBE_LAT_DRCP = 12,       /* dependent __drcp_rn + multiply chain    */
-  SPX_PROBE_LAT_DRSQRT = 13      /* dependent rsqrt chain                   */
+  SPX_PROBE_LAT_DRSQRT = 13,     /* dependent rsqrt chain                   */
+  SPX_PROBE_NBODY = 14           /* the n-body interaction arithmetic (3 sub,
+                                    r^2, sqrt, division, 3 mul, add, 3 FMA)
+                                    on register data, all SMs: interactions/s,
+                                    the ALU ceiling of SPX_OP_NBODY_*        */
 };
 
 /* Run probe `which` with `iters` inner iterations (or launches).  Writes the

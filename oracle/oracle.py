@@ -27,7 +27,8 @@ SRC = os.path.join(HERE, "spx_oracle.cpp")
 
 READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (POTRF, TRSM, SYRK, GEMM_NT_SUB, GEMM_NN_ADD, TRSM_L_FWD, GEMM_FWD,
- TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI, TRSM_INV) = range(16)
+ TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI, TRSM_INV, NBODY_SELF,
+ NBODY_PAIR) = range(18)
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +65,7 @@ def lib():
         L.spxo_factor_backward_error.restype = ctypes.c_double
         L.spxo_factor_backward_error.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int]
         L.spxo_solve_backward_error.argtypes = [P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P]
+        L.spxo_axpy_f32.argtypes = [ctypes.c_longlong, ctypes.c_float, P, P]
         L.spxo_freivalds.restype = ctypes.c_double
         L.spxo_freivalds.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P]
         _lib = L
@@ -210,6 +212,35 @@ def gemm_tasks(T: int, commutative: bool = False, mode: int | None = None):
     return tasks
 
 
+def nbody_tasks(G: int, commutative: bool = False):
+    """The particle test case: for each group i, the interactions inside it,
+    then with every later group j (both groups written; section "Numerical
+    applications": dependencies on whole groups)."""
+    mode = COMMUTATIVE_WRITE if commutative else WRITE
+    tasks = []
+    for i in range(G):
+        tasks.append((NBODY_SELF, [(("P", i), mode)], 0))
+        for j in range(i + 1, G):
+            tasks.append((NBODY_PAIR, [(("P", i), mode), (("P", j), mode)], 0))
+    return tasks
+
+
+def nbody(P: np.ndarray, sizes, commutative: bool = False) -> int:
+    """Run nbody_tasks on the particles P (N x 8 FP64, groups of the given
+    sizes stacked in order) in insertion order, accumulating phi and E."""
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    assert P.shape == (offs[-1], 8) and P.dtype == np.float64 and P.flags["C_CONTIGUOUS"]
+    return execute(nbody_tasks(len(sizes), commutative), {"P": P}, 0, groups=offs)
+
+
+def axpy_f32(x: np.ndarray, y: np.ndarray, alpha: float) -> None:
+    """y <- y + alpha x in FP32 (the AXPY test case), in place."""
+    assert x.dtype == np.float32 and y.dtype == np.float32 and x.shape == y.shape
+    x = np.ascontiguousarray(x)
+    assert y.flags["C_CONTIGUOUS"]
+    lib().spxo_axpy_f32(ctypes.c_longlong(x.size), ctypes.c_float(alpha), _p(x), _p(y))
+
+
 def access_arrays(tasks):
     """Flatten a task list to (task, key, mode) arrays; keys number tile names
     in order of first use."""
@@ -235,7 +266,7 @@ class _Tile(ctypes.Structure):
                 ("ld", ctypes.c_int), ("pad", ctypes.c_int)]
 
 
-def _tile_views(names, mats, b):
+def _tile_views(names, mats, b, groups=None):
     """Tile table for named tiles ("A", i, j) / ("B", ...) / ("C", ...) of square
     row-major matrices, ("X", i) / ("R", i) / ("D", i) row blocks of n x nrhs
     matrices and ("V", i) square diagonal-block tiles stacked in an n x b
@@ -250,6 +281,9 @@ def _tile_views(names, mats, b):
         elif name[0] == "V":
             r0, c0 = name[1] * b, 0
             rows = cols = min(b, n_rows - r0)
+        elif name[0] == "P":      # particle group: rows groups[i] .. groups[i+1]
+            r0, c0 = int(groups[name[1]]), 0
+            rows, cols = int(groups[name[1] + 1] - groups[name[1]]), n_cols
         else:
             r0, c0 = name[1] * b, name[2] * b
             rows, cols = min(b, n_rows - r0), min(b, n_cols - c0)
@@ -258,13 +292,13 @@ def _tile_views(names, mats, b):
     return tiles
 
 
-def execute(tasks, mats, b):
+def execute(tasks, mats, b, groups=None):
     """Run a task list on numpy FP64 matrices in place, in insertion order.
     Returns the LAPACK-style info (0 = success)."""
     for m in mats.values():
         assert m.dtype == np.float64 and m.flags["C_CONTIGUOUS"]
     _, _, _, names = access_arrays(tasks)
-    tiles = _tile_views(names, mats, b)
+    tiles = _tile_views(names, mats, b, groups)
     nt = len(tasks)
     ops = np.asarray([t[0] for t in tasks], np.int32)
     th = np.full((max(nt, 1), 4), -1, np.int32)

@@ -74,7 +74,9 @@ enum {
   O_AXPY = 12,        // Y <- Y + X
   O_TRMM = 13,        // Y <- T X (arg 0) or T^T X (arg 1), T lower triangular
   O_TRTRI = 14,       // V <- L^{-1}, L lower triangular
-  O_TRSM_INV = 15     // A_ik <- A_ik V^T, V = L_kk^{-1} (the TRSM by the inverse)
+  O_TRSM_INV = 15,    // A_ik <- A_ik V^T, V = L_kk^{-1} (the TRSM by the inverse)
+  O_NBODY_SELF = 16,  // Coulomb interactions inside one particle group
+  O_NBODY_PAIR = 17   // interactions between two groups, both updated
 };
 
 // ---------------------------------------------------------------------------
@@ -324,6 +326,30 @@ static void trsm_inv(const double* v, int ldv, double* a, int lda, int m, int n)
   }
 }
 
+// Direct Coulomb summation (the paper's particle test case): for each target
+// particle i of t (rows x, y, z, q, phi, Ex, Ey, Ez) and each source j of src
+// (j != i when both are the same group), with d = x_i - x_j and r = |d| > 0:
+//   phi_i += q_j / r,   E_i += q_j d / r^3.
+static void nbody_interact(double* t, int ldt, int nt, const double* src, int lds, int ns,
+                           bool self) {
+  for (int i = 0; i < nt; ++i) {
+    double* ti = t + (size_t)i * ldt;
+    for (int j = 0; j < ns; ++j) {
+      if (self && j == i) continue;
+      const double* sj = src + (size_t)j * lds;
+      const double dx = ti[0] - sj[0], dy = ti[1] - sj[1], dz = ti[2] - sj[2];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 > 0.0)) continue;
+      const double r = std::sqrt(r2);
+      const double r3 = r * r * r;
+      ti[4] = ti[4] + sj[3] / r;
+      ti[5] = ti[5] + sj[3] * dx / r3;
+      ti[6] = ti[6] + sj[3] * dy / r3;
+      ti[7] = ti[7] + sj[3] * dz / r3;
+    }
+  }
+}
+
 // A tile: base pointer, shape and leading dimension (row-major).
 typedef struct {
   double* ptr;
@@ -438,6 +464,18 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
         trsm_inv(V.ptr, V.ld, A.ptr, A.ld, A.rows, A.cols);
         break;
       }
+      case O_NBODY_SELF: {
+        const spxo_tile& P = tile(0);
+        nbody_interact(P.ptr, P.ld, P.rows, P.ptr, P.ld, P.rows, true);
+        break;
+      }
+      case O_NBODY_PAIR: {
+        const spxo_tile& P = tile(0);
+        const spxo_tile& Q = tile(1);
+        nbody_interact(P.ptr, P.ld, P.rows, Q.ptr, Q.ld, Q.rows, false);
+        nbody_interact(Q.ptr, Q.ld, Q.rows, P.ptr, P.ld, P.rows, false);
+        break;
+      }
       case O_NOP:
       case O_SPIN:
         break;
@@ -446,6 +484,14 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
     }
   }
   return 0;
+}
+
+// The AXPY test case in single precision: y <- y + alpha x over n values,
+// piece after piece (the tasks are independent: any order gives the same
+// values).  Each value is fl(fl(alpha x) + y), the product skipped when
+// alpha = 1; alpha is rounded to FP32 first.
+void spxo_axpy_f32(long long n, float alpha, const float* x, float* y) {
+  for (long long i = 0; i < n; ++i) y[i] = alpha == 1.0f ? y[i] + x[i] : alpha * x[i] + y[i];
 }
 
 // Untiled GEMM C <- C + A B (n x n, row-major, ld = n).

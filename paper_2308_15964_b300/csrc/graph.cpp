@@ -168,7 +168,7 @@ int cuda_fail(cudaError_t e) {
 
 // Operand count, shape and mode checks of the built-in ops.
 // Operand count of each built-in op (-1: any, 1..16).
-const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2};
+const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2, 1, 2};
 
 int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
                    const unsigned* h, const int* m, int nh) {
@@ -189,9 +189,11 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
   }
   const int w = nh - 1;  // written operand is the last one
   const bool atomic_ok = op == SPX_OP_GEMM_NN_ADD || op == SPX_OP_AXPY;
-  if (m[w] != SPX_WRITE && m[w] != SPX_COMMUTATIVE_WRITE && m[w] != SPX_MAYBE_WRITE &&
-      !(m[w] == SPX_ATOMIC_WRITE && atomic_ok))
-    return SPX_ERR_INVALID_ARG;
+  auto writes = [](int md) {
+    return md == SPX_WRITE || md == SPX_COMMUTATIVE_WRITE || md == SPX_MAYBE_WRITE;
+  };
+  if (!writes(m[w]) && !(m[w] == SPX_ATOMIC_WRITE && atomic_ok)) return SPX_ERR_INVALID_ARG;
+  if (op == SPX_OP_NBODY_PAIR && !writes(m[0])) return SPX_ERR_INVALID_ARG;  // both groups written
   auto R = [&](int i) { return t[h[i]].rows; };
   auto C = [&](int i) { return t[h[i]].cols; };
   bool ok = true;
@@ -210,6 +212,8 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     case SPX_OP_TRMM: ok = R(0) == C(0) && C(0) == R(1) && R(2) == R(0) && C(2) == C(1); break;
     case SPX_OP_TRTRI: ok = R(0) == C(0) && R(1) == R(0) && C(1) == C(0); break;
     case SPX_OP_TRSM_INV: ok = R(0) == C(0) && C(1) == R(0) && C(1) % 32 == 0; break;
+    case SPX_OP_NBODY_SELF: ok = C(0) == 8; break;
+    case SPX_OP_NBODY_PAIR: ok = C(0) == 8 && C(1) == 8; break;
     default: ok = false;
   }
   if (all_f32 && C(nh - 1) > 16) ok = false;
@@ -606,6 +610,20 @@ int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg) {
   return SPX_OK;
 }
 
+int spx_task_set_scalar(spx_graph_t g, unsigned task, double alpha) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (task >= g->tasks.size()) return SPX_ERR_BAD_HANDLE;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->tasks[task].op != SPX_OP_AXPY || !(alpha == alpha) || alpha == 0.0 ||
+      alpha - alpha != 0.0)
+    return SPX_ERR_INVALID_ARG;
+  long long bits;
+  std::memcpy(&bits, &alpha, sizeof bits);  // the device reads the FP64 bits
+  g->tasks[task].arg = bits;
+  g->uploaded = false;
+  return SPX_OK;
+}
+
 int spx_graph_derive(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning) return SPX_ERR_STATE;
@@ -946,7 +964,7 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
   static const char* names[SPX_NUM_OPS] = {"POTRF", "TRSM", "SYRK", "GEMM", "GEMM_NN",
                                            "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
                                            "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI",
-                                           "TRSM_INV"};
+                                           "TRSM_INV", "NBODY_SELF", "NBODY_PAIR"};
   std::fprintf(f, "digraph spx {\n");
   for (size_t u = 0; u < N; ++u)
     std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);

@@ -294,13 +294,20 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_COPY:
     case SPX_OP_AXPY:
-      op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY, t.flags & kFlagAtomic);
+      op_copy_axpy(T[t.h[0]], T[t.h[1]], u0, u1, t.op == SPX_OP_AXPY, t.flags & kFlagAtomic,
+                   (t.op == SPX_OP_AXPY && t.arg) ? __longlong_as_double(t.arg) : 1.0);
       return 0;
     case SPX_OP_TRMM:
       if (T[t.h[0]].dtype == SPX_DT_F32)
         op_trmm<float>(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
       else
         op_trmm<double>(T[t.h[0]], T[t.h[1]], T[t.h[2]], t.arg != 0, u0, u1, s);
+      return 0;
+    case SPX_OP_NBODY_SELF:
+      op_nbody(T[t.h[0]], nullptr, u0, u1, s);
+      return 0;
+    case SPX_OP_NBODY_PAIR:
+      op_nbody(T[t.h[0]], &T[t.h[1]], u0, u1, s);
       return 0;
     case SPX_OP_TRSM_INV:
       if constexpr (kTc) {
@@ -656,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     __syncthreads();
     const long long dt = clock64() - c0;
     busy += dt;
-    if (tid == 0) atomicAdd(&rs->op_cycles[t.op & 15], (unsigned long long)dt);
+    if (tid == 0) atomicAdd(&rs->op_cycles[t.op & 31], (unsigned long long)dt);
     if (tid == 0) {
       if (info > 0 && kServer) {
         // the request fails; the server and the other requests go on

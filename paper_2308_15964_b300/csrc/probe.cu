@@ -72,6 +72,37 @@ __global__ void atomic_distinct_kernel(unsigned* ctr, int iters, int n) {
 
 __global__ void empty_kernel() {}
 
+// The interaction arithmetic of the n-body ops on register data: 4
+// independent targets per thread against a moving source.
+__global__ void nbody_probe_kernel(double* out, int iters, double qv) {
+  double xi[4], phi[4], ex[4], ey[4], ez[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    xi[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+    phi[c] = ex[c] = ey[c] = ez[c] = 0.0;
+  }
+  double sx = 0.25, sy = 0.5, sz = -0.125;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double dx = xi[c] - sx, dy = xi[c] - sy, dz = xi[c] - sz;
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      const double rinv = 1.0 / sqrt(r2);
+      const double qr = qv * rinv;
+      const double s3 = qr * rinv * rinv;
+      phi[c] += qr;
+      ex[c] = fma(s3, dx, ex[c]);
+      ey[c] = fma(s3, dy, ey[c]);
+      ez[c] = fma(s3, dz, ez[c]);
+    }
+    sx += 1e-6;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s += phi[c] + ex[c] + ey[c] + ez[c];
+  if (s == 12345.678) out[threadIdx.x] = s;
+}
+
 // Latency probes: one block, thread 0 times a dependent chain with clock64()
 // and writes the SM cycles per step to out[0].
 enum LatOp { kLatDfma, kLatDdiv, kLatDsqrt, kLatSync, kLatWarpDfma, kLatWarpDdiv, kLatDrcp,
@@ -176,6 +207,10 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
         for (int i = 0; i < iters; ++i) empty_kernel<<<1, 32, 0, st>>>();
         work = iters;
         break;
+      case SPX_PROBE_NBODY:
+        nbody_probe_kernel<<<blocks, threads, 0, st>>>((double*)buf, iters, 0.75);
+        work = 4.0 * (double)iters * blocks * threads;
+        break;
       case SPX_PROBE_LAT_DFMA:
       case SPX_PROBE_LAT_DDIV:
       case SPX_PROBE_LAT_DSQRT:
@@ -197,7 +232,7 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   float t = 0.f;
   cudaEventElapsedTime(&t, e0, e1);
   double cyc = 0.0;  // latency probes: cycles per step, written by the kernel
-  if (err == cudaSuccess && which >= SPX_PROBE_LAT_DFMA)
+  if (err == cudaSuccess && which >= SPX_PROBE_LAT_DFMA && which <= SPX_PROBE_LAT_DRSQRT)
     err = cudaMemcpy(&cyc, buf, sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(buf);
   cudaEventDestroy(e0);
@@ -206,7 +241,8 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   if (work < 0) return -1;
   if (err != cudaSuccess) return -7;
   *ms = t;
-  *rate = which >= SPX_PROBE_LAT_DFMA ? cyc : work / (t * 1e-3);
+  const bool lat = which >= SPX_PROBE_LAT_DFMA && which <= SPX_PROBE_LAT_DRSQRT;
+  *rate = lat ? cyc : work / (t * 1e-3);
   return 0;
 }
 

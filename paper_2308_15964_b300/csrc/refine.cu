@@ -272,3 +272,303 @@ extern "C" int spx_copy2d(void* dst, size_t dpitch, const void* src, size_t spit
                                           cudaMemcpyDefault, (cudaStream_t)stream);
   return e == cudaSuccess ? SPX_OK : SPX_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// GMRES-based iterative refinement (Carson and Higham, "A new analysis of
+// iterative refinement and its application to accurate solution of
+// ill-conditioned sparse linear systems", SIAM J. Sci. Comput. 2017; and
+// "Accelerating the solution of linear systems by iterative refinement in
+// three precisions", 2018).  Each refinement step solves the correction
+// equation A d = r with GMRES on the left-preconditioned system
+// M^{-1} A d = M^{-1} r, M = L L^T the low-precision factor (applied by a
+// solve graph the caller built), all in FP64, instead of applying M^{-1}
+// once: the step then contracts the error even when kappa(A) u_factor is not
+// small.  The nrhs right-hand sides run in lockstep (one Krylov space each,
+// vectors stored as n x nrhs row-major blocks); orthogonalisation is
+// classical Gram-Schmidt applied twice (CGS2), the Hessenberg least-squares
+// problem is kept triangular with Givens rotations, one thread per right-hand
+// side.  The host only compares device-computed scalars with tolerances.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kMaxGmres = 64;  // Krylov vectors per refinement step
+
+// out[k * nrhs + c] = sum_i V_k[i][c] W[i][c], one CTA per k, fixed-order
+// block reduction (deterministic).
+__global__ void __launch_bounds__(256) block_dots_kernel(const double* __restrict__ V,
+                                                         long long vstride,
+                                                         const double* __restrict__ W, int n,
+                                                         int nrhs, double* __restrict__ out) {
+  __shared__ double red[256];
+  const double* v = V + (size_t)blockIdx.x * vstride;
+  double acc[kMaxRhs];
+#pragma unroll
+  for (int c = 0; c < kMaxRhs; ++c) acc[c] = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+#pragma unroll
+    for (int c = 0; c < kMaxRhs; ++c)
+      if (c < nrhs) acc[c] = fma(v[(size_t)i * nrhs + c], W[(size_t)i * nrhs + c], acc[c]);
+  }
+  for (int c = 0; c < nrhs; ++c) {
+    red[threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)blockIdx.x * nrhs + c] = red[0];
+    __syncthreads();
+  }
+}
+
+// W[i][c] += scale * sum_k coef[k * nrhs + c] V_k[i][c]
+__global__ void block_combine_kernel(double* __restrict__ W, const double* __restrict__ V,
+                                     int nvec, long long vstride, const double* __restrict__ coef,
+                                     double scale, long long len, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % nrhs);
+    double s = 0.0;
+    for (int k = 0; k < nvec; ++k) s = fma(coef[(size_t)k * nrhs + c], V[(size_t)k * vstride + e], s);
+    W[e] = fma(scale, s, W[e]);
+  }
+}
+
+// Y[i][c] = X[i][c] * s[c]
+__global__ void block_scale_kernel(double* __restrict__ Y, const double* __restrict__ X,
+                                   const double* __restrict__ s, long long len, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x)
+    Y[e] = X[e] * s[e % nrhs];
+}
+
+// GMRES state of nrhs systems, m Krylov vectors at most, FP64, laid out
+// field by field with the right-hand side fastest: H[(m+1) x m], cs[m], sn[m],
+// g[m+1], beta, inv (1 / norm of the newest vector), res (relative residual
+// estimate |g_{j+1}| / beta); resmax at the end.
+struct GmresState {
+  double *H, *cs, *sn, *g, *beta, *inv, *res, *resmax;
+  __host__ __device__ static size_t doubles(int m, int nrhs) {
+    return ((size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + 4) * nrhs + 1;
+  }
+  __host__ __device__ GmresState(double* base, int m, int nrhs) {
+    H = base;
+    cs = H + (size_t)(m + 1) * m * nrhs;
+    sn = cs + (size_t)m * nrhs;
+    g = sn + (size_t)m * nrhs;
+    beta = g + (size_t)(m + 1) * nrhs;
+    inv = beta + nrhs;
+    res = inv + nrhs;
+    resmax = res + nrhs;
+  }
+};
+
+// Start: beta = ||r0||, g = beta e_1, inv = 1 / beta (0 for r0 = 0).  One warp.
+__global__ void gmres_start_kernel(double* base, int m, int nrhs, const double* nrm2) {
+  GmresState st(base, m, nrhs);
+  const int c = threadIdx.x;
+  double r = 0.0;
+  if (c < nrhs) {
+    const double b = sqrt(nrm2[c]);
+    st.beta[c] = b;
+    st.inv[c] = b > 0.0 ? 1.0 / b : 0.0;
+    for (int k = 0; k <= m; ++k) st.g[(size_t)k * nrhs + c] = k == 0 ? b : 0.0;
+    st.res[c] = r = b > 0.0 ? 1.0 : 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if (c == 0) *st.resmax = r;
+}
+
+// Arnoldi step j: column j of H is h[0..j] (the Gram-Schmidt coefficients)
+// and sqrt(hn2) (the norm of the orthogonalised vector); apply the earlier
+// rotations, make the new one, update g and the residual estimate, and
+// inv = 1 / H[j+1][j] for the next basis vector (0 on breakdown: the Krylov
+// space holds the solution).  One warp.
+__global__ void gmres_step_kernel(double* base, int m, int nrhs, int j, const double* h,
+                                  const double* hn2) {
+  GmresState st(base, m, nrhs);
+  const int c = threadIdx.x;
+  double r = 0.0;
+  if (c < nrhs) {
+    auto H = [&](int row) -> double& { return st.H[((size_t)row * m + j) * nrhs + c]; };
+    for (int k = 0; k <= j; ++k) H(k) = h[(size_t)k * nrhs + c];
+    const double hn = sqrt(hn2[c]);
+    H(j + 1) = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = H(i), b = H(i + 1);
+      const double cs = st.cs[(size_t)i * nrhs + c], sn = st.sn[(size_t)i * nrhs + c];
+      H(i) = cs * a + sn * b;
+      H(i + 1) = -sn * a + cs * b;
+    }
+    const double a = H(j), b = H(j + 1);
+    const double rr = hypot(a, b);
+    const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
+    st.cs[(size_t)j * nrhs + c] = cs;
+    st.sn[(size_t)j * nrhs + c] = sn;
+    H(j) = rr;
+    H(j + 1) = 0.0;
+    const double gj = st.g[(size_t)j * nrhs + c];
+    st.g[(size_t)j * nrhs + c] = cs * gj;
+    st.g[(size_t)(j + 1) * nrhs + c] = -sn * gj;
+    st.inv[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+    const double beta = st.beta[c];
+    r = beta > 0.0 ? fabs(st.g[(size_t)(j + 1) * nrhs + c]) / beta : 0.0;
+    st.res[c] = r;
+  }
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if (c == 0) *st.resmax = r;
+}
+
+// y[0..j] = R^{-1} g[0..j], R the rotated (upper triangular) H.  One warp.
+__global__ void gmres_backsolve_kernel(const double* base, int m, int nrhs, int j, double* y) {
+  GmresState st(const_cast<double*>(base), m, nrhs);
+  const int c = threadIdx.x;
+  if (c >= nrhs) return;
+  for (int k = j; k >= 0; --k) {
+    double s = st.g[(size_t)k * nrhs + c];
+    for (int l = k + 1; l <= j; ++l)
+      s -= st.H[((size_t)k * m + l) * nrhs + c] * y[(size_t)l * nrhs + c];
+    const double d = st.H[((size_t)k * m + k) * nrhs + c];
+    y[(size_t)k * nrhs + c] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+int grid_for(long long len) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long b = (len + 255) / 256;
+  return (int)(b < 4LL * sms ? (b > 0 ? b : 1) : 4LL * sms);
+}
+
+// Host copy of one device double (the only data the driver reads back).
+double read_scalar(const double* p, cudaStream_t st, cudaError_t* e) {
+  double v = 0.0;
+  *e = cudaMemcpyAsync(&v, p, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (*e == cudaSuccess) *e = cudaStreamSynchronize(st);
+  return v;
+}
+
+// Apply the preconditioner: the caller's solve graph, in place on R.
+int apply_precond(spx_graph_t g, cudaStream_t st) {
+  int rc = spx_graph_reset(g);
+  if (rc != SPX_OK && rc != SPX_ERR_STATE) return rc;
+  rc = spx_graph_execute(g, st);
+  if (rc != SPX_OK) return rc;
+  int info = 0;
+  return spx_graph_wait(g, 0, &info);
+}
+
+}  // namespace
+
+extern "C" long long spx_gmres_ir_workspace(int n, int nrhs, int max_inner) {
+  if (n < 1 || nrhs < 1 || nrhs > kMaxRhs || max_inner < 1 || max_inner > kMaxGmres) return -1;
+  const long long vec = (long long)n * nrhs;
+  // basis (max_inner + 1 vectors), zero block, coefficients (2 sets + norms),
+  // y, GMRES state, ||A||, norms, eta
+  return 8LL * ((max_inner + 1) * vec + vec + 3LL * (max_inner + 1) * nrhs +
+                (long long)GmresState::doubles(max_inner, nrhs) + 1 + 3 * nrhs + nrhs + 1 + 64);
+}
+
+extern "C" int spx_gmres_ir(const double* dev_A, int n, int lda, const double* dev_B, double* dev_X,
+                            int nrhs, spx_graph_t precond, double* dev_R, void* dev_work,
+                            long long work_bytes, const spx_gmres_config_t* cfg,
+                            spx_gmres_result_t* out, void* stream) {
+  if (!dev_A || !dev_B || !dev_X || !precond || !dev_R || !dev_work || !out || n < 1 || lda < n ||
+      nrhs < 1 || nrhs > kMaxRhs || dev_R == dev_X || dev_R == dev_B)
+    return SPX_ERR_INVALID_ARG;
+  spx_gmres_config_t c{};
+  if (cfg) c = *cfg;
+  const int m = c.max_inner > 0 ? c.max_inner : 30;
+  const int maxo = c.max_outer > 0 ? c.max_outer : 20;
+  const double itol = c.inner_tol > 0.0 ? c.inner_tol : 1e-10;
+  const double tol = c.tol > 0.0 ? c.tol : 1e-14;
+  if (m > kMaxGmres || work_bytes < spx_gmres_ir_workspace(n, nrhs, m)) return SPX_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long vec = (long long)n * nrhs;
+  double* V = (double*)dev_work;                       // (m + 1) basis blocks
+  double* Z = V + (size_t)(m + 1) * vec;               // zero block (B = 0: R = -A v)
+  double* h = Z + vec;                                 // CGS coefficients, pass 1
+  double* h2 = h + (size_t)(m + 1) * nrhs;             // pass 2
+  double* y = h2 + (size_t)(m + 1) * nrhs;             // least-squares solution
+  double* S = y + (size_t)(m + 1) * nrhs;              // GMRES state
+  double* anorm = S + GmresState::doubles(m, nrhs);
+  double* norms = anorm + 1;
+  double* eta = norms + 3 * nrhs;
+  const GmresState gs(S, m, nrhs);
+  const int grid = grid_for(vec);
+  cudaError_t e = cudaMemsetAsync(Z, 0, sizeof(double) * vec, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(anorm, 0, sizeof(double), st);
+  if (e != cudaSuccess) return SPX_ERR_CUDA;
+  norm_inf_kernel<<<(n + 7) / 8, 256, 0, st>>>(dev_A, n, lda, anorm);
+  *out = spx_gmres_result_t{};
+  bool compensated = false;
+  double prev = 0.0;
+  int rc = SPX_OK;
+  for (int it = 0;; ++it) {
+    // residual and its backward error, as in classical refinement: plain
+    // residuals until eta reaches tol (or stops falling), then compensated
+    e = compensated ? residual_dispatch<true>(dev_A, n, lda, dev_X, nrhs, dev_B, nrhs, dev_R, nrhs,
+                                              nrhs, norms, st)
+                    : residual_dispatch<false>(dev_A, n, lda, dev_X, nrhs, dev_B, nrhs, dev_R,
+                                               nrhs, nrhs, norms, st);
+    if (e == cudaSuccess) eta_kernel<<<1, 32, 0, st>>>(norms, anorm, nrhs, eta);
+    double et = read_scalar(eta + nrhs, st, &e);
+    if (e != cudaSuccess) return SPX_ERR_CUDA;
+    if (!compensated && (et <= tol || (it > 0 && et > 0.9 * prev))) {
+      compensated = true;
+      e = residual_dispatch<true>(dev_A, n, lda, dev_X, nrhs, dev_B, nrhs, dev_R, nrhs, nrhs,
+                                  norms, st);
+      if (e == cudaSuccess) eta_kernel<<<1, 32, 0, st>>>(norms, anorm, nrhs, eta);
+      et = read_scalar(eta + nrhs, st, &e);
+      if (e != cudaSuccess) return SPX_ERR_CUDA;
+    }
+    prev = et;
+    out->eta = et;
+    out->outer = it;
+    if (compensated && et <= tol) {
+      out->converged = 1;
+      return SPX_OK;
+    }
+    if (it == maxo) return SPX_OK;
+    // GMRES on M^{-1} A d = M^{-1} r, d = 0 to start; x += d at the end
+    rc = apply_precond(precond, st);                    // R = M^{-1} r
+    if (rc != SPX_OK) return rc;
+    block_dots_kernel<<<1, 256, 0, st>>>(dev_R, vec, dev_R, n, nrhs, h);
+    gmres_start_kernel<<<1, 32, 0, st>>>(S, m, nrhs, h);
+    block_scale_kernel<<<grid, 256, 0, st>>>(V, dev_R, gs.inv, vec, nrhs);
+    int j = 0;
+    for (; j < m; ++j) {
+      double* vj = V + (size_t)j * vec;
+      // R = -A v_j (residual with B = 0), then R = A v_j, then M^{-1} A v_j
+      e = residual_dispatch<false>(dev_A, n, lda, vj, nrhs, Z, nrhs, dev_R, nrhs, nrhs, norms, st);
+      if (e != cudaSuccess) return SPX_ERR_CUDA;
+      axpy_kernel<<<grid, 256, 0, st>>>(dev_R, dev_R, vec, -2.0);
+      rc = apply_precond(precond, st);
+      if (rc != SPX_OK) return rc;
+      // CGS2 against v_0 .. v_j
+      block_dots_kernel<<<j + 1, 256, 0, st>>>(V, vec, dev_R, n, nrhs, h);
+      block_combine_kernel<<<grid, 256, 0, st>>>(dev_R, V, j + 1, vec, h, -1.0, vec, nrhs);
+      block_dots_kernel<<<j + 1, 256, 0, st>>>(V, vec, dev_R, n, nrhs, h2);
+      block_combine_kernel<<<grid, 256, 0, st>>>(dev_R, V, j + 1, vec, h2, -1.0, vec, nrhs);
+      axpy_kernel<<<1, 256, 0, st>>>(h, h2, (long long)(j + 1) * nrhs, 1.0);
+      block_dots_kernel<<<1, 256, 0, st>>>(dev_R, vec, dev_R, n, nrhs, h2);
+      gmres_step_kernel<<<1, 32, 0, st>>>(S, m, nrhs, j, h, h2);
+      if (j + 1 < m)
+        block_scale_kernel<<<grid, 256, 0, st>>>(V + (size_t)(j + 1) * vec, dev_R, gs.inv, vec,
+                                                 nrhs);
+      const double r = read_scalar(gs.resmax, st, &e);
+      if (e != cudaSuccess) return SPX_ERR_CUDA;
+      ++out->inner;
+      if (r <= itol) {
+        ++j;
+        break;
+      }
+    }
+    if (j > m) j = m;
+    // x += V y, y = R^{-1} g over the j vectors built
+    gmres_backsolve_kernel<<<1, 32, 0, st>>>(S, m, nrhs, j - 1, y);
+    block_combine_kernel<<<grid, 256, 0, st>>>(dev_X, V, j, vec, y, 1.0, vec, nrhs);
+    if (cudaGetLastError() != cudaSuccess) return SPX_ERR_CUDA;
+  }
+}

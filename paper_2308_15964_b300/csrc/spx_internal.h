@@ -127,7 +127,7 @@ struct RunState {
   uint32_t ctas;
   unsigned long long busy_cycles;
   unsigned long long total_cycles;
-  unsigned long long op_cycles[16];  // busy cycles by op (SPX_NUM_OPS <= 16)
+  unsigned long long op_cycles[32];  // busy cycles by op (SPX_NUM_OPS <= 32)
 };
 
 // Status of one member graph of a batched run.
@@ -352,6 +352,10 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_INV:  // 128-row blocks of A_ik (tensor cores)
       return cdiv128(t[h[1]].rows);
+    case SPX_OP_NBODY_SELF:  // 64-particle target blocks
+      return cdiv64(t[h[0]].rows);
+    case SPX_OP_NBODY_PAIR:  // target blocks of P (sources Q), then of Q (sources P)
+      return cdiv64(t[h[0]].rows) + cdiv64(t[h[1]].rows);
     case SPX_OP_TRTRI: {  // diagonal inverses, level products, zeroing (64-block units)
       const int n = t[h[0]].rows;
       if (phase == 0 || phase + 1 == trtri_phases(n)) return cdiv64(n);

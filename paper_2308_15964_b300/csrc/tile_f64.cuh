@@ -786,33 +786,168 @@ __device__ void op_identity(const TileDesc& Vt, uint32_t u0, uint32_t u1) {
   }
 }
 
-// Y <- X (axpy = false) or Y <- Y + X (axpy = true) on 64-row blocks u0..u1,
-// for X and Y each FP64 or FP32 (EX, EY); FP32 -> FP64 is exact, FP64 -> FP32
-// rounds to nearest.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// Y <- X (axpy = false) or Y <- Y + alpha X (axpy = true) on 64-row blocks
+// u0..u1, for X and Y each FP64 or FP32 (EX, EY); FP32 -> FP64 is exact,
+// FP64 -> FP32 rounds to nearest.  In Y's type: fl(fl(alpha x) + y), the
+// product skipped when alpha = 1 (no contraction into an FMA: the paper's
+// FP32 AXPY has one rounding per operation).
+// Contiguous tiles of one element type (ld == cols, 16-byte aligned): a unit
+// is one flat range, read and written with 16-byte vector accesses, four per
+// thread in flight (the HBM-bound AXPY test case).
+template <typename E>
+__device__ void copy_axpy_flat(const E* __restrict__ x, E* __restrict__ y, size_t n, bool axpy,
+                               E a, bool one) {
+  constexpr int kV = 16 / sizeof(E);  // elements per vector
+  using V = typename std::conditional<sizeof(E) == 4, float4, double2>::type;
+  const size_t nv = n / kV;
+  const V* xv = reinterpret_cast<const V*>(x);
+  V* yv = reinterpret_cast<V*>(y);
+  size_t i = threadIdx.x;
+  for (; i + 3 * kThreads < nv; i += 4 * kThreads) {
+    V xs[4], ys[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      xs[k] = __ldcs(xv + i + k * kThreads);
+      if (axpy) ys[k] = __ldcs(yv + i + k * kThreads);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      E* xe = reinterpret_cast<E*>(&xs[k]);
+      E* ye = reinterpret_cast<E*>(&ys[k]);
+#pragma unroll
+      for (int c = 0; c < kV; ++c) ye[c] = axpy ? add_rn(ye[c], one ? xe[c] : mul_rn(a, xe[c])) : xe[c];
+      __stcs(yv + i + k * kThreads, ys[k]);
+    }
+  }
+  for (; i < nv; i += kThreads) {
+    V xs = __ldcs(xv + i), ys = axpy ? __ldcs(yv + i) : xs;
+    E* xe = reinterpret_cast<E*>(&xs);
+    E* ye = reinterpret_cast<E*>(&ys);
+#pragma unroll
+    for (int c = 0; c < kV; ++c) ye[c] = axpy ? add_rn(ye[c], one ? xe[c] : mul_rn(a, xe[c])) : xe[c];
+    __stcs(yv + i, ys);
+  }
+  for (size_t e = nv * kV + threadIdx.x; e < n; e += kThreads)
+    y[e] = axpy ? add_rn(y[e], one ? x[e] : mul_rn(a, x[e])) : x[e];
+}
+
 template <typename EX, typename EY>
 __device__ void copy_axpy_t(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
-                            bool axpy, bool atomic) {
+                            bool axpy, bool atomic, double alpha) {
   const EX* x = (const EX*)Xt.ptr;
   EY* y = (EY*)Yt.ptr;
+  const EY a = (EY)alpha;
+  const bool one = alpha == 1.0;
+  if constexpr (sizeof(EX) == sizeof(EY)) {
+    if (!atomic && Xt.ld == Xt.cols && Yt.ld == Yt.cols && ((uintptr_t)x & 15) == 0 &&
+        ((uintptr_t)y & 15) == 0) {
+      const size_t r0 = (size_t)u0 * kBlk;
+      const size_t r1 = min((size_t)u1 * kBlk, (size_t)Yt.rows);
+      copy_axpy_flat<EY>(reinterpret_cast<const EY*>(x) + r0 * Yt.cols, y + r0 * Yt.cols,
+                         (r1 - r0) * Yt.cols, axpy, a, one);
+      return;
+    }
+  }
   for (uint32_t u = u0; u < u1; ++u) {
     const int r0 = (int)u * kBlk, mb = min(kBlk, Yt.rows - r0);
     for (int e = threadIdx.x; e < mb * Yt.cols; e += kThreads) {
       const int r = r0 + e / Yt.cols, c = e % Yt.cols;
-      const EX v = __ldcg(x + (size_t)r * Xt.ld + c);
+      const EY v = (EY)__ldcg(x + (size_t)r * Xt.ld + c);
       EY* py = y + (size_t)r * Yt.ld + c;
-      if (axpy && atomic) atomicAdd(py, (EY)v);  // ATOMIC_WRITE on Y
-      else *py = axpy ? (EY)(__ldcg(py) + (EY)v) : (EY)v;
+      const EY av = one ? v : mul_rn(a, v);
+      if (axpy && atomic) atomicAdd(py, av);  // ATOMIC_WRITE on Y
+      else *py = axpy ? add_rn(__ldcg(py), av) : v;
     }
   }
 }
 
 __device__ void op_copy_axpy(const TileDesc& Xt, const TileDesc& Yt, uint32_t u0, uint32_t u1,
-                             bool axpy, bool atomic = false) {
+                             bool axpy, bool atomic = false, double alpha = 1.0) {
   const bool xf = Xt.dtype == SPX_DT_F32, yf = Yt.dtype == SPX_DT_F32;
-  if (!xf && !yf) copy_axpy_t<double, double>(Xt, Yt, u0, u1, axpy, atomic);
-  else if (!xf) copy_axpy_t<double, float>(Xt, Yt, u0, u1, axpy, atomic);
-  else if (!yf) copy_axpy_t<float, double>(Xt, Yt, u0, u1, axpy, atomic);
-  else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy, atomic);
+  if (!xf && !yf) copy_axpy_t<double, double>(Xt, Yt, u0, u1, axpy, atomic, alpha);
+  else if (!xf) copy_axpy_t<double, float>(Xt, Yt, u0, u1, axpy, atomic, alpha);
+  else if (!yf) copy_axpy_t<float, double>(Xt, Yt, u0, u1, axpy, atomic, alpha);
+  else copy_axpy_t<float, float>(Xt, Yt, u0, u1, axpy, atomic, alpha);
+}
+
+// Coulomb interactions (the paper's particle test case): targets
+// [t0, t0 + mt) of group T (n x 8 FP64 rows: x, y, z, q, phi, E) against all
+// ns sources of group S; self: S is T, and a target skips itself.  Each
+// interaction adds q_j / r to phi_i and q_j (x_i - x_j) / r^3 to E_i, r = 0
+// skipped; 1 / r is 1 / sqrt(r^2) with IEEE square root and division.  The
+// 256 threads are 64 targets x 4 source slices (slice q: sources j = q mod
+// 4, in order), sources staged 256 at a time in shared memory; the four
+// partial sums of a target are added in slice order (deterministic).
+__device__ void nbody_block(double* T, int ldt, int t0, int mt, const double* S, int lds, int ns,
+                            bool self, F64Smem& s) {
+  const int tid = threadIdx.x, ti = tid & 63, q = tid >> 6;
+  const int i = t0 + ti;
+  const bool live = ti < mt;
+  const double xi = live ? T[(size_t)i * ldt + 0] : 0.0;
+  const double yi = live ? T[(size_t)i * ldt + 1] : 0.0;
+  const double zi = live ? T[(size_t)i * ldt + 2] : 0.0;
+  double phi = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+  double* src = &s.l[0][0];  // [256][4]: x, y, z, q
+  static_assert(sizeof(s.l) >= 256 * 4 * sizeof(double), "source staging");
+  static_assert(sizeof(s.x) >= 4 * 64 * 4 * sizeof(double), "partial sums");
+  for (int j0 = 0; j0 < ns; j0 += 256) {
+    const int nj = min(256, ns - j0);
+    __syncthreads();
+    for (int e = tid; e < nj * 4; e += kThreads) src[e] = __ldcg(S + (size_t)(j0 + e / 4) * lds + e % 4);
+    __syncthreads();
+    if (live) {
+      for (int jj = q; jj < nj; jj += 4) {
+        if (self && j0 + jj == i) continue;
+        const double dx = xi - src[4 * jj + 0];
+        const double dy = yi - src[4 * jj + 1];
+        const double dz = zi - src[4 * jj + 2];
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (r2 > 0.0) {
+          const double rinv = 1.0 / sqrt(r2);
+          const double qr = src[4 * jj + 3] * rinv;
+          const double s3 = qr * rinv * rinv;
+          phi += qr;
+          ex = fma(s3, dx, ex);
+          ey = fma(s3, dy, ey);
+          ez = fma(s3, dz, ez);
+        }
+      }
+    }
+  }
+  double* red = &s.x[0][0];  // [4 slices][64 targets][4]
+  __syncthreads();
+  red[(q * 64 + ti) * 4 + 0] = phi;
+  red[(q * 64 + ti) * 4 + 1] = ex;
+  red[(q * 64 + ti) * 4 + 2] = ey;
+  red[(q * 64 + ti) * 4 + 3] = ez;
+  __syncthreads();
+  if (tid < 64 && live) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int qq = 0; qq < 4; ++qq)
+      for (int c = 0; c < 4; ++c) a[c] += red[(qq * 64 + ti) * 4 + c];
+    for (int c = 0; c < 4; ++c) T[(size_t)i * ldt + 4 + c] += a[c];
+  }
+  __syncthreads();
+}
+
+// NBODY_SELF / NBODY_PAIR units: 64-target blocks of P (against P itself,
+// or against Q), then, for a pair, of Q against P.
+__device__ void op_nbody(const TileDesc& Pt, const TileDesc* Qt, uint32_t u0, uint32_t u1,
+                         F64Smem& s) {
+  const uint32_t np = cdiv64(Pt.rows);
+  for (uint32_t u = u0; u < u1; ++u) {
+    const bool onp = u < np;
+    const TileDesc& Tg = onp ? Pt : *Qt;
+    const TileDesc& Sg = Qt ? (onp ? *Qt : Pt) : Pt;
+    const int t0 = (int)(onp ? u : u - np) * kBlk;
+    nbody_block((double*)Tg.ptr, Tg.ld, t0, min(kBlk, Tg.rows - t0), (const double*)Sg.ptr, Sg.ld,
+                Sg.rows, Qt == nullptr, s);
+  }
 }
 
 }  // namespace

@@ -434,6 +434,58 @@ extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, doub
   return rc;
 }
 
+extern "C" int spx_axpy_insert(spx_graph_t g, float* dev_x, float* dev_y, long long n,
+                               long long piece, double alpha, long long* out_ntasks) {
+  if (!g || !dev_x || !dev_y || n < 1 || piece < 1 || dev_x == dev_y) return SPX_ERR_INVALID_ARG;
+  long long count = 0;
+  int rc = SPX_OK;
+  for (long long p0 = 0; p0 < n && rc == SPX_OK; p0 += piece) {
+    const long long len = n - p0 < piece ? n - p0 : piece;
+    // a piece is a (len / 1024) x 1024 tile when 1024 divides it (so that its
+    // 64-row units spread over CTAs), else one row
+    const int cols = len % 1024 == 0 ? 1024 : (int)len;
+    const long long rows = len / cols;
+    if (rows > 0x7FFFFFFF || (len % 1024 != 0 && len > 0x7FFFFFFF)) return SPX_ERR_INVALID_ARG;
+    unsigned hx = 0, hy = 0, id = 0;
+    rc = spx_tile_register(g, dev_x + p0, (int)rows, cols, cols, SPX_DT_F32, nullptr, 0, &hx);
+    if (rc == SPX_OK)
+      rc = spx_tile_register(g, dev_y + p0, (int)rows, cols, cols, SPX_DT_F32, nullptr, 0, &hy);
+    const unsigned hs[2] = {hx, hy};
+    const int ms[2] = {SPX_READ, SPX_WRITE};
+    if (rc == SPX_OK) rc = spx_task_insert(g, SPX_OP_AXPY, hs, ms, 2, 0, SPX_F64, &id);
+    if (rc == SPX_OK && alpha != 1.0) rc = spx_task_set_scalar(g, id, alpha);
+    if (rc == SPX_OK) ++count;
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_nbody_insert(spx_graph_t g, int ngroups, double* const* dev_groups,
+                                const int* sizes, int commutative, long long* out_ntasks) {
+  if (!g || ngroups < 1 || !dev_groups || !sizes) return SPX_ERR_INVALID_ARG;
+  std::vector<unsigned> h(ngroups);
+  int rc = SPX_OK;
+  for (int i = 0; i < ngroups && rc == SPX_OK; ++i) {
+    if (!dev_groups[i] || sizes[i] < 1) return SPX_ERR_INVALID_ARG;
+    rc = spx_tile_register(g, dev_groups[i], sizes[i], 8, 8, SPX_DT_F64, nullptr, 0, &h[i]);
+  }
+  const int W = commutative ? SPX_COMMUTATIVE_WRITE : SPX_WRITE;
+  long long count = 0;
+  for (int i = 0; i < ngroups && rc == SPX_OK; ++i) {
+    const int m1[1] = {W};
+    rc = spx_task_insert(g, SPX_OP_NBODY_SELF, &h[i], m1, 1, 0, SPX_F64, nullptr);
+    if (rc == SPX_OK) ++count;
+    for (int j = i + 1; j < ngroups && rc == SPX_OK; ++j) {
+      const unsigned hs[2] = {h[i], h[j]};
+      const int m2[2] = {W, W};
+      rc = spx_task_insert(g, SPX_OP_NBODY_PAIR, hs, m2, 2, 0, SPX_F64, nullptr);
+      if (rc == SPX_OK) ++count;
+    }
+  }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
 extern "C" int spx_cholesky_insert_batch(spx_graph_t g, int count, double* const* dev_A,
                                          const int* n, const int* lda, const int* b,
                                          double* const* dev_X, const int* nrhs, const int* ldx,

@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
  OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI,
- OP_TRSM_INV) = range(16)
+ OP_TRSM_INV, OP_NBODY_SELF, OP_NBODY_PAIR) = range(18)
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
-            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV")
+            "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV",
+            "NBODY_SELF", "NBODY_PAIR")
 F64, TF32, BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
@@ -54,6 +55,9 @@ def _load():
         "spx_tile_register": (I, [P, P, I, I, I, I, P, I, P]),
         "spx_task_insert": (I, [P, I, P, P, I, I, I, P]),
         "spx_task_set_arg": (I, [P, U, LL]),
+        "spx_task_set_scalar": (I, [P, U, ctypes.c_double]),
+        "spx_axpy_insert": (I, [P, P, P, LL, LL, ctypes.c_double, P]),
+        "spx_nbody_insert": (I, [P, I, P, P, I, P]),
         "spx_graph_derive": (I, [P, P]),
         "spx_graph_execute": (I, [P, P]),
         "spx_batch_execute": (I, [P, I, P]),

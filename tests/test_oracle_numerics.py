@@ -314,3 +314,74 @@ def test_cholesky_inv_matches_substitution(n, b):
     assert O.tiled_cholesky_inv(L2, b, V) == 0
     err = np.abs(np.tril(L1) - np.tril(L2)).max() / np.abs(np.tril(L1)).max()
     assert err <= 1e-13, err
+
+
+def test_axpy_f32_exact():
+    """FP32 y <- y + alpha x, one rounding per operation: numpy's float32
+    arithmetic (IEEE single, no fused multiply-add) gives the same bits;
+    alpha = 1 adds x directly; small integers and powers of two are exact."""
+    n = 100003
+    x = inputs.uniform((n,), 11).numpy().astype(np.float32)
+    y0 = inputs.uniform((n,), 12).numpy().astype(np.float32)
+    for alpha in (1.0, 0.5, -3.25, 1.1):
+        y = y0.copy()
+        O.axpy_f32(x, y, alpha)
+        a = np.float32(alpha)
+        ref = (y0 + x) if alpha == 1.0 else (a * x + y0)
+        assert ref.dtype == np.float32
+        assert np.array_equal(y, ref), alpha
+    xi = np.arange(-50, 50, dtype=np.float32)
+    yi = np.full(100, 7.0, np.float32)
+    O.axpy_f32(xi, yi, 2.0)
+    assert np.array_equal(yi, 2 * np.arange(-50, 50) + 7.0)
+
+
+def particles(sizes, seed):
+    N = int(np.sum(sizes))
+    P = np.zeros((N, 8), np.float64)
+    P[:, 0:3] = inputs.uniform((N, 3), seed).numpy()
+    P[:, 3] = inputs.uniform((N,), seed + 1).numpy()
+    return np.ascontiguousarray(P)
+
+
+def test_nbody_closed_forms():
+    """Two charges 2 and 3 at distance 2 on the x axis: phi = 3/2 and 1, E_x =
+    3 (0 - 2) / 8 = -3/4 and 2 (2 - 0) / 8 = 1/2, exactly.  Six unit charges
+    at +-e_x, +-e_y, +-e_z around a charge at the origin: phi = 6 and E = 0
+    exactly at the origin (the terms cancel pairwise in order)."""
+    P = np.zeros((2, 8))
+    P[0, 3], P[1, 0], P[1, 3] = 2.0, 2.0, 3.0
+    assert O.nbody(P, [2]) == 0
+    assert P[0, 4] == 1.5 and P[1, 4] == 1.0
+    assert P[0, 5] == -0.75 and P[1, 5] == 0.5 and not P[:, 6:].any()
+    Q = np.zeros((7, 8))
+    Q[0, 3] = 1.0
+    for k, (ax, sg) in enumerate([(0, 1), (0, -1), (1, 1), (1, -1), (2, 1), (2, -1)]):
+        Q[k + 1, ax] = sg
+        Q[k + 1, 3] = 1.0
+    Q2 = Q.copy()
+    assert O.nbody(Q, [7]) == 0
+    assert Q[0, 4] == 6.0 and not Q[0, 5:].any()
+    # the same particles in two groups (pair tasks): same values
+    assert O.nbody(Q2, [3, 4]) == 0
+    assert Q2[0, 4] == 6.0 and not Q2[0, 5:].any()
+
+
+@pytest.mark.parametrize("sizes", [[40], [7, 30, 13], [1, 1, 5]])
+def test_nbody_vs_numpy_and_newton(sizes):
+    """Random charges: the grouped task list equals the all-pairs sum (numpy
+    broadcasting over the definition) to FP64 rounding, and the total force
+    sum_i q_i E_i vanishes (Newton's third law) to rounding."""
+    P = particles(sizes, sum(sizes))
+    X, q = P[:, :3].copy(), P[:, 3].copy()
+    assert O.nbody(P, sizes) == 0
+    d = X[:, None, :] - X[None, :, :]
+    r = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    phi = (q[None, :] / r).sum(1)
+    E = (q[None, :, None] * d / r[:, :, None] ** 3).sum(1)
+    scale = (np.abs(q)[None, :] / r ** 2).sum(1).max() * len(q)
+    assert np.abs(P[:, 4] - phi).max() <= 1e-13 * np.abs(phi).max()
+    assert np.abs(P[:, 5:] - E).max() <= 1e-13 * scale
+    total = (q[:, None] * P[:, 5:]).sum(0)
+    assert np.abs(total).max() <= 1e-12 * scale
