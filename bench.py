@@ -876,6 +876,26 @@ def run_mixed(args, world, rank, local):
                          "correction_solve": inf.get("correction"),
                          "factor_cta_time_share": {k: round(v, 4) for k, v in
                                                    inf.get("factor_op_share", {}).items()}}
+    # GMRES-based refinement from the same kind of factor (Carson-Higham):
+    # each step solves the correction equation by FP64 GMRES preconditioned
+    # with the factor
+    for name, prec in (("tf32", spx.TF32), ("bf16", spx.BF16)):
+        gr = []
+        for i in range(1 + args.steps):
+            ev[0].record()
+            X, L, info = mixed.gmres_ir_solve(A0, B, b=b, prec=prec)
+            ev[1].record()
+            ev[1].synchronize()
+            if i >= 1:
+                gr.append((ev[0].elapsed_time(ev[1]), info))
+            last[name + "_gmres"] = (X, L)
+            del X, L
+        gi = gr[-1][1]
+        out[name]["gmres_ir"] = {"ms_per_solve": statistics.mean(r[0] for r in gr),
+                                 "factor_ms": statistics.mean(r[1]["factor_ms"] for r in gr),
+                                 "refine_ms": statistics.mean(r[1]["refine_ms"] for r in gr),
+                                 "converged": gi["converged"], "outer": gi["outer"],
+                                 "inner": gi["inner"], "eta_device": gi["eta_final"]}
     if rank == 0:
         # The oracle's checks of the last run of each precision (host, one
         # core): normwise backward error of X with compensated residuals, and
@@ -900,6 +920,9 @@ def run_mixed(args, world, rank, local):
             out[name]["eta_oracle_per_rhs"] = [float(x) for x in eta]
             out[name]["factor_freivalds_oracle"] = fr
             out[name]["oracle_check_s"] = {"eta": t1 - t0, "freivalds": t2 - t1}
+            Xg, _ = last[name + "_gmres"]
+            out[name]["gmres_ir"]["eta_oracle"] = float(
+                O.solve_backward_error(A0h, Xg.cpu().numpy(), Bh).max())
         del A0h
     last.clear()
     out["value"] = out["tf32"]["gflops_total"]

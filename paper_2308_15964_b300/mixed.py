@@ -272,3 +272,46 @@ def mixed_solve(A0, B, b: int = 512, prec: int = spx.TF32, tol: float = 1e-14,
     g.close()
     gs.close()
     return X, A, out
+
+
+def gmres_ir_solve(A0, B, b: int = 512, prec: int = spx.BF16, tol: float = 1e-14,
+                   max_outer: int = 20, max_inner: int = 30, inner_tol: float = 1e-10):
+    """Solve A0 X = B with the mixed-precision factor (tensor-core panel and
+    trailing updates, FP64 POTRF) and GMRES-based refinement (spx_gmres_ir):
+    each refinement step solves the correction equation by FP64 GMRES
+    preconditioned with the factor (its solve graph applying the FP64
+    inverses of the diagonal tiles).  Returns (X, L, info) with 'converged',
+    'outer', 'inner', 'eta_final' (certified when converged), 'factor_ms',
+    'refine_ms', 'status'."""
+    n, nrhs = B.shape
+    A = A0.clone()
+    Alo = torch.zeros((n, n), dtype=lowp_dtype(prec), device=A0.device)
+    X = B.clone()
+    V = torch.empty((n, min(b, n)), dtype=torch.float64, device=A0.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    g = spx.Graph()
+    factor_graph(g, A, Alo, b, X, prec, V=V)
+    ev[0].record()
+    rc, info = g.run()
+    ev[1].record()
+    g.close()
+    if rc != spx.OK:
+        return X, A, {"status": rc, "info": info, "converged": False, "outer": 0, "inner": 0}
+    R, D = torch.empty_like(B), torch.empty_like(B)
+    gp = spx.Graph(cuda_graph=True)
+    solve_inv_graph(gp, A, b, V, R, D)
+    wbytes = spx.lib.spx_gmres_ir_workspace(n, nrhs, max_inner)
+    if wbytes < 0:
+        raise ValueError("unsupported GMRES size")
+    work = torch.empty(wbytes // 8 + 1, dtype=torch.float64, device=A0.device)
+    cfg = spx.GmresConfig(max_outer, max_inner, inner_tol, tol)
+    res = spx.GmresResult()
+    rc = spx.lib.spx_gmres_ir(_p(A0), n, A0.stride(0), _p(B), _p(X), nrhs, gp._h, _p(R), _p(work),
+                              wbytes, ctypes.byref(cfg), ctypes.byref(res), _s(None))
+    ev[2].record()
+    ev[2].synchronize()
+    gp.close()
+    spx._check(rc, "spx_gmres_ir")
+    return X, A, {"status": rc, "converged": bool(res.converged), "outer": res.outer,
+                  "inner": res.inner, "eta_final": res.eta,
+                  "factor_ms": ev[0].elapsed_time(ev[1]), "refine_ms": ev[1].elapsed_time(ev[2])}

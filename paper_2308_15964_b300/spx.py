@@ -89,6 +89,8 @@ def _load():
         "spx_solve_inv_f32_insert": (I, [P, P, I, I, I, P, I, P, P, P, P, I, I, P]),
         "spx_residual_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P]),
         "spx_residual_eta_f64": (I, [P, I, I, P, I, P, I, P, I, I, P, P, P, I, P]),
+        "spx_gmres_ir_workspace": (LL, [I, I, I]),
+        "spx_gmres_ir": (I, [P, I, I, P, P, I, P, P, P, LL, P, P, P]),
         "spx_norm_inf_f64": (I, [P, I, I, P, P]),
         "spx_axpy_f64": (I, [P, P, LL, ctypes.c_double, P]),
         "spx_server_config_default": (None, [P]),
@@ -284,6 +286,16 @@ def batch_execute(graphs, stream=None):
     wait on each graph for its own status."""
     arr = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
     _check(lib.spx_batch_execute(arr, len(graphs), _stream_ptr(stream)), "spx_batch_execute")
+
+
+class GmresConfig(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("tol", ctypes.c_double)]
+
+
+class GmresResult(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer", ctypes.c_int), ("inner", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("eta", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
