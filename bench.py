@@ -370,6 +370,18 @@ def main():
                                               "unit": "GFLOP/s", "ms_per_step": statistics.mean(grec),
                                               "note": "execution only (the graph is inserted once)"}
         gg.close()
+        # the same workload with priorities from the critical path
+        gp = spx.Graph(priorities=1)
+        step(gp)
+        prec_ = []
+        for _ in range(COMPARATOR_STEPS):
+            step(gp, prec_)
+        pms = [r[0] for r in prec_]
+        out["bottom_level_priorities"] = {"value": flops / (statistics.mean(pms) * 1e-3) / 1e9,
+                                          "unit": "GFLOP/s", "ms_per_step": statistics.mean(pms),
+                                          "p99_ms": float(np.percentile(pms, 99)),
+                                          "steps": len(pms)}
+        gp.close()
         out["latency_small"] = small_latency(spx, cholesky, inputs, torch)
         out["gemm_dag"] = gemm_dag(spx, cholesky, inputs, torch, 8192, b, args.warmup, args.steps,
                                    max_mhz, comparators=True)
@@ -1052,12 +1064,13 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
     res = {}
     for name, ex, rederive, cg, solve in (
             ("persistent", spx.EXEC_PERSISTENT, False, False, True),
+            ("persistent_bottom_level", -1, False, False, True),
             ("persistent_factor_only", spx.EXEC_PERSISTENT, False, False, False),
             ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False, True),
             ("per_task", spx.EXEC_PER_TASK, False, False, True),
             ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True, True),
             ("streams", spx.EXEC_STREAMS, False, False, True)):
-        g = spx.Graph(executor=ex, cuda_graph=cg)
+        g = (spx.Graph(priorities=1) if ex < 0 else spx.Graph(executor=ex, cuda_graph=cg))
         Xs = X if solve else None
         ntasks = cholesky.cholesky_graph(g, A, b, Xs)
         lat = []
@@ -1085,18 +1098,22 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
     res["workload"] = ("n=512 tile=64, 1 RHS: factorization + block solve, 192 tasks (the "
                        "_factor_only row: the 120 factorization tasks); host wall time of "
                        "execute->wait over %d runs; the graph is reset and re-run, except "
-                       "persistent_insert_derive, which inserts and derives every time" % reps)
+                       "persistent_insert_derive, which inserts and derives every time; "
+                       "_bottom_level: priorities from the critical path (cfg.priorities = 1) "
+                       "instead of the look-ahead marks" % reps)
     res["critical_path"] = critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b)
+    res["critical_path_bottom_level"] = critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b,
+                                                            priorities=1)
     return res
 
 
-def critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b):
+def critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b, priorities=0):
     """Critical path of one traced persistent run of the small case: walk back
     from the last task to finish, each time to the predecessor that finished
     last; per task on that path, the time it ran (first part start to last
     part end, %globaltimer) and the gap since that predecessor's end (the
     release of its successors, the pop, and the wait for a free CTA)."""
-    g = spx.Graph(trace=True)
+    g = spx.Graph(trace=True, priorities=priorities)
     cholesky.cholesky_graph(g, A, b, X)
     runs = []
     for _ in range(6):

@@ -217,7 +217,10 @@ typedef struct {
                                  reset graph (state reset, queue set-up,
                                  executor, status copy) into a CUDA graph on
                                  its second execute and replay it after     */
-  int pad_;
+  int priorities;             /* 0 = the priorities given at insertion;
+                                 1 = from the critical path of the DAG (see
+                                 spx_graph_assign_priorities), at the first
+                                 execute                                      */
 } spx_graph_config_t;
 
 /* Fill *cfg with the defaults. */
@@ -279,6 +282,20 @@ int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg);
  * Errors: SPX_ERR_BAD_HANDLE, SPX_ERR_STATE, SPX_ERR_INVALID_ARG (not an
  * AXPY task, or alpha not finite or zero). */
 int spx_task_set_scalar(spx_graph_t g, unsigned task, double alpha);
+
+/* Criticality (the paper blames its Cholesky variance on scheduling without
+ * it, section "Numerical applications"): replace every task's priority by
+ * one computed from the longest paths of the DAG.  Each task weighs its
+ * number of phases (its length in dependent steps); the top level t(u) is
+ * the longest weighted path ending before u, the bottom level b(u) the
+ * longest starting at u (u included), CP = max (t + b), slack(u) = CP -
+ * t(u) - b(u).  Slack 0 (on a longest path): class 2 (critical-path queue,
+ * finer parts); slack <= CP / 10: class 1; else 0.  Both levels come from the
+ * access records in one forward and one backward pass over the tasks, with
+ * per-handle group maxima (the STF groups give each task's predecessors and
+ * successors), without the derived DAG.  Host only; the graph must be built
+ * and not running.  Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE. */
+int spx_graph_assign_priorities(spx_graph_t g);
 
 /* Derive the dependency DAG on the device (successor CSR sorted ascending,
  * de-duplicated, and in-degrees) without executing it.  Asynchronous on

@@ -34,10 +34,16 @@ enum {
   SPX_PROBE_WARP_DDIV = 11,      /* cycles per warp FP64 division, same     */
   SPX_PROBE_LAT_DRCP = 12,       /* dependent __drcp_rn + multiply chain    */
   SPX_PROBE_LAT_DRSQRT = 13,     /* dependent rsqrt chain                   */
-  SPX_PROBE_NBODY = 14           /* the n-body interaction arithmetic (3 sub,
+  SPX_PROBE_NBODY = 14,          /* the n-body interaction arithmetic (3 sub,
                                     r^2, sqrt, division, 3 mul, add, 3 FMA)
                                     on register data, all SMs: interactions/s,
                                     the ALU ceiling of SPX_OP_NBODY_*        */
+  SPX_PROBE_WIDEN_CHECK = 15     /* the integer FP32 -> FP64 widening of the
+                                    tensor-core epilogues against the
+                                    hardware conversion, over all 2^32 FP32
+                                    bit patterns: *rate = number of
+                                    mismatches (NaNs compare as NaN), 0 when
+                                    exact; iters is ignored                  */
 };
 
 /* Run probe `which` with `iters` inner iterations (or launches).  Writes the

@@ -444,7 +444,8 @@ int spx_graph_create(spx_graph_t* out, const spx_graph_config_t* cfg) {
   if (!g) return SPX_ERR_OOM;
   spx_config_default(&g->cfg);
   if (cfg) {
-    if (cfg->num_ctas < 0 || cfg->queue_capacity < 0 ||
+    if (cfg->num_ctas < 0 || cfg->queue_capacity < 0 || cfg->priorities < 0 ||
+        cfg->priorities > 1 ||
         (cfg->executor != SPX_EXEC_PERSISTENT && cfg->executor != SPX_EXEC_PER_TASK &&
          cfg->executor != SPX_EXEC_STREAMS)) {
       delete g;
@@ -624,10 +625,100 @@ int spx_task_set_scalar(spx_graph_t g, unsigned task, double alpha) {
   return SPX_OK;
 }
 
+int spx_graph_assign_priorities(spx_graph_t g) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state == kRunning) return SPX_ERR_STATE;
+  const size_t N = g->tasks.size(), H = g->tiles.size();
+  if (N == 0) return SPX_ERR_STATE;
+  // weight: phases of the task (its dependent steps; serial tasks one)
+  std::vector<double> w(N), tl(N), bl(N);
+  for (size_t u = 0; u < N; ++u) w[u] = std::max<uint32_t>(g->tasks[u].nphases, 1);
+  auto groups = [](int m) {
+    return m == SPX_READ || m == SPX_COMMUTATIVE_WRITE || m == SPX_ATOMIC_WRITE;
+  };
+  struct Fwd { int mode = -1; double last = 0.0, prev = 0.0; };
+  std::vector<Fwd> f(H);
+  for (size_t u = 0; u < N; ++u) {  // top levels, insertion order
+    double t = 0.0;
+    for (uint32_t r = g->task_rec[u]; r < g->task_rec[u + 1]; ++r) {
+      const Fwd& s = f[g->rec_handle[r]];
+      const int m = g->rec_mode[r];
+      if (s.mode < 0) continue;
+      t = std::max(t, (s.mode == m && groups(m)) ? s.prev : s.last);
+    }
+    tl[u] = t;
+    const double end = t + w[u];
+    for (uint32_t r = g->task_rec[u]; r < g->task_rec[u + 1]; ++r) {
+      Fwd& s = f[g->rec_handle[r]];
+      const int m = g->rec_mode[r];
+      if (s.mode == m && groups(m)) {
+        s.last = std::max(s.last, end);
+      } else {
+        s.prev = s.mode < 0 ? 0.0 : s.last;
+        s.last = end;
+        s.mode = m;
+      }
+    }
+  }
+  struct Bwd { int mode = -1; double cur = 0.0, next = 0.0; };
+  std::vector<Bwd> b(H);
+  for (size_t k = N; k-- > 0;) {  // bottom levels, reverse insertion order
+    double s_max = 0.0;
+    for (uint32_t r = g->task_rec[k]; r < g->task_rec[k + 1]; ++r) {
+      const Bwd& s = b[g->rec_handle[r]];
+      const int m = g->rec_mode[r];
+      if (s.mode < 0) continue;
+      s_max = std::max(s_max, (s.mode == m && groups(m)) ? s.next : s.cur);
+    }
+    bl[k] = w[k] + s_max;
+    for (uint32_t r = g->task_rec[k]; r < g->task_rec[k + 1]; ++r) {
+      Bwd& s = b[g->rec_handle[r]];
+      const int m = g->rec_mode[r];
+      if (s.mode == m && groups(m)) {
+        s.cur = std::max(s.cur, bl[k]);
+      } else {
+        s.next = s.mode < 0 ? 0.0 : s.cur;
+        s.cur = bl[k];
+        s.mode = m;
+      }
+    }
+  }
+  double cp = 0.0;
+  for (size_t u = 0; u < N; ++u) cp = std::max(cp, tl[u] + bl[u]);
+  g->items[0] = g->items[1] = g->items[2] = 0;
+  for (size_t u = 0; u < N; ++u) {
+    TaskDesc& t = g->tasks[u];
+    const double slack = cp - tl[u] - bl[u];
+    const int cls = slack <= 1e-9 * cp ? 2 : (slack <= 0.1 * cp ? 1 : 0);
+    t.prio = (uint8_t)cls;
+    uint32_t items = 1;
+    if (!(t.flags & kFlagSerial)) {
+      t.flags = (uint8_t)((t.flags & ~kFlagFine) | (cls == 2 ? kFlagFine : 0));
+      const bool fine = cls == 2;
+      t.nparts = phase_parts(op_phase_units(t.op, t.prec, g->tiles.data(), t.h, 0, fine));
+      items = 0;
+      for (uint32_t ph = 0; ph < t.nphases; ++ph)
+        items += phase_parts(op_phase_units(t.op, t.prec, g->tiles.data(), t.h, ph, fine));
+    }
+    g->items[graph_queue(t.prio)] += items;
+  }
+  g->uploaded = false;
+  g->derived = false;
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
+  return SPX_OK;
+}
+
 int spx_graph_derive(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state == kRunning) return SPX_ERR_STATE;
   if (g->tasks.empty()) return SPX_ERR_STATE;
+  if (g->cfg.priorities == 1 && g->state == kBuilding) {
+    const int rc = spx_graph_assign_priorities(g);
+    if (rc != SPX_OK) return rc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   int rc = SPX_OK;
   if (!g->uploaded) rc = prepare_device(g, st);
@@ -752,6 +843,10 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
   if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
   if (g->tasks.empty()) return SPX_ERR_STATE;
   g->batch_of = nullptr;  // runs alone from now on
+  if (g->cfg.priorities == 1 && g->state == kBuilding) {
+    const int prc = spx_graph_assign_priorities(g);
+    if (prc != SPX_OK) return prc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   int rc = SPX_OK;
   cudaError_t e = cudaSuccess;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "spx_probe.h"
+#include "tile_tc.cuh"
 
 namespace {
 
@@ -71,6 +72,19 @@ __global__ void atomic_distinct_kernel(unsigned* ctr, int iters, int n) {
 }
 
 __global__ void empty_kernel() {}
+
+// Every FP32 bit pattern: the integer widening against (double)f.
+__global__ void widen_check_kernel(unsigned long long* bad) {
+  unsigned long long nbad = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       i < (1ull << 32); i += (unsigned long long)gridDim.x * blockDim.x) {
+    const float f = __uint_as_float((uint32_t)i);
+    const double w = spx::widen_f32(f), h = (double)f;
+    const bool ok = (f != f) ? (w != w) : (__double_as_longlong(w) == __double_as_longlong(h));
+    nbad += ok ? 0u : 1u;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
 
 // The interaction arithmetic of the n-body ops on register data: 4
 // independent targets per thread against a moving source.
@@ -207,6 +221,10 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
         for (int i = 0; i < iters; ++i) empty_kernel<<<1, 32, 0, st>>>();
         work = iters;
         break;
+      case SPX_PROBE_WIDEN_CHECK:
+        widen_check_kernel<<<blocks, threads, 0, st>>>((unsigned long long*)buf);
+        work = 0.0;
+        break;
       case SPX_PROBE_NBODY:
         nbody_probe_kernel<<<blocks, threads, 0, st>>>((double*)buf, iters, 0.75);
         work = 4.0 * (double)iters * blocks * threads;
@@ -232,6 +250,9 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   float t = 0.f;
   cudaEventElapsedTime(&t, e0, e1);
   double cyc = 0.0;  // latency probes: cycles per step, written by the kernel
+  unsigned long long bad_count = 0;  // widening check: mismatches
+  if (err == cudaSuccess && which == SPX_PROBE_WIDEN_CHECK)
+    err = cudaMemcpy(&bad_count, buf, sizeof(bad_count), cudaMemcpyDeviceToHost);
   if (err == cudaSuccess && which >= SPX_PROBE_LAT_DFMA && which <= SPX_PROBE_LAT_DRSQRT)
     err = cudaMemcpy(&cyc, buf, sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(buf);
@@ -243,6 +264,7 @@ extern "C" int spx_probe(int which, int iters, double* rate, double* ms) {
   *ms = t;
   const bool lat = which >= SPX_PROBE_LAT_DFMA && which <= SPX_PROBE_LAT_DRSQRT;
   *rate = lat ? cyc : work / (t * 1e-3);
+  if (which == SPX_PROBE_WIDEN_CHECK) *rate = (double)bad_count;
   return 0;
 }
 

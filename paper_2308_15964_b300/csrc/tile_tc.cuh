@@ -52,19 +52,31 @@ struct TcState {
 };
 
 // Exact FP32 -> FP64 widening from the IEEE-754 formats, on the integer
-// pipe: for a normal float, the double keeps sign and mantissa (shifted up 29
-// bits) and rebiases the exponent (127 -> 1023); zeros keep their sign.  The
-// epilogue's FP64 pipe (2 operations per clock per SM on this GPU) then only
-// does the subtraction.  Subnormal, infinite and NaN floats take the
-// hardware conversion.
+// pipe only, so that the epilogue's FP64 pipe (2 operations per clock per SM
+// on this GPU) does nothing but the subtraction:
+//   normal (1 <= e <= 254): sign, exponent e - 127 + 1023, mantissa << 29;
+//   zero: the sign alone;
+//   subnormal (e = 0, m != 0): m 2^-149 with m of bit length L = 32 - clz(m):
+//     shift m left by s = 24 - L so its leading one sits at bit 23, then
+//     exponent L - 150 + 1023 = 897 - s and the 23 bits below the leading one
+//     as the mantissa;
+//   infinity / NaN (e = 255): exponent 2047, mantissa << 29 (payload kept).
 __device__ __forceinline__ double widen_f32(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
   const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  if (e == 0u && m == 0u) return __longlong_as_double((long long)sign);
-  if (e == 0u || e == 0xFFu) return (double)f;
+  uint32_t e64, mm;
+  if (e == 0u) {
+    if (m == 0u) return __longlong_as_double((long long)sign);
+    const uint32_t sh = (uint32_t)__clz(m) - 8u;
+    e64 = 897u - sh;
+    mm = (m << sh) & 0x7FFFFFu;
+  } else {
+    e64 = e == 0xFFu ? 2047u : e + 896u;
+    mm = m;
+  }
   return __longlong_as_double(
-      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+      (long long)(sign | ((unsigned long long)e64 << 52) | ((unsigned long long)mm << 29)));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -40,7 +40,7 @@ class Config(ctypes.Structure):
     _fields_ = [("num_ctas", ctypes.c_int), ("executor", ctypes.c_int), ("trace", ctypes.c_int),
                 ("no_split", ctypes.c_int), ("watchdog_ns", ctypes.c_ulonglong),
                 ("queue_capacity", ctypes.c_longlong), ("cuda_graph", ctypes.c_int),
-                ("pad_", ctypes.c_int)]
+                ("priorities", ctypes.c_int)]
 
 
 def _load():
@@ -67,6 +67,7 @@ def _load():
         "spx_graph_tickets": (I, [P, P, P]),
         "spx_graph_trace": (I, [P, P]),
         "spx_graph_stats": (I, [P, P, I]),
+        "spx_graph_assign_priorities": (I, [P]),
         "spx_graph_task_ops": (I, [P, P, P]),
         "spx_graph_write_dot": (I, [P, ctypes.c_char_p]),
         "spx_graph_reset": (I, [P]),
@@ -144,7 +145,7 @@ class Graph:
     """An STF task graph (spx_graph_t)."""
 
     def __init__(self, num_ctas=0, executor=EXEC_PERSISTENT, trace=False, no_split=False,
-                 watchdog_ns=0, queue_capacity=0, cuda_graph=False):
+                 watchdog_ns=0, queue_capacity=0, cuda_graph=False, priorities=0):
         cfg = Config()
         lib.spx_config_default(ctypes.byref(cfg))
         cfg.num_ctas = num_ctas
@@ -155,6 +156,7 @@ class Graph:
             cfg.watchdog_ns = watchdog_ns
         cfg.queue_capacity = queue_capacity
         cfg.cuda_graph = 1 if cuda_graph else 0
+        cfg.priorities = int(priorities)
         h = ctypes.c_void_p()
         _check(lib.spx_graph_create(ctypes.byref(h), ctypes.byref(cfg)), "spx_graph_create")
         self._h = h
@@ -235,6 +237,9 @@ class Graph:
         r = np.zeros((n, 4), np.uint64)
         _check(lib.spx_graph_trace(self._h, _ptr(r)), "spx_graph_trace")
         return r
+
+    def assign_priorities(self):
+        _check(lib.spx_graph_assign_priorities(self._h), "spx_graph_assign_priorities")
 
     def task_ops(self):
         """(op, priority class) of every task, in insertion order."""
@@ -342,6 +347,9 @@ class Server:
 
     def stop(self) -> int:
         return lib.spx_server_stop(self._h)
+
+    def assign_priorities(self):
+        _check(lib.spx_graph_assign_priorities(self._h), "spx_graph_assign_priorities")
 
     def task_ops(self):
         """(op, priority class) of every task, in insertion order."""

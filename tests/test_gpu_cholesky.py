@@ -194,3 +194,26 @@ def test_scale_16384_sampled(S):
         assert O.freivalds(A_host, L, inputs.gaussian(n, 100 + s)) <= 1e-14
     assert O.solve_backward_error(A_host, X, B_host).max() <= 1e-14
     g.close()
+
+
+@pytest.mark.parametrize("n,b", [(512, 64), (1000, 128), (2048, 512)])
+def test_bottom_level_priorities_bit_identical(S, n, b):
+    """Priorities from the critical path (cfg.priorities = 1) change only the
+    order of execution and the part sizes, never a tile's arithmetic: factor
+    and solve bit-identical to the look-ahead marks, and the ticket order
+    respects every edge."""
+    A = inputs.spd_matrix(n, 1.0, seed=n)
+    X = inputs.rhs(n, 2, seed=n)
+    rc1, _, L1, X1, g1 = run_cholesky(A.numpy(), b, X.numpy())
+    rc2, _, L2, X2, g2 = run_cholesky(A.numpy(), b, X.numpy(), priorities=1)
+    assert rc1 == rc2 == 0
+    assert np.array_equal(L1, L2) and np.array_equal(X1, X2)
+    ops, prio = g2.task_ops()
+    assert (prio == 2).any() and (prio == 0).any()
+    rp, col, _ = g2.edges()
+    s, e = g2.tickets()
+    for u in range(len(rp) - 1):
+        for p in range(rp[u], rp[u + 1]):
+            assert e[u] < s[col[p]]
+    g1.close()
+    g2.close()

@@ -75,3 +75,29 @@ def test_random_within_fp32_accumulation(S, prec):
     Cd = C.cuda()
     tc_gemm(S, Cd, Al.cuda(), Bl.cuda(), S.BF16 if prec == "bf16" else S.TF32)
     assert ((Cd.cpu() - ref).abs() <= bound).all()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("m,n,K", [(2600, 2432, 200), (4096, 4096, 256)])
+def test_integer_exact_many_units(S, prec, m, n, K):
+    """More 128 x 128 units than SMs: every CTA of the pipelined kernel runs
+    several units, reusing both TMEM accumulators and every operand stage
+    (ragged last rows and K chunk included); still bit-exact."""
+    g = torch.Generator().manual_seed(m + n + K)
+    A = torch.randint(-1, 2, (m, K), generator=g).double()
+    B = torch.randint(-1, 2, (n, K), generator=g).double()
+    C = torch.randint(-50, 51, (m, n), generator=g).double()
+    ref = C - A @ B.T
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    Cd = C.cuda()
+    tc_gemm(S, Cd, A.to(dt).cuda(), B.to(dt).cuda(), S.BF16 if prec == "bf16" else S.TF32)
+    assert torch.equal(Cd.cpu(), ref)
+
+
+def test_widening_exact_for_every_float(S):
+    """The epilogues widen the FP32 accumulator to FP64 with integer
+    operations only (normal, zero, subnormal, infinite and NaN classes from
+    the IEEE formats); over all 2^32 FP32 bit patterns the result equals the
+    hardware conversion bit for bit (NaN stays NaN)."""
+    bad, _ = S.probe(15, 1)
+    assert bad == 0.0, bad

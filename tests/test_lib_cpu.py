@@ -161,3 +161,44 @@ def test_batch_validation(S):
     assert g1.wait()[0] == S.ERR_STATE              # nothing started
     for g in (g1, g2, g3):
         g.close()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_bottom_level_priorities_match_oracle_dag(S, seed):
+    """spx_graph_assign_priorities computes top and bottom levels from the
+    access records alone; the classes must equal those from longest paths on
+    the DAG the oracle derives (unit weights: NOP tasks have one phase):
+    slack 0 -> 2, slack <= CP/10 -> 1, else 0."""
+    from oracle import oracle as O
+    from paper_2308_15964_b300 import inputs
+    n = [5, 40, 120, 300][seed % 4]
+    t, k, m = inputs.random_access_lists(n, 1 + seed % 7, 4, seed=4242 + seed, nmodes=5)
+    ntask = int(t.max()) + 1
+    g = S.Graph()
+    handles = {}
+    for key in np.unique(k):
+        handles[int(key)] = g.register(FAKE + 4096 * int(key), 8, 8, 8)
+    i = 0
+    while i < len(t):
+        j = i
+        while j < len(t) and t[j] == t[i]:
+            j += 1
+        g.insert(S.OP_NOP, [handles[int(x)] for x in k[i:j]], [int(x) for x in m[i:j]])
+        i = j
+    g.assign_priorities()
+    _, got = g.task_ops()
+    rp, col, _ = O.derive(ntask, t, k, m)
+    tl = np.zeros(ntask)
+    for u in range(ntask):
+        for p in range(rp[u], rp[u + 1]):
+            v = int(col[p])
+            tl[v] = max(tl[v], tl[u] + 1)
+    bl = np.ones(ntask)
+    for u in range(ntask - 1, -1, -1):
+        for p in range(rp[u], rp[u + 1]):
+            bl[u] = max(bl[u], 1 + bl[int(col[p])])
+    cp = (tl + bl).max()
+    slack = cp - tl - bl
+    want = np.where(slack <= 1e-9 * cp, 2, np.where(slack <= 0.1 * cp, 1, 0))
+    assert np.array_equal(got, want), (got, want)
+    g.close()
