@@ -940,22 +940,25 @@ def run_mixed(args, world, rank, local):
     out["value"] = out["tf32"]["gflops_total"]
     out["ms_per_step"] = out["tf32"]["ms_per_solve"]
     out["clocks"] = clk.summary()
-    # The factor's FP64 work (TRSM b^3 and POTRF b^3/3 per tile, full tiles)
-    # dominates its CTA time (factor_cta_time_share); the trailing updates run
-    # on the tensor cores.  Roofline: that FP64 work over the factor time
-    # against the FP64 DFMA peak.
-    T = n // b
-    fp64_flops = T * (T - 1) / 2 * b ** 3 + T * b ** 3 / 3
-    sms = spx.lib.spx_device_sm_count()
-    peak = FP64_DFMA_PER_CLK_SM * 2 * sms * (out["clocks"].get("sm_max_mhz") or 2032.0) * 1e6 / 1e12
-    ach = fp64_flops / (out["tf32"]["factor_ms"] * 1e-3) / 1e12
-    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                       "frac": ach / peak, "traffic": None,
+    # Roofline of the factorization (the trailing updates dominate its bytes
+    # and flops): with the factor tiles' low-precision copies as operands and
+    # the trailing matrix in FP64 (read and written, 16 bytes per element per
+    # update), the algorithmic traffic is sum_k 16 (n - k b)^2 / 2 ~ 16 n^3 /
+    # (6 b) bytes; the n^3 / 3 flops on the tensor cores take less time at
+    # the measured BF16 rate (TF32: half of it), so HBM bounds it.
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    tbytes = 16.0 * n ** 3 / (6.0 * b)
+    fac_ms = out["tf32"]["factor_ms"]
+    out["roofline"] = {"bound": "hbm", "achieved": tbytes / (fac_ms * 1e-3) / 1e9, "peak": hbm,
+                       "unit": "GB/s", "frac": tbytes / (fac_ms * 1e-3) / 1e9 / hbm,
+                       "traffic": None,
                        "kernel": "persistent_kernel<tensor cores> (TF32 factorization)",
-                       "note": "FP64 flops of the factor (TRSM + POTRF tiles, "
-                               f"{fp64_flops / 1e9:.0f} GFLOP) over the TF32 factor time; the "
-                               f"{(n ** 3 / 3 - fp64_flops) / 1e12:.1f} TFLOP of trailing updates run "
-                               "on the tensor cores"}
+                       "note": f"algorithmic trailing-update bytes 16 n^3 / (6 b) = "
+                               f"{tbytes / 1e9:.0f} GB over the TF32 factor time "
+                               f"({fac_ms:.0f} ms, insertion and derivation included); the "
+                               "factor is bound by its chain of FP64 diagonal POTRF steps "
+                               "(64 x about 1.3 ms), not by HBM"}
     if rank == 0:
         print(json.dumps(out))
 
