@@ -171,7 +171,33 @@ enum {
  * relative, is dropped), i.e. about FP32 accuracy; the FP64 tile receives
  * the accumulator widened exactly and the low-precision copy its rounding
  * to the task's type. */
-enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2 };
+enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2, SPX_F64_OZAKI = 3 };
+
+/* SPX_F64_OZAKI: FP64 products emulated on the BF16 tensor cores by splitting
+ * (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 2012),
+ * allowed for TRSM, SYRK and GEMM_NT_SUB whose factor tiles have split slots
+ * in a store registered with spx_ozaki_register.  The paper's Cholesky spends
+ * almost all of its flops in these trailing updates (section "Numerical
+ * applications"); on this GPU the FP64 SIMT pipe peaks at about 1.2 TFLOP/s
+ * while the BF16 tensor cores reach about 2 PFLOP/s.
+ *   TRSM solves in FP64 and then splits its result: per row r, with e_r the
+ *   smallest integer such that every |a_rk| < 2^e_r (-1022 for a zero row),
+ *   X_rk = a_rk 2^(55 - e_r) rounded to the nearest integer (ties to even)
+ *   is written as eight balanced base-128 digits, X = sum_s sigma_s 128^(7-s)
+ *   (sigma_1..7 in [-64, 63] from the bottom, sigma_0 in [-64, 64]), each
+ *   stored exactly as a BF16; e_r is stored beside them.
+ *   SYRK / GEMM_NT_SUB (C -= A B^T, K = the factor tiles' columns <= 512)
+ *   accumulate P_d = sum over s + t = d of sigma_s(A) tau_t(B)^T for
+ *   d = 0..7 in separate FP32 accumulators on the tensor cores (pairs with
+ *   s + t > 7 are dropped).  |sigma tau| <= 2^12 and K <= 512 bound every
+ *   |P_d| by 2^24, so each P_d is an exact integer.  With
+ *   F = sum_d P_d 128^(7-d) (formed exactly in integers), the entry becomes
+ *   C_rc - v with v = F 2^(e_r + f_c - 61) rounded once to FP64 and the
+ *   subtraction rounded once.  Error of v against the exact product of the
+ *   FP64 tiles: at most about 2^-52.8 * K * 2^(e_r + f_c) (the input rounding
+ *   and the dropped pairs), below the worst-case bound of an FP64 dot
+ *   product of length K.  Finite inputs; products whose scale leaves the FP64
+ *   normal range are rounded twice. */
 
 /* Element type of a registered tile. */
 enum { SPX_DT_F64 = 0, SPX_DT_F32 = 1, SPX_DT_BF16 = 2 };
@@ -254,6 +280,23 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
 int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, int dtype,
                       unsigned* out_map);
 
+/* Bytes of one split slot of an SPX_F64_OZAKI tile with pitch b: eight BF16
+ * digit planes of b x b (plane s, row r, column k at element
+ * (s * b + r) * b + k), then b int32 row exponents, rounded up to 256 bytes.
+ * 0 for a b that spx_ozaki_register rejects. */
+long long spx_ozaki_slot_bytes(int b);
+
+/* Register a store of nslots split slots (consecutive, spx_ozaki_slot_bytes(b)
+ * bytes apart from dev_ptr, which must be 256-byte aligned) for
+ * SPX_F64_OZAKI tasks: the lowp_ptr of a tile registered with
+ * spx_tile_register must then be a slot's address, with lowp_ld = b and the
+ * tile's rows, cols <= b.  b a multiple of 32, 32 <= b <= 512.  The library
+ * builds two TMA tensor maps over the store (128- and 32-row boxes of 16
+ * digits of all eight planes, 32-byte swizzle).  Registering the same base
+ * again returns the same map.  Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE,
+ * SPX_ERR_CUDA. */
+int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned* out_map);
+
 /* Insert one task (paper, section "Task insertion": one thread inserts tasks
  * with their accesses; the result equals running them in insertion order).
  *   op        SPX_OP_*; handles[nh] in the op's operand order; modes[nh] the
@@ -266,7 +309,10 @@ int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
  *             trading some per-part overhead for more SMs on the task.
  *   prec      SPX_F64, or SPX_TF32 / SPX_BF16 for TRSM, SYRK, GEMM_NT_SUB
  *             whose factor tiles have low-precision copies in a matrix
- *             registered with spx_lowp_register of the matching type.
+ *             registered with spx_lowp_register of the matching type;
+ *             SPX_F64_OZAKI for TRSM, SYRK, GEMM_NT_SUB whose factor tiles
+ *             have split slots in a store registered with
+ *             spx_ozaki_register.
  *   out_task  receives the task id (0, 1, 2, ... in insertion order); may be
  *             NULL.
  * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_BAD_HANDLE, SPX_ERR_STATE. */
@@ -457,6 +503,22 @@ int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n, int lda, 
                                   void* dev_Alo, int ldlo, double* dev_V, int ldv, double* dev_X,
                                   int nrhs, int ldx, int lookahead, int prec,
                                   long long* out_ntasks);
+
+/* spx_cholesky_insert with the trailing updates in FP64 emulated on the
+ * tensor cores (prec SPX_F64_OZAKI, see the prec enum): POTRF and the solves
+ * in FP64; TRSM solves in FP64 and splits its result into the slot of its
+ * tile; SYRK and GEMM_NT_SUB run on the tensor cores from the slots.
+ *   dev_S   the split store: the tile (i, k), i > k, uses slot
+ *           i (i - 1) / 2 + k, i.e. T (T - 1) / 2 slots for T = ceil(n / b);
+ *           S_bytes its size, at least that many times
+ *           spx_ozaki_slot_bytes(b); 256-byte aligned.  The caller owns it
+ *           and keeps it alive until the graph is waited for.
+ *   b       a multiple of 32, 32 <= b <= 512.
+ * Other arguments as spx_cholesky_insert.  Errors: as spx_cholesky_insert,
+ * and SPX_ERR_INVALID_ARG for b or the store. */
+int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_S,
+                              long long S_bytes, double* dev_X, int nrhs, int ldx, int lookahead,
+                              long long* out_ntasks);
 
 /* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
  * already in dev_L (lower triangle, tiles b x b).  Used for the correction

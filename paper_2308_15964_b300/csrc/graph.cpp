@@ -111,7 +111,10 @@ struct spx_graph {
   std::vector<TileDesc> tiles;
   std::vector<int> tile_dtype;
   std::vector<CUtensorMap> maps;      // low-precision matrices
-  struct MapInfo { uintptr_t base; size_t bytes; int ld, elem, dtype, cols_; };
+  // kind 0: low-precision matrix; 1: split store (the map with 128-row
+  // boxes; the next map, kind 2, is the same store with 32-row boxes).  For
+  // a split store ld = the slot pitch b and cols_ = the number of slots.
+  struct MapInfo { uintptr_t base; size_t bytes; int ld, elem, dtype, cols_, kind; };
   std::vector<MapInfo> map_info;
   bool has_tc = false;                // some task runs on the tensor cores
   std::unordered_map<uintptr_t, uint32_t> key_to_handle;
@@ -229,7 +232,15 @@ bool resolve_lowp(spx_graph* g, uint32_t h) {
   const uintptr_t p = (uintptr_t)t.lowp;
   for (size_t m = 0; m < g->map_info.size(); ++m) {
     const auto& mi = g->map_info[m];
-    if (p < mi.base || p >= mi.base + mi.bytes) continue;
+    if (mi.kind == 2 || p < mi.base || p >= mi.base + mi.bytes) continue;
+    if (mi.kind == 1) {  // a split slot: its index is the TMA slot coordinate
+      const size_t slot = (size_t)ozaki_slot_bytes(mi.ld), off = p - mi.base;
+      if (off % slot || t.lowp_ld != mi.ld || t.rows > mi.ld || t.cols > mi.ld) return false;
+      t.lmap = (int)m;
+      t.lr0 = (int)(off / slot);
+      t.lc0 = 0;
+      return true;
+    }
     const size_t off = p - mi.base, row_bytes = (size_t)mi.ld * mi.elem;
     if (off % mi.elem || t.lowp_ld != mi.ld) return false;
     t.lmap = (int)m;
@@ -246,6 +257,7 @@ bool resolve_lowp(spx_graph* g, uint32_t h) {
 // K extent a whole number of 128-byte chunks (or ending the matrix).
 int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
   const int want = prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32;
+  if (prec == SPX_F64_OZAKI && op == SPX_OP_TRSM_INV) return SPX_ERR_INVALID_ARG;
   int ins[2] = {-1, -1};
   switch (op) {
     case SPX_OP_TRSM:
@@ -259,6 +271,8 @@ int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
     if (!resolve_lowp(g, (uint32_t)i)) return SPX_ERR_INVALID_ARG;
     const TileDesc& t = g->tiles[i];
     const auto& mi = g->map_info[t.lmap];
+    if ((mi.kind == 1) != (prec == SPX_F64_OZAKI)) return SPX_ERR_INVALID_ARG;
+    if (mi.kind == 1) continue;  // slot shape checked by resolve_lowp
     if (mi.dtype != want) return SPX_ERR_INVALID_ARG;
     const int chunk = 128 / mi.elem;  // K elements per TMA box
     if (t.lc0 % chunk) return SPX_ERR_INVALID_ARG;
@@ -500,9 +514,35 @@ int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
   const int rc = make_tmap(&map, dev_ptr, rows, cols, ld, dtype);
   if (rc != SPX_OK) return rc;
   g->maps.push_back(map);
-  g->map_info.push_back({(uintptr_t)dev_ptr, (size_t)rows * ld * elem, ld, elem, dtype, cols});
+  g->map_info.push_back({(uintptr_t)dev_ptr, (size_t)rows * ld * elem, ld, elem, dtype, cols, 0});
   g->uploaded = false;
   if (out_map) *out_map = (unsigned)(g->maps.size() - 1);
+  return SPX_OK;
+}
+
+long long spx_ozaki_slot_bytes(int b) { return ozaki_slot_bytes(b); }
+
+int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned* out_map) {
+  if (!g || !dev_ptr || nslots < 1 || !ozaki_slot_bytes(b)) return SPX_ERR_INVALID_ARG;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  for (size_t m = 0; m < g->map_info.size(); ++m)
+    if (g->map_info[m].base == (uintptr_t)dev_ptr) {
+      const auto& mi = g->map_info[m];
+      if (mi.kind != 1 || mi.ld != b || mi.cols_ != nslots) return SPX_ERR_INVALID_ARG;
+      if (out_map) *out_map = (unsigned)m;
+      return SPX_OK;
+    }
+  CUtensorMap ma, mb;
+  int rc = make_tmap_ozaki(&ma, dev_ptr, nslots, b, 128);
+  if (rc == SPX_OK) rc = make_tmap_ozaki(&mb, dev_ptr, nslots, b, 32);
+  if (rc != SPX_OK) return rc;
+  const size_t bytes = (size_t)nslots * (size_t)ozaki_slot_bytes(b);
+  g->maps.push_back(ma);
+  g->maps.push_back(mb);
+  g->map_info.push_back({(uintptr_t)dev_ptr, bytes, b, 2, SPX_DT_BF16, nslots, 1});
+  g->map_info.push_back({(uintptr_t)dev_ptr, bytes, b, 2, SPX_DT_BF16, nslots, 2});
+  g->uploaded = false;
+  if (out_map) *out_map = (unsigned)(g->maps.size() - 2);
   return SPX_OK;
 }
 
@@ -511,7 +551,7 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state != kBuilding) return SPX_ERR_STATE;
   if (op < 0 || op >= SPX_NUM_OPS || nh < 1 || nh > kMaxHandles || !handles || !modes ||
-      priority < 0 || prec < SPX_F64 || prec > SPX_BF16)
+      priority < 0 || prec < SPX_F64 || prec > SPX_F64_OZAKI)
     return SPX_ERR_INVALID_ARG;
   if (g->tasks.size() >= kMaxTasks) return SPX_ERR_INVALID_ARG;
   for (int i = 0; i < nh; ++i) {
@@ -1149,8 +1189,11 @@ int spx_batch_execute(spx_graph_t* gs, int ng, void* stream) {
   for (int i = 0; i < ng; ++i) {
     const spx_graph* m = gs[i];
     for (const auto& mi : m->map_info) {
+      if (mi.kind == 2) continue;  // registered with its kind-1 twin
       const int rows = (int)(mi.bytes / ((size_t)mi.ld * mi.elem));
-      const int rc = spx_lowp_register(B, (void*)mi.base, rows, mi.cols_, mi.ld, mi.dtype, nullptr);
+      const int rc =
+          mi.kind == 1 ? spx_ozaki_register(B, (void*)mi.base, mi.cols_, mi.ld, nullptr)
+                       : spx_lowp_register(B, (void*)mi.base, rows, mi.cols_, mi.ld, mi.dtype, nullptr);
       if (rc != SPX_OK) return rc;
     }
     hmap.assign(m->tiles.size(), 0);

@@ -39,7 +39,7 @@ void configure(bool tc) {
   g_api_ctas_per_sm[tc ? 1 : 0] = occ > 0 ? occ : 1;
   if (tc && occ == 1) {
     // The occupancy calculator answers 1 for any kernel that allocates tensor
-    // memory.  Two CTAs of this one (128 of the 512 TMEM columns each) fit in
+    // memory.  Two CTAs of this one (256 of the 512 TMEM columns each) fit in
     // the SM's registers and shared memory, and the GPU runs them (ncu on the
     // stand-alone tensor-core kernel: two blocks per SM, one wave).  No CTA of
     // the persistent kernel waits for another to start, so a CTA that did not

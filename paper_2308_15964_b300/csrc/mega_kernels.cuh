@@ -43,6 +43,7 @@
 #include "spx_internal.h"
 #include "tile_f64.cuh"
 #include "tile_tc.cuh"
+#include "tile_oz.cuh"
 
 namespace spx {
 namespace {
@@ -232,7 +233,8 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_TRSM:
       if constexpr (kTc) {
         if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
-          if (t.prec == SPX_BF16) op_lowp_copy<true>(T[t.h[1]], u0, u1);
+          if (t.prec == SPX_F64_OZAKI) op_oz_split(T[t.h[1]], u0, u1);
+          else if (t.prec == SPX_BF16) op_lowp_copy<true>(T[t.h[1]], u0, u1);
           else op_lowp_copy<false>(T[t.h[1]], u0, u1);
           return 0;
         }
@@ -241,6 +243,8 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_SYRK:
       if constexpr (kTc) {
+        if (t.prec == SPX_F64_OZAKI)
+          return op_oz_syrk(g, T[t.h[0]], T[t.h[1]], u0, u1, tc.st, tc.buf) ? 0 : -2;
         if (lowp) {
           const bool ok = t.prec == SPX_BF16 ? op_tc_syrk<true>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc)
                                              : op_tc_syrk<false>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc);
@@ -251,6 +255,8 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_GEMM_NT_SUB:
       if constexpr (kTc) {
+        if (t.prec == SPX_F64_OZAKI)
+          return op_oz_gemm(g, T[t.h[0]], T[t.h[1]], T[t.h[2]], u0, u1, tc.st, tc.buf) ? 0 : -2;
         if (lowp) {
           const bool ok =
               t.prec == SPX_BF16

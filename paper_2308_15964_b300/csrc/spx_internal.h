@@ -288,6 +288,23 @@ __host__ __device__ inline uint32_t trtri_level_units(int n, uint32_t phase, uin
   return total;
 }
 
+// SPX_F64_OZAKI SYRK on an n x n tile: the 128-row x 32-column output blocks
+// (i, j) that reach the lower triangle (32 j < 128 (i + 1)), row block by row
+// block.  Returns their count; with unit < count, also the block of that unit.
+__host__ __device__ inline uint32_t oz_syrk_units(int n, uint32_t unit, uint32_t* ij) {
+  const uint32_t nbr = cdiv128(n), nbc = cdiv32(n);
+  uint32_t total = 0;
+  for (uint32_t i = 0; i < nbr; ++i) {
+    const uint32_t cnt = 4 * (i + 1) < nbc ? 4 * (i + 1) : nbc;
+    if (ij && unit >= total && unit < total + cnt) {
+      ij[0] = i;
+      ij[1] = unit - total;
+    }
+    total += cnt;
+  }
+  return total;
+}
+
 // Low-precision tasks (prec = SPX_TF32 / SPX_BF16): SYRK and GEMM_NT_SUB run
 // on the tensor cores in 128 x 128 output units (SYRK: lower block pairs);
 // TRSM runs its FP64 phases and then one more phase that writes the
@@ -331,11 +348,13 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return phase % 2 == 0 ? rb : rb * (nbc - 1 - j);
     }
     case SPX_OP_SYRK: {
+      if (prec == SPX_F64_OZAKI) return oz_syrk_units(t[h[1]].rows, 0xFFFFFFFFu, nullptr);
       const uint32_t nb = prec != SPX_F64 ? cdiv128(t[h[1]].rows)
                                           : (fine ? cdiv32(t[h[1]].rows) : cdiv64(t[h[1]].rows));
       return nb * (nb + 1) / 2;
     }
     case SPX_OP_GEMM_NT_SUB:
+      if (prec == SPX_F64_OZAKI) return cdiv128(t[h[2]].rows) * cdiv32(t[h[2]].cols);
       if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
       return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_NN_ADD:

@@ -32,6 +32,10 @@ constexpr int kTcStages = 3;
 constexpr int kTcChunkBytes = 128;                 // K bytes per stage (one swizzle row)
 constexpr int kTcStageBytes = kTcM * kTcChunkBytes; // 16 KB per operand per stage
 constexpr uint32_t kTcTmemCols = 128;              // FP32 accumulator columns
+// TMEM columns a CTA of the persistent kernel allocates: the 128 x 128
+// accumulator of a low-precision unit, or the eight 32-column accumulators of
+// a split-FP64 unit (tile_oz.cuh).  Two CTAs per SM use all 512.
+constexpr uint32_t kTcCtaCols = 256;
 constexpr uint32_t kTcSpinLimit = 1u << 26;
 
 // Operand stages (1024-byte aligned for the 128-byte swizzle atoms).  In the
@@ -184,7 +188,7 @@ __device__ __forceinline__ void tc_setup(TcState& s) {
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s.tmem_base)),
-                 "r"(kTcTmemCols));
+                 "r"(kTcCtaCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
@@ -206,7 +210,7 @@ __device__ __forceinline__ void tc_teardown(TcState& s) {
   tc_fence_after();
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem_base),
-                 "r"(kTcTmemCols));
+                 "r"(kTcCtaCols));
   }
 }
 

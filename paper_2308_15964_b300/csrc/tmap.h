@@ -12,4 +12,14 @@ namespace spx {
 // 16 bytes, ld * element size a multiple of 16) or SPX_ERR_CUDA.
 int make_tmap(CUtensorMap* out, const void* ptr, int rows, int cols, int ld, int dtype);
 
+// Bytes of one split slot of pitch b (eight BF16 digit planes of b x b, then
+// b int32 row exponents, rounded up to 256); 0 for b not a multiple of 32 in
+// [32, 512].
+long long ozaki_slot_bytes(int b);
+
+// Encode a store of nslots split slots at ptr (256-byte aligned) as a 4-D
+// BF16 tensor (digit column, row, plane, slot) with boxes of 16 digits x
+// box_rows (128 or 32) rows x all 8 planes and the 32-byte swizzle.
+int make_tmap_ozaki(CUtensorMap* out, const void* ptr, int nslots, int b, int box_rows);
+
 }  // namespace spx

@@ -48,22 +48,55 @@ namespace {
 
 // factor: insert the factorization tasks; dev_X: the solve tasks too;
 // dev_V (mixed precision only): the panel solves as TRTRI + TRSM_INV.
+// Tiles of the lower triangle of A whose off-diagonal tiles (i, k) own split
+// slot i (i - 1) / 2 + k of the store at S (SPX_F64_OZAKI).
+int register_ozaki_tiles(spx_graph_t g, double* A, int n, int lda, int b, char* S,
+                         long long S_bytes, Tiles& out) {
+  const long long slot = spx_ozaki_slot_bytes(b);
+  const int T = (n + b - 1) / b;
+  const long long nslots = (long long)T * (T - 1) / 2;
+  if (!slot || !S || ((uintptr_t)S & 255)) return SPX_ERR_INVALID_ARG;
+  if (nslots > 0) {
+    if (S_bytes < nslots * slot || nslots > 0x7FFFFFFF) return SPX_ERR_INVALID_ARG;
+    const int rc = spx_ozaki_register(g, S, (int)nslots, b, nullptr);
+    if (rc != SPX_OK) return rc;
+  }
+  out.T = T;
+  out.b = b;
+  out.h.assign((size_t)T * T, 0xFFFFFFFFu);
+  for (int i = 0; i < T; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const int r = n - i * b < b ? n - i * b : b;
+      const int c = n - j * b < b ? n - j * b : b;
+      char* lo = i > j ? S + ((long long)i * (i - 1) / 2 + j) * slot : nullptr;
+      const int rc = spx_tile_register(g, A + (size_t)i * b * lda + (size_t)j * b, r, c, lda,
+                                       SPX_DT_F64, lo, lo ? b : 0, &out.at(i, j));
+      if (rc != SPX_OK) return rc;
+    }
+  return SPX_OK;
+}
+
 int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo, int ldlo,
                     bool factor, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
-                    long long* out_ntasks, double* dev_V = nullptr, int ldv = 0) {
+                    long long* out_ntasks, double* dev_V = nullptr, int ldv = 0,
+                    long long S_bytes = 0) {
   if (!g || !dev_A || n < 1 || b < 1 || lda < n || (dev_X && (nrhs < 1 || ldx < nrhs)))
     return SPX_ERR_INVALID_ARG;
-  if (prec != SPX_F64 && (!dev_Alo || ldlo < n)) return SPX_ERR_INVALID_ARG;
-  if (dev_V && (prec == SPX_F64 || ldv < (b < n ? b : n))) return SPX_ERR_INVALID_ARG;
+  const bool oz = prec == SPX_F64_OZAKI;
+  if (prec != SPX_F64 && !oz && (!dev_Alo || ldlo < n)) return SPX_ERR_INVALID_ARG;
+  if (dev_V && (prec == SPX_F64 || oz || ldv < (b < n ? b : n))) return SPX_ERR_INVALID_ARG;
   const int elem = prec == SPX_BF16 ? 2 : 4;
   int rc = SPX_OK;
-  if (prec != SPX_F64)
+  if (prec != SPX_F64 && !oz)
     rc = spx_lowp_register(g, dev_Alo, n, n, ldlo, prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32,
                            nullptr);
   if (rc != SPX_OK) return rc;
   Tiles A;
-  rc = register_tiles(g, dev_A, n, n, lda, b, true, A, prec != SPX_F64 ? (char*)dev_Alo : nullptr,
-                      ldlo, elem);
+  if (oz)
+    rc = register_ozaki_tiles(g, dev_A, n, lda, b, (char*)dev_Alo, S_bytes, A);
+  else
+    rc = register_tiles(g, dev_A, n, n, lda, b, true, A,
+                        prec != SPX_F64 ? (char*)dev_Alo : nullptr, ldlo, elem);
   if (rc != SPX_OK) return rc;
   const int T = A.T;
   const int R = SPX_READ, W = SPX_WRITE;
@@ -158,6 +191,14 @@ extern "C" int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n
   if ((prec != SPX_TF32 && prec != SPX_BF16) || !dev_V) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_A, n, lda, b, dev_Alo, ldlo, true, dev_X, nrhs, ldx, lookahead,
                          prec, out_ntasks, dev_V, ldv);
+}
+
+extern "C" int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b,
+                                         void* dev_S, long long S_bytes, double* dev_X, int nrhs,
+                                         int ldx, int lookahead, long long* out_ntasks) {
+  if (!spx_ozaki_slot_bytes(b)) return SPX_ERR_INVALID_ARG;
+  return insert_cholesky(g, dev_A, n, lda, b, dev_S, 0, true, dev_X, nrhs, ldx, lookahead,
+                         SPX_F64_OZAKI, out_ntasks, nullptr, 0, S_bytes);
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,

@@ -21,7 +21,7 @@ READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
             "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV",
             "NBODY_SELF", "NBODY_PAIR")
-F64, TF32, BF16 = 0, 1, 2
+F64, TF32, BF16, F64_OZAKI = 0, 1, 2, 3
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
 
@@ -80,6 +80,9 @@ def _load():
         "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
+        "spx_ozaki_slot_bytes": (LL, [I]),
+        "spx_ozaki_register": (I, [P, P, I, I, P]),
+        "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
         "spx_cholesky_insert_mixed_inv": (I, [P, P, I, I, I, P, I, P, I, P, I, I, I, I, P]),
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),
@@ -175,6 +178,13 @@ class Graph:
         """Register a 2-D row-major view (stride(1) == 1) of a CUDA tensor."""
         assert t.dim() == 2 and t.stride(1) == 1
         return self.register(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), dtype)
+
+    def register_ozaki(self, ptr: int, nslots: int, b: int) -> int:
+        """spx_ozaki_register: a store of nslots split slots of pitch b."""
+        out = ctypes.c_uint()
+        _check(lib.spx_ozaki_register(self._h, ctypes.c_void_p(ptr), nslots, b, ctypes.byref(out)),
+               "spx_ozaki_register")
+        return out.value
 
     def insert(self, op: int, handles, modes, priority=0, prec=F64) -> int:
         h = np.ascontiguousarray(handles, dtype=np.uint32)

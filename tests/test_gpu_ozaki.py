@@ -1,0 +1,226 @@
+"""FP64 trailing updates emulated on the tensor cores (prec SPX_F64_OZAKI)
+against the oracle.
+
+* op level, bit for bit against the oracle's split product (oracle/ozaki.py):
+  a TRSM with an identity diagonal tile leaves its tile unchanged and splits
+  it, so its digit planes and row exponents must equal the oracle's split;
+  GEMM_NT_SUB and SYRK must then equal the oracle's gemm_nt_sub / syrk_lower
+  exactly: rows of spread magnitudes, zero rows, ragged shapes and K, and the
+  worst case of the digit sums (P_7 just below 2^24), which the tensor cores
+  must accumulate exactly;
+* the whole factorization + solve against the FP64 oracle with the FP64
+  path's tolerances (entry error <= 1e-12, backward errors <= 1e-14); the
+  integer and diagonal pins bit for bit; non-SPD info; bit-identical across
+  runs and executors.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import ozaki as Z
+from paper_2308_15964_b300 import inputs
+from tests._gpu import need_cuda, spx_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    need_cuda()
+    return spx_mod()
+
+
+def r32(x):
+    return (x + 31) // 32 * 32
+
+
+def slot_view(store, slot_bytes, i, b):
+    """(planes [8, b, b] float32, exponents [b] int32) of slot i."""
+    raw = store[i * slot_bytes:(i + 1) * slot_bytes]
+    planes = raw[:16 * b * b].view(torch.bfloat16).float().reshape(8, b, b).cpu().numpy()
+    exps = raw[16 * b * b:16 * b * b + 4 * b].view(torch.int32).cpu().numpy()
+    return planes, exps
+
+
+def split_op_graph(S, mats, b):
+    """Graph: TRSM(I, M) with prec F64_OZAKI for every matrix M in mats (each
+    gets slot i of a fresh store).  Returns graph, store, slot bytes, handles."""
+    slot = S.lib.spx_ozaki_slot_bytes(b)
+    store = torch.zeros(len(mats) * slot, dtype=torch.uint8, device="cuda")
+    g = S.Graph()
+    g.register_ozaki(store.data_ptr(), len(mats), b)
+    hs = []
+    for i, M in enumerate(mats):
+        K = M.shape[1]
+        eye = torch.eye(K, dtype=torch.float64, device="cuda")
+        g._keep.append(eye)
+        hI = g.register_tensor(eye)
+        hM = g.register(M.data_ptr(), M.shape[0], K, M.stride(0), S.DT_F64,
+                        store.data_ptr() + i * slot, b)
+        g.insert(S.OP_TRSM, [hI, hM], [S.READ, S.WRITE], prec=S.F64_OZAKI)
+        hs.append(hM)
+    g._keep.append(store)
+    return g, store, slot, hs
+
+
+def spread_rows(rng, m, K, lo=-30, hi=30):
+    A = rng.standard_normal((m, K)) * np.exp2(rng.integers(lo, hi, size=(m, 1)))
+    if m > 3:
+        A[2] = 0.0
+        A[3] *= np.exp2(rng.integers(-45, 0, size=K))
+    return A
+
+
+def worst_case(m, K):
+    X = 63 * 128 ** 7 + 64 * sum(128 ** j for j in range(7))
+    return np.full((m, K), -X / 2.0 ** 55)
+
+
+def check_split(store, slot, i, b, M):
+    e, D = Z.split(M)
+    planes, exps = slot_view(store, slot, i, b)
+    m, K = M.shape
+    assert np.array_equal(exps[:m], e.astype(np.int32))
+    assert np.array_equal(planes[:, :m, :K], D.astype(np.float32))
+    assert not planes[:, :m, K:].any()  # the K padding is zero
+
+
+@pytest.mark.parametrize("m,n,K", [(128, 32, 512), (200, 70, 512), (77, 33, 64), (512, 512, 512),
+                                   (256, 96, 40), (33, 130, 200)])
+def test_gemm_op_bit_exact(S, m, n, K):
+    rng = np.random.default_rng(m * 1000 + n + K)
+    A = spread_rows(rng, m, K)
+    B = spread_rows(rng, n, K)
+    C = rng.standard_normal((m, n))
+    b = r32(max(m, n, K))
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+    g, store, slot, (hA, hB) = split_op_graph(S, [Ad, Bd], b)
+    hC = g.register_tensor(Cd)
+    g.insert(S.OP_GEMM_NT_SUB, [hA, hB, hC], [S.READ, S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(Ad.cpu().numpy(), A) and np.array_equal(Bd.cpu().numpy(), B)
+    check_split(store, slot, 0, b, A)
+    check_split(store, slot, 1, b, B)
+    assert np.array_equal(Cd.cpu().numpy(), Z.gemm_nt_sub(C, A, B))
+    g.close()
+
+
+@pytest.mark.parametrize("m,K", [(512, 512), (300, 96), (40, 512)])
+def test_syrk_op_bit_exact(S, m, K):
+    rng = np.random.default_rng(m + K)
+    L = spread_rows(rng, m, K, -8, 8)
+    C = rng.standard_normal((m, m))
+    b = r32(max(m, K))
+    Ld, Cd = (torch.from_numpy(x.copy()).cuda() for x in (L, C))
+    g, store, slot, (hL,) = split_op_graph(S, [Ld], b)
+    hC = g.register_tensor(Cd)
+    g.insert(S.OP_SYRK, [hL, hC], [S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    check_split(store, slot, 0, b, L)
+    assert np.array_equal(Cd.cpu().numpy(), Z.syrk_lower(C, L))
+    g.close()
+
+
+def test_worst_case_accumulation_exact(S):
+    """Every digit -64 (the top one -63), K = 512: the digit sums reach
+    P_7 = 16 711 680, within 2^16 of 2^24; the tensor cores must add them
+    exactly for the result to match."""
+    A = worst_case(128, 512)
+    B = worst_case(64, 512)
+    B[5::7] *= -1.0
+    C = np.zeros((128, 64))
+    b = 512
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+    g, store, slot, (hA, hB) = split_op_graph(S, [Ad, Bd], b)
+    hC = g.register_tensor(Cd)
+    g.insert(S.OP_GEMM_NT_SUB, [hA, hB, hC], [S.READ, S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    want = Z.gemm_nt_sub(C, A, B)
+    assert np.array_equal(Cd.cpu().numpy(), want)
+    g.close()
+
+
+def run_ozaki(S, A_np, b, X_np=None, lookahead=True, **cfg):
+    from paper_2308_15964_b300 import cholesky
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
+    X = torch.from_numpy(np.ascontiguousarray(X_np)).cuda() if X_np is not None else None
+    g = S.Graph(**cfg)
+    cholesky.cholesky_ozaki_graph(g, A, b, X, lookahead=lookahead)
+    rc, info = g.run()
+    torch.cuda.synchronize()
+    return rc, info, A.cpu().numpy(), (X.cpu().numpy() if X is not None else None), g
+
+
+def rel_entry_err(L, Lref):
+    L, Lref = np.tril(L), np.tril(Lref)
+    return np.abs(L - Lref).max() / np.abs(Lref).max()
+
+
+@pytest.mark.parametrize("n,b,nrhs", [(512, 64, 1), (1000, 128, 2), (33, 32, 1), (700, 96, 3),
+                                      (2048, 512, 1), (1024, 256, 2)])
+def test_factor_solve_vs_oracle(S, n, b, nrhs):
+    A = inputs.spd_matrix(n, 1.0, seed=1).numpy()
+    B = inputs.rhs(n, nrhs, seed=1).numpy()
+    rc, info, L, X, g = run_ozaki(S, A, b, B)
+    assert rc == 0 and info == 0
+    Lo, Xo = A.copy(), B.copy()
+    assert O.tiled_cholesky(Lo, b, Xo) == 0
+    assert rel_entry_err(L, Lo) <= 1e-12
+    assert O.solve_backward_error(A, X, B).max() <= 1e-14
+    if n <= 1024:
+        assert O.factor_backward_error(A, L) <= 1e-14
+    assert np.array_equal(np.triu(L, 1), np.triu(A, 1))
+    g.close()
+
+
+@pytest.mark.parametrize("n,b", [(192, 64), (200, 64), (130, 32)])
+def test_integer_factor_bit_exact(S, n, b):
+    rng = np.random.default_rng(n)
+    L0 = np.tril(rng.integers(-1, 2, size=(n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L0 @ L0.T
+    x0 = rng.integers(-3, 4, size=(n, 2)).astype(np.float64)
+    rc, info, L, X, g = run_ozaki(S, A, b, A @ x0)
+    assert rc == 0
+    assert np.array_equal(np.tril(L), L0)
+    assert np.array_equal(X, x0)
+    g.close()
+
+
+def test_diagonal_bit_exact(S):
+    n = 320
+    e = (np.arange(n) % 9) - 4
+    rc, info, L, _, g = run_ozaki(S, np.diag(4.0 ** e), 64)
+    assert rc == 0 and info == 0
+    assert np.array_equal(np.tril(L), np.diag(2.0 ** e))
+    g.close()
+
+
+@pytest.mark.parametrize("col", [0, 100, 255])
+def test_not_spd_info(S, col):
+    n = 256
+    A = inputs.spd_matrix(n, 1.0, seed=3).numpy()
+    A[col, col] = -1.0
+    Lo = A.copy()
+    info_o = O.tiled_cholesky(Lo, 64)
+    rc, info, _, _, g = run_ozaki(S, A, 64)
+    assert info == info_o and info > 0
+    g.close()
+
+
+def test_determinism_and_executors(S):
+    n, b = 1536, 256
+    A = inputs.spd_matrix(n, 0.1, seed=2).numpy()
+    B = inputs.rhs(n, 2, seed=2).numpy()
+    outs = []
+    for cfg in ({}, {}, {"executor": S.EXEC_PER_TASK}, {"executor": S.EXEC_STREAMS},
+                {"num_ctas": 37}):
+        rc, info, L, X, g = run_ozaki(S, A, b, B, **cfg)
+        assert rc == 0 and info == 0
+        outs.append((L, X))
+        g.close()
+    for L, X in outs[1:]:
+        assert np.array_equal(L, outs[0][0]) and np.array_equal(X, outs[0][1])
