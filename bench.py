@@ -87,6 +87,9 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--tile", type=int, default=512)
     p.add_argument("--sigma", type=float, default=0.1)
+    p.add_argument("--arith", default="ozaki", choices=["ozaki", "f64"],
+                   help="cholesky: FP64 trailing updates emulated on the tensor cores by "
+                        "splitting (ozaki) or on the FP64 SIMT pipe (f64)")
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
     p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
                                                       "overhead", "axpy", "nbody"],
@@ -207,6 +210,39 @@ def run_reference(args):
     }))
 
 
+def ozaki_roofline(n, b, kernel_ms, fp64_peak, traffic):
+    """Roofline of the persistent kernel on the split path.  Tensor work: each
+    128 x 32 output unit with K digits issues MMAs over N = 32 (8 - p) for
+    the eight planes p, i.e. 36 digit-pair products of 2 * 128 * 32 * K flops;
+    summed over the GEMM tasks' full tiles and the SYRK tasks' lower units.
+    FP64 work: the TRSM (b^3 per tile) and POTRF (b^3 / 3) flops on the SIMT
+    pipe.  The bound is the tensor-core rate; the FP64 share is given beside."""
+    T = -(-n // b)
+    gemm_units = sum(1 for k in range(T) for j in range(k + 1, T) for i in range(j + 1, T))
+    syrk_units = 0
+    nbr, nbc = -(-b // 128), -(-b // 32)
+    for i in range(nbr):
+        syrk_units += min(4 * (i + 1), nbc)
+    unit_flops = 36 * 2 * 128 * 32 * b
+    tensor_flops = (gemm_units * nbr * nbc + (T * (T - 1) // 2) * syrk_units) * unit_flops
+    fp64_flops = T * (T - 1) // 2 * b ** 3 + T * b ** 3 / 3
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    ach = tensor_flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+            "traffic": traffic, "kernel": "persistent_kernel<tensor cores> (split-FP64 SYRK/GEMM)",
+            "kernel_ms": kernel_ms,
+            "peak_note": "measured cuBLAS bf16 burst rate (MEASURED_PEAKS.json)"
+                         if "bf16_tflops" in peaks else "fallback bf16 peak",
+            "tensor_tflop_per_launch": tensor_flops / 1e12,
+            "fp64_simt": {"flops_per_launch": fp64_flops,
+                          "achieved_tflops": fp64_flops / (kernel_ms * 1e-3) / 1e12,
+                          "peak_tflops": fp64_peak,
+                          "frac": fp64_flops / (kernel_ms * 1e-3) / 1e12 / fp64_peak},
+            "note": "FP64-equivalent rate n^3/3 over the kernel time: "
+                    f"{n ** 3 / 3 / (kernel_ms * 1e-3) / 1e12:.2f} TFLOP/s"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -248,12 +284,20 @@ def main():
     stream = torch.cuda.current_stream()
     g = spx.Graph()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    oz = args.arith == "ozaki"
+    store = cholesky.ozaki_store(n, b) if oz else None
 
-    def step(graph, record=None):
+    def build_graph(graph, ozaki=oz):
+        if ozaki:
+            cholesky.cholesky_ozaki_graph(graph, A, b, S=store)
+        else:
+            cholesky.cholesky_graph(graph, A, b)
+
+    def step(graph, record=None, ozaki=oz):
         A.copy_(A0)
         ev[0].record()
         graph.clear()
-        cholesky.cholesky_graph(graph, A, b)
+        build_graph(graph, ozaki)
         graph.execute(stream)
         rc, info = graph.wait()
         ev[1].record()
@@ -287,9 +331,15 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("f64 (SYRK/GEMM products emulated by Ozaki splitting: bf16 digit planes on tcgen05, "
+                  "exact fp32 digit sums, one fp64 rounding; POTRF/TRSM fp64)") if oz else "f64",
+        "data": "synthetic",
         "config": {"workload": f"tiled Cholesky FP64 n={n} tile={b} ({ntasks} tasks, {nedges} edges); "
-                               "step = insert + device DAG derivation + persistent execution",
+                               "step = insert + device DAG derivation + persistent execution; "
+                               + ("trailing updates by splitting on the tensor cores" if oz
+                                  else "all tile ops on the FP64 SIMT pipe"),
+                   "arith": args.arith,
                    "n": n, "tile": b, "tasks": ntasks, "edges": nedges, "sigma": args.sigma,
                    "l2": "inputs larger than L2 (matrix 8n^2 bytes)",
                    "parallelism": f"replicas x{world}"},
@@ -310,18 +360,55 @@ def main():
     max_mhz = clocks.get("sm_max_mhz") or 2032.0
     peak = FP64_DFMA_PER_CLK_SM * 2 * sms * max_mhz * 1e6 / 1e12
     run_mean = statistics.mean(run_ms)
-    achieved = flops / (run_mean * 1e-3) / 1e12
     probe_rate, _ = spx.probe(0, 4000)
     traffic = measured_traffic() if (n, b) == (16384, 512) else None
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": traffic,
-                       "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                                       "from the committed ncu summary of this workload; null when "
-                                       "the kernel sources differ from the captured ones",
-                       "kernel": "persistent_kernel (FP64 DFMA tile ops)",
-                       "kernel_ms": run_mean,
-                       "peak_note": "2 DFMA/clk/SM x 148 SMs x max SM clock (derived); "
-                                    f"live DFMA probe {probe_rate / 1e12:.3f} TFLOP/s"}
+    traffic_note = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the committed "
+                    "ncu summary of this workload; null when the kernel sources differ from the "
+                    "captured ones")
+    if oz:
+        out["roofline"] = ozaki_roofline(n, b, run_mean, peak, traffic)
+        out["roofline"]["traffic_note"] = traffic_note
+    else:
+        achieved = flops / (run_mean * 1e-3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                           "kernel": "persistent_kernel (FP64 DFMA tile ops)",
+                           "kernel_ms": run_mean,
+                           "peak_note": "2 DFMA/clk/SM x 148 SMs x max SM clock (derived); "
+                                        f"live DFMA probe {probe_rate / 1e12:.3f} TFLOP/s"}
+    out["sched"]["op_share"] = {k: round(v / max(1, stats["busy_cycles"]), 3)
+                                for k, v in stats["op_cycles"].items()}
+
+    if oz and rank == 0 and not args.no_extras:
+        # the same factorization with every tile op on the FP64 SIMT pipe, and
+        # the two factors compared (the splitting's accuracy at this size)
+        L_oz = torch.tril(A)
+        gf = spx.Graph()
+        step(gf, ozaki=False)
+        frec = []
+        for _ in range(3):
+            step(gf, frec, ozaki=False)
+        gf.close()
+        L_f = torch.tril(A)
+        fms = [r[0] for r in frec]
+        frun = statistics.mean(r[1] for r in frec)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        v = torch.rand(n, 4, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+        fr = lambda L: float(((A0 @ v - L @ (L.T @ v)).norm() / (A0.norm() * v.norm())).item())
+        out["f64_dfma"] = {"value": flops / (statistics.mean(fms) * 1e-3) / 1e9, "unit": "GFLOP/s",
+                           "ms_per_step": statistics.mean(fms),
+                           "p50_ms": float(np.percentile(fms, 50)),
+                           "p99_ms": float(np.percentile(fms, 99)), "steps": len(fms),
+                           "roofline": {"bound": "alu", "achieved": flops / (frun * 1e-3) / 1e12,
+                                        "peak": peak, "unit": "TFLOP/s",
+                                        "frac": flops / (frun * 1e-3) / 1e12 / peak,
+                                        "kernel": "persistent_kernel (FP64 DFMA tile ops)"}}
+        out["accuracy"] = {"max_rel_entry_diff_vs_dfma": float(((L_oz - L_f).abs().max()
+                                                               / L_f.abs().max()).item()),
+                           "freivalds_ozaki": fr(L_oz), "freivalds_dfma": fr(L_f),
+                           "note": "||A v - L L^T v|| / (||A||_F ||v||) with 4 random v; the "
+                                   "factors of the two arithmetics compared entry by entry"}
+        del L_oz, L_f
 
     if rank == 0 and not args.no_extras:
         # one-launch-per-task baseline, same tile code, same stream
@@ -353,7 +440,7 @@ def main():
         # (inserted once; re-runs reset and replay)
         gg = spx.Graph(executor=spx.EXEC_PER_TASK, cuda_graph=True)
         A.copy_(A0)
-        cholesky.cholesky_graph(gg, A, b)
+        build_graph(gg)
         assert gg.run()[0] == spx.OK
         grec = []
         for i in range(COMPARATOR_STEPS + 1):
@@ -394,7 +481,7 @@ def main():
             ev[0].record()
             A.copy_(Ah, non_blocking=True)
             g.clear()
-            cholesky.cholesky_graph(g, A, b)
+            build_graph(g)
             g.execute(stream)
             rc, _ = g.wait()
             assert rc == spx.OK

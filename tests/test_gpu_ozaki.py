@@ -224,3 +224,41 @@ def test_determinism_and_executors(S):
         g.close()
     for L, X in outs[1:]:
         assert np.array_equal(L, outs[0][0]) and np.array_equal(X, outs[0][1])
+
+
+@pytest.mark.slow
+def test_scale_16384_sampled(S):
+    """The benchmark's configuration (n = 16384, tile 512, split trailing
+    updates): the oracle's Freivalds probe of the factor and the oracle's
+    backward error of the solve, as for the FP64 path."""
+    from paper_2308_15964_b300 import cholesky
+    n, b = 16384, 512
+    A = inputs.spd_matrix(n, 0.1, seed=2, device="cuda")
+    A_host = A.cpu().numpy()
+    B = inputs.rhs(n, 1, seed=2, device="cuda")
+    B_host = B.cpu().numpy()
+    g = S.Graph()
+    cholesky.cholesky_ozaki_graph(g, A, b, B)
+    rc, info = g.run()
+    assert rc == 0 and info == 0
+    L = A.cpu().numpy()
+    X = B.cpu().numpy()
+    for s in range(2):
+        assert O.freivalds(A_host, L, inputs.gaussian(n, 100 + s)) <= 1e-14
+    assert O.solve_backward_error(A_host, X, B_host).max() <= 1e-14
+    g.close()
+
+
+@pytest.mark.parametrize("n,b", [(1000, 128), (2048, 512)])
+def test_bottom_level_priorities_bit_identical(S, n, b):
+    """Critical-path priorities change the order and part sizes only: the
+    split path's factor and solve are bit-identical to the look-ahead
+    marks'."""
+    A = inputs.spd_matrix(n, 1.0, seed=n).numpy()
+    X = inputs.rhs(n, 2, seed=n).numpy()
+    rc1, _, L1, X1, g1 = run_ozaki(S, A, b, X)
+    rc2, _, L2, X2, g2 = run_ozaki(S, A, b, X, priorities=1)
+    assert rc1 == rc2 == 0
+    assert np.array_equal(L1, L2) and np.array_equal(X1, X2)
+    g1.close()
+    g2.close()
