@@ -509,16 +509,27 @@ int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n, int lda, 
  * in FP64; TRSM solves in FP64 and splits its result into the slot of its
  * tile; SYRK and GEMM_NT_SUB run on the tensor cores from the slots.
  *   dev_S   the split store: the tile (i, k), i > k, uses slot
- *           i (i - 1) / 2 + k, i.e. T (T - 1) / 2 slots for T = ceil(n / b);
- *           S_bytes its size, at least that many times
- *           spx_ozaki_slot_bytes(b); 256-byte aligned.  The caller owns it
- *           and keeps it alive until the graph is waited for.
+ *           i (i - 1) / 2 + k, i.e. T (T - 1) / 2 slots for T = ceil(n / b)
+ *           (T more with dev_V, see below); S_bytes its size, at least that
+ *           many times spx_ozaki_slot_bytes(b); 256-byte aligned.  The
+ *           caller owns it and keeps it alive until the graph is waited for.
+ *   dev_V   NULL: every panel tile by FP64 substitution.  Else inverse
+ *           panels: per k, the critical panel tile (k+1, k) by FP64
+ *           substitution; TRTRI writes V_k = L_kk^{-1} (FP64, block
+ *           recursive) into the square block at row k*b of dev_V (n x b,
+ *           ldv >= b) and splits it into slot T (T - 1) / 2 + k; TRSM_INV
+ *           with the split prec then forms A_ik V_k^T for i >= k+2 as a split
+ *           product (A_ik split, product stored, result split): the panel
+ *           solves' b^3 flops per tile leave the FP64 pipe.  Substitution and
+ *           the inverse agree to rounding for well-conditioned diagonal tiles
+ *           (the error of the inverse grows with kappa(L_kk)); this is a
+ *           reading of this library, not of the paper.
  *   b       a multiple of 32, 32 <= b <= 512.
  * Other arguments as spx_cholesky_insert.  Errors: as spx_cholesky_insert,
- * and SPX_ERR_INVALID_ARG for b or the store. */
+ * and SPX_ERR_INVALID_ARG for b, the store, or ldv < b. */
 int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_S,
-                              long long S_bytes, double* dev_X, int nrhs, int ldx, int lookahead,
-                              long long* out_ntasks);
+                              long long S_bytes, double* dev_V, int ldv, double* dev_X, int nrhs,
+                              int ldx, int lookahead, long long* out_ntasks);
 
 /* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
  * already in dev_L (lower triangle, tiles b x b).  Used for the correction

@@ -35,33 +35,39 @@ def cholesky_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, prec
     return nt.value
 
 
-def ozaki_store(n: int, b: int, device="cuda"):
+def ozaki_store(n: int, b: int, device="cuda", inverse_panels: bool = False):
     """The split store of spx_cholesky_insert_ozaki for an n x n matrix in
-    b x b tiles: T (T - 1) / 2 slots of spx_ozaki_slot_bytes(b) bytes (torch
-    allocations are 256-byte aligned)."""
+    b x b tiles: T (T - 1) / 2 slots (T more with inverse panels) of
+    spx_ozaki_slot_bytes(b) bytes (torch allocations are 256-byte aligned)."""
     import torch
     T = -(-n // b)
     slot = spx.lib.spx_ozaki_slot_bytes(b)
     if slot <= 0:
         raise ValueError(f"tile {b}: the split path takes b a multiple of 32 in [32, 512]")
-    return torch.empty(max(1, T * (T - 1) // 2) * slot, dtype=torch.uint8, device=device)
+    nslots = T * (T - 1) // 2 + (T if inverse_panels else 0)
+    return torch.empty(max(1, nslots) * slot, dtype=torch.uint8, device=device)
 
 
-def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, S=None):
+def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, S=None,
+                         V=None):
     """spx_cholesky_insert_ozaki: A = L L^T with the trailing updates in FP64
     emulated on the tensor cores (digit planes in the split store S, made by
-    ozaki_store when None).  Returns the number of tasks inserted."""
+    ozaki_store when None).  V (n x b FP64, or None): inverse panels, V
+    receiving the inverses of the diagonal factor tiles.  Returns the number
+    of tasks inserted."""
     n = A.shape[0]
     assert A.stride(1) == 1 and (X is None or X.stride(1) == 1)
+    assert V is None or (V.stride(1) == 1 and V.shape[0] >= n)
     if S is None:
-        S = ozaki_store(n, b, A.device)
+        S = ozaki_store(n, b, A.device, inverse_panels=V is not None)
     nt = ctypes.c_longlong()
     spx._check(spx.lib.spx_cholesky_insert_ozaki(
         g._h, _ptr(A), n, A.stride(0), b, _ptr(S), S.numel() * S.element_size(),
+        _ptr(V) if V is not None else None, V.stride(0) if V is not None else 0,
         _ptr(X) if X is not None else None, X.shape[1] if X is not None else 0,
         X.stride(0) if X is not None else 0, 1 if lookahead else 0, ctypes.byref(nt)),
         "spx_cholesky_insert_ozaki")
-    g._keep.extend([A, S] + ([X] if X is not None else []))
+    g._keep.extend([A, S] + ([X] if X is not None else []) + ([V] if V is not None else []))
     return nt.value
 
 

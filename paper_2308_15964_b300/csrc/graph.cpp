@@ -257,11 +257,17 @@ bool resolve_lowp(spx_graph* g, uint32_t h) {
 // K extent a whole number of 128-byte chunks (or ending the matrix).
 int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
   const int want = prec == SPX_BF16 ? SPX_DT_BF16 : SPX_DT_F32;
-  if (prec == SPX_F64_OZAKI && op == SPX_OP_TRSM_INV) return SPX_ERR_INVALID_ARG;
   int ins[2] = {-1, -1};
   switch (op) {
-    case SPX_OP_TRSM:
-    case SPX_OP_TRSM_INV: ins[0] = (int)h[1]; break;
+    case SPX_OP_TRSM: ins[0] = (int)h[1]; break;
+    case SPX_OP_TRSM_INV:
+      ins[0] = (int)h[1];
+      if (prec == SPX_F64_OZAKI) ins[1] = (int)h[0];  // V's digits feed the product
+      break;
+    case SPX_OP_TRTRI:  // split prec only: V is split after the inversion
+      if (prec != SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
+      ins[0] = (int)h[1];
+      break;
     case SPX_OP_SYRK: ins[0] = (int)h[0]; break;
     case SPX_OP_GEMM_NT_SUB: ins[0] = (int)h[0]; ins[1] = (int)h[1]; break;
     default: return SPX_ERR_INVALID_ARG;

@@ -317,6 +317,13 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_TRSM_INV:
       if constexpr (kTc) {
+        if (t.prec == SPX_F64_OZAKI) {
+          if (phase != 1) {  // split the input (phase 0) or the result (phase 2)
+            op_oz_split(T[t.h[1]], u0, u1);
+            return 0;
+          }
+          return op_oz_trsm_inv(g, T[t.h[0]], T[t.h[1]], u0, u1, tc.st, tc.buf) ? 0 : -2;
+        }
         const bool ok = t.prec == SPX_BF16
                             ? op_tc_trsm_inv<true>(T[t.h[0]], T[t.h[1]], u0, u1, tc)
                             : op_tc_trsm_inv<false>(T[t.h[0]], T[t.h[1]], u0, u1, tc);
@@ -324,6 +331,13 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       }
       return -1;
     case SPX_OP_TRTRI:
+      if (t.prec == SPX_F64_OZAKI && phase == trtri_phases(T[t.h[0]].rows)) {
+        if constexpr (kTc) {
+          op_oz_split(T[t.h[1]], u0, u1);
+          return 0;
+        }
+        return -1;
+      }
       op_trtri_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
     case SPX_OP_NOP:

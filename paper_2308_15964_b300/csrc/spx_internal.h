@@ -316,7 +316,10 @@ __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* 
     case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
-    case SPX_OP_TRTRI: return trtri_phases(t[h[0]].rows);
+    case SPX_OP_TRTRI:  // split prec: one more phase splits V into its slot
+      return trtri_phases(t[h[0]].rows) + (prec == SPX_F64_OZAKI ? 1u : 0u);
+    case SPX_OP_TRSM_INV:  // split prec: split A, product into A, split the result
+      return prec == SPX_F64_OZAKI ? 3u : 1u;
     default: return 1;
   }
 }
@@ -370,6 +373,8 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     case SPX_OP_TRMM:
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_INV:  // 128-row blocks of A_ik (tensor cores)
+      if (prec == SPX_F64_OZAKI)
+        return phase == 1 ? cdiv128(t[h[1]].rows) * cdiv32(t[h[1]].cols) : cdiv64(t[h[1]].rows);
       return cdiv128(t[h[1]].rows);
     case SPX_OP_NBODY_SELF:  // 64-particle target blocks
       return cdiv64(t[h[0]].rows);
@@ -377,7 +382,7 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return cdiv64(t[h[0]].rows) + cdiv64(t[h[1]].rows);
     case SPX_OP_TRTRI: {  // diagonal inverses, level products, zeroing (64-block units)
       const int n = t[h[0]].rows;
-      if (phase == 0 || phase + 1 == trtri_phases(n)) return cdiv64(n);
+      if (phase == 0 || phase + 1 >= trtri_phases(n)) return cdiv64(n);  // (split: 64-row units)
       return trtri_level_units(n, phase);
     }
     default: return 1;

@@ -200,10 +200,12 @@ __device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32
 // B rows from slot b_slot rows b_r0.. (bmap, 32-row boxes); K digits.
 // a_exp / b_exp: the exponents of those rows.  Entries with column >
 // row + diag are left alone (SYRK's diagonal blocks).  All threads; false on
-// a barrier timeout.
+// a barrier timeout.  store: C = A B^T instead (v rounded once, no
+// subtraction).
 __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_slot, int a_r0,
                         const CUtensorMap* bmap, int b_slot, int b_r0, int K, const int* a_exp,
-                        const int* b_exp, double* C, int ldc, int m, int n, int diag) {
+                        const int* b_exp, double* C, int ldc, int m, int n, int diag,
+                        bool store = false) {
   const int nsteps = (K + 15) / 16;
   const int tid = threadIdx.x;
   const uint32_t tmem = s.tmem_base;
@@ -212,7 +214,7 @@ __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_s
   // before the TMA writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  if (tid >= 32) {
+  if (tid >= 32 && !store) {
     // pull the FP64 output block into L2 while the MMAs run (32 columns =
     // two 128-byte lines per row)
     for (int e = tid - 32; e < 2 * m; e += kThreads - 32) {
@@ -305,7 +307,7 @@ __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_s
           else
             v = scalbn(__fma_rn(__ll2double_rn(fh[j]), 268435456.0, __ll2double_rn(fl[j])), x);
           double* cp = C + (size_t)r * ldc + c;
-          *cp = __dsub_rn(*cp, v);
+          *cp = store ? v : __dsub_rn(*cp, v);
         }
       }
     }
@@ -352,6 +354,26 @@ __device__ __noinline__ bool op_oz_syrk(const DevGraph& g, const TileDesc& Lt, c
     if (!oz_unit(*st, *buf, g.maps + Lt.lmap, Lt.lr0, r0, g.maps + Lt.lmap + 1, Lt.lr0, c0,
                  Lt.cols, le + r0, le + c0, c + (size_t)r0 * Ct.ld + c0, Ct.ld,
                  min(kTcM, Ct.rows - r0), min(kOzN, Ct.cols - c0), r0 - c0))
+      return false;
+  }
+  return true;
+}
+
+// TRSM by the inverse: A (FP64) <- A V^T, V = L_kk^{-1}, from the slots of
+// A (split in the task's previous phase) and of V; units are the 128 x 32
+// blocks of A.  The product only reads the slots, so it may overwrite A.
+__device__ __noinline__ bool op_oz_trsm_inv(const DevGraph& g, const TileDesc& Vt,
+                                            const TileDesc& At, uint32_t u0, uint32_t u1,
+                                            TcState* st, TcBuf* buf) {
+  double* a = (double*)At.ptr;
+  const uint32_t nbc = cdiv32(At.cols);
+  const int* ae = oz_exps(At);
+  const int* ve = oz_exps(Vt);
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = (int)(u / nbc) * kTcM, c0 = (int)(u % nbc) * kOzN;
+    if (!oz_unit(*st, *buf, g.maps + At.lmap, At.lr0, r0, g.maps + Vt.lmap + 1, Vt.lr0, c0,
+                 At.cols, ae + r0, ve + c0, a + (size_t)r0 * At.ld + c0, At.ld,
+                 min(kTcM, At.rows - r0), min(kOzN, At.cols - c0), 1 << 30, true))
       return false;
   }
   return true;

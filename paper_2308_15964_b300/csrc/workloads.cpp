@@ -49,12 +49,13 @@ namespace {
 // factor: insert the factorization tasks; dev_X: the solve tasks too;
 // dev_V (mixed precision only): the panel solves as TRTRI + TRSM_INV.
 // Tiles of the lower triangle of A whose off-diagonal tiles (i, k) own split
-// slot i (i - 1) / 2 + k of the store at S (SPX_F64_OZAKI).
+// slot i (i - 1) / 2 + k of the store at S (SPX_F64_OZAKI); with inverse
+// panels (inv) the diagonal inverses V_k own slots T (T - 1) / 2 + k.
 int register_ozaki_tiles(spx_graph_t g, double* A, int n, int lda, int b, char* S,
-                         long long S_bytes, Tiles& out) {
+                         long long S_bytes, Tiles& out, bool inv) {
   const long long slot = spx_ozaki_slot_bytes(b);
   const int T = (n + b - 1) / b;
-  const long long nslots = (long long)T * (T - 1) / 2;
+  const long long nslots = (long long)T * (T - 1) / 2 + (inv ? T : 0);
   if (!slot || !S || ((uintptr_t)S & 255)) return SPX_ERR_INVALID_ARG;
   if (nslots > 0) {
     if (S_bytes < nslots * slot || nslots > 0x7FFFFFFF) return SPX_ERR_INVALID_ARG;
@@ -84,7 +85,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
     return SPX_ERR_INVALID_ARG;
   const bool oz = prec == SPX_F64_OZAKI;
   if (prec != SPX_F64 && !oz && (!dev_Alo || ldlo < n)) return SPX_ERR_INVALID_ARG;
-  if (dev_V && (prec == SPX_F64 || oz || ldv < (b < n ? b : n))) return SPX_ERR_INVALID_ARG;
+  if (dev_V && (prec == SPX_F64 || ldv < (b < n ? b : n))) return SPX_ERR_INVALID_ARG;
   const int elem = prec == SPX_BF16 ? 2 : 4;
   int rc = SPX_OK;
   if (prec != SPX_F64 && !oz)
@@ -93,7 +94,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
   if (rc != SPX_OK) return rc;
   Tiles A;
   if (oz)
-    rc = register_ozaki_tiles(g, dev_A, n, lda, b, (char*)dev_Alo, S_bytes, A);
+    rc = register_ozaki_tiles(g, dev_A, n, lda, b, (char*)dev_Alo, S_bytes, A, dev_V != nullptr);
   else
     rc = register_tiles(g, dev_A, n, n, lda, b, true, A,
                         prec != SPX_F64 ? (char*)dev_Alo : nullptr, ldlo, elem);
@@ -124,10 +125,16 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
       unsigned v = 0;
       if (rc == SPX_OK && k + 1 < T)
         rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, crit, nullptr, prec);
+      // split prec: V_k owns a slot after the factor tiles' and is split
+      // after the inversion (the TRSM_INV products read its digits)
+      char* vslot = oz ? (char*)dev_Alo + ((long long)T * (T - 1) / 2 + k) *
+                                              spx_ozaki_slot_bytes(b)
+                       : nullptr;
       if (rc == SPX_OK)
-        rc = spx_tile_register(g, dev_V + (size_t)k * b * ldv, bk, bk, ldv, SPX_DT_F64, nullptr, 0,
-                               &v);
-      if (rc == SPX_OK) rc = ins(SPX_OP_TRTRI, {A.at(k, k), v}, {R, W}, hi, nullptr);
+        rc = spx_tile_register(g, dev_V + (size_t)k * b * ldv, bk, bk, ldv, SPX_DT_F64, vslot,
+                               oz ? b : 0, &v);
+      if (rc == SPX_OK)
+        rc = ins(SPX_OP_TRTRI, {A.at(k, k), v}, {R, W}, hi, nullptr, oz ? prec : SPX_F64);
       for (int i = k + 2; i < T && rc == SPX_OK; ++i)
         rc = ins(SPX_OP_TRSM_INV, {v, A.at(i, k)}, {R, W}, hi, nullptr, prec);
     }
@@ -194,11 +201,12 @@ extern "C" int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n
 }
 
 extern "C" int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b,
-                                         void* dev_S, long long S_bytes, double* dev_X, int nrhs,
-                                         int ldx, int lookahead, long long* out_ntasks) {
+                                         void* dev_S, long long S_bytes, double* dev_V, int ldv,
+                                         double* dev_X, int nrhs, int ldx, int lookahead,
+                                         long long* out_ntasks) {
   if (!spx_ozaki_slot_bytes(b)) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_A, n, lda, b, dev_S, 0, true, dev_X, nrhs, ldx, lookahead,
-                         SPX_F64_OZAKI, out_ntasks, nullptr, 0, S_bytes);
+                         SPX_F64_OZAKI, out_ntasks, dev_V, ldv, S_bytes);
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,

@@ -82,7 +82,7 @@ def _load():
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
         "spx_ozaki_slot_bytes": (LL, [I]),
         "spx_ozaki_register": (I, [P, P, I, I, P]),
-        "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, I, I, P]),
+        "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, P, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
         "spx_cholesky_insert_mixed_inv": (I, [P, P, I, I, I, P, I, P, I, P, I, I, I, I, P]),
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),

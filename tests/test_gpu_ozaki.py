@@ -262,3 +262,122 @@ def test_bottom_level_priorities_bit_identical(S, n, b):
     assert np.array_equal(L1, L2) and np.array_equal(X1, X2)
     g1.close()
     g2.close()
+
+
+# --- inverse panels: TRTRI (FP64) + split, TRSM_INV as a split product --------
+
+@pytest.mark.parametrize("m,bk", [(512, 512), (200, 96), (77, 64)])
+def test_trsm_inv_op_bit_exact(S, m, bk):
+    """TRTRI with the split prec inverts L (FP64) and splits V; TRSM_INV with
+    the split prec splits A, stores A V^T by the split product and splits
+    the result.  V against the oracle's TRTRI (FP64 rounding), every digit
+    plane, exponent and product bit for bit against the oracle."""
+    Lkk = inputs.spd_matrix(bk, 1.0, seed=m + bk).numpy()
+    assert O.potrf(Lkk) == 0
+    Lkk = np.tril(Lkk)
+    A = np.random.default_rng(m).standard_normal((m, bk))
+    b = r32(max(m, bk))
+    slot = S.lib.spx_ozaki_slot_bytes(b)
+    store = torch.zeros(2 * slot, dtype=torch.uint8, device="cuda")
+    Ld = torch.from_numpy(Lkk.copy()).cuda()
+    Vd = torch.zeros((bk, bk), dtype=torch.float64, device="cuda")
+    Ad = torch.from_numpy(A.copy()).cuda()
+    g = S.Graph()
+    g.register_ozaki(store.data_ptr(), 2, b)
+    hL = g.register_tensor(Ld)
+    hV = g.register(Vd.data_ptr(), bk, bk, bk, S.DT_F64, store.data_ptr() + slot, b)
+    hA = g.register(Ad.data_ptr(), m, bk, bk, S.DT_F64, store.data_ptr(), b)
+    g.insert(S.OP_TRTRI, [hL, hV], [S.READ, S.WRITE], prec=S.F64_OZAKI)
+    g.insert(S.OP_TRSM_INV, [hV, hA], [S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    V = Vd.cpu().numpy()
+    Vo = O.trtri(Lkk)
+    assert np.abs(V - Vo).max() <= 1e-12 * np.abs(Vo).max()
+    check_split(store, slot, 1, b, V)
+    X = Ad.cpu().numpy()
+    assert np.array_equal(X, Z.products(A, V))
+    check_split(store, slot, 0, b, X)
+    g.close()
+
+
+def bidiag_lower(n, b, seed):
+    """Unit lower L0 with diagonal tiles I - S (inverses: lower triangles of
+    ones) and off-diagonal entries in {-1, 0, 1}: every inverse, product and
+    partial sum is a small integer."""
+    rng = np.random.default_rng(seed)
+    L = np.tril(rng.integers(-1, 2, size=(n, n)).astype(np.float64), -1)
+    for k in range(0, n, b):
+        e = min(n, k + b)
+        L[k:e, k:e] = np.eye(e - k) - np.eye(e - k, k=-1)
+    return L
+
+
+def run_ozaki_inv(S, A_np, b, X_np=None, **cfg):
+    from paper_2308_15964_b300 import cholesky
+    n = A_np.shape[0]
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
+    X = torch.from_numpy(np.ascontiguousarray(X_np)).cuda() if X_np is not None else None
+    V = torch.zeros((n, b), dtype=torch.float64, device="cuda")
+    g = S.Graph(**cfg)
+    cholesky.cholesky_ozaki_graph(g, A, b, X, V=V)
+    rc, info = g.run()
+    torch.cuda.synchronize()
+    return rc, info, A.cpu().numpy(), (X.cpu().numpy() if X is not None else None), V, g
+
+
+@pytest.mark.parametrize("n,b", [(1024, 256), (1000, 256), (640, 128)])
+def test_inverse_panels_integer_bit_exact(S, n, b):
+    L0 = bidiag_lower(n, b, n + b)
+    A = L0 @ L0.T
+    x0 = np.random.default_rng(3).integers(-3, 4, size=(n, 2)).astype(np.float64)
+    outs = []
+    for ex in (S.EXEC_PERSISTENT, S.EXEC_PER_TASK):
+        rc, info, L, X, V, g = run_ozaki_inv(S, A, b, A @ x0, executor=ex)
+        assert rc == 0 and info == 0
+        assert np.array_equal(np.tril(L), L0)
+        assert np.array_equal(X, x0)
+        Vh = V.cpu().numpy()
+        for k in range(0, n, b):
+            bk = min(b, n - k)
+            assert np.array_equal(Vh[k:k + bk, :bk], np.tril(np.ones((bk, bk))))
+        outs.append(L)
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("n,b,nrhs", [(512, 64, 1), (1000, 128, 2), (700, 96, 3), (2048, 512, 1),
+                                      (4096, 512, 2)])
+def test_inverse_panels_vs_oracle(S, n, b, nrhs):
+    A = inputs.spd_matrix(n, 0.1, seed=5).numpy()
+    B = inputs.rhs(n, nrhs, seed=5).numpy()
+    rc, info, L, X, V, g = run_ozaki_inv(S, A, b, B)
+    assert rc == 0 and info == 0
+    Lo = A.copy()
+    assert O.tiled_cholesky(Lo, b) == 0
+    assert rel_entry_err(L, Lo) <= 1e-12
+    assert O.solve_backward_error(A, X, B).max() <= 1e-14
+    if n <= 2048:
+        assert O.factor_backward_error(A, L) <= 1e-14
+    g.close()
+
+
+@pytest.mark.slow
+def test_inverse_panels_16384_sampled(S):
+    from paper_2308_15964_b300 import cholesky
+    n, b = 16384, 512
+    A = inputs.spd_matrix(n, 0.1, seed=2, device="cuda")
+    A_host = A.cpu().numpy()
+    B = inputs.rhs(n, 1, seed=2, device="cuda")
+    B_host = B.cpu().numpy()
+    V = torch.zeros((n, b), dtype=torch.float64, device="cuda")
+    g = S.Graph()
+    cholesky.cholesky_ozaki_graph(g, A, b, B, V=V)
+    rc, info = g.run()
+    assert rc == 0 and info == 0
+    L = A.cpu().numpy()
+    X = B.cpu().numpy()
+    for s in range(2):
+        assert O.freivalds(A_host, L, inputs.gaussian(n, 100 + s)) <= 1e-14
+    assert O.solve_backward_error(A_host, X, B_host).max() <= 1e-14
+    g.close()
