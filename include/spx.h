@@ -281,9 +281,10 @@ int spx_lowp_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
                       unsigned* out_map);
 
 /* Bytes of one split slot of an SPX_F64_OZAKI tile with pitch b: eight BF16
- * digit planes of b x b (plane s, row r, column k at element
- * (s * b + r) * b + k), then b int32 row exponents, rounded up to 256 bytes.
- * 0 for a b that spx_ozaki_register rejects. */
+ * digit planes of b x b cut into 16-column chunks (plane s, row r, column k
+ * at element ((s * (b / 16) + k / 16) * b + r) * 16 + k % 16), then b int32
+ * row exponents, rounded up to 256 bytes.  0 for a b that spx_ozaki_register
+ * rejects. */
 long long spx_ozaki_slot_bytes(int b);
 
 /* Register a store of nslots split slots (consecutive, spx_ozaki_slot_bytes(b)
@@ -291,8 +292,8 @@ long long spx_ozaki_slot_bytes(int b);
  * SPX_F64_OZAKI tasks: the lowp_ptr of a tile registered with
  * spx_tile_register must then be a slot's address, with lowp_ld = b and the
  * tile's rows, cols <= b.  b a multiple of 32, 32 <= b <= 512.  The library
- * builds two TMA tensor maps over the store (128- and 32-row boxes of 16
- * digits of all eight planes, 32-byte swizzle).  Registering the same base
+ * builds two TMA tensor maps over the store (128- and 32-row boxes of one
+ * 16-digit chunk of all eight planes, 32-byte swizzle).  Registering the same base
  * again returns the same map.  Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE,
  * SPX_ERR_CUDA. */
 int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned* out_map);

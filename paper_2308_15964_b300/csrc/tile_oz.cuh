@@ -16,7 +16,10 @@
 //          bottom: sigma_s = ((X + 64) mod 128) - 64 in [-64, 63], X <- (X -
 //          sigma_s) / 128; the top digit sigma_0 in [-64, 64].
 // The slot of the tile holds the eight digit planes as BF16 (integers of
-// magnitude <= 64 are exact in BF16) and the exponents e_r.
+// magnitude <= 64 are exact in BF16), each cut into 16-digit K chunks stored
+// one after another (plane s, chunk j, row r, digit i at element
+// ((s (b/16) + j) b + r) 16 + i), so that the operand of one K step is a
+// contiguous run of rows; then the exponents e_r.
 //
 // Product, C -= A B^T with A, B split (rows r of A, rows c of B), K <= 512:
 //   P_d = sum_{s+t=d} sum_k sigma_s[r,k] tau_t[c,k],  d = 0..7,
@@ -34,7 +37,7 @@
 // t = 0..7-s of B stacked along N (32 (8 - s) rows) in one MMA whose output
 // starts at accumulator s: output block t lands in accumulator s + t.  The K
 // step's operands (8 planes x 128 rows of A, 8 planes x 32 rows of B, 40 KB)
-// arrive by one 4-D TMA box each (32-byte swizzle), two stages.
+// arrive by one 5-D TMA box each (32-byte swizzle), two stages.
 #pragma once
 
 #include <cuda.h>
@@ -79,12 +82,13 @@ __device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z, int w) {
+// 5-D box (digit, row, K chunk, plane, slot) of the split store.
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int row, int kchunk, int slot) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(0), "r"(row), "r"(kchunk), "r"(0), "r"(slot)
       : "memory");
 }
 
@@ -188,8 +192,10 @@ __device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32
         }
         sg[0] = (int)X;
 #pragma unroll
+        // K-chunked layout: plane s, 16-digit chunk c / 16, row r, digit c % 16
         for (int s = 0; s < kOzPlanes; ++s)
-          S[((size_t)s * b + r) * b + c] = __float2bfloat16_rn((float)sg[s]);
+          S[(((size_t)s * (b / 16) + c / 16) * b + r) * 16 + (c & 15)] =
+              __float2bfloat16_rn((float)sg[s]);
       }
     }
   }
@@ -229,8 +235,8 @@ __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_s
     auto issue = [&](int st, int step) {
       uint8_t* dst = sb + st * kOzStage;
       mbar_arrive_expect_tx(&s.full[st], kOzStage);
-      tma_load_4d(dst, amap, &s.full[st], step * 16, a_r0, 0, a_slot);
-      tma_load_4d(dst + kOzStageA, bmap, &s.full[st], step * 16, b_r0, 0, b_slot);
+      tma_load_5d(dst, amap, &s.full[st], a_r0, step, a_slot);
+      tma_load_5d(dst + kOzStageA, bmap, &s.full[st], b_r0, step, b_slot);
     };
     const int pre = nsteps < kOzStages ? nsteps : kOzStages;
     for (int c = 0; c < pre; ++c) issue(c, c);
@@ -272,8 +278,13 @@ __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_s
   __syncthreads();
   if (s.error) return false;
   tc_fence_after();
-  // Epilogue: warp w reads TMEM lanes 32 (w % 4).. (rows) and columns
-  // 16 (w / 4).. of every accumulator, 8 at a time.
+  // Epilogue, 1: warp w reads TMEM lanes 32 (w % 4).. (rows) and columns
+  // 16 (w / 4).. of every accumulator, 8 at a time, forms v in integers plus
+  // one FP64 addition and stages it in shared memory (the operand stages are
+  // free: every MMA has completed).
+  constexpr int kLdv = kOzN + 1;
+  static_assert(sizeof(double) * kTcM * kLdv <= sizeof(TcBuf), "staging fits the stages");
+  double* V = reinterpret_cast<double*>(sb);
   const int warp = tid >> 5, lane = tid & 31;
   const int r = 32 * (warp & 3) + lane;
   const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -295,24 +306,39 @@ __device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_s
         else fl[j] = fl[j] * 128 + p;
       }
     }
-    if (r < m) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = cb + j;
-        if (c < n && c <= r + diag) {
-          const int x = er + b_exp[c] - 61;
-          double vh, vl, v;
-          if (oz_i2d(fh[j], 28 + x, vh) && oz_i2d(fl[j], x, vl))
-            v = __dadd_rn(vh, vl);
-          else
-            v = scalbn(__fma_rn(__ll2double_rn(fh[j]), 268435456.0, __ll2double_rn(fl[j])), x);
-          double* cp = C + (size_t)r * ldc + c;
-          *cp = store ? v : __dsub_rn(*cp, v);
-        }
+    for (int j = 0; j < 8; ++j) {
+      const int c = cb + j;
+      double v = 0.0;
+      if (r < m && c < n) {
+        const int x = er + b_exp[c] - 61;
+        double vh, vl;
+        if (oz_i2d(fh[j], 28 + x, vh) && oz_i2d(fl[j], x, vl))
+          v = __dadd_rn(vh, vl);
+        else
+          v = scalbn(__fma_rn(__ll2double_rn(fh[j]), 268435456.0, __ll2double_rn(fl[j])), x);
       }
+      V[r * kLdv + c] = v;
     }
   }
   tc_fence_before();
+  __syncthreads();
+  // Epilogue, 2: coalesced read-modify-write of the output block (a warp
+  // covers a row's 32 columns); each thread's loads are issued before any of
+  // its stores.
+  constexpr int kPer = kTcM * kOzN / kThreads;
+  double cv[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int rr = warp + (kThreads / 32) * i, c = lane;
+    cv[i] = (!store && rr < m && c < n && c <= rr + diag) ? C[(size_t)rr * ldc + c] : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int rr = warp + (kThreads / 32) * i, c = lane;
+    if (rr < m && c < n && c <= rr + diag)
+      C[(size_t)rr * ldc + c] = store ? V[rr * kLdv + c] : __dsub_rn(cv[i], V[rr * kLdv + c]);
+  }
   __syncthreads();
   return true;
 }

@@ -60,12 +60,12 @@ int make_tmap_ozaki(CUtensorMap* out, const void* ptr, int nslots, int b, int bo
     return SPX_ERR_INVALID_ARG;
   std::call_once(g_encode_once, load_encode);
   if (!g_encode) return SPX_ERR_CUDA;
-  // dims: digit column k, row r, digit plane s, slot
-  const cuuint64_t dims[4] = {(cuuint64_t)b, (cuuint64_t)b, 8, (cuuint64_t)nslots};
-  const cuuint64_t strides[3] = {(cuuint64_t)b * 2, (cuuint64_t)b * b * 2, (cuuint64_t)slot};
-  const cuuint32_t box[4] = {16, (cuuint32_t)box_rows, 8, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr),
+  // dims: digit within a 16-digit K chunk, row, K chunk, digit plane, slot
+  const cuuint64_t dims[5] = {16, (cuuint64_t)b, (cuuint64_t)b / 16, 8, (cuuint64_t)nslots};
+  const cuuint64_t strides[4] = {32, (cuuint64_t)b * 32, (cuuint64_t)b * b * 2, (cuuint64_t)slot};
+  const cuuint32_t box[5] = {16, (cuuint32_t)box_rows, 1, 8, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(ptr),
                               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

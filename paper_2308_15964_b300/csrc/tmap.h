@@ -17,9 +17,10 @@ int make_tmap(CUtensorMap* out, const void* ptr, int rows, int cols, int ld, int
 // [32, 512].
 long long ozaki_slot_bytes(int b);
 
-// Encode a store of nslots split slots at ptr (256-byte aligned) as a 4-D
-// BF16 tensor (digit column, row, plane, slot) with boxes of 16 digits x
-// box_rows (128 or 32) rows x all 8 planes and the 32-byte swizzle.
+// Encode a store of nslots split slots at ptr (256-byte aligned) as a 5-D
+// BF16 tensor (digit within a 16-digit K chunk, row, K chunk, plane, slot)
+// with boxes of 16 digits x box_rows (128 or 32) rows x one chunk x all 8
+// planes and the 32-byte swizzle.
 int make_tmap_ozaki(CUtensorMap* out, const void* ptr, int nslots, int b, int box_rows);
 
 }  // namespace spx

@@ -38,7 +38,9 @@ def r32(x):
 def slot_view(store, slot_bytes, i, b):
     """(planes [8, b, b] float32, exponents [b] int32) of slot i."""
     raw = store[i * slot_bytes:(i + 1) * slot_bytes]
-    planes = raw[:16 * b * b].view(torch.bfloat16).float().reshape(8, b, b).cpu().numpy()
+    # plane, 16-digit K chunk, row, digit -> plane, row, column
+    planes = (raw[:16 * b * b].view(torch.bfloat16).float().reshape(8, b // 16, b, 16)
+              .permute(0, 2, 1, 3).reshape(8, b, b).cpu().numpy())
     exps = raw[16 * b * b:16 * b * b + 4 * b].view(torch.int32).cpu().numpy()
     return planes, exps
 
