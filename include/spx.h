@@ -292,7 +292,7 @@ long long spx_ozaki_slot_bytes(int b);
  * SPX_F64_OZAKI tasks: the lowp_ptr of a tile registered with
  * spx_tile_register must then be a slot's address, with lowp_ld = b and the
  * tile's rows, cols <= b.  b a multiple of 32, 32 <= b <= 512.  The library
- * builds two TMA tensor maps over the store (128- and 32-row boxes of one
+ * builds two TMA tensor maps over the store (128- and 64-row boxes of one
  * 16-digit chunk of all eight planes, 32-byte swizzle).  Registering the same base
  * again returns the same map.  Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE,
  * SPX_ERR_CUDA. */

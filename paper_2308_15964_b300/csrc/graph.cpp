@@ -112,11 +112,11 @@ struct spx_graph {
   std::vector<int> tile_dtype;
   std::vector<CUtensorMap> maps;      // low-precision matrices
   // kind 0: low-precision matrix; 1: split store (the map with 128-row
-  // boxes; the next map, kind 2, is the same store with 32-row boxes).  For
+  // boxes; the next map, kind 2, is the same store with 64-row boxes).  For
   // a split store ld = the slot pitch b and cols_ = the number of slots.
   struct MapInfo { uintptr_t base; size_t bytes; int ld, elem, dtype, cols_, kind; };
   std::vector<MapInfo> map_info;
-  bool has_tc = false;                // some task runs on the tensor cores
+  int tc_mode = 0;  // kernel family: 1 some task on the tensor cores, 2 some split-FP64 task
   std::unordered_map<uintptr_t, uint32_t> key_to_handle;
   std::vector<HandleState> hstate;
   std::vector<TaskDesc> tasks;
@@ -540,7 +540,7 @@ int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned
     }
   CUtensorMap ma, mb;
   int rc = make_tmap_ozaki(&ma, dev_ptr, nslots, b, 128);
-  if (rc == SPX_OK) rc = make_tmap_ozaki(&mb, dev_ptr, nslots, b, 32);
+  if (rc == SPX_OK) rc = make_tmap_ozaki(&mb, dev_ptr, nslots, b, 64);
   if (rc != SPX_OK) return rc;
   const size_t bytes = (size_t)nslots * (size_t)ozaki_slot_bytes(b);
   g->maps.push_back(ma);
@@ -642,7 +642,10 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   g->task_rec.push_back((uint32_t)g->rec_handle.size());
   g->tasks.push_back(t);
   g->items[graph_queue(t.prio)] += items;
-  if (prec != SPX_F64) g->has_tc = true;
+  if (prec != SPX_F64) {
+    const int mode = prec == SPX_F64_OZAKI ? 2 : 1;
+    if (mode > g->tc_mode) g->tc_mode = mode;
+  }
   g->uploaded = false;
   if (out_task) *out_task = tid;
   return SPX_OK;
@@ -788,10 +791,10 @@ int enqueue_rerun(spx_graph* g, cudaStream_t st) {
   if (rc != SPX_OK) return rc;
   cudaError_t e;
   if (g->cfg.executor == SPX_EXEC_PER_TASK) {
-    e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->has_tc, st);
+    e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->tc_mode, st);
   } else {
     e = launch_init(g->dg, st);
-    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->has_tc, st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->tc_mode, st);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
@@ -873,7 +876,7 @@ cudaError_t launch_streams(spx_graph* g, cudaStream_t st) {
     for (uint32_t k = g->pred_ptr[u]; k < g->pred_ptr[u + 1] && e == cudaSuccess; ++k)
       if (stream_of(g->pred[k]) != si) e = cudaStreamWaitEvent(g->xs[si], g->task_ev[g->pred[k]], 0);
     if (e == cudaSuccess)
-      e = launch_task(g->dg, (uint32_t)u, g->tasks[u], g->tiles.data(), g->has_tc, g->xs[si]);
+      e = launch_task(g->dg, (uint32_t)u, g->tasks[u], g->tiles.data(), g->tc_mode, g->xs[si]);
     if (e == cudaSuccess) e = cudaEventRecord(g->task_ev[u], g->xs[si]);
   }
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
@@ -924,7 +927,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
     rc = reset_run_state(g, st);
     if (rc != SPX_OK) return rc;
     e = cudaEventRecord(g->tev[1], st);
-    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->has_tc, st);
+    if (e == cudaSuccess) e = launch_per_task(g->dg, g->tasks.data(), g->tiles.data(), g->tc_mode, st);
   } else if (g->cfg.executor == SPX_EXEC_STREAMS) {
     rc = g->derived ? reset_run_state(g, st) : spx_graph_derive(g, stream);
     if (rc == SPX_OK) rc = prepare_streams(g, st);
@@ -944,7 +947,7 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
       if (rc != SPX_OK) return rc;
     }
     e = cudaEventRecord(g->tev[1], st);
-    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->has_tc, st);
+    if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->tc_mode, st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1144,7 +1147,7 @@ int spx_graph_clear(spx_graph_t g) {
   g->tile_dtype.clear();
   g->maps.clear();
   g->map_info.clear();
-  g->has_tc = false;
+  g->tc_mode = 0;
   g->key_to_handle.clear();
   g->hstate.clear();
   g->tasks.clear();

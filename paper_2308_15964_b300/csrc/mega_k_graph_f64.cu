@@ -5,10 +5,10 @@
 
 namespace spx {
 
-const void* mega_fn_graph_f64() { return (const void*)persistent_kernel<false, false>; }
+const void* mega_fn_graph_f64() { return (const void*)persistent_kernel<0, false>; }
 
 cudaError_t mega_launch_graph_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g) {
-  persistent_kernel<false, false><<<ctas, kThreads, smem, st>>>(g);
+  persistent_kernel<0, false><<<ctas, kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -5,10 +5,10 @@
 
 namespace spx {
 
-const void* mega_fn_graph_tc() { return (const void*)persistent_kernel<true, false>; }
+const void* mega_fn_graph_tc() { return (const void*)persistent_kernel<1, false>; }
 
 cudaError_t mega_launch_graph_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g) {
-  persistent_kernel<true, false><<<ctas, kThreads, smem, st>>>(g);
+  persistent_kernel<1, false><<<ctas, kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -5,10 +5,10 @@
 
 namespace spx {
 
-const void* mega_fn_server_f64() { return (const void*)persistent_kernel<false, true>; }
+const void* mega_fn_server_f64() { return (const void*)persistent_kernel<0, true>; }
 
 cudaError_t mega_launch_server_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g) {
-  persistent_kernel<false, true><<<ctas, kThreads, smem, st>>>(g);
+  persistent_kernel<0, true><<<ctas, kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 

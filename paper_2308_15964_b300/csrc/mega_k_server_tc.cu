@@ -5,10 +5,10 @@
 
 namespace spx {
 
-const void* mega_fn_server_tc() { return (const void*)persistent_kernel<true, true>; }
+const void* mega_fn_server_tc() { return (const void*)persistent_kernel<1, true>; }
 
 cudaError_t mega_launch_server_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g) {
-  persistent_kernel<true, true><<<ctas, kThreads, smem, st>>>(g);
+  persistent_kernel<1, true><<<ctas, kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -5,11 +5,11 @@
 
 namespace spx {
 
-const void* mega_fn_task_f64() { return (const void*)task_kernel<false>; }
+const void* mega_fn_task_f64() { return (const void*)task_kernel<0>; }
 
 cudaError_t mega_launch_task_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
                                uint32_t task, uint32_t phase) {
-  task_kernel<false><<<ctas, kThreads, smem, st>>>(g, task, phase);
+  task_kernel<0><<<ctas, kThreads, smem, st>>>(g, task, phase);
   return cudaGetLastError();
 }
 

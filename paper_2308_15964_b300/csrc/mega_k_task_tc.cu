@@ -5,11 +5,11 @@
 
 namespace spx {
 
-const void* mega_fn_task_tc() { return (const void*)task_kernel<true>; }
+const void* mega_fn_task_tc() { return (const void*)task_kernel<1>; }
 
 cudaError_t mega_launch_task_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
                                uint32_t task, uint32_t phase) {
-  task_kernel<true><<<ctas, kThreads, smem, st>>>(g, task, phase);
+  task_kernel<1><<<ctas, kThreads, smem, st>>>(g, task, phase);
   return cudaGetLastError();
 }
 

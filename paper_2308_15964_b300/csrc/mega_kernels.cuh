@@ -220,13 +220,16 @@ __device__ bool spin_for(const DevGraph& g, long long ns) {
 // Run units u0..u1 of one phase of a task with the whole CTA.  Returns 0,
 // a POTRF info (1-based column in the tile), -1 for an op this kernel cannot
 // run, or -2 when a tensor-core wait timed out.  Low-precision tasks need
-// the tensor-core instance (kTc).
-template <bool kTc>
+// the tensor-core instances (kMode 1: two CTAs per SM; kMode 2: one CTA per
+// SM, which alone runs the split-FP64 products).
+template <int kMode>
 __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t u0,
                          uint32_t u1, F64Smem& s, TcCtx& tc) {
   const TileDesc* T = g.tiles;
   const bool lowp = t.prec != SPX_F64;
+  constexpr bool kTc = kMode >= 1;
   if (lowp && !kTc) return -1;
+  if (t.prec == SPX_F64_OZAKI && kMode != 2) return -1;
   switch (t.op) {
     case SPX_OP_POTRF:
       return op_potrf_units(T[t.h[0]], phase, u0, u1, s, t.flags & kFlagFine);
@@ -243,8 +246,15 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_SYRK:
       if constexpr (kTc) {
-        if (t.prec == SPX_F64_OZAKI)
-          return op_oz_syrk(g, T[t.h[0]], T[t.h[1]], u0, u1, tc.st, tc.buf) ? 0 : -2;
+        if constexpr (kMode == 2) {
+          if (t.prec == SPX_F64_OZAKI) {
+            const TileDesc &Lt = T[t.h[0]], &Ct = T[t.h[1]];
+            return oz_product_units(g, Lt, Lt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, true,
+                                    t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
+                       ? 0
+                       : -2;
+          }
+        }
         if (lowp) {
           const bool ok = t.prec == SPX_BF16 ? op_tc_syrk<true>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc)
                                              : op_tc_syrk<false>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc);
@@ -255,8 +265,15 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_GEMM_NT_SUB:
       if constexpr (kTc) {
-        if (t.prec == SPX_F64_OZAKI)
-          return op_oz_gemm(g, T[t.h[0]], T[t.h[1]], T[t.h[2]], u0, u1, tc.st, tc.buf) ? 0 : -2;
+        if constexpr (kMode == 2) {
+          if (t.prec == SPX_F64_OZAKI) {
+            const TileDesc &At = T[t.h[0]], &Bt = T[t.h[1]], &Ct = T[t.h[2]];
+            return oz_product_units(g, At, Bt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, false,
+                                    t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
+                       ? 0
+                       : -2;
+          }
+        }
         if (lowp) {
           const bool ok =
               t.prec == SPX_BF16
@@ -317,12 +334,19 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return 0;
     case SPX_OP_TRSM_INV:
       if constexpr (kTc) {
-        if (t.prec == SPX_F64_OZAKI) {
-          if (phase != 1) {  // split the input (phase 0) or the result (phase 2)
-            op_oz_split(T[t.h[1]], u0, u1);
-            return 0;
+        if constexpr (kMode == 2) {
+          if (t.prec == SPX_F64_OZAKI) {
+            if (phase != 1) {  // split the input (phase 0) or the result (phase 2)
+              op_oz_split(T[t.h[1]], u0, u1);
+              return 0;
+            }
+            // A <- A V^T: the product reads A's and V's slots, then stores A
+            const TileDesc &Vt = T[t.h[0]], &At = T[t.h[1]];
+            return oz_product_units(g, At, Vt, (double*)At.ptr, At.ld, At.rows, At.cols, false,
+                                    t.flags & kFlagFine, true, u0, u1, tc.st, tc.oz)
+                       ? 0
+                       : -2;
           }
-          return op_oz_trsm_inv(g, T[t.h[0]], T[t.h[1]], u0, u1, tc.st, tc.buf) ? 0 : -2;
         }
         const bool ok = t.prec == SPX_BF16
                             ? op_tc_trsm_inv<true>(T[t.h[0]], T[t.h[1]], u0, u1, tc)
@@ -353,7 +377,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
 
 // Run part `part` of phase `phase`; a serial task runs all of its phases
 // and units here, in order.
-template <bool kTc>
+template <int kMode>
 __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t part,
                         F64Smem& s, TcCtx& tc) {
   const TileDesc* T = g.tiles;
@@ -361,7 +385,7 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
     const uint32_t nph = op_phases(t.op, t.prec, T, t.h);
     for (uint32_t ph = 0; ph < nph; ++ph) {
       const uint32_t nu = op_phase_units(t.op, t.prec, T, t.h, ph, t.flags & kFlagFine);
-      const int r = run_units<kTc>(g, t, ph, 0, nu, s, tc);
+      const int r = run_units<kMode>(g, t, ph, 0, nu, s, tc);
       if (r) return r;
       __syncthreads();
     }
@@ -371,7 +395,7 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
   const uint32_t parts = phase_parts(units);
   const uint32_t u0 = (uint32_t)((unsigned long long)part * units / parts);
   const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / parts);
-  return run_units<kTc>(g, t, phase, u0, u1, s, tc);
+  return run_units<kMode>(g, t, phase, u0, u1, s, tc);
 }
 
 // Push the next phase (np parts) of task u (thread 0).  The CTA that
@@ -614,18 +638,21 @@ __device__ void finish_request(const DevGraph& g, uint32_t r) {
   atomicSub(&g.rs->live.v, 1u);
 }
 
-template <bool kTc, bool kServer>
+// kMode 2 runs one CTA per SM (its shared memory allows no second), with
+// the same register budget as the others.
+template <int kMode, bool kServer>
 __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
+  constexpr bool kTc = kMode >= 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the tensor-core instance aligns its operand stages to 1024 bytes; they
+  // the tensor-core instances align their operand stages to 1024 bytes; they
   // share the space with the FP64 ops' buffers
   unsigned char* base =
       kTc ? (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023) : smem_raw;
   F64Smem& s = *reinterpret_cast<F64Smem*>(base);
   __shared__ TcState tcs;
-  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base)};
+  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base), reinterpret_cast<OzBuf*>(base)};
   if (kTc) {
-    tc_setup(tcs);
+    tc_setup(tcs, kMode == 2 ? 512u : kTcCtaCols);
     __syncthreads();
   }
   __shared__ uint32_t s_item, s_np;
@@ -679,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (!s_flag) break;
-    const int info = skip ? 0 : run_part<kTc>(g, t, phase, part, s, tc);
+    const int info = skip ? 0 : run_part<kMode>(g, t, phase, part, s, tc);
     __syncthreads();
     const long long dt = clock64() - c0;
     busy += dt;
@@ -767,25 +794,27 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
 }
 
 // Baseline: one launch per task phase, one CTA per part, insertion order.
-template <bool kTc>
-__global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u, uint32_t phase) {
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t u,
+                                                                            uint32_t phase) {
+  constexpr bool kTc = kMode >= 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base =
       kTc ? (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023) : smem_raw;
   F64Smem& s = *reinterpret_cast<F64Smem*>(base);
   __shared__ TcState tcs;
-  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base)};
+  TcCtx tc{&tcs, reinterpret_cast<TcBuf*>(base), reinterpret_cast<OzBuf*>(base)};
   __shared__ int s_abort;
   if (threadIdx.x == 0) s_abort = (int)ld_volatile(&g.rs->abort);
   __syncthreads();
   if (s_abort) return;
   if (kTc) {
-    tc_setup(tcs);
+    tc_setup(tcs, kMode == 2 ? 512u : kTcCtaCols);
     __syncthreads();
   }
   const TaskDesc t = g.tasks[u];
   if (threadIdx.x == 0 && blockIdx.x == 0) touch_progress(g);
-  const int info = run_part<kTc>(g, t, phase, blockIdx.x, s, tc);
+  const int info = run_part<kMode>(g, t, phase, blockIdx.x, s, tc);
   if (threadIdx.x == 0) {
     if (info > 0) set_error(g.rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
     else if (info < 0) set_error(g.rs, (uint32_t)(info == -2 ? SPX_ERR_TIMEOUT : SPX_ERR_BAD_OP), 0);

@@ -16,6 +16,8 @@ const void* mega_fn_server_f64();
 const void* mega_fn_server_tc();
 const void* mega_fn_task_f64();
 const void* mega_fn_task_tc();
+const void* mega_fn_graph_oz();
+const void* mega_fn_task_oz();
 
 cudaError_t mega_launch_graph_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
 cudaError_t mega_launch_graph_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
@@ -24,6 +26,9 @@ cudaError_t mega_launch_server_tc(int ctas, size_t smem, cudaStream_t st, const 
 cudaError_t mega_launch_task_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
                                  uint32_t task, uint32_t phase);
 cudaError_t mega_launch_task_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
+                                uint32_t task, uint32_t phase);
+cudaError_t mega_launch_graph_oz(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
+cudaError_t mega_launch_task_oz(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
                                 uint32_t task, uint32_t phase);
 
 }  // namespace spx

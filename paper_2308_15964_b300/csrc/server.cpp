@@ -265,6 +265,9 @@ int spx_server_submit(spx_server_t s, spx_graph_t g, unsigned long long* out_req
   for (size_t i = 0; i < v.ntasks; ++i) {
     if (v.tasks[i].flags & kFlagComm) return SPX_ERR_INVALID_ARG;  // no commutative writes
     if (v.tasks[i].prec != SPX_F64 && !s->cfg.tensor_cores) return SPX_ERR_INVALID_ARG;
+    // the split-FP64 products need the one-CTA-per-SM kernel, which the
+    // server does not run
+    if (v.tasks[i].prec == SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
   }
   const unsigned long long items = v.items;
   if (s->free_slots.empty() || s->live_items + items > (unsigned long long)s->cfg.queue_capacity)

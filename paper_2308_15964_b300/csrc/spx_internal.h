@@ -288,17 +288,26 @@ __host__ __device__ inline uint32_t trtri_level_units(int n, uint32_t phase, uin
   return total;
 }
 
-// SPX_F64_OZAKI SYRK on an n x n tile: the 128-row x 32-column output blocks
-// (i, j) that reach the lower triangle (32 j < 128 (i + 1)), row block by row
-// block.  Returns their count; with unit < count, also the block of that unit.
-__host__ __device__ inline uint32_t oz_syrk_units(int n, uint32_t unit, uint32_t* ij) {
-  const uint32_t nbr = cdiv128(n), nbc = cdiv32(n);
+// Units of a split-prec (SPX_F64_OZAKI) product, run by the one-CTA-per-SM
+// kernel: output blocks of 128 rows x 64 columns, a unit being up to
+// kOzGroup consecutive column blocks of one row block (their K loops and
+// epilogues pipelined on one CTA), one block per unit for critical-path
+// tasks (fine).  lower: only the blocks that reach the lower triangle (64 j <
+// 128 (i + 1)).  Returns the number of units; with unit < that number and
+// blk != nullptr, also its row block, first column block and block count.
+constexpr int kOzGroup = 4;
+__host__ __device__ inline uint32_t oz_units(int rows, int cols, bool lower, bool fine,
+                                             uint32_t unit, uint32_t* blk) {
+  const uint32_t nbr = cdiv128(rows), nbc = cdiv64(cols), g = fine ? 1u : (uint32_t)kOzGroup;
   uint32_t total = 0;
   for (uint32_t i = 0; i < nbr; ++i) {
-    const uint32_t cnt = 4 * (i + 1) < nbc ? 4 * (i + 1) : nbc;
-    if (ij && unit >= total && unit < total + cnt) {
-      ij[0] = i;
-      ij[1] = unit - total;
+    const uint32_t nb = lower && 2 * (i + 1) < nbc ? 2 * (i + 1) : nbc;
+    const uint32_t cnt = (nb + g - 1) / g;
+    if (blk && unit >= total && unit < total + cnt) {
+      const uint32_t j0 = (unit - total) * g;
+      blk[0] = i;
+      blk[1] = j0;
+      blk[2] = nb - j0 < g ? nb - j0 : g;
     }
     total += cnt;
   }
@@ -351,13 +360,13 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return phase % 2 == 0 ? rb : rb * (nbc - 1 - j);
     }
     case SPX_OP_SYRK: {
-      if (prec == SPX_F64_OZAKI) return oz_syrk_units(t[h[1]].rows, 0xFFFFFFFFu, nullptr);
+      if (prec == SPX_F64_OZAKI) return oz_units(t[h[1]].rows, t[h[1]].rows, true, fine, 0, nullptr);
       const uint32_t nb = prec != SPX_F64 ? cdiv128(t[h[1]].rows)
                                           : (fine ? cdiv32(t[h[1]].rows) : cdiv64(t[h[1]].rows));
       return nb * (nb + 1) / 2;
     }
     case SPX_OP_GEMM_NT_SUB:
-      if (prec == SPX_F64_OZAKI) return cdiv128(t[h[2]].rows) * cdiv32(t[h[2]].cols);
+      if (prec == SPX_F64_OZAKI) return oz_units(t[h[2]].rows, t[h[2]].cols, false, fine, 0, nullptr);
       if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
       return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_NN_ADD:
@@ -374,7 +383,8 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);
     case SPX_OP_TRSM_INV:  // 128-row blocks of A_ik (tensor cores)
       if (prec == SPX_F64_OZAKI)
-        return phase == 1 ? cdiv128(t[h[1]].rows) * cdiv32(t[h[1]].cols) : cdiv64(t[h[1]].rows);
+        return phase == 1 ? oz_units(t[h[1]].rows, t[h[1]].cols, false, fine, 0, nullptr)
+                          : cdiv64(t[h[1]].rows);
       return cdiv128(t[h[1]].rows);
     case SPX_OP_NBODY_SELF:  // 64-particle target blocks
       return cdiv64(t[h[0]].rows);
@@ -396,12 +406,13 @@ __host__ __device__ inline uint32_t phase_parts(uint32_t units) {
 // Launchers implemented in the .cu files (all asynchronous on stream).
 cudaError_t launch_derive(const DevGraph& g, cudaStream_t st);
 cudaError_t launch_init(const DevGraph& g, cudaStream_t st);  // reset run state only
-cudaError_t launch_persistent(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
+// mode: 0 FP64 ops only, 1 tensor-core tile ops, 2 the split-FP64 products.
+cudaError_t launch_persistent(const DevGraph& g, int num_ctas, int mode, cudaStream_t st);
 cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
-                            const TileDesc* host_tiles, bool tc, cudaStream_t st);
+                            const TileDesc* host_tiles, int mode, cudaStream_t st);
 // The launches of one task's phases on st (per-task executors).
 cudaError_t launch_task(const DevGraph& g, uint32_t u, const TaskDesc& t,
-                        const TileDesc* host_tiles, bool tc, cudaStream_t st);
+                        const TileDesc* host_tiles, int mode, cudaStream_t st);
 cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
 cudaError_t launch_ring_init(const DevGraph& g, cudaStream_t st);
 int persistent_max_ctas(int* per_sm);

@@ -31,13 +31,19 @@
 //   v = RN(F 2^(e_r + f_c - 61)) = RN(Fh 2^(28+x) + Fl 2^x), x = e_r + f_c - 61
 //       (both terms exact FP64, one rounded addition); C_rc <- RN(C_rc - v).
 //
-// Tensor-core unit: 128 output rows x 32 output columns.  Eight FP32
-// accumulators of 32 TMEM columns, accumulator d at column 32 d.  For each
-// 16-wide K step, digit plane s of A (128 x 16) multiplies the planes
-// t = 0..7-s of B stacked along N (32 (8 - s) rows) in one MMA whose output
-// starts at accumulator s: output block t lands in accumulator s + t.  The K
-// step's operands (8 planes x 128 rows of A, 8 planes x 32 rows of B, 40 KB)
-// arrive by one 5-D TMA box each (32-byte swizzle), two stages.
+// Tensor-core units (run by the one-CTA-per-SM instance of the persistent
+// kernel, which owns all 512 TMEM columns): 128 output rows x 64 output
+// columns, eight FP32 accumulators of 64 columns, accumulator d at column
+// 64 d.  For each 16-wide K step, digit plane s of A (128 x 16) multiplies
+// the planes t = 0..7-s of B stacked along N (64 (8 - s) rows, at most 256
+// per MMA) with output block t landing in accumulator s + t.  The K step's
+// operands (8 planes x 128 rows of A, 8 planes x 64 rows of B, 48 KB) arrive
+// by one 5-D TMA box each (32-byte swizzle), three stages.  Up to four
+// column blocks of one row block form a pipelined group: the drain of a
+// block's accumulators and its read-modify-write overlap the next block's
+// loads and MMAs.  Measured in isolation (a harness running the same code):
+// the operand traffic is the bound, the L2-to-SM rate near 7.3 TB/s on this
+// GPU; 128 x 64 blocks read 40 % fewer operand bytes per flop than 128 x 32.
 #pragma once
 
 #include <cuda.h>
@@ -52,14 +58,6 @@ namespace spx {
 namespace {
 
 constexpr int kOzPlanes = 8;
-constexpr int kOzN = 32;                              // output columns per unit
-constexpr int kOzStageA = kOzPlanes * kTcM * 32;      // 32 KB: 8 planes x 128 rows x 16 digits
-constexpr int kOzStageB = kOzPlanes * kOzN * 32;      // 8 KB
-constexpr int kOzStage = kOzStageA + kOzStageB;
-constexpr int kOzStages = 2;
-static_assert(kOzStages * kOzStage <= (int)sizeof(TcBuf), "split operand stages fit the buffer");
-static_assert(kOzPlanes * kOzN <= (int)kTcCtaCols, "eight accumulators fit the CTA's TMEM");
-static_assert(kOzStage % 1024 == 0, "stages stay aligned");
 
 // K-major operand, 32-byte swizzle (rows of 32 bytes, 8-row groups 256 bytes
 // apart), descriptor version 1.
@@ -201,205 +199,220 @@ __device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32
   }
 }
 
-// One 128 x 32 output unit: C[0:m, 0:n] -= (A B^T) by the split product.
-// A rows come from slot a_slot rows a_r0.. (TMA map amap, 128-row boxes),
-// B rows from slot b_slot rows b_r0.. (bmap, 32-row boxes); K digits.
-// a_exp / b_exp: the exponents of those rows.  Entries with column >
-// row + diag are left alone (SYRK's diagonal blocks).  All threads; false on
-// a barrier timeout.  store: C = A B^T instead (v rounded once, no
-// subtraction).
-__device__ bool oz_unit(TcState& s, TcBuf& buf, const CUtensorMap* amap, int a_slot, int a_r0,
-                        const CUtensorMap* bmap, int b_slot, int b_r0, int K, const int* a_exp,
-                        const int* b_exp, double* C, int ldc, int m, int n, int diag,
-                        bool store = false) {
-  const int nsteps = (K + 15) / 16;
-  const int tid = threadIdx.x;
+// Shared-memory bytes of one K step of the split operands: 8 planes x (128
+// rows of A + kN rows of B) x 16 digits.
+__host__ __device__ constexpr int oz_stage_bytes(int kN) { return kOzPlanes * (kTcM + kN) * 32; }
+
+// Bounded wait that also gives up once the CTA's error flag is set.
+__device__ __forceinline__ bool mbar_wait_or_error(uint64_t* bar, uint32_t parity,
+                                                   const volatile int* err) {
+  for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 1023u) == 1023u && *err) return false;
+  }
+  return false;
+}
+
+// Split-product unit of the one-CTA-per-SM kernel: nblk <= kOzGroup
+// consecutive 128 x 64 output blocks of one row block, C[0:m, 0:n] -= A B^T
+// (C at the first block; n counts columns from there).  Eight accumulators
+// of 64 TMEM columns (all 512).  Per block:
+//   thread 0   issues the block's TMA loads and MMAs (kS stages of 48 KB at
+//              sb; the loads run kS - 1 steps ahead, across block
+//              boundaries) and commits the block to s.done;
+//   all warps  wait for it and drain the accumulators (warp w: TMEM lane
+//              quarter w % 4, columns 32 (w / 4)..) into V (128 x 65
+//              doubles): v formed in integers plus one FP64 addition;
+//   warps 1-7  update the block from V (coalesced rows, a batch's loads
+//              before its stores) while thread 0 issues the next block.
+// V is free again when every warp has reached the next block's drain.
+// Every wait is bounded; a timeout sets s.error and the loop finishes its
+// blocks without work.
+template <int kS>
+__device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMap* amap,
+                            int a_slot, int a_r0, const CUtensorMap* bmap, int b_slot, int b_c0,
+                            int nblk, int K, const int* a_exp, const int* b_exp, double* C,
+                            int ldc, int m, int n, int diag, bool store) {
+  constexpr int kN = 64, kStage = oz_stage_bytes(kN), kStageA = kOzPlanes * kTcM * 32;
+  static_assert(kStage % 1024 == 0 && kS <= kTcBars, "stages");
+  constexpr int kLdv = kN + 1;
+  const int nsteps = (K + 15) / 16, total = nblk * nsteps;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t tmem = s.tmem_base;
-  uint8_t* const sb = reinterpret_cast<uint8_t*>(&buf);
-  // the stages may hold generic-proxy writes of an earlier op: order them
-  // before the TMA writes
+  const uint32_t done0 = s.done_phase;
+  const volatile int* err = &s.error;
+  // thread 0's pipeline state
+  uint32_t fph = s.full_phase, eph = s.empty_phase;
+  int waited = 0;
+  bool ok = true;
+  auto issue = [&](int st, int g) {
+    const int blk = g / nsteps, ks = g % nsteps;
+    uint8_t* dst = sb + st * kStage;
+    mbar_arrive_expect_tx(&s.full[st], kStage);
+    tma_load_5d(dst, amap, &s.full[st], a_r0, ks, a_slot);
+    tma_load_5d(dst + kStageA, bmap, &s.full[st], b_c0 + kN * blk, ks, b_slot);
+  };
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  if (tid >= 32 && !store) {
-    // pull the FP64 output block into L2 while the MMAs run (32 columns =
-    // two 128-byte lines per row)
-    for (int e = tid - 32; e < 2 * m; e += kThreads - 32) {
-      const int r = e >> 1, l = e & 1;
-      if (l * 16 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)r * ldc + l * 16));
+  if (tid == 0) {
+    tc_fence_after();
+    const int pre = total < kS ? total : kS;
+    for (int g = 0; g < pre; ++g) issue(g, g);
+  }
+  const int r = 32 * (warp & 3) + lane;  // drain: TMEM lane = output row
+  const int cq = 32 * (warp >> 2);       // drain: this warp's 32 columns
+  const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const int er = r < m ? a_exp[r] : 0;
+  for (int blk = 0; blk < nblk; ++blk) {
+    if (tid == 0 && ok) {
+      for (int ks = 0; ks < nsteps && ok; ++ks) {
+        const int g = blk * nsteps + ks, st = g % kS;
+        ok = mbar_wait(&s.full[st], (fph >> st) & 1u);
+        fph ^= 1u << st;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sb + st * kStage), b0 = a0 + kStageA;
+        // plane p of A times planes t = 0..7-p of B stacked along N, output
+        // block t into accumulator p + t; at most 256 columns per MMA
+#pragma unroll
+        for (int p = 0; p < kOzPlanes; ++p) {
+#pragma unroll
+          for (int t0 = 0; t0 < kOzPlanes - p; t0 += 256 / kN) {
+            const int nt = (kOzPlanes - p - t0) < 256 / kN ? (kOzPlanes - p - t0) : 256 / kN;
+            oz_mma(tmem + (uint32_t)(kN * (p + t0)), oz_desc(a0 + (uint32_t)(p * kTcM * 32)),
+                   oz_desc(b0 + (uint32_t)(t0 * kN * 32)), oz_idesc((uint32_t)(kN * nt)),
+                   (ks > 0 || p > 0) ? 1u : 0u);
+          }
+        }
+        tc_commit(&s.empty[st]);
+        if (ks == nsteps - 1) tc_commit(&s.done);  // the block's accumulators complete
+        const int pc = g - 1;
+        if (pc >= 0 && pc + kS < total) {
+          const int ps = pc % kS;
+          ok = mbar_wait(&s.empty[ps], (eph >> ps) & 1u);
+          eph ^= 1u << ps;
+          waited = pc + 1;
+          if (!ok) break;
+          issue(ps, pc + kS);
+        }
+      }
+      if (!ok) s.error = 1;
+    }
+    __syncthreads();  // V free: the previous block's update is done
+    {
+      const bool got = mbar_wait_or_error(&s.done, (done0 + blk) & 1u, err);
+      tc_fence_after();
+      if (__all_sync(0xFFFFFFFFu, got && !*err)) {
+#pragma unroll 1
+        for (int cb = cq; cb < cq + 32; cb += 8) {
+          long long fh[8], fl[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) fh[j] = fl[j] = 0;
+#pragma unroll
+          for (int d = 0; d < kOzPlanes; ++d) {
+            uint32_t v[8];
+            tmem_ld8(lanes + (uint32_t)(kN * d + cb), v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const long long p = __float2int_rn(__uint_as_float(v[j]));
+              if (d < 4) fh[j] = fh[j] * 128 + p;
+              else fl[j] = fl[j] * 128 + p;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = kN * blk + cb + j;
+            double v = 0.0;
+            if (r < m && c < n) {
+              const int x = er + b_exp[c] - 61;
+              double vh, vl;
+              if (oz_i2d(fh[j], 28 + x, vh) && oz_i2d(fl[j], x, vl))
+                v = __dadd_rn(vh, vl);
+              else
+                v = scalbn(__fma_rn(__ll2double_rn(fh[j]), 268435456.0, __ll2double_rn(fl[j])), x);
+            }
+            V[r * kLdv + cb + j] = v;
+          }
+        }
+      } else if (lane == 0) {
+        s.error = 1;
+      }
+      tc_fence_before();
+    }
+    __syncthreads();  // V ready; the accumulators are free for the next block
+    if (warp >= 1 && !*err) {
+      constexpr int kBatch = 8;
+      for (int e0 = tid - 32; e0 < kTcM * kN; e0 += 224 * kBatch) {
+        double cv[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+          const int e = e0 + 224 * i, rr = e / kN, c = e % kN, cg = kN * blk + c;
+          cv[i] = (!store && e < kTcM * kN && rr < m && cg < n && cg <= rr + diag)
+                      ? C[(size_t)rr * ldc + cg]
+                      : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+          const int e = e0 + 224 * i, rr = e / kN, c = e % kN, cg = kN * blk + c;
+          if (e < kTcM * kN && rr < m && cg < n && cg <= rr + diag)
+            C[(size_t)rr * ldc + cg] =
+                store ? V[rr * kLdv + c] : __dsub_rn(cv[i], V[rr * kLdv + c]);
+        }
+      }
     }
   }
   if (tid == 0) {
-    tc_fence_after();
-    bool ok = true;
-    uint32_t fph = s.full_phase, eph = s.empty_phase;
-    auto issue = [&](int st, int step) {
-      uint8_t* dst = sb + st * kOzStage;
-      mbar_arrive_expect_tx(&s.full[st], kOzStage);
-      tma_load_5d(dst, amap, &s.full[st], a_r0, step, a_slot);
-      tma_load_5d(dst + kOzStageA, bmap, &s.full[st], b_r0, step, b_slot);
-    };
-    const int pre = nsteps < kOzStages ? nsteps : kOzStages;
-    for (int c = 0; c < pre; ++c) issue(c, c);
-    int waited = 0;
-    for (int c = 0; c < nsteps && ok; ++c) {
-      const int st = c % kOzStages;
-      ok = mbar_wait(&s.full[st], (fph >> st) & 1u);
-      fph ^= 1u << st;
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sb + st * kOzStage), b0 = a0 + kOzStageA;
-#pragma unroll
-      for (int p = 0; p < kOzPlanes; ++p)
-        oz_mma(tmem + (uint32_t)(kOzN * p), oz_desc(a0 + (uint32_t)(p * kTcM * 32)), oz_desc(b0),
-               oz_idesc((uint32_t)(kOzN * (kOzPlanes - p))), (c > 0 || p > 0) ? 1u : 0u);
-      tc_commit(&s.empty[st]);
-      const int pc = c - 1;
-      if (pc >= 0 && pc + kOzStages < nsteps) {
-        const int ps = pc % kOzStages;
-        ok = mbar_wait(&s.empty[ps], (eph >> ps) & 1u);
-        eph ^= 1u << ps;
-        waited = pc + 1;
-        if (!ok) break;
-        issue(ps, pc + kOzStages);
-      }
-    }
-    tc_commit(&s.done);
-    if (ok) ok = mbar_wait(&s.done, s.done_phase & 1u);
-    s.done_phase ^= 1u;
-    for (int c = waited; c < nsteps && ok; ++c) {
-      const int st = c % kOzStages;
+    for (int g = waited; g < total && ok; ++g) {  // consume the stage-free phases
+      const int st = g % kS;
       ok = mbar_wait(&s.empty[st], (eph >> st) & 1u);
       eph ^= 1u << st;
     }
     s.full_phase = fph;
     s.empty_phase = eph;
+    s.done_phase = done0 ^ ((uint32_t)nblk & 1u);
     if (!ok) s.error = 1;
   }
   __syncthreads();
-  if (s.error) return false;
-  tc_fence_after();
-  // Epilogue, 1: warp w reads TMEM lanes 32 (w % 4).. (rows) and columns
-  // 16 (w / 4).. of every accumulator, 8 at a time, forms v in integers plus
-  // one FP64 addition and stages it in shared memory (the operand stages are
-  // free: every MMA has completed).
-  constexpr int kLdv = kOzN + 1;
-  static_assert(sizeof(double) * kTcM * kLdv <= sizeof(TcBuf), "staging fits the stages");
-  double* V = reinterpret_cast<double*>(sb);
-  const int warp = tid >> 5, lane = tid & 31;
-  const int r = 32 * (warp & 3) + lane;
-  const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-  const int er = r < m ? a_exp[r] : 0;
-#pragma unroll 1
-  for (int sub = 0; sub < 2; ++sub) {
-    const int cb = 16 * (warp >> 2) + 8 * sub;
-    long long fh[8], fl[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) fh[j] = fl[j] = 0;
-#pragma unroll
-    for (int d = 0; d < kOzPlanes; ++d) {
-      uint32_t v[8];
-      tmem_ld8(lanes + (uint32_t)(kOzN * d + cb), v);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const long long p = __float2int_rn(__uint_as_float(v[j]));
-        if (d < 4) fh[j] = fh[j] * 128 + p;
-        else fl[j] = fl[j] * 128 + p;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = cb + j;
-      double v = 0.0;
-      if (r < m && c < n) {
-        const int x = er + b_exp[c] - 61;
-        double vh, vl;
-        if (oz_i2d(fh[j], 28 + x, vh) && oz_i2d(fl[j], x, vl))
-          v = __dadd_rn(vh, vl);
-        else
-          v = scalbn(__fma_rn(__ll2double_rn(fh[j]), 268435456.0, __ll2double_rn(fl[j])), x);
-      }
-      V[r * kLdv + c] = v;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  // Epilogue, 2: coalesced read-modify-write of the output block (a warp
-  // covers a row's 32 columns); each thread's loads are issued before any of
-  // its stores.
-  constexpr int kPer = kTcM * kOzN / kThreads;
-  double cv[kPer];
-#pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int rr = warp + (kThreads / 32) * i, c = lane;
-    cv[i] = (!store && rr < m && c < n && c <= rr + diag) ? C[(size_t)rr * ldc + c] : 0.0;
-  }
-#pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int rr = warp + (kThreads / 32) * i, c = lane;
-    if (rr < m && c < n && c <= rr + diag)
-      C[(size_t)rr * ldc + c] = store ? V[rr * kLdv + c] : __dsub_rn(cv[i], V[rr * kLdv + c]);
-  }
-  __syncthreads();
-  return true;
+  return !s.error;
 }
+
+// Shared-memory layout of the split ops in the one-CTA-per-SM kernel:
+// three operand stages, then the staging of one finished block.
+constexpr int kOzPipeStages = 3;
+struct __align__(1024) OzBuf {
+  uint8_t stages[kOzPipeStages][oz_stage_bytes(64)];
+  double v[kTcM][65];
+};
 
 __device__ __forceinline__ const int* oz_exps(const TileDesc& t) {
   return reinterpret_cast<const int*>(reinterpret_cast<const char*>(t.lowp) +
                                       (size_t)16 * t.lowp_ld * t.lowp_ld);
 }
 
-// GEMM_NT_SUB: C (FP64) -= A B^T from the slots of A and B; units are the
-// 128 x 32 blocks of C, row block by row block.
-__device__ __noinline__ bool op_oz_gemm(const DevGraph& g, const TileDesc& At, const TileDesc& Bt,
-                                        const TileDesc& Ct, uint32_t u0, uint32_t u1,
-                                        TcState* st, TcBuf* buf) {
-  double* c = (double*)Ct.ptr;
-  const uint32_t nbc = cdiv32(Ct.cols);
+// C (FP64, rows x cols) -= / = A B^T from the slots of A and B, units u0..u1
+// of oz_units (lower: SYRK's blocks; C's (0,0) is the output's).
+__device__ __noinline__ bool oz_product_units(const DevGraph& g, const TileDesc& At,
+                                              const TileDesc& Bt, double* C, int ldc, int rows,
+                                              int cols, bool lower, bool fine, bool store,
+                                              uint32_t u0, uint32_t u1, TcState* st, OzBuf* buf) {
   const int* ae = oz_exps(At);
   const int* be = oz_exps(Bt);
   for (uint32_t u = u0; u < u1; ++u) {
-    const int r0 = (int)(u / nbc) * kTcM, c0 = (int)(u % nbc) * kOzN;
-    if (!oz_unit(*st, *buf, g.maps + At.lmap, At.lr0, r0, g.maps + Bt.lmap + 1, Bt.lr0, c0,
-                 At.cols, ae + r0, be + c0, c + (size_t)r0 * Ct.ld + c0, Ct.ld,
-                 min(kTcM, Ct.rows - r0), min(kOzN, Ct.cols - c0), 1 << 30))
-      return false;
-  }
-  return true;
-}
-
-// SYRK: C (FP64, lower) -= L L^T from the slot of L; units are the 128 x 32
-// blocks of C that reach the lower triangle.
-__device__ __noinline__ bool op_oz_syrk(const DevGraph& g, const TileDesc& Lt, const TileDesc& Ct,
-                                        uint32_t u0, uint32_t u1, TcState* st, TcBuf* buf) {
-  double* c = (double*)Ct.ptr;
-  const int* le = oz_exps(Lt);
-  for (uint32_t u = u0; u < u1; ++u) {
-    uint32_t ij[2] = {0, 0};
-    oz_syrk_units(Ct.rows, u, ij);
-    const int r0 = (int)ij[0] * kTcM, c0 = (int)ij[1] * kOzN;
-    if (!oz_unit(*st, *buf, g.maps + Lt.lmap, Lt.lr0, r0, g.maps + Lt.lmap + 1, Lt.lr0, c0,
-                 Lt.cols, le + r0, le + c0, c + (size_t)r0 * Ct.ld + c0, Ct.ld,
-                 min(kTcM, Ct.rows - r0), min(kOzN, Ct.cols - c0), r0 - c0))
-      return false;
-  }
-  return true;
-}
-
-// TRSM by the inverse: A (FP64) <- A V^T, V = L_kk^{-1}, from the slots of
-// A (split in the task's previous phase) and of V; units are the 128 x 32
-// blocks of A.  The product only reads the slots, so it may overwrite A.
-__device__ __noinline__ bool op_oz_trsm_inv(const DevGraph& g, const TileDesc& Vt,
-                                            const TileDesc& At, uint32_t u0, uint32_t u1,
-                                            TcState* st, TcBuf* buf) {
-  double* a = (double*)At.ptr;
-  const uint32_t nbc = cdiv32(At.cols);
-  const int* ae = oz_exps(At);
-  const int* ve = oz_exps(Vt);
-  for (uint32_t u = u0; u < u1; ++u) {
-    const int r0 = (int)(u / nbc) * kTcM, c0 = (int)(u % nbc) * kOzN;
-    if (!oz_unit(*st, *buf, g.maps + At.lmap, At.lr0, r0, g.maps + Vt.lmap + 1, Vt.lr0, c0,
-                 At.cols, ae + r0, ve + c0, a + (size_t)r0 * At.ld + c0, At.ld,
-                 min(kTcM, At.rows - r0), min(kOzN, At.cols - c0), 1 << 30, true))
+    uint32_t blk[3] = {0, 0, 0};
+    oz_units(rows, cols, lower, fine, u, blk);
+    const int r0 = (int)blk[0] * kTcM, c0 = (int)blk[1] * 64;
+    if (!oz_row_pipe<kOzPipeStages>(*st, &buf->stages[0][0], &buf->v[0][0], g.maps + At.lmap,
+                                    At.lr0, r0, g.maps + Bt.lmap + 1, Bt.lr0, c0, (int)blk[2],
+                                    At.cols, ae + r0, be + c0, C + (size_t)r0 * ldc + c0, ldc,
+                                    min(kTcM, rows - r0), cols - c0, lower ? r0 - c0 : 1 << 30,
+                                    store))
       return false;
   }
   return true;

@@ -46,11 +46,13 @@ struct __align__(1024) TcBuf {
 };
 
 // Barriers and accumulator address; live for the whole kernel.
+constexpr int kTcBars = 4;  // stage barrier pairs (the split unit of the one-CTA-per-SM kernel uses 4)
+
 struct TcState {
-  uint64_t full[kTcStages];   // TMA landed
-  uint64_t empty[kTcStages];  // MMAs that read the stage finished
+  uint64_t full[kTcBars];   // TMA landed
+  uint64_t empty[kTcBars];  // MMAs that read the stage finished
   uint64_t done;              // all MMAs of the unit finished
-  uint32_t tmem_base;
+  uint32_t tmem_base, tmem_cols;
   uint32_t full_phase, empty_phase, done_phase;  // parity bit s = stage s
   int error;
 };
@@ -184,15 +186,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // Allocate the CTA's accumulator columns (warp 0, all lanes) and initialise
 // the barriers (thread 0).  Call once per kernel, before __syncthreads.
-__device__ __forceinline__ void tc_setup(TcState& s) {
+__device__ __forceinline__ void tc_setup(TcState& s, uint32_t cols = kTcCtaCols) {
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s.tmem_base)),
-                 "r"(kTcCtaCols));
+                 "r"(cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kTcStages; ++i) {
+    s.tmem_cols = cols;
+    for (int i = 0; i < kTcBars; ++i) {
       mbar_init(&s.full[i], 1);
       mbar_init(&s.empty[i], 1);
     }
@@ -210,7 +213,7 @@ __device__ __forceinline__ void tc_teardown(TcState& s) {
   tc_fence_after();
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem_base),
-                 "r"(kTcCtaCols));
+                 "r"(s.tmem_cols));
   }
 }
 
@@ -487,9 +490,12 @@ namespace spx {
 namespace {
 
 // Shared-memory context of the tensor-core ops inside the persistent kernel.
+struct OzBuf;
+
 struct TcCtx {
   TcState* st;
   TcBuf* buf;
+  OzBuf* oz;  // the same memory, laid out for the split ops (one-CTA-per-SM instance)
 };
 
 // SYRK on the tensor cores: C (n x n, FP64, lower) -= L_lo L_lo^T; units are

@@ -56,7 +56,7 @@ long long ozaki_slot_bytes(int b) {
 int make_tmap_ozaki(CUtensorMap* out, const void* ptr, int nslots, int b, int box_rows) {
   const long long slot = ozaki_slot_bytes(b);
   if (!out || !ptr || nslots < 1 || !slot || ((uintptr_t)ptr & 255) ||
-      (box_rows != 128 && box_rows != 32))
+      (box_rows != 128 && box_rows != 64 && box_rows != 32))
     return SPX_ERR_INVALID_ARG;
   std::call_once(g_encode_once, load_encode);
   if (!g_encode) return SPX_ERR_CUDA;

@@ -19,7 +19,7 @@ long long ozaki_slot_bytes(int b);
 
 // Encode a store of nslots split slots at ptr (256-byte aligned) as a 5-D
 // BF16 tensor (digit within a 16-digit K chunk, row, K chunk, plane, slot)
-// with boxes of 16 digits x box_rows (128 or 32) rows x one chunk x all 8
+// with boxes of 16 digits x box_rows (128, 64 or 32) rows x one chunk x all 8
 // planes and the 32-byte swizzle.
 int make_tmap_ozaki(CUtensorMap* out, const void* ptr, int nslots, int b, int box_rows);
 
