@@ -211,26 +211,30 @@ def run_reference(args):
 
 
 def ozaki_roofline(n, b, kernel_ms, fp64_peak, traffic):
-    """Roofline of the persistent kernel on the split path.  Tensor work: each
-    128 x 32 output unit with K digits issues MMAs over N = 32 (8 - p) for
-    the eight planes p, i.e. 36 digit-pair products of 2 * 128 * 32 * K flops;
-    summed over the GEMM tasks' full tiles and the SYRK tasks' lower units.
-    FP64 work: the TRSM (b^3 per tile) and POTRF (b^3 / 3) flops on the SIMT
-    pipe.  The bound is the tensor-core rate; the FP64 share is given beside."""
+    """Roofline of the persistent kernel on the split path (inverse panels).
+    Tensor work: every 128 x 64 output block with K digits issues MMAs over
+    N = 64 (8 - p) columns for the eight planes p of A, i.e. 36 digit-pair
+    products of 2 * 128 * 64 * K flops; summed over the GEMM tasks' tiles, the
+    SYRK tasks' lower blocks and the TRSM_INV products (tiles i >= k + 2).
+    FP64 SIMT work: POTRF (b^3 / 3), the critical panel tile's substitution
+    (b^3) and TRTRI (b^3 / 3) per k.  The bound is the tensor-core rate; the
+    FP64 share is given beside."""
     T = -(-n // b)
-    gemm_units = sum(1 for k in range(T) for j in range(k + 1, T) for i in range(j + 1, T))
-    syrk_units = 0
-    nbr, nbc = -(-b // 128), -(-b // 32)
-    for i in range(nbr):
-        syrk_units += min(4 * (i + 1), nbc)
-    unit_flops = 36 * 2 * 128 * 32 * b
-    tensor_flops = (gemm_units * nbr * nbc + (T * (T - 1) // 2) * syrk_units) * unit_flops
-    fp64_flops = T * (T - 1) // 2 * b ** 3 + T * b ** 3 / 3
+    nbr, nbc = -(-b // 128), -(-b // 64)
+    full = nbr * nbc
+    syrk_blocks = sum(min(2 * (i + 1), nbc) for i in range(nbr))
+    gemm_tiles = sum((T - k - 1) * (T - k - 2) // 2 for k in range(T))
+    syrk_tiles = T * (T - 1) // 2
+    inv_tiles = sum(max(0, T - k - 2) for k in range(T))
+    block_flops = 36 * 2 * 128 * 64 * b
+    tensor_flops = ((gemm_tiles + inv_tiles) * full + syrk_tiles * syrk_blocks) * block_flops
+    fp64_flops = T * b ** 3 / 3 + (T - 1) * b ** 3 + T * b ** 3 / 3
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     bf16 = peaks.get("bf16_tflops", 1800.0)
     ach = tensor_flops / (kernel_ms * 1e-3) / 1e12
     return {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-            "traffic": traffic, "kernel": "persistent_kernel<tensor cores> (split-FP64 SYRK/GEMM)",
+            "traffic": traffic,
+            "kernel": "persistent_kernel<split products> (one CTA per SM)",
             "kernel_ms": kernel_ms,
             "peak_note": "measured cuBLAS bf16 burst rate (MEASURED_PEAKS.json)"
                          if "bf16_tflops" in peaks else "fallback bf16 peak",
@@ -285,19 +289,22 @@ def main():
     g = spx.Graph()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     oz = args.arith == "ozaki"
-    store = cholesky.ozaki_store(n, b) if oz else None
+    # split path: inverse panel solves (TRTRI + split products), the diagonal
+    # inverses in V
+    store = cholesky.ozaki_store(n, b, inverse_panels=True) if oz else None
+    V = torch.zeros((n, b), dtype=torch.float64, device="cuda") if oz else None
 
-    def build_graph(graph, ozaki=oz):
+    def build_graph(graph, ozaki=oz, inverse=True):
         if ozaki:
-            cholesky.cholesky_ozaki_graph(graph, A, b, S=store)
+            cholesky.cholesky_ozaki_graph(graph, A, b, S=store, V=V if inverse else None)
         else:
             cholesky.cholesky_graph(graph, A, b)
 
-    def step(graph, record=None, ozaki=oz):
+    def step(graph, record=None, ozaki=oz, inverse=True):
         A.copy_(A0)
         ev[0].record()
         graph.clear()
-        build_graph(graph, ozaki)
+        build_graph(graph, ozaki, inverse)
         graph.execute(stream)
         rc, info = graph.wait()
         ev[1].record()
@@ -337,7 +344,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"tiled Cholesky FP64 n={n} tile={b} ({ntasks} tasks, {nedges} edges); "
                                "step = insert + device DAG derivation + persistent execution; "
-                               + ("trailing updates by splitting on the tensor cores" if oz
+                               + ("trailing updates and panel solves (TRTRI + inverse products) "
+                                  "by splitting on the tensor cores, POTRF and the critical panel "
+                                  "tile on the FP64 pipe" if oz
                                   else "all tile ops on the FP64 SIMT pipe"),
                    "arith": args.arith,
                    "n": n, "tile": b, "tasks": ntasks, "edges": nedges, "sigma": args.sigma,
@@ -383,6 +392,18 @@ def main():
         # the same factorization with every tile op on the FP64 SIMT pipe, and
         # the two factors compared (the splitting's accuracy at this size)
         L_oz = torch.tril(A)
+        # the split path with every panel tile by FP64 substitution
+        gsub = spx.Graph()
+        step(gsub, inverse=False)
+        srec_ = []
+        for _ in range(3):
+            step(gsub, srec_, inverse=False)
+        gsub.close()
+        subms = [r[0] for r in srec_]
+        out["ozaki_substitution_panels"] = {
+            "value": flops / (statistics.mean(subms) * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "ms_per_step": statistics.mean(subms), "p99_ms": float(np.percentile(subms, 99)),
+            "steps": len(subms)}
         gf = spx.Graph()
         step(gf, ozaki=False)
         frec = []
