@@ -92,7 +92,7 @@ def parse():
                         "splitting (ozaki) or on the FP64 SIMT pipe (f64)")
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
     p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
-                                                      "overhead", "axpy", "nbody"],
+                                                      "overhead", "axpy", "nbody", "splitgemm"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -267,6 +267,9 @@ def main():
         return
     if args.workload == "tc":
         run_tc(args, world, rank, local)
+        return
+    if args.workload == "splitgemm":
+        run_splitgemm(args, world, rank, local)
         return
     if args.workload == "overhead":
         run_overhead(args, world, rank, local)
@@ -877,6 +880,82 @@ def run_overhead(args, world, rank, local):
                                   "task (write or commutative write), D in {0, 10, 100} us"},
            "atomics_per_s": {"same_address": same, "distinct_addresses": distinct},
            "rows": rows}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_splitgemm(args, world, rank, local):
+    """Stand-alone rate of the split-FP64 product: the T (T - 1) GEMM_NT_SUB
+    tasks C_ij -= A_i A_j^T (i != j) of T = n / b tiles in one graph, after
+    each A_i was split by a TRSM with an identity diagonal tile (which solves
+    nothing: only its split phase matters).  The product time is the run
+    with the products minus the run with the splits alone."""
+    import torch
+    from paper_2308_15964_b300 import spx
+    b = args.tile
+    T = max(2, args.n // b)
+    slot = spx.lib.spx_ozaki_slot_bytes(b)
+    store = torch.zeros(T * slot, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    A = [torch.rand(b, b, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1 for _ in range(T)]
+    C = torch.zeros(T * b, T * b, dtype=torch.float64, device="cuda")
+    eye = torch.eye(b, dtype=torch.float64, device="cuda")
+
+    def graph(products):
+        g = spx.Graph()
+        g.register_ozaki(store.data_ptr(), T, b)
+        hI = g.register_tensor(eye)
+        hA = [g.register(A[i].data_ptr(), b, b, b, spx.DT_F64, store.data_ptr() + i * slot, b)
+              for i in range(T)]
+        for i in range(T):
+            g.insert(spx.OP_TRSM, [hI, hA[i]], [spx.READ, spx.WRITE], prec=spx.F64_OZAKI)
+        for i in range(T if products else 0):
+            for j in range(T):
+                if i != j:
+                    hc = g.register(C[i * b:(i + 1) * b, j * b:(j + 1) * b].data_ptr(), b, b,
+                                    T * b, spx.DT_F64)
+                    g.insert(spx.OP_GEMM_NT_SUB, [hA[i], hA[j], hc], [spx.READ, spx.READ, spx.WRITE],
+                             prec=spx.F64_OZAKI)
+        return g
+
+    def timed(products):
+        g = graph(products)
+        ms = []
+        for i in range(args.warmup + args.steps):
+            if i:
+                g.reset()
+            rc, _ = g.run()
+            assert rc == spx.OK
+            if i >= args.warmup:
+                ms.append(g.timing()[1])
+        st = g.stats()
+        g.close()
+        return ms, st
+
+    with Clocks(local) as clk:
+        split_ms, _ = timed(False)
+        full_ms, st = timed(True)
+    prod_ms = statistics.mean(full_ms) - statistics.mean(split_ms)
+    tasks = T * (T - 1)
+    fp64_flops = tasks * 2.0 * b ** 3
+    tensor_flops = 36.0 * fp64_flops
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    ach = tensor_flops / (prod_ms * 1e-3) / 1e12
+    out = {"metric": "split-FP64 GEMM TFLOP/s (FP64-equivalent)", "value": fp64_flops / (prod_ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": prod_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (Ozaki split, bf16 digit planes)", "data": "synthetic uniform[-1,1)",
+           "config": {"workload": f"{tasks} GEMM_NT_SUB tasks on {T} split {b} x {b} tiles, one launch",
+                      "tile": b, "tiles": T, "tasks": tasks},
+           "kernel_ms": {"splits_only": statistics.mean(split_ms), "splits_and_products": statistics.mean(full_ms)},
+           "gpu_launches": 2 * args.steps,
+           "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                        "frac": ach / bf16, "traffic": None,
+                        "kernel": "persistent_kernel<split products> (one CTA per SM)",
+                        "note": "36 digit-pair products of 2 b^3 flops per task over the product time"},
+           "sched": {"busy_frac": st["busy_cycles"] / max(1, st["total_cycles"])},
+           "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out))
 
