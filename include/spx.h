@@ -382,6 +382,51 @@ int spx_graph_execute(spx_graph_t g, void* stream);
  * finished and not reset, or empty), SPX_ERR_OOM, SPX_ERR_CUDA. */
 int spx_batch_execute(spx_graph_t* gs, int ng, void* stream);
 
+/* Streaming (paper, section "Background" / "Task insertion": tasks are
+ * inserted while the workers execute earlier ones).  spx_stream_begin
+ * launches the persistent kernel on the tasks inserted so far (possibly none)
+ * and keeps it running; spx_task_insert (and spx_tile_register, for tiles
+ * without a low-precision copy) may then be called while it runs, and
+ * spx_stream_flush hands the tasks inserted since the last flush to the
+ * kernel; spx_stream_end flushes and lets the kernel finish and exit, after
+ * which spx_graph_wait returns the run's status as for spx_graph_execute.
+ *
+ * Dependencies are derived on the host as each task is inserted, by the same
+ * rule as the device derivation (see spx_graph_host_preds); the kernel
+ * admits each published task by attaching it to its predecessors' successor
+ * lists (64 slots per task; a predecessor whose list fills gets a relay: a
+ * NOP task appended to the graph that depends on it and takes its later
+ * successors) and runs it when they have finished.  Results equal running
+ * the tasks in insertion order.
+ *   max_tasks, max_tiles, max_records, max_preds: capacities for the whole
+ *   stream (tasks including relays; access records; predecessor entries).
+ *   The graph's configuration must be the persistent executor without CUDA
+ *   graph replay or no_split; critical-path priorities are not assigned.
+ *   The kernel family (FP64, tensor-core or split tasks) is fixed by the
+ *   tasks inserted before the begin: a later task that needs another family
+ *   is refused.  Low-precision matrices and split stores must be registered
+ *   before the begin.
+ *   The device watchdog (cfg.watchdog_ns) also bounds the host: the kernel
+ *   leaves with SPX_ERR_TIMEOUT if no task finishes and none is published
+ *   for that long before the end.
+ * Errors (begin): SPX_ERR_INVALID_ARG (capacities below the tasks inserted
+ * so far, configuration), SPX_ERR_STATE (not a graph being built), SPX_ERR_OOM,
+ * SPX_ERR_CUDA.  spx_task_insert while streaming also returns
+ * SPX_ERR_QUEUE_FULL when a capacity would be exceeded (the stream then
+ * refuses further tasks; what was published still runs). */
+int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
+                     long long max_records, long long max_preds);
+int spx_stream_flush(spx_graph_t g);
+int spx_stream_end(spx_graph_t g);
+
+/* The predecessor lists of the inserted tasks as the host-side derivation of
+ * a stream computes them (CSR by task: pred_ptr[ntasks + 1], pred[cap]); no
+ * device work.  The edge set is the device derivation's (spx_graph_edges),
+ * transposed.  total receives the number of entries; SPX_ERR_QUEUE_FULL if
+ * above cap (pred then holds the first cap). */
+int spx_graph_host_preds(spx_graph_t g, unsigned* pred_ptr, unsigned* pred, long long cap,
+                         long long* total);
+
 /* Wait for a running graph.  timeout_ns = 0 waits without a host limit (the
  * device watchdog still bounds the run).  info (may be NULL) receives the
  * LAPACK-style column of a failed POTRF, else 0.

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -29,7 +30,42 @@ using namespace spx;
 
 namespace {
 
-enum State { kBuilding = 0, kFrozen = 1, kRunning = 2, kDone = 3 };
+enum State { kBuilding = 0, kFrozen = 1, kRunning = 2, kDone = 3, kStreaming = 4 };
+
+// Per-handle state of the host-side STF derivation (streaming): the members
+// of the last group of accesses and of the group before it.
+struct StreamGroup {
+  int mode = -1;
+  std::vector<uint32_t> last, prev;
+};
+
+// Predecessors of a task with the given access records, by the same rule as
+// the device derivation: a READ / COMMUTATIVE_WRITE / ATOMIC_WRITE joins a
+// last group of the same mode and depends on the group before it; any other
+// access starts a group and depends on every member of the last one.
+// Updates the handle states; returns the predecessors sorted and unique.
+std::vector<uint32_t> stf_preds(std::vector<StreamGroup>& sg, uint32_t v, const uint32_t* handle,
+                                const uint8_t* mode, uint32_t nrec) {
+  std::vector<uint32_t> preds;
+  for (uint32_t i = 0; i < nrec; ++i) {
+    StreamGroup& s = sg[handle[i]];
+    const int m = mode[i];
+    const bool join = s.mode == m && (m == SPX_READ || m == SPX_COMMUTATIVE_WRITE ||
+                                      m == SPX_ATOMIC_WRITE);
+    if (join) {
+      preds.insert(preds.end(), s.prev.begin(), s.prev.end());
+      s.last.push_back(v);
+    } else {
+      preds.insert(preds.end(), s.last.begin(), s.last.end());
+      s.prev.swap(s.last);
+      s.last.assign(1, v);
+      s.mode = m;
+    }
+  }
+  std::sort(preds.begin(), preds.end());
+  preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+  return preds;
+}
 
 struct HandleState {
   uint32_t count = 0;      // accesses so far (next position on the list)
@@ -143,6 +179,17 @@ struct spx_graph {
   cudaGraphExec_t gexec = nullptr;
   // SPX_EXEC_STREAMS: predecessor lists (host), four streams, events
   std::vector<uint32_t> pred_ptr, pred;
+  // streaming (spx_stream_begin .. spx_stream_end)
+  std::vector<StreamGroup> sg;                 // per handle
+  std::vector<std::vector<uint32_t>> spred;    // predecessors per task (relays included)
+  std::vector<uint32_t> sout, salias;          // attachments per task; its relay (or ~0)
+  uint32_t s_cap_tasks = 0, s_cap_tiles = 0, s_pub = 0, s_tiles_up = 0;
+  size_t s_cap_recs = 0, s_cap_preds = 0, s_npreds = 0, s_preds_up = 0, s_recs_up = 0;
+  unsigned long long s_items = 0, s_qcap = 0;
+  int s_fail = 0;                              // first error of the stream
+  StreamCtl* s_ctl = nullptr;                  // host-mapped control block
+  cudaStream_t s_up = nullptr;                 // uploads while the kernel runs
+  size_t s_off_cnt = 0, s_off_succ = 0, s_off_pptr = 0, s_off_pred = 0;
   cudaStream_t xs[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> task_ev;
@@ -309,6 +356,9 @@ int ensure_device(spx_graph* g) {
   return SPX_OK;
 }
 
+void set_dev(spx_graph* g, const Layout& L, size_t N, size_t H, size_t M, size_t E, size_t Q,
+             size_t NG);
+
 // Size the device allocation for the inserted graph and upload it.
 int prepare_device(spx_graph* g, cudaStream_t st) {
   int rc = ensure_device(g);
@@ -368,6 +418,18 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(g->dmem, g->pinned, L.upload_end, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e);
 
+  set_dev(g, L, N, H, M, E, Q, NG);
+  g->lay = L;
+  g->uploaded = true;
+  g->derived = false;
+  g->pred_ptr.clear();  // the four-stream executor reads the new DAG back
+  g->nedges = -1;
+  return SPX_OK;
+}
+
+// Device pointers and sizes of the graph's allocation laid out by L.
+void set_dev(spx_graph* g, const Layout& L, size_t N, size_t H, size_t M, size_t E, size_t Q,
+             size_t NG) {
   char* D = (char*)g->dmem;
   DevGraph& d = g->dg;
   d = DevGraph{};
@@ -410,12 +472,6 @@ int prepare_device(spx_graph* g, cudaStream_t st) {
   d.phase = (uint32_t*)(D + L.phase);
   d.task_group = NG ? (const uint32_t*)(D + L.task_group) : nullptr;
   d.groups = NG ? (GroupState*)(D + L.groups) : nullptr;
-  g->lay = L;
-  g->uploaded = true;
-  g->derived = false;
-  g->pred_ptr.clear();  // the four-stream executor reads the new DAG back
-  g->nedges = -1;
-  return SPX_OK;
 }
 
 // Queues to "empty", tickets, locks and run state to zero.
@@ -425,6 +481,114 @@ int reset_run_state(spx_graph* g, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(D + L.queue[0], 0xFF, L.ff_end - L.queue[0], st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D + L.rs, 0, L.zero_end - L.rs, st);
   return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming: tasks inserted while the persistent kernel runs.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoAlias = 0xFFFFFFFFu;
+
+// Queue entries a task may push (one per phase).
+uint32_t task_entries(const TaskDesc& t) { return t.nphases ? t.nphases : 1u; }
+
+// A predecessor for a new successor: p itself, or, once p's successor slots
+// are all but full, the newest relay behind it: a NOP task that depends on p
+// and takes p's later successors (the relay is appended to the task list).
+uint32_t stream_attach_target(spx_graph* g, uint32_t p) {
+  while (g->salias[p] != kNoAlias) p = g->salias[p];
+  if (g->sout[p] + 1 < kStreamSucc) return p;
+  TaskDesc r{};
+  r.op = SPX_OP_NOP;
+  r.prio = 1;
+  r.flags = kFlagSerial;
+  r.nphases = 1;
+  r.nparts = 1;
+  const uint32_t rid = (uint32_t)g->tasks.size();
+  g->tasks.push_back(r);
+  g->task_rec.push_back((uint32_t)g->rec_handle.size());
+  g->spred.push_back({p});
+  g->sout.push_back(0);
+  g->salias.push_back(kNoAlias);
+  g->sout[p] += 1;
+  g->s_npreds += 1;
+  g->s_items += 1;
+  g->salias[p] = rid;
+  return rid;
+}
+
+// Host-side derivation of the newly inserted task v (and of the relays it
+// needs); checks the stream's capacities.
+int stream_add_task(spx_graph* g, uint32_t v) {
+  const uint32_t r0 = g->task_rec[v], r1 = g->task_rec[v + 1];
+  std::vector<uint32_t> preds =
+      stf_preds(g->sg, v, g->rec_handle.data() + r0, g->rec_mode.data() + r0, r1 - r0);
+  g->spred.resize(g->tasks.size());
+  g->sout.resize(g->tasks.size(), 0);
+  g->salias.resize(g->tasks.size(), kNoAlias);
+  for (uint32_t& p : preds) {
+    p = stream_attach_target(g, p);
+    g->sout[p] += 1;
+  }
+  g->s_npreds += preds.size();
+  g->s_items += task_entries(g->tasks[v]);
+  g->spred[v] = std::move(preds);
+  if (g->tasks.size() > g->s_cap_tasks || g->s_npreds > g->s_cap_preds ||
+      g->s_items > g->s_qcap) {
+    g->s_fail = SPX_ERR_QUEUE_FULL;
+    return g->s_fail;
+  }
+  return SPX_OK;
+}
+
+// Upload the tasks inserted since the last publication (with their tiles,
+// records and predecessor lists) on the upload stream, wait for the copies,
+// then raise the published count the kernel polls.
+int stream_publish(spx_graph* g) {
+  const size_t N = g->tasks.size(), H = g->tiles.size(), M = g->rec_handle.size();
+  if (N == g->s_pub && H == g->s_tiles_up) return SPX_OK;
+  const Layout& L = g->lay;
+  char* D = (char*)g->dmem;
+  cudaStream_t up = g->s_up;
+  cudaError_t e = cudaSuccess;
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(D + off, src, bytes, cudaMemcpyHostToDevice, up);
+  };
+  put(L.tiles + g->s_tiles_up * sizeof(TileDesc), g->tiles.data() + g->s_tiles_up,
+      (H - g->s_tiles_up) * sizeof(TileDesc));
+  put(L.rec_handle + g->s_recs_up * 4, g->rec_handle.data() + g->s_recs_up, (M - g->s_recs_up) * 4);
+  put(L.rec_mode + g->s_recs_up, g->rec_mode.data() + g->s_recs_up, M - g->s_recs_up);
+  put(L.task_rec + (size_t)g->s_pub * 4, g->task_rec.data() + g->s_pub, (N + 1 - g->s_pub) * 4);
+  put(L.tasks + (size_t)g->s_pub * sizeof(TaskDesc), g->tasks.data() + g->s_pub,
+      (N - g->s_pub) * sizeof(TaskDesc));
+  // predecessor lists in task order, offsets continuing the published ones
+  std::vector<uint32_t> ptr, pred;
+  ptr.reserve(N - g->s_pub);
+  size_t at = g->s_preds_up;
+  for (size_t v = g->s_pub; v < N; ++v) {
+    pred.insert(pred.end(), g->spred[v].begin(), g->spred[v].end());
+    at += g->spred[v].size();
+    ptr.push_back((uint32_t)at);
+  }
+  put(g->s_off_pptr + (size_t)(g->s_pub + 1) * 4, ptr.data(), ptr.size() * 4);
+  put(g->s_off_pred + g->s_preds_up * 4, pred.data(), pred.size() * 4);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *(volatile uint32_t*)&g->s_ctl->published = (uint32_t)N;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  g->s_pub = (uint32_t)N;
+  g->s_tiles_up = (uint32_t)H;
+  g->s_recs_up = M;
+  g->s_preds_up = at;
+  return SPX_OK;
+}
+
+// Tell the kernel that no task follows (it drains and exits).
+void stream_close(spx_graph* g) {
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *(volatile uint32_t*)&g->s_ctl->end = 1u;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  g->state = kRunning;
 }
 
 }  // namespace
@@ -483,7 +647,7 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
   if (!g || !dev_ptr || !out_handle || rows < 1 || cols < 1 || ld < cols ||
       dtype < SPX_DT_F64 || dtype > SPX_DT_BF16 || (lowp_ptr && lowp_ld < cols))
     return SPX_ERR_INVALID_ARG;
-  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->state != kBuilding && g->state != kStreaming) return SPX_ERR_STATE;
   const uintptr_t key = (uintptr_t)dev_ptr;
   auto it = g->key_to_handle.find(key);
   if (it != g->key_to_handle.end()) {
@@ -492,6 +656,10 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
       return SPX_ERR_INVALID_ARG;
     *out_handle = it->second;
     return SPX_OK;
+  }
+  if (g->state == kStreaming) {
+    if (lowp_ptr || g->tiles.size() + 1 > g->s_cap_tiles) return SPX_ERR_INVALID_ARG;
+    g->sg.emplace_back();
   }
   const uint32_t h = (uint32_t)g->tiles.size();
   g->tiles.push_back(
@@ -555,7 +723,15 @@ int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned
 int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* modes, int nh,
                     int priority, int prec, unsigned* out_task) {
   if (!g) return SPX_ERR_INVALID_ARG;
-  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->state != kBuilding && g->state != kStreaming) return SPX_ERR_STATE;
+  if (g->state == kStreaming) {
+    if (g->s_fail) return g->s_fail;
+    // the running kernel's family is fixed; the capacities hold
+    const int mode = prec == SPX_F64 ? 0 : prec == SPX_F64_OZAKI ? 2 : 1;
+    if (mode > g->tc_mode || (mode == 1 && g->tc_mode == 2)) return SPX_ERR_INVALID_ARG;
+    if (g->tasks.size() + 1 > g->s_cap_tasks || g->rec_handle.size() + (size_t)nh > g->s_cap_recs)
+      return SPX_ERR_QUEUE_FULL;
+  }
   if (op < 0 || op >= SPX_NUM_OPS || nh < 1 || nh > kMaxHandles || !handles || !modes ||
       priority < 0 || prec < SPX_F64 || prec > SPX_F64_OZAKI)
     return SPX_ERR_INVALID_ARG;
@@ -648,13 +824,15 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   g->uploaded = false;
   if (out_task) *out_task = tid;
+  if (g->state == kStreaming) return stream_add_task(g, tid);
   return SPX_OK;
 }
 
 int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (task >= g->tasks.size()) return SPX_ERR_BAD_HANDLE;
-  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->state != kBuilding && !(g->state == kStreaming && task >= g->s_pub))
+    return SPX_ERR_STATE;
   g->tasks[task].arg = arg;
   g->uploaded = false;
   return SPX_OK;
@@ -663,7 +841,8 @@ int spx_task_set_arg(spx_graph_t g, unsigned task, long long arg) {
 int spx_task_set_scalar(spx_graph_t g, unsigned task, double alpha) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (task >= g->tasks.size()) return SPX_ERR_BAD_HANDLE;
-  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->state != kBuilding && !(g->state == kStreaming && task >= g->s_pub))
+    return SPX_ERR_STATE;
   if (g->tasks[task].op != SPX_OP_AXPY || !(alpha == alpha) || alpha == 0.0 ||
       alpha - alpha != 0.0)
     return SPX_ERR_INVALID_ARG;
@@ -762,7 +941,7 @@ int spx_graph_assign_priorities(spx_graph_t g) {
 
 int spx_graph_derive(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
-  if (g->state == kRunning) return SPX_ERR_STATE;
+  if (g->state == kRunning || g->state == kStreaming) return SPX_ERR_STATE;
   if (g->tasks.empty()) return SPX_ERR_STATE;
   if (g->cfg.priorities == 1 && g->state == kBuilding) {
     const int rc = spx_graph_assign_priorities(g);
@@ -889,7 +1068,7 @@ cudaError_t launch_streams(spx_graph* g, cudaStream_t st) {
 
 int spx_graph_execute(spx_graph_t g, void* stream) {
   if (!g) return SPX_ERR_INVALID_ARG;
-  if (g->state == kRunning || g->state == kDone) return SPX_ERR_STATE;
+  if (g->state == kRunning || g->state == kDone || g->state == kStreaming) return SPX_ERR_STATE;
   if (g->tasks.empty()) return SPX_ERR_STATE;
   g->batch_of = nullptr;  // runs alone from now on
   if (g->cfg.priorities == 1 && g->state == kBuilding) {
@@ -960,6 +1139,158 @@ int spx_graph_execute(spx_graph_t g, void* stream) {
   g->last_stream = st;
   g->state = kRunning;
   return SPX_OK;
+}
+
+int spx_graph_host_preds(spx_graph_t g, unsigned* pred_ptr, unsigned* pred, long long cap,
+                         long long* total) {
+  if (!g || !pred_ptr || (cap > 0 && !pred)) return SPX_ERR_INVALID_ARG;
+  std::vector<StreamGroup> sg(g->tiles.size());
+  const size_t N = g->tasks.size();
+  long long at = 0;
+  pred_ptr[0] = 0;
+  for (size_t v = 0; v < N; ++v) {
+    const uint32_t r0 = g->task_rec[v], r1 = g->task_rec[v + 1];
+    const std::vector<uint32_t> p = stf_preds(sg, (uint32_t)v, g->rec_handle.data() + r0,
+                                              g->rec_mode.data() + r0, r1 - r0);
+    for (uint32_t x : p) {
+      if (at < cap) pred[at] = x;
+      ++at;
+    }
+    pred_ptr[v + 1] = (unsigned)std::min<long long>(at, 0xFFFFFFFFll);
+  }
+  if (total) *total = at;
+  return at > cap ? SPX_ERR_QUEUE_FULL : SPX_OK;
+}
+
+int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
+                     long long max_records, long long max_preds) {
+  if (!g || max_tasks < 1 || max_tiles < 1 || max_records < 1 || max_preds < 1 ||
+      (unsigned)max_tasks > kMaxTasks)
+    return SPX_ERR_INVALID_ARG;
+  if (g->state != kBuilding) return SPX_ERR_STATE;
+  if (g->cfg.executor != SPX_EXEC_PERSISTENT || g->cfg.cuda_graph || g->cfg.no_split)
+    return SPX_ERR_INVALID_ARG;
+  int rc = ensure_device(g);
+  if (rc != SPX_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = (size_t)max_tasks, H = (size_t)max_tiles, M = (size_t)max_records,
+               P = (size_t)max_preds;
+  if (g->tasks.size() > N || g->tiles.size() > H || g->rec_handle.size() > M)
+    return SPX_ERR_INVALID_ARG;
+  // queue entries: one per phase of a task (bounded by the tasks' phases;
+  // 48 per task covers tiles up to 512 and the split ops)
+  const size_t Q = N * 48;
+  if (Q > 0xFFFFFFF0ull) return SPX_ERR_INVALID_ARG;
+  const Layout L = make_layout(N, H, M, 1, Q, g->maps.size(), g->cfg.trace != 0, 0);
+  size_t o = L.total;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1), 256);
+    return at;
+  };
+  g->s_off_cnt = take(N * 4);
+  g->s_off_succ = take(N * kStreamSucc * 4);
+  g->s_off_pptr = take((N + 1) * 4);
+  g->s_off_pred = take(P * 4);
+  cudaError_t e = cudaSuccess;
+  if (g->dmem && o > g->dcap) {
+    if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+    cudaFree(g->dmem);
+    g->dmem = nullptr;
+    g->dcap = 0;
+  }
+  if (!g->dmem) {
+    e = cudaMalloc(&g->dmem, o);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g->dcap = o;
+  }
+  if (!g->s_ctl) {
+    e = cudaHostAlloc((void**)&g->s_ctl, sizeof(StreamCtl), cudaHostAllocMapped);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (!g->s_up) {
+    e = cudaStreamCreateWithFlags(&g->s_up, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  StreamCtl* ctl_dev = nullptr;
+  e = cudaHostGetDevicePointer((void**)&ctl_dev, g->s_ctl, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::memset(g->s_ctl, 0, sizeof(StreamCtl));
+  g->lay = L;
+  set_dev(g, L, N, H, M, 1, Q, 0);
+  char* D = (char*)g->dmem;
+  DevGraph& d = g->dg;
+  d.sctl = ctl_dev;
+  d.succ_cnt = (uint32_t*)(D + g->s_off_cnt);
+  d.succ = (uint32_t*)(D + g->s_off_succ);
+  d.pred_ptr = (const uint32_t*)(D + g->s_off_pptr);
+  d.pred = (const uint32_t*)(D + g->s_off_pred);
+  g->uploaded = false;  // the graph's run layout is the stream's now
+  g->derived = false;
+  g->nedges = -1;
+  g->pred_ptr.clear();
+  // run state, queues, successor slots; the tile maps are fixed from here on
+  rc = reset_run_state(g, g->s_up);
+  if (rc != SPX_OK) return rc;
+  e = cudaMemsetAsync(D + g->s_off_cnt, 0, N * 4, g->s_up);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D + g->s_off_succ, 0xFF, N * kStreamSucc * 4, g->s_up);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D + g->s_off_pptr, 0, 4, g->s_up);
+  if (e == cudaSuccess && !g->maps.empty())
+    e = cudaMemcpyAsync(D + L.maps, g->maps.data(), g->maps.size() * sizeof(CUtensorMap),
+                        cudaMemcpyHostToDevice, g->s_up);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->s_up);
+  if (e != cudaSuccess) return cuda_fail(e);
+  // host-side derivation of the tasks inserted so far
+  g->s_cap_tasks = (uint32_t)N;
+  g->s_cap_tiles = (uint32_t)H;
+  g->s_cap_recs = M;
+  g->s_cap_preds = P;
+  g->s_qcap = Q;
+  g->s_pub = g->s_tiles_up = 0;
+  g->s_recs_up = g->s_preds_up = g->s_npreds = 0;
+  g->s_items = 0;
+  g->s_fail = 0;
+  g->sg.assign(g->tiles.size(), StreamGroup{});
+  g->spred.assign(g->tasks.size(), {});
+  g->sout.assign(g->tasks.size(), 0);
+  g->salias.assign(g->tasks.size(), kNoAlias);
+  g->state = kStreaming;
+  const size_t n0 = g->tasks.size();
+  for (size_t v = 0; v < n0 && rc == SPX_OK; ++v) rc = stream_add_task(g, (uint32_t)v);
+  if (rc == SPX_OK) rc = stream_publish(g);
+  if (rc != SPX_OK) {
+    g->state = kBuilding;
+    return rc;
+  }
+  // the kernel: admits published tasks and runs them until the stream ends
+  e = cudaEventRecord(g->tev[0], st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->tev[1], st);
+  if (e == cudaSuccess) e = launch_persistent(g->dg, g->cfg.num_ctas, g->tc_mode, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->tev[2], st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->host_rs, g->dg.rs, sizeof(RunState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->done_ev, st);
+  if (e != cudaSuccess) {
+    stream_close(g);
+    return cuda_fail(e);
+  }
+  g->last_stream = st;
+  return SPX_OK;
+}
+
+int spx_stream_flush(spx_graph_t g) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state != kStreaming) return SPX_ERR_STATE;
+  if (g->s_fail) return g->s_fail;
+  return stream_publish(g);
+}
+
+int spx_stream_end(spx_graph_t g) {
+  if (!g) return SPX_ERR_INVALID_ARG;
+  if (g->state != kStreaming) return SPX_ERR_STATE;
+  const int rc = g->s_fail ? g->s_fail : stream_publish(g);
+  stream_close(g);
+  return rc;
 }
 
 int spx_graph_wait(spx_graph_t g, unsigned long long timeout_ns, int* info) {
@@ -1141,7 +1472,11 @@ int spx_graph_reset(spx_graph_t g) {
 
 int spx_graph_clear(spx_graph_t g) {
   if (!g) return SPX_ERR_INVALID_ARG;
-  if (g->state == kRunning) return SPX_ERR_STATE;
+  if (g->state == kRunning || g->state == kStreaming) return SPX_ERR_STATE;
+  g->sg.clear();
+  g->spred.clear();
+  g->sout.clear();
+  g->salias.clear();
   g->batch_of = nullptr;
   g->tiles.clear();
   g->tile_dtype.clear();
@@ -1260,6 +1595,7 @@ int spx_batch_execute(spx_graph_t* gs, int ng, void* stream) {
 
 void spx_graph_destroy(spx_graph_t g) {
   if (!g) return;
+  if (g->state == kStreaming) stream_close(g);  // the kernel drains what was published
   if (g->state == kRunning) spx_graph_wait(g, 0, nullptr);
   if (g->batch_of) {  // leave the merged graph's member list
     for (spx_graph*& m : g->batch_of->members)
@@ -1281,6 +1617,8 @@ void spx_graph_destroy(spx_graph_t g) {
   if (g->dmem) cudaFree(g->dmem);
   if (g->pinned) cudaFreeHost(g->pinned);
   if (g->host_rs) cudaFreeHost(g->host_rs);
+  if (g->s_ctl) cudaFreeHost(g->s_ctl);
+  if (g->s_up) cudaStreamDestroy(g->s_up);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   for (int i = 0; i < 4; ++i) {

@@ -118,12 +118,29 @@ __device__ void advance_head(const DevGraph& g, int q, uint32_t t) {
 
 // Pop one queue entry (task << 8 | part), or kExit.  Called by one thread;
 // rnd is the CTA's pseudo-random state for the start of the scan.
-__device__ uint32_t pop(const DevGraph& g, uint32_t& empties, uint32_t& rnd) {
+constexpr uint32_t kAdmit = 0xFFFFFFFCu;  // pop result: tasks claimed for admission (stream)
+constexpr uint32_t kAdmitBatch = 64;     // tasks per admission claim
+
+__device__ uint32_t pop(const DevGraph& g, uint32_t& empties, uint32_t& rnd, uint32_t* adm) {
   RunState* rs = g.rs;
   uint32_t backoff = 32;
   uint32_t iter = 0;
   for (;;) {
     if (ld_volatile(&rs->abort)) return kExit;
+    if (g.sctl) {  // stream: admit newly published tasks first
+      const uint32_t pub = ld_volatile(&g.sctl->published);
+      uint32_t c = ld_volatile(&rs->admit_claim.v);
+      while (c < pub) {
+        const uint32_t e = min(pub, c + kAdmitBatch);
+        const uint32_t prev = atomicCAS(&rs->admit_claim.v, c, e);
+        if (prev == c) {
+          adm[0] = c;
+          adm[1] = e;
+          return kAdmit;
+        }
+        c = prev;
+      }
+    }
     for (int q = 0; q < kQueues; ++q) {
       const uint32_t h0 = ld_volatile(&rs->head[q].v);
       const uint32_t t = min(ld_volatile(&rs->tail[q].v), g.qcap);
@@ -148,7 +165,16 @@ __device__ uint32_t pop(const DevGraph& g, uint32_t& empties, uint32_t& rnd) {
       }
       advance_head(g, q, t);  // every entry looked at was taken
     }
-    if (ld_volatile(&rs->done.v) >= g.ntasks) return kExit;
+    if (g.sctl) {
+      // stream: leave once the host has ended it and every published task
+      // was admitted and has finished
+      if (ld_volatile(&g.sctl->end)) {
+        const uint32_t pub = ld_volatile(&g.sctl->published);
+        if (ld_volatile(&rs->admitted.v) >= pub && ld_volatile(&rs->done.v) >= pub) return kExit;
+      }
+    } else if (ld_volatile(&rs->done.v) >= g.ntasks) {
+      return kExit;
+    }
     ++empties;
     __nanosleep(backoff);
     if (backoff < 1024) backoff <<= 1;
@@ -156,6 +182,37 @@ __device__ uint32_t pop(const DevGraph& g, uint32_t& empties, uint32_t& rnd) {
       set_error(rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
       return kExit;
     }
+  }
+}
+
+// Warp 0: push one queue entry (phase 0 of task s, np parts) for each lane
+// with ready set, one atomicAdd per queue for the whole warp.
+__device__ void push_ready_warp(const DevGraph& g, bool ready, uint32_t s, uint32_t np,
+                                uint32_t pq) {
+  const int lane = threadIdx.x & 31;
+  __threadfence();  // order the predecessors' data before the queue entries
+  for (uint32_t q = 0; q < (uint32_t)kQueues; ++q) {
+    const bool mine = ready && pq == q;
+    const uint32_t cnt = mine ? 1u : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    uint32_t slot = 0;
+    if (lane == 0) {
+      slot = atomicAdd(&g.rs->tail[q].v, total);
+      atomicMax(&g.rs->hiwater, slot + total);
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot + total > g.qcap) {
+      if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+      continue;
+    }
+    if (mine) *(volatile uint32_t*)&g.queue[q][slot + incl - 1] = (s << kPartBits) | (np - 1);
   }
 }
 
@@ -175,30 +232,86 @@ __device__ void release(const DevGraph& g, uint32_t task) {
         pq = graph_queue(g.tasks[s].prio);
       }
     }
-    __threadfence();  // order the predecessors' data before the queue entries
-    for (uint32_t q = 0; q < (uint32_t)kQueues; ++q) {
-      const bool mine = ready && pq == q;
-      const uint32_t cnt = mine ? 1u : 0u;  // one entry: phase 0 of task s
-      uint32_t incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+    push_ready_warp(g, ready, s, np, pq);
+  }
+}
+
+// Stream mode, warp 0: admit tasks a0..a1-1.  Per task (one lane): a guard
+// count of 1 on its remaining predecessors, then for each predecessor p a
+// count of 1 and a slot on p's successor list; when p has finished already
+// (its slot count is closed) the count is taken back.  Dropping the guard
+// last makes the task ready exactly once: here when every predecessor had
+// finished, else in the release of its last predecessor.
+__device__ void admit_tasks(const DevGraph& g, uint32_t a0, uint32_t a1) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = a0; base < a1; base += 32) {
+    const uint32_t v = base + lane;
+    bool ready = false;
+    uint32_t np = 0, pq = 0;
+    if (v < a1) {
+      const TaskDesc t = g.tasks[v];
+      g.remaining[v] = t.nparts;
+      g.phase[v] = 0;
+      g.indeg_w[v] = 1u;
+      __threadfence();
+      for (uint32_t i = g.pred_ptr[v]; i < g.pred_ptr[v + 1]; ++i) {
+        const uint32_t p = g.pred[i];
+        atomicAdd(&g.indeg_w[v], 1u);
+        const uint32_t old = atomicAdd(&g.succ_cnt[p], 1u);
+        if ((old & kSuccClosed) || old >= kStreamSucc) {
+          atomicSub(&g.indeg_w[v], 1u);
+          if (!(old & kSuccClosed)) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+        } else {
+          *(volatile uint32_t*)&g.succ[(size_t)p * kStreamSucc + old] = v;
+        }
       }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      if (total == 0) continue;
-      uint32_t slot = 0;
-      if (lane == 0) {
-        slot = atomicAdd(&g.rs->tail[q].v, total);
-        atomicMax(&g.rs->hiwater, slot + total);
+      __threadfence();
+      ready = atomicSub(&g.indeg_w[v], 1u) == 1u;
+      if (ready) {
+        np = t.nparts;
+        pq = graph_queue(t.prio);
       }
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (slot + total > g.qcap) {
-        if (lane == 0) set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
-        continue;
-      }
-      if (mine) *(volatile uint32_t*)&g.queue[q][slot + incl - 1] = (s << kPartBits) | (np - 1);
     }
+    push_ready_warp(g, ready, v, np, pq);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(&g.rs->admitted.v, min(32u, a1 - base));
+    }
+  }
+  if (lane == 0) touch_progress(g);
+}
+
+// Stream mode, warp 0: close the successor list of a finished task and
+// release the successors attached so far (an attachment reserved before the
+// close but not yet written is waited for, bounded).
+__device__ void release_stream(const DevGraph& g, uint32_t u) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c = 0;
+  if (lane == 0) c = atomicOr(&g.succ_cnt[u], kSuccClosed) & ~kSuccClosed;
+  c = __shfl_sync(0xffffffffu, c, 0);
+  if (c > kStreamSucc) c = kStreamSucc;
+  for (uint32_t base = 0; base < c; base += 32) {
+    const uint32_t idx = base + lane;
+    bool ready = false;
+    uint32_t s = 0, np = 0, pq = 0;
+    if (idx < c) {
+      const uint32_t* slot = &g.succ[(size_t)u * kStreamSucc + idx];
+      uint32_t spins = 0;
+      while ((s = ld_volatile(slot)) == kEmpty) {
+        if ((++spins & 1023u) == 0 && (ld_volatile(&g.rs->abort) || watchdog_expired(g))) break;
+      }
+      if (s != kEmpty) {
+        ready = atomicSub(&g.indeg_w[s], 1u) == 1u;
+        if (ready) {
+          np = g.tasks[s].nparts;
+          pq = graph_queue(g.tasks[s].prio);
+        }
+      } else {
+        set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+      }
+    }
+    push_ready_warp(g, ready, s, np, pq);
   }
 }
 
@@ -655,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     tc_setup(tcs, kMode == 2 ? 512u : kTcCtaCols);
     __syncthreads();
   }
-  __shared__ uint32_t s_item, s_np;
+  __shared__ uint32_t s_item, s_np, s_adm[2];
   __shared__ int s_flag;
   __shared__ SubEntry s_sub;
   __shared__ uint32_t s_scan[kThreads / 32 + 1];
@@ -671,12 +784,18 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
   for (;;) {
     if (tid == 0) {
       if (next != kEmpty) s_item = next;
-      else s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties, rnd);
+      else s_item = kServer ? pop_server(g, empties, &s_sub) : pop(g, empties, rnd, s_adm);
       next = kEmpty;
     }
     __syncthreads();
     const uint32_t item = s_item;
     if (item == kExit) break;
+    if constexpr (!kServer) {
+      if (item == kAdmit) {
+        if (tid < 32) admit_tasks(g, s_adm[0], s_adm[1]);
+        continue;
+      }
+    }
     if constexpr (kServer) {
       if (item == kSubmit) {
         server_admit(g, s_sub, s_scan);
@@ -773,7 +892,8 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         if (tid < 32) {
           if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
           __syncwarp();
-          release(g, u);
+          if (g.sctl) release_stream(g, u);
+          else release(g, u);
           __syncwarp();
           if (tid == 0) {
             __threadfence();

@@ -18,6 +18,19 @@ constexpr uint32_t kMaxParts = 1u << kPartBits;
 constexpr uint32_t kMaxTasks = (1u << (32 - kPartBits)) - 2;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // free queue slot
 constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
+// Streaming (tasks inserted while the persistent kernel runs): successor
+// slots per task, filled by the admission of each successor; a task's slot
+// count gets kSuccClosed when it finishes (later attachments see it done).
+constexpr uint32_t kStreamSucc = 64;
+constexpr uint32_t kSuccClosed = 0x80000000u;
+
+// Host-mapped control block of a stream: the host raises published after
+// the tasks below it (and their tiles, records and predecessor lists) are in
+// device memory, and sets end when no task will follow.
+struct StreamCtl {
+  uint32_t published;
+  uint32_t end;
+};
 // Work queues of a graph run, popped in this order: critical-path tasks
 // (priority >= 2), high priority, normal.  The server keeps two ring queues
 // (critical and high share the first).
@@ -116,6 +129,8 @@ struct RunState {
   Line progress;         // %globaltimer >> 10 at the last finished part
   Line sub_head;         // server: submissions claimed by the device
   Line live;             // server: requests claimed and not finished
+  Line admit_claim;      // stream: tasks claimed for admission
+  Line admitted;         // stream: tasks whose admission finished
   // control words, read by every popping CTA
   alignas(128) uint32_t status;  // SPX_OK or an error / SPX_NOT_SPD
   int32_t info;          // failed POTRF column (1-based)
@@ -192,6 +207,14 @@ struct DevGraph {
   uint32_t* task_req;          // [pool tasks] request slot of a task
   ReqDev* reqs;                // [kMaxRequests]
   HostCtl* ctl;                // device address of the host-mapped block
+  // stream mode (sctl != nullptr): tasks arrive while the kernel runs; their
+  // predecessors come from the host (pred_ptr / pred, in task order) and are
+  // attached on admission to the predecessors' successor slots
+  StreamCtl* sctl;             // device address of the host-mapped block
+  uint32_t* succ_cnt;          // [task capacity] slots taken | kSuccClosed
+  uint32_t* succ;              // [task capacity * kStreamSucc], kEmpty = not written yet
+  const uint32_t* pred_ptr;    // [task capacity + 1]
+  const uint32_t* pred;        // [predecessor capacity]
 };
 
 

@@ -81,6 +81,10 @@ def _load():
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),
         "spx_ozaki_slot_bytes": (LL, [I]),
+        "spx_stream_begin": (I, [P, P, I, I, LL, LL]),
+        "spx_stream_flush": (I, [P]),
+        "spx_stream_end": (I, [P]),
+        "spx_graph_host_preds": (I, [P, P, P, LL, P]),
         "spx_ozaki_register": (I, [P, P, I, I, P]),
         "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, P, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
@@ -196,6 +200,30 @@ class Graph:
 
     def set_arg(self, task: int, arg: int):
         _check(lib.spx_task_set_arg(self._h, task, arg), "spx_task_set_arg")
+
+    # -- streaming --------------------------------------------------------
+    def stream_begin(self, max_tasks, max_tiles, max_records, max_preds, stream=None):
+        """spx_stream_begin: run the tasks inserted so far and keep running;
+        insert more, then stream_flush / stream_end."""
+        _check(lib.spx_stream_begin(self._h, _stream_ptr(stream), max_tasks, max_tiles,
+                                    max_records, max_preds), "spx_stream_begin")
+
+    def stream_flush(self):
+        _check(lib.spx_stream_flush(self._h), "spx_stream_flush")
+
+    def stream_end(self):
+        _check(lib.spx_stream_end(self._h), "spx_stream_end")
+
+    def host_preds(self):
+        """(pred_ptr, pred): the host-side derivation's predecessor lists."""
+        n = self.sizes()[0]
+        ptr = np.zeros(n + 1, np.uint32)
+        total = ctypes.c_longlong()
+        lib.spx_graph_host_preds(self._h, _ptr(ptr), None, 0, ctypes.byref(total))
+        pred = np.zeros(max(1, total.value), np.uint32)
+        _check(lib.spx_graph_host_preds(self._h, _ptr(ptr), _ptr(pred), total.value,
+                                        ctypes.byref(total)), "spx_graph_host_preds")
+        return ptr, pred[:total.value]
 
     # -- running ----------------------------------------------------------
     def derive(self, stream=None):

@@ -1,0 +1,154 @@
+"""Streaming STF on the GPU: tasks inserted while the persistent kernel runs
+(spx_stream_begin / spx_stream_flush / spx_stream_end).
+
+* the tiled Cholesky inserted panel by panel, each panel flushed while the
+  earlier ones run: the factor is bit-identical to the one-shot graph's (the
+  same tile operations on the same data, in an order the dependencies fix);
+* random access lists (three and five modes) inserted in batches of NOP
+  tasks: every edge of the oracle's DAG is respected by the execution
+  tickets (end of the predecessor before the start of the successor) and
+  every task ran;
+* a writer followed by 300 readers and a writer: the first writer's 300
+  successors overflow its 64 successor slots, so relays are appended; the
+  order is still the STF order;
+* errors: insertion beyond the capacity, calls after the end.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2308_15964_b300 import inputs
+from tests._gpu import need_cuda, run_cholesky, spx_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    need_cuda()
+    return spx_mod()
+
+
+def insert_cholesky_panel(S, g, h, T, b, k, n):
+    """The tasks of panel k of the tiled Cholesky (insertion order and
+    priorities of spx_cholesky_insert with look-ahead)."""
+    R, W = S.READ, S.WRITE
+    t = g.insert(S.OP_POTRF, [h[k][k]], [W], 2)
+    g.set_arg(t, k * b)
+    for i in range(k + 1, T):
+        g.insert(S.OP_TRSM, [h[k][k], h[i][k]], [R, W], 2 if i == k + 1 else 1)
+    for i in range(k + 1, T):
+        g.insert(S.OP_SYRK, [h[i][k], h[i][i]], [R, W], 2 if i == k + 1 else 1)
+    for j in range(k + 1, T):
+        for i in range(j + 1, T):
+            g.insert(S.OP_GEMM_NT_SUB, [h[i][k], h[j][k], h[i][j]], [R, R, W],
+                     (2 if i == k + 2 else 1) if j == k + 1 else 0)
+
+
+@pytest.mark.parametrize("n,b,pause", [(1024, 128, 0.002), (2048, 256, 0.0), (1000, 128, 0.01)])
+def test_stream_cholesky_bit_identical(S, n, b, pause):
+    A = inputs.spd_matrix(n, 1.0, seed=n).numpy()
+    rc, info, Lref, _, g0 = run_cholesky(A, b)
+    assert rc == 0 and info == 0
+    g0.close()
+    Ad = torch.from_numpy(A.copy()).cuda()
+    T = -(-n // b)
+    g = S.Graph()
+    h = [[None] * T for _ in range(T)]
+    for i in range(T):
+        for j in range(i + 1):
+            r, c = min(b, n - i * b), min(b, n - j * b)
+            h[i][j] = g.register(Ad[i * b:, j * b:].data_ptr(), r, c, n)
+    g.stream_begin(max_tasks=4096, max_tiles=T * T, max_records=16384, max_preds=32768)
+    for k in range(T):
+        insert_cholesky_panel(S, g, h, T, b, k, n)
+        g.stream_flush()
+        if pause:
+            time.sleep(pause)
+    g.stream_end()
+    rc, info = g.wait()
+    assert rc == 0 and info == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(np.tril(Ad.cpu().numpy()), np.tril(Lref))
+    g.close()
+
+
+@pytest.mark.parametrize("seed,nmodes,batch", [(1, 3, 100), (2, 5, 37), (3, 3, 1), (4, 5, 500)])
+def test_stream_random_lists_tickets(S, seed, nmodes, batch):
+    ntasks = 1500
+    task, key, mode = inputs.random_access_lists(ntasks, 24, 4, seed, nmodes=nmodes)
+    rp, col, _ = O.derive(ntasks, task, key, mode)
+    g = S.Graph()
+    base = 0x7f0000000000
+    handles = {int(k): g.register(base + 4096 * int(k), 8, 8, 8) for k in np.unique(key)}
+    g.stream_begin(max_tasks=4 * ntasks, max_tiles=64, max_records=8 * ntasks,
+                   max_preds=64 * ntasks)
+    ids = []
+    i = 0
+    for t in range(ntasks):
+        j = i
+        while j < len(task) and task[j] == t:
+            j += 1
+        ids.append(g.insert(S.OP_NOP, [handles[int(k)] for k in key[i:j]],
+                            [int(m) for m in mode[i:j]]))
+        i = j
+        if (t + 1) % batch == 0:
+            g.stream_flush()
+    g.stream_end()
+    rc, _ = g.wait()
+    assert rc == 0
+    s, e = g.tickets()
+    ids = np.asarray(ids)
+    assert (e[ids] > 0).all() and (s[ids] != 0xFFFFFFFF).all()
+    for u in range(ntasks):
+        for v in col[rp[u]:rp[u + 1]]:
+            assert e[ids[u]] < s[ids[int(v)]], (u, int(v))
+    g.close()
+
+
+def test_stream_fanout_relays(S):
+    g = S.Graph()
+    hx = g.register(0x7f0000000000, 8, 8, 8)
+    g.stream_begin(max_tasks=1024, max_tiles=4, max_records=1024, max_preds=4096)
+    w0 = g.insert(S.OP_NOP, [hx], [S.WRITE])
+    readers = [g.insert(S.OP_NOP, [hx], [S.READ]) for _ in range(300)]
+    w1 = g.insert(S.OP_NOP, [hx], [S.WRITE])
+    g.stream_end()
+    rc, _ = g.wait()
+    assert rc == 0
+    ntasks = g.sizes()[0]
+    assert ntasks > 302  # relays were appended (300 successors, 64 slots per task)
+    s, e = g.tickets()
+    for r in readers:
+        assert e[w0] < s[r] and e[r] < s[w1]
+    assert (e[:ntasks] > 0).all()
+    g.close()
+
+
+def test_stream_errors(S):
+    g = S.Graph()
+    hx = g.register(0x7f0000000000, 8, 8, 8)
+    g.stream_begin(max_tasks=4, max_tiles=2, max_records=8, max_preds=16)
+    for _ in range(4):
+        g.insert(S.OP_NOP, [hx], [S.WRITE])
+    with pytest.raises(S.SpxError) as ex:
+        g.insert(S.OP_NOP, [hx], [S.WRITE])
+    assert ex.value.code == S.ERR_QUEUE_FULL
+    g.stream_end()
+    rc, _ = g.wait()
+    assert rc == 0
+    with pytest.raises(S.SpxError) as ex:
+        g.stream_flush()
+    assert ex.value.code == S.ERR_STATE
+    with pytest.raises(S.SpxError) as ex:
+        g.insert(S.OP_NOP, [hx], [S.WRITE])
+    assert ex.value.code == S.ERR_STATE
+    g.close()
+    g2 = S.Graph()  # an empty stream
+    g2.stream_begin(max_tasks=8, max_tiles=2, max_records=8, max_preds=8)
+    g2.stream_end()
+    assert g2.wait()[0] == 0
+    g2.close()
