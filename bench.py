@@ -92,7 +92,7 @@ def parse():
                         "splitting (ozaki) or on the FP64 SIMT pipe (f64)")
     p.add_argument("--no-extras", action="store_true", help="skip baseline / e2e / cpu legs")
     p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
-                                                      "overhead", "axpy", "nbody", "splitgemm"],
+                                                      "overhead", "axpy", "nbody", "splitgemm", "stream"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
@@ -267,6 +267,9 @@ def main():
         return
     if args.workload == "tc":
         run_tc(args, world, rank, local)
+        return
+    if args.workload == "stream":
+        run_stream(args, world, rank, local)
         return
     if args.workload == "splitgemm":
         run_splitgemm(args, world, rank, local)
@@ -880,6 +883,98 @@ def run_overhead(args, world, rank, local):
                                   "task (write or commutative write), D in {0, 10, 100} us"},
            "atomics_per_s": {"same_address": same, "distinct_addresses": distinct},
            "rows": rows}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_stream(args, world, rank, local):
+    """Streaming insertion (spx_stream_begin / flush / end) on the split-path
+    Cholesky with substitution panels: the host inserts panel k's tasks one
+    call at a time (Python, spx_task_insert) and flushes them while the
+    kernel runs the earlier panels.  Time to solution by the host clock, from
+    the first insertion to the return of the wait, against inserting every
+    task first (the same Python calls) and then executing, and against the
+    C insertion of the whole graph (spx_cholesky_insert_ozaki) + execution."""
+    import torch
+    from paper_2308_15964_b300 import cholesky, inputs, spx
+    n, b = args.n, args.tile
+    T = -(-n // b)
+    A0 = inputs.spd_matrix(n, args.sigma, seed=2, device="cuda")
+    A = torch.empty_like(A0)
+    store = cholesky.ozaki_store(n, b)
+    slot = spx.lib.spx_ozaki_slot_bytes(b)
+    OZ, R, W = spx.F64_OZAKI, spx.READ, spx.WRITE
+
+    def tiles(g):
+        g.register_ozaki(store.data_ptr(), max(1, T * (T - 1) // 2), b)
+        h = [[None] * T for _ in range(T)]
+        for i in range(T):
+            for j in range(i + 1):
+                lo = store.data_ptr() + (i * (i - 1) // 2 + j) * slot if i > j else 0
+                h[i][j] = g.register(A[i * b:, j * b:].data_ptr(), min(b, n - i * b),
+                                     min(b, n - j * b), n, spx.DT_F64, lo, b if lo else 0)
+        return h
+
+    def panel(g, h, k):
+        t = g.insert(spx.OP_POTRF, [h[k][k]], [W], 2)
+        g.set_arg(t, k * b)
+        for i in range(k + 1, T):
+            g.insert(spx.OP_TRSM, [h[k][k], h[i][k]], [R, W], 2 if i == k + 1 else 1, OZ)
+        for i in range(k + 1, T):
+            g.insert(spx.OP_SYRK, [h[i][k], h[i][i]], [R, W], 2 if i == k + 1 else 1, OZ)
+        for j in range(k + 1, T):
+            for i in range(j + 1, T):
+                g.insert(spx.OP_GEMM_NT_SUB, [h[i][k], h[j][k], h[i][j]], [R, R, W],
+                         (2 if i == k + 2 else 1) if j == k + 1 else 0, OZ)
+
+    ntasks = T + T * (T - 1) + T * (T - 1) * (T - 2) // 6
+    rows = {"streamed": [], "insert_then_execute": [], "c_insert_then_execute": []}
+    L = {}
+    for it in range(args.warmup + args.steps):
+        for mode in rows:
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            g = spx.Graph()
+            h = tiles(g) if mode != "c_insert_then_execute" else None
+            t0 = time.perf_counter()
+            if mode == "streamed":
+                panel(g, h, 0)  # fixes the kernel family (split tasks)
+                g.stream_begin(max_tasks=2 * ntasks + 4 * T, max_tiles=T * T, max_records=4 * ntasks,
+                               max_preds=16 * ntasks)
+                for k in range(1, T):
+                    panel(g, h, k)
+                    g.stream_flush()
+                g.stream_end()
+                rc, _ = g.wait()
+            elif mode == "insert_then_execute":
+                for k in range(T):
+                    panel(g, h, k)
+                rc, _ = g.run()
+            else:
+                cholesky.cholesky_ozaki_graph(g, A, b, S=store)
+                rc, _ = g.run()
+            dt = time.perf_counter() - t0
+            assert rc == spx.OK, (mode, rc)
+            g.close()
+            if it >= args.warmup:
+                rows[mode].append(dt)
+            if it == args.warmup + args.steps - 1:
+                L[mode] = torch.tril(A).clone()
+    flops = n ** 3 / 3.0
+    same = all(torch.equal(L["streamed"], L[m]) for m in L)
+    out = {"metric": "Cholesky GFLOP/s, time to solution with streamed insertion (host clock)",
+           "value": flops / statistics.mean(rows["streamed"]) / 1e9, "unit": "GFLOP/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.mean(rows["streamed"]), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split products)",
+           "data": "synthetic",
+           "config": {"workload": f"split-path Cholesky n={n} tile={b} ({ntasks} tasks), tasks "
+                                  "inserted from Python one call each, flushed per panel",
+                      "n": n, "tile": b, "tasks": ntasks},
+           "rows_ms": {m: {"mean": 1e3 * statistics.mean(v), "p99": 1e3 * float(np.percentile(v, 99))}
+                       for m, v in rows.items()},
+           "factors_bit_identical": bool(same),
+           "gpu_launches": 1}
     if rank == 0:
         print(json.dumps(out))
 

@@ -385,10 +385,11 @@ int spx_batch_execute(spx_graph_t* gs, int ng, void* stream);
 /* Streaming (paper, section "Background" / "Task insertion": tasks are
  * inserted while the workers execute earlier ones).  spx_stream_begin
  * launches the persistent kernel on the tasks inserted so far (possibly none)
- * and keeps it running; spx_task_insert (and spx_tile_register, for tiles
- * without a low-precision copy) may then be called while it runs, and
- * spx_stream_flush hands the tasks inserted since the last flush to the
- * kernel; spx_stream_end flushes and lets the kernel finish and exit, after
+ * and keeps it running; spx_task_insert (on tiles registered before the
+ * begin) may then be called while it runs, and spx_stream_flush hands the
+ * tasks inserted since the last flush to the kernel (asynchronously: their
+ * descriptors and predecessor lists are copied by the copy engine, then the
+ * count the kernel polls is raised on the same stream); spx_stream_end flushes and lets the kernel finish and exit, after
  * which spx_graph_wait returns the run's status as for spx_graph_execute.
  *
  * Dependencies are derived on the host as each task is inserted, by the same
@@ -399,13 +400,13 @@ int spx_batch_execute(spx_graph_t* gs, int ng, void* stream);
  * successors) and runs it when they have finished.  Results equal running
  * the tasks in insertion order.
  *   max_tasks, max_tiles, max_records, max_preds: capacities for the whole
- *   stream (tasks including relays; access records; predecessor entries).
+ *   stream (tasks including relays; tiles, all registered before the begin;
+ *   access records; predecessor entries).
  *   The graph's configuration must be the persistent executor without CUDA
  *   graph replay or no_split; critical-path priorities are not assigned.
  *   The kernel family (FP64, tensor-core or split tasks) is fixed by the
  *   tasks inserted before the begin: a later task that needs another family
- *   is refused.  Low-precision matrices and split stores must be registered
- *   before the begin.
+ *   is refused.
  *   The device watchdog (cfg.watchdog_ns) also bounds the host: the kernel
  *   leaves with SPX_ERR_TIMEOUT if no task finishes and none is published
  *   for that long before the end.

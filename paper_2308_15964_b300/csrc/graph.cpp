@@ -187,7 +187,8 @@ struct spx_graph {
   size_t s_cap_recs = 0, s_cap_preds = 0, s_npreds = 0, s_preds_up = 0, s_recs_up = 0;
   unsigned long long s_items = 0, s_qcap = 0;
   int s_fail = 0;                              // first error of the stream
-  StreamCtl* s_ctl = nullptr;                  // host-mapped control block
+  StreamCtl s_ctl_host{};                      // the values last sent to the device
+  StreamCtl* s_ctl = nullptr;                  // the kernel's copy (device memory)
   cudaStream_t s_up = nullptr;                 // uploads while the kernel runs
   size_t s_off_cnt = 0, s_off_succ = 0, s_off_pptr = 0, s_off_pred = 0;
   cudaStream_t xs[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -571,11 +572,11 @@ int stream_publish(spx_graph* g) {
   }
   put(g->s_off_pptr + (size_t)(g->s_pub + 1) * 4, ptr.data(), ptr.size() * 4);
   put(g->s_off_pred + g->s_preds_up * 4, pred.data(), pred.size() * 4);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+  // the count the kernel polls, written after the data on the same stream
+  // (copies from pageable memory return once the source has been staged)
+  g->s_ctl_host.published = (uint32_t)N;
+  put((size_t)((char*)&g->s_ctl->published - D), &g->s_ctl_host.published, 4);
   if (e != cudaSuccess) return cuda_fail(e);
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  *(volatile uint32_t*)&g->s_ctl->published = (uint32_t)N;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
   g->s_pub = (uint32_t)N;
   g->s_tiles_up = (uint32_t)H;
   g->s_recs_up = M;
@@ -585,9 +586,8 @@ int stream_publish(spx_graph* g) {
 
 // Tell the kernel that no task follows (it drains and exits).
 void stream_close(spx_graph* g) {
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  *(volatile uint32_t*)&g->s_ctl->end = 1u;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  g->s_ctl_host.end = 1u;
+  cudaMemcpyAsync(&g->s_ctl->end, &g->s_ctl_host.end, 4, cudaMemcpyHostToDevice, g->s_up);
   g->state = kRunning;
 }
 
@@ -657,10 +657,7 @@ int spx_tile_register(spx_graph_t g, void* dev_ptr, int rows, int cols, int ld, 
     *out_handle = it->second;
     return SPX_OK;
   }
-  if (g->state == kStreaming) {
-    if (lowp_ptr || g->tiles.size() + 1 > g->s_cap_tiles) return SPX_ERR_INVALID_ARG;
-    g->sg.emplace_back();
-  }
+  if (g->state == kStreaming) return SPX_ERR_STATE;  // tiles come before the stream
   const uint32_t h = (uint32_t)g->tiles.size();
   g->tiles.push_back(
       TileDesc{dev_ptr, lowp_ptr, rows, cols, ld, lowp_ptr ? lowp_ld : 0, -1, 0, 0, dtype});
@@ -1177,6 +1174,11 @@ int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
                P = (size_t)max_preds;
   if (g->tasks.size() > N || g->tiles.size() > H || g->rec_handle.size() > M)
     return SPX_ERR_INVALID_ARG;
+  // A tile's copy position is resolved at its first low-precision / split
+  // use; tile descriptors are uploaded as they are registered, so resolve
+  // them all now (no tile with a copy may be registered while streaming).
+  for (uint32_t h = 0; h < g->tiles.size(); ++h)
+    if (g->tiles[h].lowp && !resolve_lowp(g, h)) return SPX_ERR_INVALID_ARG;
   // queue entries: one per phase of a task (bounded by the tasks' phases;
   // 48 per task covers tiles up to 512 and the split ops)
   const size_t Q = N * 48;
@@ -1192,6 +1194,7 @@ int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
   g->s_off_succ = take(N * kStreamSucc * 4);
   g->s_off_pptr = take((N + 1) * 4);
   g->s_off_pred = take(P * 4);
+  const size_t off_ctl = take(sizeof(StreamCtl));
   cudaError_t e = cudaSuccess;
   if (g->dmem && o > g->dcap) {
     if (g->last_stream) cudaStreamSynchronize(g->last_stream);
@@ -1204,23 +1207,17 @@ int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
     if (e != cudaSuccess) return cuda_fail(e);
     g->dcap = o;
   }
-  if (!g->s_ctl) {
-    e = cudaHostAlloc((void**)&g->s_ctl, sizeof(StreamCtl), cudaHostAllocMapped);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
   if (!g->s_up) {
     e = cudaStreamCreateWithFlags(&g->s_up, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  StreamCtl* ctl_dev = nullptr;
-  e = cudaHostGetDevicePointer((void**)&ctl_dev, g->s_ctl, 0);
-  if (e != cudaSuccess) return cuda_fail(e);
-  std::memset(g->s_ctl, 0, sizeof(StreamCtl));
+  g->s_ctl = (StreamCtl*)((char*)g->dmem + off_ctl);
+  g->s_ctl_host = StreamCtl{};
   g->lay = L;
   set_dev(g, L, N, H, M, 1, Q, 0);
   char* D = (char*)g->dmem;
   DevGraph& d = g->dg;
-  d.sctl = ctl_dev;
+  d.sctl = g->s_ctl;
   d.succ_cnt = (uint32_t*)(D + g->s_off_cnt);
   d.succ = (uint32_t*)(D + g->s_off_succ);
   d.pred_ptr = (const uint32_t*)(D + g->s_off_pptr);
@@ -1235,6 +1232,7 @@ int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
   e = cudaMemsetAsync(D + g->s_off_cnt, 0, N * 4, g->s_up);
   if (e == cudaSuccess) e = cudaMemsetAsync(D + g->s_off_succ, 0xFF, N * kStreamSucc * 4, g->s_up);
   if (e == cudaSuccess) e = cudaMemsetAsync(D + g->s_off_pptr, 0, 4, g->s_up);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D + off_ctl, 0, sizeof(StreamCtl), g->s_up);
   if (e == cudaSuccess && !g->maps.empty())
     e = cudaMemcpyAsync(D + L.maps, g->maps.data(), g->maps.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice, g->s_up);
@@ -1613,11 +1611,11 @@ void spx_graph_destroy(spx_graph_t g) {
     g->batch = nullptr;
   }
   if (g->host_groups) cudaFreeHost(g->host_groups);
+  if (g->s_up) cudaStreamSynchronize(g->s_up);
   if (g->last_stream) cudaStreamSynchronize(g->last_stream);
   if (g->dmem) cudaFree(g->dmem);
   if (g->pinned) cudaFreeHost(g->pinned);
   if (g->host_rs) cudaFreeHost(g->host_rs);
-  if (g->s_ctl) cudaFreeHost(g->s_ctl);
   if (g->s_up) cudaStreamDestroy(g->s_up);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);

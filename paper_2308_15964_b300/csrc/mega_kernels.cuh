@@ -64,6 +64,20 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
   return *(const volatile uint32_t*)p;
 }
 
+// Task descriptors and access records are read from L2 (ld.global.cg): in
+// stream mode they are uploaded while the kernel runs, and a line cached in
+// an SM's L1 from an earlier batch may hold older bytes of them.
+__device__ __forceinline__ TaskDesc load_task(const TaskDesc* p) {
+  static_assert(sizeof(TaskDesc) == 32, "two 16-byte loads");
+  const uint4 a = __ldcg(reinterpret_cast<const uint4*>(p));
+  const uint4 b = __ldcg(reinterpret_cast<const uint4*>(p) + 1);
+  TaskDesc t;
+  uint4* d = reinterpret_cast<uint4*>(&t);
+  d[0] = a;
+  d[1] = b;
+  return t;
+}
+
 __device__ __forceinline__ void set_error(RunState* rs, uint32_t code, int info) {
   if (atomicCAS(&rs->status, 0u, code) == 0u) rs->info = info;
   atomicExch(&rs->abort, 1u);
@@ -228,8 +242,9 @@ __device__ void release(const DevGraph& g, uint32_t task) {
       s = g.col[idx];
       ready = atomicSub(&g.indeg_w[s], 1u) == 1u;
       if (ready) {
-        np = g.tasks[s].nparts;
-        pq = graph_queue(g.tasks[s].prio);
+        const TaskDesc ts = load_task(&g.tasks[s]);
+        np = ts.nparts;
+        pq = graph_queue(ts.prio);
       }
     }
     push_ready_warp(g, ready, s, np, pq);
@@ -249,13 +264,14 @@ __device__ void admit_tasks(const DevGraph& g, uint32_t a0, uint32_t a1) {
     bool ready = false;
     uint32_t np = 0, pq = 0;
     if (v < a1) {
-      const TaskDesc t = g.tasks[v];
+      const TaskDesc t = load_task(&g.tasks[v]);
       g.remaining[v] = t.nparts;
       g.phase[v] = 0;
       g.indeg_w[v] = 1u;
       __threadfence();
-      for (uint32_t i = g.pred_ptr[v]; i < g.pred_ptr[v + 1]; ++i) {
-        const uint32_t p = g.pred[i];
+      const uint32_t i1 = __ldcg(&g.pred_ptr[v + 1]);
+      for (uint32_t i = __ldcg(&g.pred_ptr[v]); i < i1; ++i) {
+        const uint32_t p = __ldcg(&g.pred[i]);
         atomicAdd(&g.indeg_w[v], 1u);
         const uint32_t old = atomicAdd(&g.succ_cnt[p], 1u);
         if ((old & kSuccClosed) || old >= kStreamSucc) {
@@ -304,8 +320,9 @@ __device__ void release_stream(const DevGraph& g, uint32_t u) {
       if (s != kEmpty) {
         ready = atomicSub(&g.indeg_w[s], 1u) == 1u;
         if (ready) {
-          np = g.tasks[s].nparts;
-          pq = graph_queue(g.tasks[s].prio);
+          const TaskDesc ts = load_task(&g.tasks[s]);
+          np = ts.nparts;
+          pq = graph_queue(ts.prio);
         }
       } else {
         set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
@@ -362,6 +379,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
         if constexpr (kMode == 2) {
           if (t.prec == SPX_F64_OZAKI) {
             const TileDesc &Lt = T[t.h[0]], &Ct = T[t.h[1]];
+            if (Lt.lmap < 0) return -1;
             return oz_product_units(g, Lt, Lt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, true,
                                     t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
                        ? 0
@@ -369,6 +387,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
           }
         }
         if (lowp) {
+          if (T[t.h[0]].lmap < 0) return -1;
           const bool ok = t.prec == SPX_BF16 ? op_tc_syrk<true>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc)
                                              : op_tc_syrk<false>(g, T[t.h[0]], T[t.h[1]], u0, u1, tc);
           return ok ? 0 : -2;
@@ -381,6 +400,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
         if constexpr (kMode == 2) {
           if (t.prec == SPX_F64_OZAKI) {
             const TileDesc &At = T[t.h[0]], &Bt = T[t.h[1]], &Ct = T[t.h[2]];
+            if (At.lmap < 0 || Bt.lmap < 0) return -1;
             return oz_product_units(g, At, Bt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, false,
                                     t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
                        ? 0
@@ -388,6 +408,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
           }
         }
         if (lowp) {
+          if (T[t.h[0]].lmap < 0 || T[t.h[1]].lmap < 0) return -1;
           const bool ok =
               t.prec == SPX_BF16
                   ? op_tc_gemm<true>(g, T[t.h[0]], T[t.h[1]], T[t.h[2]], u0, u1, tc)
@@ -455,6 +476,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
             }
             // A <- A V^T: the product reads A's and V's slots, then stores A
             const TileDesc &Vt = T[t.h[0]], &At = T[t.h[1]];
+            if (At.lmap < 0 || Vt.lmap < 0) return -1;
             return oz_product_units(g, At, Vt, (double*)At.ptr, At.ld, At.rows, At.cols, false,
                                     t.flags & kFlagFine, true, u0, u1, tc.st, tc.oz)
                        ? 0
@@ -532,9 +554,10 @@ __device__ void push_phase(const DevGraph& g, uint32_t u, uint32_t np, uint32_t 
 // Take the COMMUTATIVE_WRITE locks of task u in ascending handle order
 // (records of a task are sorted by handle).  One thread.  False on abort.
 __device__ bool lock_comm(const DevGraph& g, uint32_t u) {
-  for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r) {
-    if (g.rec_mode[r] != SPX_COMMUTATIVE_WRITE) continue;
-    uint32_t* lk = &g.locks[g.rec_handle[r]];
+  const uint32_t r1 = __ldcg(&g.task_rec[u + 1]);
+  for (uint32_t r = __ldcg(&g.task_rec[u]); r < r1; ++r) {
+    if (__ldcg(&g.rec_mode[r]) != SPX_COMMUTATIVE_WRITE) continue;
+    uint32_t* lk = &g.locks[__ldcg(&g.rec_handle[r])];
     uint32_t spins = 0;
     while (atomicCAS(lk, 0u, u + 1) != 0u) {
       __nanosleep(64);
@@ -553,8 +576,10 @@ __device__ bool lock_comm(const DevGraph& g, uint32_t u) {
 
 __device__ void unlock_comm(const DevGraph& g, uint32_t u) {
   __threadfence();
-  for (uint32_t r = g.task_rec[u]; r < g.task_rec[u + 1]; ++r)
-    if (g.rec_mode[r] == SPX_COMMUTATIVE_WRITE) atomicExch(&g.locks[g.rec_handle[r]], 0u);
+  const uint32_t r1 = __ldcg(&g.task_rec[u + 1]);
+  for (uint32_t r = __ldcg(&g.task_rec[u]); r < r1; ++r)
+    if (__ldcg(&g.rec_mode[r]) == SPX_COMMUTATIVE_WRITE)
+      atomicExch(&g.locks[__ldcg(&g.rec_handle[r])], 0u);
 }
 
 
@@ -803,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
       }
     }
     const uint32_t u = item >> kPartBits, part = item & (kMaxParts - 1);
-    const TaskDesc t = g.tasks[u];
+    const TaskDesc t = load_task(&g.tasks[u]);
     // the phase was written before its parts were pushed (and fenced)
     const uint32_t phase = t.nphases > 1 ? ld_volatile(&g.phase[u]) : 0u;
     const uint32_t req = kServer ? g.task_req[u] : (g.task_group ? g.task_group[u] : 0u);

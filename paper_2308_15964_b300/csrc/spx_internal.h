@@ -24,9 +24,10 @@ constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
 constexpr uint32_t kStreamSucc = 64;
 constexpr uint32_t kSuccClosed = 0x80000000u;
 
-// Host-mapped control block of a stream: the host raises published after
-// the tasks below it (and their tiles, records and predecessor lists) are in
-// device memory, and sets end when no task will follow.
+// Control block of a stream, in device memory: the host's copy engine raises
+// published after the tasks below it (their descriptors, records and
+// predecessor lists) were written, on the same stream, and sets end when no
+// task will follow.
 struct StreamCtl {
   uint32_t published;
   uint32_t end;
@@ -210,7 +211,7 @@ struct DevGraph {
   // stream mode (sctl != nullptr): tasks arrive while the kernel runs; their
   // predecessors come from the host (pred_ptr / pred, in task order) and are
   // attached on admission to the predecessors' successor slots
-  StreamCtl* sctl;             // device address of the host-mapped block
+  StreamCtl* sctl;             // the stream's control block
   uint32_t* succ_cnt;          // [task capacity] slots taken | kSuccClosed
   uint32_t* succ;              // [task capacity * kStreamSucc], kEmpty = not written yet
   const uint32_t* pred_ptr;    // [task capacity + 1]

@@ -152,3 +152,55 @@ def test_stream_errors(S):
     g2.stream_end()
     assert g2.wait()[0] == 0
     g2.close()
+
+
+def test_stream_split_cholesky_bit_identical(S):
+    """The split path streamed panel by panel (tiles with split slots, the
+    kernel family fixed by the first panel inserted before the begin) gives
+    the one-shot split graph's factor bit for bit."""
+    from paper_2308_15964_b300 import cholesky
+    n, b = 1536, 256
+    T = n // b
+    A = inputs.spd_matrix(n, 1.0, seed=5).numpy()
+    Aref = torch.from_numpy(A.copy()).cuda()
+    g0 = S.Graph()
+    cholesky.cholesky_ozaki_graph(g0, Aref, b)
+    assert g0.run()[0] == 0
+    torch.cuda.synchronize()
+    Lref = np.tril(Aref.cpu().numpy())
+    g0.close()
+    Ad = torch.from_numpy(A.copy()).cuda()
+    store = cholesky.ozaki_store(n, b)
+    slot = S.lib.spx_ozaki_slot_bytes(b)
+    g = S.Graph()
+    g.register_ozaki(store.data_ptr(), T * (T - 1) // 2, b)
+    h = [[None] * T for _ in range(T)]
+    for i in range(T):
+        for j in range(i + 1):
+            lo = store.data_ptr() + (i * (i - 1) // 2 + j) * slot if i > j else 0
+            h[i][j] = g.register(Ad[i * b:, j * b:].data_ptr(), b, b, n, S.DT_F64, lo, b if lo else 0)
+    R, W, OZ = S.READ, S.WRITE, S.F64_OZAKI
+
+    def panel(k):
+        t = g.insert(S.OP_POTRF, [h[k][k]], [W], 2)
+        g.set_arg(t, k * b)
+        for i in range(k + 1, T):
+            g.insert(S.OP_TRSM, [h[k][k], h[i][k]], [R, W], 2 if i == k + 1 else 1, OZ)
+        for i in range(k + 1, T):
+            g.insert(S.OP_SYRK, [h[i][k], h[i][i]], [R, W], 2 if i == k + 1 else 1, OZ)
+        for j in range(k + 1, T):
+            for i in range(j + 1, T):
+                g.insert(S.OP_GEMM_NT_SUB, [h[i][k], h[j][k], h[i][j]], [R, R, W],
+                         (2 if i == k + 2 else 1) if j == k + 1 else 0, OZ)
+
+    panel(0)
+    g.stream_begin(max_tasks=512, max_tiles=T * T, max_records=2048, max_preds=4096)
+    for k in range(1, T):
+        panel(k)
+        g.stream_flush()
+    g.stream_end()
+    rc, info = g.wait()
+    assert rc == 0 and info == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(np.tril(Ad.cpu().numpy()), Lref)
+    g.close()
