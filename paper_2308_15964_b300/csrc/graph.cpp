@@ -81,7 +81,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t tasks, tiles, maps, rec_handle, rec_seq, rec_mode, task_rec, task_group, upload_end;
   size_t queue[kQueues], t_start, ff_end;
-  size_t rs, locks, t_end, trace, phase, qclaim[kQueues], groups, zero_end;
+  size_t rs, locks, t_end, trace, phase, qclaim[kQueues], groups, wl_lock, wl_head, wl_tail, wnext,
+      comm_next, zero_end;
   size_t hptr, s_task, s_mode, s_first, rec_pos, gid, gpos, ucount, row_ptr, col, indeg,
       indeg_w, remaining, total;
 };
@@ -114,6 +115,11 @@ Layout make_layout(size_t N, size_t H, size_t M, size_t E, size_t Q, size_t NM, 
   L.phase = take(N * 4);
   for (int q = 0; q < kQueues; ++q) L.qclaim[q] = take(Q * 4);
   L.groups = take(NG * sizeof(GroupState));
+  L.wl_lock = take(H * 4);
+  L.wl_head = take(H * 4);
+  L.wl_tail = take(H * 4);
+  L.wnext = take(N * 4);
+  L.comm_next = take(N * 4);
   L.zero_end = o;
   L.hptr = take((H + 1) * 4);
   L.s_task = take(M * 4);
@@ -473,6 +479,11 @@ void set_dev(spx_graph* g, const Layout& L, size_t N, size_t H, size_t M, size_t
   d.phase = (uint32_t*)(D + L.phase);
   d.task_group = NG ? (const uint32_t*)(D + L.task_group) : nullptr;
   d.groups = NG ? (GroupState*)(D + L.groups) : nullptr;
+  d.wl_lock = (uint32_t*)(D + L.wl_lock);
+  d.wl_head = (uint32_t*)(D + L.wl_head);
+  d.wl_tail = (uint32_t*)(D + L.wl_tail);
+  d.wnext = (uint32_t*)(D + L.wnext);
+  d.comm_next = (uint32_t*)(D + L.comm_next);
 }
 
 // Queues to "empty", tickets, locks and run state to zero.
@@ -781,17 +792,18 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   for (int i = 0; i < 3; ++i) t.h[i] = i < nh ? handles[i] : 0;
   uint32_t items = 1;  // queue entries over all phases
-  if (g->cfg.no_split || (t.flags & kFlagComm)) {
+  if (g->cfg.no_split) {
     t.flags |= kFlagSerial;
     t.nphases = 1;
     t.nparts = 1;
   } else {
-    t.nphases = op_phases(op, prec, g->tiles.data(), t.h);
-    const bool fine = t.flags & kFlagFine;
-    t.nparts = phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, 0, fine));
+    t.nphases = task_phases(t, g->tiles.data());
+    t.nparts = phase_parts(task_phase_units(t, g->tiles.data(), 0));
     items = 0;
     for (uint32_t ph = 0; ph < t.nphases; ++ph)
-      items += phase_parts(op_phase_units(op, prec, g->tiles.data(), t.h, ph, fine));
+      items += phase_parts(task_phase_units(t, g->tiles.data(), ph));
+    if (t.flags & kFlagComm)  // an acquire entry again for each lock handed over
+      for (int i = 0; i < k; ++i) items += mm[i] == SPX_COMMUTATIVE_WRITE ? 1u : 0u;
   }
   t.arg = 0;
 
@@ -857,7 +869,10 @@ int spx_graph_assign_priorities(spx_graph_t g) {
   if (N == 0) return SPX_ERR_STATE;
   // weight: phases of the task (its dependent steps; serial tasks one)
   std::vector<double> w(N), tl(N), bl(N);
-  for (size_t u = 0; u < N; ++u) w[u] = std::max<uint32_t>(g->tasks[u].nphases, 1);
+  for (size_t u = 0; u < N; ++u) {  // the op's phases (a commutative task's lock phase aside)
+    const TaskDesc& t = g->tasks[u];
+    w[u] = (t.flags & kFlagSerial) ? 1.0 : std::max<uint32_t>(op_phases(t.op, t.prec, g->tiles.data(), t.h), 1);
+  }
   auto groups = [](int m) {
     return m == SPX_READ || m == SPX_COMMUTATIVE_WRITE || m == SPX_ATOMIC_WRITE;
   };
@@ -919,11 +934,13 @@ int spx_graph_assign_priorities(spx_graph_t g) {
     uint32_t items = 1;
     if (!(t.flags & kFlagSerial)) {
       t.flags = (uint8_t)((t.flags & ~kFlagFine) | (cls == 2 ? kFlagFine : 0));
-      const bool fine = cls == 2;
-      t.nparts = phase_parts(op_phase_units(t.op, t.prec, g->tiles.data(), t.h, 0, fine));
+      t.nparts = phase_parts(task_phase_units(t, g->tiles.data(), 0));
       items = 0;
       for (uint32_t ph = 0; ph < t.nphases; ++ph)
-        items += phase_parts(op_phase_units(t.op, t.prec, g->tiles.data(), t.h, ph, fine));
+        items += phase_parts(task_phase_units(t, g->tiles.data(), ph));
+      if (t.flags & kFlagComm)
+        for (uint32_t r = g->task_rec[u]; r < g->task_rec[u + 1]; ++r)
+          items += g->rec_mode[r] == SPX_COMMUTATIVE_WRITE ? 1u : 0u;
     }
     g->items[graph_queue(t.prio)] += items;
   }

@@ -124,7 +124,7 @@ cudaError_t launch_task(const DevGraph& g, uint32_t u, const TaskDesc& t,
     const uint32_t np =
         (t.flags & kFlagSerial)
             ? 1u
-            : phase_parts(op_phase_units(t.op, t.prec, host_tiles, t.h, ph, t.flags & kFlagFine));
+            : phase_parts(task_phase_units(t, host_tiles, ph));
     if (mode == 2) mega_launch_task_oz((int)np, smem_bytes(2), st, g, u, ph);
     else if (mode == 1) mega_launch_task_tc((int)np, smem_bytes(1), st, g, u, ph);
     else mega_launch_task_f64((int)np, smem_bytes(0), st, g, u, ph);

@@ -512,10 +512,22 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
 
 // Run part `part` of phase `phase`; a serial task runs all of its phases
 // and units here, in order.
+constexpr int kParked = -100;  // run_part: the task waits on a lock's list (no part finished)
+__device__ int acquire_comm(const DevGraph& g, uint32_t u, const TaskDesc& t);
+
 template <int kMode>
 __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, uint32_t part,
-                        F64Smem& s, TcCtx& tc) {
+                        F64Smem& s, TcCtx& tc, uint32_t u, bool locks) {
   const TileDesc* T = g.tiles;
+  if (comm_acquire_phase(t)) {
+    if (phase == 0) {  // the lock phase (the per-task executors run tasks one by one)
+      __shared__ int s_got;
+      if (threadIdx.x == 0) s_got = locks ? acquire_comm(g, u, t) : 1;
+      __syncthreads();
+      return s_got > 0 ? 0 : (s_got == 0 ? kParked : -2);
+    }
+    --phase;
+  }
   if (t.flags & kFlagSerial) {
     const uint32_t nph = op_phases(t.op, t.prec, T, t.h);
     for (uint32_t ph = 0; ph < nph; ++ph) {
@@ -528,6 +540,7 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
   }
   const uint32_t units = op_phase_units(t.op, t.prec, T, t.h, phase, t.flags & kFlagFine);
   const uint32_t parts = phase_parts(units);
+  (void)u;
   const uint32_t u0 = (uint32_t)((unsigned long long)part * units / parts);
   const uint32_t u1 = (uint32_t)((unsigned long long)(part + 1) * units / parts);
   return run_units<kMode>(g, t, phase, u0, u1, s, tc);
@@ -580,6 +593,96 @@ __device__ void unlock_comm(const DevGraph& g, uint32_t u) {
   for (uint32_t r = __ldcg(&g.task_rec[u]); r < r1; ++r)
     if (__ldcg(&g.rec_mode[r]) == SPX_COMMUTATIVE_WRITE)
       atomicExch(&g.locks[__ldcg(&g.rec_handle[r])], 0u);
+}
+
+// Short spin lock guarding a tile's wait list (one thread).  False on abort
+// or watchdog.
+__device__ bool wl_enter(const DevGraph& g, uint32_t h) {
+  uint32_t spins = 0;
+  while (atomicCAS(&g.wl_lock[h], 0u, 1u) != 0u) {
+    if ((++spins & 255u) == 0) {
+      if (ld_volatile(&g.rs->abort)) return false;
+      if (watchdog_expired(g)) {
+        set_error(g.rs, (uint32_t)SPX_ERR_TIMEOUT, 0);
+        return false;
+      }
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+__device__ void wl_leave(const DevGraph& g, uint32_t h) {
+  __threadfence();
+  atomicExch(&g.wl_lock[h], 0u);
+}
+
+// Lock phase of a commutative task u (graph runs): take its
+// COMMUTATIVE_WRITE locks in ascending handle order, from the record after
+// the last lock it was handed (comm_next).  A lock held by another task
+// parks u at the end of that tile's FIFO, so the CTA moves on instead of
+// spinning; the holder hands the lock to the first parked task when it
+// releases it and pushes that task's lock phase again.  The ascending order
+// keeps the waits acyclic.  Returns 1 when u holds every lock, 0 when
+// parked, -1 on abort / watchdog.  One thread.
+__device__ int acquire_comm(const DevGraph& g, uint32_t u, const TaskDesc& t) {
+  (void)t;
+  const uint32_t r0 = __ldcg(&g.task_rec[u]), r1 = __ldcg(&g.task_rec[u + 1]);
+  for (uint32_t r = r0 + ld_volatile(&g.comm_next[u]); r < r1; ++r) {
+    if (__ldcg(&g.rec_mode[r]) != SPX_COMMUTATIVE_WRITE) continue;
+    const uint32_t h = __ldcg(&g.rec_handle[r]);
+    if (!wl_enter(g, h)) return -1;
+    if (ld_volatile(&g.locks[h]) == 0u) {
+      *(volatile uint32_t*)&g.locks[h] = u + 1;
+      wl_leave(g, h);
+      continue;
+    }
+    *(volatile uint32_t*)&g.comm_next[u] = r + 1 - r0;  // resumes after h
+    *(volatile uint32_t*)&g.wnext[u] = 0u;
+    const uint32_t tail = ld_volatile(&g.wl_tail[h]);
+    if (tail) *(volatile uint32_t*)&g.wnext[tail - 1] = u + 1;
+    else *(volatile uint32_t*)&g.wl_head[h] = u + 1;
+    *(volatile uint32_t*)&g.wl_tail[h] = u + 1;
+    wl_leave(g, h);
+    return 0;
+  }
+  __threadfence();
+  return 1;
+}
+
+// Push the lock phase of task w again (one part).  One thread.
+__device__ void push_lock_phase(const DevGraph& g, uint32_t w) {
+  const TaskDesc t = load_task(&g.tasks[w]);
+  const uint32_t q = graph_queue(t.prio);
+  const uint32_t slot = atomicAdd(&g.rs->tail[q].v, 1u);
+  atomicMax(&g.rs->hiwater, slot + 1u);
+  if (slot >= g.qcap) {
+    set_error(g.rs, (uint32_t)SPX_ERR_QUEUE_FULL, 0);
+    return;
+  }
+  __threadfence();
+  *(volatile uint32_t*)&g.queue[q][slot] = w << kPartBits;
+}
+
+// Release the locks of task u after its last phase: a lock with parked
+// tasks goes straight to the first of them.  One thread.
+__device__ void release_comm(const DevGraph& g, uint32_t u) {
+  __threadfence();
+  const uint32_t r0 = __ldcg(&g.task_rec[u]), r1 = __ldcg(&g.task_rec[u + 1]);
+  for (uint32_t r = r0; r < r1; ++r) {
+    if (__ldcg(&g.rec_mode[r]) != SPX_COMMUTATIVE_WRITE) continue;
+    const uint32_t h = __ldcg(&g.rec_handle[r]);
+    if (!wl_enter(g, h)) return;
+    const uint32_t w = ld_volatile(&g.wl_head[h]);
+    if (w) {
+      const uint32_t nx = ld_volatile(&g.wnext[w - 1]);
+      *(volatile uint32_t*)&g.wl_head[h] = nx;
+      if (!nx) *(volatile uint32_t*)&g.wl_tail[h] = 0u;
+    }
+    *(volatile uint32_t*)&g.locks[h] = w;  // the parked task (+1), or free
+    wl_leave(g, h);
+    if (w) push_lock_phase(g, w - 1);
+  }
 }
 
 
@@ -839,10 +942,13 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     const long long c0 = clock64();
     if (tid == 0) {
       s_flag = 1;
-      if (t.flags & kFlagComm) s_flag = lock_comm(g, u) ? 1 : 0;
+      if ((t.flags & kFlagComm) && (t.flags & kFlagSerial)) s_flag = lock_comm(g, u) ? 1 : 0;
+      // a commutative task starts when it holds its locks: its lock phase
+      // (possibly parked and pushed again) is not part of its execution
+      const bool lockph = comm_acquire_phase(t) && phase == 0;
       const uint32_t tk = atomicAdd(&rs->ticket.v, 1u);
-      atomicMin(&g.t_start[u], tk);
-      if (g.trace && part == 0 && phase == 0) {
+      if (!lockph) atomicMin(&g.t_start[u], tk);
+      if (g.trace && part == 0 && phase == (comm_acquire_phase(t) ? 1u : 0u)) {
         g.trace_rec[4 * u + 0] = globaltimer();
         g.trace_rec[4 * u + 2] = smid();
         g.trace_rec[4 * u + 3] = t.nparts;
@@ -850,8 +956,11 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
     }
     __syncthreads();
     if (!s_flag) break;
-    const int info = skip ? 0 : run_part<kMode>(g, t, phase, part, s, tc);
+    // a skipped commutative task still takes (and later releases) its locks
+    const bool run = !skip || (comm_acquire_phase(t) && phase == 0);
+    const int info = run ? run_part<kMode>(g, t, phase, part, s, tc, u, true) : 0;
     __syncthreads();
+    if (info == kParked) continue;  // handed its lock later, pushed again
     const long long dt = clock64() - c0;
     busy += dt;
     if (tid == 0) atomicAdd(&rs->op_cycles[t.op & 31], (unsigned long long)dt);
@@ -881,8 +990,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
         s_flag = atomicSub(&g.remaining[u], 1u) == 1u ? 2 : 1;
         if (s_flag == 2 && phase + 1 < t.nphases) {
           // last part of a phase: set up the next phase before pushing it
-          const uint32_t np = phase_parts(
-              op_phase_units(t.op, t.prec, g.tiles, t.h, phase + 1, t.flags & kFlagFine));
+          const uint32_t np = phase_parts(task_phase_units(t, g.tiles, phase + 1));
           *(volatile uint32_t*)&g.phase[u] = phase + 1;
           atomicExch(&g.remaining[u], np);
           s_np = np;
@@ -915,7 +1023,10 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
       }
       if (s_flag == 2) {
         if (tid < 32) {
-          if ((t.flags & kFlagComm) && tid == 0) unlock_comm(g, u);
+          if ((t.flags & kFlagComm) && tid == 0) {
+            if (comm_acquire_phase(t)) release_comm(g, u);
+            else unlock_comm(g, u);
+          }
           __syncwarp();
           if (g.sctl) release_stream(g, u);
           else release(g, u);
@@ -959,7 +1070,7 @@ __global__ void __launch_bounds__(kThreads, 2) task_kernel(DevGraph g, uint32_t 
   }
   const TaskDesc t = g.tasks[u];
   if (threadIdx.x == 0 && blockIdx.x == 0) touch_progress(g);
-  const int info = run_part<kMode>(g, t, phase, blockIdx.x, s, tc);
+  const int info = run_part<kMode>(g, t, phase, blockIdx.x, s, tc, u, false);
   if (threadIdx.x == 0) {
     if (info > 0) set_error(g.rs, (uint32_t)SPX_NOT_SPD, (int)t.arg + info);
     else if (info < 0) set_error(g.rs, (uint32_t)(info == -2 ? SPX_ERR_TIMEOUT : SPX_ERR_BAD_OP), 0);

@@ -318,6 +318,12 @@ int spx_server_submit(spx_server_t s, spx_graph_t g, unsigned long long* out_req
   off += al(b_tasks);
   for (size_t i = 0; i < v.ntasks; ++i) {
     pt[i] = v.tasks[i];
+    // the server takes a commutative task's locks at its single part
+    if (pt[i].flags & kFlagComm) {
+      pt[i].flags |= kFlagSerial;
+      pt[i].nphases = 1;
+      pt[i].nparts = 1;
+    }
     for (int k = 0; k < 3; ++k) pt[i].h[k] += (uint32_t)L.hb;
   }
   TileDesc* ptl = (TileDesc*)(P + off);

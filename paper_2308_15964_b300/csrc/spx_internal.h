@@ -42,10 +42,13 @@ __host__ __device__ inline uint32_t graph_queue(uint32_t prio) {
 constexpr int kThreads = 256;             // threads per persistent CTA
 constexpr int kBlk = 64;                  // edge of a FP64 sub-tile part
 
-// kFlagComm: the task has a COMMUTATIVE_WRITE access (runs as one part and
-// takes tile locks).  kFlagSerial: one CTA runs every phase and every unit of
-// the task in order (no-split graphs and commutative tasks); the arithmetic
-// per unit is the same as when the units are spread over CTAs.  kFlagFine:
+// kFlagComm: the task has a COMMUTATIVE_WRITE access: a leading phase of one
+// part takes the tiles' locks (see comm_acquire_phase), the op's phases
+// follow, and the last one releases them.  kFlagSerial: one CTA runs every
+// phase and every unit of the task in order (no-split graphs, and the
+// server's commutative tasks, which take the locks at their single part);
+// the arithmetic per unit is the same as when the units are spread over
+// CTAs.  kFlagFine:
 // the task is on the critical path (inserted with priority >= 2): its POTRF,
 // TRSM and FP64 SYRK / GEMM phases use smaller units so that more SMs share
 // it.
@@ -190,6 +193,14 @@ struct DevGraph {
   // so a wide phase is handed out without a compare-and-swap loop)
   uint32_t* qclaim[kQueues];   // [qcap] each, zero at the start of a run
   uint32_t* locks;             // [ntiles] owner task + 1, 0 = free
+  // commutative tasks of graph runs: a FIFO of parked tasks per tile (task
+  // + 1, 0 = none) behind a short spin lock, and per task the next record
+  // to lock when it is handed a lock it waited for; all zero at the start
+  uint32_t* wl_lock;           // [ntiles]
+  uint32_t* wl_head;           // [ntiles]
+  uint32_t* wl_tail;           // [ntiles]
+  uint32_t* wnext;             // [ntasks]
+  uint32_t* comm_next;         // [ntasks]
   uint32_t* t_start;           // [ntasks] tickets
   uint32_t* t_end;             // [ntasks]
   unsigned long long* trace_rec;  // [4*ntasks] when trace
@@ -425,6 +436,26 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
 
 __host__ __device__ inline uint32_t phase_parts(uint32_t units) {
   return units < kMaxParts ? units : kMaxParts;
+}
+
+// A commutative task that is not serial starts with a phase of one part that
+// acquires its tile locks (or parks the task on a lock's wait list); the
+// op's phase p is the task's phase p + 1.
+__host__ __device__ inline bool comm_acquire_phase(const TaskDesc& t) {
+  return (t.flags & kFlagComm) && !(t.flags & kFlagSerial);
+}
+
+__host__ __device__ inline uint32_t task_phases(const TaskDesc& t, const TileDesc* tiles) {
+  return op_phases(t.op, t.prec, tiles, t.h) + (comm_acquire_phase(t) ? 1u : 0u);
+}
+
+__host__ __device__ inline uint32_t task_phase_units(const TaskDesc& t, const TileDesc* tiles,
+                                                     uint32_t phase) {
+  if (comm_acquire_phase(t)) {
+    if (phase == 0) return 1u;
+    --phase;
+  }
+  return op_phase_units(t.op, t.prec, tiles, t.h, phase, t.flags & kFlagFine);
 }
 
 // Launchers implemented in the .cu files (all asynchronous on stream).
