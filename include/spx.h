@@ -101,6 +101,16 @@ enum {
  *                                               triangle of L_kk; V_k square,
  *                                               written whole, zero above its
  *                                               diagonal)
+ *   SPX_OP_POTRF_PANEL  (A_kk:W, A_ik:W)        POTRF of A_kk and the solve
+ *                                               A_ik <- A_ik L_kk^{-T} in one
+ *                                               task: the rows of A_ik join the
+ *                                               panel rows of each 64-column
+ *                                               step (the same arithmetic as
+ *                                               POTRF then TRSM, fewer phase
+ *                                               boundaries on the critical
+ *                                               path); A_ik.cols = A_kk.cols.
+ *                                               prec SPX_F64, or SPX_F64_OZAKI
+ *                                               to split A_ik at the end
  *   SPX_OP_NBODY_SELF   (P:W)                   interactions of the particles
  *                                               of group P with each other
  *   SPX_OP_NBODY_PAIR   (P:W, Q:W)              interactions between groups P
@@ -154,7 +164,8 @@ enum {
   SPX_OP_TRSM_INV = 15,
   SPX_OP_NBODY_SELF = 16,
   SPX_OP_NBODY_PAIR = 17,
-  SPX_NUM_OPS = 18
+  SPX_OP_POTRF_PANEL = 18,
+  SPX_NUM_OPS = 19
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
@@ -571,12 +582,17 @@ int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n, int lda, 
  *           the inverse agree to rounding for well-conditioned diagonal tiles
  *           (the error of the inverse grows with kappa(L_kk)); this is a
  *           reading of this library, not of the paper.
+ *   fuse_panel  1: POTRF(k) and the solve of the critical panel tile
+ *           (k+1, k) run as one SPX_OP_POTRF_PANEL task (the same arithmetic;
+ *           the critical path crosses fewer phase and task boundaries); 0:
+ *           separate POTRF and TRSM tasks.
  *   b       a multiple of 32, 32 <= b <= 512.
  * Other arguments as spx_cholesky_insert.  Errors: as spx_cholesky_insert,
  * and SPX_ERR_INVALID_ARG for b, the store, or ldv < b. */
 int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_S,
-                              long long S_bytes, double* dev_V, int ldv, double* dev_X, int nrhs,
-                              int ldx, int lookahead, long long* out_ntasks);
+                              long long S_bytes, double* dev_V, int ldv, int fuse_panel,
+                              double* dev_X, int nrhs, int ldx, int lookahead,
+                              long long* out_ntasks);
 
 /* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
  * already in dev_L (lower triangle, tiles b x b).  Used for the correction

@@ -28,7 +28,7 @@ SRC = os.path.join(HERE, "spx_oracle.cpp")
 READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (POTRF, TRSM, SYRK, GEMM_NT_SUB, GEMM_NN_ADD, TRSM_L_FWD, GEMM_FWD,
  TRSM_LT_BWD, GEMM_BWD, NOP, SPIN, COPY, AXPY, TRMM, TRTRI, TRSM_INV, NBODY_SELF,
- NBODY_PAIR) = range(18)
+ NBODY_PAIR, POTRF_PANEL) = range(19)
 
 
 def build(force: bool = False) -> str:

@@ -76,7 +76,8 @@ enum {
   O_TRTRI = 14,       // V <- L^{-1}, L lower triangular
   O_TRSM_INV = 15,    // A_ik <- A_ik V^T, V = L_kk^{-1} (the TRSM by the inverse)
   O_NBODY_SELF = 16,  // Coulomb interactions inside one particle group
-  O_NBODY_PAIR = 17   // interactions between two groups, both updated
+  O_NBODY_PAIR = 17,  // interactions between two groups, both updated
+  O_POTRF_PANEL = 18  // POTRF of A_kk, then A_ik <- A_ik L_kk^{-T}
 };
 
 // ---------------------------------------------------------------------------
@@ -467,6 +468,17 @@ int spxo_execute(int ntasks, const int* task_op, const int* task_tiles,
       case O_NBODY_SELF: {
         const spxo_tile& P = tile(0);
         nbody_interact(P.ptr, P.ld, P.rows, P.ptr, P.ld, P.rows, true);
+        break;
+      }
+      case O_POTRF_PANEL: {
+        const spxo_tile& L = tile(0);
+        const spxo_tile& A = tile(1);
+        const int r = spxo_potrf(L.ptr, L.rows, L.ld);
+        if (r != 0) {
+          *info = (int)task_arg[t] + r;
+          return 1;
+        }
+        trsm_right_lt(L.ptr, L.ld, A.ptr, A.rows, A.cols, A.ld);
         break;
       }
       case O_NBODY_PAIR: {

@@ -49,12 +49,13 @@ def ozaki_store(n: int, b: int, device="cuda", inverse_panels: bool = False):
 
 
 def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, S=None,
-                         V=None):
+                         V=None, fuse_panel: bool = False):
     """spx_cholesky_insert_ozaki: A = L L^T with the trailing updates in FP64
     emulated on the tensor cores (digit planes in the split store S, made by
     ozaki_store when None).  V (n x b FP64, or None): inverse panels, V
     receiving the inverses of the diagonal factor tiles.  Returns the number
-    of tasks inserted."""
+    of tasks inserted.  fuse_panel: POTRF and the critical panel tile's solve as
+    one POTRF_PANEL task."""
     n = A.shape[0]
     assert A.stride(1) == 1 and (X is None or X.stride(1) == 1)
     assert V is None or (V.stride(1) == 1 and V.shape[0] >= n)
@@ -64,7 +65,7 @@ def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True
     spx._check(spx.lib.spx_cholesky_insert_ozaki(
         g._h, _ptr(A), n, A.stride(0), b, _ptr(S), S.numel() * S.element_size(),
         _ptr(V) if V is not None else None, V.stride(0) if V is not None else 0,
-        _ptr(X) if X is not None else None, X.shape[1] if X is not None else 0,
+        1 if fuse_panel else 0, _ptr(X) if X is not None else None, X.shape[1] if X is not None else 0,
         X.stride(0) if X is not None else 0, 1 if lookahead else 0, ctypes.byref(nt)),
         "spx_cholesky_insert_ozaki")
     g._keep.extend([A, S] + ([X] if X is not None else []) + ([V] if V is not None else []))

@@ -225,7 +225,7 @@ int cuda_fail(cudaError_t e) {
 
 // Operand count, shape and mode checks of the built-in ops.
 // Operand count of each built-in op (-1: any, 1..16).
-const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2, 1, 2};
+const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2, 1, 2, 2};
 
 int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
                    const unsigned* h, const int* m, int nh) {
@@ -250,12 +250,14 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     return md == SPX_WRITE || md == SPX_COMMUTATIVE_WRITE || md == SPX_MAYBE_WRITE;
   };
   if (!writes(m[w]) && !(m[w] == SPX_ATOMIC_WRITE && atomic_ok)) return SPX_ERR_INVALID_ARG;
-  if (op == SPX_OP_NBODY_PAIR && !writes(m[0])) return SPX_ERR_INVALID_ARG;  // both groups written
+  if ((op == SPX_OP_NBODY_PAIR || op == SPX_OP_POTRF_PANEL) && !writes(m[0]))
+    return SPX_ERR_INVALID_ARG;  // both operands written
   auto R = [&](int i) { return t[h[i]].rows; };
   auto C = [&](int i) { return t[h[i]].cols; };
   bool ok = true;
   switch (op) {
     case SPX_OP_POTRF: ok = R(0) == C(0); break;
+    case SPX_OP_POTRF_PANEL: ok = R(0) == C(0) && C(1) == C(0); break;
     case SPX_OP_TRSM: ok = R(0) == C(0) && C(1) == R(0); break;
     case SPX_OP_SYRK: ok = R(1) == C(1) && R(0) == R(1); break;
     case SPX_OP_GEMM_NT_SUB: ok = R(0) == R(2) && R(1) == C(2) && C(0) == C(1); break;
@@ -314,6 +316,10 @@ int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
   int ins[2] = {-1, -1};
   switch (op) {
     case SPX_OP_TRSM: ins[0] = (int)h[1]; break;
+    case SPX_OP_POTRF_PANEL:  // split prec only: A_ik is split after its solve
+      if (prec != SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
+      ins[0] = (int)h[1];
+      break;
     case SPX_OP_TRSM_INV:
       ins[0] = (int)h[1];
       if (prec == SPX_F64_OZAKI) ins[1] = (int)h[0];  // V's digits feed the product
@@ -1454,7 +1460,8 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
   static const char* names[SPX_NUM_OPS] = {"POTRF", "TRSM", "SYRK", "GEMM", "GEMM_NN",
                                            "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
                                            "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI",
-                                           "TRSM_INV", "NBODY_SELF", "NBODY_PAIR"};
+                                           "TRSM_INV", "NBODY_SELF", "NBODY_PAIR",
+                                           "POTRF_PANEL"};
   std::fprintf(f, "digraph spx {\n");
   for (size_t u = 0; u < N; ++u)
     std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);

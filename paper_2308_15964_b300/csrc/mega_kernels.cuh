@@ -363,6 +363,15 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
   switch (t.op) {
     case SPX_OP_POTRF:
       return op_potrf_units(T[t.h[0]], phase, u0, u1, s, t.flags & kFlagFine);
+    case SPX_OP_POTRF_PANEL:
+      if (t.prec == SPX_F64_OZAKI && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
+        if constexpr (kMode == 2) {
+          op_oz_split(T[t.h[1]], u0, u1);
+          return 0;
+        }
+        return -1;
+      }
+      return op_potrf_panel_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s, t.flags & kFlagFine);
     case SPX_OP_TRSM:
       if constexpr (kTc) {
         if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {

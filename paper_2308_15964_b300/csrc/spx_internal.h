@@ -357,6 +357,8 @@ __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* 
                                               const uint32_t* h) {
   switch (op) {
     case SPX_OP_POTRF: return 3 * cdiv64(t[h[0]].rows) - 2;
+    case SPX_OP_POTRF_PANEL:  // POTRF's, one more solving A_ik's last block; split prec: the split
+      return 3 * cdiv64(t[h[0]].rows) - 1 + (prec == SPX_F64_OZAKI ? 1u : 0u);
     case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
@@ -387,6 +389,16 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       if (phase % 3 == 1) return fine ? cdiv16(below) : cdiv64(below);
       const uint32_t q = fine ? cdiv32(below) : cdiv64(below);
       return q * (q + 1) / 2;
+    }
+    case SPX_OP_POTRF_PANEL: {  // POTRF's units, then those of the rows of A_ik
+      const int n = t[h[0]].rows, qm = t[h[1]].rows;
+      const int rest = n - kBlk * (int)(phase / 3 + 1), below = rest > 0 ? rest : 0;
+      const uint32_t nb = cdiv64(n), qrb = fine ? cdiv16(qm) : cdiv64(qm);
+      if (phase >= 3 * nb - 1) return cdiv64(qm);  // split of A_ik
+      if (phase % 3 == 0) return 1u;
+      if (phase % 3 == 1) return (fine ? cdiv16(below) : cdiv64(below)) + qrb;
+      const uint32_t q = fine ? cdiv32(below) : cdiv64(below);
+      return q * (q + 1) / 2 + qrb * (nb - 1 - phase / 3);
     }
     case SPX_OP_TRSM: {
       const uint32_t nbr = cdiv64(t[h[1]].rows), nbc = cdiv64(t[h[1]].cols), j = phase / 2;

@@ -478,6 +478,60 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
   }
 }
 
+// POTRF of P with the solve Q <- Q L^{-T} folded into its steps (one task on
+// the critical path instead of two): in step j, after P's diagonal block is
+// factored, Q's rows are solved with it beside P's rows below it, and Q's
+// columns right of block j are updated beside P's trailing blocks.  Units of
+// a phase: POTRF's own first, then Q's (row blocks, or row blocks x 64-column
+// blocks); each Q unit is the TRSM op's unit of the same step, so the result
+// is that of POTRF then TRSM.  Returns POTRF's info.
+__device__ int op_potrf_panel_units(const TileDesc& P, const TileDesc& Q, uint32_t phase,
+                                    uint32_t u0, uint32_t u1, F64Smem& s, bool fine) {
+  const double* l = (const double*)P.ptr;
+  double* a = (double*)Q.ptr;
+  const int n = P.rows, m = Q.rows, lda = Q.ld, ldl = P.ld;
+  // phases: POTRF's 3 nb - 2, then one more (j = nb - 1, phase % 3 == 1)
+  // solving Q's last column block
+  const int j = (int)(phase / 3), jb = j * kBlk, w = min(kBlk, n - jb);
+  const int below = max(0, n - jb - w), rb = fine ? 16 : kBlk;
+  if (phase % 3 == 0) return op_potrf_units(P, phase, u0, u1, s, fine);
+  if (phase % 3 == 1) {
+    const uint32_t np = fine ? cdiv16(below) : cdiv64(below);
+    if (u0 < np) op_potrf_units(P, phase, u0, min(u1, np), s, fine);
+    if (u1 <= np) return 0;
+    load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+    __syncthreads();
+    prep_lower(s.l, w, s.rinv, false);
+    for (uint32_t u = max(u0, np); u < u1; ++u) {
+      const int ib = rb * (int)(u - np), mb = min(rb, m - ib);
+      double* x = a + (size_t)ib * lda + jb;
+      load_rows(s.x, x, lda, mb, w);
+      __syncthreads();
+      trsm_rt_smem(s.x, s.l, s.rinv, mb, w);
+      store_rows(x, lda, s.x, mb, w);
+      __syncthreads();
+    }
+    return 0;
+  }
+  const uint32_t q = fine ? cdiv32(below) : cdiv64(below), np = q * (q + 1) / 2;
+  if (u0 < np) op_potrf_units(P, phase, u0, min(u1, np), s, fine);
+  const uint32_t right = cdiv64(n) - 1 - (uint32_t)j;
+  for (uint32_t u = max(u0, np); u < u1; ++u) {
+    const uint32_t v = u - np;
+    const int ib = rb * (int)(v / right), lb = (j + 1 + (int)(v % right)) * kBlk;
+    double* c = a + (size_t)ib * lda + lb;
+    const double* ap = a + (size_t)ib * lda + jb;
+    const double* bp = l + (size_t)lb * ldl + jb;
+    if (fine)
+      gemm_block<false, false, 4, 1>(c, lda, ap, lda, bp, ldl, min(16, m - ib), min(kBlk, n - lb),
+                                     w, -1.0, false, s.gs);
+    else
+      gemm_block<false, false>(c, lda, ap, lda, bp, ldl, min(kBlk, m - ib), min(kBlk, n - lb), w,
+                               -1.0, false, s.gs);
+  }
+  return 0;
+}
+
 // TRSM phase `phase`, units u0..u1: A (m x n) <- A L^{-T}, right-looking over
 // 64-column blocks j of A: solve block column j, then update the columns to
 // its right.

@@ -80,7 +80,7 @@ int register_ozaki_tiles(spx_graph_t g, double* A, int n, int lda, int b, char* 
 int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* dev_Alo, int ldlo,
                     bool factor, double* dev_X, int nrhs, int ldx, int lookahead, int prec,
                     long long* out_ntasks, double* dev_V = nullptr, int ldv = 0,
-                    long long S_bytes = 0) {
+                    long long S_bytes = 0, bool fuse = false) {
   if (!g || !dev_A || n < 1 || b < 1 || lda < n || (dev_X && (nrhs < 1 || ldx < nrhs)))
     return SPX_ERR_INVALID_ARG;
   const bool oz = prec == SPX_F64_OZAKI;
@@ -114,7 +114,13 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
   };
   for (int k = 0; k < T && rc == SPX_OK && factor; ++k) {
     unsigned t = 0;
-    rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, crit, &t, SPX_F64);
+    // fuse: POTRF(k) and the solve of the critical panel tile (k+1, k) as one
+    // task (POTRF_PANEL), the rest of the panel as below
+    const bool fused = fuse && k + 1 < T;
+    if (fused)
+      rc = ins(SPX_OP_POTRF_PANEL, {A.at(k, k), A.at(k + 1, k)}, {W, W}, crit, &t, prec);
+    else
+      rc = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, crit, &t, SPX_F64);
     if (rc == SPX_OK) rc = spx_task_set_arg(g, t, (long long)k * b);
     if (dev_V) {
       // The panel below the critical one: V_k <- L_kk^{-1} (FP64), then
@@ -123,7 +129,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
       // inversion stays off the critical path.
       const int bk = n - k * b < b ? n - k * b : b;
       unsigned v = 0;
-      if (rc == SPX_OK && k + 1 < T)
+      if (rc == SPX_OK && k + 1 < T && !fused)
         rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, crit, nullptr, prec);
       // split prec: V_k owns a slot after the factor tiles' and is split
       // after the inversion (the TRSM_INV products read its digits)
@@ -138,7 +144,7 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
       for (int i = k + 2; i < T && rc == SPX_OK; ++i)
         rc = ins(SPX_OP_TRSM_INV, {v, A.at(i, k)}, {R, W}, hi, nullptr, prec);
     }
-    for (int i = k + 1; i < T && rc == SPX_OK && !dev_V; ++i)
+    for (int i = k + (fused ? 2 : 1); i < T && rc == SPX_OK && !dev_V; ++i)
       rc = ins(SPX_OP_TRSM, {A.at(k, k), A.at(i, k)}, {R, W}, i == k + 1 ? crit : hi, nullptr,
                prec);
     for (int i = k + 1; i < T && rc == SPX_OK; ++i)
@@ -202,11 +208,11 @@ extern "C" int spx_cholesky_insert_mixed_inv(spx_graph_t g, double* dev_A, int n
 
 extern "C" int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int b,
                                          void* dev_S, long long S_bytes, double* dev_V, int ldv,
-                                         double* dev_X, int nrhs, int ldx, int lookahead,
-                                         long long* out_ntasks) {
-  if (!spx_ozaki_slot_bytes(b)) return SPX_ERR_INVALID_ARG;
+                                         int fuse_panel, double* dev_X, int nrhs, int ldx,
+                                         int lookahead, long long* out_ntasks) {
+  if (!spx_ozaki_slot_bytes(b) || fuse_panel < 0 || fuse_panel > 1) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_A, n, lda, b, dev_S, 0, true, dev_X, nrhs, ldx, lookahead,
-                         SPX_F64_OZAKI, out_ntasks, dev_V, ldv, S_bytes);
+                         SPX_F64_OZAKI, out_ntasks, dev_V, ldv, S_bytes, fuse_panel != 0);
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,

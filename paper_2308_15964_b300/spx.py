@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
  OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI,
- OP_TRSM_INV, OP_NBODY_SELF, OP_NBODY_PAIR) = range(18)
+ OP_TRSM_INV, OP_NBODY_SELF, OP_NBODY_PAIR, OP_POTRF_PANEL) = range(19)
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
             "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV",
-            "NBODY_SELF", "NBODY_PAIR")
+            "NBODY_SELF", "NBODY_PAIR", "POTRF_PANEL")
 F64, TF32, BF16, F64_OZAKI = 0, 1, 2, 3
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
@@ -86,7 +86,7 @@ def _load():
         "spx_stream_end": (I, [P]),
         "spx_graph_host_preds": (I, [P, P, P, LL, P]),
         "spx_ozaki_register": (I, [P, P, I, I, P]),
-        "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, P, I, I, I, P]),
+        "spx_cholesky_insert_ozaki": (I, [P, P, I, I, I, P, LL, P, I, I, P, I, I, I, P]),
         "spx_cholesky_insert_mixed": (I, [P, P, I, I, I, P, I, P, I, I, I, I, P]),
         "spx_cholesky_insert_mixed_inv": (I, [P, P, I, I, I, P, I, P, I, P, I, I, I, I, P]),
         "spx_solve_insert": (I, [P, P, I, I, I, P, I, I, P]),

@@ -383,3 +383,93 @@ def test_inverse_panels_16384_sampled(S):
         assert O.freivalds(A_host, L, inputs.gaussian(n, 100 + s)) <= 1e-14
     assert O.solve_backward_error(A_host, X, B_host).max() <= 1e-14
     g.close()
+
+
+# --- the critical panel tile solved inside POTRF (POTRF_PANEL) -----------------
+
+@pytest.mark.parametrize("n,m,b", [(512, 512, 512), (256, 100, 256), (320, 320, 320)])
+def test_potrf_panel_op(S, n, m, b):
+    """POTRF_PANEL (FP64) against the oracle's POTRF then TRSM (its
+    definition), and bit-identical to the POTRF and TRSM tasks on the GPU."""
+    Afull = inputs.spd_matrix(n + m, 1.0, seed=n + m).numpy()
+    P0 = np.ascontiguousarray(Afull[:n, :n])
+    Q0 = np.ascontiguousarray(Afull[n:, :n])
+    outs = []
+    for fused in (True, False):
+        Pd = torch.from_numpy(P0.copy()).cuda()
+        Qd = torch.from_numpy(Q0.copy()).cuda()
+        g = S.Graph()
+        hp, hq = g.register_tensor(Pd), g.register_tensor(Qd)
+        if fused:
+            g.insert(S.OP_POTRF_PANEL, [hp, hq], [S.WRITE, S.WRITE], 2)
+        else:
+            g.insert(S.OP_POTRF, [hp], [S.WRITE], 2)
+            g.insert(S.OP_TRSM, [hp, hq], [S.READ, S.WRITE], 2)
+        assert g.run()[0] == 0
+        torch.cuda.synchronize()
+        outs.append((Pd.cpu().numpy(), Qd.cpu().numpy()))
+        g.close()
+    assert np.array_equal(np.tril(outs[0][0]), np.tril(outs[1][0]))
+    assert np.array_equal(outs[0][1], outs[1][1])
+    # the oracle: tiles (0, 0) and (1, 0) of the (n + m) square matrix, tile n
+    mats = {"A": Afull.copy()}
+    info = O.execute([(O.POTRF_PANEL, [(("A", 0, 0), O.WRITE), (("A", 1, 0), O.WRITE)], 0)], mats,
+                     n)
+    assert info == 0
+    Lo = np.tril(mats["A"][:n, :n])
+    Qo = mats["A"][n:, :n]
+    assert np.abs(np.tril(outs[0][0]) - Lo).max() <= 1e-12 * np.abs(Lo).max()
+    assert np.abs(outs[0][1] - Qo).max() <= 1e-12 * np.abs(Qo).max()
+
+
+@pytest.mark.parametrize("n,b,inverse", [(2048, 512, True), (1000, 128, True), (1536, 256, False)])
+def test_fused_panel_bit_identical(S, n, b, inverse):
+    """The split Cholesky with the fused critical panel equals the unfused one
+    bit for bit, and the oracle within the FP64 tolerances."""
+    from paper_2308_15964_b300 import cholesky
+    A = inputs.spd_matrix(n, 0.1, seed=9).numpy()
+    B = inputs.rhs(n, 2, seed=9).numpy()
+    res = []
+    for fuse in (True, False):
+        Ad = torch.from_numpy(A.copy()).cuda()
+        Xd = torch.from_numpy(B.copy()).cuda()
+        V = torch.zeros((n, b), dtype=torch.float64, device="cuda") if inverse else None
+        g = S.Graph()
+        cholesky.cholesky_ozaki_graph(g, Ad, b, Xd, V=V, fuse_panel=fuse)
+        rc, info = g.run()
+        assert rc == 0 and info == 0
+        torch.cuda.synchronize()
+        res.append((Ad.cpu().numpy(), Xd.cpu().numpy()))
+        g.close()
+    assert np.array_equal(np.tril(res[0][0]), np.tril(res[1][0]))
+    assert np.array_equal(res[0][1], res[1][1])
+    Lo = A.copy()
+    assert O.tiled_cholesky(Lo, b) == 0
+    assert rel_entry_err(res[0][0], Lo) <= 1e-12
+    assert O.solve_backward_error(A, res[0][1], B).max() <= 1e-14
+
+
+def test_fused_panel_integer_and_not_spd(S):
+    from paper_2308_15964_b300 import cholesky
+    n, b = 1024, 256
+    L0 = bidiag_lower(n, b, 77)
+    A = L0 @ L0.T
+    Ad = torch.from_numpy(A.copy()).cuda()
+    V = torch.zeros((n, b), dtype=torch.float64, device="cuda")
+    g = S.Graph()
+    cholesky.cholesky_ozaki_graph(g, Ad, b, V=V, fuse_panel=True)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(np.tril(Ad.cpu().numpy()), L0)
+    g.close()
+    A2 = inputs.spd_matrix(512, 1.0, seed=3).numpy()
+    A2[300, 300] = -1.0
+    Lo = A2.copy()
+    info_o = O.tiled_cholesky(Lo, 128)
+    Ad = torch.from_numpy(A2.copy()).cuda()
+    g = S.Graph()
+    cholesky.cholesky_ozaki_graph(g, Ad, 128, V=torch.zeros((512, 128), dtype=torch.float64,
+                                                            device="cuda"), fuse_panel=True)
+    rc, info = g.run()
+    assert info == info_o and info > 0
+    g.close()
