@@ -564,13 +564,19 @@ def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, compara
                        "one task per (i, j, k) on C_ij (WRITE chain or COMMUTATIVE_WRITE run)",
            "n": n, "tile": b, "flops_per_step": flops}
 
-    def timed(g, commutative, nsteps, nwarm):
+    T = -(-n // b)
+    S = torch.empty(2 * T * T * spx.lib.spx_ozaki_slot_bytes(b), dtype=torch.uint8, device="cuda")
+
+    def timed(g, commutative, nsteps, nwarm, split=False):
         rec = []
         for i in range(nwarm + nsteps):
             C.copy_(C0)
             ev[0].record()
             g.clear()
-            cholesky.gemm_graph(g, A, B, C, b, commutative=commutative)
+            if split:
+                cholesky.gemm_ozaki_graph(g, A, B, C, b, commutative=commutative, S=S)
+            else:
+                cholesky.gemm_graph(g, A, B, C, b, commutative=commutative)
             g.execute(stream)
             rc, _ = g.wait()
             ev[1].record()
@@ -609,7 +615,31 @@ def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, compara
                              "tasks_per_s": ntasks / (statistics.mean(bms) * 1e-3),
                              "p99_ms": float(np.percentile(bms, 99)), "steps": len(bms)}
         res[mode] = row
-    del A, B, C, C0
+    # the same DAG with each task's product split on the tensor cores (SPLIT
+    # tasks for the tiles of A, SPLIT_T for B, then the GEMM_NN_ADD tasks)
+    block_flops = 36 * 2 * 128 * 64 * b
+    tensor_flops = T ** 3 * (-(-b // 128)) * (-(-b // 64)) * block_flops
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    for mode, comm in (("split_write", False), ("split_commutative", True)):
+        g = spx.Graph()
+        rec = timed(g, comm, steps, warmup, split=True)
+        ntasks, nedges, _, _ = g.sizes()
+        g.close()
+        ms = [r[0] for r in rec]
+        kern = statistics.mean(r[1] for r in rec)
+        ach = tensor_flops / (kern * 1e-3) / 1e12
+        res[mode] = {"value": flops / (statistics.mean(ms) * 1e-3) / 1e9, "unit": "GFLOP/s",
+                     "ms_per_step": statistics.mean(ms), "steps": len(ms), "tasks": ntasks,
+                     "edges": nedges, "tasks_per_s": ntasks / (statistics.mean(ms) * 1e-3),
+                     "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                     "arith": "FP64 by split products (Ozaki) on the BF16 tensor cores",
+                     "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16,
+                                  "unit": "TFLOP/s", "frac": ach / bf16,
+                                  "kernel": "persistent_kernel<split products> (one CTA per SM)",
+                                  "kernel_ms": kern,
+                                  "tensor_tflop_per_launch": tensor_flops / 1e12}}
+    del A, B, C, C0, S
     torch.cuda.empty_cache()
     # CPU oracle (one host core, insertion order): bounded samples (about 4 s
     # in all; n = 2048 takes 40 s), n^3 extrapolation to the workload size

@@ -111,6 +111,18 @@ enum {
  *                                               path); A_ik.cols = A_kk.cols.
  *                                               prec SPX_F64, or SPX_F64_OZAKI
  *                                               to split A_ik at the end
+ *   SPX_OP_SPLIT        (X:W)                   split X (FP64) into the split
+ *                                               slot of its tile: row r gets
+ *                                               its own exponent, K = X's
+ *                                               columns (the A operand of a
+ *                                               split product); X's FP64
+ *                                               entries are not changed.
+ *                                               prec SPX_F64_OZAKI only
+ *   SPX_OP_SPLIT_T      (X:W)                   split X^T into the slot: slot
+ *                                               row c is column c of X with
+ *                                               its own exponent, K = X's
+ *                                               rows (the B operand of C +=
+ *                                               A X).  prec SPX_F64_OZAKI only
  *   SPX_OP_NBODY_SELF   (P:W)                   interactions of the particles
  *                                               of group P with each other
  *   SPX_OP_NBODY_PAIR   (P:W, Q:W)              interactions between groups P
@@ -131,9 +143,14 @@ enum {
  *                                               TRSM of the mixed-precision
  *                                               factorization as a product on
  *                                               the tensor cores; prec
- *                                               SPX_TF32 / SPX_BF16 only (see
- *                                               the prec enum), A_ik.cols a
+ *                                               SPX_TF32 / SPX_BF16 /
+ *                                               SPX_F64_OZAKI only (see the
+ *                                               prec enum), A_ik.cols a
  *                                               multiple of 32
+ * GEMM_NN_ADD with prec SPX_F64_OZAKI forms C_ij + A_ik B_kj as a split
+ * product on the tensor cores from A_ik's slot (written by SPLIT) and B_kj's
+ * slot (written by SPLIT_T), one rounding per task and entry; C_ij by WRITE
+ * or COMMUTATIVE_WRITE (not ATOMIC_WRITE).
  * Operand element types: SPX_DT_F64 throughout, except that GEMM_FWD,
  * GEMM_BWD and TRMM also take all three operands SPX_DT_F32 (FP32
  * arithmetic) when the written tile has at most 16 columns, and COPY / AXPY
@@ -165,7 +182,9 @@ enum {
   SPX_OP_NBODY_SELF = 16,
   SPX_OP_NBODY_PAIR = 17,
   SPX_OP_POTRF_PANEL = 18,
-  SPX_NUM_OPS = 19
+  SPX_OP_SPLIT = 19,
+  SPX_OP_SPLIT_T = 20,
+  SPX_NUM_OPS = 21
 };
 
 /* Arithmetic of a task.  SPX_F64: FP64 throughout.  SPX_TF32 / SPX_BF16
@@ -181,7 +200,19 @@ enum {
  * hi*hi + hi*lo + lo*hi accumulate in FP32 (the lo*lo term, about 2^-22
  * relative, is dropped), i.e. about FP32 accuracy; the FP64 tile receives
  * the accumulator widened exactly and the low-precision copy its rounding
- * to the task's type. */
+ * to the task's type.
+ * SPX_F64_OZAKI (the split scheme of Ozaki, Ogita, Oishi and Rump, 2012;
+ * one-CTA-per-SM kernel): a split operand keeps, per row, the exponent e_r
+ * (the smallest e >= -1022 with every |a_rk| < 2^e) and the integer X_rk =
+ * a_rk 2^(55 - e_r) rounded to nearest even, as eight balanced base-128
+ * digits stored as BF16 in the tile's split slot (SPLIT, SPLIT_T, or the
+ * last phase of TRSM / TRTRI / TRSM_INV / POTRF_PANEL writes it).  A split
+ * product sums the digit products of planes s + t <= 7 on the tensor cores
+ * in FP32 (every partial sum an integer below 2^24, so exact for K <= 512),
+ * joins them in 64-bit integers and rounds once to FP64: per entry the error
+ * is at most K 9.05 2^-56 2^(e_r + f_c) before the final rounding, the
+ * accuracy of an FP64 dot product.  SYRK and GEMM_NT_SUB subtract the
+ * product, GEMM_NN_ADD adds it, TRSM_INV stores it. */
 enum { SPX_F64 = 0, SPX_TF32 = 1, SPX_BF16 = 2, SPX_F64_OZAKI = 3 };
 
 /* SPX_F64_OZAKI: FP64 products emulated on the BF16 tensor cores by splitting
@@ -322,8 +353,9 @@ int spx_ozaki_register(spx_graph_t g, void* dev_ptr, int nslots, int b, unsigned
  *   prec      SPX_F64, or SPX_TF32 / SPX_BF16 for TRSM, SYRK, GEMM_NT_SUB
  *             whose factor tiles have low-precision copies in a matrix
  *             registered with spx_lowp_register of the matching type;
- *             SPX_F64_OZAKI for TRSM, SYRK, GEMM_NT_SUB whose factor tiles
- *             have split slots in a store registered with
+ *             SPX_F64_OZAKI for TRSM, SYRK, GEMM_NT_SUB, TRTRI, TRSM_INV,
+ *             POTRF_PANEL, GEMM_NN_ADD, SPLIT and SPLIT_T whose split
+ *             operands have slots in a store registered with
  *             spx_ozaki_register.
  *   out_task  receives the task id (0, 1, 2, ... in insertion order); may be
  *             NULL.
@@ -686,6 +718,27 @@ int spx_refine_inv_insert(spx_graph_t g, double* dev_A0, int n, int lda, double*
  * Errors: SPX_ERR_INVALID_ARG; as spx_tile_register / spx_task_insert. */
 int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n, int ld,
                     int b, int commutative, long long* out_ntasks);
+
+/* spx_gemm_insert with the products in FP64 emulated on the tensor cores
+ * (prec SPX_F64_OZAKI): first one SPLIT task per tile A_ik and one SPLIT_T
+ * task per tile B_kj (row-major order of each matrix), then the GEMM_NN_ADD
+ * tasks of spx_gemm_insert with the split prec, each reading the two slots
+ * and adding its product into C_ij with one rounding per entry.
+ *   dev_S   the split store: A_ik uses slot i T + k, B_kj slot T^2 + k T + j
+ *           (2 T^2 slots, T = ceil(n / b)); S_bytes its size, at least that
+ *           many times spx_ozaki_slot_bytes(b); 256-byte aligned; owned by
+ *           the caller until the graph is waited for.
+ *   commutative  0 (WRITE) or 1 (COMMUTATIVE_WRITE); the split product is
+ *           not an atomic update, so 2 is SPX_ERR_INVALID_ARG.
+ *   b       a multiple of 32, 32 <= b <= 512.
+ * Error of one product entry: at most n_k 9.05 2^-56 2^(e_r + f_c) before its
+ * rounding (n_k = the K extent, e_r and f_c the exponents of row r of A_ik
+ * and column c of B_kj), FP64's level.
+ * Errors: SPX_ERR_INVALID_ARG; as spx_ozaki_register / spx_tile_register /
+ * spx_task_insert. */
+int spx_gemm_insert_ozaki(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C, int n,
+                          int ld, int b, int commutative, void* dev_S, long long S_bytes,
+                          long long* out_ntasks);
 
 /* Insert the AXPY of the paper's numerical applications (section "Numerical
  * applications": a vector split into pieces, one independent task per piece,

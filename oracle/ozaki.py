@@ -16,7 +16,8 @@ split(A), per row r of an FP64 matrix:
            the least significant end: sigma = ((X + 64) mod 128) - 64, then
            X <- (X - sigma) / 128; what remains after seven digits is sigma_0.
 
-gemm_nt_sub(C, A, B) = C - A B^T entry by entry, with v_rc the split product:
+gemm_nt_sub(C, A, B) = C - A B^T entry by entry (gemm_nn_add(C, A, B) = C +
+A B the same way, with the columns of B split), v_rc the split product:
     P_d  = sum over s + t = d (d = 0..7) of sigma_s(A) tau_t(B)^T;
     F    = sum_d P_d * 128^(7-d)                    (an exact integer);
     v_rc = F * 2^(e_r + f_c - 61), rounded once to FP64;
@@ -26,7 +27,8 @@ X Y = 2^49 * sum_d P_d 128^(7-d) plus the dropped pairs s + t > 7.)
 
 Pinned in tests/test_oracle_ozaki.py against a hand-worked split, exact
 integer products, a closed-form worst case of the digit sums, and the exact
-rational product within the error bound of the scheme.
+rational product within the error bound of the scheme; the NN form against
+exact integer products and the exact scaling of single columns of B.
 """
 from __future__ import annotations
 
@@ -93,6 +95,27 @@ def products(A, B):
 def gemm_nt_sub(C, A, B):
     """C - A B^T by the split product (a new array)."""
     return np.asarray(C, np.float64) - products(A, B)
+
+
+def gemm_nn_add(C, A, B):
+    """C + A B by the split product (a new array): A split by rows, B by
+    columns (the rows of B^T, each column with its own exponent)."""
+    return np.asarray(C, np.float64) + products(A, np.asarray(B, np.float64).T)
+
+
+def tiled_gemm_nn_add(A, B, C, b):
+    """The tiled GEMM C += A B of the paper's numerical applications with each
+    task's product split: for every block C_ij, the tasks k = 0, 1, ... in
+    order, each adding its split product with one rounding (in place)."""
+    n = A.shape[0]
+    T = -(-n // b)
+    for i in range(T):
+        for j in range(T):
+            ri, cj = slice(i * b, min(n, (i + 1) * b)), slice(j * b, min(n, (j + 1) * b))
+            for k in range(T):
+                rk = slice(k * b, min(n, (k + 1) * b))
+                C[ri, cj] = gemm_nn_add(C[ri, cj], A[ri, rk], B[rk, cj])
+    return C
 
 
 def syrk_lower(C, L):

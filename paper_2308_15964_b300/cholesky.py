@@ -85,6 +85,30 @@ def gemm_graph(g: spx.Graph, A, B, C, b: int, commutative: bool = False, atomic:
     return nt.value
 
 
+def gemm_ozaki_graph(g: spx.Graph, A, B, C, b: int, commutative: bool = False, S=None):
+    """spx_gemm_insert_ozaki: C += A B with the products in FP64 emulated on
+    the tensor cores: SPLIT tasks for the tiles of A, SPLIT_T for those of B,
+    then one GEMM_NN_ADD per (i, j, k) (WRITE, or COMMUTATIVE_WRITE on C_ij).
+    S: the split store (2 T^2 slots; allocated when None).  Returns the
+    number of tasks inserted."""
+    import torch
+    n = A.shape[0]
+    assert A.stride(0) == B.stride(0) == C.stride(0) and A.stride(1) == 1
+    T = -(-n // b)
+    slot = spx.lib.spx_ozaki_slot_bytes(b)
+    if slot <= 0:
+        raise ValueError(f"tile {b}: the split path takes b a multiple of 32 in [32, 512]")
+    if S is None:
+        S = torch.empty(2 * T * T * slot, dtype=torch.uint8, device=A.device)
+    nt = ctypes.c_longlong()
+    spx._check(spx.lib.spx_gemm_insert_ozaki(g._h, _ptr(A), _ptr(B), _ptr(C), n, A.stride(0), b,
+                                             1 if commutative else 0, _ptr(S),
+                                             S.numel() * S.element_size(), ctypes.byref(nt)),
+               "spx_gemm_insert_ozaki")
+    g._keep.extend([A, B, C, S])
+    return nt.value
+
+
 def cholesky_flops(n: int, nrhs: int = 0) -> float:
     """Algorithmic flops: n^3/3 for the factorization (leading order, exact
     for the tiled task counts) plus 2 n^2 per right-hand side for the solve."""

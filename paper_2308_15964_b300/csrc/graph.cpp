@@ -225,7 +225,7 @@ int cuda_fail(cudaError_t e) {
 
 // Operand count, shape and mode checks of the built-in ops.
 // Operand count of each built-in op (-1: any, 1..16).
-const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2, 1, 2, 2};
+const int kWantNh[SPX_NUM_OPS] = {1, 2, 2, 3, 3, 2, 3, 2, 3, -1, -1, 2, 2, 3, 2, 2, 1, 2, 2, 1, 1};
 
 int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int>& dt,
                    const unsigned* h, const int* m, int nh) {
@@ -273,6 +273,8 @@ int check_operands(int op, const std::vector<TileDesc>& t, const std::vector<int
     case SPX_OP_TRSM_INV: ok = R(0) == C(0) && C(1) == R(0) && C(1) % 32 == 0; break;
     case SPX_OP_NBODY_SELF: ok = C(0) == 8; break;
     case SPX_OP_NBODY_PAIR: ok = C(0) == 8 && C(1) == 8; break;
+    case SPX_OP_SPLIT:
+    case SPX_OP_SPLIT_T: break;  // the slot's shape is checked with the split store
     default: ok = false;
   }
   if (all_f32 && C(nh - 1) > 16) ok = false;
@@ -330,6 +332,16 @@ int check_lowp(spx_graph* g, int op, int prec, const unsigned* h) {
       break;
     case SPX_OP_SYRK: ins[0] = (int)h[0]; break;
     case SPX_OP_GEMM_NT_SUB: ins[0] = (int)h[0]; ins[1] = (int)h[1]; break;
+    case SPX_OP_GEMM_NN_ADD:  // split prec only, K within one slot
+      if (prec != SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
+      ins[0] = (int)h[0];
+      ins[1] = (int)h[1];
+      break;
+    case SPX_OP_SPLIT:
+    case SPX_OP_SPLIT_T:
+      if (prec != SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
+      ins[0] = (int)h[0];
+      break;
     default: return SPX_ERR_INVALID_ARG;
   }
   for (int i : ins) {
@@ -756,7 +768,10 @@ int spx_task_insert(spx_graph_t g, int op, const unsigned* handles, const int* m
   }
   int rc = check_operands(op, g->tiles, g->tile_dtype, handles, modes, nh);
   if (rc != SPX_OK) return rc;
-  if (op == SPX_OP_TRSM_INV && prec == SPX_F64) return SPX_ERR_INVALID_ARG;  // tensor cores only
+  if ((op == SPX_OP_TRSM_INV || op == SPX_OP_SPLIT || op == SPX_OP_SPLIT_T) && prec == SPX_F64)
+    return SPX_ERR_INVALID_ARG;  // tensor cores / split store only
+  if (op == SPX_OP_GEMM_NN_ADD && prec == SPX_F64_OZAKI && modes[2] == SPX_ATOMIC_WRITE)
+    return SPX_ERR_INVALID_ARG;  // the split product's update is not atomic
   if (prec != SPX_F64) {
     rc = check_lowp(g, op, prec, handles);
     if (rc != SPX_OK) return rc;
@@ -1461,7 +1476,7 @@ int spx_graph_write_dot(spx_graph_t g, const char* path) {
                                            "TRSM_FWD", "GEMM_FWD", "TRSM_BWD", "GEMM_BWD",
                                            "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI",
                                            "TRSM_INV", "NBODY_SELF", "NBODY_PAIR",
-                                           "POTRF_PANEL"};
+                                           "POTRF_PANEL", "SPLIT", "SPLIT_T"};
   std::fprintf(f, "digraph spx {\n");
   for (size_t u = 0; u < N; ++u)
     std::fprintf(f, "  t%zu [label=\"%s #%zu\"];\n", u, names[g->tasks[u].op], u);

@@ -390,7 +390,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
             const TileDesc &Lt = T[t.h[0]], &Ct = T[t.h[1]];
             if (Lt.lmap < 0) return -1;
             return oz_product_units(g, Lt, Lt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, true,
-                                    t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
+                                    t.flags & kFlagFine, kOzSub, u0, u1, tc.st, tc.oz)
                        ? 0
                        : -2;
           }
@@ -411,7 +411,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
             const TileDesc &At = T[t.h[0]], &Bt = T[t.h[1]], &Ct = T[t.h[2]];
             if (At.lmap < 0 || Bt.lmap < 0) return -1;
             return oz_product_units(g, At, Bt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, false,
-                                    t.flags & kFlagFine, false, u0, u1, tc.st, tc.oz)
+                                    t.flags & kFlagFine, kOzSub, u0, u1, tc.st, tc.oz)
                        ? 0
                        : -2;
           }
@@ -429,6 +429,16 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
                             t.flags & kFlagFine);
       return 0;
     case SPX_OP_GEMM_NN_ADD:
+      if constexpr (kMode == 2) {
+        if (t.prec == SPX_F64_OZAKI) {  // C += A B from A's row split and B's column split
+          const TileDesc &At = T[t.h[0]], &Bt = T[t.h[1]], &Ct = T[t.h[2]];
+          if (At.lmap < 0 || Bt.lmap < 0) return -1;
+          return oz_product_units(g, At, Bt, (double*)Ct.ptr, Ct.ld, Ct.rows, Ct.cols, false,
+                                  t.flags & kFlagFine, kOzAdd, u0, u1, tc.st, tc.oz)
+                     ? 0
+                     : -2;
+        }
+      }
       op_gemm<false, true>(T[t.h[0]], T[t.h[1]], T[t.h[2]], T[t.h[0]].cols, 1.0, u0, u1, s,
                            t.flags & kFlagFine, t.flags & kFlagAtomic);
       return 0;
@@ -487,7 +497,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
             const TileDesc &Vt = T[t.h[0]], &At = T[t.h[1]];
             if (At.lmap < 0 || Vt.lmap < 0) return -1;
             return oz_product_units(g, At, Vt, (double*)At.ptr, At.ld, At.rows, At.cols, false,
-                                    t.flags & kFlagFine, true, u0, u1, tc.st, tc.oz)
+                                    t.flags & kFlagFine, kOzStore, u0, u1, tc.st, tc.oz)
                        ? 0
                        : -2;
           }
@@ -508,6 +518,16 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       }
       op_trtri_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s);
       return 0;
+    case SPX_OP_SPLIT:
+    case SPX_OP_SPLIT_T:
+      if constexpr (kMode == 2) {
+        if (t.op == SPX_OP_SPLIT)
+          op_oz_split(T[t.h[0]], u0, u1);
+        else  // the V staging area is free between products: the column maxima
+          op_oz_split_t(T[t.h[0]], u0, u1, reinterpret_cast<unsigned long long*>(&tc.oz->v[0][0]));
+        return 0;
+      }
+      return -1;
     case SPX_OP_NOP:
       return 0;
     case SPX_OP_SPIN:

@@ -417,7 +417,10 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
       if (prec != SPX_F64) return cdiv128(t[h[2]].rows) * cdiv128(t[h[2]].cols);
       return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
     case SPX_OP_GEMM_NN_ADD:
+      if (prec == SPX_F64_OZAKI) return oz_units(t[h[2]].rows, t[h[2]].cols, false, fine, 0, nullptr);
       return (fine ? cdiv16(t[h[2]].rows) : cdiv64(t[h[2]].rows)) * cdiv64(t[h[2]].cols);
+    case SPX_OP_SPLIT: return cdiv64(t[h[0]].rows);    // 64 rows per unit
+    case SPX_OP_SPLIT_T: return cdiv64(t[h[0]].cols);  // 64 columns per unit
     case SPX_OP_GEMM_FWD:
     case SPX_OP_GEMM_BWD:
       return rhs_row_units(t[h[2]].rows, t[h[2]].cols) * rhs_col_blocks(t[h[2]].cols);

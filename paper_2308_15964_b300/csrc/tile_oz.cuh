@@ -199,6 +199,85 @@ __device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32
   }
 }
 
+// Split the transpose of the FP64 tile Xt into its slot: slot row c is column
+// c of Xt (exponent e_c = the column's), the K index is Xt's row, so that a
+// product reading this slot as its B operand forms A Xt (the NN form of the
+// tiled GEMM).  Unit u = columns [64 u, 64 u + 64); K indices rows..b-1 are
+// written as zeros.  Warp w takes the 32 columns 64 u + 32 (w & 1) + lane and
+// the 16-row K chunks j = w / 2, w / 2 + 4, ...: loads of one row are 256
+// coalesced bytes, and one lane's 16 digits of a chunk and plane are the 32
+// contiguous bytes of its slot row, so a warp's stores are 1 KB runs.  The
+// column maximum is reduced over the four chunk warps through red (2 KB of
+// shared memory, 4 x 64 words).
+__device__ __noinline__ void op_oz_split_t(const TileDesc& Xt, uint32_t u0, uint32_t u1,
+                                           unsigned long long* red) {
+  const int b = Xt.lowp_ld, nch = b / 16;
+  uint4* S = reinterpret_cast<uint4*>(Xt.lowp);  // 32 bytes = 2 x uint4 per (plane, chunk, row)
+  int* Ex = reinterpret_cast<int*>(reinterpret_cast<char*>(Xt.lowp) + (size_t)16 * b * b);
+  const double* A = reinterpret_cast<const double*>(Xt.ptr);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = warp & 1, q = warp >> 1;
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int c = (int)u * 64 + 32 * half + lane;
+    const bool live = c < Xt.cols;
+    unsigned long long mx = 0;
+    for (int j = q; j < nch; j += 4) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int r = 16 * j + i;
+        if (live && r < Xt.rows) {
+          const unsigned long long mag =
+              (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * Xt.ld + c)) &
+              0x7FFFFFFFFFFFFFFFull;
+          mx = mag > mx ? mag : mx;
+        }
+      }
+    }
+    red[q * 64 + 32 * half + lane] = mx;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned long long y = red[k * 64 + 32 * half + lane];
+      mx = y > mx ? y : mx;
+    }
+    __syncthreads();  // red is reused by the next unit
+    const int ef = (int)(mx >> 52);
+    const int e = ef ? ef - 1022 : -1022;
+    if (!live) continue;  // slot rows past the tile's columns are never read
+    if (q == 0) Ex[c] = e;
+    for (int j = q; j < nch; j += 4) {
+      uint32_t pk[kOzPlanes][8];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int r = 16 * j + i;
+        const unsigned long long bits =
+            r < Xt.rows ? (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * Xt.ld + c))
+                        : 0ull;
+        long long X = oz_fixed(bits, e);
+        int sg[kOzPlanes];
+#pragma unroll
+        for (int s = kOzPlanes - 1; s >= 1; --s) {
+          const int d = (int)((X + 64) & 127) - 64;
+          sg[s] = d;
+          X = (X - d) >> 7;
+        }
+        sg[0] = (int)X;
+#pragma unroll
+        for (int s = 0; s < kOzPlanes; ++s) {
+          const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn((float)sg[s]));
+          pk[s][i >> 1] = (i & 1) ? (pk[s][i >> 1] | (h << 16)) : h;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < kOzPlanes; ++s) {
+        uint4* dst = S + (((size_t)s * nch + j) * b + c) * 2;
+        dst[0] = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+        dst[1] = make_uint4(pk[s][4], pk[s][5], pk[s][6], pk[s][7]);
+      }
+    }
+  }
+}
+
 // Shared-memory bytes of one K step of the split operands: 8 planes x (128
 // rows of A + kN rows of B) x 16 digits.
 __host__ __device__ constexpr int oz_stage_bytes(int kN) { return kOzPlanes * (kTcM + kN) * 32; }
@@ -239,7 +318,7 @@ template <int kS>
 __device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMap* amap,
                             int a_slot, int a_r0, const CUtensorMap* bmap, int b_slot, int b_c0,
                             int nblk, int K, const int* a_exp, const int* b_exp, double* C,
-                            int ldc, int m, int n, int diag, bool store) {
+                            int ldc, int m, int n, int diag, int wmode) {
   constexpr int kN = 64, kStage = oz_stage_bytes(kN), kStageA = kOzPlanes * kTcM * 32;
   static_assert(kStage % 1024 == 0 && kS <= kTcBars, "stages");
   constexpr int kLdv = kN + 1;
@@ -354,7 +433,7 @@ __device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMa
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
           const int e = e0 + 224 * i, rr = e / kN, c = e % kN, cg = kN * blk + c;
-          cv[i] = (!store && e < kTcM * kN && rr < m && cg < n && cg <= rr + diag)
+          cv[i] = (wmode != 1 && e < kTcM * kN && rr < m && cg < n && cg <= rr + diag)
                       ? C[(size_t)rr * ldc + cg]
                       : 0.0;
         }
@@ -362,8 +441,9 @@ __device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMa
         for (int i = 0; i < kBatch; ++i) {
           const int e = e0 + 224 * i, rr = e / kN, c = e % kN, cg = kN * blk + c;
           if (e < kTcM * kN && rr < m && cg < n && cg <= rr + diag)
-            C[(size_t)rr * ldc + cg] =
-                store ? V[rr * kLdv + c] : __dsub_rn(cv[i], V[rr * kLdv + c]);
+            C[(size_t)rr * ldc + cg] = wmode == 1   ? V[rr * kLdv + c]  // store
+                                       : wmode == 2 ? __dadd_rn(cv[i], V[rr * kLdv + c])
+                                                    : __dsub_rn(cv[i], V[rr * kLdv + c]);
         }
       }
     }
@@ -383,6 +463,9 @@ __device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMa
   return !s.error;
 }
 
+// Write modes of a split product into its FP64 output.
+constexpr int kOzSub = 0, kOzStore = 1, kOzAdd = 2;
+
 // Shared-memory layout of the split ops in the one-CTA-per-SM kernel:
 // three operand stages, then the staging of one finished block.
 constexpr int kOzPipeStages = 3;
@@ -396,11 +479,12 @@ __device__ __forceinline__ const int* oz_exps(const TileDesc& t) {
                                       (size_t)16 * t.lowp_ld * t.lowp_ld);
 }
 
-// C (FP64, rows x cols) -= / = A B^T from the slots of A and B, units u0..u1
+// C (FP64, rows x cols) -= / = / += A B^T (wmode kOzSub / kOzStore / kOzAdd)
+// from the slots of A and B, units u0..u1
 // of oz_units (lower: SYRK's blocks; C's (0,0) is the output's).
 __device__ __noinline__ bool oz_product_units(const DevGraph& g, const TileDesc& At,
                                               const TileDesc& Bt, double* C, int ldc, int rows,
-                                              int cols, bool lower, bool fine, bool store,
+                                              int cols, bool lower, bool fine, int wmode,
                                               uint32_t u0, uint32_t u1, TcState* st, OzBuf* buf) {
   const int* ae = oz_exps(At);
   const int* be = oz_exps(Bt);
@@ -412,7 +496,7 @@ __device__ __noinline__ bool oz_product_units(const DevGraph& g, const TileDesc&
                                     At.lr0, r0, g.maps + Bt.lmap + 1, Bt.lr0, c0, (int)blk[2],
                                     At.cols, ae + r0, be + c0, C + (size_t)r0 * ldc + c0, ldc,
                                     min(kTcM, rows - r0), cols - c0, lower ? r0 - c0 : 1 << 30,
-                                    store))
+                                    wmode))
       return false;
   }
   return true;

@@ -11,6 +11,7 @@
 //   * the scheduler-overhead pattern of the paper's engine benchmark: chains
 //     of tasks that only wait.
 #include <cstdint>
+#include <initializer_list>
 #include <vector>
 
 #include "spx.h"
@@ -485,6 +486,60 @@ extern "C" int spx_gemm_insert(spx_graph_t g, double* dev_A, double* dev_B, doub
         rc = spx_task_insert(g, SPX_OP_GEMM_NN_ADD, hs, ms, 3, 0, SPX_F64, nullptr);
         if (rc == SPX_OK) ++count;
       }
+  if (out_ntasks) *out_ntasks = count;
+  return rc;
+}
+
+extern "C" int spx_gemm_insert_ozaki(spx_graph_t g, double* dev_A, double* dev_B, double* dev_C,
+                                     int n, int ld, int b, int commutative, void* dev_S,
+                                     long long S_bytes, long long* out_ntasks) {
+  if (!g || !dev_A || !dev_B || !dev_C || n < 1 || ld < n || commutative < 0 ||
+      commutative > 1 || !dev_S || ((uintptr_t)dev_S & 255))
+    return SPX_ERR_INVALID_ARG;
+  const long long slot = spx_ozaki_slot_bytes(b);
+  if (!slot) return SPX_ERR_INVALID_ARG;
+  const int T = (n + b - 1) / b;
+  const long long nslots = 2LL * T * T;
+  if (S_bytes < nslots * slot || nslots > 0x7FFFFFFF) return SPX_ERR_INVALID_ARG;
+  int rc = spx_ozaki_register(g, dev_S, (int)nslots, b, nullptr);
+  if (rc != SPX_OK) return rc;
+  // A_ik owns slot i T + k, B_kj slot T^2 + k T + j
+  Tiles A, B, C;
+  A.T = B.T = T;
+  A.b = B.b = b;
+  A.h.assign((size_t)T * T, 0);
+  B.h.assign((size_t)T * T, 0);
+  char* S = (char*)dev_S;
+  for (int i = 0; i < T && rc == SPX_OK; ++i)
+    for (int j = 0; j < T && rc == SPX_OK; ++j) {
+      const int r = n - i * b < b ? n - i * b : b;
+      const int c = n - j * b < b ? n - j * b : b;
+      const size_t off = (size_t)i * b * ld + (size_t)j * b;
+      rc = spx_tile_register(g, dev_A + off, r, c, ld, SPX_DT_F64,
+                             S + ((long long)i * T + j) * slot, b, &A.at(i, j));
+      if (rc == SPX_OK)
+        rc = spx_tile_register(g, dev_B + off, r, c, ld, SPX_DT_F64,
+                               S + ((long long)T * T + (long long)i * T + j) * slot, b,
+                               &B.at(i, j));
+    }
+  if (rc == SPX_OK) rc = register_tiles(g, dev_C, n, n, ld, b, false, C);
+  long long count = 0;
+  auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms) {
+    const int r = spx_task_insert(g, op, hs.begin(), ms.begin(), (int)hs.size(), 0,
+                                  SPX_F64_OZAKI, nullptr);
+    if (r == SPX_OK) ++count;
+    return r;
+  };
+  for (int i = 0; i < T && rc == SPX_OK; ++i)
+    for (int k = 0; k < T && rc == SPX_OK; ++k) rc = ins(SPX_OP_SPLIT, {A.at(i, k)}, {SPX_WRITE});
+  for (int k = 0; k < T && rc == SPX_OK; ++k)
+    for (int j = 0; j < T && rc == SPX_OK; ++j) rc = ins(SPX_OP_SPLIT_T, {B.at(k, j)}, {SPX_WRITE});
+  const int mode = commutative ? SPX_COMMUTATIVE_WRITE : SPX_WRITE;
+  for (int i = 0; i < T && rc == SPX_OK; ++i)
+    for (int j = 0; j < T && rc == SPX_OK; ++j)
+      for (int k = 0; k < T && rc == SPX_OK; ++k)
+        rc = ins(SPX_OP_GEMM_NN_ADD, {A.at(i, k), B.at(k, j), C.at(i, j)},
+                 {SPX_READ, SPX_READ, mode});
   if (out_ntasks) *out_ntasks = count;
   return rc;
 }

@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libspx.so")
 READ, WRITE, COMMUTATIVE_WRITE, ATOMIC_WRITE, MAYBE_WRITE = 0, 1, 2, 3, 4
 (OP_POTRF, OP_TRSM, OP_SYRK, OP_GEMM_NT_SUB, OP_GEMM_NN_ADD, OP_TRSM_L_FWD, OP_GEMM_FWD,
  OP_TRSM_LT_BWD, OP_GEMM_BWD, OP_NOP, OP_SPIN, OP_COPY, OP_AXPY, OP_TRMM, OP_TRTRI,
- OP_TRSM_INV, OP_NBODY_SELF, OP_NBODY_PAIR, OP_POTRF_PANEL) = range(19)
+ OP_TRSM_INV, OP_NBODY_SELF, OP_NBODY_PAIR, OP_POTRF_PANEL, OP_SPLIT, OP_SPLIT_T) = range(21)
 OP_NAMES = ("POTRF", "TRSM", "SYRK", "GEMM_NT_SUB", "GEMM_NN_ADD", "TRSM_L_FWD", "GEMM_FWD",
             "TRSM_LT_BWD", "GEMM_BWD", "NOP", "SPIN", "COPY", "AXPY", "TRMM", "TRTRI", "TRSM_INV",
-            "NBODY_SELF", "NBODY_PAIR", "POTRF_PANEL")
+            "NBODY_SELF", "NBODY_PAIR", "POTRF_PANEL", "SPLIT", "SPLIT_T")
 F64, TF32, BF16, F64_OZAKI = 0, 1, 2, 3
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 EXEC_PERSISTENT, EXEC_PER_TASK, EXEC_STREAMS = 0, 1, 2
@@ -77,6 +77,7 @@ def _load():
         "spx_graph_timing": (I, [P, P, P]),
         "spx_cholesky_insert": (I, [P, P, I, I, I, P, I, I, I, I, P]),
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
+        "spx_gemm_insert_ozaki": (I, [P, P, P, P, I, I, I, I, P, LL, P]),
         "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),

@@ -473,3 +473,160 @@ def test_fused_panel_integer_and_not_spd(S):
     rc, info = g.run()
     assert info == info_o and info > 0
     g.close()
+
+
+# --- the NN form: SPLIT / SPLIT_T tasks and GEMM_NN_ADD on split products ----
+
+def split_nn_graph(S, Ad, Bd, b):
+    """Graph: SPLIT(A) into slot 0, SPLIT_T(B) into slot 1 of a fresh store."""
+    slot = S.lib.spx_ozaki_slot_bytes(b)
+    store = torch.full((2 * slot,), 0x7F, dtype=torch.uint8, device="cuda")  # not zeros
+    g = S.Graph()
+    g.register_ozaki(store.data_ptr(), 2, b)
+    hA = g.register(Ad.data_ptr(), Ad.shape[0], Ad.shape[1], Ad.stride(0), S.DT_F64,
+                    store.data_ptr(), b)
+    hB = g.register(Bd.data_ptr(), Bd.shape[0], Bd.shape[1], Bd.stride(0), S.DT_F64,
+                    store.data_ptr() + slot, b)
+    g.insert(S.OP_SPLIT, [hA], [S.WRITE], prec=S.F64_OZAKI)
+    g.insert(S.OP_SPLIT_T, [hB], [S.WRITE], prec=S.F64_OZAKI)
+    g._keep.append(store)
+    return g, store, slot, hA, hB
+
+
+@pytest.mark.parametrize("m,n,K", [(128, 64, 512), (200, 70, 136), (33, 130, 200),
+                                   (512, 512, 512), (77, 33, 40)])
+def test_gemm_nn_op_bit_exact(S, m, n, K):
+    """SPLIT writes the oracle's row split of A, SPLIT_T the split of B^T
+    (column exponents, K = B's rows, zero K padding over a store that starts
+    non-zero); GEMM_NN_ADD then equals the oracle's C + A B bit for bit."""
+    rng = np.random.default_rng(7 * m + 3 * n + K)
+    A = spread_rows(rng, m, K)
+    B = np.ascontiguousarray(spread_rows(rng, n, K).T)  # columns of spread magnitudes
+    C = rng.standard_normal((m, n))
+    b = r32(max(m, n, K))
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+    g, store, slot, hA, hB = split_nn_graph(S, Ad, Bd, b)
+    hC = g.register_tensor(Cd)
+    g.insert(S.OP_GEMM_NN_ADD, [hA, hB, hC], [S.READ, S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(Ad.cpu().numpy(), A) and np.array_equal(Bd.cpu().numpy(), B)
+    check_split(store, slot, 0, b, A)
+    check_split(store, slot, 1, b, B.T)
+    assert np.array_equal(Cd.cpu().numpy(), Z.gemm_nn_add(C, A, B))
+    g.close()
+
+
+def test_gemm_nn_worst_case_exact(S):
+    """The worst digit sums (P_7 just below 2^24) through the NN form."""
+    A = worst_case(128, 512)
+    B = np.ascontiguousarray(worst_case(64, 512).T)
+    B[:, 3::5] *= -1.0
+    C = np.zeros((128, 64))
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+    g, store, slot, hA, hB = split_nn_graph(S, Ad, Bd, 512)
+    hC = g.register_tensor(Cd)
+    g.insert(S.OP_GEMM_NN_ADD, [hA, hB, hC], [S.READ, S.READ, S.WRITE], prec=S.F64_OZAKI)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(Cd.cpu().numpy(), Z.gemm_nn_add(C, A, B))
+    g.close()
+
+
+def test_gemm_nn_rejects_bad_use(S):
+    """SPLIT needs the split prec and a slot; the split GEMM is not atomic."""
+    Ad = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    Bd, Cd = torch.zeros_like(Ad), torch.zeros_like(Ad)
+    g, store, slot, hA, hB = split_nn_graph(S, Ad, Bd, 64)
+    hC = g.register_tensor(Cd)
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_SPLIT, [hA], [S.WRITE], prec=S.F64)
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_SPLIT, [hC], [S.WRITE], prec=S.F64_OZAKI)  # no slot
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_GEMM_NN_ADD, [hA, hB, hC], [S.READ, S.READ, S.ATOMIC_WRITE],
+                 prec=S.F64_OZAKI)
+    with pytest.raises(S.SpxError):
+        g.insert(S.OP_GEMM_NN_ADD, [hA, hC, hB], [S.READ, S.READ, S.WRITE], prec=S.F64_OZAKI)
+    g.close()
+
+
+def run_gemm_ozaki(S, A, B, C, b, commutative=False, **cfg):
+    from paper_2308_15964_b300 import cholesky
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+    g = S.Graph(**cfg)
+    nt = cholesky.gemm_ozaki_graph(g, Ad, Bd, Cd, b, commutative=commutative)
+    rc = g.run()[0]
+    torch.cuda.synchronize()
+    out = Cd.cpu().numpy()
+    g.close()
+    return rc, nt, out
+
+
+@pytest.mark.parametrize("n,b", [(600, 128), (512, 256), (96, 32)])
+def test_gemm_dag_vs_oracle(S, n, b):
+    """spx_gemm_insert_ozaki (WRITE on C_ij: k in order) bit for bit against
+    the oracle's tiled split GEMM, with the persistent and per-task
+    executors; ragged last tiles."""
+    rng = np.random.default_rng(n + b)
+    A = inputs.uniform((n, n), seed=n).numpy()
+    B = rng.uniform(-1, 1, (n, n)) * np.exp2(rng.integers(-20, 20, size=(1, n)))
+    C = rng.uniform(-1, 1, (n, n))
+    want = Z.tiled_gemm_nn_add(A, B, C.copy(), b)
+    T = -(-n // b)
+    for ex in (S.EXEC_PERSISTENT, S.EXEC_PER_TASK):
+        rc, nt, got = run_gemm_ozaki(S, A, B, C, b, executor=ex)
+        assert rc == 0 and nt == 2 * T * T + T ** 3
+        assert np.array_equal(got, want), ex
+    # FP64's accuracy against the exact-enough reference
+    ref = C + A @ B
+    scale = np.abs(A) @ np.abs(B) + np.abs(C)
+    assert np.max(np.abs(want - ref) / scale) < 1e-14
+
+
+def test_gemm_dag_commutative(S):
+    """COMMUTATIVE_WRITE: the k order of a block is free, so the result
+    equals the oracle's to rounding, and bit for bit on integer inputs
+    (every split product and sum then exact)."""
+    n, b = 512, 128
+    rng = np.random.default_rng(5)
+    A = rng.uniform(-1, 1, (n, n))
+    B = rng.uniform(-1, 1, (n, n))
+    C = rng.uniform(-1, 1, (n, n))
+    rc, _, got = run_gemm_ozaki(S, A, B, C, b, commutative=True)
+    assert rc == 0
+    want = Z.tiled_gemm_nn_add(A, B, C.copy(), b)
+    assert np.max(np.abs(got - want)) <= 4 * 2.0 ** -52 * np.max(np.abs(want))
+    Ai = rng.integers(-2 ** 19, 2 ** 19, size=(n, n)).astype(np.float64)
+    Bi = rng.integers(-2 ** 19, 2 ** 19, size=(n, n)).astype(np.float64)
+    Ci = rng.integers(-2 ** 30, 2 ** 30, size=(n, n)).astype(np.float64)
+    rc, _, got = run_gemm_ozaki(S, Ai, Bi, Ci, b, commutative=True)
+    assert rc == 0
+    exact = (Ci.astype(np.int64) + Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(got, exact)
+
+
+def test_gemm_dag_8192_sampled(S):
+    """The benchmark's size (n = 8192, tile 512, entries uniform[-1, 1]),
+    WRITE form: sampled entries against the oracle's split products taken
+    one entry and one k at a time, in the tasks' order."""
+    from paper_2308_15964_b300 import cholesky
+    n, b = 8192, 512
+    Ad, Bd, Cd = (inputs.uniform((n, n), sd, device="cuda") for sd in (3, 4, 5))
+    A, B, C = Ad.cpu(), Bd.cpu(), Cd.cpu()
+    g = S.Graph()
+    cholesky.gemm_ozaki_graph(g, Ad, Bd, Cd, b)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    got = Cd.cpu().numpy()
+    g.close()
+    An, Bn, Cn = A.numpy(), B.numpy(), C.numpy()
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([[0, n - 1, 511, 512], rng.integers(0, n, 12)])
+    cols = np.concatenate([[n - 1, 0, 512, 511], rng.integers(0, n, 12)])
+    for r, c in zip(rows, cols):
+        v = Cn[r, c]
+        for k in range(n // b):
+            ks = slice(k * b, (k + 1) * b)
+            v = v + Z.products(An[r:r + 1, ks], Bn[ks, c][None, :])[0, 0]
+        assert got[r, c] == v, (r, c)

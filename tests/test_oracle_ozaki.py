@@ -137,6 +137,47 @@ def test_error_bound_worst_case_catches_dropped_pair():
     assert Fraction(K * (2 * 63 * 64 + 6 * 64 * 64), 2 ** 61) > Fraction(K * 91, 10) * Fraction(2) ** -56
 
 
+def test_gemm_nn_add_integer_exact():
+    """Integer A, B below 2^19: the NN split product is exact, so C + A B
+    equals the integer sum (tiled too, whatever the tile size)."""
+    rng = np.random.default_rng(11)
+    A = rng.integers(-2 ** 19, 2 ** 19, size=(37, 70))
+    B = rng.integers(-2 ** 19, 2 ** 19, size=(70, 45))
+    C = rng.integers(-2 ** 40, 2 ** 40, size=(37, 45))
+    want = (C + A @ B).astype(np.float64)
+    got = Z.gemm_nn_add(C.astype(np.float64), A.astype(np.float64), B.astype(np.float64))
+    assert np.array_equal(got, want)
+    n = 70
+    A2 = rng.integers(-2 ** 19, 2 ** 19, size=(n, n))
+    B2 = rng.integers(-2 ** 19, 2 ** 19, size=(n, n))
+    C2 = rng.integers(-2 ** 30, 2 ** 30, size=(n, n))
+    for b in (32, 64):
+        got = Z.tiled_gemm_nn_add(A2.astype(np.float64), B2.astype(np.float64),
+                                  C2.astype(np.float64), b)
+        assert np.array_equal(got, (C2 + A2 @ B2).astype(np.float64))
+
+
+def test_gemm_nn_add_splits_columns_of_b():
+    """Each column of B carries its own exponent: scaling column c of B by
+    2^s scales column c of the product by exactly 2^s and leaves the others
+    bit for bit.  A split of B by rows (a transposed operand) would mix the
+    columns' magnitudes in one row exponent and fail both."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((9, 40))
+    B = rng.standard_normal((40, 6))
+    C = np.zeros((9, 6))
+    base = Z.gemm_nn_add(C, A, B)
+    for c, sh in ((0, 40), (3, -35), (5, 7)):
+        B2 = B.copy()
+        B2[:, c] *= 2.0 ** sh
+        got = Z.gemm_nn_add(C, A, B2)
+        assert np.array_equal(got[:, c], base[:, c] * 2.0 ** sh)
+        others = [j for j in range(6) if j != c]
+        assert np.array_equal(got[:, others], base[:, others])
+    # and the result is within the scheme's bound of the exact product
+    bound_check(A, np.ascontiguousarray(B.T))
+
+
 def test_syrk_lower_matches_gemm():
     rng = np.random.default_rng(7)
     L = rng.standard_normal((20, 33))
