@@ -94,6 +94,8 @@ def parse():
     p.add_argument("--workload", default="cholesky", choices=["cholesky", "gemm", "batch", "mixed", "serve", "tc",
                                                       "overhead", "axpy", "nbody", "splitgemm", "stream"],
                    help="batch: 4096 uneven solves (n in 32..1024, 1..16 RHS) in one launch")
+    p.add_argument("--gemm-rows", default="all", choices=["all", "split", "f64"],
+                   help="gemm: which DAG forms to time (split products, FP64 pipe, or both)")
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second")
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -544,7 +546,8 @@ def main():
         dist.destroy_process_group()
 
 
-def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, comparators=False):
+def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, comparators=False,
+             rows="all"):
     """The paper's tiled GEMM whose tasks depend on the blocks of C (section
     "Numerical applications"): C += A B, one GEMM_NN_ADD task per (i, j, k),
     each with a WRITE on C_ij (the 16 tasks of a block form a chain) or a
@@ -586,7 +589,7 @@ def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, compara
                 rec.append((ev[0].elapsed_time(ev[1]), g.timing()[1]))
         return rec
 
-    for mode, comm in (("write", False), ("commutative", True)):
+    for mode, comm in (("write", False), ("commutative", True)) if rows != "split" else ():
         g = spx.Graph()
         rec = timed(g, comm, steps, warmup)
         ntasks, nedges, _, _ = g.sizes()
@@ -621,7 +624,7 @@ def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, compara
     tensor_flops = T ** 3 * (-(-b // 128)) * (-(-b // 64)) * block_flops
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     bf16 = peaks.get("bf16_tflops", 1800.0)
-    for mode, comm in (("split_write", False), ("split_commutative", True)):
+    for mode, comm in (("split_write", False), ("split_commutative", True)) if rows != "f64" else ():
         g = spx.Graph()
         rec = timed(g, comm, steps, warmup, split=True)
         ntasks, nedges, _, _ = g.sizes()
@@ -669,15 +672,25 @@ def run_gemm(args, world, rank, local):
     from paper_2308_15964_b300 import cholesky, inputs, spx
     n = args.n if args.n != 16384 else 8192
     with Clocks(local) as clk:
+        rows = args.gemm_rows
+        if rows == "all" and args.no_extras:  # the line's own form only
+            rows = "split" if args.arith == "ozaki" else "f64"
         res = gemm_dag(spx, cholesky, inputs, torch, n, args.tile, args.warmup, args.steps, 2032.0,
-                       comparators=not args.no_extras)
+                       comparators=not args.no_extras, rows=rows)
     clocks = clk.summary()
-    w = res["write"]
+    # the line's value: the split-product DAG (--arith ozaki, default) or
+    # the FP64 SIMT DAG (--arith f64), WRITE form; every row in gemm_dag
+    oz = args.arith == "ozaki"
+    w = res["split_write" if oz else "write"]
     out = {"metric": METRIC, "value": w["value"], "unit": "GFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["ms_per_step"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": ("f64 (products emulated by Ozaki splitting: bf16 digit planes on tcgen05, "
+                     "exact fp32 digit sums, one fp64 rounding per task)") if oz else "f64",
            "data": "synthetic",
-           "config": {"workload": res["workload"], "n": n, "tile": args.tile,
+           "config": {"workload": res["workload"] + (", products split on the tensor cores "
+                                                     "(SPLIT / SPLIT_T tasks first)" if oz else ""),
+                      "arith": args.arith, "n": n, "tile": args.tile,
                       "l2": "inputs larger than L2 (3 x 8 n^2 bytes)"},
            "roofline": w["roofline"], "cpu_baseline": res["cpu_baseline"], "gemm_dag": res,
            "clocks": clocks, "gpu_launches": 2 * args.steps}
