@@ -955,6 +955,7 @@ int spx_graph_assign_priorities(spx_graph_t g) {
     uint32_t items = 1;
     if (!(t.flags & kFlagSerial)) {
       t.flags = (uint8_t)((t.flags & ~kFlagFine) | (cls == 2 ? kFlagFine : 0));
+      t.nphases = task_phases(t, g->tiles.data());  // the TRSM row form has fewer
       t.nparts = phase_parts(task_phase_units(t, g->tiles.data(), 0));
       items = 0;
       for (uint32_t ph = 0; ph < t.nphases; ++ph)

@@ -366,7 +366,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_POTRF_PANEL:
       if (t.prec == SPX_F64_OZAKI && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
         if constexpr (kMode == 2) {
-          op_oz_split(T[t.h[1]], u0, u1);
+          op_oz_split(T[t.h[1]], u0, u1, &tc.oz->v[0][0]);
           return 0;
         }
         return -1;
@@ -374,14 +374,17 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
       return op_potrf_panel_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s, t.flags & kFlagFine);
     case SPX_OP_TRSM:
       if constexpr (kTc) {
-        if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h)) {
-          if (t.prec == SPX_F64_OZAKI) op_oz_split(T[t.h[1]], u0, u1);
+        if (lowp && phase + 1 == op_phases(t.op, t.prec, T, t.h, t.flags & kFlagFine)) {
+          if (t.prec == SPX_F64_OZAKI) op_oz_split(T[t.h[1]], u0, u1, &tc.oz->v[0][0]);
           else if (t.prec == SPX_BF16) op_lowp_copy<true>(T[t.h[1]], u0, u1);
           else op_lowp_copy<false>(T[t.h[1]], u0, u1);
           return 0;
         }
       }
-      op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s, t.flags & kFlagFine);
+      if (trsm_row_form(T[t.h[1]].cols, t.flags & kFlagFine))
+        op_trsm_rows(T[t.h[0]], T[t.h[1]], u0, u1, s);
+      else
+        op_trsm_units(T[t.h[0]], T[t.h[1]], phase, u0, u1, s, t.flags & kFlagFine);
       return 0;
     case SPX_OP_SYRK:
       if constexpr (kTc) {
@@ -490,7 +493,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
         if constexpr (kMode == 2) {
           if (t.prec == SPX_F64_OZAKI) {
             if (phase != 1) {  // split the input (phase 0) or the result (phase 2)
-              op_oz_split(T[t.h[1]], u0, u1);
+              op_oz_split(T[t.h[1]], u0, u1, &tc.oz->v[0][0]);
               return 0;
             }
             // A <- A V^T: the product reads A's and V's slots, then stores A
@@ -511,7 +514,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_TRTRI:
       if (t.prec == SPX_F64_OZAKI && phase == trtri_phases(T[t.h[0]].rows)) {
         if constexpr (kTc) {
-          op_oz_split(T[t.h[1]], u0, u1);
+          op_oz_split(T[t.h[1]], u0, u1, &tc.oz->v[0][0]);
           return 0;
         }
         return -1;
@@ -522,7 +525,7 @@ __device__ int run_units(const DevGraph& g, const TaskDesc& t, uint32_t phase, u
     case SPX_OP_SPLIT_T:
       if constexpr (kMode == 2) {
         if (t.op == SPX_OP_SPLIT)
-          op_oz_split(T[t.h[0]], u0, u1);
+          op_oz_split(T[t.h[0]], u0, u1, &tc.oz->v[0][0]);
         else  // the V staging area is free between products: the column maxima
           op_oz_split_t(T[t.h[0]], u0, u1, reinterpret_cast<unsigned long long*>(&tc.oz->v[0][0]));
         return 0;
@@ -558,7 +561,7 @@ __device__ int run_part(const DevGraph& g, const TaskDesc& t, uint32_t phase, ui
     --phase;
   }
   if (t.flags & kFlagSerial) {
-    const uint32_t nph = op_phases(t.op, t.prec, T, t.h);
+    const uint32_t nph = op_phases(t.op, t.prec, T, t.h, t.flags & kFlagFine);
     for (uint32_t ph = 0; ph < nph; ++ph) {
       const uint32_t nu = op_phase_units(t.op, t.prec, T, t.h, ph, t.flags & kFlagFine);
       const int r = run_units<kMode>(g, t, ph, 0, nu, s, tc);

@@ -249,6 +249,10 @@ struct DevGraph {
 //     for the POTRF and SYRK updates: one SM
 //     does about 2 FP64 FMA per clock, so a 64 x 64 x 64 unit alone takes
 //     tens of microseconds, and the critical path is a chain of such units.
+//   Fine TRSM with n <= 512 (row form): one phase of kTrsmRows-row units,
+//     each solving all column blocks of its rows (rows are independent); the
+//     2 nbc - 1 phase boundaries of the column form, each waiting for CTAs
+//     to pick up its parts, were most of a critical panel solve's time.
 //   TRSM_INV (A_ik <- A_ik V^T, tensor cores): one phase, 128-row blocks of
 //     A_ik (each block runs its 128-column output blocks right to left: output
 //     column c needs input columns <= c only, V being lower triangular, so
@@ -349,17 +353,27 @@ __host__ __device__ inline uint32_t oz_units(int rows, int cols, bool lower, boo
   return total;
 }
 
+// Row form of the TRSM of critical-path tasks: units of kTrsmRows rows, the
+// rows held in shared memory (n <= kTrsmRowMaxN).
+constexpr int kTrsmRows = 4;
+constexpr int kTrsmRowMaxN = 512;
+__host__ __device__ inline bool trsm_row_form(int n, bool fine) {
+  return fine && n <= kTrsmRowMaxN;
+}
+
 // Low-precision tasks (prec = SPX_TF32 / SPX_BF16): SYRK and GEMM_NT_SUB run
 // on the tensor cores in 128 x 128 output units (SYRK: lower block pairs);
 // TRSM runs its FP64 phases and then one more phase that writes the
 // low-precision copy of its result (64-row units).
 __host__ __device__ inline uint32_t op_phases(int op, int prec, const TileDesc* t,
-                                              const uint32_t* h) {
+                                              const uint32_t* h, bool fine = false) {
   switch (op) {
     case SPX_OP_POTRF: return 3 * cdiv64(t[h[0]].rows) - 2;
     case SPX_OP_POTRF_PANEL:  // POTRF's, one more solving A_ik's last block; split prec: the split
       return 3 * cdiv64(t[h[0]].rows) - 1 + (prec == SPX_F64_OZAKI ? 1u : 0u);
-    case SPX_OP_TRSM: return 2 * cdiv64(t[h[1]].cols) - 1 + (prec != SPX_F64 ? 1u : 0u);
+    case SPX_OP_TRSM:
+      return (trsm_row_form(t[h[1]].cols, fine) ? 1u : 2 * cdiv64(t[h[1]].cols) - 1) +
+             (prec != SPX_F64 ? 1u : 0u);
     case SPX_OP_TRSM_L_FWD:
     case SPX_OP_TRSM_LT_BWD: return 2 * cdiv64(t[h[0]].rows) - 1;
     case SPX_OP_TRTRI:  // split prec: one more phase splits V into its slot
@@ -402,6 +416,8 @@ __host__ __device__ inline uint32_t op_phase_units(int op, int prec, const TileD
     }
     case SPX_OP_TRSM: {
       const uint32_t nbr = cdiv64(t[h[1]].rows), nbc = cdiv64(t[h[1]].cols), j = phase / 2;
+      if (trsm_row_form(t[h[1]].cols, fine))  // the solve, then the low-precision copy
+        return phase == 0 ? ((uint32_t)t[h[1]].rows + kTrsmRows - 1) / kTrsmRows : nbr;
       if (phase >= 2 * nbc - 1) return nbr;  // low-precision copy
       const uint32_t rb = fine ? cdiv16(t[h[1]].rows) : nbr;
       return phase % 2 == 0 ? rb : rb * (nbc - 1 - j);
@@ -461,7 +477,8 @@ __host__ __device__ inline bool comm_acquire_phase(const TaskDesc& t) {
 }
 
 __host__ __device__ inline uint32_t task_phases(const TaskDesc& t, const TileDesc* tiles) {
-  return op_phases(t.op, t.prec, tiles, t.h) + (comm_acquire_phase(t) ? 1u : 0u);
+  return op_phases(t.op, t.prec, tiles, t.h, t.flags & kFlagFine) +
+         (comm_acquire_phase(t) ? 1u : 0u);
 }
 
 __host__ __device__ inline uint32_t task_phase_units(const TaskDesc& t, const TileDesc* tiles,

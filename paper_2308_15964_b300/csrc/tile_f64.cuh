@@ -572,6 +572,103 @@ __device__ void op_trsm_units(const TileDesc& Lt, const TileDesc& At, uint32_t p
   }
 }
 
+// X <- X L^{-T} for m <= 16 rows of a shared array (row pitch ldx, the
+// w-column block at column c0), L scaled by column: the arithmetic of
+// trsm_rt_smem (a half-warp per row).  Warps whose two rows are both past m
+// return at once; no barrier inside.
+__device__ void trsm_rt_rows(double* xs, int ldx, int c0, const double (*l)[kLds],
+                             const double* rinv, int m, int w) {
+  const int tid = threadIdx.x, q = tid & 15, r = tid >> 4;
+  if ((r & ~1) >= m) return;
+  double* x = xs + (size_t)r * ldx + c0;
+  double v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = q + 16 * j < w ? x[q + 16 * j] : 0.0;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    for (int cl = 0; cl < 16; ++cl) {
+      const int c = 16 * jj + cl;
+      if (c >= w) break;
+      const double yc = __shfl_sync(0xffffffffu, v[jj], cl, 16);
+#pragma unroll
+      for (int j = jj; j < 4; ++j) {
+        const int cc = q + 16 * j;
+        if (cc > c && cc < w) v[j] = fma(-yc, l[cc][c], v[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (q + 16 * j < w) x[q + 16 * j] = v[j] * rinv[q + 16 * j];
+}
+
+// TRSM in row form (critical-path tasks, n <= kTrsmRowMaxN): A (m x n) <- A
+// L^{-T} in one phase; unit u = rows [kTrsmRows u, kTrsmRows (u + 1)), held
+// in shared memory while every column block j of them is solved (the column
+// form's in-block substitution) and subtracted, times L's blocks below the
+// diagonal, from the blocks to its right (the column form's update: one FMA
+// chain over k per entry, then one subtraction).  The same operations on
+// the same values as op_trsm_units, so the result is bit-identical; each
+// next L block is fetched into registers during the FMAs of the current one.
+__device__ __noinline__ void op_trsm_rows(const TileDesc& Lt, const TileDesc& At, uint32_t u0,
+                                          uint32_t u1, F64Smem& s) {
+  static_assert(sizeof(GemmSmem) >= sizeof(double) * kTrsmRows * kTrsmRowMaxN, "row buffer");
+  static_assert(kTrsmRows * kBlk == kThreads, "one update entry per thread");
+  constexpr int kPre = kBlk * kBlk / kThreads;  // L entries fetched per thread
+  const double* l = (const double*)Lt.ptr;
+  double* a = (double*)At.ptr;
+  const int m = At.rows, n = At.cols, lda = At.ld, ldl = Lt.ld;
+  const int nb = (n + kBlk - 1) / kBlk;
+  double* xs = reinterpret_cast<double*>(&s.gs);  // kTrsmRows x n, pitch n
+  const int tid = threadIdx.x, ur = tid / kBlk, uc = tid % kBlk;
+  double pre[kPre];
+  auto fetch = [&](int jb, int w, int ib) {  // L block (ib, j) into pre
+    const int lb = ib * kBlk, wc = min(kBlk, n - lb);
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      const int e = tid + kThreads * i, rr = e / kBlk, cc = e % kBlk;
+      pre[i] = (rr < wc && cc < w) ? __ldcg(l + (size_t)(lb + rr) * ldl + jb + cc) : 0.0;
+    }
+  };
+  for (uint32_t u = u0; u < u1; ++u) {
+    const int r0 = kTrsmRows * (int)u, mr = min(kTrsmRows, m - r0);
+    for (int e = tid; e < kTrsmRows * n; e += kThreads) {
+      const int r = e / n, c = e % n;
+      xs[e] = r < mr ? __ldcg(a + (size_t)(r0 + r) * lda + c) : 0.0;
+    }
+    for (int j = 0; j < nb; ++j) {
+      const int jb = j * kBlk, w = min(kBlk, n - jb);
+      load_block(s.l, l + (size_t)jb * ldl + jb, ldl, w, w);
+      if (j + 1 < nb) fetch(jb, w, j + 1);
+      __syncthreads();
+      prep_lower(s.l, w, s.rinv, false);
+      trsm_rt_rows(xs, n, jb, s.l, s.rinv, mr, w);
+      for (int ib = j + 1; ib < nb; ++ib) {
+        __syncthreads();  // the solved block is in xs; s.x is free
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+          const int e = tid + kThreads * i;
+          s.x[e / kBlk][e % kBlk] = pre[i];
+        }
+        __syncthreads();
+        if (ib + 1 < nb) fetch(jb, w, ib + 1);
+        const int lb = ib * kBlk, wc = min(kBlk, n - lb);
+        if (ur < mr && uc < wc) {
+          const double* xr = xs + (size_t)ur * n + jb;
+          double acc = 0.0;
+          for (int k = 0; k < w; ++k) acc = fma(xr[k], s.x[uc][k], acc);
+          double* p = xs + (size_t)ur * n + lb + uc;
+          *p = *p - acc;
+        }
+      }
+      __syncthreads();  // xs complete through block j; s.l is reloaded next
+    }
+    for (int e = tid; e < mr * n; e += kThreads)
+      a[(size_t)(r0 + e / n) * lda + e % n] = xs[e];
+    __syncthreads();
+  }
+}
+
 // SYRK: C (n x n, lower) -= L L^T, L (n x k); units = lower 64-block pairs.
 __device__ void op_syrk(const TileDesc& Lt, const TileDesc& Ct, uint32_t u0, uint32_t u1,
                         F64Smem& s, bool fine) {

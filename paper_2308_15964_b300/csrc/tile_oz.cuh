@@ -143,59 +143,118 @@ __device__ __forceinline__ long long oz_fixed(unsigned long long bits, int e) {
   return (bits >> 63) ? -(long long)X : (long long)X;
 }
 
+// The eight balanced base-128 digits sigma_0..7 of X (|X| <= 2^55) as the
+// FP32 bit patterns of their values: the bottom four from the low 28 bits
+// of X, the top four from X >> 28 plus the carry left by the bottom ones,
+// in 32-bit integers.  The same digits as peeling X from the bottom in 64
+// bits: a digit only depends on its remainder mod 128, and X = (X >> 28)
+// 2^28 + (X mod 2^28) with 2^28 a multiple of 128^4.  The upper half of
+// each pattern is the digit's BF16 encoding (|sigma| <= 64: exact).
+__device__ __forceinline__ void oz_digits(long long X, uint32_t* fb) {
+  int lo = (int)((unsigned long long)X & 0x0FFFFFFFull);
+  int hi = (int)(X >> 28);
+#pragma unroll
+  for (int s = kOzPlanes - 1; s >= 4; --s) {
+    const int d = ((lo + 64) & 127) - 64;
+    fb[s] = __float_as_uint((float)d);
+    lo = (lo - d) >> 7;
+  }
+  hi += lo;  // 0 or 1
+#pragma unroll
+  for (int s = 3; s >= 1; --s) {
+    const int d = ((hi + 64) & 127) - 64;
+    fb[s] = __float_as_uint((float)d);
+    hi = (hi - d) >> 7;
+  }
+  fb[0] = __float_as_uint((float)hi);
+}
+
 // Split rows [64 u, 64 u + 64) of the FP64 tile Lt into its slot (lowp =
 // slot address, lowp_ld = pitch b <= 512).  Columns cols..b-1 of each digit
-// plane are written as zeros (the K padding the tensor cores read).  One
-// warp per row, 16 columns per lane.
-__device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32_t u1) {
-  const int b = Lt.lowp_ld;
-  __nv_bfloat16* S = reinterpret_cast<__nv_bfloat16*>(Lt.lowp);
+// plane are written as zeros (the K padding the tensor cores read).  A warp
+// per row: the row is read coalesced (column lane + 32 j) and its exponent
+// reduced over the warp, the row is staged in shared memory (one double of
+// skew per 16 columns, so that a lane's 16 consecutive columns fall in
+// distinct banks), and lane i then splits the 16-digit K chunk i: its digits
+// of one plane are the 32 contiguous bytes of the slot's (plane, chunk, row)
+// run, written as two 16-byte stores.  scratch: kOzSplitStage doubles of
+// shared memory per warp.
+constexpr int kOzSplitStage = 544;  // 512 columns + 32 skew
+__device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32_t u1,
+                                         double* scratch) {
+  // the descriptor's fields in registers (the stores below may alias it)
+  const int b = Lt.lowp_ld, nch = b / 16, rows = Lt.rows, cols = Lt.cols, ld = Lt.ld;
+  uint4* S = reinterpret_cast<uint4*>(Lt.lowp);
   int* Ex = reinterpret_cast<int*>(reinterpret_cast<char*>(Lt.lowp) + (size_t)16 * b * b);
   const double* A = reinterpret_cast<const double*>(Lt.ptr);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nj = b / 32;
-  for (uint32_t u = u0; u < u1; ++u) {
-    const int rend = min((int)(u + 1) * 64, Lt.rows);
-    for (int r = (int)u * 64 + warp; r < rend; r += kThreads / 32) {
-      unsigned long long bits[16];
-      unsigned long long mx = 0;
+  double* row = scratch + warp * kOzSplitStage;
+  // this warp's rows of units u0..u1, the next row's loads in flight while
+  // the current one is split
+  auto load_row = [&](int r, unsigned long long* v) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int c = lane + 32 * j;
-        bits[j] = (j < nj && c < Lt.cols)
-                      ? (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * Lt.ld + c))
-                      : 0ull;
-        const unsigned long long mag = bits[j] & 0x7FFFFFFFFFFFFFFFull;
+    for (int j = 0; j < 16; ++j) {
+      const int c = lane + 32 * j;
+      v[j] = (c < cols)
+                 ? (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * ld + c))
+                 : 0ull;
+    }
+  };
+  auto next_row = [&](uint32_t& u, int r) {  // the row after r, or -1
+    r += kThreads / 32;
+    while (u < u1 && r >= min((int)(u + 1) * 64, rows)) {
+      ++u;
+      r = (int)u * 64 + warp;
+    }
+    return u < u1 ? r : -1;
+  };
+  uint32_t u = u0;
+  int r = next_row(u, (int)u0 * 64 + warp - kThreads / 32);
+  unsigned long long v[16];
+  if (r >= 0) load_row(r, v);
+  while (r >= 0) {
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = lane + 32 * j;
+      if (c < b) {
+        const unsigned long long mag = v[j] & 0x7FFFFFFFFFFFFFFFull;
         mx = mag > mx ? mag : mx;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-        mx = y > mx ? y : mx;
-      }
-      const int ef = (int)(mx >> 52);
-      const int e = ef ? ef - 1022 : -1022;
-      if (lane == 0) Ex[r] = e;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (j >= nj) break;
-        const int c = lane + 32 * j;
-        long long X = oz_fixed(bits[j], e);
-        int sg[kOzPlanes];
-#pragma unroll
-        for (int s = kOzPlanes - 1; s >= 1; --s) {
-          const int d = (int)((X + 64) & 127) - 64;
-          sg[s] = d;
-          X = (X - d) >> 7;
-        }
-        sg[0] = (int)X;
-#pragma unroll
-        // K-chunked layout: plane s, 16-digit chunk c / 16, row r, digit c % 16
-        for (int s = 0; s < kOzPlanes; ++s)
-          S[(((size_t)s * (b / 16) + c / 16) * b + r) * 16 + (c & 15)] =
-              __float2bfloat16_rn((float)sg[s]);
+        row[c + (c >> 4)] = __longlong_as_double((long long)v[j]);
       }
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+      mx = y > mx ? y : mx;
+    }
+    const int ef = (int)(mx >> 52);
+    const int e = ef ? ef - 1022 : -1022;
+    if (lane == 0) Ex[r] = e;
+    const int rn = next_row(u, r);
+    if (rn >= 0) load_row(rn, v);
+    __syncwarp();
+    if (lane < nch) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {  // 8 columns: one 16-byte store per plane
+        uint32_t pk[kOzPlanes][4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {  // two columns: one 32-bit word per plane
+          const double* x = row + lane * 17 + 8 * h + i;
+          uint32_t f0[kOzPlanes], f1[kOzPlanes];
+          oz_digits(oz_fixed((unsigned long long)__double_as_longlong(x[0]), e), f0);
+          oz_digits(oz_fixed((unsigned long long)__double_as_longlong(x[1]), e), f1);
+#pragma unroll
+          for (int s = 0; s < kOzPlanes; ++s) pk[s][i >> 1] = __byte_perm(f0[s], f1[s], 0x7632);
+        }
+#pragma unroll
+        for (int s = 0; s < kOzPlanes; ++s)
+          S[(((size_t)s * nch + lane) * b + r) * 2 + h] =
+              make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+      }
+    }
+    __syncwarp();  // the staging row is reused
+    r = rn;
   }
 }
 
@@ -211,7 +270,8 @@ __device__ __noinline__ void op_oz_split(const TileDesc& Lt, uint32_t u0, uint32
 // shared memory, 4 x 64 words).
 __device__ __noinline__ void op_oz_split_t(const TileDesc& Xt, uint32_t u0, uint32_t u1,
                                            unsigned long long* red) {
-  const int b = Xt.lowp_ld, nch = b / 16;
+  // the descriptor's fields in registers (the stores below may alias it)
+  const int b = Xt.lowp_ld, nch = b / 16, rows = Xt.rows, cols = Xt.cols, ld = Xt.ld;
   uint4* S = reinterpret_cast<uint4*>(Xt.lowp);  // 32 bytes = 2 x uint4 per (plane, chunk, row)
   int* Ex = reinterpret_cast<int*>(reinterpret_cast<char*>(Xt.lowp) + (size_t)16 * b * b);
   const double* A = reinterpret_cast<const double*>(Xt.ptr);
@@ -219,15 +279,15 @@ __device__ __noinline__ void op_oz_split_t(const TileDesc& Xt, uint32_t u0, uint
   const int half = warp & 1, q = warp >> 1;
   for (uint32_t u = u0; u < u1; ++u) {
     const int c = (int)u * 64 + 32 * half + lane;
-    const bool live = c < Xt.cols;
+    const bool live = c < cols;
     unsigned long long mx = 0;
     for (int j = q; j < nch; j += 4) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int r = 16 * j + i;
-        if (live && r < Xt.rows) {
+        if (live && r < rows) {
           const unsigned long long mag =
-              (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * Xt.ld + c)) &
+              (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * ld + c)) &
               0x7FFFFFFFFFFFFFFFull;
           mx = mag > mx ? mag : mx;
         }
@@ -246,33 +306,30 @@ __device__ __noinline__ void op_oz_split_t(const TileDesc& Xt, uint32_t u0, uint
     if (!live) continue;  // slot rows past the tile's columns are never read
     if (q == 0) Ex[c] = e;
     for (int j = q; j < nch; j += 4) {
-      uint32_t pk[kOzPlanes][8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int r = 16 * j + i;
-        const unsigned long long bits =
-            r < Xt.rows ? (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * Xt.ld + c))
-                        : 0ull;
-        long long X = oz_fixed(bits, e);
-        int sg[kOzPlanes];
+      for (int h = 0; h < 2; ++h) {  // 8 rows: one 16-byte store per plane
+        uint32_t pk[kOzPlanes][4];
 #pragma unroll
-        for (int s = kOzPlanes - 1; s >= 1; --s) {
-          const int d = (int)((X + 64) & 127) - 64;
-          sg[s] = d;
-          X = (X - d) >> 7;
+        for (int i = 0; i < 8; i += 2) {  // two rows: one 32-bit word per plane
+          const int r = 16 * j + 8 * h + i;
+          const unsigned long long b0 =
+              r < rows
+                  ? (unsigned long long)__double_as_longlong(__ldcg(A + (size_t)r * ld + c))
+                  : 0ull;
+          const unsigned long long b1 =
+              r + 1 < rows ? (unsigned long long)__double_as_longlong(
+                                    __ldcg(A + (size_t)(r + 1) * ld + c))
+                              : 0ull;
+          uint32_t f0[kOzPlanes], f1[kOzPlanes];
+          oz_digits(oz_fixed(b0, e), f0);
+          oz_digits(oz_fixed(b1, e), f1);
+#pragma unroll
+          for (int s = 0; s < kOzPlanes; ++s) pk[s][i >> 1] = __byte_perm(f0[s], f1[s], 0x7632);
         }
-        sg[0] = (int)X;
 #pragma unroll
-        for (int s = 0; s < kOzPlanes; ++s) {
-          const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn((float)sg[s]));
-          pk[s][i >> 1] = (i & 1) ? (pk[s][i >> 1] | (h << 16)) : h;
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < kOzPlanes; ++s) {
-        uint4* dst = S + (((size_t)s * nch + j) * b + c) * 2;
-        dst[0] = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
-        dst[1] = make_uint4(pk[s][4], pk[s][5], pk[s][6], pk[s][7]);
+        for (int s = 0; s < kOzPlanes; ++s)
+          S[(((size_t)s * nch + j) * b + c) * 2 + h] =
+              make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
       }
     }
   }
@@ -471,8 +528,9 @@ constexpr int kOzSub = 0, kOzStore = 1, kOzAdd = 2;
 constexpr int kOzPipeStages = 3;
 struct __align__(1024) OzBuf {
   uint8_t stages[kOzPipeStages][oz_stage_bytes(64)];
-  double v[kTcM][65];
+  double v[kTcM][65];  // also the split's row staging (kOzSplitStage per warp)
 };
+static_assert(sizeof(OzBuf::v) >= sizeof(double) * kOzSplitStage * (kThreads / 32), "staging");
 
 __device__ __forceinline__ const int* oz_exps(const TileDesc& t) {
   return reinterpret_cast<const int*>(reinterpret_cast<const char*>(t.lowp) +
