@@ -90,14 +90,25 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// 8 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+// 8 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes; the
+// registers are valid after tmem_wait4 (several loads share one wait).
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7])
       : "r"(taddr));
+}
+
+// Wait for the warp's TMEM loads; the four 8-register groups pass through an
+// empty statement after the wait so that no use of them moves above it.
+__device__ __forceinline__ void tmem_wait4(uint32_t (*v)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    asm volatile(""
+                 : "+r"(v[d][0]), "+r"(v[d][1]), "+r"(v[d][2]), "+r"(v[d][3]), "+r"(v[d][4]),
+                   "+r"(v[d][5]), "+r"(v[d][6]), "+r"(v[d][7]));
 }
 
 // N * 2^y as FP64 when that is exact and normal: |N| < 2^53 and the result's
@@ -448,18 +459,22 @@ __device__ bool oz_row_pipe(TcState& s, uint8_t* sb, double* V, const CUtensorMa
       if (__all_sync(0xFFFFFFFFu, got && !*err)) {
 #pragma unroll 1
         for (int cb = cq; cb < cq + 32; cb += 8) {
+          // accumulators 0-3 (Fh), then 4-7 (Fl): four loads per wait
           long long fh[8], fl[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) fh[j] = fl[j] = 0;
+          for (int hl = 0; hl < 2; ++hl) {
+            uint32_t v[4][8];
 #pragma unroll
-          for (int d = 0; d < kOzPlanes; ++d) {
-            uint32_t v[8];
-            tmem_ld8(lanes + (uint32_t)(kN * d + cb), v);
+            for (int d = 0; d < 4; ++d)
+              tmem_ld8_async(lanes + (uint32_t)(kN * (4 * hl + d) + cb), v[d]);
+            tmem_wait4(v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const long long p = __float2int_rn(__uint_as_float(v[j]));
-              if (d < 4) fh[j] = fh[j] * 128 + p;
-              else fl[j] = fl[j] * 128 + p;
+              long long f = 0;
+#pragma unroll
+              for (int d = 0; d < 4; ++d) f = f * 128 + __float2int_rn(__uint_as_float(v[d][j]));
+              if (hl == 0) fh[j] = f;
+              else fl[j] = f;
             }
           }
 #pragma unroll
