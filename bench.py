@@ -38,6 +38,7 @@ METRIC = "Cholesky GFLOP/s & tasks/s (device DAG vs per-task launch); p50/p99 la
 PEAKS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 ROOT = os.path.dirname(os.path.abspath(__file__))
 DRAM_PROFILE = os.path.join(ROOT, "profiles", "persistent_kernel_dram_cholesky_n16384_t512.md")
+GEMM_DRAM_PROFILE = os.path.join(ROOT, "profiles", "split_gemm_dag_n8192_t512.md")
 
 
 def kernel_source_hash() -> str:
@@ -639,6 +640,8 @@ def gemm_dag(spx, cholesky, inputs, torch, n, b, warmup, steps, max_mhz, compara
                      "arith": "FP64 by split products (Ozaki) on the BF16 tensor cores",
                      "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16,
                                   "unit": "TFLOP/s", "frac": ach / bf16,
+                                  "traffic": measured_traffic(GEMM_DRAM_PROFILE)
+                                  if (n, b) == (8192, 512) else None,
                                   "kernel": "persistent_kernel<split products> (one CTA per SM)",
                                   "kernel_ms": kern,
                                   "tensor_tflop_per_launch": tensor_flops / 1e12}}
