@@ -922,7 +922,8 @@ int spx_axpy_f64(double* dev_Y, const double* dev_X, long long count, double alp
  * calls above and not executed; the server copies it (the graph may be
  * cleared or destroyed after submit returns, the tile memory must live until
  * the request is done).  Requests may not use COMMUTATIVE_WRITE; low-precision
- * tasks need tensor_cores = 1. */
+ * tasks need tensor_cores >= 1, split-FP64 tasks (SPX_F64_OZAKI) need
+ * tensor_cores = 2. */
 typedef struct spx_server* spx_server_t;
 
 typedef struct {
@@ -933,7 +934,10 @@ typedef struct {
   long long max_maps;
   long long queue_capacity;  /* ring entries per priority                    */
   int num_ctas;              /* resident CTAs; 0 = resident maximum          */
-  int tensor_cores;          /* 1 = resident kernel with TMEM (TF32/BF16)    */
+  int tensor_cores;          /* 0 = FP64 tile ops only (two CTAs per SM);
+                                1 = with the TF32/BF16 tensor-core ops;
+                                2 = one CTA per SM owning all of TMEM: also
+                                the split-FP64 products (SPX_F64_OZAKI)     */
   unsigned long long watchdog_ns; /* live work without progress -> error     */
   unsigned long long idle_ns;     /* resident kernel exits when idle this long
                                      (relaunched by the next submit/poll)   */

@@ -36,7 +36,7 @@ void configure(int mode) {
   const void* graph_fn =
       mode == 0 ? mega_fn_graph_f64() : mode == 1 ? mega_fn_graph_tc() : mega_fn_graph_oz();
   const void* fns[3] = {graph_fn,
-                        mode == 0 ? mega_fn_server_f64() : mode == 1 ? mega_fn_server_tc() : nullptr,
+                        mode == 0 ? mega_fn_server_f64() : mode == 1 ? mega_fn_server_tc() : mega_fn_server_oz(),
                         mode == 0 ? mega_fn_task_f64() : mode == 1 ? mega_fn_task_tc() : mega_fn_task_oz()};
   for (const void* f : fns) {
     if (!f) continue;
@@ -94,16 +94,17 @@ cudaError_t launch_persistent(const DevGraph& g, int num_ctas, int mode, cudaStr
                      : mega_launch_graph_oz(n, smem_bytes(2), st, g);
 }
 
-cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st) {
+cudaError_t launch_server(const DevGraph& g, int num_ctas, int mode, cudaStream_t st) {
   persistent_max_ctas(nullptr);
   // The server kernel exits when idle and is launched again by the next
   // submission: it keeps to the occupancy the calculator guarantees, so that
   // no CTA of an exited launch can start late beside the next one.
-  const int maxc = g_sms * g_api_ctas_per_sm[tc ? 1 : 0];
+  const int maxc = g_sms * g_api_ctas_per_sm[mode];
   int n = num_ctas > 0 ? num_ctas : maxc;
   if (n > maxc) n = maxc;
-  return tc ? mega_launch_server_tc(n, smem_bytes(1), st, g)
-            : mega_launch_server_f64(n, smem_bytes(0), st, g);
+  return mode == 0   ? mega_launch_server_f64(n, smem_bytes(0), st, g)
+         : mode == 1 ? mega_launch_server_tc(n, smem_bytes(1), st, g)
+                     : mega_launch_server_oz(n, smem_bytes(2), st, g);
 }
 
 __global__ void ring_init_kernel(uint32_t* s0, uint32_t* s1, uint32_t cap) {

@@ -18,6 +18,7 @@ const void* mega_fn_task_f64();
 const void* mega_fn_task_tc();
 const void* mega_fn_graph_oz();
 const void* mega_fn_task_oz();
+const void* mega_fn_server_oz();
 
 cudaError_t mega_launch_graph_f64(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
 cudaError_t mega_launch_graph_tc(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
@@ -30,5 +31,6 @@ cudaError_t mega_launch_task_tc(int ctas, size_t smem, cudaStream_t st, const De
 cudaError_t mega_launch_graph_oz(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
 cudaError_t mega_launch_task_oz(int ctas, size_t smem, cudaStream_t st, const DevGraph& g,
                                 uint32_t task, uint32_t phase);
+cudaError_t mega_launch_server_oz(int ctas, size_t smem, cudaStream_t st, const DevGraph& g);
 
 }  // namespace spx

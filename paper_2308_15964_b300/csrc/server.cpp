@@ -118,7 +118,7 @@ int ensure_running(spx_server* s) {
     if (status) return (int)(int32_t)status;
     s->launched = false;
   }
-  cudaError_t e = launch_server(s->dg, s->cfg.num_ctas, s->cfg.tensor_cores != 0, s->run_stream);
+  cudaError_t e = launch_server(s->dg, s->cfg.num_ctas, s->cfg.tensor_cores, s->run_stream);
   if (e == cudaSuccess) e = cudaEventRecord(s->run_done, s->run_stream);
   if (e != cudaSuccess) return cuda_err(e);
   s->launched = true;
@@ -165,7 +165,8 @@ int spx_server_create(spx_server_t* out, const spx_server_config_t* cfg) {
   const spx_server_config_t& c = s->cfg;
   if (c.max_tasks < 2 || c.max_tasks > (long long)kMaxTasks || c.max_tiles < 2 ||
       c.max_records < 2 || c.max_edges < 1 || c.queue_capacity < 64 ||
-      c.queue_capacity > 0x40000000ll || c.num_ctas < 0) {
+      c.queue_capacity > 0x40000000ll || c.num_ctas < 0 || c.tensor_cores < 0 ||
+      c.tensor_cores > 2) {
     delete s;
     return SPX_ERR_INVALID_ARG;
   }
@@ -265,9 +266,8 @@ int spx_server_submit(spx_server_t s, spx_graph_t g, unsigned long long* out_req
   for (size_t i = 0; i < v.ntasks; ++i) {
     if (v.tasks[i].flags & kFlagComm) return SPX_ERR_INVALID_ARG;  // no commutative writes
     if (v.tasks[i].prec != SPX_F64 && !s->cfg.tensor_cores) return SPX_ERR_INVALID_ARG;
-    // the split-FP64 products need the one-CTA-per-SM kernel, which the
-    // server does not run
-    if (v.tasks[i].prec == SPX_F64_OZAKI) return SPX_ERR_INVALID_ARG;
+    // the split-FP64 products need the one-CTA-per-SM instance (tensor_cores = 2)
+    if (v.tasks[i].prec == SPX_F64_OZAKI && s->cfg.tensor_cores != 2) return SPX_ERR_INVALID_ARG;
   }
   const unsigned long long items = v.items;
   if (s->free_slots.empty() || s->live_items + items > (unsigned long long)s->cfg.queue_capacity)

@@ -500,7 +500,7 @@ cudaError_t launch_per_task(const DevGraph& g, const TaskDesc* host_tasks,
 // The launches of one task's phases on st (per-task executors).
 cudaError_t launch_task(const DevGraph& g, uint32_t u, const TaskDesc& t,
                         const TileDesc* host_tiles, int mode, cudaStream_t st);
-cudaError_t launch_server(const DevGraph& g, int num_ctas, bool tc, cudaStream_t st);
+cudaError_t launch_server(const DevGraph& g, int num_ctas, int mode, cudaStream_t st);  // mode as launch_persistent
 cudaError_t launch_ring_init(const DevGraph& g, cudaStream_t st);
 int persistent_max_ctas(int* per_sm);
 size_t persistent_smem_bytes();
