@@ -1155,14 +1155,17 @@ def run_serve(args, world, rank, local):
     from paper_2308_15964_b300 import serve
     with Clocks(local) as clk:
         out = serve.serve(rate=args.rate, duration=args.duration, budget=120e9, seed=6 + rank,
-                          drain=False, max_wall=args.duration + 120)
+                          drain=False, max_wall=args.duration + 120,
+                          split_fp64=args.arith == "ozaki")
     res = {"metric": METRIC, "value": out["gflops"], "unit": "GFLOP/s", "n_gpus": world,
            "steps": 1, "warmup": 0, "ms_per_step": out["wall_s"] * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64 / tf32+f64 refinement",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": ("f64 (orders >= %d by split products on the tensor cores) / tf32+f64 refinement"
+                     % serve.SPLIT_MIN_N) if args.arith == "ozaki" else "f64 / tf32+f64 refinement",
            "data": "synthetic",
            "config": {"workload": f"serving: Poisson {args.rate}/s for {args.duration} s, n log-uniform "
                                   "64..16384, 1..64 RHS, 50% TF32+refinement, 120 GB budget",
-                      "rate": args.rate, "duration_s": args.duration},
+                      "rate": args.rate, "duration_s": args.duration, "arith": args.arith},
            "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "serve": out, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(res))

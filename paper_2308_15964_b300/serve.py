@@ -38,6 +38,7 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     status: int = 0
+    split: bool = False          # FP64 by split products on the tensor cores
     views: dict = field(default_factory=dict)
 
 
@@ -70,8 +71,22 @@ def tile_for(n: int, prec: int) -> int:
     return 128 if n <= 2048 else (256 if n <= 8192 else 512)
 
 
-def request_bytes(n: int, nrhs: int, prec: int) -> int:
+# FP64 requests of at least this order run by split products (with split_fp64)
+SPLIT_MIN_N = 2048
+
+
+def split_store_bytes(n: int, b: int) -> int:
+    """Split store of spx_cholesky_insert_ozaki with inverse panels."""
+    T = -(-n // b)
+    return (T * (T - 1) // 2 + T) * spx.lib.spx_ozaki_slot_bytes(b)
+
+
+def request_bytes(n: int, nrhs: int, prec: int, split: bool = False) -> int:
     pad = lambda b: (b + 255) // 256 * 256
+    if prec == spx.F64 and split:
+        b = tile_for(n, prec)
+        # A, X, the split store, V (the diagonal-tile inverses, n x b)
+        return pad(8 * n * n) + pad(8 * n * nrhs) + pad(split_store_bytes(n, b)) + pad(8 * n * b)
     if prec == spx.F64:
         return pad(8 * n * n) + pad(8 * n * nrhs)
     # A (factored), A0 (original), A_lo (FP32 for TF32), V (diagonal-tile
@@ -140,10 +155,18 @@ def build_graph(req: Request, arena: Arena, src: Sources, stream, sweeps: int = 
     g = spx.Graph()
     if req.prec == spx.F64:
         X = arena.view(o, (n, r))
+        o += pad(8 * n * r)
         src.stage(A, src.A, n, n, stream)
         src.stage(X, src.B, n, r, stream)
         stream.synchronize()
-        cholesky.cholesky_graph(g, A, req.tile, X)
+        if req.split:
+            sb = split_store_bytes(n, req.tile)
+            S = arena.view(o, (sb,), torch.uint8)
+            o += pad(sb)
+            V = arena.view(o, (n, req.tile))
+            cholesky.cholesky_ozaki_graph(g, A, req.tile, X, S=S, V=V)
+        else:
+            cholesky.cholesky_graph(g, A, req.tile, X)
         req.views = {"A": A, "X": X}
         return g
     A0 = arena.view(o, (n, n))
@@ -174,15 +197,18 @@ def build_graph(req: Request, arena: Arena, src: Sources, stream, sweeps: int = 
 
 
 def serve(rate=200.0, duration=60.0, budget=120e9, seed=6, nmax=16384, rhs_max=64, tf32_frac=0.5,
-          sweeps=4, drain=True, max_wall=None, keep_results=False):
-    """Run the stream; returns a summary dict (and the finished requests)."""
+          sweeps=4, drain=True, max_wall=None, keep_results=False, split_fp64=False):
+    """Run the stream; returns a summary dict (and the finished requests).
+    split_fp64: FP64 requests of order >= SPLIT_MIN_N run by split products
+    on the tensor cores (the server's one-CTA-per-SM kernel), FP64 results."""
     reqs = request_stream(rate, duration, seed, nmax=nmax, rhs_max=rhs_max, tf32_frac=tf32_frac)
     src = Sources(nmax, rhs_max, seed)
     arena = Arena(int(budget))
-    srv = spx.Server(tensor_cores=1, idle_ns=200_000_000)
+    srv = spx.Server(tensor_cores=2 if split_fp64 else 1, idle_ns=200_000_000)
     stream = torch.cuda.Stream()
     for q in reqs:
-        q.bytes = request_bytes(q.n, q.nrhs, q.prec)
+        q.split = split_fp64 and q.prec == spx.F64 and q.n >= SPLIT_MIN_N
+        q.bytes = request_bytes(q.n, q.nrhs, q.prec, q.split)
     pending = list(reqs)
     live, finished = [], []
     t0 = time.perf_counter()
@@ -237,5 +263,6 @@ def serve(rate=200.0, duration=60.0, budget=120e9, seed=6, nmax=16384, rhs_max=6
         "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "throughput_req_s": len(finished) / wall, "gflops": flops / wall / 1e9,
         "tf32_requests": sum(1 for q in finished if q.prec != spx.F64),
+        "split_fp64_requests": sum(1 for q in finished if q.split),
     }
     return (out, finished, arena) if keep_results else out
