@@ -213,15 +213,9 @@ def run_reference(args):
     }))
 
 
-def ozaki_roofline(n, b, kernel_ms, fp64_peak, traffic):
-    """Roofline of the persistent kernel on the split path (inverse panels).
-    Tensor work: every 128 x 64 output block with K digits issues MMAs over
-    N = 64 (8 - p) columns for the eight planes p of A, i.e. 36 digit-pair
-    products of 2 * 128 * 64 * K flops; summed over the GEMM tasks' tiles, the
-    SYRK tasks' lower blocks and the TRSM_INV products (tiles i >= k + 2).
-    FP64 SIMT work: POTRF (b^3 / 3), the critical panel tile's substitution
-    (b^3) and TRTRI (b^3 / 3) per k.  The bound is the tensor-core rate; the
-    FP64 share is given beside."""
+def ozaki_work(n, b):
+    """(BF16 tensor flops, FP64 SIMT flops) of the split-path Cholesky with
+    inverse panels, tiles b (the last one may be ragged: counted as full)."""
     T = -(-n // b)
     nbr, nbc = -(-b // 128), -(-b // 64)
     full = nbr * nbc
@@ -232,6 +226,19 @@ def ozaki_roofline(n, b, kernel_ms, fp64_peak, traffic):
     block_flops = 36 * 2 * 128 * 64 * b
     tensor_flops = ((gemm_tiles + inv_tiles) * full + syrk_tiles * syrk_blocks) * block_flops
     fp64_flops = T * b ** 3 / 3 + (T - 1) * b ** 3 + T * b ** 3 / 3
+    return tensor_flops, fp64_flops
+
+
+def ozaki_roofline(n, b, kernel_ms, fp64_peak, traffic):
+    """Roofline of the persistent kernel on the split path (inverse panels).
+    Tensor work: every 128 x 64 output block with K digits issues MMAs over
+    N = 64 (8 - p) columns for the eight planes p of A, i.e. 36 digit-pair
+    products of 2 * 128 * 64 * K flops; summed over the GEMM tasks' tiles, the
+    SYRK tasks' lower blocks and the TRSM_INV products (tiles i >= k + 2).
+    FP64 SIMT work: POTRF (b^3 / 3), the critical panel tile's substitution
+    (b^3) and TRTRI (b^3 / 3) per k.  The bound is the tensor-core rate; the
+    FP64 share is given beside."""
+    tensor_flops, fp64_flops = ozaki_work(n, b)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     bf16 = peaks.get("bf16_tflops", 1800.0)
     ach = tensor_flops / (kernel_ms * 1e-3) / 1e12
@@ -1301,8 +1308,9 @@ def run_batch(args, world, rank, local):
     from paper_2308_15964_b300 import batch as Bt
     from paper_2308_15964_b300 import spx
     n, r = Bt.problem_sizes(args.count, seed=5 + rank)
+    split = args.arith == "ozaki"
     t0 = time.perf_counter()
-    best, table = Bt.autotune(n)
+    best, table = Bt.autotune(n, split=split)
     tune_s = time.perf_counter() - t0
     tiles = [best[int(k)] for k in n]
     bt = Bt.Batch(n, r, seed=5 + rank)
@@ -1315,7 +1323,7 @@ def run_batch(args, world, rank, local):
         bt.restore()
         ev[0].record()
         g.clear()
-        ntasks = Bt.insert(g, bt, tiles)
+        ntasks = Bt.insert(g, bt, tiles, split=split)
         rc, _ = g.run()
         ev[1].record()
         ev[1].synchronize()
@@ -1347,11 +1355,14 @@ def run_batch(args, world, rank, local):
     kern = statistics.mean(x[1] for x in recs)
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (trailing updates and panel products split on the tensor cores)" if split
+           else "f64", "data": "synthetic",
            "config": {"workload": f"batched uneven Cholesky solves: {args.count} problems, n in "
                                   "32..1024 (multiples of 32), 1..16 RHS, autotuned tiles, "
                                   "one persistent launch, CUDA-graph replay",
-                      "count": args.count, "tasks": ntasks, "parallelism": f"replicas x{world}"},
+                      "count": args.count, "tasks": ntasks, "parallelism": f"replicas x{world}",
+                      "arith": args.arith},
            "tasks_per_s": ntasks / (statistics.mean(step_ms) * 1e-3),
            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
            "full_step_ms": statistics.mean(full),
@@ -1360,9 +1371,20 @@ def run_batch(args, world, rank, local):
            "roofline": {"bound": "alu", "achieved": flops / (kern * 1e-3) / 1e12, "peak": peak,
                         "unit": "TFLOP/s", "frac": flops / (kern * 1e-3) / 1e12 / peak,
                         "traffic": None, "kernel": "persistent_kernel", "kernel_ms": kern}}
+    if split:  # the tensor-core bound over the digit-pair flops, the FP64 share beside it
+        tf, ff = (sum(x) for x in zip(*(ozaki_work(int(k), int(b)) for k, b in zip(n, tiles))))
+        bf16 = (json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}).get(
+            "bf16_tflops", 1800.0)
+        ach = tf / (kern * 1e-3) / 1e12
+        out["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                           "frac": ach / bf16, "traffic": None,
+                           "kernel": "persistent_kernel<split products> (one CTA per SM)",
+                           "kernel_ms": kern, "tensor_tflop_per_launch": tf / 1e12,
+                           "fp64_simt": {"flops_per_launch": ff,
+                                         "frac": ff / (kern * 1e-3) / 1e12 / peak}}
     if rank == 0:
         gb = spx.Graph(executor=spx.EXEC_PER_TASK, cuda_graph=True)
-        Bt.insert(gb, bt, tiles)
+        Bt.insert(gb, bt, tiles, split=split)
         bms = []
         for i in range(3):
             bt.restore()

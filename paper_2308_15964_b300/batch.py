@@ -70,14 +70,49 @@ class Batch:
     def flops(self) -> float:
         return float(sum(cholesky.cholesky_flops(int(k), int(r)) for k, r in zip(self.n, self.nrhs)))
 
+    def split_buffers(self, tiles):
+        """Per-problem split stores (spx_cholesky_insert_ozaki with inverse
+        panels: T (T - 1) / 2 + T slots) and diagonal-inverse blocks V_i
+        (n_i x b_i), packed on 256-byte boundaries; kept for the tile choice."""
+        key = tuple(int(t) for t in tiles)
+        if getattr(self, "_split_key", None) != key:
+            s_sz, v_sz = [], []
+            for k, b in zip(self.n, key):
+                T = -(-int(k) // b)
+                s_sz.append((T * (T - 1) // 2 + T) * spx.lib.spx_ozaki_slot_bytes(b))
+                v_sz.append((int(k) * b + 31) // 32 * 32)
+            self.s_off = np.concatenate([[0], np.cumsum(s_sz)[:-1]]).astype(np.int64)
+            self.s_len = np.asarray(s_sz, np.int64)
+            self.v_off = np.concatenate([[0], np.cumsum(v_sz)[:-1]]).astype(np.int64)
+            self.S = torch.empty(int(sum(s_sz)), dtype=torch.uint8, device=self.A.device)
+            self.V = torch.empty(int(sum(v_sz)), dtype=torch.float64, device=self.A.device)
+            self._split_key = key
+        return self.S, self.V
 
-def insert(g: spx.Graph, batch: Batch, tiles, lookahead: bool = False) -> int:
+
+def insert(g: spx.Graph, batch: Batch, tiles, lookahead: bool = False, split: bool = False) -> int:
     """Insert every problem of the batch; tiles[i] is problem i's tile.  By
     default without look-ahead priorities: thousands of independent problems
     keep every SM busy, so critical-path splitting (finer parts, more queue
     traffic) only costs throughput (measured: 842 vs 860 GFLOP/s on the
-    4096-problem batch)."""
+    4096-problem batch).  split: every problem by spx_cholesky_insert_ozaki
+    (trailing updates and inverse panel products split on the tensor cores,
+    FP64 results; tiles multiples of 32), with the stores of split_buffers."""
     c = batch.count
+    if split:
+        S, V = batch.split_buffers(tiles)
+        total, nt = 0, ctypes.c_longlong()
+        for i in range(c):
+            k, b, r = int(batch.n[i]), int(tiles[i]), int(batch.nrhs[i])
+            spx._check(spx.lib.spx_cholesky_insert_ozaki(
+                g._h, ctypes.c_void_p(batch.A.data_ptr() + 8 * int(batch.a_off[i])), k, k, b,
+                ctypes.c_void_p(S.data_ptr() + int(batch.s_off[i])), int(batch.s_len[i]),
+                ctypes.c_void_p(V.data_ptr() + 8 * int(batch.v_off[i])), b, 0,
+                ctypes.c_void_p(batch.X.data_ptr() + 8 * int(batch.x_off[i])), r, r,
+                1 if lookahead else 0, ctypes.byref(nt)), "spx_cholesky_insert_ozaki")
+            total += nt.value
+        g._keep.append(batch)
+        return total
     base_a, base_x = batch.A.data_ptr(), batch.X.data_ptr()
     pa = (ctypes.c_void_p * c)(*[base_a + 8 * int(o) for o in batch.a_off])
     px = (ctypes.c_void_p * c)(*[base_x + 8 * int(o) for o in batch.x_off])
@@ -93,14 +128,17 @@ def insert(g: spx.Graph, batch: Batch, tiles, lookahead: bool = False) -> int:
     return nt.value
 
 
-def autotune(sizes, copies: int = 148, candidates=TILES, seed: int = 99):
+def autotune(sizes, copies: int = 148, candidates=TILES, seed: int = 99, split: bool = False):
     """Pick, for every distinct n, the tile with the shortest persistent-kernel
     time on a batch of `copies` problems of that order (one matrix replicated).
     Candidates larger than n collapse to one tile, so only the smallest of
-    them is tried.  Returns ({n: tile}, {n: {tile: ms}})."""
+    them is tried.  split: time the split-product form (insert(split=True)).
+    Returns ({n: tile}, {n: {tile: ms}})."""
     best, table = {}, {}
     for k in sorted(set(int(s) for s in sizes)):
         cands = [b for b in candidates if b < k] + [min([b for b in candidates if b >= k] or [k])]
+        if split:  # split slots hold tiles of at most 512
+            cands = [b for b in cands if b <= 512]
         bt = Batch([k] * copies, [1] * copies, seed, fill=False)
         a = inputs.spd_matrix(k, 1.0, seed)
         a_dev = a.cuda()
@@ -110,7 +148,7 @@ def autotune(sizes, copies: int = 148, candidates=TILES, seed: int = 99):
                 bt.a_view(i).copy_(a_dev)
             bt.X.fill_(1.0)
             g = spx.Graph(cuda_graph=True)
-            insert(g, bt, [b] * copies)
+            insert(g, bt, [b] * copies, split=split)
             rc, _ = g.run()
             assert rc == spx.OK, rc
             g.reset()

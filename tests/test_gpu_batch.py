@@ -90,3 +90,37 @@ def test_autotune_small(S):
     assert set(best) == {96, 160}
     assert set(table[96]) == {32, 64, 128} and set(table[160]) == {32, 64, 128, 256}
     assert all(t > 0 for v in table.values() for t in v.values())
+
+
+def test_split_batch_vs_oracle_and_alone(S):
+    """The batch with every problem on the split path (trailing updates and
+    inverse panel products split on the tensor cores): each problem within
+    the FP64 tolerances of the oracle, bit-identical alone and in the batch,
+    and on CUDA-graph replay; the autotuner in the same mode."""
+    from paper_2308_15964_b300 import batch as Bt
+    n, r = Bt.problem_sizes(48, seed=7, nmax=512)
+    tiles = [[32, 64, 128, 256][i % 4] for i in range(len(n))]
+    bt = Bt.Batch(n, r, seed=7)
+    g = S.Graph(cuda_graph=True)
+    ntask = Bt.insert(g, bt, tiles, split=True)
+    assert ntask == g.sizes()[0]
+    assert g.run()[0] == 0
+    for i in range(len(n)):
+        check_problem(bt, i, tiles[i])
+    first = (bt.A.clone(), bt.X.clone())
+    g.reset()
+    bt.restore()
+    assert g.run()[0] == 0
+    assert torch.equal(bt.A, first[0]) and torch.equal(bt.X, first[1])
+    g.close()
+    for i in (0, 5, 31):
+        one = Bt.Batch([n[i]], [r[i]], seed=7, fill=False)
+        one.a_view(0).copy_(bt.A0[int(bt.a_off[i]):int(bt.a_off[i]) + int(n[i]) ** 2].view(int(n[i]), -1))
+        one.x_view(0).copy_(bt.X0[int(bt.x_off[i]):int(bt.x_off[i]) + int(n[i] * r[i])].view(int(n[i]), -1))
+        g1 = S.Graph()
+        Bt.insert(g1, one, [tiles[i]], split=True)
+        assert g1.run()[0] == 0
+        assert torch.equal(one.a_view(0), bt.a_view(i)) and torch.equal(one.x_view(0), bt.x_view(i))
+        g1.close()
+    best, table = Bt.autotune([96, 320], copies=8, split=True)
+    assert set(best) == {96, 320} and all(t > 0 for v in table.values() for t in v.values())
