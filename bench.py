@@ -1418,17 +1418,18 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
     A, X = torch.empty_like(A0), torch.empty_like(X0)
     flops_fs = cholesky.cholesky_flops(n, 1)
     res = {}
-    for name, ex, rederive, cg, solve in (
-            ("persistent", spx.EXEC_PERSISTENT, False, False, True),
-            ("persistent_bottom_level", -1, False, False, True),
-            ("persistent_factor_only", spx.EXEC_PERSISTENT, False, False, False),
-            ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False, True),
-            ("per_task", spx.EXEC_PER_TASK, False, False, True),
-            ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True, True),
-            ("streams", spx.EXEC_STREAMS, False, False, True)):
+    for name, ex, rederive, cg, solve, la in (
+            ("persistent", spx.EXEC_PERSISTENT, False, False, True, 1),
+            ("persistent_all_critical", spx.EXEC_PERSISTENT, False, False, True, 2),
+            ("persistent_bottom_level", -1, False, False, True, 1),
+            ("persistent_factor_only", spx.EXEC_PERSISTENT, False, False, False, 1),
+            ("persistent_insert_derive", spx.EXEC_PERSISTENT, True, False, True, 1),
+            ("per_task", spx.EXEC_PER_TASK, False, False, True, 1),
+            ("per_task_cudagraph", spx.EXEC_PER_TASK, False, True, True, 1),
+            ("streams", spx.EXEC_STREAMS, False, False, True, 1)):
         g = (spx.Graph(priorities=1) if ex < 0 else spx.Graph(executor=ex, cuda_graph=cg))
         Xs = X if solve else None
-        ntasks = cholesky.cholesky_graph(g, A, b, Xs)
+        ntasks = cholesky.cholesky_graph(g, A, b, Xs, lookahead=la)
         lat = []
         for i in range(reps + 5):
             A.copy_(A0)
@@ -1437,7 +1438,7 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
             t0 = time.perf_counter()
             if rederive and i > 0:
                 g.clear()
-                cholesky.cholesky_graph(g, A, b, Xs)
+                cholesky.cholesky_graph(g, A, b, Xs, lookahead=la)
             g.execute()
             rc, _ = g.wait()
             t1 = time.perf_counter()
@@ -1456,7 +1457,8 @@ def small_latency(spx, cholesky, inputs, torch, reps=200):
                        "execute->wait over %d runs; the graph is reset and re-run, except "
                        "persistent_insert_derive, which inserts and derives every time; "
                        "_bottom_level: priorities from the critical path (cfg.priorities = 1) "
-                       "instead of the look-ahead marks" % reps)
+                       "instead of the look-ahead marks; _all_critical: every task on the "
+                       "critical-path queue with the finer parts (lookahead = 2)" % reps)
     res["critical_path"] = critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b)
     res["critical_path_bottom_level"] = critical_path_trace(spx, cholesky, torch, A, A0, X, X0, b,
                                                             priorities=1)

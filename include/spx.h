@@ -554,7 +554,10 @@ void spx_graph_destroy(spx_graph_t g);
  *           (the last tile row/column is ragged when b does not divide n).
  *   dev_X   n x nrhs FP64 row-major (ldx >= nrhs) or NULL.
  *   lookahead  1: POTRF, TRSM, SYRK, the GEMMs of the next panel column and
- *           the diagonal solves get the high priority.
+ *           the diagonal solves get the high priority; 2: every task on
+ *           the critical-path queue with the finer parts (the latency form
+ *           for small problems, whose DAG is essentially one chain); 0: all
+ *           tasks normal.
  *   prec    SPX_F64.
  *   out_ntasks  number of tasks inserted (may be NULL).
  * Errors: as spx_tile_register / spx_task_insert; tasks inserted before an

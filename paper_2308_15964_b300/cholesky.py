@@ -30,7 +30,7 @@ def cholesky_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True, prec
     spx._check(spx.lib.spx_cholesky_insert(
         g._h, _ptr(A), n, A.stride(0), b, _ptr(X) if X is not None else None,
         X.shape[1] if X is not None else 0, X.stride(0) if X is not None else 0,
-        1 if lookahead else 0, prec, ctypes.byref(nt)), "spx_cholesky_insert")
+        int(lookahead), prec, ctypes.byref(nt)), "spx_cholesky_insert")
     g._keep.extend([A] + ([X] if X is not None else []))
     return nt.value
 
@@ -66,7 +66,7 @@ def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True
         g._h, _ptr(A), n, A.stride(0), b, _ptr(S), S.numel() * S.element_size(),
         _ptr(V) if V is not None else None, V.stride(0) if V is not None else 0,
         1 if fuse_panel else 0, _ptr(X) if X is not None else None, X.shape[1] if X is not None else 0,
-        X.stride(0) if X is not None else 0, 1 if lookahead else 0, ctypes.byref(nt)),
+        X.stride(0) if X is not None else 0, int(lookahead), ctypes.byref(nt)),
         "spx_cholesky_insert_ozaki")
     g._keep.extend([A, S] + ([X] if X is not None else []) + ([V] if V is not None else []))
     return nt.value

@@ -105,11 +105,13 @@ int insert_cholesky(spx_graph_t g, double* dev_A, int n, int lda, int b, void* d
   const int hi = lookahead ? 1 : 0;
   const int crit = lookahead ? 2 : 0;  // critical path: high priority, finer parts
   long long count = 0;
+  // lookahead >= 2 (small problems, where the whole DAG is one chain): every
+  // task on the critical-path queue, cut into the finer parts
   auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
                  int prio, unsigned* id, int p = SPX_F64) {
     const unsigned* hp = hs.begin();
     const int* mp = ms.begin();
-    int r = spx_task_insert(g, op, hp, mp, (int)hs.size(), prio, p, id);
+    int r = spx_task_insert(g, op, hp, mp, (int)hs.size(), lookahead >= 2 ? 2 : prio, p, id);
     if (r == SPX_OK) ++count;
     return r;
   };

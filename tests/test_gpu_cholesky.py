@@ -91,7 +91,7 @@ def test_determinism_and_executors(S):
     outs = [run_cholesky(A, b, B), run_cholesky(A, b, B, executor=S.EXEC_PER_TASK),
             run_cholesky(A, b, B, executor=S.EXEC_STREAMS),
             run_cholesky(A, b, B, no_split=True), run_cholesky(A, b, B, num_ctas=3),
-            run_cholesky(A, b, B, lookahead=False)]
+            run_cholesky(A, b, B, lookahead=False), run_cholesky(A, b, B, lookahead=2)]
     for o in outs:
         assert o[0] == 0
         assert np.array_equal(o[2], ref[2]) and np.array_equal(o[3], ref[3])
