@@ -463,6 +463,17 @@ int spx_stream_begin(spx_graph_t g, void* stream, int max_tasks, int max_tiles,
 int spx_stream_flush(spx_graph_t g);
 int spx_stream_end(spx_graph_t g);
 
+/* Copy tile data from host memory to the device while streaming, ordered
+ * before the next flush: the tasks flushed after this call read the copied
+ * data (the copy runs on the stream's upload stream, ahead of the count the
+ * kernel polls).  rows x width_bytes from host_src (row pitch spitch) to
+ * dev_dst (row pitch dpitch), as cudaMemcpy2DAsync; host_src should be
+ * pinned (a pageable source is staged before the call returns).  The data
+ * must not be touched by a task published earlier.
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_STATE (not streaming), SPX_ERR_CUDA. */
+int spx_stream_copy_h2d(spx_graph_t g, void* dev_dst, size_t dpitch, const void* host_src,
+                        size_t spitch, size_t width_bytes, size_t rows);
+
 /* The predecessor lists of the inserted tasks as the host-side derivation of
  * a stream computes them (CSR by task: pred_ptr[ntasks + 1], pred[cap]); no
  * device work.  The edge set is the device derivation's (spx_graph_edges),
@@ -628,6 +639,28 @@ int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, int lda, int 
                               long long S_bytes, double* dev_V, int ldv, int fuse_panel,
                               double* dev_X, int nrhs, int ldx, int lookahead,
                               long long* out_ntasks);
+
+/* End to end from host memory: the split-FP64 Cholesky of
+ * spx_cholesky_insert_ozaki (inverse panels, look-ahead marks, no solve) of
+ * the matrix in host_A (n x n FP64 row-major, ld_host; pinned memory for
+ * asynchronous copies; the lower triangle is read), its factor written into
+ * the lower triangle of host_L (same layout; the strict upper part of the
+ * diagonal blocks receives dev_A's, the rest of the upper triangle is not
+ * written).  The column blocks of the lower triangle are copied into dev_A
+ * (n x n, lda) while the persistent kernel runs (streaming insertion: block
+ * column j's first-step tasks are published after its copy, block 0 is
+ * copied before the launch), then the factor's column blocks are copied
+ * back after the run.  The same tasks and per-tile order as
+ * spx_cholesky_insert_ozaki: the factor is bit-identical.  g: a graph being
+ * built with no tasks (persistent executor); dev_S, S_bytes, dev_V, ldv as
+ * in spx_cholesky_insert_ozaki (dev_V required); stream: the launch stream,
+ * synchronised before the return.  Returns SPX_OK or SPX_NOT_SPD (info: the
+ * failed column, 1-based) like spx_graph_wait, or an error as
+ * spx_stream_begin / spx_task_insert / spx_graph_wait.  After the return
+ * the graph is finished (spx_graph_reset / spx_graph_clear to reuse). */
+int spx_cholesky_host_ozaki(spx_graph_t g, const double* host_A, double* host_L, int n,
+                            int ld_host, int b, double* dev_A, int lda, void* dev_S,
+                            long long S_bytes, double* dev_V, int ldv, void* stream, int* info);
 
 /* Insert only the block solve tasks L L^T Y = X (Y over X) for a factor L
  * already in dev_L (lower triangle, tiles b x b).  Used for the correction

@@ -72,6 +72,34 @@ def cholesky_ozaki_graph(g: spx.Graph, A, b: int, X=None, lookahead: bool = True
     return nt.value
 
 
+def cholesky_host_ozaki(g: spx.Graph, A_host, L_host, b: int, dev_A=None, S=None, V=None,
+                        stream=None):
+    """spx_cholesky_host_ozaki: the split-path Cholesky (inverse panels) of the
+    host matrix A_host (pinned CPU float64 tensor, row-major), its factor in
+    L_host's lower triangle; the column blocks are uploaded while the kernel
+    runs.  Device buffers are allocated when not given.  Returns (status,
+    info): spx.OK, or spx.NOT_SPD with the failed column."""
+    import torch
+    n = A_host.shape[0]
+    assert A_host.stride(1) == 1 and L_host.stride(0) == A_host.stride(0) and L_host.stride(1) == 1
+    if dev_A is None:
+        dev_A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    if S is None:
+        S = ozaki_store(n, b, dev_A.device, inverse_panels=True)
+    if V is None:
+        V = torch.empty((n, min(b, n)), dtype=torch.float64, device=dev_A.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    info = ctypes.c_int()
+    rc = spx.lib.spx_cholesky_host_ozaki(
+        g._h, _ptr(A_host), _ptr(L_host), n, A_host.stride(0), b, _ptr(dev_A), dev_A.stride(0),
+        _ptr(S), S.numel() * S.element_size(), _ptr(V), V.stride(0),
+        ctypes.c_void_p(st.cuda_stream), ctypes.byref(info))
+    if rc not in (spx.OK, spx.NOT_SPD):
+        spx._check(rc, "spx_cholesky_host_ozaki")
+    g._keep.extend([dev_A, S, V])
+    return rc, info.value
+
+
 def gemm_graph(g: spx.Graph, A, B, C, b: int, commutative: bool = False, atomic: bool = False):
     """Insert C += A B, one task per (i, j, k), i and j outer, k inner, with a
     WRITE, COMMUTATIVE_WRITE (commutative) or ATOMIC_WRITE (atomic) on C_ij."""

@@ -1322,6 +1322,19 @@ int spx_stream_flush(spx_graph_t g) {
   return stream_publish(g);
 }
 
+int spx_stream_copy_h2d(spx_graph_t g, void* dev_dst, size_t dpitch, const void* host_src,
+                        size_t spitch, size_t width_bytes, size_t rows) {
+  if (!g || !dev_dst || !host_src || width_bytes > dpitch || width_bytes > spitch)
+    return SPX_ERR_INVALID_ARG;
+  if (g->state != kStreaming) return SPX_ERR_STATE;
+  if (g->s_fail) return g->s_fail;
+  if (!rows || !width_bytes) return SPX_OK;
+  // on the upload stream: ahead of the next publication's count
+  const cudaError_t e = cudaMemcpy2DAsync(dev_dst, dpitch, host_src, spitch, width_bytes, rows,
+                                          cudaMemcpyHostToDevice, g->s_up);
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
 int spx_stream_end(spx_graph_t g) {
   if (!g) return SPX_ERR_INVALID_ARG;
   if (g->state != kStreaming) return SPX_ERR_STATE;

@@ -14,6 +14,8 @@
 #include <initializer_list>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "spx.h"
 
 namespace {
@@ -216,6 +218,95 @@ extern "C" int spx_cholesky_insert_ozaki(spx_graph_t g, double* dev_A, int n, in
   if (!spx_ozaki_slot_bytes(b) || fuse_panel < 0 || fuse_panel > 1) return SPX_ERR_INVALID_ARG;
   return insert_cholesky(g, dev_A, n, lda, b, dev_S, 0, true, dev_X, nrhs, ldx, lookahead,
                          SPX_F64_OZAKI, out_ntasks, dev_V, ldv, S_bytes, fuse_panel != 0);
+}
+
+extern "C" int spx_cholesky_host_ozaki(spx_graph_t g, const double* host_A, double* host_L,
+                                       int n, int ld_host, int b, double* dev_A, int lda,
+                                       void* dev_S, long long S_bytes, double* dev_V, int ldv,
+                                       void* stream, int* info) {
+  if (info) *info = 0;
+  if (!g || !host_A || !host_L || !dev_A || !dev_V || n < 1 || ld_host < n || lda < n ||
+      !spx_ozaki_slot_bytes(b) || ldv < (b < n ? b : n))
+    return SPX_ERR_INVALID_ARG;
+  Tiles A;
+  int rc = register_ozaki_tiles(g, dev_A, n, lda, b, (char*)dev_S, S_bytes, A, true);
+  if (rc != SPX_OK) return rc;
+  const int T = A.T;
+  const long long slot = spx_ozaki_slot_bytes(b);
+  std::vector<unsigned> V(T);
+  for (int k = 0; k < T && rc == SPX_OK; ++k) {  // V_k owns slot T (T - 1) / 2 + k
+    const int bk = n - k * b < b ? n - k * b : b;
+    rc = spx_tile_register(g, dev_V + (size_t)k * b * ldv, bk, bk, ldv, SPX_DT_F64,
+                           (char*)dev_S + ((long long)T * (T - 1) / 2 + k) * slot, b, &V[k]);
+  }
+  if (rc != SPX_OK) return rc;
+  // the task list of spx_cholesky_insert_ozaki (inverse panels, look-ahead
+  // marks), its first step ordered by column so that column block j's tasks
+  // follow its upload (same accesses per tile in the same order: same DAG)
+  long long tasks = T;
+  for (int k = 0; k < T; ++k) {
+    const long long r = T - k - 1;
+    tasks += 1 + (r > 0 ? 1 : 0) + (r > 1 ? r - 1 : 0) + r + r * (r - 1) / 2;
+  }
+  const long long cap = tasks + (long long)T * T + 64;  // relays
+  const int R = SPX_READ, W = SPX_WRITE, P = SPX_F64_OZAKI;
+  auto ins = [&](int op, std::initializer_list<unsigned> hs, std::initializer_list<int> ms,
+                 int prio, int prec, unsigned* id = nullptr) {
+    return spx_task_insert(g, op, hs.begin(), ms.begin(), (int)hs.size(), prio, prec, id);
+  };
+  auto head = [&](int k) {  // POTRF, critical solve, inversion, inverse panel products
+    unsigned t = 0;
+    int r = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, 2, SPX_F64, &t);
+    if (r == SPX_OK) r = spx_task_set_arg(g, t, (long long)k * b);
+    if (r == SPX_OK && k + 1 < T) r = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, 2, P);
+    if (r == SPX_OK) r = ins(SPX_OP_TRTRI, {A.at(k, k), V[k]}, {R, W}, 1, P);
+    for (int i = k + 2; i < T && r == SPX_OK; ++i)
+      r = ins(SPX_OP_TRSM_INV, {V[k], A.at(i, k)}, {R, W}, 1, P);
+    return r;
+  };
+  auto update = [&](int k, int j) {  // SYRK(j, k) and the GEMMs of column j
+    int r = ins(SPX_OP_SYRK, {A.at(j, k), A.at(j, j)}, {R, W}, j == k + 1 ? 2 : 1, P);
+    for (int i = j + 1; i < T && r == SPX_OK; ++i)
+      r = ins(SPX_OP_GEMM_NT_SUB, {A.at(i, k), A.at(j, k), A.at(i, j)}, {R, R, W},
+              j == k + 1 ? (i == k + 2 ? 2 : 1) : 0, P);
+    return r;
+  };
+  // column block 0 on the launch stream, ahead of the kernel; its tasks (split
+  // prec: they fix the kernel family) inserted before the stream begins
+  const int w0 = n < b ? n : b;
+  rc = spx_copy2d(dev_A, (size_t)lda * 8, host_A, (size_t)ld_host * 8, (size_t)w0 * 8, (size_t)n,
+                  stream);
+  if (rc == SPX_OK) rc = head(0);
+  if (rc == SPX_OK)
+    rc = spx_stream_begin(g, stream, (int)cap, (int)(T * (T + 1) / 2 + T), 3 * cap, 16 * cap);
+  if (rc != SPX_OK) return rc;
+  for (int j = 1; j < T && rc == SPX_OK; ++j) {  // upload column block j, then its step-0 tasks
+    const int c0 = j * b, w = n - c0 < b ? n - c0 : b;
+    rc = spx_stream_copy_h2d(g, dev_A + (size_t)c0 * lda + c0, (size_t)lda * 8,
+                             host_A + (size_t)c0 * ld_host + c0, (size_t)ld_host * 8,
+                             (size_t)w * 8, (size_t)(n - c0));
+    if (rc == SPX_OK) rc = update(0, j);
+    if (rc == SPX_OK) rc = spx_stream_flush(g);
+  }
+  for (int k = 1; k < T && rc == SPX_OK; ++k) {
+    rc = head(k);
+    for (int j = k + 1; j < T && rc == SPX_OK; ++j) rc = update(k, j);
+    if (rc == SPX_OK) rc = spx_stream_flush(g);
+  }
+  const int end_rc = spx_stream_end(g);
+  int wrc = spx_graph_wait(g, 0, info);
+  if (rc == SPX_OK) rc = end_rc;
+  if (rc == SPX_OK) rc = wrc;
+  if (rc != SPX_OK && rc != SPX_NOT_SPD) return rc;
+  // the factor's column blocks back to the host
+  for (int j = 0; j < T; ++j) {
+    const int c0 = j * b, w = n - c0 < b ? n - c0 : b;
+    const int e = spx_copy2d(host_L + (size_t)c0 * ld_host + c0, (size_t)ld_host * 8,
+                             dev_A + (size_t)c0 * lda + c0, (size_t)lda * 8, (size_t)w * 8,
+                             (size_t)(n - c0), stream);
+    if (e != SPX_OK) return e;
+  }
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? rc : SPX_ERR_CUDA;
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,

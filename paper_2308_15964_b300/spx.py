@@ -78,6 +78,9 @@ def _load():
         "spx_cholesky_insert": (I, [P, P, I, I, I, P, I, I, I, I, P]),
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
         "spx_gemm_insert_ozaki": (I, [P, P, P, P, I, I, I, I, P, LL, P]),
+        "spx_cholesky_host_ozaki": (I, [P, P, P, I, I, I, P, I, P, LL, P, I, P, P]),
+        "spx_stream_copy_h2d": (I, [P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_size_t,
+                                    ctypes.c_size_t]),
         "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
         "spx_tc_gemm_nt": (I, [P, I, I, I, P, I, P, I, I, I, P, P]),
         "spx_lowp_register": (I, [P, P, I, I, I, I, P]),

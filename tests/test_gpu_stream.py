@@ -204,3 +204,50 @@ def test_stream_split_cholesky_bit_identical(S):
     torch.cuda.synchronize()
     assert np.array_equal(np.tril(Ad.cpu().numpy()), Lref)
     g.close()
+
+
+# --- end to end from host memory (spx_cholesky_host_ozaki) ------------------
+
+@pytest.mark.parametrize("n,b", [(2000, 256), (1536, 128), (512, 512), (1100, 512)])
+def test_host_entry_bit_identical(S, n, b):
+    """The host-buffer entry (column blocks uploaded while the kernel runs)
+    gives the same factor, bit for bit, as the device-resident split graph,
+    and writes nothing above the diagonal blocks of L_host."""
+    import torch
+    from paper_2308_15964_b300 import cholesky, inputs
+    A0 = inputs.spd_matrix(n, 0.1, seed=n + b)
+    Ah = A0.clone().pin_memory()
+    Lh = torch.full((n, n), 7.0, dtype=torch.float64).pin_memory()
+    g = S.Graph()
+    rc, info = cholesky.cholesky_host_ozaki(g, Ah, Lh, b)
+    g.close()
+    assert rc == 0 and info == 0
+    Ad = A0.cuda()
+    V = torch.zeros((n, min(b, n)), dtype=torch.float64, device="cuda")
+    g = S.Graph()
+    cholesky.cholesky_ozaki_graph(g, Ad, b, V=V)
+    assert g.run()[0] == 0
+    torch.cuda.synchronize()
+    g.close()
+    L = Lh.numpy()
+    want = Ad.cpu().numpy()
+    assert np.array_equal(np.tril(L), np.tril(want))
+    # above the diagonal blocks: untouched
+    T = -(-n // b)
+    for j in range(1, T):
+        assert (L[:j * b, j * b:(j + 1) * b] == 7.0).all()
+    assert torch.equal(Ah, A0.pin_memory())  # the input is only read
+
+
+def test_host_entry_not_spd(S):
+    import torch
+    from paper_2308_15964_b300 import cholesky, inputs
+    n, b = 1024, 256
+    A0 = inputs.spd_matrix(n, 1.0, seed=3)
+    A0[700, 700] = -5.0
+    Ah = A0.clone().pin_memory()
+    Lh = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+    g = S.Graph()
+    rc, info = cholesky.cholesky_host_ozaki(g, Ah, Lh, b)
+    g.close()
+    assert rc == S.NOT_SPD and info == 701
