@@ -553,8 +553,9 @@ def main():
                           "h2d_bytes_per_step": lower, "d2h_bytes_per_step": lower,
                           "ms_per_step": statistics.mean(e2e),
                           "how": "spx_cholesky_host_ozaki: pinned host matrix in, factor out; "
-                                 "column blocks of the lower triangle uploaded while the kernel "
-                                 "runs", "whole_matrix_copies": whole}
+                                 "the lower triangle's column blocks uploaded while the kernel "
+                                 "runs, the factor's downloaded as each one's last writers "
+                                 "finish", "whole_matrix_copies": whole}
         else:
             out["e2e"] = whole
         del Ah, Lh

@@ -506,6 +506,15 @@ int spx_graph_edges(spx_graph_t g, unsigned* row_ptr, unsigned* col, unsigned* i
  * every edge u->v, end[u] < start[v].  Errors: SPX_ERR_STATE. */
 int spx_graph_tickets(spx_graph_t g, unsigned* start, unsigned* end);
 
+/* Completion of tasks of a running (or streaming, or finished) graph on the
+ * persistent executor: done[i] = 1 when task tasks[i] has finished (its
+ * results are in memory and no later task of the graph writes them unless it
+ * depends on it), else 0.  Reads a snapshot of the device's end tickets by
+ * the copy engine while the kernel runs (microseconds; poll with a pause).
+ * Errors: SPX_ERR_INVALID_ARG, SPX_ERR_BAD_HANDLE, SPX_ERR_STATE (not
+ * launched, another executor, a batched member), SPX_ERR_CUDA. */
+int spx_graph_tasks_done(spx_graph_t g, const unsigned* tasks, int count, int* done);
+
 /* Trace of the last run with cfg.trace = 1 (paper, section "Visualization"):
  * 4 values per task: start ns, end ns (device %globaltimer), SM id of the
  * first part, number of parts.  Errors: SPX_ERR_STATE (tracing off). */

@@ -196,6 +196,8 @@ struct spx_graph {
   StreamCtl s_ctl_host{};                      // the values last sent to the device
   StreamCtl* s_ctl = nullptr;                  // the kernel's copy (device memory)
   cudaStream_t s_up = nullptr;                 // uploads while the kernel runs
+  cudaStream_t done_stream = nullptr;          // completion snapshots (spx_graph_tasks_done)
+  std::vector<uint32_t> done_buf;
   size_t s_off_cnt = 0, s_off_succ = 0, s_off_pptr = 0, s_off_pred = 0;
   cudaStream_t xs[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1441,7 +1443,31 @@ int spx_graph_tickets(spx_graph_t g, unsigned* start, unsigned* end) {
   cudaError_t e = cudaSuccess;
   if (start) e = cudaMemcpy(start, g->dg.t_start, N * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && end) e = cudaMemcpy(end, g->dg.t_end, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && end)
+    for (size_t i = 0; i < N; ++i) end[i] &= ~kTaskDone;  // the ticket alone
   return e == cudaSuccess ? SPX_OK : cuda_fail(e);
+}
+
+int spx_graph_tasks_done(spx_graph_t g, const unsigned* tasks, int count, int* done) {
+  if (!g || count < 0 || (count && (!tasks || !done))) return SPX_ERR_INVALID_ARG;
+  if (g->state != kRunning && g->state != kStreaming && g->state != kDone) return SPX_ERR_STATE;
+  if (g->cfg.executor != SPX_EXEC_PERSISTENT || g->batch_of) return SPX_ERR_STATE;
+  const size_t N = g->tasks.size();
+  for (int i = 0; i < count; ++i)
+    if (tasks[i] >= N) return SPX_ERR_BAD_HANDLE;
+  if (!g->done_stream) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&g->done_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  g->done_buf.resize(N);
+  // a snapshot of the end tickets, read by the copy engine while the kernel runs
+  cudaError_t e = cudaMemcpyAsync(g->done_buf.data(), g->dg.t_end, N * 4, cudaMemcpyDeviceToHost,
+                                  g->done_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->done_stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < count; ++i)
+    done[i] = g->state == kDone || (g->done_buf[tasks[i]] & kTaskDone) ? 1 : 0;
+  return SPX_OK;
 }
 
 int spx_graph_trace(spx_graph_t g, unsigned long long* rec) {
@@ -1670,6 +1696,7 @@ void spx_graph_destroy(spx_graph_t g) {
   if (g->pinned) cudaFreeHost(g->pinned);
   if (g->host_rs) cudaFreeHost(g->host_rs);
   if (g->s_up) cudaStreamDestroy(g->s_up);
+  if (g->done_stream) cudaStreamDestroy(g->done_stream);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   for (int i = 0; i < 4; ++i) {

@@ -1066,6 +1066,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(DevGraph g) {
           if (tid == 0) {
             __threadfence();
             atomicAdd(&rs->done.v, 1u);
+            atomicOr(&g.t_end[u], kTaskDone);  // the host may copy the task's results now
           }
         }
       }

@@ -18,6 +18,9 @@ constexpr uint32_t kMaxParts = 1u << kPartBits;
 constexpr uint32_t kMaxTasks = (1u << (32 - kPartBits)) - 2;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // free queue slot
 constexpr uint32_t kExit = 0xFFFFFFFEu;   // pop result: leave the loop
+// Top bit of a task's end ticket: set once the task has finished (graph
+// executors; tickets themselves stay below 2^31).
+constexpr uint32_t kTaskDone = 0x80000000u;
 // Streaming (tasks inserted while the persistent kernel runs): successor
 // slots per task, filled by the admission of each successor; a task's slot
 // count gets kSuccClosed when it finishes (later attachments see it done).

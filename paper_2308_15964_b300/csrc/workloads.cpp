@@ -10,6 +10,7 @@
 //     that applies them as products (TRMM), for refinement;
 //   * the scheduler-overhead pattern of the paper's engine benchmark: chains
 //     of tasks that only wait.
+#include <chrono>
 #include <cstdint>
 #include <initializer_list>
 #include <vector>
@@ -254,14 +255,22 @@ extern "C" int spx_cholesky_host_ozaki(spx_graph_t g, const double* host_A, doub
                  int prio, int prec, unsigned* id = nullptr) {
     return spx_task_insert(g, op, hs.begin(), ms.begin(), (int)hs.size(), prio, prec, id);
   };
+  // the last writers of column block k: POTRF(k), its panel's solve and products
+  std::vector<std::vector<unsigned>> last(T);
   auto head = [&](int k) {  // POTRF, critical solve, inversion, inverse panel products
     unsigned t = 0;
     int r = ins(SPX_OP_POTRF, {A.at(k, k)}, {W}, 2, SPX_F64, &t);
+    if (r == SPX_OK) last[k].push_back(t);
     if (r == SPX_OK) r = spx_task_set_arg(g, t, (long long)k * b);
-    if (r == SPX_OK && k + 1 < T) r = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, 2, P);
+    if (r == SPX_OK && k + 1 < T) {
+      r = ins(SPX_OP_TRSM, {A.at(k, k), A.at(k + 1, k)}, {R, W}, 2, P, &t);
+      if (r == SPX_OK) last[k].push_back(t);
+    }
     if (r == SPX_OK) r = ins(SPX_OP_TRTRI, {A.at(k, k), V[k]}, {R, W}, 1, P);
-    for (int i = k + 2; i < T && r == SPX_OK; ++i)
-      r = ins(SPX_OP_TRSM_INV, {V[k], A.at(i, k)}, {R, W}, 1, P);
+    for (int i = k + 2; i < T && r == SPX_OK; ++i) {
+      r = ins(SPX_OP_TRSM_INV, {V[k], A.at(i, k)}, {R, W}, 1, P, &t);
+      if (r == SPX_OK) last[k].push_back(t);
+    }
     return r;
   };
   auto update = [&](int k, int j) {  // SYRK(j, k) and the GEMMs of column j
@@ -294,19 +303,54 @@ extern "C" int spx_cholesky_host_ozaki(spx_graph_t g, const double* host_A, doub
     if (rc == SPX_OK) rc = spx_stream_flush(g);
   }
   const int end_rc = spx_stream_end(g);
-  int wrc = spx_graph_wait(g, 0, info);
-  if (rc == SPX_OK) rc = end_rc;
-  if (rc == SPX_OK) rc = wrc;
-  if (rc != SPX_OK && rc != SPX_NOT_SPD) return rc;
-  // the factor's column blocks back to the host
-  for (int j = 0; j < T; ++j) {
+  // the factor's column blocks back to the host, each as soon as its last
+  // writers have finished (copy engine, beside the running kernel)
+  cudaStream_t down = nullptr;
+  if (cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) down = nullptr;
+  int next = 0, copy_rc = SPX_OK;
+  auto download = [&](int j) {
     const int c0 = j * b, w = n - c0 < b ? n - c0 : b;
     const int e = spx_copy2d(host_L + (size_t)c0 * ld_host + c0, (size_t)ld_host * 8,
                              dev_A + (size_t)c0 * lda + c0, (size_t)lda * 8, (size_t)w * 8,
-                             (size_t)(n - c0), stream);
-    if (e != SPX_OK) return e;
+                             (size_t)(n - c0), down ? (void*)down : stream);
+    if (copy_rc == SPX_OK) copy_rc = e;
+  };
+  int wrc = SPX_ERR_TIMEOUT;
+  bool finished = false;
+  auto since = std::chrono::steady_clock::now();
+  while (rc == SPX_OK && end_rc == SPX_OK && down) {
+    std::vector<int> done;
+    while (next < T) {
+      done.assign(last[next].size(), 0);
+      if (spx_graph_tasks_done(g, last[next].data(), (int)last[next].size(), done.data()) != SPX_OK)
+        break;
+      bool all = true;
+      for (int d : done) all = all && d;
+      if (!all) break;
+      download(next++);
+      since = std::chrono::steady_clock::now();
+    }
+    if (next == T) break;
+    wrc = spx_graph_wait(g, 200000, info);  // a 0.2 ms pause, or the run's end
+    if (wrc != SPX_ERR_TIMEOUT) {
+      finished = true;
+      break;
+    }
+    // a device watchdog also answers SPX_ERR_TIMEOUT: stop polling when no
+    // column has finished for a long time and wait for the status below
+    if (std::chrono::steady_clock::now() - since > std::chrono::seconds(30)) break;
   }
-  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? rc : SPX_ERR_CUDA;
+  if (!finished) wrc = spx_graph_wait(g, 0, info);
+  if (rc == SPX_OK) rc = end_rc;
+  if (rc == SPX_OK) rc = wrc;
+  if (rc == SPX_OK || rc == SPX_NOT_SPD)
+    while (next < T) download(next++);
+  const bool synced = (!down || cudaStreamSynchronize(down) == cudaSuccess) &&
+                      cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess;
+  if (down) cudaStreamDestroy(down);
+  if (rc != SPX_OK && rc != SPX_NOT_SPD) return rc;
+  if (copy_rc != SPX_OK) return copy_rc;
+  return synced ? rc : SPX_ERR_CUDA;
 }
 
 extern "C" int spx_solve_insert(spx_graph_t g, double* dev_L, int n, int ld, int b,

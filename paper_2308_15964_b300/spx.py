@@ -79,6 +79,7 @@ def _load():
         "spx_gemm_insert": (I, [P, P, P, P, I, I, I, I, P]),
         "spx_gemm_insert_ozaki": (I, [P, P, P, P, I, I, I, I, P, LL, P]),
         "spx_cholesky_host_ozaki": (I, [P, P, P, I, I, I, P, I, P, LL, P, I, P, P]),
+        "spx_graph_tasks_done": (I, [P, P, I, P]),
         "spx_stream_copy_h2d": (I, [P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_size_t,
                                     ctypes.c_size_t]),
         "spx_cholesky_insert_batch": (I, [P, I, P, P, P, P, P, P, P, I, I, P]),
@@ -273,6 +274,13 @@ class Graph:
         e = np.zeros(n, np.uint32)
         _check(lib.spx_graph_tickets(self._h, _ptr(s), _ptr(e)), "spx_graph_tickets")
         return s, e
+
+    def tasks_done(self, tasks):
+        """spx_graph_tasks_done: 1 for each task that has finished, else 0."""
+        t = np.ascontiguousarray(tasks, dtype=np.uint32)
+        d = np.zeros(len(t), dtype=np.int32)
+        _check(lib.spx_graph_tasks_done(self._h, _ptr(t), len(t), _ptr(d)), "spx_graph_tasks_done")
+        return d
 
     def trace(self):
         n = self.sizes()[0]

@@ -251,3 +251,25 @@ def test_host_entry_not_spd(S):
     rc, info = cholesky.cholesky_host_ozaki(g, Ah, Lh, b)
     g.close()
     assert rc == S.NOT_SPD and info == 701
+
+
+def test_tasks_done_while_streaming(S):
+    """spx_graph_tasks_done: every task of a finished stream reads as done;
+    tasks published behind a held chain read as not done while it runs."""
+    import torch
+    g = S.Graph()
+    X = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    h = g.register_tensor(X)
+    t0 = g.insert(S.OP_SPIN, [h], [S.WRITE])
+    g.set_arg(t0, 300_000_000)
+    g.stream_begin(max_tasks=64, max_tiles=4, max_records=64, max_preds=64)
+    ids = [g.insert(S.OP_NOP, [h], [S.WRITE]) for _ in range(5)]
+    g.stream_flush()
+    early = g.tasks_done([t0] + ids)
+    g.stream_end()
+    assert g.wait()[0] == 0
+    assert not early[1:].any()                   # behind the 0.3 s spin
+    assert g.tasks_done([t0] + ids).all()
+    start, end = g.tickets()
+    assert (end < 2 ** 31).all()                 # the ticket alone
+    g.close()
