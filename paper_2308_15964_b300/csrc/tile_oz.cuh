@@ -38,7 +38,7 @@
 // the planes t = 0..7-s of B stacked along N (64 (8 - s) rows, at most 256
 // per MMA) with output block t landing in accumulator s + t.  The K step's
 // operands (8 planes x 128 rows of A, 8 planes x 64 rows of B, 48 KB) arrive
-// by one 5-D TMA box each (32-byte swizzle), three stages.  Up to four
+// by one 5-D TMA box each (32-byte swizzle), three stages.  Up to eight
 // column blocks of one row block form a pipelined group: the drain of a
 // block's accumulators and its read-modify-write overlap the next block's
 // loads and MMAs.  Measured in isolation (a harness running the same code):
