@@ -202,3 +202,38 @@ def test_bottom_level_priorities_match_oracle_dag(S, seed):
     want = np.where(slack <= 1e-9 * cp, 2, np.where(slack <= 0.1 * cp, 1, 0))
     assert np.array_equal(got, want), (got, want)
     g.close()
+
+
+def test_streaming_and_host_entry_validation(S):
+    """The streaming upload, the completion query and the host-memory
+    Cholesky refuse bad use on the host, before any device call."""
+    g = S.Graph()
+    h = g.register(FAKE, 8, 8, 8)
+    g.insert(S.OP_NOP, [h], [S.WRITE])
+    buf = (ctypes.c_double * 64)()
+    # not streaming: no upload
+    rc = S.lib.spx_stream_copy_h2d(g._h, ctypes.c_void_p(FAKE), 64, buf, 64, 64, 8)
+    assert rc == S.ERR_STATE
+    # width above a pitch
+    rc = S.lib.spx_stream_copy_h2d(g._h, ctypes.c_void_p(FAKE), 32, buf, 64, 64, 8)
+    assert rc == S.ERR_INVALID_ARG
+    # not launched: no completion snapshot
+    t = np.zeros(1, dtype=np.uint32)
+    d = np.zeros(1, dtype=np.int32)
+    rc = S.lib.spx_graph_tasks_done(g._h, t.ctypes.data_as(ctypes.c_void_p), 1,
+                                    d.ctypes.data_as(ctypes.c_void_p))
+    assert rc == S.ERR_STATE
+    rc = S.lib.spx_graph_tasks_done(g._h, None, -1, None)
+    assert rc == S.ERR_INVALID_ARG
+    g.close()
+    g = S.Graph()
+    info = ctypes.c_int(7)
+    # null host buffers, a tile that is no multiple of 32, a short leading dimension
+    for args in ((None, buf, 64, 64, 64, FAKE, 64), (buf, buf, 64, 64, 48, FAKE, 64),
+                 (buf, buf, 64, 32, 64, FAKE, 64)):
+        ha, hl, n, ldh, b, dA, lda = args
+        rc = S.lib.spx_cholesky_host_ozaki(g._h, ha, hl, n, ldh, b, ctypes.c_void_p(dA), lda,
+                                           ctypes.c_void_p(FAKE), 1 << 20, ctypes.c_void_p(FAKE),
+                                           64, None, ctypes.byref(info))
+        assert rc == S.ERR_INVALID_ARG and info.value == 0
+    g.close()
