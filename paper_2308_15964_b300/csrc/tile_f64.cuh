@@ -246,8 +246,11 @@ __device__ __forceinline__ void store_block(double* dst, int ld, const double (*
 // chain per column is one reciprocal (about 730 clocks) and two dependent
 // FP64 operations instead of a square root and a division (about 2400); at
 // the end l_jj = sqrt(S_jj) and l_ij = S_ij (1 / l_jj).
-// `rc` is w doubles of scratch.
-__device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc) {
+// `rc` and `sc` are w doubles of scratch each.  The FP64 pipe is shared
+// by the SM (two FMAs a clock), so the trailing update competes with the
+// pivot chain: warps 1..7 form the product -S_ij / S_jj of each row once
+// (in sc, behind a barrier of their own) and spend one FMA per entry.
+__device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc, double* sc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     const double d = a[0][0];
@@ -271,14 +274,16 @@ __device__ int potrf_smem(double (*a)[kLds], int w, int* s_info, double* rc) {
         if (d > 0.0) rc[j + 1] = __drcp_rn(d);
         else *s_info = j + 2;
       }
-    } else {
+    } else if (t > 1) {  // rows j+2.. (row j+1's one entry is the pivot)
+      for (int i = j + 2 + tid - 32; i < w; i += kThreads - 32) sc[i] = -a[i][j] * r;
+      asm volatile("bar.sync 1, %0;" ::"n"(kThreads - 32) : "memory");
       for (int p = warp - 1; p < (t + 1) / 2; p += kThreads / 32 - 1) {
         const int ra = p, rb = t - 1 - p;
         const int na = ra + 1, nb = rb != ra ? rb + 1 : 0;
         for (int q = lane + (p == 0 ? 1 : 0); q < na + nb; q += 32) {
           const int rr = q < na ? ra : rb, cc = q < na ? q : q - na;
           const int i = j + 1 + rr, c = j + 1 + cc;
-          a[i][c] = fma(-a[i][j] * r, a[c][j], a[i][c]);
+          a[i][c] = fma(sc[i], a[c][j], a[i][c]);
         }
       }
     }
@@ -435,7 +440,7 @@ __device__ int op_potrf_units(const TileDesc& A, uint32_t phase, uint32_t u0, ui
     case 0: {  // factor the diagonal block
       load_block(s.l, ajj, lda, w, w);
       __syncthreads();
-      const int info = potrf_smem(s.l, w, &s.info, s.rinv);
+      const int info = potrf_smem(s.l, w, &s.info, s.rinv, &s.x[0][0]);
       if (info) return jb + info;
       store_block(ajj, lda, s.l, w, w, true);
       __syncthreads();
