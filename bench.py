@@ -4,16 +4,20 @@
                     [--n 16384] [--tile 512]
 
 One step = the whole hot path on one synthetic SPD matrix resident in HBM:
-insert the task graph (spx_cholesky_insert: POTRF/TRSM/SYRK/GEMM tasks),
-derive the DAG on the device, run it in the persistent kernel, wait.  The
-matrix is restored from a pristine copy before each step (outside the timed
-events).  Inputs (2.1 GB) are larger than L2, so no flush is needed.
+insert the task graph (default: spx_cholesky_insert_ozaki, FP64 results with
+the SYRK/GEMM and inverse-panel products split on the tensor cores;
+--arith f64: spx_cholesky_insert, everything on the FP64 pipe), derive the
+DAG on the device, run it in the persistent kernel, wait.  The matrix is
+restored from a pristine copy before each step (outside the timed events).
+Inputs (2.1 GB) are larger than L2, so no flush is needed.
 
 Printed: one JSON line (rank 0) with GFLOP/s (n^3/3 per step), tasks/s,
-p50/p99 step latency, the one-launch-per-task baseline on the same GPU,
-the small-matrix latency case (n=512, tile 64), the roofline of the
-persistent kernel against the FP64 SIMT peak, the end-to-end number through
-host buffers, the CPU oracle on a bounded sample, and the SM clocks seen.
+p50/p99 step latency, the one-launch-per-task and four-stream baselines on
+the same GPU, the small-matrix latency case (n=512, tile 64), the roofline
+of the persistent kernel (the BF16 tensor rate on the split path, the FP64
+SIMT peak on the FP64 pipe) with its DRAM traffic from the committed ncu
+summary, the end-to-end number through pinned host buffers, the CPU oracle
+on a bounded sample, and the SM clocks seen.
 
 --impl reference times the CPU oracle (plain single-threaded FP64 loops,
 insertion order) on a bounded sample of the same workload.
