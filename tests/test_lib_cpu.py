@@ -237,3 +237,30 @@ def test_streaming_and_host_entry_validation(S):
                                            64, None, ctypes.byref(info))
         assert rc == S.ERR_INVALID_ARG and info.value == 0
     g.close()
+
+
+@pytest.mark.parametrize("n,b", [(1024, 256), (1000, 256), (512, 512), (96, 32)])
+@pytest.mark.parametrize("inverse_panels", [False, True])
+def test_split_store_size_is_what_the_library_requires(S, n, b, inverse_panels):
+    """cholesky.ozaki_store's size passes the library's host-side check, one
+    slot less does not (the exact size gets as far as the first CUDA call,
+    which has no device here); one tile without inverse panels needs none."""
+    from paper_2308_15964_b300 import cholesky
+    store = cholesky.ozaki_store(n, b, device="cpu", inverse_panels=inverse_panels)
+    slot = S.lib.spx_ozaki_slot_bytes(b)
+    T = -(-n // b)
+    need = T * (T - 1) // 2 + (T if inverse_panels else 0)
+    assert store.numel() == max(1, need) * slot
+    cases = [(store.numel(), True)] + ([(store.numel() - slot, False)] if need else [])
+    for nbytes, want_ok in cases:
+        g = S.Graph()
+        nt = ctypes.c_longlong()
+        rc = S.lib.spx_cholesky_insert_ozaki(
+            g._h, ctypes.c_void_p(FAKE), n, n, b, ctypes.c_void_p(FAKE + (1 << 32)),
+            ctypes.c_longlong(nbytes), ctypes.c_void_p(FAKE + (1 << 33)) if inverse_panels else None,
+            b if inverse_panels else 0, 0, None, 0, 0, 1, ctypes.byref(nt))
+        g.close()
+        if want_ok:
+            assert rc in (S.OK, S.ERR_CUDA), rc
+        else:
+            assert rc == S.ERR_INVALID_ARG, rc
